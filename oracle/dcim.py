@@ -1,0 +1,176 @@
+"""Two-level discrete complex image fits (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Follows Sec. 3.2, Steps 1-3 (eqs. ``compleximageapp`` and
+``closedformgreen``):
+
+* Step 1: sample the density on two paths in the k_lz plane,
+      C_ap1: k_lz = i k_l (T0 + t),          0 <= t <= T1   (1st level)
+      C_ap2: k_lz = k_l (1 - t/T0 + i t),     0 <= t <= T0   (2nd level)
+  with T0 = sqrt(((max_m Re k_m + 0.8)/Re k_l)^2 - 1), T1 = 10 and 101
+  samples per level (Sec. 3.3, the Table 3.1 set-up).
+* Step 2: approximate the samples by sum_j A_j e^{-i k_lz Z_j} with the
+  generalized pencil-of-function method (GPOF; Hua & Sarkar 1989): first level
+  on C_ap1, then (reading: the standard two-level procedure) the first-level
+  images are subtracted from the C_ap2 samples and the rest is fitted there.
+* Step 3: the Sommerfeld identity turns every image into a free-space Hankel
+  function at a complex distance, A_j h0(k_l sqrt(rho^2 + (w - Z_j)^2)).
+
+Same-layer reading: the reaction field of u_ll splits into terms tau with a
+real image distance zeta_tau (see ``Medium.same_layer_terms``); each term is
+fitted once, as F_tau(k_z) = s_tau(k_rho) e^{i k_z zeta_min,tau}, so that
+
+    u_tau(r, r') ~= sum_j A_j h0(k_l sqrt(rho^2 + (zeta_tau(z,z') - zeta_min,tau - Z_j)^2)).
+
+GPOF parameters (the paper does not state them): pencil parameter N/2, model
+order = number of singular values above ``rel_tol`` * sigma_max, capped per
+level; the images of both levels together are at most ``n_images``.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .medium import Medium, kz_branch
+
+
+def default_T0(med: Medium, l):
+    kmax = float(np.max(med.k.real))
+    kl = float(med.k[l].real)
+    return math.sqrt(max(((kmax + 0.8) / kl) ** 2 - 1.0, 1e-6))
+
+
+ABS_TOL = 1e-14
+
+
+def gpof(y, m_max, rel_tol=1e-12, decaying=False):
+    """Generalized pencil of function: y_n ~= sum_j b_j z_j^n.
+
+    Returns (z, b).  Model order: singular values of the Hankel data matrix
+    above max(rel_tol * sigma_0, ABS_TOL * N) (the sampled functions are O(1),
+    so anything below the absolute floor is rounding noise), at most m_max.
+    With ``decaying`` only poles with |z| < 1 are kept (images that decay
+    along the first-level path).
+    """
+    y = np.asarray(y, dtype=complex)
+    N = y.size
+    Lp = N // 2
+    Y = np.array([y[i:i + Lp + 1] for i in range(N - Lp)])     # (N-Lp) x (Lp+1)
+    _, S, Vh = np.linalg.svd(Y)
+    m = int(min(m_max, np.count_nonzero(S > max(rel_tol * S[0], ABS_TOL * N))))
+    if m == 0:
+        return np.zeros(0, complex), np.zeros(0, complex)
+    V = Vh.conj().T[:, :m]                                     # (Lp+1) x m
+    V1, V2 = V[:-1, :], V[1:, :]
+    Zmat = V2.conj().T @ np.linalg.pinv(V1.conj().T)
+    z = np.linalg.eigvals(Zmat)
+    if decaying:
+        z = z[np.abs(z) < 1.0]
+        if z.size == 0:
+            return np.zeros(0, complex), np.zeros(0, complex)
+    vand = z[None, :] ** np.arange(N)[:, None]
+    b, *_ = np.linalg.lstsq(vand, y, rcond=None)
+    return z, b
+
+
+def sample_paths(k, T0, T1, n):
+    """k_lz samples on C_ap1 and C_ap2 and their steps (Step 1)."""
+    t1 = np.linspace(0.0, T1, n)
+    t2 = np.linspace(0.0, T0, n)
+    kz1 = 1j * k * (T0 + t1)
+    kz2 = k * (1.0 - t2 / T0 + 1j * t2)
+    return kz1, kz2, T1 / (n - 1), T0 / (n - 1)
+
+
+def fit_two_level(F, k, T0, T1=10.0, n=101, n_images=8, m1=None, rel_tol=1e-12):
+    """Fit F(k_z) ~= sum_j A_j e^{-i k_z Z_j} (Steps 1-2).  Returns (A, Z, info)."""
+    k = complex(k)
+    kz1, kz2, dt1, dt2 = sample_paths(k, T0, T1, n)
+    y1 = F(kz1)
+    y2 = F(kz2)
+    if m1 is None:
+        m1 = n_images // 2
+    # level 1: e^{-i kz Z} = e^{k T0 Z} (e^{k dt1 Z})^n
+    z1, b1 = gpof(y1, m1, rel_tol, decaying=True)
+    Z1 = np.log(z1) / (k * dt1)
+    A1 = b1 * np.exp(-k * T0 * Z1)
+    # level 2 on the residual: e^{-i kz Z} = e^{-i k Z} (e^{-i k (i - 1/T0) dt2 Z})^n
+    res2 = y2 - (np.exp(-1j * kz2[:, None] * Z1[None, :]) @ A1 if A1.size else 0.0)
+    z2, b2 = gpof(res2, n_images - A1.size, rel_tol)
+    c = -1j * k * (1j - 1.0 / T0) * dt2
+    Z2 = np.log(z2) / c
+    A2 = b2 * np.exp(1j * k * Z2)
+    A = np.concatenate([A1, A2])
+    Z = np.concatenate([Z1, Z2])
+    approx1 = np.exp(-1j * kz1[:, None] * Z[None, :]) @ A
+    approx2 = np.exp(-1j * kz2[:, None] * Z[None, :]) @ A
+    info = {
+        'resid1': float(np.max(np.abs(approx1 - y1))),
+        'resid2': float(np.max(np.abs(approx2 - y2))),
+        'scale': float(max(np.max(np.abs(y1)), np.max(np.abs(y2)))),
+        'n1': int(A1.size), 'n2': int(A2.size),
+    }
+    return A, Z, info
+
+
+class ImageTable:
+    """Same-layer DCIM images of one medium (one fit per (layer, term)).
+
+    ``terms[l]`` is a list of dicts with keys tag, sz, szp, c, zeta_min, A, Z.
+    The 'ud' and 'du' terms of an interior layer have the same s_tau and the
+    same zeta_min, so they share one fit.
+    """
+
+    def __init__(self, med: Medium, zext, n_images=8, T1=10.0, n_samples=101,
+                 T0=None, m1=None, rel_tol=1e-12):
+        self.med = med
+        self.zext = [tuple(map(float, e)) for e in zext]
+        self.terms = []
+        for l in range(med.n_layers):
+            lst = []
+            zlo, zhi = self.zext[l]
+            shared = None
+            for tag, sz, szp, c in med.same_layer_terms(l):
+                if tag == 'uu':
+                    zmin = 2.0 * zlo + c
+                elif tag == 'dd':
+                    zmin = c - 2.0 * zhi
+                else:
+                    zmin = (zlo - zhi) + c
+                kl = med.k[l]
+                t0 = default_T0(med, l) if T0 is None else T0
+                if tag in ('ud', 'du') and shared is not None:
+                    A, Z, info = shared
+                else:
+                    def F(kz, tag=tag, l=l, zmin=zmin, kl=kl):
+                        krho = np.sqrt(kl * kl - kz * kz)
+                        return self.med.s_tau(l, tag, krho) * np.exp(1j * kz * zmin)
+                    A, Z, info = fit_two_level(F, kl, t0, T1, n_samples, n_images, m1, rel_tol)
+                    if tag in ('ud', 'du'):
+                        shared = (A, Z, info)
+                lst.append(dict(tag=tag, sz=sz, szp=szp, c=c, zeta_min=zmin, A=A, Z=Z, info=info))
+            self.terms.append(lst)
+
+    def reaction(self, l, x, y, z, xp, yp, zp):
+        """Same-layer DCIM reaction field sum_tau sum_j A_j h0(k R_j) (vectorised)."""
+        kl = self.med.k[l]
+        rho2 = (x - xp) ** 2 + (y - yp) ** 2
+        out = np.zeros(np.broadcast(x, xp).shape, dtype=complex)
+        for t in self.terms[l]:
+            zeta = t['sz'] * z + t['szp'] * zp + t['c']
+            for A, Z in zip(t['A'], t['Z']):
+                w = zeta - t['zeta_min'] - Z
+                R = np.sqrt(rho2 + w * w)
+                out = out + A * np.exp(1j * kl * R) / (1j * kl * R)
+        return out
+
+    def flat(self):
+        """Flattened arrays (layer, term, A, Z, sz, szp, c, zeta_min) of all images."""
+        rows = []
+        for l, lst in enumerate(self.terms):
+            for ti, t in enumerate(lst):
+                for A, Z in zip(t['A'], t['Z']):
+                    rows.append((l, ti, A, Z, t['sz'], t['szp'], t['c'], t['zeta_min']))
+        return rows

@@ -1,0 +1,97 @@
+"""Taylor coefficients of e^{ikR}/R at a complex point (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Sec. 3.2, eq. ``recurrsion``: with x = r - r' (third component possibly
+complex, an image point), phi = e^{ikR}/R, psi = e^{ikR}, R = sqrt(x.x)
+(principal branch), a_k = D^k phi / k!, b_k = D^k psi / k!.
+
+The printed recurrence has wrong coefficients and an undefined psi.  Re-derived
+from R^2 d_i phi + x_i phi = i k x_i psi and d_i psi = i k x_i phi by matching
+Taylor coefficients and summing over i, it reads
+
+    |k| R^2 a_k + (2|k|-1) sum_i x_i a_{k-e_i} + (|k|-1) sum_i a_{k-2e_i}
+                                   = i k sum_i (x_i b_{k-e_i} + b_{k-2e_i}),
+    |k| b_k = i k sum_i (x_i a_{k-e_i} + a_{k-2e_i}),
+
+(coefficients with a negative index are zero), a_0 = e^{ikR}/R, b_0 = e^{ikR}.
+The Taylor coefficients of h0(kR) = e^{ikR}/(ikR) are a_k/(ik).
+
+Multi-index order used everywhere in the oracle ("graded, k1 descending"):
+for n = 0..P, for k1 = n..0, for k2 = n-k1..0, k3 = n-k1-k2.
+"""
+from __future__ import annotations
+
+from functools import lru_cache
+
+import numpy as np
+
+
+@lru_cache(maxsize=None)
+def multi_indices(P):
+    out = []
+    for n in range(P + 1):
+        for k1 in range(n, -1, -1):
+            for k2 in range(n - k1, -1, -1):
+                out.append((k1, k2, n - k1 - k2))
+    return np.array(out, dtype=np.int64)
+
+
+@lru_cache(maxsize=None)
+def index_map(P):
+    return {tuple(int(v) for v in m): i for i, m in enumerate(multi_indices(P))}
+
+
+def n_coeffs(P):
+    return (P + 1) * (P + 2) * (P + 3) // 6
+
+
+def taylor_phi(X, Y, W, k, P):
+    """a[..., idx(k)] = D^k (e^{ikR}/R) / k!  at x = (X, Y, W), |k| <= P.
+
+    X, Y real or complex arrays, W complex array (broadcast together).
+    """
+    X, Y, W = np.broadcast_arrays(np.asarray(X, complex), np.asarray(Y, complex),
+                                  np.asarray(W, complex))
+    x = (X, Y, W)
+    R2 = X * X + Y * Y + W * W
+    R = np.sqrt(R2)
+    k = complex(k)
+    mi = multi_indices(P)
+    im = index_map(P)
+    T = len(mi)
+    a = np.zeros(X.shape + (T,), dtype=complex)
+    b = np.zeros(X.shape + (T,), dtype=complex)
+    e = np.exp(1j * k * R)
+    a[..., 0] = e / R
+    b[..., 0] = e
+    for t in range(1, T):
+        kk = mi[t]
+        n = int(kk.sum())
+        sb = 0
+        sa1 = 0
+        sa2 = 0
+        sbr = 0
+        for i in range(3):
+            if kk[i] >= 1:
+                km = kk.copy()
+                km[i] -= 1
+                j = im[tuple(int(v) for v in km)]
+                sb = sb + x[i] * a[..., j]
+                sa1 = sa1 + x[i] * a[..., j]
+                sbr = sbr + x[i] * b[..., j]
+            if kk[i] >= 2:
+                km = kk.copy()
+                km[i] -= 2
+                j = im[tuple(int(v) for v in km)]
+                sb = sb + a[..., j]
+                sa2 = sa2 + a[..., j]
+                sbr = sbr + b[..., j]
+        b[..., t] = 1j * k * sb / n
+        a[..., t] = (1j * k * sbr - (2 * n - 1) * sa1 - (n - 1) * sa2) / (n * R2)
+    return a
+
+
+def taylor_h0(X, Y, W, k, P):
+    """D^k h0(kR)/k! = a_k/(ik)."""
+    return taylor_phi(X, Y, W, k, P) / (1j * complex(k))

@@ -1,0 +1,547 @@
+"""CPU Taylor-expansion FMM in layered media, FP64 (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Follows Sec. 3 of the paper:
+* Sec. 3.1 (free space): source-box TE alpha_k = sum_j q_j (r_j - r_c)^k
+  (eq. ``taylorexpfarxcfree``), target-box TE beta_k (eq.
+  ``taylorexplocxclfree``), M2M by the binomial shift (eqs. ``LETOLEmat``,
+  ``TETartoTETar``), L2L (eq. ``freeletole``), and the box-to-box translation
+  L_k^{k'} = D_r^k D_{r'}^{k'} h0 / (k! k'!).
+* Sec. 3.1 (layered media): the same M2M/L2L, and the layered M2L of eq.
+  ``tesourceboxtotargetbox`` with D_r^k D_{r'}^{k'} u / (k! k'!).
+* Sec. 3.2: DCIM images and the derivative recurrence (``oracle.derivs``).
+* Algorithm 1 (upward pass, downward pass with L2L and M2L, L2P, near-field
+  direct sum) and the component loop of the heterogeneous algorithm that
+  follows it (free space for l = l', up/down reaction components).
+
+Readings where the paper is silent (all stated the same way for the CUDA path):
+* One octree per layer, all in one root cube: lo = min over all points per
+  axis, side = max over axes of (max - min) (1 if zero).  Integer box
+  coordinates i = min(floor(((x - lo) / side) * 2^21), 2^21 - 1) with plain
+  IEEE double operations (no fused multiply-add); 63-bit Morton keys with bit
+  3b+2 = bit b of ix, 3b+1 = iy, 3b = iz.  Points are sorted by (layer, key,
+  input index).  Box centre of coordinate i at level l: lo + (i + 0.5) *
+  (side / 2^l).
+* A box is split while max(#sources, #targets) > leaf_cap and level <
+  max_level; only children holding a point exist.  Nodes are ordered by
+  (layer, level, Morton prefix).
+* Interaction lists: a dual-tree traversal of (target tree, source tree),
+  which for one tree is the classic adaptive U/V/W/X construction
+  (Carrier-Greengard-Rokhlin).  V pairs go through M2L; U, W and X pairs are
+  evaluated directly (P2P) -- W/X boxes are whole subtrees.
+* Same-layer reaction terms are written in the image-distance form of
+  ``Medium.same_layer_terms``; with W = sz z + szp z' + c,
+  D_r^k D_r'^k' f / (k! k'!) = (-1)^{k1'+k2'} sz^{k3} szp^{k3'} C(k+k', k) a_{k+k'}
+  where a_g = D^g f / g!, C(k+k', k) = prod_i (k_i+k'_i)!/(k_i! k'_i!).
+  Offsets of M2L pairs are taken from integer box coordinates:
+  X0 = di_x * (side / 2^l), and zt_c + zs_c = 2 lo_z + (i_t + i_s + 1) * (side / 2^l).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .derivs import multi_indices, index_map, n_coeffs, taylor_h0
+
+NBITS = 21
+
+
+def morton_encode(ix, iy, iz):
+    key = np.zeros(ix.shape, dtype=np.uint64)
+    for b in range(NBITS):
+        key |= ((ix >> b) & 1).astype(np.uint64) << np.uint64(3 * b + 2)
+        key |= ((iy >> b) & 1).astype(np.uint64) << np.uint64(3 * b + 1)
+        key |= ((iz >> b) & 1).astype(np.uint64) << np.uint64(3 * b)
+    return key
+
+
+def morton_decode(prefix, level):
+    ix = np.zeros(np.shape(prefix), dtype=np.int64)
+    iy = np.zeros_like(ix)
+    iz = np.zeros_like(ix)
+    p = np.asarray(prefix, dtype=np.uint64)
+    for b in range(level):
+        iz |= ((p >> np.uint64(3 * b)) & np.uint64(1)).astype(np.int64) << b
+        iy |= ((p >> np.uint64(3 * b + 1)) & np.uint64(1)).astype(np.int64) << b
+        ix |= ((p >> np.uint64(3 * b + 2)) & np.uint64(1)).astype(np.int64) << b
+    return ix, iy, iz
+
+
+def root_cube(points):
+    lo = points.min(axis=0)
+    hi = points.max(axis=0)
+    side = float(np.max(hi - lo))
+    if side == 0.0:
+        side = 1.0
+    return lo.astype(np.float64), side
+
+
+def int_coords(xyz, lo, side):
+    t = (xyz - lo[None, :]) / side
+    t = t * float(1 << NBITS)
+    i = np.floor(t).astype(np.int64)
+    return np.clip(i, 0, (1 << NBITS) - 1)
+
+
+class Trees:
+    """Per-layer octrees in a common root cube (see module docstring)."""
+
+    def __init__(self, med, src, tgt, leaf_cap, max_level=NBITS, cube=None):
+        self.med = med
+        allp = np.concatenate([src, tgt], 0)
+        self.lo, self.side = root_cube(allp) if cube is None else cube
+        self.leaf_cap = leaf_cap
+        self.max_level = max_level
+        self.slay = med.layer_of(src[:, 2])
+        self.tlay = med.layer_of(tgt[:, 2])
+        if np.any(self.slay < 0) or np.any(self.tlay < 0):
+            raise ValueError("point on an interface")
+        si = int_coords(src, self.lo, self.side)
+        ti = int_coords(tgt, self.lo, self.side)
+        self.skey = morton_encode(si[:, 0], si[:, 1], si[:, 2])
+        self.tkey = morton_encode(ti[:, 0], ti[:, 1], ti[:, 2])
+        self.sperm = np.lexsort((np.arange(len(src)), self.skey, self.slay))
+        self.tperm = np.lexsort((np.arange(len(tgt)), self.tkey, self.tlay))
+        sk = self.skey[self.sperm]
+        tk = self.tkey[self.tperm]
+        sl = self.slay[self.sperm]
+        tl = self.tlay[self.tperm]
+        nodes = []      # (layer, level, prefix, parent, s0, s1, t0, t1)
+        children = []
+        self.root = {}
+        for l in range(med.n_layers):
+            s0, s1 = np.searchsorted(sl, l, 'left'), np.searchsorted(sl, l, 'right')
+            t0, t1 = np.searchsorted(tl, l, 'left'), np.searchsorted(tl, l, 'right')
+            if s1 - s0 + t1 - t0 == 0:
+                continue
+            self.root[l] = len(nodes)
+            nodes.append([l, 0, 0, -1, s0, s1, t0, t1])
+            children.append([])
+            frontier = [self.root[l]]
+            level = 0
+            while frontier:
+                nxt = []
+                for nid in frontier:
+                    _, lev, pre, _, a0, a1, b0, b1 = nodes[nid]
+                    if max(a1 - a0, b1 - b0) <= leaf_cap or lev >= max_level:
+                        continue
+                    shift = np.uint64(3 * (NBITS - lev - 1))
+                    sc = (sk[a0:a1] >> shift) & np.uint64(7)
+                    tc = (tk[b0:b1] >> shift) & np.uint64(7)
+                    for c in range(8):
+                        cs0 = a0 + np.searchsorted(sc, c, 'left')
+                        cs1 = a0 + np.searchsorted(sc, c, 'right')
+                        ct0 = b0 + np.searchsorted(tc, c, 'left')
+                        ct1 = b0 + np.searchsorted(tc, c, 'right')
+                        if cs1 - cs0 + ct1 - ct0 == 0:
+                            continue
+                        cid = len(nodes)
+                        nodes.append([l, lev + 1, (pre << 3) | c, nid, cs0, cs1, ct0, ct1])
+                        children.append([])
+                        children[nid].append(cid)
+                        nxt.append(cid)
+                frontier = nxt
+                level += 1
+        # reorder within each layer by (level, prefix): BFS above already gives
+        # level order and, because parents are visited in prefix order and
+        # children in child-index order, ascending prefix within a level.
+        arr = np.array(nodes, dtype=object)
+        self.n_nodes = len(nodes)
+        self.layer = np.array([n[0] for n in nodes], dtype=np.int64)
+        self.level = np.array([n[1] for n in nodes], dtype=np.int64)
+        self.prefix = np.array([n[2] for n in nodes], dtype=np.uint64)
+        self.parent = np.array([n[3] for n in nodes], dtype=np.int64)
+        self.s0 = np.array([n[4] for n in nodes], dtype=np.int64)
+        self.s1 = np.array([n[5] for n in nodes], dtype=np.int64)
+        self.t0 = np.array([n[6] for n in nodes], dtype=np.int64)
+        self.t1 = np.array([n[7] for n in nodes], dtype=np.int64)
+        self.children = children
+        self.is_leaf = np.array([len(c) == 0 for c in children])
+        ix, iy, iz = [], [], []
+        for n in nodes:
+            a, b, c = morton_decode(np.uint64(n[2]), n[1])
+            ix.append(int(a)); iy.append(int(b)); iz.append(int(c))
+        self.ix = np.array(ix, dtype=np.int64)
+        self.iy = np.array(iy, dtype=np.int64)
+        self.iz = np.array(iz, dtype=np.int64)
+        del arr
+
+    def ns(self, n):
+        return self.s1[n] - self.s0[n]
+
+    def nt(self, n):
+        return self.t1[n] - self.t0[n]
+
+    def center(self, n):
+        h = self.side / float(1 << int(self.level[n]))
+        return np.array([self.lo[0] + (self.ix[n] + 0.5) * h,
+                         self.lo[1] + (self.iy[n] + 0.5) * h,
+                         self.lo[2] + (self.iz[n] + 0.5) * h])
+
+    def adjacent(self, a, b):
+        la, lb = int(self.level[a]), int(self.level[b])
+        if la > lb:
+            a, b, la, lb = b, a, lb, la
+        s = lb - la
+        for ca, cb in ((self.ix[a], self.ix[b]), (self.iy[a], self.iy[b]), (self.iz[a], self.iz[b])):
+            lo_ = int(ca) << s
+            hi_ = ((int(ca) + 1) << s) - 1
+            if int(cb) < lo_ - 1 or int(cb) > hi_ + 1:
+                return False
+        return True
+
+
+def build_lists(tr: Trees, lt, ls):
+    """Dual-tree traversal of target tree ``lt`` against source tree ``ls``.
+
+    Returns (V, P2P): dicts target node -> sorted list of source nodes; P2P
+    only has target leaves, and already folds U, W and the X entries of every
+    ancestor-or-self.
+    """
+    if lt not in tr.root or ls not in tr.root:
+        return {}, {}
+    rt, rs = tr.root[lt], tr.root[ls]
+    if tr.nt(rt) == 0 or tr.ns(rs) == 0:
+        return {}, {}
+    U, V, W, X = {}, {}, {}, {}
+
+    def add(D, a, b):
+        D.setdefault(a, []).append(b)
+
+    def ch_t(n):
+        return [c for c in tr.children[n] if tr.nt(c) > 0]
+
+    def ch_s(n):
+        return [c for c in tr.children[n] if tr.ns(c) > 0]
+
+    def leaf_target(t, c):
+        if tr.is_leaf[c]:
+            add(U, t, c)
+            return
+        for cc in ch_s(c):
+            if tr.adjacent(t, cc):
+                leaf_target(t, cc)
+            else:
+                add(W, t, cc)
+
+    def leaf_source(c, s):
+        if tr.is_leaf[c]:
+            add(U, c, s)
+            return
+        for cc in ch_t(c):
+            if tr.adjacent(cc, s):
+                leaf_source(cc, s)
+            else:
+                add(X, cc, s)
+
+    stack = [(rt, rs)]
+    while stack:
+        t, s = stack.pop()
+        lt_, ls_ = tr.is_leaf[t], tr.is_leaf[s]
+        if lt_ and ls_:
+            add(U, t, s)
+        elif lt_:
+            for c in ch_s(s):
+                if tr.adjacent(t, c):
+                    leaf_target(t, c)
+                else:
+                    add(W, t, c)
+        elif ls_:
+            for c in ch_t(t):
+                if tr.adjacent(c, s):
+                    leaf_source(c, s)
+                else:
+                    add(X, c, s)
+        else:
+            for ct in ch_t(t):
+                for cs in ch_s(s):
+                    if tr.adjacent(ct, cs):
+                        stack.append((ct, cs))
+                    else:
+                        add(V, ct, cs)
+    P2P = {}
+    leaves = [n for n in range(tr.n_nodes) if tr.layer[n] == lt and tr.is_leaf[n] and tr.nt(n) > 0]
+    for t in leaves:
+        lst = list(U.get(t, [])) + list(W.get(t, []))
+        a = t
+        while a >= 0:
+            lst += X.get(a, [])
+            a = tr.parent[a]
+        if lst:
+            P2P[t] = sorted(lst)
+    V = {t: sorted(v) for t, v in V.items()}
+    return V, P2P
+
+
+# ----------------------------------------------------------------------------
+# Taylor-expansion operators (Sec. 3.1)
+
+class Ops:
+    def __init__(self, p):
+        self.p = p
+        self.mi = multi_indices(p)
+        self.np_ = len(self.mi)
+        im2 = index_map(2 * p)
+        mi = self.mi
+        n = self.np_
+        self.g = np.zeros((n, n), dtype=np.int64)        # index of k + k' in the order-2p list
+        self.mult = np.zeros((n, n))                     # prod_i C(k_i + k'_i, k_i)
+        self.sxy = np.zeros((n, n))                      # (-1)^{k1' + k2'}
+        self.s3p = np.zeros((n, n))                      # (-1)^{k3'}
+        self.s3g = np.zeros((n, n))                      # (-1)^{k3 + k3'}
+        for a in range(n):
+            for b in range(n):
+                gg = mi[a] + mi[b]
+                self.g[a, b] = im2[tuple(int(v) for v in gg)]
+                self.mult[a, b] = np.prod([math.comb(int(gg[i]), int(mi[a][i])) for i in range(3)])
+                self.sxy[a, b] = (-1.0) ** (mi[b][0] + mi[b][1])
+                self.s3p[a, b] = (-1.0) ** mi[b][2]
+                self.s3g[a, b] = (-1.0) ** (mi[a][2] + mi[b][2])
+        # binomial tables for M2M / L2L: C(k, k') for k' <= k componentwise
+        self.binom = np.zeros((n, n))
+        self.dpow = np.zeros((n, n), dtype=np.int64)     # index of k - k'
+        self.valid = np.zeros((n, n), dtype=bool)
+        im = index_map(p)
+        for a in range(n):
+            for b in range(n):
+                d = mi[a] - mi[b]
+                if np.all(d >= 0):
+                    self.valid[a, b] = True
+                    self.binom[a, b] = np.prod([math.comb(int(mi[a][i]), int(mi[b][i])) for i in range(3)])
+                    self.dpow[a, b] = im[tuple(int(v) for v in d)]
+
+    def monomials(self, d):
+        """d: (..., 3) -> (..., n_p) with d^k."""
+        d = np.asarray(d)
+        out = np.ones(d.shape[:-1] + (self.np_,), dtype=d.dtype if np.iscomplexobj(d) else float)
+        for t, k in enumerate(self.mi):
+            out[..., t] = d[..., 0] ** k[0] * d[..., 1] ** k[1] * d[..., 2] ** k[2]
+        return out
+
+    def p2m(self, pts, q, c):
+        """alpha_k = sum_j q_j (r_j - c)^k."""
+        return q @ self.monomials(pts - c[None, :])
+
+    def m2m(self, alpha_child, dc):
+        """Parent moments from a child's, dc = child centre - parent centre:
+        gamma_k = sum_{k' <= k} C(k, k') dc^{k-k'} alpha_{k'}."""
+        m = self.monomials(dc[None, :])[0]
+        B = np.where(self.valid, self.binom * m[self.dpow], 0.0)
+        return B @ alpha_child
+
+    def l2l(self, beta_parent, dc):
+        """Child local from the parent's, dc = child centre - parent centre:
+        lambda_k = sum_{k' >= k} C(k', k) dc^{k'-k} beta_{k'}."""
+        m = self.monomials(dc[None, :])[0]
+        B = np.where(self.valid, self.binom * m[self.dpow], 0.0)
+        return B.T @ beta_parent
+
+    def l2p(self, beta, pts, c):
+        return self.monomials(pts - c[None, :]) @ beta
+
+    def m2l_matrix(self, A, B):
+        """M2L matrix from the combined derivative tables (see module docstring):
+        H[k,k'] = C(k+k',k) (-1)^{k1'+k2'} (A_{k+k'} + (-1)^{k3'} B_{k+k'})."""
+        return self.mult * self.sxy * (A[self.g] + self.s3p * B[self.g])
+
+
+class TEFMM:
+    """Algorithm 1 + the component loop, for every (target layer, source layer)."""
+
+    def __init__(self, med, images, p, leaf_cap, max_level=NBITS, cube=None):
+        self.med = med
+        self.images = images
+        self.p = p
+        self.leaf_cap = leaf_cap
+        self.max_level = max_level
+        self.cube = cube
+        self.ops = Ops(p)
+
+    def setup(self, src, tgt):
+        self.src = np.asarray(src, float)
+        self.tgt = np.asarray(tgt, float)
+        self.tr = Trees(self.med, self.src, self.tgt, self.leaf_cap, self.max_level, self.cube)
+        self.lists = {}
+        for lt in range(self.med.n_layers):
+            for ls in range(self.med.n_layers):
+                V, P = build_lists(self.tr, lt, ls)
+                if V or P:
+                    if lt != ls:
+                        raise NotImplementedError("cross-layer components")
+                    self.lists[(lt, ls)] = (V, P)
+        return self
+
+    # -- upward pass --------------------------------------------------------
+    def upward(self, q):
+        tr, ops = self.tr, self.ops
+        sp = self.src[tr.sperm]
+        qs = np.asarray(q)[tr.sperm]
+        alpha = np.zeros((tr.n_nodes, ops.np_), dtype=complex)
+        order = np.argsort(-tr.level, kind='stable')
+        for n in order:
+            if tr.ns(n) == 0:
+                continue
+            c = tr.center(n)
+            if tr.is_leaf[n]:
+                a, b = tr.s0[n], tr.s1[n]
+                alpha[n] = ops.p2m(sp[a:b], qs[a:b], c)
+            else:
+                for ch in tr.children[n]:
+                    if tr.ns(ch) > 0:
+                        alpha[n] += ops.m2m(alpha[ch], tr.center(ch) - c)
+        return alpha
+
+    # -- derivative tables (Sec. 3.2) ---------------------------------------
+    def _tables(self, l, lev, keysB, keysA):
+        """Combined tables per key at one level of layer l.
+
+        keysB: (n, 3) integer offsets (dix, diy, diz) -> B = free + ud + (-1)^{g3} du
+        keysA: (n, 3) (dix, diy, izt + izs)           -> A = uu + (-1)^{g3} dd
+        """
+        tr = self.tr
+        P2 = 2 * self.p
+        k = self.med.k[l]
+        h = tr.side / float(1 << lev)
+        mi2 = multi_indices(P2)
+        odd3 = (-1.0) ** mi2[:, 2]
+        terms = {t['tag']: t for t in self.images.terms[l]} if self.images is not None else {}
+        TB = np.zeros((len(keysB), len(mi2)), dtype=complex)
+        TA = np.zeros((len(keysA), len(mi2)), dtype=complex)
+        if len(keysB):
+            X0 = keysB[:, 0] * h
+            Y0 = keysB[:, 1] * h
+            dz = keysB[:, 2] * h
+            TB += taylor_h0(X0, Y0, dz.astype(complex), k, P2)
+            for tag, sgn in (('ud', None), ('du', odd3)):
+                if tag not in terms:
+                    continue
+                t = terms[tag]
+                W0 = t['sz'] * dz + t['c']          # sz z_t + szp z_s + c with szp = -sz
+                for A, Z in zip(t['A'], t['Z']):
+                    tab = A * taylor_h0(X0, Y0, W0 - t['zeta_min'] - Z, k, P2)
+                    TB += tab if sgn is None else tab * sgn[None, :]
+        if len(keysA):
+            X0 = keysA[:, 0] * h
+            Y0 = keysA[:, 1] * h
+            zsum = 2.0 * tr.lo[2] + (keysA[:, 2] + 1) * h
+            for tag, sgn in (('uu', None), ('dd', odd3)):
+                if tag not in terms:
+                    continue
+                t = terms[tag]
+                W0 = t['sz'] * zsum + t['c']        # sz = szp for these terms
+                for A, Z in zip(t['A'], t['Z']):
+                    tab = A * taylor_h0(X0, Y0, W0 - t['zeta_min'] - Z, k, P2)
+                    TA += tab if sgn is None else tab * sgn[None, :]
+        return TB, TA
+
+    # -- downward pass -------------------------------------------------------
+    def downward(self, alpha, only_targets=None):
+        """Local expansions of every target node (or only the ancestors of the
+        given target leaves)."""
+        tr, ops = self.tr, self.ops
+        beta = np.zeros((tr.n_nodes, ops.np_), dtype=complex)
+        need = None
+        if only_targets is not None:
+            need = set()
+            for n in only_targets:
+                a = n
+                while a >= 0:
+                    need.add(a)
+                    a = tr.parent[a]
+        for (lt, ls), (V, _) in self.lists.items():
+            # group V pairs by level
+            pairs = [(t, s) for t, lst in V.items() for s in lst if need is None or t in need]
+            if not pairs:
+                continue
+            pairs = np.array(pairs, dtype=np.int64)
+            for lev in np.unique(tr.level[pairs[:, 0]]):
+                sel = pairs[tr.level[pairs[:, 0]] == lev]
+                t, s = sel[:, 0], sel[:, 1]
+                kB = np.stack([tr.ix[t] - tr.ix[s], tr.iy[t] - tr.iy[s], tr.iz[t] - tr.iz[s]], 1)
+                kA = np.stack([tr.ix[t] - tr.ix[s], tr.iy[t] - tr.iy[s], tr.iz[t] + tr.iz[s]], 1)
+                uB, invB = np.unique(kB, axis=0, return_inverse=True)
+                uA, invA = np.unique(kA, axis=0, return_inverse=True)
+                TB, TA = self._tables(lt, int(lev), uB, uA)
+                zero = np.zeros(TB.shape[1], dtype=complex)
+                invB = invB.reshape(-1)
+                invA = invA.reshape(-1)
+                contrib = np.zeros((len(t), ops.np_), dtype=complex)
+                for i in range(len(uB)):
+                    m = invB == i
+                    contrib[m] += alpha[s[m]] @ ops.m2l_matrix(zero, TB[i]).T
+                for i in range(len(uA)):
+                    m = invA == i
+                    contrib[m] += alpha[s[m]] @ ops.m2l_matrix(TA[i], zero).T
+                np.add.at(beta, t, contrib)
+        order = np.argsort(tr.level, kind='stable')
+        for n in order:
+            par = tr.parent[n]
+            if par < 0 or tr.nt(n) == 0:
+                continue
+            if need is not None and n not in need:
+                continue
+            beta[n] += ops.l2l(beta[par], tr.center(n) - tr.center(par))
+        return beta
+
+    # -- near field ----------------------------------------------------------
+    def _kernel_same_layer(self, l, tpts, spts):
+        """free h0 (skip identical coordinates) + DCIM images, (nt, ns) matrix."""
+        k = self.med.k[l]
+        dx = tpts[:, None, 0] - spts[None, :, 0]
+        dy = tpts[:, None, 1] - spts[None, :, 1]
+        dz = tpts[:, None, 2] - spts[None, :, 2]
+        r = np.sqrt(dx * dx + dy * dy + dz * dz)
+        same = (tpts[:, None, 0] == spts[None, :, 0]) & (tpts[:, None, 1] == spts[None, :, 1]) & \
+            (tpts[:, None, 2] == spts[None, :, 2])
+        with np.errstate(divide='ignore', invalid='ignore'):
+            G = np.where(same, 0.0, np.exp(1j * k * r) / (1j * k * np.where(same, 1.0, r)))
+        if self.images is not None:
+            G = G + self.images.reaction(l, tpts[:, None, 0], tpts[:, None, 1], tpts[:, None, 2],
+                                         spts[None, :, 0], spts[None, :, 1], spts[None, :, 2])
+        return G
+
+    def evaluate(self, q, target_index=None):
+        """Phi at all targets (input order), or at the given target indices."""
+        tr, ops = self.tr, self.ops
+        q = np.asarray(q, dtype=complex)
+        alpha = self.upward(q)
+        tp = self.tgt[tr.tperm]
+        sp = self.src[tr.sperm]
+        qs = q[tr.sperm]
+        inv_t = np.empty_like(tr.tperm)
+        inv_t[tr.tperm] = np.arange(len(tr.tperm))
+        if target_index is None:
+            want_sorted = np.arange(len(tp))
+        else:
+            want_sorted = inv_t[np.asarray(target_index)]
+        # leaf of every sorted target
+        leaf_of = np.full(len(tp), -1, dtype=np.int64)
+        for n in range(tr.n_nodes):
+            if tr.is_leaf[n] and tr.nt(n) > 0:
+                leaf_of[tr.t0[n]:tr.t1[n]] = n
+        leaves = np.unique(leaf_of[want_sorted])
+        beta = self.downward(alpha, only_targets=None if target_index is None else leaves)
+        phi_sorted = np.zeros(len(tp), dtype=complex)
+        wanted = np.zeros(len(tp), dtype=bool)
+        wanted[want_sorted] = True
+        for t in leaves:
+            a, b = tr.t0[t], tr.t1[t]
+            idx = np.arange(a, b)[wanted[a:b]]
+            pts = tp[idx]
+            val = ops.l2p(beta[t], pts, tr.center(t))
+            l = int(tr.layer[t])
+            for (lt, ls), (_, P2P) in self.lists.items():
+                if lt != l or t not in P2P:
+                    continue
+                for s in P2P[t]:
+                    s0, s1 = tr.s0[s], tr.s1[s]
+                    G = self._kernel_same_layer(l, pts, sp[s0:s1])
+                    val = val + G @ qs[s0:s1]
+            phi_sorted[idx] = val
+        out = np.zeros(len(tp), dtype=complex)
+        out[tr.tperm] = phi_sorted
+        if target_index is None:
+            return out
+        return out[np.asarray(target_index)]

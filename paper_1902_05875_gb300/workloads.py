@@ -1,0 +1,88 @@
+"""Seeded synthetic workloads (inputs only; none of the method's arithmetic).
+
+Shared by the tests, the bench and the oracle-facing test code.  Every
+generator draws positions first, then charges, with ``numpy.random.
+default_rng(seed)``; particles of several layers are drawn layer by layer, top
+to bottom.  The media and particle recipes follow the workloads of the paper's
+Sec. 5 (uniform particles in slabs inside the layers of a two- or three-layer
+medium) at the sizes this library is measured on.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Workload:
+    name: str
+    interfaces: list            # d_0 > d_1 > ... (len = n_layers - 1)
+    k: list                     # complex wavenumber per layer
+    zext: list                  # per layer (zlo, zhi) of the particle slab (DCIM zeta_min)
+    src: np.ndarray             # (N, 3) float64
+    q: np.ndarray               # (N,) complex128
+    p: int
+    leaf_cap: int
+    n_images: int = 8
+    tgt: np.ndarray = None      # None: targets are the sources
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def targets(self):
+        return self.src if self.tgt is None else self.tgt
+
+
+THREE_LAYER_D = [0.0, -1.2]
+THREE_LAYER_K = [1.2, 1.5, 2.0]
+THREE_LAYER_ZEXT = [(0.1, 1.1), (-1.1, -0.1), (-2.3, -1.3)]
+
+
+def _charges(rng, n):
+    re = rng.uniform(0.0, 1.0, n)
+    im = rng.uniform(0.0, 1.0, n)
+    return re + 1j * im
+
+
+def middle_layer_uniform(n, p, leaf_cap, seed=0, n_images=8, name=None):
+    """Three layers (interfaces 0, -1.2; k = 1.2, 1.5, 2.0); n uniform points in
+    [-1,1]^2 x [-1.1,-0.1] (middle layer); charges re, im ~ U[0,1]."""
+    rng = np.random.default_rng(seed)
+    src = rng.uniform([-1.0, -1.0, -1.1], [1.0, 1.0, -0.1], size=(n, 3))
+    q = _charges(rng, n)
+    return Workload(name or f"middle_layer_uniform_n{n}_p{p}", THREE_LAYER_D, THREE_LAYER_K,
+                    THREE_LAYER_ZEXT, src, q, p, leaf_cap, n_images)
+
+
+def three_layer_slabs(n, p, leaf_cap, seed=0, n_images=8, k=(2.0, 3.0, 4.0 + 0.01j),
+                      half_width=2.0, name=None):
+    """Three layers (interfaces 0, -1.2), n points split equally over the three
+    slabs [-w,w]^2 x {[0.1,1.1], [-1.1,-0.1], [-2.3,-1.3]}, top layer first."""
+    rng = np.random.default_rng(seed)
+    counts = [n // 3 + (1 if i < n % 3 else 0) for i in range(3)]
+    parts = []
+    for (zlo, zhi), c in zip(THREE_LAYER_ZEXT, counts):
+        parts.append(rng.uniform([-half_width, -half_width, zlo], [half_width, half_width, zhi],
+                                 size=(c, 3)))
+    src = np.concatenate(parts, 0)
+    q = _charges(rng, n)
+    return Workload(name or f"three_layer_slabs_n{n}_p{p}", THREE_LAYER_D, list(k),
+                    THREE_LAYER_ZEXT, src, q, p, leaf_cap, n_images)
+
+
+def cfg_small():
+    """2000 points in the middle layer, p = 6, leaf cap 60, 8 images per term."""
+    return middle_layer_uniform(2000, 6, 60, seed=0, n_images=8,
+                                name="three_layer_middle_n2000_p6")
+
+
+def cfg_fp64_200k():
+    """200k points in the middle layer, p = 8, leaf cap 64."""
+    return middle_layer_uniform(200_000, 8, 64, seed=0, n_images=8,
+                                name="three_layer_middle_n200k_p8")
+
+
+def cfg_mixed_2m():
+    """2M points over three layers, k = (2, 3, 4 + 0.01i), p = 10, leaf cap 64."""
+    return three_layer_slabs(2_000_000, 10, 64, seed=0, n_images=8,
+                             name="three_layer_slabs_n2M_p10")

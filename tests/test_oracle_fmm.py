@@ -1,0 +1,124 @@
+"""Pins of the CPU TE-FMM oracle (Sec. 3, Algorithm 1 and the component loop).
+
+* brute force: at N = 500 the FMM matches the FP64 direct sum with an error
+  that falls as p rises (p = 2, 4, 6, 8);
+* homogeneous medium (all k equal): the reaction field vanishes and the FMM
+  is the free-space FMM of the whole particle set;
+* polynomial exactness of M2M and L2L (Sec. 3.1 translations are exact shifts);
+* the interaction lists partition the (target, source) pairs: every pair is
+  covered exactly once by a V pair of an ancestor or a P2P entry, V pairs are
+  never adjacent, P2P pairs of U type are adjacent;
+* the direct sum's reaction part matches Sommerfeld quadrature;
+* a per-target evaluation equals the full evaluation.
+"""
+import numpy as np
+import pytest
+
+from oracle.medium import Medium
+from oracle.dcim import ImageTable
+from oracle.tefmm import TEFMM, Trees, build_lists, Ops
+from oracle.direct import direct_sum
+from oracle.sommerfeld import reaction_derivative
+from paper_1902_05875_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = W.middle_layer_uniform(500, 4, 20, seed=3)
+    med = Medium(w.interfaces, w.k)
+    img = ImageTable(med, w.zext, n_images=8)
+    ref = direct_sum(med, img, w.src, w.q, w.src)
+    return w, med, img, ref
+
+
+def test_fmm_error_falls_with_p(small):
+    w, med, img, ref = small
+    errs = []
+    for p in (2, 4, 6, 8):
+        phi = TEFMM(med, img, p, 20).setup(w.src, w.src).evaluate(w.q)
+        errs.append(np.linalg.norm(phi - ref) / np.linalg.norm(ref))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 2e-6, errs
+
+
+def test_fmm_detects_planted_sign_error(small):
+    """A sign flip planted in the oracle's M2L must break the brute-force match."""
+    w, med, img, ref = small
+    f = TEFMM(med, img, 6, 20).setup(w.src, w.src)
+    f.ops.s3p = -f.ops.s3p
+    phi = f.evaluate(w.q)
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) > 1e-3
+
+
+def test_homogeneous_medium_is_free_space():
+    rng = np.random.default_rng(7)
+    src = rng.uniform([-1, -1, -1.0], [1, 1, -0.2], size=(400, 3))
+    q = rng.uniform(0, 1, 400) + 1j * rng.uniform(0, 1, 400)
+    med = Medium([0.0, -1.2], [1.5, 1.5, 1.5])
+    img = ImageTable(med, [(0.1, 1.1), (-1.1, -0.1), (-2.3, -1.3)], n_images=8)
+    for lst in img.terms:
+        for t in lst:
+            assert np.max(np.abs(t['A']), initial=0.0) < 1e-12
+    phi = TEFMM(med, img, 8, 16).setup(src, src).evaluate(q)
+    d = src[:, None, :] - src[None, :, :]
+    r = np.sqrt((d * d).sum(-1))
+    np.fill_diagonal(r, 1.0)
+    G = np.exp(1.5j * r) / (1.5j * r)
+    np.fill_diagonal(G, 0.0)
+    ref = G @ q
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-6
+
+
+def test_m2m_l2l_polynomial_exactness():
+    ops = Ops(5)
+    rng = np.random.default_rng(1)
+    pts = rng.uniform(-0.2, 0.2, size=(30, 3))
+    q = rng.normal(size=30) + 1j * rng.normal(size=30)
+    c_child = np.array([0.05, -0.03, 0.02])
+    c_par = np.array([0.0, 0.0, 0.0])
+    a_child = ops.p2m(pts, q, c_child)
+    a_par = ops.m2m(a_child, c_child - c_par)
+    assert np.allclose(a_par, ops.p2m(pts, q, c_par), rtol=1e-12, atol=1e-14)
+    beta = rng.normal(size=ops.np_) + 1j * rng.normal(size=ops.np_)
+    lam = ops.l2l(beta, c_child - c_par)
+    x = rng.uniform(-0.1, 0.1, size=(10, 3)) + c_child
+    assert np.allclose(ops.l2p(lam, x, c_child), ops.l2p(beta, x, c_par), rtol=1e-12, atol=1e-13)
+
+
+def test_lists_partition_all_pairs(small):
+    w, med, img, _ = small
+    tr = Trees(med, w.src, w.src, 20)
+    V, P2P = build_lists(tr, 1, 1)
+    ns = len(w.src)
+    cover = np.zeros((ns, ns), dtype=np.int64)   # [sorted target, sorted source]
+    for t, lst in V.items():
+        for s in lst:
+            assert not tr.adjacent(t, s)
+            assert tr.level[t] == tr.level[s]
+            cover[tr.t0[t]:tr.t1[t], tr.s0[s]:tr.s1[s]] += 1
+    for t, lst in P2P.items():
+        assert tr.is_leaf[t]
+        for s in lst:
+            cover[tr.t0[t]:tr.t1[t], tr.s0[s]:tr.s1[s]] += 1
+    assert np.all(cover == 1)
+
+
+def test_direct_sum_reaction_matches_quadrature():
+    med = Medium([0.0, -1.2], [1.2, 1.5, 2.0])
+    img = ImageTable(med, [(0.1, 1.1), (-1.1, -0.1), (-2.3, -1.3)], n_images=24)
+    rng = np.random.default_rng(4)
+    src = rng.uniform([-1, -1, -1.1], [1, 1, -0.1], size=(3, 3))
+    tgt = rng.uniform([-1, -1, -1.1], [1, 1, -0.1], size=(2, 3))
+    q = np.array([1.0, 0.5 - 0.2j, -0.3j])
+    got = direct_sum(med, img, src, q, tgt, include_free=False)
+    for i in range(2):
+        want = sum(q[j] * reaction_derivative(med, 1, 1, tgt[i], src[j], part='both') for j in range(3))
+        assert abs(got[i] - want) < 1e-7 * abs(want)
+
+
+def test_sampled_targets_equal_full(small):
+    w, med, img, _ = small
+    f = TEFMM(med, img, 4, 20).setup(w.src, w.src)
+    phi = f.evaluate(w.q)
+    sel = np.array([0, 5, 77, 311, 499])
+    assert np.max(np.abs(f.evaluate(w.q, sel) - phi[sel])) < 1e-12 * np.max(np.abs(phi))
