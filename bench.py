@@ -1,0 +1,287 @@
+"""Benchmark of the layered-media TE-FMM matrix-vector product.
+
+One step = one full ``tefmm_eval`` (Morton sort, octrees, lists, P2M/M2M,
+derivative tables, M2L, L2L, L2P and near field) over the whole particle set,
+inputs resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload NAME] [--precision fp64|mixed]
+
+Multi-GPU: the path does not shard (one matvec per GPU); N ranks run N
+independent replicas of the same workload ("replicas only"); value sums the
+ranks' interactions over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM matvec interactions/s (N_t*N_s per matvec time)"
+UNIT = "interactions/s"
+
+WORKLOADS = {
+    "three_layer_middle_n200k_p8": lambda: __import__(
+        "paper_1902_05875_gb300.workloads", fromlist=["x"]).cfg_fp64_200k(),
+    "three_layer_middle_n2000_p6": lambda: __import__(
+        "paper_1902_05875_gb300.workloads", fromlist=["x"]).cfg_small(),
+}
+DEFAULT_WORKLOAD = "three_layer_middle_n200k_p8"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 peak: the nominal dense FP64 rate of GB300 (no measured FP64 figure is
+# provided); used for the FP64 SIMT kernels.
+FP64_PEAK_TFLOPS = 1.25
+
+# algorithmic FP64 flops per evaluation of e^{ikR}/R with complex R (image
+# term) and with real r (free-space term); counted from the formulas:
+#   complex R^2 (rho^2 + w^2): 6; principal sqrt: 8; i k R: 6; exp(re)*(cos,sin)
+#   of the imaginary part: 4; division by R: 11; times amplitude and
+#   accumulate: 8  -> 43 per image term
+#   real r = sqrt(dx^2+dy^2+dz^2): 6; e^{ikr}: 6; / r: 2; times q, accumulate: 8 -> 22
+FLOPS_IMAGE = 43
+FLOPS_FREE = 22
+
+
+def clocks_start():
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    try:
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=f, stderr=subprocess.DEVNULL)
+    except Exception:
+        p = None
+    return p, f.name
+
+
+def clocks_stop(p, path, gpu_index):
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    os.unlink(path)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(w, seconds=12.0, timer=time.perf_counter):
+    """The oracle's FP64 direct sum (C, OpenMP, all host cores) on a bounded
+    sample of targets against every source of the workload."""
+    from oracle.medium import Medium
+    from oracle.dcim import ImageTable
+    from oracle.direct import direct_sum
+    med = Medium(w.interfaces, w.k)
+    img = ImageTable(med, w.zext, n_images=w.n_images)
+    rng = np.random.default_rng(123)
+    n = 8
+    t0 = timer()
+    direct_sum(med, img, w.src, w.q, w.src[rng.choice(len(w.src), n, replace=False)])
+    dt = max(timer() - t0, 1e-3)
+    n = int(max(8, min(len(w.src), n * seconds / dt)))
+    tgt = w.src[rng.choice(len(w.src), n, replace=False)]
+    t0 = timer()
+    direct_sum(med, img, w.src, w.q, tgt)
+    dt = timer() - t0
+    cores = os.cpu_count()
+    return {"value": n * len(w.src) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 direct sum (C/OpenMP) for {n} sampled targets x all {len(w.src)} "
+                      f"sources of {w.name}, {dt:.1f} s"}
+
+
+def run_reference(args, w):
+    """--impl reference: the oracle on the host cores, one bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(w, seconds=2.0)
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(w, seconds=8.0)
+        vals.append(last["value"])
+    v = float(np.mean(vals))
+    ms = len(w.src) * len(w.src) / v * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": len(w.src), "p": w.p, "leaf_cap": w.leaf_cap,
+                       "n_images": w.n_images},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                             "sample": last["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1902_05875_gb300 import tefmm
+    plan = tefmm.Plan(w.interfaces, w.k, p=w.p, leaf_cap=w.leaf_cap, n_images=w.n_images, zext=w.zext)
+    x, y, z = [torch.tensor(np.ascontiguousarray(w.src[:, i]), device=dev) for i in range(3)]
+    q = torch.tensor(w.q, device=dev)
+    out = torch.empty(len(w.src), dtype=torch.complex128, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    for _ in range(max(3, args.warmup)):
+        plan.eval(x, y, z, q, out=out)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = plan.stats()["n_launches"]
+    cp, cpath = clocks_start()
+    times = []
+    phase = {k: [] for k in ("ms_tree", "ms_upward", "ms_tables", "ms_m2l", "ms_downward", "ms_near")}
+    barrier()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.eval(x, y, z, q, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        st = plan.stats()
+        for k in phase:
+            phase[k].append(st[k])
+    barrier()
+    clocks = clocks_stop(cp, cpath, local)
+    launches = plan.stats()["n_launches"] - launches0
+    ms = float(np.mean(times))
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    N = len(w.src)
+    value = world * N * N / (ms * 1e-3)
+    st = plan.stats()
+
+    # e2e: host buffers through tefmm_eval_host, copies inside the timed region
+    pin = {k: torch.tensor(np.ascontiguousarray(a)).pin_memory() for k, a in
+           (("src", w.src), ("q", np.stack([w.q.real, w.q.imag], -1)))}
+    src_h = pin["src"].numpy()
+    q_h = pin["q"].numpy()
+    qc = q_h[:, 0] + 1j * q_h[:, 1]
+    plan.eval_host(src_h, qc)
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.eval_host(src_h, qc)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_ms = float(np.mean(e2e_t)) * 1e3
+
+    # roofline of the dominant kernel (each timed phase is one kernel)
+    pk, pk_src = peaks()
+    ph = {k: float(np.mean(v)) for k, v in phase.items()}
+    dom = max(("ms_near", "ms_m2l", "ms_tables"), key=lambda k: ph[k])
+    imgs = plan.images()
+    n_img_layer = sum(len(t["A"]) for t in imgs if t["layer"] == 1)
+    np_ = plan.np
+    if dom == "ms_near":
+        flops = st["n_p2p_pairs"] * (FLOPS_FREE + FLOPS_IMAGE * n_img_layer)
+        kern = "k_near_fp64 (L2P + P2P, free space + DCIM images)"
+    elif dom == "ms_m2l":
+        flops = 2 * st["n_v_pairs"] * 8 * np_ * np_
+        kern = "k_m2l_fp64 (key-grouped complex M2L contraction)"
+    else:
+        np2 = (2 * w.p + 1) * (2 * w.p + 2) * (2 * w.p + 3) // 6
+        flops = st["n_tables"] * (n_img_layer + 1) * np2 * 40
+        kern = "k_tables (derivative recurrence)"
+    ach = flops / (ph[dom] * 1e-3) / 1e12
+    roof = {"kernel": kern, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "nominal GB300 FP64 (no measured FP64 figure)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n": N, "p": w.p, "leaf_cap": w.leaf_cap, "n_images": w.n_images,
+                   "precision": "fp64", "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "phases_ms": ph,
+        "counts": {"nodes": st["n_nodes"], "levels": st["n_levels"], "v_pairs": st["n_v_pairs"],
+                   "p2p_pairs": st["n_p2p_pairs"], "tables": st["n_tables"],
+                   "images_total": st["n_images_total"]},
+        "roofline": roof,
+        "e2e": {"value": world * N * N / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(N * 40), "d2h_bytes_per_step": int(N * 16),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "peaks_source": pk_src,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * tefmm.h -- C ABI of the GB300 Taylor-expansion FMM for the 3-D Helmholtz
+ * equation in layered media (Wang, Zhang, Cai: arXiv 1902.05875).
+ *
+ * The library computes the matrix-vector product of the paper's Sec. 3.1,
+ * eq. ``totalinteraction``:
+ *
+ *   Phi_l(r_i) = sum_{j in layer l, r_j != r_i} q_j h0(k_l |r_i - r_j|)
+ *              + sum_{l'} sum_{j in layer l'} q_j (u^up_{l l'} + u^down_{l l'})(r_i, r_j),
+ *
+ * with h0(z) = e^{iz}/(iz) and the factor i k_l / (4 pi) omitted (Sec. 3.1),
+ * by the TE-FMM of Algorithm 1 applied to every component of the heterogeneous
+ * loop that follows it (Sec. 3.3).  The reaction components are represented by
+ * discrete complex images (Sec. 3.2, eq. ``closedformgreen``) fitted at plan
+ * time.  Everything below these calls runs in this library's own CUDA kernels.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Medium: n_layers = L+1 layers numbered 0 (top) .. L (bottom); interfaces
+ *   z = d_0 > d_1 > ... > d_{L-1}; layer l is d_l < z < d_{l-1} (Sec. 2.1).
+ * - Complex numbers are interleaved (re, im) doubles.
+ * - Return value: TEFMM_OK (0) or a negative TEFMM_ERR_* code; nothing is
+ *   modified on an argument error.  tefmm_status_string() names the code.
+ * - Streams: ``stream`` is a cudaStream_t (NULL = legacy default stream).
+ *   Work is queued on it; calls that build trees read sizes back and so
+ *   synchronise the stream internally.
+ * - Memory: pointers named d_* are caller-owned DEVICE memory of the current
+ *   CUDA device; h_* are caller-owned HOST memory.  The library never frees
+ *   or retains caller memory.  A plan owns its tables and scratch, released by
+ *   tefmm_plan_destroy().
+ * - Threading: a plan may be used by one host thread at a time.
+ */
+#ifndef TEFMM_H
+#define TEFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TEFMM_OK 0
+#define TEFMM_ERR_INVALID_ARG (-1)        /* bad argument (sizes, ordering, NULL)        */
+#define TEFMM_ERR_POINT_ON_INTERFACE (-2) /* some z equals an interface depth exactly    */
+#define TEFMM_ERR_OUT_OF_DOMAIN (-3)      /* a point lies outside its layer's slab       */
+#define TEFMM_ERR_OOM (-4)                /* device allocation failed                    */
+#define TEFMM_ERR_CUDA (-5)               /* a CUDA runtime call failed                  */
+#define TEFMM_ERR_FIT_FAILED (-6)         /* DCIM fit produced no usable images          */
+#define TEFMM_ERR_LIST_OVERFLOW (-7)      /* an interaction list exceeded its capacity   */
+#define TEFMM_ERR_NOT_IMPLEMENTED (-8)    /* configuration not supported by this build   */
+#define TEFMM_ERR_DEVICE_CHECK (-9)       /* a device-side consistency check failed      */
+
+#define TEFMM_FP64 0   /* every step in FP64                                          */
+#define TEFMM_MIXED 1  /* M2L on tensor cores and P2P in FP32; FP64 tables and sums   */
+
+typedef struct tefmm_plan_s *tefmm_plan;
+
+typedef struct {
+    int p;                 /* Taylor order (|k| <= p), 1..12                          */
+    int leaf_cap;          /* split a box while max(#sources, #targets) > leaf_cap    */
+    int max_level;         /* deepest octree level, 1..20                             */
+    int precision;         /* TEFMM_FP64 or TEFMM_MIXED                               */
+    int n_images;          /* DCIM images per fitted term (<= 32; <= 24 per level)    */
+    int n_samples;         /* DCIM samples per level, 8..127 (Sec. 3.3 uses 101)     */
+    double T1;             /* length of the first-level path (Sec. 3.3 uses 10)       */
+    double T0;             /* second-level path; <= 0: sqrt(((max Re k + 0.8)/Re k_l)^2 - 1) */
+    double zext[2 * 16];   /* per layer (zlo, zhi): z-range of the particles, used for
+                              the DCIM shift zeta_min (Sec. 3.2, z_min); a point outside
+                              its layer's range is TEFMM_ERR_OUT_OF_DOMAIN             */
+} tefmm_options;
+
+typedef struct {
+    int n_nodes;           /* octree nodes, all layers                                */
+    int n_levels;          /* deepest level + 1                                       */
+    int64_t n_v_pairs;     /* M2L (V-list) pairs, all components                      */
+    int64_t n_p2p_pairs;   /* near-field (target, source) particle pairs              */
+    int n_tables;          /* derivative tables built (distinct M2L keys)             */
+    int n_images_total;    /* DCIM images held by the plan                            */
+    double ms_tree;        /* last eval: keys, sort, tree, lists                      */
+    double ms_upward;      /* P2M + M2M                                               */
+    double ms_tables;      /* derivative tables                                       */
+    double ms_m2l;         /* M2L contractions                                        */
+    double ms_downward;    /* L2L                                                     */
+    double ms_near;        /* L2P + P2P                                               */
+    double fit_max_resid;  /* worst DCIM fit residual on the samples (relative)       */
+    int64_t n_launches;    /* kernels of this library launched by this plan so far    */
+} tefmm_stats;
+
+/* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,
+ * 8 images, 101 samples, T1 = 10, T0 = formula, zext = whole layers. */
+int tefmm_default_options(tefmm_options *opt);
+
+/* Create a plan for a layered medium (Sec. 2.1) and fit its DCIM images
+ * (Sec. 3.2, Steps 1-2) on the device.
+ *   n_layers        1..8;
+ *   interfaces      host array [n_layers-1], strictly decreasing;
+ *   k_re, k_im      host arrays [n_layers], k_im >= 0;
+ *   opt             host struct (NULL = defaults);
+ *   stream          cudaStream_t used for the fits;
+ *   out             receives the plan.
+ * Errors: INVALID_ARG, OOM, CUDA, FIT_FAILED. */
+int tefmm_plan_create(int n_layers, const double *interfaces, const double *k_re,
+                      const double *k_im, const tefmm_options *opt, void *stream,
+                      tefmm_plan *out);
+
+/* Release a plan and everything it owns.  NULL is accepted. */
+int tefmm_plan_destroy(tefmm_plan plan);
+
+/* The matrix-vector product (Sec. 3.1, eq. ``totalinteraction``; Algorithm 1
+ * for every component).  Builds the octrees and lists for the given points,
+ * then runs the upward pass, the M2L translations, the downward pass, L2P and
+ * the near field.
+ *   ns, d_sx/d_sy/d_sz  source coordinates (device, ns doubles each);
+ *   d_q                 source charges (device, 2*ns doubles, interleaved);
+ *   nt, d_tx/d_ty/d_tz  target coordinates (device); passing the source
+ *                       pointers with nt == ns selects the "targets are the
+ *                       sources" case (self pairs skipped in free space only);
+ *   d_phi               output potentials (device, 2*nt doubles), overwritten.
+ * Errors: INVALID_ARG, POINT_ON_INTERFACE, OUT_OF_DOMAIN, OOM, CUDA,
+ *         LIST_OVERFLOW, DEVICE_CHECK.  ns == 0 or nt == 0 writes zeros. */
+int tefmm_eval(tefmm_plan plan, int64_t ns, const double *d_sx, const double *d_sy,
+               const double *d_sz, const double *d_q, int64_t nt, const double *d_tx,
+               const double *d_ty, const double *d_tz, double *d_phi, void *stream);
+
+/* Same as tefmm_eval with HOST arrays: copies the inputs to plan-owned device
+ * buffers, evaluates, copies Phi back, and synchronises the stream. */
+int tefmm_eval_host(tefmm_plan plan, int64_t ns, const double *h_sx, const double *h_sy,
+                    const double *h_sz, const double *h_q, int64_t nt, const double *h_tx,
+                    const double *h_ty, const double *h_tz, double *h_phi, void *stream);
+
+/* Statistics and phase timings of the last evaluation (host struct). */
+int tefmm_get_stats(tefmm_plan plan, tefmm_stats *out);
+
+/* Human-readable name of a status code (static string). */
+const char *tefmm_status_string(int status);
+
+/* ---- inspection hooks (used by the parity tests) ------------------------
+ * Images are described per (layer, term): term tags 0 = up-up, 1 = down-down,
+ * 2 = up-down, 3 = down-up.  A same-layer reaction term is written with a real
+ * image distance zeta = sz*z + szp*z' + c (> 0 inside the layer) and contributes
+ * sum_j A_j h0(k_l sqrt(rho^2 + (zeta - zeta_min - Z_j)^2)) (Sec. 3.2, Step 3,
+ * eq. ``closedformgreen`` with the density's reflection exponentials folded
+ * into zeta).  For each term: sz, szp, c, zeta_min and its images (A_j, Z_j).
+ */
+
+/* Number of (layer, term) entries and of images held by the plan. */
+int tefmm_plan_image_counts(tefmm_plan plan, int *n_terms, int *n_images);
+
+/* Copy the plan's images to host arrays:
+ *   term_layer[n_terms], term_tag[n_terms], term_first[n_terms], term_count[n_terms],
+ *   term_geom[4*n_terms] = (sz, szp, c, zeta_min), A[2*n_images], Z[2*n_images]. */
+int tefmm_plan_get_images(tefmm_plan plan, int *term_layer, int *term_tag, int *term_first,
+                          int *term_count, double *term_geom, double *A, double *Z);
+
+/* Replace the images of every term (same term layout as get_images: same
+ * n_terms, per-term counts may change, total <= 32 * n_terms). */
+int tefmm_plan_set_images(tefmm_plan plan, const int *term_count, const double *A,
+                          const double *Z);
+
+/* Tree of the last evaluation.  With all pointers NULL only the counts are
+ * returned.  Node arrays (host, n_nodes each): layer, level, ix, iy, iz,
+ * parent, s0, s1, t0, t1 (ranges in the sorted source / target order);
+ * perm_s[ns], perm_t[nt]: sorted position -> input index. */
+int tefmm_export_tree(tefmm_plan plan, int *n_nodes, int64_t *ns, int64_t *nt, int *layer,
+                      int *level, int *ix, int *iy, int *iz, int *parent, int *s0, int *s1,
+                      int *t0, int *t1, int *perm_s, int *perm_t);
+
+/* Interaction lists of the last evaluation as CSR over target nodes:
+ * V lists (M2L) and near-field lists (target leaves only; empty elsewhere).
+ * With NULL arrays only the sizes are returned. */
+int tefmm_export_lists(tefmm_plan plan, int64_t *n_v, int64_t *n_near, int *v_ptr, int *v_src,
+                       int *near_ptr, int *near_src);
+
+/* Moments (P2M/M2M) and locals (after L2L, before L2P) of the last
+ * evaluation: host arrays [n_nodes * n_coeffs * 2] in graded multi-index order
+ * (n = 0..p; k1 = n..0; k2 = n-k1..0; k3 = n-k1-k2).  NULL skips one. */
+int tefmm_export_expansions(tefmm_plan plan, double *alpha, double *beta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TEFMM_H */

@@ -18,14 +18,14 @@ Follows Sec. 3 of the paper:
 Readings where the paper is silent (all stated the same way for the CUDA path):
 * One octree per layer, all in one root cube: lo = min over all points per
   axis, side = max over axes of (max - min) (1 if zero).  Integer box
-  coordinates i = min(floor(((x - lo) / side) * 2^21), 2^21 - 1) with plain
-  IEEE double operations (no fused multiply-add); 63-bit Morton keys with bit
+  coordinates i = min(floor(((x - lo) / side) * 2^20), 2^20 - 1) with plain
+  IEEE double operations (no fused multiply-add); 60-bit Morton keys with bit
   3b+2 = bit b of ix, 3b+1 = iy, 3b = iz.  Points are sorted by (layer, key,
   input index).  Box centre of coordinate i at level l: lo + (i + 0.5) *
   (side / 2^l).
 * A box is split while max(#sources, #targets) > leaf_cap and level <
-  max_level; only children holding a point exist.  Nodes are ordered by
-  (layer, level, Morton prefix).
+  max_level; only children holding a point exist.  Nodes are numbered
+  level-major: by (level, layer, Morton prefix).
 * Interaction lists: a dual-tree traversal of (target tree, source tree),
   which for one tree is the classic adaptive U/V/W/X construction
   (Carrier-Greengard-Rokhlin).  V pairs go through M2L; U, W and X pairs are
@@ -45,7 +45,7 @@ import numpy as np
 
 from .derivs import multi_indices, index_map, n_coeffs, taylor_h0
 
-NBITS = 21
+NBITS = 20
 
 
 def morton_encode(ix, iy, iz):
@@ -111,6 +111,7 @@ class Trees:
         nodes = []      # (layer, level, prefix, parent, s0, s1, t0, t1)
         children = []
         self.root = {}
+        frontier = []
         for l in range(med.n_layers):
             s0, s1 = np.searchsorted(sl, l, 'left'), np.searchsorted(sl, l, 'right')
             t0, t1 = np.searchsorted(tl, l, 'left'), np.searchsorted(tl, l, 'right')
@@ -119,35 +120,32 @@ class Trees:
             self.root[l] = len(nodes)
             nodes.append([l, 0, 0, -1, s0, s1, t0, t1])
             children.append([])
-            frontier = [self.root[l]]
-            level = 0
-            while frontier:
-                nxt = []
-                for nid in frontier:
-                    _, lev, pre, _, a0, a1, b0, b1 = nodes[nid]
-                    if max(a1 - a0, b1 - b0) <= leaf_cap or lev >= max_level:
+            frontier.append(self.root[l])
+        # level-major: all level-(l+1) nodes after all level-l nodes; within a
+        # level parents are visited in (layer, prefix) order and children in
+        # child-index order, so a level is ordered by (layer, prefix).
+        while frontier:
+            nxt = []
+            for nid in frontier:
+                l, lev, pre, _, a0, a1, b0, b1 = nodes[nid]
+                if max(a1 - a0, b1 - b0) <= leaf_cap or lev >= max_level:
+                    continue
+                shift = np.uint64(3 * (NBITS - lev - 1))
+                sc = (sk[a0:a1] >> shift) & np.uint64(7)
+                tc = (tk[b0:b1] >> shift) & np.uint64(7)
+                for c in range(8):
+                    cs0 = a0 + np.searchsorted(sc, c, 'left')
+                    cs1 = a0 + np.searchsorted(sc, c, 'right')
+                    ct0 = b0 + np.searchsorted(tc, c, 'left')
+                    ct1 = b0 + np.searchsorted(tc, c, 'right')
+                    if cs1 - cs0 + ct1 - ct0 == 0:
                         continue
-                    shift = np.uint64(3 * (NBITS - lev - 1))
-                    sc = (sk[a0:a1] >> shift) & np.uint64(7)
-                    tc = (tk[b0:b1] >> shift) & np.uint64(7)
-                    for c in range(8):
-                        cs0 = a0 + np.searchsorted(sc, c, 'left')
-                        cs1 = a0 + np.searchsorted(sc, c, 'right')
-                        ct0 = b0 + np.searchsorted(tc, c, 'left')
-                        ct1 = b0 + np.searchsorted(tc, c, 'right')
-                        if cs1 - cs0 + ct1 - ct0 == 0:
-                            continue
-                        cid = len(nodes)
-                        nodes.append([l, lev + 1, (pre << 3) | c, nid, cs0, cs1, ct0, ct1])
-                        children.append([])
-                        children[nid].append(cid)
-                        nxt.append(cid)
-                frontier = nxt
-                level += 1
-        # reorder within each layer by (level, prefix): BFS above already gives
-        # level order and, because parents are visited in prefix order and
-        # children in child-index order, ascending prefix within a level.
-        arr = np.array(nodes, dtype=object)
+                    cid = len(nodes)
+                    nodes.append([l, lev + 1, (pre << 3) | c, nid, cs0, cs1, ct0, ct1])
+                    children.append([])
+                    children[nid].append(cid)
+                    nxt.append(cid)
+            frontier = nxt
         self.n_nodes = len(nodes)
         self.layer = np.array([n[0] for n in nodes], dtype=np.int64)
         self.level = np.array([n[1] for n in nodes], dtype=np.int64)
@@ -166,7 +164,6 @@ class Trees:
         self.ix = np.array(ix, dtype=np.int64)
         self.iy = np.array(iy, dtype=np.int64)
         self.iz = np.array(iz, dtype=np.int64)
-        del arr
 
     def ns(self, n):
         return self.s1[n] - self.s0[n]

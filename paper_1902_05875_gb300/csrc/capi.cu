@@ -1,0 +1,173 @@
+// C-ABI entry points: evaluation, statistics and inspection hooks.
+#include <string.h>
+
+#include "internal.cuh"
+
+extern "C" const char *tefmm_status_string(int s) {
+    switch (s) {
+        case TEFMM_OK: return "ok";
+        case TEFMM_ERR_INVALID_ARG: return "invalid argument";
+        case TEFMM_ERR_POINT_ON_INTERFACE: return "a point lies exactly on an interface";
+        case TEFMM_ERR_OUT_OF_DOMAIN: return "a point lies outside its layer's particle range";
+        case TEFMM_ERR_OOM: return "device allocation failed";
+        case TEFMM_ERR_CUDA: return "CUDA runtime error";
+        case TEFMM_ERR_FIT_FAILED: return "DCIM fit failed";
+        case TEFMM_ERR_LIST_OVERFLOW: return "interaction list capacity exceeded";
+        case TEFMM_ERR_NOT_IMPLEMENTED: return "configuration not implemented";
+        case TEFMM_ERR_DEVICE_CHECK: return "device-side check failed";
+        default: return "unknown status";
+    }
+}
+
+namespace {
+__global__ void k_zero(int64_t n, double *a) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 0.0;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+}  // namespace
+
+extern "C" int tefmm_eval(tefmm_plan P, int64_t ns, const double *sx, const double *sy,
+                          const double *sz, const double *q, int64_t nt, const double *tx,
+                          const double *ty, const double *tz, double *phi, void *stream) {
+    if (!P || ns < 0 || nt < 0 || ns > (1LL << 30) || nt > (1LL << 30)) return TEFMM_ERR_INVALID_ARG;
+    if (nt > 0 && !phi) return TEFMM_ERR_INVALID_ARG;
+    if (ns > 0 && (!sx || !sy || !sz || !q)) return TEFMM_ERR_INVALID_ARG;
+    if (nt > 0 && (!tx || !ty || !tz)) return TEFMM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ns == 0 || nt == 0) {
+        if (nt > 0) {
+            k_zero<<<grid_for(2 * nt, 256), 256, 0, st>>>(2 * nt, phi);
+            P->launches++;
+        }
+        CUDA_TRY(cudaGetLastError());
+        return TEFMM_OK;
+    }
+    P->ns = ns;
+    P->nt = nt;
+    P->shared_pts = (tx == sx && ty == sy && tz == sz && nt == ns);
+    CUDA_TRY(cudaEventRecord(P->ev[0], st));
+    TRY(tree_build(P, sx, sy, sz, q, tx, ty, tz, st));
+    TRY(check_flags(P, st));
+    TRY(lists_build(P, st));
+    TRY(check_flags(P, st));
+    TRY(m2l_prepare(P, st));
+    CUDA_TRY(cudaEventRecord(P->ev[1], st));
+    TRY(upward_pass(P, st));
+    CUDA_TRY(cudaEventRecord(P->ev[2], st));
+    TRY(m2l_tables(P, st));
+    CUDA_TRY(cudaEventRecord(P->ev[3], st));
+    TRY(m2l_apply(P, st));
+    CUDA_TRY(cudaEventRecord(P->ev[4], st));
+    TRY(downward_pass(P, st));
+    CUDA_TRY(cudaEventRecord(P->ev[5], st));
+    TRY(near_field(P, phi, st));
+    CUDA_TRY(cudaEventRecord(P->ev[6], st));
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_eval_host(tefmm_plan P, int64_t ns, const double *sx, const double *sy,
+                               const double *sz, const double *q, int64_t nt, const double *tx,
+                               const double *ty, const double *tz, double *phi, void *stream) {
+    if (!P || ns < 0 || nt < 0) return TEFMM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    bool shared = (tx == sx && ty == sy && tz == sz && nt == ns);
+    size_t nin = (size_t)ns * 5 + (shared ? 0 : (size_t)nt * 3);
+    TRY(dbuf_ensure(P->h_in, nin * sizeof(double) + 64));
+    TRY(dbuf_ensure(P->h_out, (size_t)nt * 2 * sizeof(double) + 64));
+    double *d = dp<double>(P->h_in);
+    double *dsx = d, *dsy = d + ns, *dsz = d + 2 * ns, *dq = d + 3 * ns;
+    double *dtx = dsx, *dty = dsy, *dtz = dsz;
+    if (ns > 0) {
+        CUDA_TRY(cudaMemcpyAsync(dsx, sx, ns * 8, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(dsy, sy, ns * 8, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(dsz, sz, ns * 8, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(dq, q, ns * 16, cudaMemcpyHostToDevice, st));
+    }
+    if (!shared && nt > 0) {
+        dtx = d + 5 * ns;
+        dty = dtx + nt;
+        dtz = dty + nt;
+        CUDA_TRY(cudaMemcpyAsync(dtx, tx, nt * 8, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(dty, ty, nt * 8, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyAsync(dtz, tz, nt * 8, cudaMemcpyHostToDevice, st));
+    }
+    TRY(tefmm_eval(P, ns, dsx, dsy, dsz, dq, nt, dtx, dty, dtz, dp<double>(P->h_out), stream));
+    if (nt > 0) CUDA_TRY(cudaMemcpyAsync(phi, P->h_out.p, nt * 16, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
+    if (!P || !o) return TEFMM_ERR_INVALID_ARG;
+    memset(o, 0, sizeof(*o));
+    o->n_nodes = P->n_nodes;
+    o->n_levels = P->n_levels;
+    o->n_v_pairs = P->n_v;
+    o->n_p2p_pairs = P->n_p2p_pairs;
+    o->n_tables = P->n_tables;
+    o->n_images_total = (int)P->A.size();
+    o->fit_max_resid = P->fit_max_resid;
+    o->n_launches = P->launches;
+    if (P->n_nodes > 0 && cudaEventQuery(P->ev[6]) == cudaSuccess) {
+        o->ms_tree = elapsed(P->ev[0], P->ev[1]);
+        o->ms_upward = elapsed(P->ev[1], P->ev[2]);
+        o->ms_tables = elapsed(P->ev[2], P->ev[3]);
+        o->ms_m2l = elapsed(P->ev[3], P->ev[4]);
+        o->ms_downward = elapsed(P->ev[4], P->ev[5]);
+        o->ms_near = elapsed(P->ev[5], P->ev[6]);
+    }
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_export_tree(tefmm_plan P, int *n_nodes, int64_t *ns, int64_t *nt, int *layer,
+                                 int *level, int *ix, int *iy, int *iz, int *parent, int *s0,
+                                 int *s1, int *t0, int *t1, int *perm_s, int *perm_t) {
+    if (!P) return TEFMM_ERR_INVALID_ARG;
+    if (n_nodes) *n_nodes = P->n_nodes;
+    if (ns) *ns = P->ns;
+    if (nt) *nt = P->nt;
+    const int nn = P->n_nodes;
+    struct {
+        int *h;
+        DBuf *d;
+    } m[] = {{layer, &P->n_layer}, {level, &P->n_level}, {ix, &P->n_ix}, {iy, &P->n_iy},
+             {iz, &P->n_iz},       {parent, &P->n_parent}, {s0, &P->n_s0}, {s1, &P->n_s1},
+             {t0, &P->n_t0},       {t1, &P->n_t1}};
+    for (auto &e : m)
+        if (e.h && nn > 0) CUDA_TRY(cudaMemcpy(e.h, e.d->p, nn * sizeof(int), cudaMemcpyDeviceToHost));
+    if (perm_s && P->ns > 0) CUDA_TRY(cudaMemcpy(perm_s, P->perm_s.p, P->ns * 4, cudaMemcpyDeviceToHost));
+    if (perm_t && P->nt > 0)
+        CUDA_TRY(cudaMemcpy(perm_t, P->shared_pts ? P->perm_s.p : P->perm_t.p, P->nt * 4,
+                            cudaMemcpyDeviceToHost));
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_export_lists(tefmm_plan P, int64_t *n_v, int64_t *n_near, int *v_ptr,
+                                  int *v_src, int *near_ptr, int *near_src) {
+    if (!P) return TEFMM_ERR_INVALID_ARG;
+    if (n_v) *n_v = P->n_v;
+    if (n_near) *n_near = P->n_near;
+    const int nn = P->n_nodes;
+    if (v_ptr && nn > 0) CUDA_TRY(cudaMemcpy(v_ptr, P->v_ptr.p, (nn + 1) * 4, cudaMemcpyDeviceToHost));
+    if (near_ptr && nn > 0)
+        CUDA_TRY(cudaMemcpy(near_ptr, P->near_ptr.p, (nn + 1) * 4, cudaMemcpyDeviceToHost));
+    if (v_src && P->n_v > 0) CUDA_TRY(cudaMemcpy(v_src, P->v_src.p, P->n_v * 4, cudaMemcpyDeviceToHost));
+    if (near_src && P->n_near > 0)
+        CUDA_TRY(cudaMemcpy(near_src, P->near_src.p, P->n_near * 4, cudaMemcpyDeviceToHost));
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_export_expansions(tefmm_plan P, double *alpha, double *beta) {
+    if (!P) return TEFMM_ERR_INVALID_ARG;
+    size_t n = (size_t)P->n_nodes * P->np * sizeof(cplx);
+    if (alpha && n) CUDA_TRY(cudaMemcpy(alpha, P->alpha.p, n, cudaMemcpyDeviceToHost));
+    if (beta && n) CUDA_TRY(cudaMemcpy(beta, P->beta.p, n, cudaMemcpyDeviceToHost));
+    return TEFMM_OK;
+}

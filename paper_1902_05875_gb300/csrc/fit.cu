@@ -1,0 +1,632 @@
+// Plan-time DCIM fits on the device (Sec. 3.2, Steps 1-2), one CTA per fit.
+//
+// Step 1 samples, on the two paths of the k_lz plane
+//   C_ap1: k_lz = i k_l (T0 + t), 0 <= t <= T1;   C_ap2: k_lz = k_l (1 - t/T0 + i t), 0 <= t <= T0,
+// the function F(k_z) = s_tau(k_rho) e^{i k_z zeta_min} of one same-layer
+// reaction term, where s_tau is the multiple-reflection factor of the term's
+// density: the densities come from a direct solve of the interface conditions
+// of Sec. 2.1 (u continuous, k-weighted flux continuous, decay at +-inf) at
+// every sample.  Step 2 fits sum_j A_j e^{-i k_z Z_j} with the generalized
+// pencil-of-function method (Hua & Sarkar): a Hankel data matrix, its SVD (a
+// one-sided complex Jacobi method), the eigenvalues of the m x m pencil
+// V2^H V1 (V1^H V1)^{-1} (Hessenberg reduction + shifted QR), and the
+// amplitudes by Householder least squares.  The first level keeps only
+// decaying poles; the second level fits what the first leaves on C_ap2.
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int MAXN = 127;        // samples per level
+constexpr int MAXC = 64;         // Hankel columns (pencil parameter + 1, even)
+constexpr int MAXU = 16;         // unknowns of the interface solve (8 layers)
+constexpr int MAXM = TEFMM_MAX_IMG;  // images per fit (both levels)
+constexpr int MAXLS = 24;            // images per level
+constexpr double REL_TOL = 1e-12;
+constexpr double ABS_TOL = 1e-14;
+
+struct FitJob {
+    int layer, tag, nL;
+    double d[TEFMM_MAX_LAYERS];
+    cplx k[TEFMM_MAX_LAYERS];
+    double zmin, T0, T1;
+    int n, n_images;
+};
+
+__device__ __forceinline__ cplx conjc(cplx a) { return mkc(a.x, -a.y); }
+__device__ __forceinline__ double abs2(cplx a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ double cabs_(cplx a) { return hypot(a.x, a.y); }
+__device__ __forceinline__ cplx clog_(cplx a) { return mkc(log(cabs_(a)), atan2(a.y, a.x)); }
+
+__device__ cplx kz_of(cplx k, cplx krho2) {
+    // sqrt(k^2 - k_rho^2) with Im >= 0
+    cplx s = csqrt_p(csub(cmul(k, k), krho2));
+    if (s.y < 0) s = mkc(-s.x, -s.y);
+    return s;
+}
+
+// s_tau at one sample.  Unknowns: b_0, (a_1, b_1), ..., (a_{L-1}, b_{L-1}), a_L.
+// Basis: up-going b e^{i kz (z - d_l)} / kz (bottom interface reference),
+// down-going a e^{-i kz (z - d_{l-1})} / kz (top interface reference).
+__device__ cplx s_tau_sample(const FitJob &J, cplx kz_l) {
+    const int L = J.nL - 1, nu = 2 * L;
+    cplx krho2 = csub(cmul(J.k[J.layer], J.k[J.layer]), cmul(kz_l, kz_l));
+    cplx kz[TEFMM_MAX_LAYERS];
+    for (int m = 0; m <= L; ++m) kz[m] = kz_of(J.k[m], krho2);
+    cplx A[MAXU][MAXU + 2];
+    for (int r = 0; r < nu; ++r)
+        for (int c = 0; c < nu + 2; ++c) A[r][c] = mkc(0, 0);
+    for (int j = 0; j < L; ++j) {
+        for (int side = 0; side < 2; ++side) {
+            int m = j + side;
+            double sg = side == 0 ? 1.0 : -1.0;
+            cplx kw = J.k[m];
+            // b basis (m < L)
+            if (m < L) {
+                int col = 2 * m;
+                cplx ex = cexp_(cmul(mkc(0, 1), cscale(kz[m], J.d[j] - J.d[m])));
+                cplx v = cdiv(ex, kz[m]);
+                cplx dv = cmul(mkc(0, 1), ex);
+                A[2 * j][col] = cadd(A[2 * j][col], cscale(v, sg));
+                A[2 * j + 1][col] = cadd(A[2 * j + 1][col], cscale(cmul(kw, dv), sg));
+            }
+            if (m > 0) {
+                int col = 2 * m - 1;
+                cplx ex = cexp_(cmul(mkc(0, -1), cscale(kz[m], J.d[j] - J.d[m - 1])));
+                cplx v = cdiv(ex, kz[m]);
+                cplx dv = cmul(mkc(0, -1), ex);
+                A[2 * j][col] = cadd(A[2 * j][col], cscale(v, sg));
+                A[2 * j + 1][col] = cadd(A[2 * j + 1][col], cscale(cmul(kw, dv), sg));
+            }
+        }
+    }
+    const int lp = J.layer;
+    // right-hand sides: column nu = unit wave S1 (source below interface lp-1),
+    // column nu+1 = unit wave S2 (source above interface lp)
+    if (lp > 0) {
+        int j = lp - 1;
+        A[2 * j][nu] = cadd(A[2 * j][nu], cdiv(mkc(1, 0), kz[lp]));
+        A[2 * j + 1][nu] = cadd(A[2 * j + 1][nu], cmul(J.k[lp], mkc(0, 1)));
+    }
+    if (lp < L) {
+        int j = lp;
+        A[2 * j][nu + 1] = csub(A[2 * j][nu + 1], cdiv(mkc(1, 0), kz[lp]));
+        A[2 * j + 1][nu + 1] = csub(A[2 * j + 1][nu + 1], cmul(J.k[lp], mkc(0, -1)));
+    }
+    // Gaussian elimination with partial pivoting
+    for (int c = 0; c < nu; ++c) {
+        int piv = c;
+        double best = abs2(A[c][c]);
+        for (int r = c + 1; r < nu; ++r)
+            if (abs2(A[r][c]) > best) {
+                best = abs2(A[r][c]);
+                piv = r;
+            }
+        if (piv != c)
+            for (int q = 0; q < nu + 2; ++q) {
+                cplx t = A[c][q];
+                A[c][q] = A[piv][q];
+                A[piv][q] = t;
+            }
+        cplx inv = cdiv(mkc(1, 0), A[c][c]);
+        for (int r = c + 1; r < nu; ++r) {
+            cplx f = cmul(A[r][c], inv);
+            if (f.x == 0 && f.y == 0) continue;
+            for (int q = c; q < nu + 2; ++q) A[r][q] = csub(A[r][q], cmul(f, A[c][q]));
+        }
+    }
+    cplx x[MAXU][2];
+    for (int r = nu - 1; r >= 0; --r)
+        for (int h = 0; h < 2; ++h) {
+            cplx s = A[r][nu + h];
+            for (int q = r + 1; q < nu; ++q) s = csub(s, cmul(A[r][q], x[q][h]));
+            x[r][h] = cdiv(s, A[r][r]);
+        }
+    const int l = J.layer;
+    cplx eD = mkc(1, 0);
+    if (l > 0 && l < L) eD = cexp_(cmul(mkc(0, -1), cscale(kz[l], J.d[l - 1] - J.d[l])));  // e^{-i kz D}
+    switch (J.tag) {
+        case 0: return x[2 * l][1];                       // up-up: b_l(S2)
+        case 1: return x[2 * l - 1][0];                   // down-down: a_l(S1), top reference
+        case 2: return cmul(x[2 * l][0], eD);             // up-down: b_l(S1) e^{-i kz D}
+        default: return cmul(x[2 * l - 1][1], eD);        // down-up: a_l(S2) e^{-i kz D}
+    }
+}
+
+// ---------------------------------------------------------------- GPOF
+struct GpofSmem {
+    union {
+        cplx Y[MAXC][MAXC];          // column-major Hankel data (column c, row r)
+        cplx Q[MAXN][MAXLS + 1];     // least-squares work (after the pencil step)
+    };
+    cplx V[MAXC][MAXC];      // right rotations (column c, row r)
+    cplx y[MAXN];
+    cplx res[MAXN];
+    double sv[MAXC];
+    int order[MAXC];
+    int arr[MAXC];
+    cplx H[MAXLS][MAXLS];
+    cplx B2[MAXLS][MAXLS];
+    cplx zp[MAXLS];
+    cplx bb[MAXLS];
+    int m;
+    int nconv;
+};
+
+// one-sided Jacobi on the ncol (even) columns of Y, rows nrow; V accumulates.
+__device__ void jacobi_svd(GpofSmem &S, int nrow, int ncol) {
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = threadIdx.x; c < ncol * ncol; c += blockDim.x) {
+        int a = c / ncol, b = c % ncol;
+        S.V[a][b] = mkc(a == b ? 1.0 : 0.0, 0.0);
+    }
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) S.arr[c] = c;
+    __syncthreads();
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        if (threadIdx.x == 0) S.nconv = 0;
+        __syncthreads();
+        for (int round = 0; round < ncol - 1; ++round) {
+            for (int pi = warp; pi < ncol / 2; pi += nw) {
+                int p = S.arr[pi], q = S.arr[ncol - 1 - pi];
+                if (p > q) {
+                    int t = p;
+                    p = q;
+                    q = t;
+                }
+                double al = 0, be = 0;
+                cplx ga = mkc(0, 0);
+                for (int r = lane; r < nrow; r += 32) {
+                    cplx a = S.Y[p][r], b = S.Y[q][r];
+                    al += abs2(a);
+                    be += abs2(b);
+                    ga = cadd(ga, cmul(conjc(a), b));
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga.x += __shfl_xor_sync(0xffffffffu, ga.x, o);
+                    ga.y += __shfl_xor_sync(0xffffffffu, ga.y, o);
+                }
+                double g = cabs_(ga);
+                if (g > 1e-15 * sqrt(al * be) && g > 1e-300) {
+                    if (lane == 0) atomicAdd(&S.nconv, 1);
+                    double zeta = (be - al) / (2.0 * g);
+                    double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                    cplx ph = cscale(ga, 1.0 / g);   // e^{i phi}
+                    for (int r = lane; r < nrow; r += 32) {
+                        cplx a = S.Y[p][r], b = S.Y[q][r];
+                        cplx pb = cmul(ph, b);
+                        S.Y[p][r] = csub(cscale(a, c), cscale(pb, s));
+                        S.Y[q][r] = cadd(cscale(a, s), cscale(pb, c));
+                    }
+                    for (int r = lane; r < ncol; r += 32) {
+                        cplx a = S.V[p][r], b = S.V[q][r];
+                        cplx pb = cmul(ph, b);
+                        S.V[p][r] = csub(cscale(a, c), cscale(pb, s));
+                        S.V[q][r] = cadd(cscale(a, s), cscale(pb, c));
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int last = S.arr[ncol - 1];
+                for (int i = ncol - 1; i > 1; --i) S.arr[i] = S.arr[i - 1];
+                S.arr[1] = last;
+            }
+            __syncthreads();
+        }
+        if (S.nconv == 0) break;
+        __syncthreads();
+    }
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        double s = 0;
+        for (int r = 0; r < nrow; ++r) s += abs2(S.Y[c][r]);
+        S.sv[c] = sqrt(s);
+    }
+    __syncthreads();
+}
+
+// eigenvalues of the m x m complex matrix S.H (destroyed), single thread
+__device__ void eig_small(GpofSmem &S, int n) {
+    // Householder reduction to upper Hessenberg form
+    for (int k = 0; k < n - 2; ++k) {
+        double nx = 0;
+        for (int i = k + 1; i < n; ++i) nx += abs2(S.H[i][k]);
+        nx = sqrt(nx);
+        if (nx == 0) continue;
+        cplx x0 = S.H[k + 1][k];
+        double a0 = cabs_(x0);
+        cplx ph = a0 > 0 ? cscale(x0, 1.0 / a0) : mkc(1, 0);
+        cplx alpha = cscale(ph, -nx);
+        cplx v[MAXLS];
+        for (int i = 0; i < n; ++i) v[i] = mkc(0, 0);
+        for (int i = k + 1; i < n; ++i) v[i] = S.H[i][k];
+        v[k + 1] = csub(v[k + 1], alpha);
+        double nv = 0;
+        for (int i = k + 1; i < n; ++i) nv += abs2(v[i]);
+        nv = sqrt(nv);
+        if (nv == 0) continue;
+        for (int i = k + 1; i < n; ++i) v[i] = cscale(v[i], 1.0 / nv);
+        // H = (I - 2 v v^H) H
+        for (int j = 0; j < n; ++j) {
+            cplx s = mkc(0, 0);
+            for (int i = k + 1; i < n; ++i) s = cadd(s, cmul(conjc(v[i]), S.H[i][j]));
+            for (int i = k + 1; i < n; ++i) S.H[i][j] = csub(S.H[i][j], cscale(cmul(v[i], s), 2.0));
+        }
+        // H = H (I - 2 v v^H)
+        for (int i = 0; i < n; ++i) {
+            cplx s = mkc(0, 0);
+            for (int j = k + 1; j < n; ++j) s = cadd(s, cmul(S.H[i][j], v[j]));
+            for (int j = k + 1; j < n; ++j) S.H[i][j] = csub(S.H[i][j], cscale(cmul(s, conjc(v[j])), 2.0));
+        }
+    }
+    int hi = n - 1, iter = 0;
+    double cs[MAXLS];
+    cplx sn[MAXLS];
+    while (hi >= 0) {
+        if (hi == 0) {
+            S.zp[0] = S.H[0][0];
+            break;
+        }
+        int l = hi;
+        for (; l > 0; --l) {
+            double sc = cabs_(S.H[l][l]) + cabs_(S.H[l - 1][l - 1]);
+            if (cabs_(S.H[l][l - 1]) <= 1e-16 * (sc > 0 ? sc : 1.0)) {
+                S.H[l][l - 1] = mkc(0, 0);
+                break;
+            }
+        }
+        if (l == hi) {
+            S.zp[hi] = S.H[hi][hi];
+            --hi;
+            iter = 0;
+            continue;
+        }
+        if (++iter > 300) {       // give up: take the diagonal
+            for (int i = l; i <= hi; ++i) S.zp[i] = S.H[i][i];
+            hi = l - 1;
+            iter = 0;
+            continue;
+        }
+        cplx a = S.H[hi - 1][hi - 1], b = S.H[hi - 1][hi], c = S.H[hi][hi - 1], d = S.H[hi][hi];
+        cplx mu;
+        if (iter % 11 == 10) {
+            mu = cadd(d, mkc(cabs_(c), 0));
+        } else {
+            cplx half = cscale(csub(a, d), 0.5);
+            cplx disc = csqrt_p(cadd(cmul(half, half), cmul(b, c)));
+            cplx m1 = cadd(cscale(cadd(a, d), 0.5), disc), m2 = csub(cscale(cadd(a, d), 0.5), disc);
+            mu = cabs_(csub(m1, d)) < cabs_(csub(m2, d)) ? m1 : m2;
+        }
+        for (int i = l; i <= hi; ++i) S.H[i][i] = csub(S.H[i][i], mu);
+        for (int k2 = l; k2 < hi; ++k2) {
+            cplx x = S.H[k2][k2], y = S.H[k2 + 1][k2];
+            double r = sqrt(abs2(x) + abs2(y));
+            double c0;
+            cplx s0;
+            if (r == 0) {
+                c0 = 1;
+                s0 = mkc(0, 0);
+            } else if (cabs_(x) == 0) {
+                c0 = 0;
+                s0 = cscale(conjc(y), 1.0 / r);
+            } else {
+                double ax = cabs_(x);
+                c0 = ax / r;
+                s0 = cscale(cmul(cscale(x, 1.0 / ax), conjc(y)), 1.0 / r);
+            }
+            cs[k2] = c0;
+            sn[k2] = s0;
+            for (int j = k2; j <= hi; ++j) {
+                cplx u = S.H[k2][j], w = S.H[k2 + 1][j];
+                S.H[k2][j] = cadd(cscale(u, c0), cmul(s0, w));
+                S.H[k2 + 1][j] = csub(cscale(w, c0), cmul(conjc(s0), u));
+            }
+        }
+        for (int k2 = l; k2 < hi; ++k2) {
+            double c0 = cs[k2];
+            cplx s0 = sn[k2];
+            int top = k2 + 2 < hi ? k2 + 2 : hi;
+            for (int i = l; i <= top; ++i) {
+                cplx u = S.H[i][k2], w = S.H[i][k2 + 1];
+                S.H[i][k2] = cadd(cscale(u, c0), cmul(conjc(s0), w));
+                S.H[i][k2 + 1] = csub(cscale(w, c0), cmul(s0, u));
+            }
+        }
+        for (int i = l; i <= hi; ++i) S.H[i][i] = cadd(S.H[i][i], mu);
+    }
+}
+
+// least squares  min || sum_j b_j z_j^n - y_n ||, n < N, single thread (Householder)
+__device__ void vandermonde_lsq(GpofSmem &S, int N, int m) {
+    for (int n = 0; n < N; ++n) {
+        for (int j = 0; j < m; ++j) {
+            // z^n by repeated multiplication
+            cplx v = mkc(1, 0);
+            for (int e = 0; e < n; ++e) v = cmul(v, S.zp[j]);
+            S.Q[n][j] = v;
+        }
+        S.Q[n][m] = S.res[n];
+    }
+    for (int j = 0; j < m; ++j) {
+        double nx = 0;
+        for (int i = j; i < N; ++i) nx += abs2(S.Q[i][j]);
+        nx = sqrt(nx);
+        if (nx == 0) continue;
+        cplx x0 = S.Q[j][j];
+        double a0 = cabs_(x0);
+        cplx ph = a0 > 0 ? cscale(x0, 1.0 / a0) : mkc(1, 0);
+        cplx alpha = cscale(ph, -nx);
+        // v = x - alpha e1 stored in place below the diagonal (column j)
+        cplx v0 = csub(x0, alpha);
+        double nv = abs2(v0);
+        for (int i = j + 1; i < N; ++i) nv += abs2(S.Q[i][j]);
+        nv = sqrt(nv);
+        if (nv == 0) continue;
+        S.Q[j][j] = v0;
+        for (int i = j; i < N; ++i) S.Q[i][j] = cscale(S.Q[i][j], 1.0 / nv);
+        for (int c = j + 1; c <= m; ++c) {
+            cplx s = mkc(0, 0);
+            for (int i = j; i < N; ++i) s = cadd(s, cmul(conjc(S.Q[i][j]), S.Q[i][c]));
+            for (int i = j; i < N; ++i) S.Q[i][c] = csub(S.Q[i][c], cscale(cmul(S.Q[i][j], s), 2.0));
+        }
+        S.Q[j][j] = alpha;   // R diagonal
+        for (int i = j + 1; i < N; ++i) S.Q[i][j] = mkc(0, 0);
+    }
+    for (int j = m - 1; j >= 0; --j) {
+        cplx s = S.Q[j][m];
+        for (int c = j + 1; c < m; ++c) s = csub(s, cmul(S.Q[j][c], S.bb[c]));
+        S.bb[j] = cdiv(s, S.Q[j][j]);
+    }
+}
+
+// GPOF on S.res[0..N): poles in S.zp, amplitudes in S.bb, order in S.m
+__device__ void gpof(GpofSmem &S, int N, int mmax, bool decaying) {
+    const int Lp = N / 2;
+    const int nrow = N - Lp, ncolr = Lp + 1;
+    const int ncol = (ncolr + 1) & ~1;
+    for (int e = threadIdx.x; e < ncol * MAXC; e += blockDim.x) {
+        int c = e / MAXC, r = e % MAXC;
+        S.Y[c][r] = (c < ncolr && r < nrow) ? S.res[r + c] : mkc(0, 0);
+    }
+    __syncthreads();
+    jacobi_svd(S, nrow, ncol);
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < ncol; ++c) S.order[c] = c;
+        for (int i = 1; i < ncol; ++i) {      // sort by singular value, descending
+            int v = S.order[i], j = i - 1;
+            while (j >= 0 && S.sv[S.order[j]] < S.sv[v]) {
+                S.order[j + 1] = S.order[j];
+                --j;
+            }
+            S.order[j + 1] = v;
+        }
+        double smax = S.sv[S.order[0]];
+        double thr = fmax(REL_TOL * smax, ABS_TOL * N);
+        int m = 0;
+        int cap = mmax < MAXLS ? mmax : MAXLS;
+        while (m < ncol && m < cap && S.sv[S.order[m]] > thr) ++m;
+        // pencil: Zmat = V2^H V1 (V1^H V1)^{-1}; eigenvalues of (V1^H V1)^{-1} V2^H V1
+        // V1 = rows 0..Lp-1, V2 = rows 1..Lp of the m leading right singular vectors
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b) {
+                cplx g = mkc(0, 0), h = mkc(0, 0);
+                const cplx *va = S.V[S.order[a]], *vb = S.V[S.order[b]];
+                for (int r = 0; r < Lp; ++r) {
+                    g = cadd(g, cmul(conjc(va[r]), vb[r]));
+                    h = cadd(h, cmul(conjc(va[r + 1]), vb[r]));
+                }
+                S.H[a][b] = g;   // V1^H V1
+                S.B2[a][b] = h;  // V2^H V1
+            }
+        // solve (V1^H V1) X = V2^H V1 by Gaussian elimination, X -> H
+        for (int c = 0; c < m; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < m; ++r)
+                if (abs2(S.H[r][c]) > abs2(S.H[piv][c])) piv = r;
+            for (int q = 0; q < m; ++q) {
+                cplx t = S.H[c][q];
+                S.H[c][q] = S.H[piv][q];
+                S.H[piv][q] = t;
+                t = S.B2[c][q];
+                S.B2[c][q] = S.B2[piv][q];
+                S.B2[piv][q] = t;
+            }
+            cplx inv = cdiv(mkc(1, 0), S.H[c][c]);
+            for (int r = 0; r < m; ++r) {
+                if (r == c) continue;
+                cplx f = cmul(S.H[r][c], inv);
+                for (int q = 0; q < m; ++q) {
+                    S.H[r][q] = csub(S.H[r][q], cmul(f, S.H[c][q]));
+                    S.B2[r][q] = csub(S.B2[r][q], cmul(f, S.B2[c][q]));
+                }
+            }
+            for (int q = 0; q < m; ++q) S.B2[c][q] = cmul(S.B2[c][q], inv);
+            for (int q = 0; q < m; ++q) S.H[c][q] = cmul(S.H[c][q], inv);
+        }
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b) S.H[a][b] = S.B2[a][b];
+        if (m > 0) eig_small(S, m);
+        if (decaying) {
+            int w = 0;
+            for (int j = 0; j < m; ++j)
+                if (cabs_(S.zp[j]) < 1.0) S.zp[w++] = S.zp[j];
+            m = w;
+        }
+        if (m > 0) vandermonde_lsq(S, N, m);
+        S.m = m;
+    }
+    __syncthreads();
+}
+
+__global__ void k_fit(const FitJob *jobs, int njobs, cplx *outA, cplx *outZ, int *outN,
+                      double *outRes) {
+    int jb = blockIdx.x;
+    if (jb >= njobs) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    GpofSmem &S = *reinterpret_cast<GpofSmem *>(smraw);
+    const FitJob J = jobs[jb];
+    const int N = J.n;
+    const cplx k = J.k[J.layer];
+    const double T0 = J.T0, T1 = J.T1;
+    const double dt1 = T1 / (N - 1), dt2 = T0 / (N - 1);
+    __shared__ cplx y1[MAXN], y2[MAXN], A1[MAXM], Z1[MAXM];
+    __shared__ int n1;
+    // Step 1: samples
+    for (int n = threadIdx.x; n < 2 * N; n += blockDim.x) {
+        int lev = n / N, i = n % N;
+        cplx kz;
+        if (lev == 0) kz = cmul(mkc(0, 1), cscale(k, T0 + i * dt1));
+        else {
+            double t = i * dt2;
+            kz = cmul(k, mkc(1.0 - t / T0, t));
+        }
+        cplx F = cmul(s_tau_sample(J, kz), cexp_(cmul(mkc(0, 1), cscale(kz, J.zmin))));
+        if (lev == 0) y1[i] = F;
+        else y2[i] = F;
+    }
+    __syncthreads();
+    // level 1
+    for (int i = threadIdx.x; i < N; i += blockDim.x) S.res[i] = y1[i];
+    __syncthreads();
+    gpof(S, N, J.n_images / 2, true);
+    if (threadIdx.x == 0) {
+        n1 = S.m;
+        for (int j = 0; j < S.m; ++j) {
+            cplx Z = cdiv(clog_(S.zp[j]), cscale(k, dt1));          // z = e^{k dt1 Z}
+            Z1[j] = Z;
+            A1[j] = cmul(S.bb[j], cexp_(cscale(cmul(k, Z), -T0)));  // A = b e^{-k T0 Z}
+        }
+    }
+    __syncthreads();
+    // level 2 on the residual
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        double t = i * dt2;
+        cplx kz = cmul(k, mkc(1.0 - t / T0, t));
+        cplx s = y2[i];
+        for (int j = 0; j < n1; ++j)
+            s = csub(s, cmul(A1[j], cexp_(cmul(mkc(0, -1), cmul(kz, Z1[j])))));
+        S.res[i] = s;
+    }
+    __syncthreads();
+    gpof(S, N, J.n_images - n1, false);
+    if (threadIdx.x == 0) {
+        int m2 = S.m;
+        cplx cst = cscale(cmul(cmul(mkc(0, -1), k), mkc(-1.0 / T0, 1.0)), dt2);   // -i k (i - 1/T0) dt2
+        int tot = 0;
+        for (int j = 0; j < n1; ++j) {
+            outA[jb * MAXM + tot] = A1[j];
+            outZ[jb * MAXM + tot] = Z1[j];
+            ++tot;
+        }
+        for (int j = 0; j < m2; ++j) {
+            cplx Z = cdiv(clog_(S.zp[j]), cst);
+            outZ[jb * MAXM + tot] = Z;
+            outA[jb * MAXM + tot] = cmul(S.bb[j], cexp_(cmul(mkc(0, 1), cmul(k, Z))));   // A = b e^{ikZ}
+            ++tot;
+        }
+        outN[jb] = tot;
+        // residual on both paths, relative to the largest sample
+        double res = 0, sc = 0;
+        for (int lev = 0; lev < 2; ++lev)
+            for (int i = 0; i < N; ++i) {
+                cplx kz;
+                if (lev == 0) kz = cmul(mkc(0, 1), cscale(k, T0 + i * dt1));
+                else {
+                    double t = i * dt2;
+                    kz = cmul(k, mkc(1.0 - t / T0, t));
+                }
+                cplx s = lev == 0 ? y1[i] : y2[i];
+                sc = fmax(sc, cabs_(s));
+                cplx ap = mkc(0, 0);
+                for (int j = 0; j < tot; ++j)
+                    ap = cadd(ap, cmul(outA[jb * MAXM + j], cexp_(cmul(mkc(0, -1), cmul(kz, outZ[jb * MAXM + j])))));
+                res = fmax(res, cabs_(csub(ap, s)));
+            }
+        outRes[jb] = sc > 0 ? res / sc : 0.0;
+    }
+}
+
+}  // namespace
+
+int plan_fit_images(tefmm_plan_s *P, cudaStream_t st) {
+    P->A.clear();
+    P->Z.clear();
+    P->fit_max_resid = 0;
+    if (P->terms.empty() || P->opt.n_images == 0) {
+        for (auto &t : P->terms) t.first = t.count = 0;
+        return TEFMM_OK;
+    }
+    if (P->nL > 8 || P->opt.n_samples > MAXN) return TEFMM_ERR_NOT_IMPLEMENTED;
+    // one job per term; the down-up term reuses the up-down fit (same s_tau, zeta_min)
+    std::vector<FitJob> jobs;
+    std::vector<int> job_of(P->terms.size(), -1);
+    double kmax = 0;
+    for (int l = 0; l < P->nL; ++l) kmax = fmax(kmax, P->k[l].x);
+    for (size_t i = 0; i < P->terms.size(); ++i) {
+        const TermDesc &t = P->terms[i];
+        if (t.tag == 3 && i > 0 && P->terms[i - 1].tag == 2 && P->terms[i - 1].layer == t.layer) {
+            job_of[i] = job_of[i - 1];
+            continue;
+        }
+        FitJob J;
+        J.layer = t.layer;
+        J.tag = t.tag;
+        J.nL = P->nL;
+        for (int m = 0; m < TEFMM_MAX_LAYERS; ++m) {
+            J.d[m] = m < P->nL - 1 ? P->d[m] : 0.0;
+            J.k[m] = m < P->nL ? P->k[m] : mkc(1, 0);
+        }
+        J.zmin = t.zmin;
+        double kl = P->k[t.layer].x;
+        J.T0 = P->opt.T0 > 0 ? P->opt.T0 : sqrt(fmax(((kmax + 0.8) / kl) * ((kmax + 0.8) / kl) - 1.0, 1e-6));
+        J.T1 = P->opt.T1;
+        J.n = P->opt.n_samples;
+        J.n_images = P->opt.n_images;
+        job_of[i] = (int)jobs.size();
+        jobs.push_back(J);
+    }
+    int nj = (int)jobs.size();
+    FitJob *djobs = nullptr;
+    cplx *dA = nullptr, *dZ = nullptr;
+    int *dN = nullptr;
+    double *dR = nullptr;
+    CUDA_TRY(cudaMalloc(&djobs, nj * sizeof(FitJob)));
+    CUDA_TRY(cudaMalloc(&dA, nj * MAXM * sizeof(cplx)));
+    CUDA_TRY(cudaMalloc(&dZ, nj * MAXM * sizeof(cplx)));
+    CUDA_TRY(cudaMalloc(&dN, nj * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&dR, nj * sizeof(double)));
+    CUDA_TRY(cudaMemcpyAsync(djobs, jobs.data(), nj * sizeof(FitJob), cudaMemcpyHostToDevice, st));
+    size_t sm = sizeof(GpofSmem);
+    CUDA_TRY(cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fit<<<nj, 512, sm, st>>>(djobs, nj, dA, dZ, dN, dR);
+    CUDA_TRY(cudaGetLastError());
+    std::vector<cplx> hA(nj * MAXM), hZ(nj * MAXM);
+    std::vector<int> hN(nj);
+    std::vector<double> hR(nj);
+    CUDA_TRY(cudaMemcpyAsync(hA.data(), dA, nj * MAXM * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hZ.data(), dZ, nj * MAXM * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hN.data(), dN, nj * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hR.data(), dR, nj * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(djobs);
+    cudaFree(dA);
+    cudaFree(dZ);
+    cudaFree(dN);
+    cudaFree(dR);
+    for (size_t i = 0; i < P->terms.size(); ++i) {
+        int jb = job_of[i];
+        TermDesc &t = P->terms[i];
+        t.first = (int)P->A.size();
+        t.count = hN[jb];
+        for (int j = 0; j < hN[jb]; ++j) {
+            P->A.push_back(hA[jb * MAXM + j]);
+            P->Z.push_back(hZ[jb * MAXM + j]);
+        }
+        if (!(hR[jb] == hR[jb])) return TEFMM_ERR_FIT_FAILED;
+        P->fit_max_resid = fmax(P->fit_max_resid, hR[jb]);
+    }
+    return TEFMM_OK;
+}

@@ -1,0 +1,209 @@
+// Internal declarations shared by the translation units of libtefmm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "tefmm.h"
+
+#define TEFMM_NBITS 20          // bits per axis of the Morton code (levels 0..20)
+#define TEFMM_MAX_LAYERS 16
+#define TEFMM_MAX_TERMS 4       // same-layer reaction terms per layer
+#define TEFMM_MAX_IMG 32        // images per term
+
+// device-side error flags (bit mask, OR-ed by kernels)
+#define FLAG_ON_INTERFACE 1
+#define FLAG_OUT_OF_DOMAIN 2
+#define FLAG_LIST_OVERFLOW 4
+#define FLAG_CROSS_LAYER 8
+#define FLAG_CHECK 16
+
+// ---------------------------------------------------------------- complex
+struct cplx {
+    double x, y;
+};
+
+__host__ __device__ __forceinline__ cplx mkc(double x, double y) { return cplx{x, y}; }
+__host__ __device__ __forceinline__ cplx cadd(cplx a, cplx b) { return cplx{a.x + b.x, a.y + b.y}; }
+__host__ __device__ __forceinline__ cplx csub(cplx a, cplx b) { return cplx{a.x - b.x, a.y - b.y}; }
+__host__ __device__ __forceinline__ cplx cmul(cplx a, cplx b) {
+    return cplx{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+__host__ __device__ __forceinline__ cplx cscale(cplx a, double s) { return cplx{a.x * s, a.y * s}; }
+__host__ __device__ __forceinline__ cplx cdiv(cplx a, cplx b) {
+    // Smith's algorithm
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, den = b.x + b.y * r;
+        return cplx{(a.x + a.y * r) / den, (a.y - a.x * r) / den};
+    } else {
+        double r = b.x / b.y, den = b.x * r + b.y;
+        return cplx{(a.x * r + a.y) / den, (a.y * r - a.x) / den};
+    }
+}
+// principal square root (Re >= 0)
+__host__ __device__ __forceinline__ cplx csqrt_p(cplx z) {
+    double r = hypot(z.x, z.y);
+    if (r == 0.0) return cplx{0.0, 0.0};
+    if (z.x >= 0.0) {
+        double t = sqrt(0.5 * (r + z.x));
+        return cplx{t, z.y / (2.0 * t)};
+    } else {
+        double t = sqrt(0.5 * (r - z.x));
+        return cplx{fabs(z.y) / (2.0 * t), copysign(t, z.y)};
+    }
+}
+__host__ __device__ __forceinline__ cplx cexp_(cplx z) {
+    double e = exp(z.x), s, c;
+#ifdef __CUDA_ARCH__
+    sincos(z.y, &s, &c);
+#else
+    s = sin(z.y);
+    c = cos(z.y);
+#endif
+    return cplx{e * c, e * s};
+}
+// h0(kR) = e^{ikR}/(ikR)
+__host__ __device__ __forceinline__ cplx h0c(cplx kR) {
+    cplx ikr = cplx{-kR.y, kR.x};
+    return cdiv(cexp_(ikr), ikr);
+}
+
+// ------------------------------------------------------------ multi-indices
+// graded order: n = 0..P; k1 = n..0; k2 = n-k1..0; k3 = n-k1-k2
+__host__ __device__ __forceinline__ int ncoef(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
+__host__ __device__ __forceinline__ int midx(int k1, int k2, int k3) {
+    int n = k1 + k2 + k3;
+    int a = n - k1;
+    return n * (n + 1) * (n + 2) / 6 + a * (a + 1) / 2 + (a - k2);
+}
+
+// ------------------------------------------------------------ device buffers
+struct DBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+int dbuf_ensure(DBuf &b, size_t bytes);   // grow (contents not preserved)
+void dbuf_free(DBuf &b);
+
+template <class T>
+static inline T *dp(DBuf &b) { return reinterpret_cast<T *>(b.p); }
+
+// ---------------------------------------------------------------- images
+struct TermDesc {          // one same-layer reaction term of one layer
+    int layer, tag;        // tag: 0 uu, 1 dd, 2 ud, 3 du
+    int first, count;      // range in the image arrays
+    double sz, szp, c, zmin;
+};
+
+struct DevTerm {           // POD copy for kernels
+    double sz, szp, c, zmin;
+    int first, count, layer, tag;
+};
+
+// ---------------------------------------------------------------- plan
+struct tefmm_plan_s {
+    int nL = 0;
+    double d[TEFMM_MAX_LAYERS] = {0};
+    cplx k[TEFMM_MAX_LAYERS] = {};
+    tefmm_options opt{};
+    int p = 0, np = 0, np2 = 0;
+    int device = 0;
+
+    // images (host mirror + device copy)
+    std::vector<TermDesc> terms;
+    std::vector<cplx> A, Z;
+    int layer_term_first[TEFMM_MAX_LAYERS] = {0};
+    int layer_term_count[TEFMM_MAX_LAYERS] = {0};
+    DBuf d_terms, d_A, d_Z, d_k;
+    double fit_max_resid = 0.0;
+
+    // operator tables (device)
+    DBuf d_mi;        // int [np2*3] multi-indices up to order 2p
+    DBuf d_m2l_g;     // uint16 [np*np]  index of k+k' (layout [k'][k])
+    DBuf d_m2l_cB;    // double [np*np]  C(k+k',k) (-1)^{k1'+k2'} (-1)^{k3'}  ([k'][k])
+    DBuf d_m2l_cA;    // double [np*np]  C(k+k',k) (-1)^{k1'+k2'}            ([k'][k])
+    DBuf d_binom;     // double [(2p+1)^2]
+
+    // workspace of the last evaluation
+    int64_t ns = 0, nt = 0, nitems = 0;
+    bool shared_pts = false;
+    DBuf keys_in, keys_out, vals_in, vals_out, cub_tmp, scan_tmp;
+    DBuf item_node, item_flag, item_scan, cnt_s, cnt_t;
+    DBuf sx, sy, sz, sq, tx, ty, tz, perm_s, perm_t;
+    DBuf n_layer, n_level, n_ix, n_iy, n_iz, n_parent, n_cfirst, n_nchild, n_s0, n_s1, n_t0,
+        n_t1, n_i0, n_i1, n_split;
+    DBuf bbox, flags, counters;
+    int n_nodes = 0, n_levels = 0;
+    std::vector<int> level_off;   // node range per level: [level_off[l], level_off[l+1])
+    double lo[3] = {0, 0, 0}, side = 1.0;
+
+    // lists
+    DBuf C_list, C_cnt, D_list, D_cnt, X_list, X_cnt, V_tmp, V_cnt;
+    DBuf v_ptr, v_src, near_ptr, near_src, near_tmp, near_cnt;
+    int64_t n_v = 0, n_near = 0, n_p2p_pairs = 0;
+    int cap_C = 0, cap_V = 0, cap_D = 64, cap_X = 0, cap_near = 0;
+
+    // expansions
+    DBuf alpha, beta;
+
+    // M2L grouping and tables
+    DBuf keyslot_flag, keyslot_table, pair_t, pair_s, pair_slot, pair_slot_sorted, pair_idx,
+        pair_idx_sorted, chunk_key, chunk_start, chunk_cnt, tables, table_slot, seg_tmp;
+    int n_tables = 0;
+    int64_t n_chunks = 0;
+
+    // host staging for tefmm_eval_host
+    DBuf h_in, h_out;
+
+    // timing
+    cudaEvent_t ev[8] = {};
+    double ms_tree = 0, ms_upward = 0, ms_tables = 0, ms_m2l = 0, ms_downward = 0, ms_near = 0;
+    int64_t launches = 0;    // kernels of this library launched so far
+};
+
+// ---------------------------------------------------------------- helpers
+#define CUDA_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t _e = (expr);                                                          \
+        if (_e != cudaSuccess) {                                                          \
+            fprintf(stderr, "tefmm: %s failed at %s:%d: %s\n", #expr, __FILE__, __LINE__,  \
+                    cudaGetErrorString(_e));                                              \
+            return (_e == cudaErrorMemoryAllocation) ? TEFMM_ERR_OOM : TEFMM_ERR_CUDA;    \
+        }                                                                                 \
+    } while (0)
+
+#define TRY(expr)                         \
+    do {                                  \
+        int _r = (expr);                  \
+        if (_r != TEFMM_OK) return _r;    \
+    } while (0)
+
+static inline int grid_for(int64_t n, int block) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > 2147483647LL) g = 2147483647LL;
+    return (int)g;
+}
+
+// ------------------------------------------------------------ entry points
+// tree.cu
+int tree_build(tefmm_plan_s *P, const double *sx, const double *sy, const double *sz,
+               const double *q, const double *tx, const double *ty, const double *tz,
+               cudaStream_t st);
+int lists_build(tefmm_plan_s *P, cudaStream_t st);
+int check_flags(tefmm_plan_s *P, cudaStream_t st);
+// ops.cu
+int upward_pass(tefmm_plan_s *P, cudaStream_t st);
+int m2l_prepare(tefmm_plan_s *P, cudaStream_t st);
+int m2l_tables(tefmm_plan_s *P, cudaStream_t st);
+int m2l_apply(tefmm_plan_s *P, cudaStream_t st);
+int downward_pass(tefmm_plan_s *P, cudaStream_t st);
+int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st);
+// plan.cu
+int plan_upload_images(tefmm_plan_s *P);
+int plan_build_operator_tables(tefmm_plan_s *P);
+// fit.cu
+int plan_fit_images(tefmm_plan_s *P, cudaStream_t st);

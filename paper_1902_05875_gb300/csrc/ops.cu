@@ -1,0 +1,837 @@
+// Taylor-expansion operators of Sec. 3.1 and the near field (FP64 form).
+//
+//   P2M   alpha_k = sum_j q_j (r_j - c)^k                          (eq. taylorexpfar3layers)
+//   M2M   gamma_k = sum_{k'<=k} C(k,k') (c - c')^{k-k'} alpha_k'    (eqs. LETOLEmat, TETartoTETar)
+//   M2L   beta_k += sum_k' alpha_k' D_r^k D_r'^k' u / (k! k'!)     (eq. tesourceboxtotargetbox)
+//   L2L   lambda_k = sum_{k'>=k} C(k',k) (c~ - c)^{k'-k} beta_k'   (eq. freeletole)
+//   L2P   Phi(r) += sum_k beta_k (r - c)^k                         (eq. taylorexploc2ld)
+//   P2P   free-space h0 plus the DCIM image sum (Sec. 3.2, eq. closedformgreen)
+//
+// M2L follows the per-key batching of Sec. 3.2 (the derivative tables depend
+// only on the box centres): V pairs are grouped by a key, one derivative table
+// a_g = D^g f / g!, |g| <= 2p, is built per key with the recurrence of eq.
+// ``recurrsion`` (corrected form, see the derivative-table kernel), and each
+// pair contracts H[k][k'] = C(k+k',k) (-1)^{k1'+k2'} (A_{k+k'} + (-1)^{k3'} B_{k+k'})
+// with its source moments.  For a same-layer term with image distance
+// W = sz z + szp z' + c one has D_r^k D_r'^k' f = (-1)^{k1'+k2'} sz^{k3} szp^{k3'}
+// D^{k+k'} f, so the terms split into
+//   B (sz*szp = -1): free space, up-down, down-up; key (level, layer, dx, dy, dz)
+//   A (sz*szp = +1): up-up, down-down;             key (level, layer, dx, dy, iz_t+iz_s)
+// with (-1)^{g3} folded into the down-up and down-down images.
+#include <cub/cub.cuh>
+
+#include "internal.cuh"
+
+namespace {
+
+constexpr int CH = 16;          // pairs per M2L work chunk
+
+struct TreeArrays {
+    const int *layer, *level, *ix, *iy, *iz, *parent, *cfirst, *nchild, *s0, *s1, *t0, *t1, *split;
+};
+
+TreeArrays tree_arrays(tefmm_plan_s *P) {
+    TreeArrays T;
+    T.layer = dp<int>(P->n_layer);
+    T.level = dp<int>(P->n_level);
+    T.ix = dp<int>(P->n_ix);
+    T.iy = dp<int>(P->n_iy);
+    T.iz = dp<int>(P->n_iz);
+    T.parent = dp<int>(P->n_parent);
+    T.cfirst = dp<int>(P->n_cfirst);
+    T.nchild = dp<int>(P->n_nchild);
+    T.s0 = dp<int>(P->n_s0);
+    T.s1 = dp<int>(P->n_s1);
+    T.t0 = dp<int>(P->n_t0);
+    T.t1 = dp<int>(P->n_t1);
+    T.split = dp<int>(P->n_split);
+    return T;
+}
+
+struct Cube {
+    double lo[3];
+    double side;
+};
+
+// box centre lo + (i + 0.5) * (side / 2^l), no contraction
+__device__ __forceinline__ double centre(double lo, int i, double h) {
+    return __dadd_rn(lo, __dmul_rn((double)i + 0.5, h));
+}
+__device__ __forceinline__ double box_h(double side, int l) { return side / (double)(1 << l); }
+
+__device__ __forceinline__ double binom(int n, int k) {
+    double r = 1.0;
+    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
+    return r;
+}
+
+// ------------------------------------------------------------------ P2M
+__global__ void k_p2m(int nn, TreeArrays T, Cube cb, int p, int np, const int *__restrict__ mi,
+                      const double *__restrict__ sx, const double *__restrict__ sy,
+                      const double *__restrict__ sz, const double *__restrict__ sq,
+                      cplx *__restrict__ alpha) {
+    int node = blockIdx.x;
+    if (node >= nn || T.split[node]) return;
+    int s0 = T.s0[node], s1 = T.s1[node];
+    if (s1 <= s0) return;
+    extern __shared__ double sm[];
+    const int TILE = 64;
+    const int P1 = p + 1;
+    double *pw = sm;                       // [TILE][3][P1]
+    cplx *qq = (cplx *)(pw + TILE * 3 * P1);
+    int l = T.level[node];
+    double h = box_h(cb.side, l);
+    double cx = centre(cb.lo[0], T.ix[node], h);
+    double cy = centre(cb.lo[1], T.iy[node], h);
+    double cz = centre(cb.lo[2], T.iz[node], h);
+    const int R = 4;                       // up to 4 coefficients per thread (np <= 4*blockDim)
+    cplx acc[R];
+    int kk[R][3];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        acc[r] = mkc(0, 0);
+        int k = threadIdx.x + r * blockDim.x;
+        if (k < np) {
+            kk[r][0] = mi[3 * k];
+            kk[r][1] = mi[3 * k + 1];
+            kk[r][2] = mi[3 * k + 2];
+        } else {
+            kk[r][0] = kk[r][1] = kk[r][2] = 0;
+        }
+    }
+    for (int base = s0; base < s1; base += TILE) {
+        int cnt = min(TILE, s1 - base);
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            double d[3] = {sx[base + j] - cx, sy[base + j] - cy, sz[base + j] - cz};
+            for (int a = 0; a < 3; ++a) {
+                double v = 1.0;
+                for (int e = 0; e < P1; ++e) {
+                    pw[(j * 3 + a) * P1 + e] = v;
+                    v *= d[a];
+                }
+            }
+            qq[j] = mkc(sq[2 * (base + j)], sq[2 * (base + j) + 1]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int k = threadIdx.x + r * blockDim.x;
+            if (k >= np) continue;
+            for (int j = 0; j < cnt; ++j) {
+                double m = pw[(j * 3 + 0) * P1 + kk[r][0]] * pw[(j * 3 + 1) * P1 + kk[r][1]] *
+                           pw[(j * 3 + 2) * P1 + kk[r][2]];
+                acc[r].x += qq[j].x * m;
+                acc[r].y += qq[j].y * m;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int k = threadIdx.x + r * blockDim.x;
+        if (k < np) alpha[(int64_t)node * np + k] = acc[r];
+    }
+}
+
+// ------------------------------------------------------------------ M2M
+__global__ void k_m2m(int off, int cnt, TreeArrays T, Cube cb, int p, int np,
+                      const int *__restrict__ mi, cplx *__restrict__ alpha) {
+    int node = off + blockIdx.x;
+    if (blockIdx.x >= cnt || !T.split[node] || T.s1[node] <= T.s0[node]) return;
+    extern __shared__ double sm[];
+    cplx *ac = (cplx *)sm;                   // child moments [np]
+    double *pw = (double *)(ac + np);        // [3][p+1]
+    int l = T.level[node];
+    double h = box_h(cb.side, l), hc = box_h(cb.side, l + 1);
+    double c[3] = {centre(cb.lo[0], T.ix[node], h), centre(cb.lo[1], T.iy[node], h),
+                   centre(cb.lo[2], T.iz[node], h)};
+    const int R = 4;
+    cplx acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = mkc(0, 0);
+    int c0 = T.cfirst[node], c1 = c0 + T.nchild[node];
+    for (int ch = c0; ch < c1; ++ch) {
+        if (T.s1[ch] <= T.s0[ch]) continue;
+        __syncthreads();
+        for (int k = threadIdx.x; k < np; k += blockDim.x) ac[k] = alpha[(int64_t)ch * np + k];
+        if (threadIdx.x < 3) {
+            int a = threadIdx.x;
+            int ic = a == 0 ? T.ix[ch] : (a == 1 ? T.iy[ch] : T.iz[ch]);
+            double d = centre(cb.lo[a], ic, hc) - c[a];   // child centre - parent centre
+            double v = 1.0;
+            for (int e = 0; e <= p; ++e) {
+                pw[a * (p + 1) + e] = v;
+                v *= d;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int k = threadIdx.x + r * blockDim.x;
+            if (k >= np) continue;
+            int k1 = mi[3 * k], k2 = mi[3 * k + 1], k3 = mi[3 * k + 2];
+            cplx s = mkc(0, 0);
+            for (int j1 = 0; j1 <= k1; ++j1) {
+                double b1 = binom(k1, j1) * pw[0 * (p + 1) + k1 - j1];
+                for (int j2 = 0; j2 <= k2; ++j2) {
+                    double b2 = b1 * binom(k2, j2) * pw[1 * (p + 1) + k2 - j2];
+                    for (int j3 = 0; j3 <= k3; ++j3) {
+                        double b = b2 * binom(k3, j3) * pw[2 * (p + 1) + k3 - j3];
+                        cplx a = ac[midx(j1, j2, j3)];
+                        s.x += b * a.x;
+                        s.y += b * a.y;
+                    }
+                }
+            }
+            acc[r] = cadd(acc[r], s);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int k = threadIdx.x + r * blockDim.x;
+        if (k < np) alpha[(int64_t)node * np + k] = acc[r];
+    }
+}
+
+// ------------------------------------------------------------------ L2L
+__global__ void k_l2l(int off, int cnt, TreeArrays T, Cube cb, int p, int np,
+                      const int *__restrict__ mi, cplx *__restrict__ beta) {
+    int node = off + blockIdx.x;
+    if (blockIdx.x >= cnt || T.t1[node] <= T.t0[node]) return;
+    int par = T.parent[node];
+    if (par < 0) return;
+    extern __shared__ double sm[];
+    cplx *bp = (cplx *)sm;
+    double *pw = (double *)(bp + np);
+    int l = T.level[node];
+    double h = box_h(cb.side, l), hp = box_h(cb.side, l - 1);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) bp[k] = beta[(int64_t)par * np + k];
+    if (threadIdx.x < 3) {
+        int a = threadIdx.x;
+        int ic = a == 0 ? T.ix[node] : (a == 1 ? T.iy[node] : T.iz[node]);
+        int ip = a == 0 ? T.ix[par] : (a == 1 ? T.iy[par] : T.iz[par]);
+        double d = centre(cb.lo[a], ic, h) - centre(cb.lo[a], ip, hp);
+        double v = 1.0;
+        for (int e = 0; e <= p; ++e) {
+            pw[a * (p + 1) + e] = v;
+            v *= d;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        int k1 = mi[3 * k], k2 = mi[3 * k + 1], k3 = mi[3 * k + 2];
+        cplx s = mkc(0, 0);
+        for (int j1 = k1; j1 <= p; ++j1) {
+            double b1 = binom(j1, k1) * pw[0 * (p + 1) + j1 - k1];
+            for (int j2 = k2; j1 + j2 <= p; ++j2) {
+                double b2 = b1 * binom(j2, k2) * pw[1 * (p + 1) + j2 - k2];
+                for (int j3 = k3; j1 + j2 + j3 <= p; ++j3) {
+                    double b = b2 * binom(j3, k3) * pw[2 * (p + 1) + j3 - k3];
+                    cplx a = bp[midx(j1, j2, j3)];
+                    s.x += b * a.x;
+                    s.y += b * a.y;
+                }
+            }
+        }
+        beta[(int64_t)node * np + k] = cadd(beta[(int64_t)node * np + k], s);
+    }
+}
+
+// ------------------------------------------------------------------ M2L keys
+// key layout (64 bits): kind(2) level(5) layer(4) dx+3(3) dy+3(3) w(22)
+//   kind 0 = B (w = dz + 3), kind 1 = A (w = iz_t + iz_s)
+__device__ __forceinline__ uint64_t m2l_key(int kind, int l, int lay, int dx, int dy, int w) {
+    return ((uint64_t)kind << 62) | ((uint64_t)l << 57) | ((uint64_t)lay << 53) |
+           ((uint64_t)(dx + 3) << 50) | ((uint64_t)(dy + 3) << 47) | (uint64_t)w;
+}
+
+__global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pair_t,
+                            const int *__restrict__ v_src, const int *__restrict__ has_A,
+                            uint64_t *__restrict__ keys, int *__restrict__ vals) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nv) return;
+    int t = pair_t[e], s = v_src[e];
+    int l = T.level[t], lay = T.layer[t];
+    int dx = T.ix[t] - T.ix[s], dy = T.iy[t] - T.iy[s], dz = T.iz[t] - T.iz[s];
+    keys[2 * e] = m2l_key(0, l, lay, dx, dy, dz + 3);
+    keys[2 * e + 1] = has_A[lay] ? m2l_key(1, l, lay, dx, dy, T.iz[t] + T.iz[s]) : ~0ULL;
+    vals[2 * e] = (int)(2 * e);
+    vals[2 * e + 1] = (int)(2 * e + 1);
+}
+
+__global__ void k_heads(int64_t n, const uint64_t *__restrict__ keys, int *__restrict__ head,
+                        int *__restrict__ nvalid) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool valid = keys[i] != ~0ULL;
+    head[i] = valid && (i == 0 || keys[i] != keys[i - 1]);
+    // invalid keys sort last: the first invalid position is the valid count
+    if (!valid && (i == 0 || keys[i - 1] != ~0ULL)) *nvalid = (int)i;
+}
+
+__global__ void k_seg_start(int64_t n, const int *__restrict__ head, const int *__restrict__ seg_incl,
+                            const uint64_t *__restrict__ keys, int *__restrict__ seg_start,
+                            uint64_t *__restrict__ table_key) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || !head[i]) return;
+    int s = seg_incl[i] - 1;
+    seg_start[s] = (int)i;
+    table_key[s] = keys[i];
+}
+
+__global__ void k_chunk_heads(int64_t n, const uint64_t *__restrict__ keys,
+                              const int *__restrict__ seg_incl, const int *__restrict__ seg_start,
+                              int *__restrict__ chead) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int f = 0;
+    if (keys[i] != ~0ULL) {
+        int s = seg_incl[i] - 1;
+        f = ((i - seg_start[s]) % CH) == 0;
+    }
+    chead[i] = f;
+}
+
+__global__ void k_chunks(int64_t n, int64_t nvalid, const int *__restrict__ chead,
+                         const int *__restrict__ cscan, const int *__restrict__ seg_incl,
+                         int *__restrict__ chunk_start, int *__restrict__ chunk_table,
+                         int *__restrict__ chunk_cnt, int nchunks) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || !chead[i]) return;
+    int c = cscan[i] - 1;
+    chunk_start[c] = (int)i;
+    chunk_table[c] = seg_incl[i] - 1;
+    (void)nchunks;
+    (void)nvalid;
+}
+
+__global__ void k_chunk_cnt(int nchunks, int64_t nvalid, const int *__restrict__ chunk_start,
+                            const int *__restrict__ chunk_table, int *__restrict__ chunk_cnt) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    int end = (c + 1 < nchunks) ? chunk_start[c + 1] : (int)nvalid;
+    int cnt = end - chunk_start[c];
+    chunk_cnt[c] = cnt < CH ? cnt : CH;
+}
+
+// ------------------------------------------------------------------ derivative tables
+struct ImgView {
+    const DevTerm *terms;
+    const cplx *A, *Z;
+    const int *lt_first, *lt_count;   // per layer: term range
+    const cplx *k;
+};
+
+// One derivative table per key: sum over the key's images of
+// A_j D^g h0(k R_j) / g!, |g| <= 2p, by the recurrence (Sec. 3.2)
+//   |g| R^2 a_g + (2|g|-1) sum_i x_i a_{g-e_i} + (|g|-1) sum_i a_{g-2e_i}
+//       = i k sum_i (x_i b_{g-e_i} + b_{g-2e_i}),
+//   |g| b_g = i k sum_i (x_i a_{g-e_i} + a_{g-2e_i}),
+// a_0 = e^{ikR}/R, b_0 = e^{ikR}, D^g h0 / g! = a_g / (ik).
+__device__ void recur_accumulate(int P2, int np2, const int *mi, cplx k, double X, double Y, cplx W,
+                                 cplx coef, bool flip3, cplx *a, cplx *b, cplx *acc) {
+    if (threadIdx.x == 0) {
+        cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
+        cplx R = csqrt_p(R2);
+        cplx ikR = cmul(mkc(-k.y, k.x), R);
+        cplx e = cexp_(ikR);
+        a[0] = cdiv(e, R);
+        b[0] = e;
+    }
+    __syncthreads();
+    cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
+    cplx ik = mkc(-k.y, k.x);
+    for (int n = 1; n <= P2; ++n) {
+        int first = n * (n + 1) * (n + 2) / 6, last = (n + 1) * (n + 2) * (n + 3) / 6;
+        for (int g = first + threadIdx.x; g < last; g += blockDim.x) {
+            int kk[3] = {mi[3 * g], mi[3 * g + 1], mi[3 * g + 2]};
+            cplx xs[3] = {mkc(X, 0), mkc(Y, 0), W};
+            cplx sa1 = mkc(0, 0), sa2 = mkc(0, 0), sb = mkc(0, 0);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (kk[i] >= 1) {
+                    int m[3] = {kk[0], kk[1], kk[2]};
+                    m[i] -= 1;
+                    int j = midx(m[0], m[1], m[2]);
+                    sa1 = cadd(sa1, cmul(xs[i], a[j]));
+                    sb = cadd(sb, cmul(xs[i], b[j]));
+                }
+                if (kk[i] >= 2) {
+                    int m[3] = {kk[0], kk[1], kk[2]};
+                    m[i] -= 2;
+                    int j = midx(m[0], m[1], m[2]);
+                    sa2 = cadd(sa2, a[j]);
+                    sb = cadd(sb, b[j]);
+                }
+            }
+            cplx bg = cscale(cmul(ik, cadd(sa1, sa2)), 1.0 / n);
+            cplx num = csub(csub(cmul(ik, sb), cscale(sa1, 2.0 * n - 1.0)), cscale(sa2, n - 1.0));
+            cplx ag = cdiv(num, cscale(R2, (double)n));
+            a[g] = ag;
+            b[g] = bg;
+        }
+        __syncthreads();
+    }
+    // acc += coef * a / (ik) * (-1)^{g3 if flip3}
+    cplx c2 = cdiv(coef, ik);
+    for (int g = threadIdx.x; g < np2; g += blockDim.x) {
+        cplx v = cmul(c2, a[g]);
+        if (flip3 && (mi[3 * g + 2] & 1)) v = mkc(-v.x, -v.y);
+        acc[g] = cadd(acc[g], v);
+    }
+    __syncthreads();
+}
+
+__global__ void k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube cb, int P2, int np2,
+                         const int *__restrict__ mi_g, ImgView im, cplx *__restrict__ tables) {
+    int tb = blockIdx.x;
+    if (tb >= ntab) return;
+    extern __shared__ double sm[];
+    cplx *a = (cplx *)sm;
+    cplx *b = a + np2;
+    cplx *acc = b + np2;
+    int *mi = (int *)(acc + np2);
+    for (int g = threadIdx.x; g < 3 * np2; g += blockDim.x) mi[g] = mi_g[g];
+    for (int g = threadIdx.x; g < np2; g += blockDim.x) acc[g] = mkc(0, 0);
+    __syncthreads();
+    uint64_t key = table_key[tb];
+    int kind = (int)(key >> 62);
+    int l = (int)((key >> 57) & 31);
+    int lay = (int)((key >> 53) & 15);
+    int dx = (int)((key >> 50) & 7) - 3;
+    int dy = (int)((key >> 47) & 7) - 3;
+    int w = (int)(key & ((1ULL << 47) - 1));
+    double h = box_h(cb.side, l);
+    double X = (double)dx * h, Y = (double)dy * h;
+    cplx k = im.k[lay];
+    int tf = im.lt_first[lay], tc = im.lt_count[lay];
+    if (kind == 0) {
+        double dz = (double)(w - 3) * h;
+        recur_accumulate(P2, np2, mi, k, X, Y, mkc(dz, 0), mkc(1, 0), false, a, b, acc);
+        for (int ti = tf; ti < tf + tc; ++ti) {
+            DevTerm t = im.terms[ti];
+            if (t.tag != 2 && t.tag != 3) continue;
+            double W0 = __dadd_rn(__dmul_rn(t.sz, dz), t.c);
+            for (int j = t.first; j < t.first + t.count; ++j) {
+                cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
+                recur_accumulate(P2, np2, mi, k, X, Y, Wj, im.A[j], t.tag == 3, a, b, acc);
+            }
+        }
+    } else {
+        double zsum = __dadd_rn(2.0 * cb.lo[2], __dmul_rn((double)(w + 1), h));
+        for (int ti = tf; ti < tf + tc; ++ti) {
+            DevTerm t = im.terms[ti];
+            if (t.tag != 0 && t.tag != 1) continue;
+            double W0 = __dadd_rn(__dmul_rn(t.sz, zsum), t.c);
+            for (int j = t.first; j < t.first + t.count; ++j) {
+                cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
+                recur_accumulate(P2, np2, mi, k, X, Y, Wj, im.A[j], t.tag == 1, a, b, acc);
+            }
+        }
+    }
+    for (int g = threadIdx.x; g < np2; g += blockDim.x) tables[(int64_t)tb * np2 + g] = acc[g];
+}
+
+// ------------------------------------------------------------------ M2L apply (FP64)
+__global__ void k_m2l_fp64(int nchunks, const int *__restrict__ chunk_start,
+                           const int *__restrict__ chunk_table, const int *__restrict__ chunk_cnt,
+                           const uint64_t *__restrict__ table_key, const cplx *__restrict__ tables,
+                           const int *__restrict__ sorted_vals, const int *__restrict__ pair_t,
+                           const int *__restrict__ v_src, int np, int np2,
+                           const unsigned short *__restrict__ G, const double *__restrict__ cB,
+                           const double *__restrict__ cA, const cplx *__restrict__ alpha,
+                           cplx *__restrict__ beta) {
+    int c = blockIdx.x;
+    if (c >= nchunks) return;
+    extern __shared__ double sm[];
+    cplx *tab = (cplx *)sm;                  // [np2]
+    cplx *al = tab + np2;                    // [CH][np]
+    __shared__ int tgt[CH];
+    int tb = chunk_table[c];
+    int cnt = chunk_cnt[c];
+    int st = chunk_start[c];
+    int kind = (int)(table_key[tb] >> 62);
+    const double *coef = kind == 0 ? cB : cA;
+    for (int g = threadIdx.x; g < np2; g += blockDim.x) tab[g] = tables[(int64_t)tb * np2 + g];
+    for (int q = 0; q < cnt; ++q) {
+        int item = sorted_vals[st + q];
+        int e = item >> 1;
+        int s = v_src[e];
+        if (threadIdx.x == 0) tgt[q] = pair_t[e];
+        for (int k = threadIdx.x; k < np; k += blockDim.x) al[q * np + k] = alpha[(int64_t)s * np + k];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        cplx acc[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) acc[q] = mkc(0, 0);
+        for (int kp = 0; kp < np; ++kp) {
+            double cf = coef[(int64_t)kp * np + k];
+            cplx hv = tab[G[(int64_t)kp * np + k]];
+            hv.x *= cf;
+            hv.y *= cf;
+#pragma unroll
+            for (int q = 0; q < CH; ++q) {
+                if (q < cnt) {
+                    cplx a = al[q * np + kp];
+                    acc[q].x += hv.x * a.x - hv.y * a.y;
+                    acc[q].y += hv.x * a.y + hv.y * a.x;
+                }
+            }
+        }
+        for (int q = 0; q < cnt; ++q) {
+            double *dst = (double *)&beta[(int64_t)tgt[q] * np + k];
+            atomicAdd(dst, acc[q].x);
+            atomicAdd(dst + 1, acc[q].y);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ near field (FP64)
+struct NearArgs {
+    TreeArrays T;
+    Cube cb;
+    int p, np;
+    const int *mi;
+    const int *near_ptr, *near_src;
+    const double *sx, *sy, *sz, *sq, *tx, *ty, *tz;
+    const int *perm_t;
+    const cplx *beta;
+    ImgView im;
+    double *phi;
+};
+
+__device__ __forceinline__ cplx eikr_over_r(cplx ik, cplx R) {
+    // e^{ikR}/R
+    cplx e = cexp_(cmul(ik, R));
+    return cdiv(e, R);
+}
+
+__global__ void k_near_fp64(int nn, NearArgs a) {
+    int node = blockIdx.x;
+    if (node >= nn) return;
+    const TreeArrays &T = a.T;
+    if (T.split[node]) return;
+    int t0 = T.t0[node], t1 = T.t1[node];
+    int nt = t1 - t0;
+    if (nt <= 0) return;
+    const int TILE = 128;
+    __shared__ double xs[TILE], ys[TILE], zs[TILE];
+    __shared__ cplx qs[TILE];
+    __shared__ cplx red[128];
+    __shared__ cplx imgA[TEFMM_MAX_TERMS * TEFMM_MAX_IMG], imgZ[TEFMM_MAX_TERMS * TEFMM_MAX_IMG];
+    __shared__ double tgeo[TEFMM_MAX_TERMS][4];
+    __shared__ int tcnt[TEFMM_MAX_TERMS];
+    int lay = T.layer[node];
+    cplx k = a.im.k[lay];
+    cplx ik = mkc(-k.y, k.x);
+    cplx inv_ik = cdiv(mkc(1, 0), ik);
+    int tf = a.im.lt_first[lay], ntm = a.im.lt_count[lay];
+    if (threadIdx.x < ntm) {
+        DevTerm t = a.im.terms[tf + threadIdx.x];
+        tgeo[threadIdx.x][0] = t.sz;
+        tgeo[threadIdx.x][1] = t.szp;
+        tgeo[threadIdx.x][2] = t.c;
+        tgeo[threadIdx.x][3] = t.zmin;
+        tcnt[threadIdx.x] = t.count;
+    }
+    for (int ti = 0; ti < ntm; ++ti) {
+        DevTerm t = a.im.terms[tf + ti];
+        for (int j = threadIdx.x; j < t.count; j += blockDim.x) {
+            imgA[ti * TEFMM_MAX_IMG + j] = cmul(a.im.A[t.first + j], inv_ik);
+            imgZ[ti * TEFMM_MAX_IMG + j] = a.im.Z[t.first + j];
+        }
+    }
+    // thread layout: nslice threads per target
+    int ntp = 1;
+    while (ntp < nt && ntp < 128) ntp <<= 1;
+    int nslice = 128 / ntp;
+    int my_t = threadIdx.x % ntp, slice = threadIdx.x / ntp;
+    int l = T.level[node];
+    double h = box_h(a.cb.side, l);
+    double cx = centre(a.cb.lo[0], T.ix[node], h), cy = centre(a.cb.lo[1], T.iy[node], h),
+           cz = centre(a.cb.lo[2], T.iz[node], h);
+    int nb0 = a.near_ptr[node], nb1 = a.near_ptr[node + 1];
+    for (int tbase = 0; tbase < nt; tbase += ntp) {
+        int ti = tbase + my_t;
+        bool active = ti < nt;
+        double xt = 0, yt = 0, zt = 0;
+        if (active) {
+            xt = a.tx[t0 + ti];
+            yt = a.ty[t0 + ti];
+            zt = a.tz[t0 + ti];
+        }
+        cplx accf = mkc(0, 0);     // sum q e^{ikr}/r (free)
+        cplx acci = mkc(0, 0);     // sum q A/(ik) e^{ikR}/R (images)
+        __syncthreads();
+        for (int nb = nb0; nb < nb1; ++nb) {
+            int s = a.near_src[nb];
+            int s0 = T.s0[s], s1 = T.s1[s];
+            for (int base = s0; base < s1; base += TILE) {
+                int cnt = min(TILE, s1 - base);
+                __syncthreads();
+                for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+                    xs[j] = a.sx[base + j];
+                    ys[j] = a.sy[base + j];
+                    zs[j] = a.sz[base + j];
+                    qs[j] = mkc(a.sq[2 * (base + j)], a.sq[2 * (base + j) + 1]);
+                }
+                __syncthreads();
+                if (active) {
+                    for (int j = slice; j < cnt; j += nslice) {
+                        double dx = xt - xs[j], dy = yt - ys[j], dz = zt - zs[j];
+                        double rho2 = dx * dx + dy * dy;
+                        cplx q = qs[j];
+                        if (!(xt == xs[j] && yt == ys[j] && zt == zs[j])) {
+                            double r = sqrt(rho2 + dz * dz);
+                            cplx g = eikr_over_r(ik, mkc(r, 0));
+                            accf = cadd(accf, cmul(q, g));
+                        }
+                        cplx gi = mkc(0, 0);
+                        for (int tm = 0; tm < ntm; ++tm) {
+                            double zeta = tgeo[tm][0] * zt + tgeo[tm][1] * zs[j] + tgeo[tm][2] - tgeo[tm][3];
+                            for (int m = 0; m < tcnt[tm]; ++m) {
+                                cplx Z = imgZ[tm * TEFMM_MAX_IMG + m];
+                                cplx w = mkc(zeta - Z.x, -Z.y);
+                                cplx R = csqrt_p(mkc(rho2 + w.x * w.x - w.y * w.y, 2.0 * w.x * w.y));
+                                gi = cadd(gi, cmul(imgA[tm * TEFMM_MAX_IMG + m], eikr_over_r(ik, R)));
+                            }
+                        }
+                        acci = cadd(acci, cmul(q, gi));
+                    }
+                }
+            }
+        }
+        cplx tot = cadd(cmul(accf, inv_ik), acci);
+        __syncthreads();
+        red[threadIdx.x] = tot;
+        __syncthreads();
+        if (slice == 0 && active) {
+            for (int sl = 1; sl < nslice; ++sl) tot = cadd(tot, red[sl * ntp + my_t]);
+            // L2P
+            double d[3] = {xt - cx, yt - cy, zt - cz};
+            double pw[3][13];
+            for (int e = 0; e < 3; ++e) {
+                double v = 1.0;
+                for (int q = 0; q <= a.p; ++q) {
+                    pw[e][q] = v;
+                    v *= d[e];
+                }
+            }
+            const cplx *bt = a.beta + (int64_t)node * a.np;
+            cplx loc = mkc(0, 0);
+            for (int kk = 0; kk < a.np; ++kk) {
+                double m = pw[0][a.mi[3 * kk]] * pw[1][a.mi[3 * kk + 1]] * pw[2][a.mi[3 * kk + 2]];
+                cplx b = bt[kk];
+                loc.x += b.x * m;
+                loc.y += b.y * m;
+            }
+            tot = cadd(tot, loc);
+            int out = a.perm_t[t0 + ti];
+            a.phi[2 * out] = tot.x;
+            a.phi[2 * out + 1] = tot.y;
+        }
+    }
+}
+
+ImgView img_view(tefmm_plan_s *P) {
+    ImgView im;
+    im.terms = dp<DevTerm>(P->d_terms);
+    im.A = dp<cplx>(P->d_A);
+    im.Z = dp<cplx>(P->d_Z);
+    im.k = dp<cplx>(P->d_k);
+    im.lt_first = dp<int>(P->d_k) == nullptr ? nullptr : (const int *)(dp<cplx>(P->d_k) + TEFMM_MAX_LAYERS);
+    im.lt_count = im.lt_first + TEFMM_MAX_LAYERS;
+    return im;
+}
+
+Cube cube_of(tefmm_plan_s *P) {
+    Cube c;
+    for (int d = 0; d < 3; ++d) c.lo[d] = P->lo[d];
+    c.side = P->side;
+    return c;
+}
+
+int scan_i(tefmm_plan_s *P, const int *in, int *out, int64_t n, bool inclusive, cudaStream_t st) {
+    size_t bytes = 0;
+    if (inclusive) cub::DeviceScan::InclusiveSum(nullptr, bytes, in, out, (int)n, st);
+    else cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, (int)n, st);
+    TRY(dbuf_ensure(P->scan_tmp, bytes));
+    if (inclusive) CUDA_TRY(cub::DeviceScan::InclusiveSum(P->scan_tmp.p, bytes, in, out, (int)n, st));
+    else CUDA_TRY(cub::DeviceScan::ExclusiveSum(P->scan_tmp.p, bytes, in, out, (int)n, st));
+    return TEFMM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+int upward_pass(tefmm_plan_s *P, cudaStream_t st) {
+    const int nn = P->n_nodes, np = P->np, p = P->p;
+    TRY(dbuf_ensure(P->alpha, (size_t)nn * np * sizeof(cplx)));
+    CUDA_TRY(cudaMemsetAsync(P->alpha.p, 0, (size_t)nn * np * sizeof(cplx), st));
+    TreeArrays T = tree_arrays(P);
+    Cube cb = cube_of(P);
+    size_t sm_p2m = 64 * 3 * (p + 1) * sizeof(double) + 64 * sizeof(cplx);
+    k_p2m<<<nn, 128, sm_p2m, st>>>(nn, T, cb, p, np, dp<int>(P->d_mi), dp<double>(P->sx),
+                                   dp<double>(P->sy), dp<double>(P->sz), dp<double>(P->sq),
+                                   dp<cplx>(P->alpha));
+    P->launches++;
+    size_t sm_m2m = np * sizeof(cplx) + 3 * (p + 1) * sizeof(double);
+    for (int l = P->n_levels - 2; l >= 0; --l) {
+        int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
+        if (cnt > 0) {
+            k_m2m<<<cnt, 128, sm_m2m, st>>>(off, cnt, T, cb, p, np, dp<int>(P->d_mi),
+                                            dp<cplx>(P->alpha));
+            P->launches++;
+        }
+    }
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
+    const int64_t nv = P->n_v;
+    P->n_tables = 0;
+    P->n_chunks = 0;
+    if (nv == 0) return TEFMM_OK;
+    const int64_t ni = 2 * nv;
+    TRY(dbuf_ensure(P->pair_slot, ni * 8));
+    TRY(dbuf_ensure(P->pair_slot_sorted, ni * 8));
+    TRY(dbuf_ensure(P->pair_idx, ni * 4));
+    TRY(dbuf_ensure(P->pair_idx_sorted, ni * 4));
+    // has_A per layer: any up-up or down-down term with images
+    int hasA[TEFMM_MAX_LAYERS] = {0};
+    for (auto &t : P->terms)
+        if ((t.tag == 0 || t.tag == 1) && t.count > 0) hasA[t.layer] = 1;
+    TRY(dbuf_ensure(P->seg_tmp, sizeof(hasA)));
+    CUDA_TRY(cudaMemcpyAsync(P->seg_tmp.p, hasA, sizeof(hasA), cudaMemcpyHostToDevice, st));
+    TreeArrays T = tree_arrays(P);
+    k_m2l_items<<<grid_for(nv, 256), 256, 0, st>>>(nv, T, dp<int>(P->pair_t), dp<int>(P->v_src),
+                                                   dp<int>(P->seg_tmp), dp<uint64_t>(P->pair_slot),
+                                                   dp<int>(P->pair_idx));
+    P->launches++;
+    size_t bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, bytes, dp<uint64_t>(P->pair_slot),
+                                    dp<uint64_t>(P->pair_slot_sorted), dp<int>(P->pair_idx),
+                                    dp<int>(P->pair_idx_sorted), (int)ni, 0, 64, st);
+    TRY(dbuf_ensure(P->cub_tmp, bytes));
+    CUDA_TRY(cub::DeviceRadixSort::SortPairs(P->cub_tmp.p, bytes, dp<uint64_t>(P->pair_slot),
+                                             dp<uint64_t>(P->pair_slot_sorted), dp<int>(P->pair_idx),
+                                             dp<int>(P->pair_idx_sorted), (int)ni, 0, 64, st));
+    const uint64_t *keys = dp<uint64_t>(P->pair_slot_sorted);
+    // heads and segments (reuse item buffers as scratch)
+    TRY(dbuf_ensure(P->item_flag, (ni + 1) * 4));
+    TRY(dbuf_ensure(P->item_scan, (ni + 1) * 4));
+    TRY(dbuf_ensure(P->item_node, (ni + 1) * 4));
+    int *head = dp<int>(P->item_flag), *seg = dp<int>(P->item_scan), *chead = dp<int>(P->item_node);
+    TRY(dbuf_ensure(P->counters, 64));
+    int ni_int = (int)ni;
+    CUDA_TRY(cudaMemcpyAsync(P->counters.p, &ni_int, 4, cudaMemcpyHostToDevice, st));
+    k_heads<<<grid_for(ni, 256), 256, 0, st>>>(ni, keys, head, dp<int>(P->counters));
+    P->launches++;
+    TRY(scan_i(P, head, seg, ni, true, st));
+    int nseg = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nseg, seg + ni - 1, 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    P->n_tables = nseg;
+    TRY(dbuf_ensure(P->keyslot_flag, (size_t)(nseg + 1) * 4));      // segment start
+    TRY(dbuf_ensure(P->table_slot, (size_t)(nseg + 1) * 8));        // table key
+    k_seg_start<<<grid_for(ni, 256), 256, 0, st>>>(ni, head, seg, keys, dp<int>(P->keyslot_flag),
+                                                   dp<uint64_t>(P->table_slot));
+    P->launches++;
+    k_chunk_heads<<<grid_for(ni, 256), 256, 0, st>>>(ni, keys, seg, dp<int>(P->keyslot_flag), chead);
+    P->launches++;
+    TRY(dbuf_ensure(P->keyslot_table, (ni + 1) * 4));
+    TRY(scan_i(P, chead, dp<int>(P->keyslot_table), ni, true, st));
+    int nch = 0, nvalid_i = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nch, dp<int>(P->keyslot_table) + ni - 1, 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&nvalid_i, P->counters.p, 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    P->n_chunks = nch;
+    TRY(dbuf_ensure(P->chunk_start, (size_t)(nch + 1) * 4));
+    TRY(dbuf_ensure(P->chunk_key, (size_t)(nch + 1) * 4));
+    TRY(dbuf_ensure(P->chunk_cnt, (size_t)(nch + 1) * 4));
+    k_chunks<<<grid_for(ni, 256), 256, 0, st>>>(ni, ni, chead, dp<int>(P->keyslot_table), seg,
+                                                dp<int>(P->chunk_start), dp<int>(P->chunk_key),
+                                                dp<int>(P->chunk_cnt), nch);
+    P->launches++;
+    const int64_t nvalid = nvalid_i;
+    k_chunk_cnt<<<grid_for(nch, 256), 256, 0, st>>>(nch, nvalid, dp<int>(P->chunk_start),
+                                                    dp<int>(P->chunk_key), dp<int>(P->chunk_cnt));
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+int m2l_tables(tefmm_plan_s *P, cudaStream_t st) {
+    if (P->n_tables == 0) return TEFMM_OK;
+    const int np2 = P->np2;
+    TRY(dbuf_ensure(P->tables, (size_t)P->n_tables * np2 * sizeof(cplx)));
+    size_t sm = 3 * (size_t)np2 * sizeof(cplx) + 3 * (size_t)np2 * sizeof(int);
+    CUDA_TRY(cudaFuncSetAttribute(k_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_tables<<<P->n_tables, 256, sm, st>>>(P->n_tables, dp<uint64_t>(P->table_slot), cube_of(P),
+                                           2 * P->p, np2, dp<int>(P->d_mi), img_view(P),
+                                           dp<cplx>(P->tables));
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+int m2l_apply(tefmm_plan_s *P, cudaStream_t st) {
+    const int nn = P->n_nodes, np = P->np;
+    TRY(dbuf_ensure(P->beta, (size_t)nn * np * sizeof(cplx)));
+    CUDA_TRY(cudaMemsetAsync(P->beta.p, 0, (size_t)nn * np * sizeof(cplx), st));
+    if (P->n_chunks == 0) return TEFMM_OK;
+    size_t sm = (size_t)P->np2 * sizeof(cplx) + (size_t)CH * np * sizeof(cplx);
+    CUDA_TRY(cudaFuncSetAttribute(k_m2l_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_m2l_fp64<<<(int)P->n_chunks, 256, sm, st>>>(
+        (int)P->n_chunks, dp<int>(P->chunk_start), dp<int>(P->chunk_key), dp<int>(P->chunk_cnt),
+        dp<uint64_t>(P->table_slot), dp<cplx>(P->tables), dp<int>(P->pair_idx_sorted),
+        dp<int>(P->pair_t), dp<int>(P->v_src), np, P->np2, dp<unsigned short>(P->d_m2l_g),
+        dp<double>(P->d_m2l_cB), dp<double>(P->d_m2l_cA), dp<cplx>(P->alpha), dp<cplx>(P->beta));
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+int downward_pass(tefmm_plan_s *P, cudaStream_t st) {
+    TreeArrays T = tree_arrays(P);
+    Cube cb = cube_of(P);
+    size_t sm = P->np * sizeof(cplx) + 3 * (P->p + 1) * sizeof(double);
+    for (int l = 1; l < P->n_levels; ++l) {
+        int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
+        if (cnt > 0) {
+            k_l2l<<<cnt, 128, sm, st>>>(off, cnt, T, cb, P->p, P->np, dp<int>(P->d_mi),
+                                        dp<cplx>(P->beta));
+            P->launches++;
+        }
+    }
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st) {
+    NearArgs a;
+    a.T = tree_arrays(P);
+    a.cb = cube_of(P);
+    a.p = P->p;
+    a.np = P->np;
+    a.mi = dp<int>(P->d_mi);
+    a.near_ptr = dp<int>(P->near_ptr);
+    a.near_src = dp<int>(P->near_src);
+    a.sx = dp<double>(P->sx);
+    a.sy = dp<double>(P->sy);
+    a.sz = dp<double>(P->sz);
+    a.sq = dp<double>(P->sq);
+    a.tx = P->shared_pts ? a.sx : dp<double>(P->tx);
+    a.ty = P->shared_pts ? a.sy : dp<double>(P->ty);
+    a.tz = P->shared_pts ? a.sz : dp<double>(P->tz);
+    a.perm_t = P->shared_pts ? dp<int>(P->perm_s) : dp<int>(P->perm_t);
+    a.beta = dp<cplx>(P->beta);
+    a.im = img_view(P);
+    a.phi = phi;
+    k_near_fp64<<<P->n_nodes, 128, 0, st>>>(P->n_nodes, a);
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}

@@ -1,0 +1,750 @@
+// Morton keys, sort, per-layer octrees and interaction lists.
+//
+// Tree rule (the paper's adaptive tree, Algorithm 1, with the details it
+// leaves open fixed as follows): one octree per layer inside one common root
+// cube; integer coordinates i = min(floor(((x - lo)/side) * 2^20), 2^20 - 1)
+// with correctly rounded double operations (no FMA); 60-bit Morton codes with
+// the layer in bits 60..63; a box is split while max(#sources, #targets) >
+// leaf_cap; only boxes that hold a point exist; nodes are numbered
+// level-major, by (level, layer, Morton prefix).
+//
+// Lists: the dual-tree traversal of (target tree, source tree) that for a
+// single tree is the classic adaptive U/V/W/X construction; V pairs go to M2L,
+// U/W/X pairs to the near field.  Built level by level from per-node sets
+//   C(t): same-level adjacent source boxes reached by the traversal,
+//   D(t): coarser adjacent source leaves handed down to t,
+//   X(t): source leaves not adjacent to t handed down from its parent,
+//   V(t): children of C(parent) boxes that are not adjacent to t.
+#include <cub/cub.cuh>
+
+#include "internal.cuh"
+
+namespace {
+
+struct Geo {
+    double d[TEFMM_MAX_LAYERS];
+    double zlo[TEFMM_MAX_LAYERS], zhi[TEFMM_MAX_LAYERS];
+    double lo[3];
+    double side;
+    int nL;
+};
+
+__device__ __forceinline__ unsigned long long ord_of(double v) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ULL);
+}
+__host__ __device__ __forceinline__ double double_of(unsigned long long o) {
+    unsigned long long u = (o >> 63) ? (o & 0x7fffffffffffffffULL) : ~o;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)u);
+#else
+    double d;
+    memcpy(&d, &u, 8);
+    return d;
+#endif
+}
+
+__global__ void k_bbox(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ z, unsigned long long *bb) {
+    unsigned long long mn[3] = {~0ULL, ~0ULL, ~0ULL}, mx[3] = {0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long o[3] = {ord_of(x[i]), ord_of(y[i]), ord_of(z[i])};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = o[d] < mn[d] ? o[d] : mn[d];
+            mx[d] = o[d] > mx[d] ? o[d] : mx[d];
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        for (int off = 16; off > 0; off >>= 1) {
+            unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], off);
+            unsigned long long b = __shfl_xor_sync(0xffffffffu, mx[d], off);
+            mn[d] = a < mn[d] ? a : mn[d];
+            mx[d] = b > mx[d] ? b : mx[d];
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&bb[d], mn[d]);
+            atomicMax(&bb[3 + d], mx[d]);
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0xfffffULL;   // 20 bits
+    x = (x | (x << 32)) & 0x1f00000000ffffULL;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffULL;
+    x = (x | (x << 8)) & 0x100f00f00f00f00fULL;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ULL;
+    x = (x | (x << 2)) & 0x1249249249249249ULL;
+    return x;
+}
+
+__device__ __forceinline__ int icoord(double v, double lo, double side) {
+    double t = __dsub_rn(v, lo);
+    t = __ddiv_rn(t, side);
+    t = __dmul_rn(t, 1048576.0);
+    double f = floor(t);
+    long long i = (long long)f;
+    if (i < 0) i = 0;
+    if (i > (1 << TEFMM_NBITS) - 1) i = (1 << TEFMM_NBITS) - 1;
+    return (int)i;
+}
+
+__global__ void k_keys(int64_t nitems, int64_t ns, const double *__restrict__ sx,
+                       const double *__restrict__ sy, const double *__restrict__ sz,
+                       const double *__restrict__ tx, const double *__restrict__ ty,
+                       const double *__restrict__ tz, Geo g, uint64_t *__restrict__ keys,
+                       int *__restrict__ vals, int *flags) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nitems) return;
+    double x, y, z;
+    if (i < ns) {
+        x = sx[i]; y = sy[i]; z = sz[i];
+    } else {
+        x = tx[i - ns]; y = ty[i - ns]; z = tz[i - ns];
+    }
+    int lay = 0;
+    bool on = false;
+    for (int m = 0; m < g.nL - 1; ++m) {
+        lay += (z < g.d[m]) ? 1 : 0;
+        on |= (z == g.d[m]);
+    }
+    if (on) atomicOr(flags, FLAG_ON_INTERFACE);
+    else if (z < g.zlo[lay] || z > g.zhi[lay]) atomicOr(flags, FLAG_OUT_OF_DOMAIN);
+    uint64_t key = spread3(icoord(x, g.lo[0], g.side)) << 2 | spread3(icoord(y, g.lo[1], g.side)) << 1 |
+                   spread3(icoord(z, g.lo[2], g.side));
+    keys[i] = ((uint64_t)lay << 60) | key;
+    vals[i] = (int)i;
+}
+
+// sorted items -> sorted source / target arrays and their counting scans
+__global__ void k_is_src(int64_t nitems, int64_t ns, const int *__restrict__ vals,
+                         int *__restrict__ is_src) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < nitems) is_src[i] = vals[i] < ns ? 1 : 0;
+}
+
+__global__ void k_gather(int64_t nitems, int64_t ns, bool shared, const int *__restrict__ vals,
+                         const int *__restrict__ cnt_s, const double *__restrict__ sx,
+                         const double *__restrict__ sy, const double *__restrict__ sz,
+                         const double *__restrict__ q, const double *__restrict__ tx,
+                         const double *__restrict__ ty, const double *__restrict__ tz,
+                         double *osx, double *osy, double *osz, double *oq, double *otx,
+                         double *oty, double *otz, int *perm_s, int *perm_t) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nitems) return;
+    int v = vals[i];
+    if (v < ns) {
+        int64_t pos = shared ? i : cnt_s[i];
+        osx[pos] = sx[v];
+        osy[pos] = sy[v];
+        osz[pos] = sz[v];
+        oq[2 * pos] = q[2 * v];
+        oq[2 * pos + 1] = q[2 * v + 1];
+        perm_s[pos] = v;
+    } else {
+        int64_t pos = i - cnt_s[i];
+        int w = (int)(v - ns);
+        otx[pos] = tx[w];
+        oty[pos] = ty[w];
+        otz[pos] = tz[w];
+        perm_t[pos] = w;
+    }
+}
+
+__device__ __forceinline__ uint64_t prefix_at(uint64_t key, int l) {
+    // layer bits and the Morton prefix of level l
+    uint64_t lay = key >> 60;
+    uint64_t m = key & 0x0fffffffffffffffULL;
+    return (lay << 60) | (m >> (3 * (TEFMM_NBITS - l)));
+}
+
+__global__ void k_mark(int64_t nitems, int l, const uint64_t *__restrict__ keys,
+                       const int *__restrict__ item_node, const int *__restrict__ n_i0,
+                       const int *__restrict__ n_split, int *__restrict__ flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nitems) return;
+    int f = 0;
+    if (l == 0) {
+        f = (i == 0) || ((keys[i] >> 60) != (keys[i - 1] >> 60));
+    } else {
+        int pn = item_node[i];
+        if (pn >= 0 && n_split[pn]) {
+            f = (i == n_i0[pn]) || (prefix_at(keys[i], l) != prefix_at(keys[i - 1], l));
+        }
+    }
+    flag[i] = f;
+}
+
+__global__ void k_make_nodes(int64_t nitems, int l, int off, const uint64_t *__restrict__ keys,
+                             const int *__restrict__ flag, const int *__restrict__ scan,
+                             int *__restrict__ item_node, int *n_layer, int *n_level, int *n_ix,
+                             int *n_iy, int *n_iz, int *n_parent, int *n_i0, int *n_nchild,
+                             int *n_cfirst, int *n_split) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nitems) return;
+    int pn = (l == 0) ? 0 : item_node[i];
+    bool inside = (l == 0) || (pn >= 0 && n_split[pn]);
+    if (!inside) {
+        item_node[i] = -1;
+        return;
+    }
+    int c = off + scan[i] - 1;     // inclusive scan
+    if (flag[i]) {
+        uint64_t key = keys[i];
+        uint64_t m = key & 0x0fffffffffffffffULL;
+        uint64_t pre = (l == 0) ? 0 : (m >> (3 * (TEFMM_NBITS - l)));
+        int ix = 0, iy = 0, iz = 0;
+        for (int b = 0; b < l; ++b) {
+            iz |= (int)((pre >> (3 * b)) & 1) << b;
+            iy |= (int)((pre >> (3 * b + 1)) & 1) << b;
+            ix |= (int)((pre >> (3 * b + 2)) & 1) << b;
+        }
+        n_layer[c] = (int)(key >> 60);
+        n_level[c] = l;
+        n_ix[c] = ix;
+        n_iy[c] = iy;
+        n_iz[c] = iz;
+        n_parent[c] = (l == 0) ? -1 : pn;
+        n_i0[c] = (int)i;
+        n_nchild[c] = 0;
+        n_cfirst[c] = -1;
+        n_split[c] = 0;
+    }
+    item_node[i] = c;
+}
+
+__global__ void k_node_ranges(int off, int cnt, int64_t nitems, int l, int leaf_cap, int max_level,
+                              const int *__restrict__ n_i0, const int *__restrict__ n_parent,
+                              const int *__restrict__ cnt_s, const int *__restrict__ cnt_t,
+                              bool shared, int *n_i1, int *n_s0, int *n_s1, int *n_t0,
+                              int *n_t1, int *n_split, int *n_cfirst, int *n_nchild,
+                              int *nsplit_count) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cnt) return;
+    int c = off + j;
+    int par = n_parent[c];
+    int i1;
+    if (j + 1 < cnt && n_parent[c + 1] == par) i1 = n_i0[c + 1];
+    else i1 = (l == 0) ? (int)nitems : n_i1[par];
+    int i0 = n_i0[c];
+    n_i1[c] = i1;
+    int s0, s1, t0, t1;
+    if (shared) {
+        s0 = t0 = i0;
+        s1 = t1 = i1;
+    } else {
+        s0 = cnt_s[i0];
+        s1 = cnt_s[i1];
+        t0 = i0 - s0;
+        t1 = i1 - s1;
+    }
+    n_s0[c] = s0;
+    n_s1[c] = s1;
+    n_t0[c] = t0;
+    n_t1[c] = t1;
+    int nmax = max(s1 - s0, t1 - t0);
+    int sp = (nmax > leaf_cap && l < max_level) ? 1 : 0;
+    n_split[c] = sp;
+    if (sp) atomicAdd(nsplit_count, 1);
+    if (par >= 0) {
+        if (j == 0 || n_parent[c - 1] != par) n_cfirst[par] = c;
+        atomicAdd(&n_nchild[par], 1);
+    }
+}
+
+// ---------------------------------------------------------------- lists
+struct NodeView {
+    const int *layer, *level, *ix, *iy, *iz, *parent, *cfirst, *nchild, *s0, *s1, *t0, *t1, *split;
+};
+
+__device__ __forceinline__ bool adjacent(const NodeView &N, int a, int b) {
+    int la = N.level[a], lb = N.level[b];
+    int ax = N.ix[a], ay = N.iy[a], az = N.iz[a];
+    int bx = N.ix[b], by = N.iy[b], bz = N.iz[b];
+    if (la > lb) {
+        int t;
+        t = la; la = lb; lb = t;
+        t = ax; ax = bx; bx = t;
+        t = ay; ay = by; by = t;
+        t = az; az = bz; bz = t;
+    }
+    int s = lb - la;
+    int lo, hi;
+    lo = ax << s; hi = ((ax + 1) << s) - 1;
+    if (bx < lo - 1 || bx > hi + 1) return false;
+    lo = ay << s; hi = ((ay + 1) << s) - 1;
+    if (by < lo - 1 || by > hi + 1) return false;
+    lo = az << s; hi = ((az + 1) << s) - 1;
+    if (bz < lo - 1 || bz > hi + 1) return false;
+    return true;
+}
+
+__device__ __forceinline__ void isort(int *a, int n) {
+    for (int i = 1; i < n; ++i) {
+        int v = a[i], j = i - 1;
+        while (j >= 0 && a[j] > v) {
+            a[j + 1] = a[j];
+            --j;
+        }
+        a[j + 1] = v;
+    }
+}
+
+// level 0: C(root_t) = every root that holds sources
+__global__ void k_lists_root(int nroots, NodeView N, int *C_list, int *C_cnt, int capC, int *D_cnt,
+                             int *X_cnt, int *V_cnt) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nroots) return;
+    int n = 0;
+    if (N.t1[t] > N.t0[t]) {
+        for (int s = 0; s < nroots; ++s)
+            if (N.s1[s] > N.s0[s]) C_list[(int64_t)t * capC + n++] = s;
+    }
+    C_cnt[t] = n;
+    D_cnt[t] = 0;
+    X_cnt[t] = 0;
+    V_cnt[t] = 0;
+}
+
+__global__ void k_lists_level(int off, int cnt, NodeView N, int *C_list, int *C_cnt, int capC,
+                              int *D_list, int *D_cnt, int capD, int *X_list, int *X_cnt, int capX,
+                              int *V_list, int *V_cnt, int capV, int *flags) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cnt) return;
+    int t = off + j;
+    int nc = 0, nd = 0, nx = 0, nv = 0;
+    if (N.t1[t] > N.t0[t]) {
+        int P = N.parent[t];
+        int *Cl = C_list + (int64_t)t * capC;
+        int *Dl = D_list + (int64_t)t * capD;
+        int *Xl = X_list + (int64_t)t * capX;
+        int *Vl = V_list + (int64_t)t * capV;
+        bool ovf = false;
+        const int *CP = C_list + (int64_t)P * capC;
+        for (int a = 0; a < C_cnt[P]; ++a) {
+            int s = CP[a];
+            if (N.split[s]) {
+                int c0 = N.cfirst[s], c1 = c0 + N.nchild[s];
+                for (int c = c0; c < c1; ++c) {
+                    if (N.s1[c] <= N.s0[c]) continue;
+                    if (adjacent(N, t, c)) {
+                        if (nc < capC) Cl[nc++] = c; else ovf = true;
+                    } else {
+                        if (nv < capV) Vl[nv++] = c; else ovf = true;
+                    }
+                }
+            } else {
+                if (adjacent(N, t, s)) {
+                    if (nd < capD) Dl[nd++] = s; else ovf = true;
+                } else {
+                    if (nx < capX) Xl[nx++] = s; else ovf = true;
+                }
+            }
+        }
+        const int *DP = D_list + (int64_t)P * capD;
+        for (int a = 0; a < D_cnt[P]; ++a) {
+            int s = DP[a];
+            if (adjacent(N, t, s)) {
+                if (nd < capD) Dl[nd++] = s; else ovf = true;
+            } else {
+                if (nx < capX) Xl[nx++] = s; else ovf = true;
+            }
+        }
+        isort(Dl, nd);
+        isort(Xl, nx);
+        if (ovf) atomicOr(flags, FLAG_LIST_OVERFLOW);
+    }
+    C_cnt[t] = nc;
+    D_cnt[t] = nd;
+    X_cnt[t] = nx;
+    V_cnt[t] = nv;
+}
+
+// near-field list of a target leaf: U (leaves of C(t), D(t), the adjacent
+// leaves found below the non-leaf boxes of C(t)), W (non-adjacent boxes found
+// there) and X of t and of every ancestor.
+__global__ void k_near(int off, int cnt, NodeView N, const int *C_list, const int *C_cnt, int capC,
+                       const int *D_list, const int *D_cnt, int capD, const int *X_list,
+                       const int *X_cnt, int capX, int *near_tmp, int *near_cnt, int capN,
+                       int *flags) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cnt) return;
+    int t = off + j;
+    int n = 0;
+    if (N.t1[t] > N.t0[t] && !N.split[t]) {
+        int *L = near_tmp + (int64_t)t * capN;
+        bool ovf = false;
+        int stack[160];
+        int sp = 0;
+        const int *Cl = C_list + (int64_t)t * capC;
+        for (int a = 0; a < C_cnt[t]; ++a) {
+            int s = Cl[a];
+            if (!N.split[s]) {
+                if (n < capN) L[n++] = s; else ovf = true;
+            } else {
+                if (sp < 160) stack[sp++] = s; else ovf = true;
+                while (sp > 0) {
+                    int u = stack[--sp];
+                    int c0 = N.cfirst[u], c1 = c0 + N.nchild[u];
+                    for (int c = c0; c < c1; ++c) {
+                        if (N.s1[c] <= N.s0[c]) continue;
+                        if (adjacent(N, t, c) && N.split[c]) {
+                            if (sp < 160) stack[sp++] = c; else ovf = true;
+                        } else {
+                            if (n < capN) L[n++] = c; else ovf = true;
+                        }
+                    }
+                }
+            }
+        }
+        const int *Dl = D_list + (int64_t)t * capD;
+        for (int a = 0; a < D_cnt[t]; ++a) {
+            if (n < capN) L[n++] = Dl[a]; else ovf = true;
+        }
+        for (int a = t; a >= 0; a = N.parent[a]) {
+            const int *Xl = X_list + (int64_t)a * capX;
+            for (int b = 0; b < X_cnt[a]; ++b) {
+                if (n < capN) L[n++] = Xl[b]; else ovf = true;
+            }
+        }
+        isort(L, n);
+        if (ovf) atomicOr(flags, FLAG_LIST_OVERFLOW);
+    }
+    near_cnt[t] = n;
+}
+
+__global__ void k_csr_fill(int n_nodes, const int *__restrict__ cnt, const int *__restrict__ tmp,
+                           int cap, const int *__restrict__ ptr, int *__restrict__ out,
+                           int *__restrict__ out_t) {
+    int t = blockIdx.x;
+    if (t >= n_nodes) return;
+    int c = cnt[t], base = ptr[t];
+    for (int a = threadIdx.x; a < c; a += blockDim.x) {
+        out[base + a] = tmp[(int64_t)t * cap + a];
+        if (out_t) out_t[base + a] = t;
+    }
+}
+
+__global__ void k_count_pairs(int n_nodes, const int *__restrict__ near_ptr,
+                              const int *__restrict__ near_src, const int *__restrict__ s0,
+                              const int *__restrict__ s1, const int *__restrict__ t0,
+                              const int *__restrict__ t1, unsigned long long *out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes) return;
+    unsigned long long acc = 0;
+    int nt = t1[t] - t0[t];
+    for (int a = near_ptr[t]; a < near_ptr[t + 1]; ++a) {
+        int s = near_src[a];
+        acc += (unsigned long long)nt * (unsigned long long)(s1[s] - s0[s]);
+    }
+    if (acc) atomicAdd(out, acc);
+}
+
+__global__ void k_layer_mismatch(int n_nodes, const int *__restrict__ layer,
+                                 const int *__restrict__ ptr, const int *__restrict__ src,
+                                 int *flags) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes) return;
+    for (int a = ptr[t]; a < ptr[t + 1]; ++a)
+        if (layer[src[a]] != layer[t]) {
+            atomicOr(flags, FLAG_CROSS_LAYER);
+            return;
+        }
+}
+
+int scan_excl(tefmm_plan_s *P, const int *in, int *out, int64_t n, cudaStream_t st) {
+    size_t bytes = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, (int)n, st);
+    TRY(dbuf_ensure(P->scan_tmp, bytes));
+    CUDA_TRY(cub::DeviceScan::ExclusiveSum(P->scan_tmp.p, bytes, in, out, (int)n, st));
+    return TEFMM_OK;
+}
+int scan_incl(tefmm_plan_s *P, const int *in, int *out, int64_t n, cudaStream_t st) {
+    size_t bytes = 0;
+    cub::DeviceScan::InclusiveSum(nullptr, bytes, in, out, (int)n, st);
+    TRY(dbuf_ensure(P->scan_tmp, bytes));
+    CUDA_TRY(cub::DeviceScan::InclusiveSum(P->scan_tmp.p, bytes, in, out, (int)n, st));
+    return TEFMM_OK;
+}
+
+// grow node arrays keeping their contents
+int grow_nodes(tefmm_plan_s *P, int64_t need, int64_t have, cudaStream_t st) {
+    DBuf *arrs[] = {&P->n_layer, &P->n_level, &P->n_ix, &P->n_iy, &P->n_iz, &P->n_parent,
+                    &P->n_cfirst, &P->n_nchild, &P->n_s0, &P->n_s1, &P->n_t0, &P->n_t1,
+                    &P->n_i0, &P->n_i1, &P->n_split};
+    for (DBuf *b : arrs) {
+        if (b->cap >= (size_t)need * sizeof(int)) continue;
+        size_t ncap = (size_t)(need * 2) * sizeof(int);
+        void *np_ = nullptr;
+        CUDA_TRY(cudaMalloc(&np_, ncap));
+        if (have > 0 && b->p) CUDA_TRY(cudaMemcpyAsync(np_, b->p, have * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (b->p) cudaFree(b->p);
+        b->p = np_;
+        b->cap = ncap;
+    }
+    return TEFMM_OK;
+}
+
+NodeView node_view(tefmm_plan_s *P) {
+    NodeView N;
+    N.layer = dp<int>(P->n_layer);
+    N.level = dp<int>(P->n_level);
+    N.ix = dp<int>(P->n_ix);
+    N.iy = dp<int>(P->n_iy);
+    N.iz = dp<int>(P->n_iz);
+    N.parent = dp<int>(P->n_parent);
+    N.cfirst = dp<int>(P->n_cfirst);
+    N.nchild = dp<int>(P->n_nchild);
+    N.s0 = dp<int>(P->n_s0);
+    N.s1 = dp<int>(P->n_s1);
+    N.t0 = dp<int>(P->n_t0);
+    N.t1 = dp<int>(P->n_t1);
+    N.split = dp<int>(P->n_split);
+    return N;
+}
+
+}  // namespace
+
+int check_flags(tefmm_plan_s *P, cudaStream_t st) {
+    int f = 0;
+    CUDA_TRY(cudaMemcpyAsync(&f, P->flags.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (f & FLAG_ON_INTERFACE) return TEFMM_ERR_POINT_ON_INTERFACE;
+    if (f & FLAG_OUT_OF_DOMAIN) return TEFMM_ERR_OUT_OF_DOMAIN;
+    if (f & FLAG_LIST_OVERFLOW) return TEFMM_ERR_LIST_OVERFLOW;
+    if (f & FLAG_CROSS_LAYER) return TEFMM_ERR_NOT_IMPLEMENTED;
+    if (f & FLAG_CHECK) return TEFMM_ERR_DEVICE_CHECK;
+    return TEFMM_OK;
+}
+
+int tree_build(tefmm_plan_s *P, const double *sx, const double *sy, const double *sz,
+               const double *q, const double *tx, const double *ty, const double *tz,
+               cudaStream_t st) {
+    const int64_t ns = P->ns, nt = P->nt;
+    const bool shared = P->shared_pts;
+    const int64_t nitems = shared ? ns : ns + nt;
+    P->nitems = nitems;
+    TRY(dbuf_ensure(P->flags, 64));
+    CUDA_TRY(cudaMemsetAsync(P->flags.p, 0, 64, st));
+
+    // bounding box of all points
+    TRY(dbuf_ensure(P->bbox, 6 * sizeof(unsigned long long)));
+    unsigned long long init[6] = {~0ULL, ~0ULL, ~0ULL, 0, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(P->bbox.p, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    k_bbox<<<grid_for(ns, 256) > 1024 ? 1024 : grid_for(ns, 256), 256, 0, st>>>(
+        ns, sx, sy, sz, dp<unsigned long long>(P->bbox));
+    P->launches++;
+    if (!shared) {
+        k_bbox<<<grid_for(nt, 256) > 1024 ? 1024 : grid_for(nt, 256), 256, 0, st>>>(
+            nt, tx, ty, tz, dp<unsigned long long>(P->bbox));
+        P->launches++;
+    }
+    unsigned long long bb[6];
+    CUDA_TRY(cudaMemcpyAsync(bb, P->bbox.p, sizeof(bb), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    double lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = double_of(bb[d]);
+        hi[d] = double_of(bb[3 + d]);
+    }
+    double side = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double e = hi[d] - lo[d];
+        if (e > side) side = e;
+    }
+    if (side == 0.0) side = 1.0;
+    for (int d = 0; d < 3; ++d) P->lo[d] = lo[d];
+    P->side = side;
+
+    Geo g;
+    for (int m = 0; m < TEFMM_MAX_LAYERS; ++m) {
+        g.d[m] = m < P->nL - 1 ? P->d[m] : 0.0;
+        g.zlo[m] = P->opt.zext[2 * m];
+        g.zhi[m] = P->opt.zext[2 * m + 1];
+    }
+    for (int d = 0; d < 3; ++d) g.lo[d] = lo[d];
+    g.side = side;
+    g.nL = P->nL;
+
+    // keys and stable sort (layer, Morton key, input index)
+    TRY(dbuf_ensure(P->keys_in, nitems * 8));
+    TRY(dbuf_ensure(P->keys_out, nitems * 8));
+    TRY(dbuf_ensure(P->vals_in, nitems * 4));
+    TRY(dbuf_ensure(P->vals_out, nitems * 4));
+    k_keys<<<grid_for(nitems, 256), 256, 0, st>>>(nitems, ns, sx, sy, sz, tx, ty, tz, g,
+                                                  dp<uint64_t>(P->keys_in), dp<int>(P->vals_in),
+                                                  dp<int>(P->flags));
+    P->launches++;
+    size_t bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, bytes, dp<uint64_t>(P->keys_in),
+                                    dp<uint64_t>(P->keys_out), dp<int>(P->vals_in),
+                                    dp<int>(P->vals_out), (int)nitems, 0, 64, st);
+    TRY(dbuf_ensure(P->cub_tmp, bytes));
+    CUDA_TRY(cub::DeviceRadixSort::SortPairs(P->cub_tmp.p, bytes, dp<uint64_t>(P->keys_in),
+                                             dp<uint64_t>(P->keys_out), dp<int>(P->vals_in),
+                                             dp<int>(P->vals_out), (int)nitems, 0, 64, st));
+    const uint64_t *keys = dp<uint64_t>(P->keys_out);
+
+    // counting scans and sorted particle arrays
+    TRY(dbuf_ensure(P->cnt_s, (nitems + 1) * 4));
+    TRY(dbuf_ensure(P->item_flag, (nitems + 1) * 4));
+    if (!shared) {
+        CUDA_TRY(cudaMemsetAsync(P->item_flag.p, 0, (nitems + 1) * 4, st));
+        k_is_src<<<grid_for(nitems, 256), 256, 0, st>>>(nitems, ns, dp<int>(P->vals_out),
+                                                        dp<int>(P->item_flag));
+        P->launches++;
+        TRY(scan_excl(P, dp<int>(P->item_flag), dp<int>(P->cnt_s), nitems + 1, st));
+    }
+    TRY(dbuf_ensure(P->sx, ns * 8));
+    TRY(dbuf_ensure(P->sy, ns * 8));
+    TRY(dbuf_ensure(P->sz, ns * 8));
+    TRY(dbuf_ensure(P->sq, ns * 16));
+    TRY(dbuf_ensure(P->perm_s, ns * 4 + 4));
+    if (!shared) {
+        TRY(dbuf_ensure(P->tx, nt * 8));
+        TRY(dbuf_ensure(P->ty, nt * 8));
+        TRY(dbuf_ensure(P->tz, nt * 8));
+        TRY(dbuf_ensure(P->perm_t, nt * 4 + 4));
+    }
+    k_gather<<<grid_for(nitems, 256), 256, 0, st>>>(
+        nitems, ns, shared, dp<int>(P->vals_out), dp<int>(P->cnt_s), sx, sy, sz, q, tx, ty, tz,
+        dp<double>(P->sx), dp<double>(P->sy), dp<double>(P->sz), dp<double>(P->sq),
+        shared ? nullptr : dp<double>(P->tx), shared ? nullptr : dp<double>(P->ty),
+        shared ? nullptr : dp<double>(P->tz), dp<int>(P->perm_s),
+        shared ? nullptr : dp<int>(P->perm_t));
+    P->launches++;
+
+    // level-by-level octree
+    TRY(dbuf_ensure(P->item_node, nitems * 4));
+    TRY(dbuf_ensure(P->item_scan, nitems * 4));
+    TRY(dbuf_ensure(P->counters, 64));
+    P->level_off.clear();
+    P->level_off.push_back(0);
+    int64_t total = 0;
+    int max_level = P->opt.max_level;
+    for (int l = 0; l <= max_level; ++l) {
+        k_mark<<<grid_for(nitems, 256), 256, 0, st>>>(nitems, l, keys, dp<int>(P->item_node),
+                                                      dp<int>(P->n_i0), dp<int>(P->n_split),
+                                                      dp<int>(P->item_flag));
+        P->launches++;
+        TRY(scan_incl(P, dp<int>(P->item_flag), dp<int>(P->item_scan), nitems, st));
+        int cnt = 0;
+        CUDA_TRY(cudaMemcpyAsync(&cnt, dp<int>(P->item_scan) + nitems - 1, 4,
+                                 cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        if (cnt == 0) break;
+        TRY(grow_nodes(P, total + cnt, total, st));
+        k_make_nodes<<<grid_for(nitems, 256), 256, 0, st>>>(
+            nitems, l, (int)total, keys, dp<int>(P->item_flag), dp<int>(P->item_scan),
+            dp<int>(P->item_node), dp<int>(P->n_layer), dp<int>(P->n_level), dp<int>(P->n_ix),
+            dp<int>(P->n_iy), dp<int>(P->n_iz), dp<int>(P->n_parent), dp<int>(P->n_i0),
+            dp<int>(P->n_nchild), dp<int>(P->n_cfirst), dp<int>(P->n_split));
+        P->launches++;
+        CUDA_TRY(cudaMemsetAsync(P->counters.p, 0, 4, st));
+        k_node_ranges<<<grid_for(cnt, 256), 256, 0, st>>>(
+            (int)total, cnt, nitems, l, P->opt.leaf_cap, max_level, dp<int>(P->n_i0),
+            dp<int>(P->n_parent), dp<int>(P->cnt_s), nullptr, shared, dp<int>(P->n_i1),
+            dp<int>(P->n_s0), dp<int>(P->n_s1), dp<int>(P->n_t0), dp<int>(P->n_t1),
+            dp<int>(P->n_split), dp<int>(P->n_cfirst), dp<int>(P->n_nchild),
+            dp<int>(P->counters));
+        P->launches++;
+        int nsplit = 0;
+        CUDA_TRY(cudaMemcpyAsync(&nsplit, P->counters.p, 4, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        total += cnt;
+        P->level_off.push_back((int)total);
+        if (nsplit == 0) break;
+    }
+    P->n_nodes = (int)total;
+    P->n_levels = (int)P->level_off.size() - 1;
+    return TEFMM_OK;
+}
+
+int lists_build(tefmm_plan_s *P, cudaStream_t st) {
+    const int nn = P->n_nodes;
+    P->cap_C = 27 * P->nL;
+    P->cap_V = 189 * P->nL;
+    P->cap_D = 64;
+    P->cap_X = 27 * P->nL + 64;
+    P->cap_near = 512;
+    TRY(dbuf_ensure(P->C_list, (size_t)nn * P->cap_C * 4));
+    TRY(dbuf_ensure(P->C_cnt, (size_t)nn * 4));
+    TRY(dbuf_ensure(P->D_list, (size_t)nn * P->cap_D * 4));
+    TRY(dbuf_ensure(P->D_cnt, (size_t)nn * 4));
+    TRY(dbuf_ensure(P->X_list, (size_t)nn * P->cap_X * 4));
+    TRY(dbuf_ensure(P->X_cnt, (size_t)nn * 4));
+    TRY(dbuf_ensure(P->V_tmp, (size_t)nn * P->cap_V * 4));
+    TRY(dbuf_ensure(P->V_cnt, (size_t)(nn + 1) * 4));
+    TRY(dbuf_ensure(P->near_tmp, (size_t)nn * P->cap_near * 4));
+    TRY(dbuf_ensure(P->near_cnt, (size_t)(nn + 1) * 4));
+    CUDA_TRY(cudaMemsetAsync(P->V_cnt.p, 0, (size_t)(nn + 1) * 4, st));
+    CUDA_TRY(cudaMemsetAsync(P->near_cnt.p, 0, (size_t)(nn + 1) * 4, st));
+    NodeView N = node_view(P);
+    int nroots = P->level_off[1];
+    k_lists_root<<<1, 32, 0, st>>>(nroots, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C,
+                                   dp<int>(P->D_cnt), dp<int>(P->X_cnt), dp<int>(P->V_cnt));
+    P->launches++;
+    for (int l = 1; l < P->n_levels; ++l) {
+        int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
+        k_lists_level<<<grid_for(cnt, 128), 128, 0, st>>>(
+            off, cnt, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C, dp<int>(P->D_list),
+            dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X,
+            dp<int>(P->V_tmp), dp<int>(P->V_cnt), P->cap_V, dp<int>(P->flags));
+        P->launches++;
+    }
+    for (int l = 0; l < P->n_levels; ++l) {
+        int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
+        k_near<<<grid_for(cnt, 64), 64, 0, st>>>(
+            off, cnt, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C, dp<int>(P->D_list),
+            dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X,
+            dp<int>(P->near_tmp), dp<int>(P->near_cnt), P->cap_near, dp<int>(P->flags));
+        P->launches++;
+    }
+    // CSR
+    TRY(dbuf_ensure(P->v_ptr, (size_t)(nn + 1) * 4));
+    TRY(dbuf_ensure(P->near_ptr, (size_t)(nn + 1) * 4));
+    TRY(scan_excl(P, dp<int>(P->V_cnt), dp<int>(P->v_ptr), nn + 1, st));
+    TRY(scan_excl(P, dp<int>(P->near_cnt), dp<int>(P->near_ptr), nn + 1, st));
+    int tot[2];
+    CUDA_TRY(cudaMemcpyAsync(&tot[0], dp<int>(P->v_ptr) + nn, 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&tot[1], dp<int>(P->near_ptr) + nn, 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    P->n_v = tot[0];
+    P->n_near = tot[1];
+    TRY(dbuf_ensure(P->v_src, (size_t)(P->n_v + 1) * 4));
+    TRY(dbuf_ensure(P->pair_t, (size_t)(P->n_v + 1) * 4));
+    TRY(dbuf_ensure(P->near_src, (size_t)(P->n_near + 1) * 4));
+    if (nn > 0) {
+        k_csr_fill<<<nn, 64, 0, st>>>(nn, dp<int>(P->V_cnt), dp<int>(P->V_tmp), P->cap_V,
+                                      dp<int>(P->v_ptr), dp<int>(P->v_src), dp<int>(P->pair_t));
+        P->launches++;
+        k_csr_fill<<<nn, 64, 0, st>>>(nn, dp<int>(P->near_cnt), dp<int>(P->near_tmp), P->cap_near,
+                                      dp<int>(P->near_ptr), dp<int>(P->near_src), nullptr);
+        P->launches++;
+        k_layer_mismatch<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_layer),
+                                                            dp<int>(P->v_ptr), dp<int>(P->v_src),
+                                                            dp<int>(P->flags));
+        P->launches++;
+        k_layer_mismatch<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_layer),
+                                                            dp<int>(P->near_ptr),
+                                                            dp<int>(P->near_src), dp<int>(P->flags));
+        P->launches++;
+    }
+    TRY(dbuf_ensure(P->counters, 64));
+    CUDA_TRY(cudaMemsetAsync(P->counters.p, 0, 8, st));
+    if (nn > 0) {
+        k_count_pairs<<<grid_for(nn, 128), 128, 0, st>>>(
+            nn, dp<int>(P->near_ptr), dp<int>(P->near_src), dp<int>(P->n_s0), dp<int>(P->n_s1),
+            dp<int>(P->n_t0), dp<int>(P->n_t1), dp<unsigned long long>(P->counters));
+        P->launches++;
+    }
+    unsigned long long np2p = 0;
+    CUDA_TRY(cudaMemcpyAsync(&np2p, P->counters.p, 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    P->n_p2p_pairs = (int64_t)np2p;
+    return TEFMM_OK;
+}

@@ -1,0 +1,44 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/tefmm.h declares (no GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tefmm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(tefmm_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1902_05875_gb300 import _build, tefmm
+    lib = ctypes.CDLL(_build.build())
+    names = _declared()
+    assert "tefmm_eval" in names and "tefmm_plan_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) <= set(tefmm.EXPORTED) | {"tefmm_plan_image_counts"}
+
+
+def test_status_strings_without_gpu():
+    from paper_1902_05875_gb300 import tefmm
+    lib = tefmm.load()
+    assert lib.tefmm_status_string(0) == b"ok"
+    assert b"interface" in lib.tefmm_status_string(-2)
+
+
+def test_default_options_without_gpu():
+    from paper_1902_05875_gb300 import tefmm
+    lib = tefmm.load()
+    o = tefmm.Options()
+    assert lib.tefmm_default_options(ctypes.byref(o)) == 0
+    assert (o.p, o.leaf_cap, o.n_images, o.n_samples) == (6, 64, 8, 101)
+    assert lib.tefmm_default_options(None) == -1
+
+
+def test_built_for_sm103a():
+    from paper_1902_05875_gb300 import _build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
