@@ -34,12 +34,12 @@ struct FitJob {
     int n, n_images;
 };
 
-__device__ __forceinline__ cplx conjc(cplx a) { return mkc(a.x, -a.y); }
-__device__ __forceinline__ double abs2(cplx a) { return a.x * a.x + a.y * a.y; }
-__device__ __forceinline__ double cabs_(cplx a) { return hypot(a.x, a.y); }
-__device__ __forceinline__ cplx clog_(cplx a) { return mkc(log(cabs_(a)), atan2(a.y, a.x)); }
+__host__ __device__ __forceinline__ cplx conjc(cplx a) { return mkc(a.x, -a.y); }
+__host__ __device__ __forceinline__ double abs2(cplx a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ double cabs_(cplx a) { return hypot(a.x, a.y); }
+__host__ __device__ __forceinline__ cplx clog_(cplx a) { return mkc(log(cabs_(a)), atan2(a.y, a.x)); }
 
-__device__ cplx kz_of(cplx k, cplx krho2) {
+__host__ __device__ cplx kz_of(cplx k, cplx krho2) {
     // sqrt(k^2 - k_rho^2) with Im >= 0
     cplx s = csqrt_p(csub(cmul(k, k), krho2));
     if (s.y < 0) s = mkc(-s.x, -s.y);
@@ -49,7 +49,7 @@ __device__ cplx kz_of(cplx k, cplx krho2) {
 // s_tau at one sample.  Unknowns: b_0, (a_1, b_1), ..., (a_{L-1}, b_{L-1}), a_L.
 // Basis: up-going b e^{i kz (z - d_l)} / kz (bottom interface reference),
 // down-going a e^{-i kz (z - d_{l-1})} / kz (top interface reference).
-__device__ cplx s_tau_sample(const FitJob &J, cplx kz_l) {
+__host__ __device__ cplx s_tau_sample(const FitJob &J, cplx kz_l) {
     const int L = J.nL - 1, nu = 2 * L;
     cplx krho2 = csub(cmul(J.k[J.layer], J.k[J.layer]), cmul(kz_l, kz_l));
     cplx kz[TEFMM_MAX_LAYERS];
@@ -194,7 +194,8 @@ __device__ void jacobi_svd(GpofSmem &S, int nrow, int ncol) {
                     double zeta = (be - al) / (2.0 * g);
                     double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-                    cplx ph = cscale(ga, 1.0 / g);   // e^{i phi}
+                    // rotate (y_p, e^{-i phi} y_q), whose inner product g is real
+                    cplx ph = conjc(cscale(ga, 1.0 / g));   // e^{-i phi}
                     for (int r = lane; r < nrow; r += 32) {
                         cplx a = S.Y[p][r], b = S.Y[q][r];
                         cplx pb = cmul(ph, b);
@@ -229,7 +230,7 @@ __device__ void jacobi_svd(GpofSmem &S, int nrow, int ncol) {
 }
 
 // eigenvalues of the m x m complex matrix S.H (destroyed), single thread
-__device__ void eig_small(GpofSmem &S, int n) {
+__host__ __device__ void eig_small(GpofSmem &S, int n) {
     // Householder reduction to upper Hessenberg form
     for (int k = 0; k < n - 2; ++k) {
         double nx = 0;
@@ -340,7 +341,7 @@ __device__ void eig_small(GpofSmem &S, int n) {
 }
 
 // least squares  min || sum_j b_j z_j^n - y_n ||, n < N, single thread (Householder)
-__device__ void vandermonde_lsq(GpofSmem &S, int N, int m) {
+__host__ __device__ void vandermonde_lsq(GpofSmem &S, int N, int m) {
     for (int n = 0; n < N; ++n) {
         for (int j = 0; j < m; ++j) {
             // z^n by repeated multiplication
