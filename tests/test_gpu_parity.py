@@ -208,7 +208,8 @@ def test_eval_host_matches_device():
     push_images(plan, img)
     a = gpu_eval(plan, torch, w.src, w.q)
     b = plan.eval_host(w.src, w.q)
-    assert np.array_equal(a, b)
+    # M2L accumulates with atomics, so the summation order (last bits) may differ
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
 
 
 def test_full_size_200k_sampled_targets():
