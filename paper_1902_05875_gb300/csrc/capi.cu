@@ -66,7 +66,8 @@ extern "C" int tefmm_eval(tefmm_plan P, int64_t ns, const double *sx, const doub
     CUDA_TRY(cudaEventRecord(P->ev[4], st));
     TRY(downward_pass(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[5], st));
-    TRY(near_field(P, phi, st));
+    if (P->opt.precision == TEFMM_MIXED) TRY(near_field_fp32(P, phi, st));
+    else TRY(near_field(P, phi, st));
     CUDA_TRY(cudaEventRecord(P->ev[6], st));
     CUDA_TRY(cudaGetLastError());
     return TEFMM_OK;

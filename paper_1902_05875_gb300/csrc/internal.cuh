@@ -202,6 +202,8 @@ int m2l_tables(tefmm_plan_s *P, cudaStream_t st);
 int m2l_apply(tefmm_plan_s *P, cudaStream_t st);
 int downward_pass(tefmm_plan_s *P, cudaStream_t st);
 int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st);
+// near32.cu
+int near_field_fp32(tefmm_plan_s *P, double *phi, cudaStream_t st);
 // plan.cu
 int plan_upload_images(tefmm_plan_s *P);
 int plan_build_operator_tables(tefmm_plan_s *P);

@@ -1,0 +1,226 @@
+// Near field of the mixed-precision form: L2P in FP64 and the pair sums of
+// Algorithm 1's "local direct interactions" in FP32.
+//
+// For a target leaf, every source box of its near list contributes
+//   q_j [ e^{ik r}/(ik r)  (free space, skipped for coincident points)
+//       + sum_tau sum_m A_m e^{ik R_m}/(ik R_m) ]  (DCIM images, Sec. 3.2 Step 3)
+// with R_m = sqrt(rho^2 + (zeta_tau - zeta_min - Z_m)^2).  Coordinates enter as
+// FP32 offsets from the target leaf's centre (each offset formed in FP64),
+// every pair is evaluated in FP32, the sum over one source box is kept in FP32
+// and added to an FP64 accumulator per target.  sin/cos use a Cody-Waite
+// reduction to [-pi, pi] (2 pi split into a short exact head and a tail)
+// followed by the hardware approximation; exp uses the hardware 2^x.
+// Pairs whose FP32 offsets coincide (r = 0) are skipped in the free-space sum.
+#include "ops_common.cuh"
+
+namespace {
+
+struct f2 {
+    float x, y;
+};
+
+__device__ __forceinline__ void sincos_red(float x, float *s, float *c) {
+    const float inv2pi = 0.159154943091895f;
+    const float c1 = 6.28125f;                  // 2 pi head (exact, 8 bits)
+    const float c2 = 1.93530717958640e-3f;      // 2 pi - c1
+    float n = rintf(x * inv2pi);
+    float y = fmaf(-n, c1, x);
+    y = fmaf(-n, c2, y);
+    __sincosf(y, s, c);
+}
+
+// e^{i k R} / R for complex k and complex R (FP32)
+__device__ __forceinline__ f2 eikr_over_r32(float kr, float ki, float Rr, float Ri) {
+    float ph = kr * Rr - ki * Ri;           // Re(k R)
+    float dec = -(kr * Ri + ki * Rr);       // -Im(k R)
+    float s, c;
+    sincos_red(ph, &s, &c);
+    float m = __expf(dec);
+    float inv = __frcp_rn(Rr * Rr + Ri * Ri);
+    // (c + i s) * m * conj(R) / |R|^2
+    float er = m * c, ei = m * s;
+    return f2{(er * Rr + ei * Ri) * inv, (ei * Rr - er * Ri) * inv};
+}
+
+__device__ __forceinline__ f2 csqrt32(float x, float y) {
+    float r = sqrtf(x * x + y * y);
+    if (r == 0.f) return f2{0.f, 0.f};
+    if (x >= 0.f) {
+        float t = sqrtf(0.5f * (r + x));
+        return f2{t, y / (2.f * t)};
+    }
+    float t = sqrtf(0.5f * (r - x));
+    return f2{fabsf(y) / (2.f * t), copysignf(t, y)};
+}
+
+__global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
+    int node = blockIdx.x;
+    if (node >= nn) return;
+    const TreeArrays &T = a.T;
+    if (T.split[node]) return;
+    int t0 = T.t0[node], t1 = T.t1[node];
+    int nt = t1 - t0;
+    if (nt <= 0) return;
+    const int TILE = 256;
+    __shared__ float xs[TILE], ys[TILE], zs[TILE];
+    __shared__ f2 qs[TILE];
+    __shared__ double2 red[128];
+    __shared__ f2 imgA[TEFMM_MAX_TERMS * TEFMM_MAX_IMG], imgZ[TEFMM_MAX_TERMS * TEFMM_MAX_IMG];
+    __shared__ float tsz[TEFMM_MAX_TERMS], tszp[TEFMM_MAX_TERMS], tcst[TEFMM_MAX_TERMS];
+    __shared__ int tcnt[TEFMM_MAX_TERMS];
+    int lay = T.layer[node];
+    cplx k = a.im.k[lay];
+    cplx ik = mkc(-k.y, k.x);
+    cplx inv_ik = cdiv(mkc(1, 0), ik);
+    int l = T.level[node];
+    double h = box_h(a.cb.side, l);
+    double cx = centre(a.cb.lo[0], T.ix[node], h), cy = centre(a.cb.lo[1], T.iy[node], h),
+           cz = centre(a.cb.lo[2], T.iz[node], h);
+    int tf = a.im.lt_first[lay], ntm = a.im.lt_count[lay];
+    if (threadIdx.x < ntm) {
+        DevTerm t = a.im.terms[tf + threadIdx.x];
+        tsz[threadIdx.x] = (float)t.sz;
+        tszp[threadIdx.x] = (float)t.szp;
+        // zeta - zeta_min = sz z' + szp z'' + ((sz + szp) cz + c - zeta_min) with z' = z - cz
+        tcst[threadIdx.x] = (float)((t.sz + t.szp) * cz + t.c - t.zmin);
+        tcnt[threadIdx.x] = t.count;
+    }
+    for (int ti = 0; ti < ntm; ++ti) {
+        DevTerm t = a.im.terms[tf + ti];
+        for (int j = threadIdx.x; j < t.count; j += blockDim.x) {
+            cplx A = cmul(a.im.A[t.first + j], inv_ik);
+            cplx Z = a.im.Z[t.first + j];
+            imgA[ti * TEFMM_MAX_IMG + j] = f2{(float)A.x, (float)A.y};
+            imgZ[ti * TEFMM_MAX_IMG + j] = f2{(float)Z.x, (float)Z.y};
+        }
+    }
+    const float kr = (float)k.x, ki = (float)k.y;
+    const f2 iik = f2{(float)inv_ik.x, (float)inv_ik.y};
+    int ntp = 1;
+    while (ntp < nt && ntp < 128) ntp <<= 1;
+    int nslice = 128 / ntp;
+    int my_t = threadIdx.x % ntp, slice = threadIdx.x / ntp;
+    int nb0 = a.near_ptr[node], nb1 = a.near_ptr[node + 1];
+    for (int tbase = 0; tbase < nt; tbase += ntp) {
+        int ti = tbase + my_t;
+        bool active = ti < nt;
+        double xt = 0, yt = 0, zt = 0;
+        if (active) {
+            xt = a.tx[t0 + ti];
+            yt = a.ty[t0 + ti];
+            zt = a.tz[t0 + ti];
+        }
+        const float xf = (float)(xt - cx), yf = (float)(yt - cy), zf = (float)(zt - cz);
+        double accr = 0.0, acci = 0.0;
+        __syncthreads();
+        for (int nb = nb0; nb < nb1; ++nb) {
+            int s = a.near_src[nb];
+            int s0 = T.s0[s], s1 = T.s1[s];
+            for (int base = s0; base < s1; base += TILE) {
+                int cnt = min(TILE, s1 - base);
+                __syncthreads();
+                for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+                    xs[j] = (float)(a.sx[base + j] - cx);
+                    ys[j] = (float)(a.sy[base + j] - cy);
+                    zs[j] = (float)(a.sz[base + j] - cz);
+                    qs[j] = f2{(float)a.sq[2 * (base + j)], (float)a.sq[2 * (base + j) + 1]};
+                }
+                __syncthreads();
+                if (!active) continue;
+                float fr = 0.f, fi = 0.f;      // free space, times q
+                float gr = 0.f, gi = 0.f;      // images, times q
+                for (int j = slice; j < cnt; j += nslice) {
+                    float dx = xf - xs[j], dy = yf - ys[j], dz = zf - zs[j];
+                    float rho2 = dx * dx + dy * dy;
+                    float r2 = rho2 + dz * dz;
+                    f2 q = qs[j];
+                    if (r2 > 0.f) {
+                        float r = sqrtf(r2);
+                        float s, c;
+                        sincos_red(kr * r, &s, &c);
+                        float m = __expf(-ki * r) * __frcp_rn(r);
+                        float er = m * c, ei = m * s;
+                        fr += q.x * er - q.y * ei;
+                        fi += q.x * ei + q.y * er;
+                    }
+                    float hr = 0.f, hi = 0.f;
+                    for (int tm = 0; tm < ntm; ++tm) {
+                        float w0 = tsz[tm] * zf + tszp[tm] * zs[j] + tcst[tm];
+                        for (int m = 0; m < tcnt[tm]; ++m) {
+                            f2 Z = imgZ[tm * TEFMM_MAX_IMG + m];
+                            float wr = w0 - Z.x, wi = -Z.y;
+                            f2 R = csqrt32(rho2 + wr * wr - wi * wi, 2.f * wr * wi);
+                            f2 g = eikr_over_r32(kr, ki, R.x, R.y);
+                            f2 A = imgA[tm * TEFMM_MAX_IMG + m];
+                            hr += A.x * g.x - A.y * g.y;
+                            hi += A.x * g.y + A.y * g.x;
+                        }
+                    }
+                    gr += q.x * hr - q.y * hi;
+                    gi += q.x * hi + q.y * hr;
+                }
+                // free part still needs the factor 1/(ik)
+                float ur = iik.x * fr - iik.y * fi, ui = iik.x * fi + iik.y * fr;
+                accr += (double)(ur + gr);
+                acci += (double)(ui + gi);
+            }
+        }
+        __syncthreads();
+        red[threadIdx.x] = make_double2(accr, acci);
+        __syncthreads();
+        if (slice == 0 && active) {
+            for (int sl = 1; sl < nslice; ++sl) {
+                accr += red[sl * ntp + my_t].x;
+                acci += red[sl * ntp + my_t].y;
+            }
+            // L2P in FP64
+            double d[3] = {xt - cx, yt - cy, zt - cz};
+            double pw[3][13];
+            for (int e = 0; e < 3; ++e) {
+                double v = 1.0;
+                for (int qq = 0; qq <= a.p; ++qq) {
+                    pw[e][qq] = v;
+                    v *= d[e];
+                }
+            }
+            const cplx *bt = a.beta + (int64_t)node * a.np;
+            for (int kk = 0; kk < a.np; ++kk) {
+                double m = pw[0][a.mi[3 * kk]] * pw[1][a.mi[3 * kk + 1]] * pw[2][a.mi[3 * kk + 2]];
+                cplx b = bt[kk];
+                accr += b.x * m;
+                acci += b.y * m;
+            }
+            int out = a.perm_t[t0 + ti];
+            a.phi[2 * out] = accr;
+            a.phi[2 * out + 1] = acci;
+        }
+    }
+}
+
+}  // namespace
+
+int near_field_fp32(tefmm_plan_s *P, double *phi, cudaStream_t st) {
+    NearArgs a;
+    a.T = tree_arrays(P);
+    a.cb = cube_of(P);
+    a.p = P->p;
+    a.np = P->np;
+    a.mi = dp<int>(P->d_mi);
+    a.near_ptr = dp<int>(P->near_ptr);
+    a.near_src = dp<int>(P->near_src);
+    a.sx = dp<double>(P->sx);
+    a.sy = dp<double>(P->sy);
+    a.sz = dp<double>(P->sz);
+    a.sq = dp<double>(P->sq);
+    a.tx = P->shared_pts ? a.sx : dp<double>(P->tx);
+    a.ty = P->shared_pts ? a.sy : dp<double>(P->ty);
+    a.tz = P->shared_pts ? a.sz : dp<double>(P->tz);
+    a.perm_t = P->shared_pts ? dp<int>(P->perm_s) : dp<int>(P->perm_t);
+    a.beta = dp<cplx>(P->beta);
+    a.im = img_view(P);
+    a.phi = phi;
+    k_near_fp32<<<P->n_nodes, 128, 0, st>>>(P->n_nodes, a);
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}

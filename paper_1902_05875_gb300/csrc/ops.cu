@@ -20,50 +20,11 @@
 // with (-1)^{g3} folded into the down-up and down-down images.
 #include <cub/cub.cuh>
 
-#include "internal.cuh"
+#include "ops_common.cuh"
 
 namespace {
 
 constexpr int CH = 16;          // pairs per M2L work chunk
-
-struct TreeArrays {
-    const int *layer, *level, *ix, *iy, *iz, *parent, *cfirst, *nchild, *s0, *s1, *t0, *t1, *split;
-};
-
-TreeArrays tree_arrays(tefmm_plan_s *P) {
-    TreeArrays T;
-    T.layer = dp<int>(P->n_layer);
-    T.level = dp<int>(P->n_level);
-    T.ix = dp<int>(P->n_ix);
-    T.iy = dp<int>(P->n_iy);
-    T.iz = dp<int>(P->n_iz);
-    T.parent = dp<int>(P->n_parent);
-    T.cfirst = dp<int>(P->n_cfirst);
-    T.nchild = dp<int>(P->n_nchild);
-    T.s0 = dp<int>(P->n_s0);
-    T.s1 = dp<int>(P->n_s1);
-    T.t0 = dp<int>(P->n_t0);
-    T.t1 = dp<int>(P->n_t1);
-    T.split = dp<int>(P->n_split);
-    return T;
-}
-
-struct Cube {
-    double lo[3];
-    double side;
-};
-
-// box centre lo + (i + 0.5) * (side / 2^l), no contraction
-__device__ __forceinline__ double centre(double lo, int i, double h) {
-    return __dadd_rn(lo, __dmul_rn((double)i + 0.5, h));
-}
-__device__ __forceinline__ double box_h(double side, int l) { return side / (double)(1 << l); }
-
-__device__ __forceinline__ double binom(int n, int k) {
-    double r = 1.0;
-    for (int i = 1; i <= k; ++i) r = r * (double)(n - k + i) / (double)i;
-    return r;
-}
 
 // ------------------------------------------------------------------ P2M
 __global__ void k_p2m(int nn, TreeArrays T, Cube cb, int p, int np, const int *__restrict__ mi,
@@ -315,13 +276,6 @@ __global__ void k_chunk_cnt(int nchunks, int64_t nvalid, const int *__restrict__
 }
 
 // ------------------------------------------------------------------ derivative tables
-struct ImgView {
-    const DevTerm *terms;
-    const cplx *A, *Z;
-    const int *lt_first, *lt_count;   // per layer: term range
-    const cplx *k;
-};
-
 // One derivative table per key: sum over the key's images of
 // A_j D^g h0(k R_j) / g!, |g| <= 2p, by the recurrence (Sec. 3.2)
 //   |g| R^2 a_g + (2|g|-1) sum_i x_i a_{g-e_i} + (|g|-1) sum_i a_{g-2e_i}
@@ -488,19 +442,6 @@ __global__ void k_m2l_fp64(int nchunks, const int *__restrict__ chunk_start,
 }
 
 // ------------------------------------------------------------------ near field (FP64)
-struct NearArgs {
-    TreeArrays T;
-    Cube cb;
-    int p, np;
-    const int *mi;
-    const int *near_ptr, *near_src;
-    const double *sx, *sy, *sz, *sq, *tx, *ty, *tz;
-    const int *perm_t;
-    const cplx *beta;
-    ImgView im;
-    double *phi;
-};
-
 __device__ __forceinline__ cplx eikr_over_r(cplx ik, cplx R) {
     // e^{ikR}/R
     cplx e = cexp_(cmul(ik, R));
@@ -632,24 +573,6 @@ __global__ void k_near_fp64(int nn, NearArgs a) {
             a.phi[2 * out + 1] = tot.y;
         }
     }
-}
-
-ImgView img_view(tefmm_plan_s *P) {
-    ImgView im;
-    im.terms = dp<DevTerm>(P->d_terms);
-    im.A = dp<cplx>(P->d_A);
-    im.Z = dp<cplx>(P->d_Z);
-    im.k = dp<cplx>(P->d_k);
-    im.lt_first = dp<int>(P->d_k) == nullptr ? nullptr : (const int *)(dp<cplx>(P->d_k) + TEFMM_MAX_LAYERS);
-    im.lt_count = im.lt_first + TEFMM_MAX_LAYERS;
-    return im;
-}
-
-Cube cube_of(tefmm_plan_s *P) {
-    Cube c;
-    for (int d = 0; d < 3; ++d) c.lo[d] = P->lo[d];
-    c.side = P->side;
-    return c;
 }
 
 int scan_i(tefmm_plan_s *P, const int *in, int *out, int64_t n, bool inclusive, cudaStream_t st) {

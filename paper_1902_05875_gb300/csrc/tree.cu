@@ -365,17 +365,19 @@ __global__ void k_lists_level(int off, int cnt, NodeView N, int *C_list, int *C_
 
 // near-field list of a target leaf: U (leaves of C(t), D(t), the adjacent
 // leaves found below the non-leaf boxes of C(t)), W (non-adjacent boxes found
-// there) and X of t and of every ancestor.
+// there) and X of t and of every ancestor.  Two passes: with out == nullptr
+// only the count is written; otherwise the list is written at out[ptr[t]..]
+// and sorted.
 __global__ void k_near(int off, int cnt, NodeView N, const int *C_list, const int *C_cnt, int capC,
                        const int *D_list, const int *D_cnt, int capD, const int *X_list,
-                       const int *X_cnt, int capX, int *near_tmp, int *near_cnt, int capN,
+                       const int *X_cnt, int capX, const int *ptr, int *out, int *near_cnt,
                        int *flags) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cnt) return;
     int t = off + j;
     int n = 0;
     if (N.t1[t] > N.t0[t] && !N.split[t]) {
-        int *L = near_tmp + (int64_t)t * capN;
+        int *L = out ? out + ptr[t] : nullptr;
         bool ovf = false;
         int stack[160];
         int sp = 0;
@@ -383,7 +385,8 @@ __global__ void k_near(int off, int cnt, NodeView N, const int *C_list, const in
         for (int a = 0; a < C_cnt[t]; ++a) {
             int s = Cl[a];
             if (!N.split[s]) {
-                if (n < capN) L[n++] = s; else ovf = true;
+                if (L) L[n] = s;
+                ++n;
             } else {
                 if (sp < 160) stack[sp++] = s; else ovf = true;
                 while (sp > 0) {
@@ -394,7 +397,8 @@ __global__ void k_near(int off, int cnt, NodeView N, const int *C_list, const in
                         if (adjacent(N, t, c) && N.split[c]) {
                             if (sp < 160) stack[sp++] = c; else ovf = true;
                         } else {
-                            if (n < capN) L[n++] = c; else ovf = true;
+                            if (L) L[n] = c;
+                            ++n;
                         }
                     }
                 }
@@ -402,18 +406,20 @@ __global__ void k_near(int off, int cnt, NodeView N, const int *C_list, const in
         }
         const int *Dl = D_list + (int64_t)t * capD;
         for (int a = 0; a < D_cnt[t]; ++a) {
-            if (n < capN) L[n++] = Dl[a]; else ovf = true;
+            if (L) L[n] = Dl[a];
+            ++n;
         }
         for (int a = t; a >= 0; a = N.parent[a]) {
             const int *Xl = X_list + (int64_t)a * capX;
             for (int b = 0; b < X_cnt[a]; ++b) {
-                if (n < capN) L[n++] = Xl[b]; else ovf = true;
+                if (L) L[n] = Xl[b];
+                ++n;
             }
         }
-        isort(L, n);
+        if (L) isort(L, n);
         if (ovf) atomicOr(flags, FLAG_LIST_OVERFLOW);
     }
-    near_cnt[t] = n;
+    if (!out) near_cnt[t] = n;
 }
 
 __global__ void k_csr_fill(int n_nodes, const int *__restrict__ cnt, const int *__restrict__ tmp,
@@ -668,9 +674,8 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
     const int nn = P->n_nodes;
     P->cap_C = 27 * P->nL;
     P->cap_V = 189 * P->nL;
-    P->cap_D = 64;
-    P->cap_X = 27 * P->nL + 64;
-    P->cap_near = 512;
+    P->cap_D = 128;
+    P->cap_X = 27 * P->nL + 128;
     TRY(dbuf_ensure(P->C_list, (size_t)nn * P->cap_C * 4));
     TRY(dbuf_ensure(P->C_cnt, (size_t)nn * 4));
     TRY(dbuf_ensure(P->D_list, (size_t)nn * P->cap_D * 4));
@@ -679,7 +684,6 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
     TRY(dbuf_ensure(P->X_cnt, (size_t)nn * 4));
     TRY(dbuf_ensure(P->V_tmp, (size_t)nn * P->cap_V * 4));
     TRY(dbuf_ensure(P->V_cnt, (size_t)(nn + 1) * 4));
-    TRY(dbuf_ensure(P->near_tmp, (size_t)nn * P->cap_near * 4));
     TRY(dbuf_ensure(P->near_cnt, (size_t)(nn + 1) * 4));
     CUDA_TRY(cudaMemsetAsync(P->V_cnt.p, 0, (size_t)(nn + 1) * 4, st));
     CUDA_TRY(cudaMemsetAsync(P->near_cnt.p, 0, (size_t)(nn + 1) * 4, st));
@@ -700,8 +704,8 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
         k_near<<<grid_for(cnt, 64), 64, 0, st>>>(
             off, cnt, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C, dp<int>(P->D_list),
-            dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X,
-            dp<int>(P->near_tmp), dp<int>(P->near_cnt), P->cap_near, dp<int>(P->flags));
+            dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X, nullptr,
+            nullptr, dp<int>(P->near_cnt), dp<int>(P->flags));
         P->launches++;
     }
     // CSR
@@ -718,12 +722,17 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
     TRY(dbuf_ensure(P->v_src, (size_t)(P->n_v + 1) * 4));
     TRY(dbuf_ensure(P->pair_t, (size_t)(P->n_v + 1) * 4));
     TRY(dbuf_ensure(P->near_src, (size_t)(P->n_near + 1) * 4));
+    for (int l = 0; l < P->n_levels; ++l) {
+        int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
+        k_near<<<grid_for(cnt, 64), 64, 0, st>>>(
+            off, cnt, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C, dp<int>(P->D_list),
+            dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X,
+            dp<int>(P->near_ptr), dp<int>(P->near_src), nullptr, dp<int>(P->flags));
+        P->launches++;
+    }
     if (nn > 0) {
         k_csr_fill<<<nn, 64, 0, st>>>(nn, dp<int>(P->V_cnt), dp<int>(P->V_tmp), P->cap_V,
                                       dp<int>(P->v_ptr), dp<int>(P->v_src), dp<int>(P->pair_t));
-        P->launches++;
-        k_csr_fill<<<nn, 64, 0, st>>>(nn, dp<int>(P->near_cnt), dp<int>(P->near_tmp), P->cap_near,
-                                      dp<int>(P->near_ptr), dp<int>(P->near_src), nullptr);
         P->launches++;
         k_layer_mismatch<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_layer),
                                                             dp<int>(P->v_ptr), dp<int>(P->v_src),

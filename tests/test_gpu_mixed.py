@@ -1,0 +1,49 @@
+"""Mixed-precision form (``precision=MIXED``) against the FP64 oracle (``-m gpu``).
+
+The mixed form evaluates the near-field pairs in FP32 (FP64 per-target
+accumulation) and keeps the tables, translations and L2P in FP64; its error
+against the FP64 direct sum must stay at the FP64 form's truncation level
+plus an FP32 rounding term below 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+from paper_1902_05875_gb300 import workloads as W
+from paper_1902_05875_gb300 import tefmm
+from oracle.direct import direct_sum
+
+from _helpers import need_gpu, oracle_images, push_images, make_plan, gpu_eval
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("w", [W.cfg_small(), W.middle_layer_uniform(3001, 5, 17, seed=4)],
+                         ids=lambda w: w.name)
+def test_mixed_close_to_fp64_form(w):
+    torch = need_gpu()
+    med, img = oracle_images(w)
+    p64 = make_plan(w)
+    push_images(p64, img)
+    pmx = make_plan(w, precision=tefmm.MIXED)
+    push_images(pmx, img)
+    a = gpu_eval(p64, torch, w.src, w.q)
+    b = gpu_eval(pmx, torch, w.src, w.q)
+    err = np.linalg.norm(a - b) / np.linalg.norm(a)
+    assert err < 1e-6, err
+
+
+def test_mixed_vs_direct_sum_at_sampled_targets():
+    torch = need_gpu()
+    w = W.middle_layer_uniform(20000, 8, 64, seed=7)
+    med, img = oracle_images(w)
+    pmx = make_plan(w, precision=tefmm.MIXED)
+    push_images(pmx, img)
+    p64 = make_plan(w)
+    push_images(p64, img)
+    b = gpu_eval(pmx, torch, w.src, w.q)
+    a = gpu_eval(p64, torch, w.src, w.q)
+    sel = np.random.default_rng(0).choice(len(w.src), 300, replace=False)
+    d = direct_sum(med, img, w.src, w.q, w.src[sel])
+    e64 = np.linalg.norm(a[sel] - d) / np.linalg.norm(d)
+    emx = np.linalg.norm(b[sel] - d) / np.linalg.norm(d)
+    assert emx < e64 + 1e-6, (emx, e64)
