@@ -60,6 +60,12 @@ FP64_PEAK_TFLOPS = 1.25
 FLOPS_IMAGE = 43
 FLOPS_FREE = 22
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
+# it stands (profiles/), keyed by (kernel, workload); None when not captured.
+TRAFFIC = {
+    ("k_m2l_fp64", "three_layer_middle_n200k_p8"): 4.659415e9 + 3.872982e9,
+}
+
 
 def clocks_start():
     f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
@@ -254,7 +260,7 @@ def main():
         kern = "k_tables (derivative recurrence)"
     ach = flops / (ph[dom] * 1e-3) / 1e12
     roof = {"kernel": kern, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((kern.split()[0], w.name)),
             "peak_source": "nominal GB300 FP64 (no measured FP64 figure)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

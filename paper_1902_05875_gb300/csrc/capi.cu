@@ -62,7 +62,8 @@ extern "C" int tefmm_eval(tefmm_plan P, int64_t ns, const double *sx, const doub
     CUDA_TRY(cudaEventRecord(P->ev[2], st));
     TRY(m2l_tables(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[3], st));
-    TRY(m2l_apply(P, st));
+    if (P->opt.precision == TEFMM_MIXED) TRY(m2l_apply_tc(P, st));
+    else TRY(m2l_apply(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[4], st));
     TRY(downward_pass(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[5], st));

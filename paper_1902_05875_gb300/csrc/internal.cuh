@@ -154,6 +154,11 @@ struct tefmm_plan_s {
         pair_idx_sorted, chunk_key, chunk_start, chunk_cnt, tables, table_slot, seg_tmp;
     int n_tables = 0;
     int64_t n_chunks = 0;
+    int chunk_pairs = 16;     // pairs per M2L work chunk (FP64 SIMT: 16, tensor cores: 128)
+
+    // tensor-core M2L buffers (mixed form)
+    DBuf tc_ah, tc_al, tc_bt, tc_cfA, tc_cfB;
+    int tc_cf_np = 0;
 
     // host staging for tefmm_eval_host
     DBuf h_in, h_out;
@@ -200,6 +205,9 @@ int upward_pass(tefmm_plan_s *P, cudaStream_t st);
 int m2l_prepare(tefmm_plan_s *P, cudaStream_t st);
 int m2l_tables(tefmm_plan_s *P, cudaStream_t st);
 int m2l_apply(tefmm_plan_s *P, cudaStream_t st);
+// m2l_tc.cu
+int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st);
+void m2l_tc_geometry(int np, int *Kpad, int *Ncta, int *nsplit, int *nblk);
 int downward_pass(tefmm_plan_s *P, cudaStream_t st);
 int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st);
 // near32.cu

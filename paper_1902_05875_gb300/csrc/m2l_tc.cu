@@ -1,0 +1,372 @@
+// M2L of the mixed-precision form on the 5th-generation tensor cores.
+//
+// Per key (a group of V pairs sharing one derivative table, see ops.cu) the
+// translation of eq. ``tesourceboxtotargetbox`` is a complex matrix product
+//   beta_t += H alpha_s,  H[k][k'] = C(k+k',k) (-1)^{k1'+k2'} (A_{k+k'} + (-1)^{k3'} B_{k+k'}),
+// written here in real form  C^T (pairs x 2np) = X^T (pairs x 2np) . W^T  with
+//   X^T[pair] = (Re alpha~_s, Im alpha~_s),  W = [[Re H, -Im H], [Im H, Re H]].
+// Scaling by the box size h: alpha~_k = alpha_k / h^{|k|}, the table is used as
+// T~_g = T_g h^{|g|}, and the result beta~_k = h^{|k|} beta_k.
+//
+// Precision: FP32 values split into TF32 hi/lo parts; three tcgen05.mma
+// kind::tf32 products (hi.hi + hi.lo + lo.hi) accumulate in FP32 in TMEM.
+//
+// Kernel layout: one CTA per chunk of <= 128 pairs of one key (M = 128 rows of
+// TMEM = pairs) and one slice of the output columns (N <= 512 TMEM columns).
+// The K dimension (2np, padded to 16) is walked in chunks of 16: all 256
+// threads generate the W^T slice from the table and gather the X^T slice into
+// one of two shared-memory buffers while the tensor core works on the other;
+// thread 0 issues the MMAs and commits them to the buffer's mbarrier.
+// Operands are K-major without swizzle (8-row x 16-byte core matrices,
+// LBO = 128 B between K-neighbours, SBO = 512 B between 8-row groups).
+// Every wait is bounded; on a timeout the CTA raises a flag, skips its output
+// and still releases its TMEM.
+#include "ops_common.cuh"
+
+namespace {
+
+constexpr int TM = 128;      // pairs per CTA (MMA M)
+constexpr int KC = 16;       // K elements per chunk
+constexpr int NTHR = 256;
+constexpr long SPIN_LIMIT = 4000000;
+
+struct TcArgs {
+    int nchunks;
+    const int *chunk_start, *chunk_table, *chunk_cnt;
+    const uint64_t *table_key;
+    const cplx *tables;
+    const int *items;            // sorted pair items (pair << 1 | kind)
+    const int *pair_t, *v_src;
+    const float *ah, *al;        // scaled moments, hi / lo, [node][Kpad]
+    float *bt;                   // scaled locals accumulator [node][Ntot]
+    const unsigned short *G;     // [k'][k]
+    const float *cfA, *cfB;      // [k'][k] coefficients with signs
+    const int *mi;
+    int np, np2, Kpad, Ncta, Ntot, nblk;
+    double side;
+    int *flags;
+};
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;   // LBO
+    d |= (uint64_t)(512 >> 4) << 32;   // SBO
+    d |= (uint64_t)1 << 46;            // descriptor version
+    return d;
+}
+
+// byte offset of (row r, k) in a K-major no-swizzle tile with KC columns
+__device__ __forceinline__ int koff(int r, int k) {
+    return (r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return __uint_as_float(u);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long it = 0; it < SPIN_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
+    const int c = blockIdx.x;
+    const int half = blockIdx.y;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    // layout: [2 buffers][Xh | Xl | Wh | Wl] then table
+    const int xbytes = TM * KC * 4;
+    const int wbytes = a.Ncta * KC * 4;
+    const int bufbytes = 2 * xbytes + 2 * wbytes;
+    unsigned char *buf0 = smem;
+    float2 *tab = (float2 *)(smem + 2 * bufbytes);
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_src[TM], s_tgt[TM];
+    __shared__ int s_fail;
+
+    const int tb = a.chunk_table[c];
+    const int cnt = a.chunk_cnt[c];
+    const int st = a.chunk_start[c];
+    const uint64_t key = a.table_key[tb];
+    const int kind = (int)(key >> 62);
+    const int lev = (int)((key >> 57) & 31);
+    const double h = a.side / (double)(1 << lev);
+    const float *cf = kind == 0 ? a.cfB : a.cfA;
+
+    if (tid == 0) s_fail = 0;
+    if (tid < TM) {
+        if (tid < cnt) {
+            int e = a.items[st + tid] >> 1;
+            s_src[tid] = a.v_src[e];
+            s_tgt[tid] = a.pair_t[e];
+        } else {
+            s_src[tid] = -1;
+            s_tgt[tid] = -1;
+        }
+    }
+    // scaled table T~_g = T_g h^{|g|} in FP32
+    for (int g = tid; g < a.np2; g += NTHR) {
+        int n = a.mi[3 * g] + a.mi[3 * g + 1] + a.mi[3 * g + 2];
+        double s = 1.0;
+        for (int i = 0; i < n; ++i) s *= h;
+        cplx v = a.tables[(int64_t)tb * a.np2 + g];
+        tab[g] = make_float2((float)(v.x * s), (float)(v.y * s));
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(su32(&tmem_base)), "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    const int nblk = a.nblk, blkN = a.Ncta / nblk;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(blkN >> 3) << 17) |
+                           ((uint32_t)(TM >> 4) << 24);
+    const int nk = a.Kpad / KC;
+    const int np = a.np;
+    const int n0 = half * a.Ncta;       // first output column of this CTA
+    bool ok = true;
+
+    for (int ch = 0; ch < nk; ++ch) {
+        const int b = ch & 1;
+        unsigned char *buf = buf0 + b * bufbytes;
+        unsigned char *Xh = buf, *Xl = buf + xbytes, *Wh = buf + 2 * xbytes, *Wl = buf + 2 * xbytes + wbytes;
+        if (ch >= 2) {
+            if (!mbar_wait(su32(&mbar[b]), ((ch - 2) >> 1) & 1)) ok = false;
+        }
+        const int c0 = ch * KC;
+        // X^T slice: rows = pairs, 16 K columns, hi and lo (16-byte pieces)
+        for (int i = tid; i < TM * 4 * 2; i += NTHR) {
+            int part = i / (TM * 4), rem = i % (TM * 4);
+            int r = rem >> 2, q = rem & 3;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            int s = s_src[r];
+            if (s >= 0) {
+                const float *srcp = (part == 0 ? a.ah : a.al) + (int64_t)s * a.Kpad + c0 + 4 * q;
+                v = *reinterpret_cast<const float4 *>(srcp);
+            }
+            *reinterpret_cast<float4 *>((part == 0 ? Xh : Xl) + koff(r, 4 * q)) = v;
+        }
+        // W^T slice: rows = output columns n, 16 K columns
+        for (int i = tid; i < a.Ncta * KC; i += NTHR) {
+            int nl = i / KC, kk = i % KC;
+            int n = n0 + nl, col = c0 + kk;
+            float w = 0.f;
+            if (n < 2 * np && col < 2 * np) {
+                int k = n < np ? n : n - np, po = n < np ? 0 : 1;
+                int kp = col < np ? col : col - np, pi = col < np ? 0 : 1;
+                int64_t o = (int64_t)kp * np + k;
+                float cfv = cf[o];
+                float2 t = tab[a.G[o]];
+                float hr = cfv * t.x, hi = cfv * t.y;
+                // [[Re H, -Im H], [Im H, Re H]]
+                w = (po == pi) ? hr : (po == 0 ? -hi : hi);
+            }
+            float wh = tf32_rn(w);
+            float wl = tf32_rn(w - wh);
+            *reinterpret_cast<float *>(Wh + koff(nl, kk)) = wh;
+            *reinterpret_cast<float *>(Wl + koff(nl, kk)) = wl;
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (int j = 0; j < KC / 8; ++j) {
+                for (int bl = 0; bl < nblk; ++bl) {
+                    uint32_t d = tmem + (uint32_t)(bl * blkN);
+                    uint32_t wo = (uint32_t)(bl * blkN / 8) * 512 + j * 256;
+                    uint64_t dxh = sdesc(su32(Xh) + j * 256), dxl = sdesc(su32(Xl) + j * 256);
+                    uint64_t dwh = sdesc(su32(Wh) + wo), dwl = sdesc(su32(Wl) + wo);
+                    uint32_t acc0 = (ch > 0 || j > 0) ? 1u : 0u;
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                 :: "r"(d), "l"(dxh), "l"(dwh), "r"(idesc), "r"(acc0));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                 :: "r"(d), "l"(dxh), "l"(dwl), "r"(idesc), "r"(1u));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                 :: "r"(d), "l"(dxl), "l"(dwh), "r"(idesc), "r"(1u));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(su32(&mbar[b])) : "memory");
+        }
+    }
+    // the last commit covers every MMA issued before it
+    if (!mbar_wait(su32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1)) ok = false;
+    if (!ok) atomicExch(&s_fail, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!s_fail) {
+        // epilogue: warp w reads TMEM lanes 32*(w%4).., column half w/4
+        const int row = (warp & 3) * 32 + lane;
+        const int chalf = warp >> 2;
+        const int colw = a.Ncta / 2;
+        const int t = s_tgt[row];
+        for (int cc = chalf * colw; cc < (chalf + 1) * colw; cc += 16) {
+            uint32_t r[16];
+            uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cc;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                           "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                           "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (t >= 0) {
+                float *dst = a.bt + (int64_t)t * a.Ntot + n0 + cc;
+                for (int q = 0; q < 16; q += 4) {
+                    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                                 :: "l"(dst + q), "f"(__uint_as_float(r[q])), "f"(__uint_as_float(r[q + 1])),
+                                    "f"(__uint_as_float(r[q + 2])), "f"(__uint_as_float(r[q + 3]))
+                                 : "memory");
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicOr(a.flags, FLAG_CHECK);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+    }
+}
+
+// alpha (FP64 complex, [node][np]) -> scaled FP32 TF32 hi/lo rows [node][Kpad]
+__global__ void k_split_alpha(int nn, const int *__restrict__ level, double side, int np, int Kpad,
+                              const int *__restrict__ mi, const cplx *__restrict__ alpha,
+                              float *__restrict__ ah, float *__restrict__ al) {
+    int node = blockIdx.x;
+    if (node >= nn) return;
+    double h = side / (double)(1 << level[node]);
+    double ih = 1.0 / h;
+    for (int c = threadIdx.x; c < Kpad; c += blockDim.x) {
+        float v = 0.f;
+        if (c < 2 * np) {
+            int k = c < np ? c : c - np;
+            int n = mi[3 * k] + mi[3 * k + 1] + mi[3 * k + 2];
+            double s = 1.0;
+            for (int i = 0; i < n; ++i) s *= ih;
+            cplx x = alpha[(int64_t)node * np + k];
+            v = (float)((c < np ? x.x : x.y) * s);
+        }
+        float hi = tf32_rn(v);
+        ah[(int64_t)node * Kpad + c] = hi;
+        al[(int64_t)node * Kpad + c] = tf32_rn(v - hi);
+    }
+}
+
+// beta (FP64) += beta~ / h^{|k|}
+__global__ void k_fold_beta(int nn, const int *__restrict__ level, double side, int np, int Ntot,
+                            const int *__restrict__ mi, const float *__restrict__ bt,
+                            cplx *__restrict__ beta) {
+    int node = blockIdx.x;
+    if (node >= nn) return;
+    double h = side / (double)(1 << level[node]);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        int n = mi[3 * k] + mi[3 * k + 1] + mi[3 * k + 2];
+        double s = 1.0;
+        for (int i = 0; i < n; ++i) s *= h;
+        double is = 1.0 / s;
+        cplx v = beta[(int64_t)node * np + k];
+        v.x += (double)bt[(int64_t)node * Ntot + k] * is;
+        v.y += (double)bt[(int64_t)node * Ntot + np + k] * is;
+        beta[(int64_t)node * np + k] = v;
+    }
+}
+
+}  // namespace
+
+// column geometry of the tensor-core M2L for order p
+void m2l_tc_geometry(int np, int *Kpad, int *Ncta, int *nsplit, int *nblk) {
+    int R = 2 * np;
+    *Kpad = (R + KC - 1) / KC * KC;
+    int ns = (R + 479) / 480;
+    int nc = ((R + ns - 1) / ns + 31) / 32 * 32;
+    *nsplit = ns;
+    *Ncta = nc;
+    *nblk = nc > 256 ? 2 : 1;
+}
+
+int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st) {
+    const int nn = P->n_nodes, np = P->np;
+    int Kpad, Ncta, nsplit, nblk;
+    m2l_tc_geometry(np, &Kpad, &Ncta, &nsplit, &nblk);
+    const int Ntot = Ncta * nsplit;
+    TRY(dbuf_ensure(P->beta, (size_t)nn * np * sizeof(cplx)));
+    CUDA_TRY(cudaMemsetAsync(P->beta.p, 0, (size_t)nn * np * sizeof(cplx), st));
+    if (P->n_chunks == 0) return TEFMM_OK;
+    TRY(dbuf_ensure(P->tc_ah, (size_t)nn * Kpad * 4));
+    TRY(dbuf_ensure(P->tc_al, (size_t)nn * Kpad * 4));
+    TRY(dbuf_ensure(P->tc_bt, (size_t)nn * Ntot * 4));
+    TRY(dbuf_ensure(P->tc_cfA, (size_t)np * np * 4));
+    TRY(dbuf_ensure(P->tc_cfB, (size_t)np * np * 4));
+    CUDA_TRY(cudaMemsetAsync(P->tc_bt.p, 0, (size_t)nn * Ntot * 4, st));
+    if (P->tc_cf_np != np) {
+        // FP32 copies of the M2L coefficients (exact: multinomials < 2^24 and signs)
+        std::vector<double> a((size_t)np * np), b((size_t)np * np);
+        CUDA_TRY(cudaMemcpy(a.data(), P->d_m2l_cA.p, a.size() * 8, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(b.data(), P->d_m2l_cB.p, b.size() * 8, cudaMemcpyDeviceToHost));
+        std::vector<float> fa(a.begin(), a.end()), fb(b.begin(), b.end());
+        CUDA_TRY(cudaMemcpy(P->tc_cfA.p, fa.data(), fa.size() * 4, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(P->tc_cfB.p, fb.data(), fb.size() * 4, cudaMemcpyHostToDevice));
+        P->tc_cf_np = np;
+    }
+    k_split_alpha<<<nn, 128, 0, st>>>(nn, dp<int>(P->n_level), P->side, np, Kpad, dp<int>(P->d_mi),
+                                      dp<cplx>(P->alpha), dp<float>(P->tc_ah), dp<float>(P->tc_al));
+    P->launches++;
+    TcArgs a;
+    a.nchunks = (int)P->n_chunks;
+    a.chunk_start = dp<int>(P->chunk_start);
+    a.chunk_table = dp<int>(P->chunk_key);
+    a.chunk_cnt = dp<int>(P->chunk_cnt);
+    a.table_key = dp<uint64_t>(P->table_slot);
+    a.tables = dp<cplx>(P->tables);
+    a.items = dp<int>(P->pair_idx_sorted);
+    a.pair_t = dp<int>(P->pair_t);
+    a.v_src = dp<int>(P->v_src);
+    a.ah = dp<float>(P->tc_ah);
+    a.al = dp<float>(P->tc_al);
+    a.bt = dp<float>(P->tc_bt);
+    a.G = dp<unsigned short>(P->d_m2l_g);
+    a.cfA = dp<float>(P->tc_cfA);
+    a.cfB = dp<float>(P->tc_cfB);
+    a.mi = dp<int>(P->d_mi);
+    a.np = np;
+    a.np2 = P->np2;
+    a.Kpad = Kpad;
+    a.Ncta = Ncta;
+    a.Ntot = Ntot;
+    a.nblk = nblk;
+    a.side = P->side;
+    a.flags = dp<int>(P->flags);
+    size_t sm = 2 * (size_t)(2 * TM * KC * 4 + 2 * Ncta * KC * 4) + (size_t)P->np2 * sizeof(float2);
+    CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid((unsigned)P->n_chunks, (unsigned)nsplit);
+    k_m2l_tc<<<grid, NTHR, sm, st>>>(a);
+    P->launches++;
+    k_fold_beta<<<nn, 128, 0, st>>>(nn, dp<int>(P->n_level), P->side, np, Ntot, dp<int>(P->d_mi),
+                                    dp<float>(P->tc_bt), dp<cplx>(P->beta));
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}

@@ -242,13 +242,13 @@ __global__ void k_seg_start(int64_t n, const int *__restrict__ head, const int *
 
 __global__ void k_chunk_heads(int64_t n, const uint64_t *__restrict__ keys,
                               const int *__restrict__ seg_incl, const int *__restrict__ seg_start,
-                              int *__restrict__ chead) {
+                              int *__restrict__ chead, int chsize) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     int f = 0;
     if (keys[i] != ~0ULL) {
         int s = seg_incl[i] - 1;
-        f = ((i - seg_start[s]) % CH) == 0;
+        f = ((i - seg_start[s]) % chsize) == 0;
     }
     chead[i] = f;
 }
@@ -267,12 +267,13 @@ __global__ void k_chunks(int64_t n, int64_t nvalid, const int *__restrict__ chea
 }
 
 __global__ void k_chunk_cnt(int nchunks, int64_t nvalid, const int *__restrict__ chunk_start,
-                            const int *__restrict__ chunk_table, int *__restrict__ chunk_cnt) {
+                            const int *__restrict__ chunk_table, int *__restrict__ chunk_cnt,
+                            int chsize) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nchunks) return;
     int end = (c + 1 < nchunks) ? chunk_start[c + 1] : (int)nvalid;
     int cnt = end - chunk_start[c];
-    chunk_cnt[c] = cnt < CH ? cnt : CH;
+    chunk_cnt[c] = cnt < chsize ? cnt : chsize;
 }
 
 // ------------------------------------------------------------------ derivative tables
@@ -662,7 +663,9 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     k_seg_start<<<grid_for(ni, 256), 256, 0, st>>>(ni, head, seg, keys, dp<int>(P->keyslot_flag),
                                                    dp<uint64_t>(P->table_slot));
     P->launches++;
-    k_chunk_heads<<<grid_for(ni, 256), 256, 0, st>>>(ni, keys, seg, dp<int>(P->keyslot_flag), chead);
+    P->chunk_pairs = (P->opt.precision == TEFMM_MIXED) ? 128 : CH;
+    k_chunk_heads<<<grid_for(ni, 256), 256, 0, st>>>(ni, keys, seg, dp<int>(P->keyslot_flag), chead,
+                                                     P->chunk_pairs);
     P->launches++;
     TRY(dbuf_ensure(P->keyslot_table, (ni + 1) * 4));
     TRY(scan_i(P, chead, dp<int>(P->keyslot_table), ni, true, st));
@@ -680,7 +683,8 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     P->launches++;
     const int64_t nvalid = nvalid_i;
     k_chunk_cnt<<<grid_for(nch, 256), 256, 0, st>>>(nch, nvalid, dp<int>(P->chunk_start),
-                                                    dp<int>(P->chunk_key), dp<int>(P->chunk_cnt));
+                                                    dp<int>(P->chunk_key), dp<int>(P->chunk_cnt),
+                                                    P->chunk_pairs);
     P->launches++;
     CUDA_TRY(cudaGetLastError());
     return TEFMM_OK;

@@ -213,7 +213,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
                    &P->keyslot_flag, &P->keyslot_table, &P->pair_t, &P->pair_s, &P->pair_slot,
                    &P->pair_slot_sorted, &P->pair_idx, &P->pair_idx_sorted, &P->chunk_key,
                    &P->chunk_start, &P->chunk_cnt, &P->tables, &P->table_slot, &P->seg_tmp,
-                   &P->h_in, &P->h_out};
+                   &P->h_in, &P->h_out, &P->tc_ah, &P->tc_al, &P->tc_bt, &P->tc_cfA, &P->tc_cfB};
     for (DBuf *b : all) dbuf_free(*b);
     for (int i = 0; i < 8; ++i)
         if (P->ev[i]) cudaEventDestroy(P->ev[i]);
