@@ -47,3 +47,27 @@ def test_mixed_vs_direct_sum_at_sampled_targets():
     e64 = np.linalg.norm(a[sel] - d) / np.linalg.norm(d)
     emx = np.linalg.norm(b[sel] - d) / np.linalg.norm(d)
     assert emx < e64 + 1e-6, (emx, e64)
+
+
+@pytest.mark.parametrize("w", [W.cfg_small(), W.middle_layer_uniform(20000, 8, 64, seed=7)],
+                         ids=lambda w: w.name)
+def test_tensor_core_m2l_locals(w):
+    """Locals after the tensor-core M2L (3xTF32, scaled) against the FP64 form's."""
+    torch = need_gpu()
+    med, img = oracle_images(w)
+    p64 = make_plan(w)
+    push_images(p64, img)
+    pmx = make_plan(w, precision=tefmm.MIXED)
+    push_images(pmx, img)
+    gpu_eval(p64, torch, w.src, w.q)
+    gpu_eval(pmx, torch, w.src, w.q)
+    a64, b64 = p64.export_expansions()
+    amx, bmx = pmx.export_expansions()
+    assert np.array_equal(a64, amx)          # the upward pass is FP64 in both forms
+    worst = 0.0
+    for n in range(b64.shape[0]):
+        s = np.max(np.abs(b64[n]))
+        if s > 0:
+            worst = max(worst, np.max(np.abs(bmx[n] - b64[n])) / s)
+    assert worst < 2e-5, worst
+    assert pmx.stats()["n_v_pairs"] == p64.stats()["n_v_pairs"]
