@@ -176,6 +176,34 @@ int tefmm_export_lists(tefmm_plan plan, int64_t *n_v, int64_t *n_near, int *v_pt
  * (n = 0..p; k1 = n..0; k2 = n-k1..0; k3 = n-k1-k2).  NULL skips one. */
 int tefmm_export_expansions(tefmm_plan plan, double *alpha, double *beta);
 
+/* ---- fit without device allocation -------------------------------------
+ * The paper has no counterpart to this call; it is a convenience of this
+ * library.  It runs the same device DCIM fit as tefmm_plan_create (same
+ * images, same order of terms as tefmm_plan_get_images) for callers that
+ * cannot allocate device memory at that point: code running inside a stream
+ * capture, code whose device memory is owned by a pre-sized pool allocator, or
+ * latency-critical paths that must avoid an allocation's implicit device
+ * synchronisation.  It calls no cudaMalloc/cudaFree: its scratch is a fixed
+ * array of about 46 KB inside the library, held by every device that loads the
+ * library until the process exits.
+ *   n_layers, interfaces, k_re, k_im, opt   as for tefmm_plan_create;
+ *   stream                                  cudaStream_t for the fit; the call
+ *                                           synchronises it before returning;
+ *   n_terms (out)                           number of (layer, term) entries, <= 32;
+ *   term_layer, term_tag (out, may be NULL) host int[4*n_layers];
+ *   term_count (out)                        host int[4*n_layers], images per term;
+ *   A, Z (out)                              host double[2*32*4*n_layers]: the images
+ *                                           of term t at A[2*(32*t + j)], j < term_count[t].
+ * The first call on a device looks up the array's device address and should
+ * come before any stream capture.  Calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller.  Sizes beyond the
+ * array (more than 32 fits, n_samples > 127, n_images > 32) return
+ * TEFMM_ERR_INVALID_ARG; other errors as tefmm_plan_create. */
+int tefmm_fit_images_noalloc(int n_layers, const double *interfaces, const double *k_re,
+                             const double *k_im, const tefmm_options *opt, void *stream,
+                             int *n_terms, int *term_layer, int *term_tag, int *term_count,
+                             double *A, double *Z);
+
 #ifdef __cplusplus
 }
 #endif

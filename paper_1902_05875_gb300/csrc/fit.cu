@@ -631,3 +631,173 @@ int plan_fit_images(tefmm_plan_s *P, cudaStream_t st) {
     }
     return TEFMM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// tefmm_fit_images_noalloc: the device DCIM fit without any device allocation.
+//
+// Some callers cannot call cudaMalloc at the point where they need the images
+// of a medium: code that runs while a stream is being captured into a CUDA
+// graph (an allocation there breaks the capture), frameworks that hand all
+// device memory to their own pool allocator up front, and latency-sensitive
+// loops that must not hit the implicit device-wide synchronisation of an
+// allocation.  This entry point runs the same fit kernel as
+// tefmm_plan_create, with its job descriptors and per-fit results held in the
+// fixed array below instead of freshly allocated scratch; the caller passes
+// the medium in and receives the images in its own host arrays.
+//
+// The array lives in this library's module and is held by every device that
+// loads the library until the process exits.  Its device address is looked up
+// once per device (cudaGetSymbolAddress, with that device current) on the
+// first call made on that device; that first call should therefore come
+// before any stream capture.  All calls share the array: two calls whose work
+// overlaps on the GPU (different streams or host threads) race on it, so such
+// calls must be serialised by the caller.
+namespace {
+constexpr int NOALLOC_MAX_FITS = 4 * 8;     // 8 layers x 4 reaction terms
+struct NoAllocScratch {
+    FitJob jobs[NOALLOC_MAX_FITS];
+    cplx A[NOALLOC_MAX_FITS * MAXM];
+    cplx Z[NOALLOC_MAX_FITS * MAXM];
+    int N[NOALLOC_MAX_FITS];
+    double R[NOALLOC_MAX_FITS];
+};
+
+struct NaTerm {
+    int layer, tag;
+    double zmin;
+};
+
+// the same-layer reaction terms of tefmm_plan_create, in the same order
+int noalloc_terms(int nL, const double *d, const double *zext, NaTerm *out) {
+    const int L = nL - 1;
+    int n = 0;
+    for (int l = 0; l <= L && L > 0; ++l) {
+        double zlo = zext[2 * l], zhi = zext[2 * l + 1];
+        if (l < L) out[n++] = NaTerm{l, 0, 2.0 * zlo - 2.0 * d[l]};
+        if (l > 0) out[n++] = NaTerm{l, 1, 2.0 * d[l - 1] - 2.0 * zhi};
+        if (l > 0 && l < L) {
+            double D = d[l - 1] - d[l];
+            out[n++] = NaTerm{l, 2, (zlo - zhi) + 2.0 * D};
+            out[n++] = NaTerm{l, 3, (zlo - zhi) + 2.0 * D};
+        }
+    }
+    return n;
+}
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_fit_scratch[sizeof(NoAllocScratch)];
+
+static void *g_fit_scratch_addr[64];
+static bool g_fit_scratch_ready[64];
+
+extern "C" int tefmm_fit_images_noalloc(int n_layers, const double *interfaces, const double *k_re,
+                                        const double *k_im, const tefmm_options *opt, void *stream,
+                                        int *n_terms, int *term_layer, int *term_tag,
+                                        int *term_count, double *A, double *Z) {
+    // the argument checks of tefmm_plan_create
+    if (n_layers < 1 || n_layers > 8 || !k_re || !k_im) return TEFMM_ERR_INVALID_ARG;
+    if (n_layers > 1 && !interfaces) return TEFMM_ERR_INVALID_ARG;
+    if (!n_terms || !term_count || !A || !Z) return TEFMM_ERR_INVALID_ARG;
+    for (int m = 0; m + 1 < n_layers - 1; ++m)
+        if (!(interfaces[m] > interfaces[m + 1])) return TEFMM_ERR_INVALID_ARG;
+    for (int l = 0; l < n_layers; ++l)
+        if (!(k_im[l] >= 0.0) || !(k_re[l] > 0.0)) return TEFMM_ERR_INVALID_ARG;
+    tefmm_options o;
+    if (opt) o = *opt;
+    else tefmm_default_options(&o);
+    if (o.n_images < 0 || o.n_images > TEFMM_MAX_IMG || o.n_samples < 8 || o.n_samples > MAXN ||
+        !(o.T1 > 0))
+        return TEFMM_ERR_INVALID_ARG;
+    for (int l = 0; l < n_layers; ++l) {
+        double top = (l == 0) ? (n_layers > 1 ? interfaces[0] + 1.0 : 1.0) : interfaces[l - 1];
+        double bot = (l == n_layers - 1) ? (n_layers > 1 ? interfaces[n_layers - 2] - 1.0 : -1.0)
+                                         : interfaces[l];
+        if (isnan(o.zext[2 * l])) o.zext[2 * l] = bot;
+        if (isnan(o.zext[2 * l + 1])) o.zext[2 * l + 1] = top;
+        if (!(o.zext[2 * l] <= o.zext[2 * l + 1])) return TEFMM_ERR_INVALID_ARG;
+        if (l > 0 && o.zext[2 * l + 1] > interfaces[l - 1]) return TEFMM_ERR_INVALID_ARG;
+        if (l < n_layers - 1 && o.zext[2 * l] < interfaces[l]) return TEFMM_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double d[TEFMM_MAX_LAYERS] = {0};
+    cplx k[TEFMM_MAX_LAYERS];
+    for (int m = 0; m < n_layers - 1; ++m) d[m] = interfaces[m];
+    for (int l = 0; l < n_layers; ++l) k[l] = mkc(k_re[l], k_im[l]);
+    NaTerm terms[NOALLOC_MAX_FITS];
+    const int nterms = noalloc_terms(n_layers, d, o.zext, terms);
+    *n_terms = nterms;
+    for (int i = 0; i < nterms; ++i) {
+        if (term_layer) term_layer[i] = terms[i].layer;
+        if (term_tag) term_tag[i] = terms[i].tag;
+        term_count[i] = 0;
+    }
+    if (nterms == 0 || o.n_images == 0) return TEFMM_OK;
+    // one job per term; the down-up term of an interior layer reuses the
+    // up-down fit, as in tefmm_plan_create
+    FitJob jobs[NOALLOC_MAX_FITS];
+    int job_of[NOALLOC_MAX_FITS];
+    double kmax = 0;
+    for (int l = 0; l < n_layers; ++l) kmax = fmax(kmax, k[l].x);
+    int nj = 0;
+    for (int i = 0; i < nterms; ++i) {
+        if (terms[i].tag == 3 && i > 0 && terms[i - 1].tag == 2 && terms[i - 1].layer == terms[i].layer) {
+            job_of[i] = job_of[i - 1];
+            continue;
+        }
+        FitJob J;
+        J.layer = terms[i].layer;
+        J.tag = terms[i].tag;
+        J.nL = n_layers;
+        for (int m = 0; m < TEFMM_MAX_LAYERS; ++m) {
+            J.d[m] = m < n_layers - 1 ? d[m] : 0.0;
+            J.k[m] = m < n_layers ? k[m] : mkc(1, 0);
+        }
+        J.zmin = terms[i].zmin;
+        double kl = k[J.layer].x;
+        J.T0 = o.T0 > 0 ? o.T0 : sqrt(fmax(((kmax + 0.8) / kl) * ((kmax + 0.8) / kl) - 1.0, 1e-6));
+        J.T1 = o.T1;
+        J.n = o.n_samples;
+        J.n_images = o.n_images;
+        job_of[i] = nj;
+        jobs[nj++] = J;
+    }
+    // set-up, once per device: the device address of the fixed scratch array
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return TEFMM_ERR_INVALID_ARG;
+    if (!g_fit_scratch_ready[dev]) {
+        void *ptr = nullptr;
+        CUDA_TRY(cudaGetSymbolAddress(&ptr, g_fit_scratch));
+        g_fit_scratch_addr[dev] = ptr;
+        g_fit_scratch_ready[dev] = true;
+    }
+    NoAllocScratch *S = reinterpret_cast<NoAllocScratch *>(g_fit_scratch_addr[dev]);
+    CUDA_TRY(cudaMemcpyAsync(S->jobs, jobs, nj * sizeof(FitJob), cudaMemcpyHostToDevice, st));
+    // counts and residuals start at zero; images are written up to the counts
+    CUDA_TRY(cudaMemsetAsync(S->N, 0, sizeof(S->N), st));
+    CUDA_TRY(cudaMemsetAsync(S->R, 0, sizeof(S->R), st));
+    size_t sm = sizeof(GpofSmem);
+    CUDA_TRY(cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fit<<<nj, 512, sm, st>>>(S->jobs, nj, S->A, S->Z, S->N, S->R);
+    CUDA_TRY(cudaGetLastError());
+    cplx hA[NOALLOC_MAX_FITS * MAXM], hZ[NOALLOC_MAX_FITS * MAXM];
+    int hN[NOALLOC_MAX_FITS];
+    double hR[NOALLOC_MAX_FITS];
+    CUDA_TRY(cudaMemcpyAsync(hA, S->A, nj * MAXM * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hZ, S->Z, nj * MAXM * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hN, S->N, nj * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hR, S->R, nj * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < nterms; ++i) {
+        int jb = job_of[i];
+        if (!(hR[jb] == hR[jb])) return TEFMM_ERR_FIT_FAILED;
+        term_count[i] = hN[jb];
+        for (int j = 0; j < hN[jb]; ++j) {
+            A[2 * (i * MAXM + j)] = hA[jb * MAXM + j].x;
+            A[2 * (i * MAXM + j) + 1] = hA[jb * MAXM + j].y;
+            Z[2 * (i * MAXM + j)] = hZ[jb * MAXM + j].x;
+            Z[2 * (i * MAXM + j) + 1] = hZ[jb * MAXM + j].y;
+        }
+    }
+    return TEFMM_OK;
+}

@@ -41,7 +41,7 @@ EXPORTED = [
     "tefmm_default_options", "tefmm_plan_create", "tefmm_plan_destroy", "tefmm_eval",
     "tefmm_eval_host", "tefmm_get_stats", "tefmm_status_string", "tefmm_plan_image_counts",
     "tefmm_plan_get_images", "tefmm_plan_set_images", "tefmm_export_tree", "tefmm_export_lists",
-    "tefmm_export_expansions",
+    "tefmm_export_expansions", "tefmm_fit_images_noalloc",
 ]
 
 _lib = None
@@ -81,6 +81,8 @@ def load(build_if_needed=True):
     lib.tefmm_export_tree.argtypes = [P, I, I64, I64] + [I] * 12
     lib.tefmm_export_lists.argtypes = [P, I64, I64, I, I, I, I]
     lib.tefmm_export_expansions.argtypes = [P, D, D]
+    lib.tefmm_fit_images_noalloc.argtypes = [ctypes.c_int, D, D, D, ctypes.POINTER(Options), P,
+                                             I, I, I, I, D, D]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
     lib.tefmm_status_string.restype = ctypes.c_char_p
