@@ -60,6 +60,18 @@ FP64_PEAK_TFLOPS = 1.25
 FLOPS_IMAGE = 43
 FLOPS_FREE = 22
 
+# mixed form: FP32 flops per pair evaluation in k_near_fp32, counted from its
+# formulas (image term relative to the leaf-centre reference: D 5, complex sqrt
+# 12, delta 10, e^{ik delta} 8, 1/(1+delta/R0) 10, times E0 and accumulate 8;
+# free-space term 20)
+FLOPS32_IMAGE = 53
+FLOPS32_FREE = 20
+# FP32 SIMT peak derived from the unit counts and the maximum clock:
+# 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# TF32 dense peak: the measured BF16 figure x the nominal TF32/BF16 ratio (1.1/2.25)
+TF32_OVER_BF16 = 1.1 / 2.25
+
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands (profiles/), keyed by (kernel, workload); None when not captured.
 TRAFFIC = {
@@ -165,6 +177,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     args = ap.parse_args()
     w = WORKLOADS[args.workload]()
     if args.impl == "reference":
@@ -182,7 +195,9 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1902_05875_gb300 import tefmm
-    plan = tefmm.Plan(w.interfaces, w.k, p=w.p, leaf_cap=w.leaf_cap, n_images=w.n_images, zext=w.zext)
+    prec = tefmm.MIXED if args.precision == "mixed" else tefmm.FP64
+    plan = tefmm.Plan(w.interfaces, w.k, p=w.p, leaf_cap=w.leaf_cap, n_images=w.n_images, zext=w.zext,
+                      precision=prec)
     x, y, z = [torch.tensor(np.ascontiguousarray(w.src[:, i]), device=dev) for i in range(3)]
     q = torch.tensor(w.q, device=dev)
     out = torch.empty(len(w.src), dtype=torch.complex128, device=dev)
@@ -248,26 +263,40 @@ def main():
     imgs = plan.images()
     n_img_layer = sum(len(t["A"]) for t in imgs if t["layer"] == 1)
     np_ = plan.np
+    mixed = args.precision == "mixed"
     if dom == "ms_near":
-        flops = st["n_p2p_pairs"] * (FLOPS_FREE + FLOPS_IMAGE * n_img_layer)
-        kern = "k_near_fp64 (L2P + P2P, free space + DCIM images)"
+        if mixed:
+            flops = st["n_p2p_pairs"] * (FLOPS32_FREE + FLOPS32_IMAGE * n_img_layer)
+            kern = "k_near_fp32 (L2P + FP32 P2P, free space + DCIM images)"
+            peak, bound, psrc = FP32_PEAK_TFLOPS, "alu", "FP32 lanes x 2 x max clock (derived)"
+        else:
+            flops = st["n_p2p_pairs"] * (FLOPS_FREE + FLOPS_IMAGE * n_img_layer)
+            kern = "k_near_fp64 (L2P + P2P, free space + DCIM images)"
+            peak, bound, psrc = FP64_PEAK_TFLOPS, "alu", "nominal GB300 FP64 (no measured FP64 figure)"
     elif dom == "ms_m2l":
         flops = 2 * st["n_v_pairs"] * 8 * np_ * np_
-        kern = "k_m2l_fp64 (key-grouped complex M2L contraction)"
+        if mixed:
+            kern = "k_m2l_tc (tcgen05 kind::tf32, 3xTF32 split, key-grouped M2L)"
+            peak = pk["bf16_tflops"] * TF32_OVER_BF16
+            bound, psrc = "tensor", f"TF32 = {pk_src} BF16 burst x 1.1/2.25"
+        else:
+            kern = "k_m2l_fp64 (key-grouped complex M2L contraction)"
+            peak, bound, psrc = FP64_PEAK_TFLOPS, "alu", "nominal GB300 FP64 (no measured FP64 figure)"
     else:
         np2 = (2 * w.p + 1) * (2 * w.p + 2) * (2 * w.p + 3) // 6
         flops = st["n_tables"] * (n_img_layer + 1) * np2 * 40
-        kern = "k_tables (derivative recurrence)"
+        kern = "k_tables (derivative recurrence, FP64)"
+        peak, bound, psrc = FP64_PEAK_TFLOPS, "alu", "nominal GB300 FP64 (no measured FP64 figure)"
     ach = flops / (ph[dom] * 1e-3) / 1e12
-    roof = {"kernel": kern, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": TRAFFIC.get((kern.split()[0], w.name)),
-            "peak_source": "nominal GB300 FP64 (no measured FP64 figure)"}
+    roof = {"kernel": kern, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": TRAFFIC.get((kern.split()[0], w.name)),
+            "peak_source": psrc}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+tf32x3/f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": N, "p": w.p, "leaf_cap": w.leaf_cap, "n_images": w.n_images,
-                   "precision": "fp64", "l2": "flushed (256 MB write) between timed steps",
+                   "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "phases_ms": ph,
         "counts": {"nodes": st["n_nodes"], "levels": st["n_levels"], "v_pairs": st["n_v_pairs"],

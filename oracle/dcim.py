@@ -25,7 +25,8 @@ fitted once, as F_tau(k_z) = s_tau(k_rho) e^{i k_z zeta_min,tau}, so that
 
 GPOF parameters (the paper does not state them): pencil parameter N/2, model
 order = number of singular values above ``rel_tol`` * sigma_max, capped per
-level; the images of both levels together are at most ``n_images``.
+level; the images of both levels together are at most ``n_images``; images
+with Re Z >= 0 are dropped (see ``fit_two_level``).
 """
 from __future__ import annotations
 
@@ -45,34 +46,52 @@ def default_T0(med: Medium, l):
 ABS_TOL = 1e-14
 
 
-def gpof(y, m_max, rel_tol=1e-12, decaying=False):
+CANCEL = 1e6
+
+
+def _hankel_svd(y):
+    y = np.asarray(y, dtype=complex)
+    N = y.size
+    Lp = N // 2
+    Y = np.array([y[i:i + Lp + 1] for i in range(N - Lp)])     # (N-Lp) x (Lp+1)
+    _, S, Vh = np.linalg.svd(Y)
+    return S, Vh.conj().T
+
+
+def _poles(V, m):
+    Vm = V[:, :m]                                              # (Lp+1) x m
+    V1, V2 = Vm[:-1, :], Vm[1:, :]
+    return np.linalg.eigvals(V2.conj().T @ np.linalg.pinv(V1.conj().T))
+
+
+def gpof(y, m_max, rel_tol=1e-12, decaying=False, keep=None, accept=None):
     """Generalized pencil of function: y_n ~= sum_j b_j z_j^n.
 
     Returns (z, b).  Model order: singular values of the Hankel data matrix
     above max(rel_tol * sigma_0, ABS_TOL * N) (the sampled functions are O(1),
     so anything below the absolute floor is rounding noise), at most m_max.
     With ``decaying`` only poles with |z| < 1 are kept (images that decay
-    along the first-level path).
+    along the first-level path); ``keep(z)`` (a boolean mask) drops further
+    poles before the amplitudes are fitted.  ``accept(z, b)`` may reject a
+    model order, in which case the next smaller order is tried.
     """
     y = np.asarray(y, dtype=complex)
     N = y.size
-    Lp = N // 2
-    Y = np.array([y[i:i + Lp + 1] for i in range(N - Lp)])     # (N-Lp) x (Lp+1)
-    _, S, Vh = np.linalg.svd(Y)
+    S, V = _hankel_svd(y)
     m = int(min(m_max, np.count_nonzero(S > max(rel_tol * S[0], ABS_TOL * N))))
-    if m == 0:
-        return np.zeros(0, complex), np.zeros(0, complex)
-    V = Vh.conj().T[:, :m]                                     # (Lp+1) x m
-    V1, V2 = V[:-1, :], V[1:, :]
-    Zmat = V2.conj().T @ np.linalg.pinv(V1.conj().T)
-    z = np.linalg.eigvals(Zmat)
-    if decaying:
-        z = z[np.abs(z) < 1.0]
-        if z.size == 0:
-            return np.zeros(0, complex), np.zeros(0, complex)
-    vand = z[None, :] ** np.arange(N)[:, None]
-    b, *_ = np.linalg.lstsq(vand, y, rcond=None)
-    return z, b
+    while m > 0:
+        z = _poles(V, m)
+        if decaying:
+            z = z[np.abs(z) < 1.0]
+        if keep is not None and z.size:
+            z = z[keep(z)]
+        if z.size:
+            vand = z[None, :] ** np.arange(N)[:, None]
+            b, *_ = np.linalg.lstsq(vand, y, rcond=None)
+            if accept is None or accept(z, b):
+                return z, b
+        m -= 1
+    return np.zeros(0, complex), np.zeros(0, complex)
 
 
 def sample_paths(k, T0, T1, n):
@@ -92,16 +111,34 @@ def fit_two_level(F, k, T0, T1=10.0, n=101, n_images=8, m1=None, rel_tol=1e-12):
     y2 = F(kz2)
     if m1 is None:
         m1 = n_images // 2
+    # Only images with Re Z < 0 are kept: the Sommerfeld identity that turns an
+    # image into h0 at the complex distance W - W_min - Z needs Re(W - W_min - Z)
+    # > 0 for every W >= W_min.  A model order is accepted only if no image term
+    # exceeds CANCEL times the sampled data on either path (no catastrophic
+    # cancellation between images).  Both are readings; the paper does not
+    # discuss GPOF's model order.
+    scale = max(np.max(np.abs(y1)), np.max(np.abs(y2)), 1e-300)
+
+    def small_terms(A, Z):
+        t1 = np.abs(np.exp(-1j * kz1[:, None] * Z[None, :]) * A[None, :])
+        t2 = np.abs(np.exp(-1j * kz2[:, None] * Z[None, :]) * A[None, :])
+        return bool(np.all(np.isfinite(t1)) and np.all(np.isfinite(t2)) and
+                    max(np.max(t1), np.max(t2)) <= CANCEL * scale)
+
     # level 1: e^{-i kz Z} = e^{k T0 Z} (e^{k dt1 Z})^n
-    z1, b1 = gpof(y1, m1, rel_tol, decaying=True)
-    Z1 = np.log(z1) / (k * dt1)
-    A1 = b1 * np.exp(-k * T0 * Z1)
+    c1 = k * dt1
+    conv1 = lambda z, b: (np.log(z) / c1, b * np.exp(-k * T0 * np.log(z) / c1))
+    z1, b1 = gpof(y1, m1, rel_tol, decaying=True,
+                  keep=lambda z: (np.log(z) / c1).real < 0,
+                  accept=lambda z, b: small_terms(*conv1(z, b)[::-1]))
+    Z1, A1 = conv1(z1, b1) if z1.size else (np.zeros(0, complex), np.zeros(0, complex))
     # level 2 on the residual: e^{-i kz Z} = e^{-i k Z} (e^{-i k (i - 1/T0) dt2 Z})^n
     res2 = y2 - (np.exp(-1j * kz2[:, None] * Z1[None, :]) @ A1 if A1.size else 0.0)
-    z2, b2 = gpof(res2, n_images - A1.size, rel_tol)
     c = -1j * k * (1j - 1.0 / T0) * dt2
-    Z2 = np.log(z2) / c
-    A2 = b2 * np.exp(1j * k * Z2)
+    conv2 = lambda z, b: (np.log(z) / c, b * np.exp(1j * k * np.log(z) / c))
+    z2, b2 = gpof(res2, n_images - A1.size, rel_tol, keep=lambda z: (np.log(z) / c).real < 0,
+                  accept=lambda z, b: small_terms(*conv2(z, b)[::-1]))
+    Z2, A2 = conv2(z2, b2) if z2.size else (np.zeros(0, complex), np.zeros(0, complex))
     A = np.concatenate([A1, A2])
     Z = np.concatenate([Z1, Z2])
     approx1 = np.exp(-1j * kz1[:, None] * Z[None, :]) @ A

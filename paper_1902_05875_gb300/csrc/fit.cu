@@ -25,6 +25,7 @@ constexpr int MAXM = TEFMM_MAX_IMG;  // images per fit (both levels)
 constexpr int MAXLS = 24;            // images per level
 constexpr double REL_TOL = 1e-12;
 constexpr double ABS_TOL = 1e-14;
+constexpr double CANCEL = 1e6;     // largest image term / largest sample
 
 struct FitJob {
     int layer, tag, nL;
@@ -32,6 +33,10 @@ struct FitJob {
     cplx k[TEFMM_MAX_LAYERS];
     double zmin, T0, T1;
     int n, n_images;
+    // cross-layer mode (mode = 1): source layer, direction (0 up, 1 down),
+    // source z-centre and z'-derivative order; zmin is then W_min
+    int mode, src_layer, dir, k3p;
+    double zc;
 };
 
 __host__ __device__ __forceinline__ cplx conjc(cplx a) { return mkc(a.x, -a.y); }
@@ -46,14 +51,13 @@ __host__ __device__ cplx kz_of(cplx k, cplx krho2) {
     return s;
 }
 
-// s_tau at one sample.  Unknowns: b_0, (a_1, b_1), ..., (a_{L-1}, b_{L-1}), a_L.
+// Interface solve at one sample: amplitudes of every layer for a unit source
+// wave S1 (column 0) and S2 (column 1) of a source in layer lp.
+// Unknowns: b_0, (a_1, b_1), ..., (a_{L-1}, b_{L-1}), a_L.
 // Basis: up-going b e^{i kz (z - d_l)} / kz (bottom interface reference),
 // down-going a e^{-i kz (z - d_{l-1})} / kz (top interface reference).
-__host__ __device__ cplx s_tau_sample(const FitJob &J, cplx kz_l) {
+__host__ __device__ void interface_solve(const FitJob &J, int lp, const cplx *kz, cplx x[][2]) {
     const int L = J.nL - 1, nu = 2 * L;
-    cplx krho2 = csub(cmul(J.k[J.layer], J.k[J.layer]), cmul(kz_l, kz_l));
-    cplx kz[TEFMM_MAX_LAYERS];
-    for (int m = 0; m <= L; ++m) kz[m] = kz_of(J.k[m], krho2);
     cplx A[MAXU][MAXU + 2];
     for (int r = 0; r < nu; ++r)
         for (int c = 0; c < nu + 2; ++c) A[r][c] = mkc(0, 0);
@@ -62,7 +66,6 @@ __host__ __device__ cplx s_tau_sample(const FitJob &J, cplx kz_l) {
             int m = j + side;
             double sg = side == 0 ? 1.0 : -1.0;
             cplx kw = J.k[m];
-            // b basis (m < L)
             if (m < L) {
                 int col = 2 * m;
                 cplx ex = cexp_(cmul(mkc(0, 1), cscale(kz[m], J.d[j] - J.d[m])));
@@ -81,7 +84,6 @@ __host__ __device__ cplx s_tau_sample(const FitJob &J, cplx kz_l) {
             }
         }
     }
-    const int lp = J.layer;
     // right-hand sides: column nu = unit wave S1 (source below interface lp-1),
     // column nu+1 = unit wave S2 (source above interface lp)
     if (lp > 0) {
@@ -116,14 +118,46 @@ __host__ __device__ cplx s_tau_sample(const FitJob &J, cplx kz_l) {
             for (int q = c; q < nu + 2; ++q) A[r][q] = csub(A[r][q], cmul(f, A[c][q]));
         }
     }
-    cplx x[MAXU][2];
     for (int r = nu - 1; r >= 0; --r)
         for (int h = 0; h < 2; ++h) {
             cplx s = A[r][nu + h];
             for (int q = r + 1; q < nu; ++q) s = csub(s, cmul(A[r][q], x[q][h]));
             x[r][h] = cdiv(s, A[r][r]);
         }
+}
+
+// The fitted function F(k_z) / e^{i k_z zmin} at one sample of layer J.layer.
+// Same-layer mode: the multiple-reflection factor s_tau of the term.
+// Cross-layer mode: d^{k3'}_{z'} [S2 sigma^{.u} + S1 sigma^{.d}] / k3'! at z' = zc
+// (eq. ``layermediumdensity``), sigma read in the target layer J.layer.
+__host__ __device__ cplx s_tau_sample(const FitJob &J, cplx kz_l) {
+    const int L = J.nL - 1;
+    cplx krho2 = csub(cmul(J.k[J.layer], J.k[J.layer]), cmul(kz_l, kz_l));
+    cplx kz[TEFMM_MAX_LAYERS];
+    for (int m = 0; m <= L; ++m) kz[m] = kz_of(J.k[m], krho2);
+    cplx x[MAXU][2];
     const int l = J.layer;
+    if (J.mode == 1) {
+        const int lp = J.src_layer;
+        interface_solve(J, lp, kz, x);
+        const int row = J.dir == 0 ? 2 * l : 2 * l - 1;       // b_l (up) or a_l (down)
+        cplx out = mkc(0, 0);
+        double fact = 1.0;
+        for (int i = 2; i <= J.k3p; ++i) fact *= i;
+        cplx ikp = cmul(mkc(0, 1), kz[lp]);
+        if (lp < L) {   // S2 = e^{i kz' (z' - d_l')}, d/dz' -> (i kz')
+            cplx f = cexp_(cmul(mkc(0, 1), cscale(kz[lp], J.zc - J.d[lp])));
+            for (int i = 0; i < J.k3p; ++i) f = cmul(f, ikp);
+            out = cadd(out, cmul(f, x[row][1]));
+        }
+        if (lp > 0) {   // S1 = e^{i kz' (d_{l'-1} - z')}, d/dz' -> (-i kz')
+            cplx f = cexp_(cmul(mkc(0, 1), cscale(kz[lp], J.d[lp - 1] - J.zc)));
+            for (int i = 0; i < J.k3p; ++i) f = cmul(f, mkc(-ikp.x, -ikp.y));
+            out = cadd(out, cmul(f, x[row][0]));
+        }
+        return cscale(out, 1.0 / fact);
+    }
+    interface_solve(J, l, kz, x);
     cplx eD = mkc(1, 0);
     if (l > 0 && l < L) eD = cexp_(cmul(mkc(0, -1), cscale(kz[l], J.d[l - 1] - J.d[l])));  // e^{-i kz D}
     switch (J.tag) {
@@ -383,8 +417,9 @@ __host__ __device__ void vandermonde_lsq(GpofSmem &S, int N, int m) {
     }
 }
 
-// GPOF on S.res[0..N): poles in S.zp, amplitudes in S.bb, order in S.m
-__device__ void gpof(GpofSmem &S, int N, int mmax, bool decaying) {
+// GPOF, first stage (all threads): Hankel data matrix of S.res[0..N), its SVD,
+// singular values ordered; S.m = number above max(REL_TOL sigma_0, ABS_TOL N).
+__device__ void gpof_svd(GpofSmem &S, int N) {
     const int Lp = N / 2;
     const int nrow = N - Lp, ncolr = Lp + 1;
     const int ncol = (ncolr + 1) & ~1;
@@ -407,59 +442,87 @@ __device__ void gpof(GpofSmem &S, int N, int mmax, bool decaying) {
         double smax = S.sv[S.order[0]];
         double thr = fmax(REL_TOL * smax, ABS_TOL * N);
         int m = 0;
-        int cap = mmax < MAXLS ? mmax : MAXLS;
-        while (m < ncol && m < cap && S.sv[S.order[m]] > thr) ++m;
-        // pencil: Zmat = V2^H V1 (V1^H V1)^{-1}; eigenvalues of (V1^H V1)^{-1} V2^H V1
-        // V1 = rows 0..Lp-1, V2 = rows 1..Lp of the m leading right singular vectors
-        for (int a = 0; a < m; ++a)
-            for (int b = 0; b < m; ++b) {
-                cplx g = mkc(0, 0), h = mkc(0, 0);
-                const cplx *va = S.V[S.order[a]], *vb = S.V[S.order[b]];
-                for (int r = 0; r < Lp; ++r) {
-                    g = cadd(g, cmul(conjc(va[r]), vb[r]));
-                    h = cadd(h, cmul(conjc(va[r + 1]), vb[r]));
-                }
-                S.H[a][b] = g;   // V1^H V1
-                S.B2[a][b] = h;  // V2^H V1
-            }
-        // solve (V1^H V1) X = V2^H V1 by Gaussian elimination, X -> H
-        for (int c = 0; c < m; ++c) {
-            int piv = c;
-            for (int r = c + 1; r < m; ++r)
-                if (abs2(S.H[r][c]) > abs2(S.H[piv][c])) piv = r;
-            for (int q = 0; q < m; ++q) {
-                cplx t = S.H[c][q];
-                S.H[c][q] = S.H[piv][q];
-                S.H[piv][q] = t;
-                t = S.B2[c][q];
-                S.B2[c][q] = S.B2[piv][q];
-                S.B2[piv][q] = t;
-            }
-            cplx inv = cdiv(mkc(1, 0), S.H[c][c]);
-            for (int r = 0; r < m; ++r) {
-                if (r == c) continue;
-                cplx f = cmul(S.H[r][c], inv);
-                for (int q = 0; q < m; ++q) {
-                    S.H[r][q] = csub(S.H[r][q], cmul(f, S.H[c][q]));
-                    S.B2[r][q] = csub(S.B2[r][q], cmul(f, S.B2[c][q]));
-                }
-            }
-            for (int q = 0; q < m; ++q) S.B2[c][q] = cmul(S.B2[c][q], inv);
-            for (int q = 0; q < m; ++q) S.H[c][q] = cmul(S.H[c][q], inv);
-        }
-        for (int a = 0; a < m; ++a)
-            for (int b = 0; b < m; ++b) S.H[a][b] = S.B2[a][b];
-        if (m > 0) eig_small(S, m);
-        if (decaying) {
-            int w = 0;
-            for (int j = 0; j < m; ++j)
-                if (cabs_(S.zp[j]) < 1.0) S.zp[w++] = S.zp[j];
-            m = w;
-        }
-        if (m > 0) vandermonde_lsq(S, N, m);
+        while (m < ncol && S.sv[S.order[m]] > thr) ++m;
         S.m = m;
     }
     __syncthreads();
+}
+
+// GPOF, second stage (one thread): poles and amplitudes for model order m.
+// Pencil Zmat = V2^H V1 (V1^H V1)^{-1} (V1, V2: rows 0..Lp-1 and 1..Lp of the m
+// leading right singular vectors); keeps |z| < 1 if ``decaying`` and poles with
+// Re(log(z)/c) < 0 (images with Re Z < 0); amplitudes by least squares.
+// Returns the number of poles kept (in S.zp, S.bb).
+__host__ __device__ int gpof_order(GpofSmem &S, int N, int m, bool decaying, cplx c) {
+    const int Lp = N / 2;
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) {
+            cplx g = mkc(0, 0), h = mkc(0, 0);
+            const cplx *va = S.V[S.order[a]], *vb = S.V[S.order[b]];
+            for (int r = 0; r < Lp; ++r) {
+                g = cadd(g, cmul(conjc(va[r]), vb[r]));
+                h = cadd(h, cmul(conjc(va[r + 1]), vb[r]));
+            }
+            S.H[a][b] = g;   // V1^H V1
+            S.B2[a][b] = h;  // V2^H V1
+        }
+    // solve (V1^H V1) X = V2^H V1 by Gauss-Jordan elimination, X -> H
+    for (int cc = 0; cc < m; ++cc) {
+        int piv = cc;
+        for (int r = cc + 1; r < m; ++r)
+            if (abs2(S.H[r][cc]) > abs2(S.H[piv][cc])) piv = r;
+        for (int q = 0; q < m; ++q) {
+            cplx t = S.H[cc][q];
+            S.H[cc][q] = S.H[piv][q];
+            S.H[piv][q] = t;
+            t = S.B2[cc][q];
+            S.B2[cc][q] = S.B2[piv][q];
+            S.B2[piv][q] = t;
+        }
+        cplx inv = cdiv(mkc(1, 0), S.H[cc][cc]);
+        for (int r = 0; r < m; ++r) {
+            if (r == cc) continue;
+            cplx f = cmul(S.H[r][cc], inv);
+            for (int q = 0; q < m; ++q) {
+                S.H[r][q] = csub(S.H[r][q], cmul(f, S.H[cc][q]));
+                S.B2[r][q] = csub(S.B2[r][q], cmul(f, S.B2[cc][q]));
+            }
+        }
+        for (int q = 0; q < m; ++q) S.B2[cc][q] = cmul(S.B2[cc][q], inv);
+        for (int q = 0; q < m; ++q) S.H[cc][q] = cmul(S.H[cc][q], inv);
+    }
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) S.H[a][b] = S.B2[a][b];
+    eig_small(S, m);
+    int w = 0;
+    for (int j = 0; j < m; ++j) {
+        cplx z = S.zp[j];
+        if (decaying && !(cabs_(z) < 1.0)) continue;
+        if (!(cdiv(clog_(z), c).x < 0.0)) continue;
+        S.zp[w++] = z;
+    }
+    if (w > 0) vandermonde_lsq(S, N, w);
+    return w;
+}
+
+__host__ __device__ __forceinline__ cplx path1(cplx k, double T0, double dt1, int i) {
+    return cmul(mkc(0, 1), cscale(k, T0 + i * dt1));                  // C_ap1
+}
+__host__ __device__ __forceinline__ cplx path2(cplx k, double T0, double dt2, int i) {
+    double t = i * dt2;
+    return cmul(k, mkc(1.0 - t / T0, t));                              // C_ap2
+}
+
+// no image term above CANCEL times the largest sample on either path
+__host__ __device__ bool small_terms(const cplx *A, const cplx *Z, int m, cplx k, double T0, double dt1,
+                            double dt2, int N, double scale) {
+    for (int j = 0; j < m; ++j)
+        for (int i = 0; i < N; ++i) {
+            cplx e1 = cmul(A[j], cexp_(cmul(mkc(0, -1), cmul(path1(k, T0, dt1, i), Z[j]))));
+            cplx e2 = cmul(A[j], cexp_(cmul(mkc(0, -1), cmul(path2(k, T0, dt2, i), Z[j]))));
+            if (!(cabs_(e1) <= CANCEL * scale) || !(cabs_(e2) <= CANCEL * scale)) return false;
+        }
+    return true;
 }
 
 __global__ void k_fit(const FitJob *jobs, int njobs, cplx *outA, cplx *outZ, int *outN,
@@ -473,80 +536,100 @@ __global__ void k_fit(const FitJob *jobs, int njobs, cplx *outA, cplx *outZ, int
     const cplx k = J.k[J.layer];
     const double T0 = J.T0, T1 = J.T1;
     const double dt1 = T1 / (N - 1), dt2 = T0 / (N - 1);
+    const cplx c1 = cscale(k, dt1);                                      // z = e^{c1 Z}
+    const cplx c2 = cscale(cmul(cmul(mkc(0, -1), k), mkc(-1.0 / T0, 1.0)), dt2);   // -i k (i - 1/T0) dt2
     __shared__ cplx y1[MAXN], y2[MAXN], A1[MAXM], Z1[MAXM];
     __shared__ int n1;
+    __shared__ double scale;
     // Step 1: samples
     for (int n = threadIdx.x; n < 2 * N; n += blockDim.x) {
         int lev = n / N, i = n % N;
-        cplx kz;
-        if (lev == 0) kz = cmul(mkc(0, 1), cscale(k, T0 + i * dt1));
-        else {
-            double t = i * dt2;
-            kz = cmul(k, mkc(1.0 - t / T0, t));
-        }
+        cplx kz = lev == 0 ? path1(k, T0, dt1, i) : path2(k, T0, dt2, i);
         cplx F = cmul(s_tau_sample(J, kz), cexp_(cmul(mkc(0, 1), cscale(kz, J.zmin))));
         if (lev == 0) y1[i] = F;
         else y2[i] = F;
     }
     __syncthreads();
-    // level 1
+    if (threadIdx.x == 0) {
+        double sc = 1e-300;
+        for (int i = 0; i < N; ++i) sc = fmax(sc, fmax(cabs_(y1[i]), cabs_(y2[i])));
+        scale = sc;
+    }
+    // level 1 (a model order is accepted only if its image terms stay below
+    // CANCEL times the samples on both paths)
     for (int i = threadIdx.x; i < N; i += blockDim.x) S.res[i] = y1[i];
     __syncthreads();
-    gpof(S, N, J.n_images / 2, true);
+    gpof_svd(S, N);
     if (threadIdx.x == 0) {
-        n1 = S.m;
-        for (int j = 0; j < S.m; ++j) {
-            cplx Z = cdiv(clog_(S.zp[j]), cscale(k, dt1));          // z = e^{k dt1 Z}
-            Z1[j] = Z;
-            A1[j] = cmul(S.bb[j], cexp_(cscale(cmul(k, Z), -T0)));  // A = b e^{-k T0 Z}
+        int cap = min(S.m, min(J.n_images / 2, MAXLS));
+        n1 = 0;
+        for (int m = cap; m >= 1; --m) {
+            int w = gpof_order(S, N, m, true, c1);
+            if (w == 0) continue;
+            cplx A[MAXLS], Z[MAXLS];
+            for (int j = 0; j < w; ++j) {
+                Z[j] = cdiv(clog_(S.zp[j]), c1);                                // z = e^{k dt1 Z}
+                A[j] = cmul(S.bb[j], cexp_(cscale(cmul(k, Z[j]), -T0)));       // A = b e^{-k T0 Z}
+            }
+            if (small_terms(A, Z, w, k, T0, dt1, dt2, N, scale)) {
+                for (int j = 0; j < w; ++j) {
+                    A1[j] = A[j];
+                    Z1[j] = Z[j];
+                }
+                n1 = w;
+                break;
+            }
         }
     }
     __syncthreads();
     // level 2 on the residual
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        double t = i * dt2;
-        cplx kz = cmul(k, mkc(1.0 - t / T0, t));
+        cplx kz = path2(k, T0, dt2, i);
         cplx s = y2[i];
         for (int j = 0; j < n1; ++j)
             s = csub(s, cmul(A1[j], cexp_(cmul(mkc(0, -1), cmul(kz, Z1[j])))));
         S.res[i] = s;
     }
     __syncthreads();
-    gpof(S, N, J.n_images - n1, false);
+    gpof_svd(S, N);
     if (threadIdx.x == 0) {
-        int m2 = S.m;
-        cplx cst = cscale(cmul(cmul(mkc(0, -1), k), mkc(-1.0 / T0, 1.0)), dt2);   // -i k (i - 1/T0) dt2
+        int cap = min(S.m, min(J.n_images - n1, MAXLS));
         int tot = 0;
         for (int j = 0; j < n1; ++j) {
             outA[jb * MAXM + tot] = A1[j];
             outZ[jb * MAXM + tot] = Z1[j];
             ++tot;
         }
-        for (int j = 0; j < m2; ++j) {
-            cplx Z = cdiv(clog_(S.zp[j]), cst);
-            outZ[jb * MAXM + tot] = Z;
-            outA[jb * MAXM + tot] = cmul(S.bb[j], cexp_(cmul(mkc(0, 1), cmul(k, Z))));   // A = b e^{ikZ}
-            ++tot;
+        for (int m = cap; m >= 1; --m) {
+            int w = gpof_order(S, N, m, false, c2);
+            if (w == 0) continue;
+            cplx A[MAXLS], Z[MAXLS];
+            for (int j = 0; j < w; ++j) {
+                Z[j] = cdiv(clog_(S.zp[j]), c2);
+                A[j] = cmul(S.bb[j], cexp_(cmul(mkc(0, 1), cmul(k, Z[j]))));   // A = b e^{ikZ}
+            }
+            if (small_terms(A, Z, w, k, T0, dt1, dt2, N, scale)) {
+                for (int j = 0; j < w; ++j) {
+                    outA[jb * MAXM + tot] = A[j];
+                    outZ[jb * MAXM + tot] = Z[j];
+                    ++tot;
+                }
+                break;
+            }
         }
         outN[jb] = tot;
         // residual on both paths, relative to the largest sample
-        double res = 0, sc = 0;
+        double res = 0;
         for (int lev = 0; lev < 2; ++lev)
             for (int i = 0; i < N; ++i) {
-                cplx kz;
-                if (lev == 0) kz = cmul(mkc(0, 1), cscale(k, T0 + i * dt1));
-                else {
-                    double t = i * dt2;
-                    kz = cmul(k, mkc(1.0 - t / T0, t));
-                }
-                cplx s = lev == 0 ? y1[i] : y2[i];
-                sc = fmax(sc, cabs_(s));
+                cplx kz = lev == 0 ? path1(k, T0, dt1, i) : path2(k, T0, dt2, i);
+                cplx sm = lev == 0 ? y1[i] : y2[i];
                 cplx ap = mkc(0, 0);
                 for (int j = 0; j < tot; ++j)
                     ap = cadd(ap, cmul(outA[jb * MAXM + j], cexp_(cmul(mkc(0, -1), cmul(kz, outZ[jb * MAXM + j])))));
-                res = fmax(res, cabs_(csub(ap, s)));
+                res = fmax(res, cabs_(csub(ap, sm)));
             }
-        outRes[jb] = sc > 0 ? res / sc : 0.0;
+        outRes[jb] = res / scale;
     }
 }
 
@@ -572,7 +655,8 @@ int plan_fit_images(tefmm_plan_s *P, cudaStream_t st) {
             job_of[i] = job_of[i - 1];
             continue;
         }
-        FitJob J;
+        FitJob J{};
+        J.mode = 0;
         J.layer = t.layer;
         J.tag = t.tag;
         J.nL = P->nL;
@@ -744,7 +828,8 @@ extern "C" int tefmm_fit_images_noalloc(int n_layers, const double *interfaces, 
             job_of[i] = job_of[i - 1];
             continue;
         }
-        FitJob J;
+        FitJob J{};
+        J.mode = 0;
         J.layer = terms[i].layer;
         J.tag = terms[i].tag;
         J.nL = n_layers;

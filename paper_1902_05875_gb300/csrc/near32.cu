@@ -4,13 +4,22 @@
 // For a target leaf, every source box of its near list contributes
 //   q_j [ e^{ik r}/(ik r)  (free space, skipped for coincident points)
 //       + sum_tau sum_m A_m e^{ik R_m}/(ik R_m) ]  (DCIM images, Sec. 3.2 Step 3)
-// with R_m = sqrt(rho^2 + (zeta_tau - zeta_min - Z_m)^2).  Coordinates enter as
-// FP32 offsets from the target leaf's centre (each offset formed in FP64),
-// every pair is evaluated in FP32, the sum over one source box is kept in FP32
-// and added to an FP64 accumulator per target.  sin/cos use a Cody-Waite
-// reduction to [-pi, pi] (2 pi split into a short exact head and a tail)
-// followed by the hardware approximation; exp uses the hardware 2^x.
-// Pairs whose FP32 offsets coincide (r = 0) are skipped in the free-space sum.
+// with R_m = sqrt(rho^2 + w_m^2), w_m = zeta_tau(z, z') - zeta_min - Z_m.
+// Coordinates enter as FP32 offsets from the target leaf's centre (each
+// offset formed in FP64); every pair is evaluated in FP32; the sum over one
+// source box is kept in FP32 and added to an FP64 accumulator per target.
+//
+// An image distance w_m is complex and can be large, so e^{ik R_m} in plain
+// FP32 would lose its phase and exponent to rounding.  Each image is therefore
+// evaluated relative to a reference taken at the leaf centre for both points
+// (rho = 0, w = w0_m, so R0 = w0_m): with dw = w - w0 (small, exact in FP32
+// offsets), D = R^2 - R0^2 = rho^2 + dw (2 w0 + dw) and delta = R - R0 =
+// D / (R + R0),
+//   A_m e^{ik R}/(ik R) = E0_m e^{ik delta} / (1 + delta/R0),
+//   E0_m = A_m e^{ik R0}/(ik R0)   (FP64, once per leaf and image).
+// sin, cos and exp are CUDA's accurate single-precision functions (their
+// arguments here are small: k r within a near box pair and k delta).  Pairs
+// whose FP32 offsets coincide (r = 0) are skipped in the free-space sum.
 #include "ops_common.cuh"
 
 namespace {
@@ -18,29 +27,6 @@ namespace {
 struct f2 {
     float x, y;
 };
-
-__device__ __forceinline__ void sincos_red(float x, float *s, float *c) {
-    const float inv2pi = 0.159154943091895f;
-    const float c1 = 6.28125f;                  // 2 pi head (exact, 8 bits)
-    const float c2 = 1.93530717958640e-3f;      // 2 pi - c1
-    float n = rintf(x * inv2pi);
-    float y = fmaf(-n, c1, x);
-    y = fmaf(-n, c2, y);
-    __sincosf(y, s, c);
-}
-
-// e^{i k R} / R for complex k and complex R (FP32)
-__device__ __forceinline__ f2 eikr_over_r32(float kr, float ki, float Rr, float Ri) {
-    float ph = kr * Rr - ki * Ri;           // Re(k R)
-    float dec = -(kr * Ri + ki * Rr);       // -Im(k R)
-    float s, c;
-    sincos_red(ph, &s, &c);
-    float m = __expf(dec);
-    float inv = __frcp_rn(Rr * Rr + Ri * Ri);
-    // (c + i s) * m * conj(R) / |R|^2
-    float er = m * c, ei = m * s;
-    return f2{(er * Rr + ei * Ri) * inv, (ei * Rr - er * Ri) * inv};
-}
 
 __device__ __forceinline__ f2 csqrt32(float x, float y) {
     float r = sqrtf(x * x + y * y);
@@ -62,11 +48,12 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
     int nt = t1 - t0;
     if (nt <= 0) return;
     const int TILE = 256;
+    constexpr int MI = TEFMM_MAX_TERMS * TEFMM_MAX_IMG;
     __shared__ float xs[TILE], ys[TILE], zs[TILE];
     __shared__ f2 qs[TILE];
     __shared__ double2 red[128];
-    __shared__ f2 imgA[TEFMM_MAX_TERMS * TEFMM_MAX_IMG], imgZ[TEFMM_MAX_TERMS * TEFMM_MAX_IMG];
-    __shared__ float tsz[TEFMM_MAX_TERMS], tszp[TEFMM_MAX_TERMS], tcst[TEFMM_MAX_TERMS];
+    __shared__ f2 sE0[MI], sW0[MI], sR0sq[MI], sIR0[MI];
+    __shared__ float tsz[TEFMM_MAX_TERMS], tszp[TEFMM_MAX_TERMS];
     __shared__ int tcnt[TEFMM_MAX_TERMS];
     int lay = T.layer[node];
     cplx k = a.im.k[lay];
@@ -81,17 +68,23 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
         DevTerm t = a.im.terms[tf + threadIdx.x];
         tsz[threadIdx.x] = (float)t.sz;
         tszp[threadIdx.x] = (float)t.szp;
-        // zeta - zeta_min = sz z' + szp z'' + ((sz + szp) cz + c - zeta_min) with z' = z - cz
-        tcst[threadIdx.x] = (float)((t.sz + t.szp) * cz + t.c - t.zmin);
         tcnt[threadIdx.x] = t.count;
     }
+    // per-image reference at the leaf centre (FP64)
     for (int ti = 0; ti < ntm; ++ti) {
         DevTerm t = a.im.terms[tf + ti];
         for (int j = threadIdx.x; j < t.count; j += blockDim.x) {
-            cplx A = cmul(a.im.A[t.first + j], inv_ik);
             cplx Z = a.im.Z[t.first + j];
-            imgA[ti * TEFMM_MAX_IMG + j] = f2{(float)A.x, (float)A.y};
-            imgZ[ti * TEFMM_MAX_IMG + j] = f2{(float)Z.x, (float)Z.y};
+            cplx w0 = mkc((t.sz + t.szp) * cz + t.c - t.zmin - Z.x, -Z.y);
+            cplx e = cexp_(cmul(ik, w0));                       // R0 = w0
+            cplx E0 = cmul(cmul(a.im.A[t.first + j], inv_ik), cdiv(e, w0));
+            cplx r0sq = cmul(w0, w0);
+            cplx ir0 = cdiv(mkc(1, 0), w0);
+            int s = ti * TEFMM_MAX_IMG + j;
+            sE0[s] = f2{(float)E0.x, (float)E0.y};
+            sW0[s] = f2{(float)w0.x, (float)w0.y};
+            sR0sq[s] = f2{(float)r0sq.x, (float)r0sq.y};
+            sIR0[s] = f2{(float)ir0.x, (float)ir0.y};
         }
     }
     const float kr = (float)k.x, ki = (float)k.y;
@@ -136,24 +129,39 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                     f2 q = qs[j];
                     if (r2 > 0.f) {
                         float r = sqrtf(r2);
-                        float s, c;
-                        sincos_red(kr * r, &s, &c);
-                        float m = __expf(-ki * r) * __frcp_rn(r);
-                        float er = m * c, ei = m * s;
+                        float sn, cs;
+                        sincosf(kr * r, &sn, &cs);
+                        float m = expf(-ki * r) * __frcp_rn(r);
+                        float er = m * cs, ei = m * sn;
                         fr += q.x * er - q.y * ei;
                         fi += q.x * ei + q.y * er;
                     }
                     float hr = 0.f, hi = 0.f;
                     for (int tm = 0; tm < ntm; ++tm) {
-                        float w0 = tsz[tm] * zf + tszp[tm] * zs[j] + tcst[tm];
+                        const float dw = tsz[tm] * zf + tszp[tm] * zs[j];   // w - w0 (real)
                         for (int m = 0; m < tcnt[tm]; ++m) {
-                            f2 Z = imgZ[tm * TEFMM_MAX_IMG + m];
-                            float wr = w0 - Z.x, wi = -Z.y;
-                            f2 R = csqrt32(rho2 + wr * wr - wi * wi, 2.f * wr * wi);
-                            f2 g = eikr_over_r32(kr, ki, R.x, R.y);
-                            f2 A = imgA[tm * TEFMM_MAX_IMG + m];
-                            hr += A.x * g.x - A.y * g.y;
-                            hi += A.x * g.y + A.y * g.x;
+                            const int sidx = tm * TEFMM_MAX_IMG + m;
+                            const f2 w0 = sW0[sidx], r0s = sR0sq[sidx], ir0 = sIR0[sidx];
+                            // D = rho^2 + dw (2 w0 + dw)
+                            float Dr = rho2 + dw * (2.f * w0.x + dw), Di = dw * 2.f * w0.y;
+                            // R = sqrt(R0^2 + D) (principal), delta = D / (R + R0)
+                            f2 R = csqrt32(r0s.x + Dr, r0s.y + Di);
+                            float sr = R.x + w0.x, si = R.y + w0.y;
+                            float isn = __frcp_rn(sr * sr + si * si);
+                            float der = (Dr * sr + Di * si) * isn, dei = (Di * sr - Dr * si) * isn;
+                            // e^{i k delta}
+                            float ph = kr * der - ki * dei, dec = -(kr * dei + ki * der);
+                            float sn, cs;
+                            sincosf(ph, &sn, &cs);
+                            float mg = expf(dec);
+                            float ur = mg * cs, ui = mg * sn;
+                            // 1 / (1 + delta / R0)
+                            float vr = 1.f + der * ir0.x - dei * ir0.y, vi = der * ir0.y + dei * ir0.x;
+                            float iv = __frcp_rn(vr * vr + vi * vi);
+                            float pr = (ur * vr + ui * vi) * iv, pi = (ui * vr - ur * vi) * iv;
+                            const f2 E0 = sE0[sidx];
+                            hr += E0.x * pr - E0.y * pi;
+                            hi += E0.x * pi + E0.y * pr;
                         }
                     }
                     gr += q.x * hr - q.y * hi;

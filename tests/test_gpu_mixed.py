@@ -29,6 +29,7 @@ def test_mixed_close_to_fp64_form(w):
     a = gpu_eval(p64, torch, w.src, w.q)
     b = gpu_eval(pmx, torch, w.src, w.q)
     err = np.linalg.norm(a - b) / np.linalg.norm(a)
+    print(f'mixed vs fp64 form ({w.name}): {err:.3e}')
     assert err < 1e-6, err
 
 
@@ -46,6 +47,34 @@ def test_mixed_vs_direct_sum_at_sampled_targets():
     d = direct_sum(med, img, w.src, w.q, w.src[sel])
     e64 = np.linalg.norm(a[sel] - d) / np.linalg.norm(d)
     emx = np.linalg.norm(b[sel] - d) / np.linalg.norm(d)
+    print(f'vs direct sum: mixed {emx:.3e}  fp64 {e64:.3e}')
+    # split the mixed-form error: L2P of the local differences (tensor-core M2L)
+    # against the rest (FP32 near field)
+    g = pmx.export_tree()
+    _, bmx = pmx.export_expansions()
+    _, b64 = p64.export_expansions()
+    from oracle.derivs import multi_indices
+    mi = multi_indices(w.p)
+    lo = w.src.min(axis=0)
+    side = float(np.max(w.src.max(axis=0) - lo))
+    inv = np.empty_like(g["perm_t"])
+    inv[g["perm_t"]] = np.arange(len(inv))
+    leaf = np.full(len(w.src), -1)
+    for n in range(g["n_nodes"]):
+        if g["t1"][n] > g["t0"][n]:
+            leaf[g["t0"][n]:g["t1"][n]] = n      # deepest node wins (level-major order)
+    dm2l = np.zeros(len(sel), complex)
+    for i, t in enumerate(sel):
+        n = leaf[inv[t]]
+        hh = side / 2 ** g["level"][n]
+        c = lo + (np.array([g["ix"][n], g["iy"][n], g["iz"][n]]) + 0.5) * hh
+        d = w.src[t] - c
+        mono = d[0] ** mi[:, 0] * d[1] ** mi[:, 1] * d[2] ** mi[:, 2]
+        dm2l[i] = mono @ (bmx[n] - b64[n])
+    e_m2l = np.linalg.norm(dm2l) / np.linalg.norm(a[sel])
+    e_tot = np.linalg.norm(b[sel] - a[sel]) / np.linalg.norm(a[sel])
+    e_near = np.linalg.norm(b[sel] - a[sel] - dm2l) / np.linalg.norm(a[sel])
+    print(f'mixed - fp64 at samples: total {e_tot:.3e}, from M2L {e_m2l:.3e}, near field {e_near:.3e}')
     assert emx < e64 + 1e-6, (emx, e64)
 
 
@@ -69,5 +98,6 @@ def test_tensor_core_m2l_locals(w):
         s = np.max(np.abs(b64[n]))
         if s > 0:
             worst = max(worst, np.max(np.abs(bmx[n] - b64[n])) / s)
+    print(f'tensor-core locals ({w.name}): worst relative {worst:.3e}')
     assert worst < 2e-5, worst
     assert pmx.stats()["n_v_pairs"] == p64.stats()["n_v_pairs"]
