@@ -23,9 +23,12 @@ Readings where the paper is silent (all stated the same way for the CUDA path):
   3b+2 = bit b of ix, 3b+1 = iy, 3b = iz.  Points are sorted by (layer, key,
   input index).  Box centre of coordinate i at level l: lo + (i + 0.5) *
   (side / 2^l).
-* A box is split while max(#sources, #targets) > leaf_cap and level <
+* A box is split while max(#sources, #targets) > leaf_cap, or while it is
+  adjacent to a box of the same level in another layer's tree, and level <
   max_level; only children holding a point exist.  Nodes are numbered
-  level-major: by (level, layer, Morton prefix).
+  level-major: by (level, layer, Morton prefix).  The second rule (a reading)
+  keeps leaves of different layers apart, so that every cross-layer
+  interaction is an M2L (V-list) pair.
 * Interaction lists: a dual-tree traversal of (target tree, source tree),
   which for one tree is the classic adaptive U/V/W/X construction
   (Carrier-Greengard-Rokhlin).  V pairs go through M2L; U, W and X pairs are
@@ -36,6 +39,16 @@ Readings where the paper is silent (all stated the same way for the CUDA path):
   where a_g = D^g f / g!, C(k+k', k) = prod_i (k_i+k'_i)!/(k_i! k'_i!).
   Offsets of M2L pairs are taken from integer box coordinates:
   X0 = di_x * (side / 2^l), and zt_c + zs_c = 2 lo_z + (i_t + i_s + 1) * (side / 2^l).
+* Cross-layer components (target layer l != source layer l', Sec. 3.2): per
+  source z-centre z_c and k3' = 0..p the images of Theta^{k3'} (``oracle.cross``)
+  give d^{k3'}_{z'} u / k3'! as image Hankel functions of (X, Y, W), W = z - d_l
+  (up) or d_{l-1} - z (down); hence
+  D_r^k D_r'^k' u / (k! k'!) = (-1)^{k1'+k2'} C(k1+k1',k1) C(k2+k2',k2)
+                               sz^{k3} T^{(k3')}_{(k1+k1', k2+k2', k3)},
+  T^{(k3')}_g = sum_j A_j D^g h0(k_l R_j) / g! at (X0, Y0, W(z_t) - W_min - Z_j),
+  sz = +1 (up), -1 (down).  Cross-layer near-field pairs are not supported
+  (leaves must be small enough that boxes of different layers are never
+  adjacent).
 """
 from __future__ import annotations
 
@@ -44,6 +57,7 @@ import math
 import numpy as np
 
 from .derivs import multi_indices, index_map, n_coeffs, taylor_h0
+from . import cross as xl
 
 NBITS = 20
 
@@ -126,9 +140,24 @@ class Trees:
         # child-index order, so a level is ordered by (layer, prefix).
         while frontier:
             nxt = []
+            # boxes of this level by layer, for the cross-layer adjacency rule
+            coords = {}
+            for nid in frontier:
+                l, lev, pre = nodes[nid][0], nodes[nid][1], nodes[nid][2]
+                a, b, c = morton_decode(np.uint64(pre), lev)
+                coords[nid] = (l, int(a), int(b), int(c))
+
+            def cross_adjacent(nid):
+                l, a, b, c = coords[nid]
+                for o, (lo_, a2, b2, c2) in coords.items():
+                    if lo_ != l and abs(a - a2) <= 1 and abs(b - b2) <= 1 and abs(c - c2) <= 1:
+                        return True
+                return False
             for nid in frontier:
                 l, lev, pre, _, a0, a1, b0, b1 = nodes[nid]
-                if max(a1 - a0, b1 - b0) <= leaf_cap or lev >= max_level:
+                if lev >= max_level:
+                    continue
+                if max(a1 - a0, b1 - b0) <= leaf_cap and not cross_adjacent(nid):
                     continue
                 shift = np.uint64(3 * (NBITS - lev - 1))
                 sc = (sk[a0:a1] >> shift) & np.uint64(7)
@@ -338,6 +367,25 @@ class Ops:
     def l2p(self, beta, pts, c):
         return self.monomials(pts - c[None, :]) @ beta
 
+    def cross_maps(self):
+        """Index (into the order-2p list) and coefficient of the cross-layer M2L:
+        gx[k,k'] = idx(k1+k1', k2+k2', k3), cx[k,k'] = (-1)^{k1'+k2'} C(k1+k1',k1) C(k2+k2',k2),
+        k3p[k'] = k3'."""
+        if not hasattr(self, 'gx'):
+            im2 = index_map(2 * self.p)
+            mi = self.mi
+            n = self.np_
+            self.gx = np.zeros((n, n), dtype=np.int64)
+            self.cx = np.zeros((n, n))
+            for a in range(n):
+                for b in range(n):
+                    g = (int(mi[a][0] + mi[b][0]), int(mi[a][1] + mi[b][1]), int(mi[a][2]))
+                    self.gx[a, b] = im2[g]
+                    self.cx[a, b] = ((-1.0) ** (mi[b][0] + mi[b][1]) *
+                                     math.comb(g[0], int(mi[a][0])) * math.comb(g[1], int(mi[a][1])))
+            self.k3p = mi[:, 2].copy()
+        return self.gx, self.cx, self.k3p
+
     def m2l_matrix(self, A, B):
         """M2L matrix from the combined derivative tables (see module docstring):
         H[k,k'] = C(k+k',k) (-1)^{k1'+k2'} (A_{k+k'} + (-1)^{k3'} B_{k+k'})."""
@@ -347,9 +395,15 @@ class Ops:
 class TEFMM:
     """Algorithm 1 + the component loop, for every (target layer, source layer)."""
 
-    def __init__(self, med, images, p, leaf_cap, max_level=NBITS, cube=None):
+    def __init__(self, med, images, p, leaf_cap, max_level=NBITS, cube=None, zext=None,
+                 cross_images=None, n_images=None):
         self.med = med
         self.images = images
+        self.zext = zext if zext is not None else (images.zext if images is not None else None)
+        # cross-layer images: dict (lt, ls, direction, level, izs, k3p) -> (A, Z);
+        # missing entries are fitted with oracle.cross.fit_cross
+        self.cross_images = {} if cross_images is None else cross_images
+        self.n_images = n_images if n_images is not None else 8
         self.p = p
         self.leaf_cap = leaf_cap
         self.max_level = max_level
@@ -365,8 +419,8 @@ class TEFMM:
             for ls in range(self.med.n_layers):
                 V, P = build_lists(self.tr, lt, ls)
                 if V or P:
-                    if lt != ls:
-                        raise NotImplementedError("cross-layer components")
+                    if lt != ls and P:
+                        raise NotImplementedError("cross-layer near-field pairs")
                     self.lists[(lt, ls)] = (V, P)
         return self
 
@@ -448,6 +502,9 @@ class TEFMM:
                     need.add(a)
                     a = tr.parent[a]
         for (lt, ls), (V, _) in self.lists.items():
+            if lt != ls:
+                self._cross_m2l(lt, ls, V, alpha, beta, need)
+                continue
             # group V pairs by level
             pairs = [(t, s) for t, lst in V.items() for s in lst if need is None or t in need]
             if not pairs:
@@ -481,6 +538,55 @@ class TEFMM:
                 continue
             beta[n] += ops.l2l(beta[par], tr.center(n) - tr.center(par))
         return beta
+
+    def cross_image(self, lt, ls, direction, lev, izs, k3p):
+        key = (lt, ls, direction, lev, izs, k3p)
+        if key not in self.cross_images:
+            h = self.tr.side / float(1 << lev)
+            zc = self.tr.lo[2] + (izs + 0.5) * h
+            wmin = xl.W_min(self.med, lt, direction, self.zext)
+            A, Z, _ = xl.fit_cross(self.med, lt, ls, direction, zc, k3p, wmin, self.n_images)
+            self.cross_images[key] = (A, Z)
+        return self.cross_images[key]
+
+    def _cross_tables(self, lt, ls, lev, key):
+        """T^{(k3')} of one cross key (dix, diy, izt, izs), shape (p+1, n_{2p})."""
+        tr, p = self.tr, self.p
+        dix, diy, izt, izs = key
+        h = tr.side / float(1 << lev)
+        X0, Y0 = dix * h, diy * h
+        zt = tr.lo[2] + (izt + 0.5) * h
+        mi2 = multi_indices(2 * p)
+        odd3 = (-1.0) ** mi2[:, 2]
+        T = np.zeros((p + 1, len(mi2)), dtype=complex)
+        k = self.med.k[lt]
+        for direction in xl.directions(self.med, lt):
+            wmin = xl.W_min(self.med, lt, direction, self.zext)
+            W0 = float(xl.W_of(self.med, lt, direction, zt))
+            sgn = 1.0 if direction == 'up' else odd3
+            for k3p in range(p + 1):
+                A, Z = self.cross_image(lt, ls, direction, lev, izs, k3p)
+                if len(A) == 0:
+                    continue
+                tab = taylor_h0(np.full(len(A), X0), np.full(len(A), Y0), W0 - wmin - np.asarray(Z), k, 2 * p)
+                T[k3p] += sgn * (np.asarray(A)[:, None] * tab).sum(0)
+        return T
+
+    def _cross_m2l(self, lt, ls, V, alpha, beta, need):
+        tr, ops = self.tr, self.ops
+        gx, cx, k3p = ops.cross_maps()
+        pairs = [(t, s) for t, lst in V.items() for s in lst if need is None or t in need]
+        groups = {}
+        for t, s in pairs:
+            key = (int(tr.level[t]), int(tr.ix[t] - tr.ix[s]), int(tr.iy[t] - tr.iy[s]),
+                   int(tr.iz[t]), int(tr.iz[s]))
+            groups.setdefault(key, []).append((t, s))
+        for (lev, dix, diy, izt, izs), lst in groups.items():
+            T = self._cross_tables(lt, ls, lev, (dix, diy, izt, izs))
+            H = cx * T[k3p[None, :], gx]
+            t = np.array([a for a, _ in lst])
+            s_ = np.array([b for _, b in lst])
+            np.add.at(beta, t, alpha[s_] @ H.T)
 
     # -- near field ----------------------------------------------------------
     def _kernel_same_layer(self, l, tpts, spts):
