@@ -64,21 +64,25 @@ def _poles(V, m):
     return np.linalg.eigvals(V2.conj().T @ np.linalg.pinv(V1.conj().T))
 
 
-def gpof(y, m_max, rel_tol=1e-12, decaying=False, keep=None, accept=None):
+def gpof(y, m_max, rel_tol=1e-12, decaying=False, keep=None, accept=None, score=None):
     """Generalized pencil of function: y_n ~= sum_j b_j z_j^n.
 
-    Returns (z, b).  Model order: singular values of the Hankel data matrix
-    above max(rel_tol * sigma_0, ABS_TOL * N) (the sampled functions are O(1),
-    so anything below the absolute floor is rounding noise), at most m_max.
-    With ``decaying`` only poles with |z| < 1 are kept (images that decay
-    along the first-level path); ``keep(z)`` (a boolean mask) drops further
-    poles before the amplitudes are fitted.  ``accept(z, b)`` may reject a
-    model order, in which case the next smaller order is tried.
+    Returns (z, b).  Largest model order: the number of singular values of the
+    Hankel data matrix above max(rel_tol * sigma_0, ABS_TOL * N) (the sampled
+    functions are O(1), so anything below the absolute floor is rounding
+    noise), at most m_max.  With ``decaying`` only poles with |z| < 1 are kept
+    (images that decay along the first-level path); ``keep(z)`` (a boolean
+    mask) drops further poles before the amplitudes are fitted.  ``accept(z,
+    b)`` may reject a model order.  Without ``score`` the largest accepted
+    order is returned; with it, every order from the largest down to 1 is
+    tried and the accepted one with the smallest ``score(z, b)`` wins (ties:
+    the larger order).
     """
     y = np.asarray(y, dtype=complex)
     N = y.size
     S, V = _hankel_svd(y)
     m = int(min(m_max, np.count_nonzero(S > max(rel_tol * S[0], ABS_TOL * N))))
+    best, best_s = None, np.inf
     while m > 0:
         z = _poles(V, m)
         if decaying:
@@ -89,8 +93,14 @@ def gpof(y, m_max, rel_tol=1e-12, decaying=False, keep=None, accept=None):
             vand = z[None, :] ** np.arange(N)[:, None]
             b, *_ = np.linalg.lstsq(vand, y, rcond=None)
             if accept is None or accept(z, b):
-                return z, b
+                if score is None:
+                    return z, b
+                sc = score(z, b)
+                if sc < best_s:
+                    best, best_s = (z, b), sc
         m -= 1
+    if best is not None:
+        return best
     return np.zeros(0, complex), np.zeros(0, complex)
 
 
@@ -115,8 +125,11 @@ def fit_two_level(F, k, T0, T1=10.0, n=101, n_images=8, m1=None, rel_tol=1e-12):
     # image into h0 at the complex distance W - W_min - Z needs Re(W - W_min - Z)
     # > 0 for every W >= W_min.  A model order is accepted only if no image term
     # exceeds CANCEL times the sampled data on either path (no catastrophic
-    # cancellation between images).  Both are readings; the paper does not
-    # discuss GPOF's model order.
+    # cancellation between images), and among the accepted orders the one with
+    # the smallest sample residual is taken (level 1: on C_ap1; level 2: of all
+    # images on both paths), since an ill-conditioned pencil at a high order
+    # can give a poor fit.  These are readings; the paper does not discuss
+    # GPOF's model order.
     scale = max(np.max(np.abs(y1)), np.max(np.abs(y2)), 1e-300)
 
     def small_terms(A, Z):
@@ -128,16 +141,25 @@ def fit_two_level(F, k, T0, T1=10.0, n=101, n_images=8, m1=None, rel_tol=1e-12):
     # level 1: e^{-i kz Z} = e^{k T0 Z} (e^{k dt1 Z})^n
     c1 = k * dt1
     conv1 = lambda z, b: (np.log(z) / c1, b * np.exp(-k * T0 * np.log(z) / c1))
+    def resid1(z, b):
+        Z, A = conv1(z, b)
+        return float(np.max(np.abs(np.exp(-1j * kz1[:, None] * Z[None, :]) @ A - y1)))
     z1, b1 = gpof(y1, m1, rel_tol, decaying=True,
                   keep=lambda z: (np.log(z) / c1).real < 0,
-                  accept=lambda z, b: small_terms(*conv1(z, b)[::-1]))
+                  accept=lambda z, b: small_terms(*conv1(z, b)[::-1]), score=resid1)
     Z1, A1 = conv1(z1, b1) if z1.size else (np.zeros(0, complex), np.zeros(0, complex))
     # level 2 on the residual: e^{-i kz Z} = e^{-i k Z} (e^{-i k (i - 1/T0) dt2 Z})^n
     res2 = y2 - (np.exp(-1j * kz2[:, None] * Z1[None, :]) @ A1 if A1.size else 0.0)
     c = -1j * k * (1j - 1.0 / T0) * dt2
     conv2 = lambda z, b: (np.log(z) / c, b * np.exp(1j * k * np.log(z) / c))
+    def resid_all(z, b):
+        Z, A = conv2(z, b)
+        Z, A = np.concatenate([Z1, Z]), np.concatenate([A1, A])
+        r1 = np.max(np.abs(np.exp(-1j * kz1[:, None] * Z[None, :]) @ A - y1))
+        r2 = np.max(np.abs(np.exp(-1j * kz2[:, None] * Z[None, :]) @ A - y2))
+        return float(max(r1, r2))
     z2, b2 = gpof(res2, n_images - A1.size, rel_tol, keep=lambda z: (np.log(z) / c).real < 0,
-                  accept=lambda z, b: small_terms(*conv2(z, b)[::-1]))
+                  accept=lambda z, b: small_terms(*conv2(z, b)[::-1]), score=resid_all)
     Z2, A2 = conv2(z2, b2) if z2.size else (np.zeros(0, complex), np.zeros(0, complex))
     A = np.concatenate([A1, A2])
     Z = np.concatenate([Z1, Z2])

@@ -70,6 +70,25 @@ def three_layer_slabs(n, p, leaf_cap, seed=0, n_images=8, k=(2.0, 3.0, 4.0 + 0.0
                     THREE_LAYER_ZEXT, src, q, p, leaf_cap, n_images)
 
 
+CROSS_D = [0.0, -1.4]
+CROSS_K = [2.0, 3.0, 4.0 + 0.01j]
+CROSS_ZEXT = [(0.5, 0.9), (-1.0, -0.4), (-2.3, -1.9)]
+
+
+def cross_layer_slabs(n_per_layer, p, leaf_cap, seed=0, n_images=16, k=None, name=None):
+    """Three layers (interfaces 0, -1.4; k = 2, 3, 4 + 0.01i unless given),
+    n_per_layer uniform points in each slab [-0.5,0.5]^2 x {[0.5,0.9],
+    [-1.0,-0.4], [-2.3,-1.9]}, top layer first.  Small enough for the oracle's
+    cross-layer direct sum (one DCIM fit per source point)."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.uniform([-0.5, -0.5, a], [0.5, 0.5, b], size=(n_per_layer, 3)) for a, b in CROSS_ZEXT]
+    src = np.concatenate(parts, 0)
+    q = _charges(rng, len(src))
+    kk = list(CROSS_K if k is None else k)
+    return Workload(name or f"cross_layer_slabs_n{3 * n_per_layer}_p{p}", CROSS_D, kk, CROSS_ZEXT,
+                    src, q, p, leaf_cap, n_images)
+
+
 def cfg_small():
     """2000 points in the middle layer, p = 6, leaf cap 60, 8 images per term."""
     return middle_layer_uniform(2000, 6, 60, seed=0, n_images=8,

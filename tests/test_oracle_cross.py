@@ -1,0 +1,185 @@
+"""Pins of the oracle's cross-layer components (Sec. 3.2, target layer l differs
+from source layer l').
+
+What fixes them independently of the oracle's own formulas:
+
+* homogeneous medium (every k_l equal): the transmitted field of a source in
+  another layer is the free-space field, so u_{l l'} = e^{ikR}/(ikR) exactly
+  (closed form; checked on the Sommerfeld quadrature, on the per-point DCIM
+  sum and on the whole TE-FMM);
+* reciprocity of the transmission problem: with the k-weighted flux condition
+  the weak form sum_l k_l int (grad u . grad v - k_l^2 u v) is symmetric, which
+  gives k_l' G(r'; r) = k_l G(r; r'); the potentials here omit i k_l / 4pi of
+  the target layer, hence  k_l^2 u_{l l'}(r; r') = k_l'^2 u_{l' l}(r'; r);
+* the DCIM fits of d^{k3'}_{z'} u / k3'! (every k3') against the Sommerfeld
+  quadrature of the same derivative;
+* brute force: the TE-FMM with all nine components against the direct sum
+  (same-layer images + per-source-point cross-layer fits), with an error that
+  falls as p rises; a planted sign error in the down-going cross-layer tables
+  is detected;
+* the cross-layer split rule: no cross-layer pair is left to the near field,
+  and the lists still cover every (target, source) pair exactly once.
+"""
+import numpy as np
+import pytest
+
+from oracle.medium import Medium
+from oracle.dcim import ImageTable
+from oracle.cross import CrossDirect, fit_cross, image_sum, W_min
+from oracle.direct import direct_sum
+from oracle.sommerfeld import reaction_derivative
+from oracle.tefmm import TEFMM, Trees, build_lists
+from paper_1902_05875_gb300 import workloads as W
+
+R_A = np.r_[0.3, -0.2, 0.7]      # layer 0
+R_B = np.r_[-0.1, 0.4, -0.7]     # layer 1
+R_C = np.r_[0.2, 0.1, -2.0]      # layer 2
+
+
+def test_quadrature_homogeneous_cross_layer_is_free_space():
+    med = Medium(W.CROSS_D, [3.0, 3.0, 3.0])
+    for (a, la), (b, lb) in [((R_A, 0), (R_B, 1)), ((R_A, 0), (R_C, 2)), ((R_C, 2), (R_B, 1))]:
+        u = reaction_derivative(med, la, lb, a, b)
+        R = np.linalg.norm(a - b)
+        ref = np.exp(3j * R) / (3j * R)
+        assert abs(u - ref) <= 1e-12 * abs(ref), (la, lb, u, ref)
+
+
+def test_quadrature_reciprocity():
+    med = Medium(W.CROSS_D, W.CROSS_K)
+    k = med.k
+    for (a, la), (b, lb) in [((R_A, 0), (R_B, 1)), ((R_A, 0), (R_C, 2)), ((R_B, 1), (R_C, 2))]:
+        u1 = reaction_derivative(med, la, lb, a, b)
+        u2 = reaction_derivative(med, lb, la, b, a)
+        lhs, rhs = k[la] ** 2 * u1, k[lb] ** 2 * u2
+        assert abs(lhs - rhs) <= 1e-10 * abs(lhs), (la, lb, lhs, rhs)
+
+
+@pytest.mark.parametrize("l,lp,part,k3p", [(0, 1, 'up', 0), (0, 2, 'up', 0), (0, 2, 'up', 3),
+                                           (1, 0, 'down', 6), (2, 1, 'down', 3), (1, 2, 'up', 6),
+                                           (1, 0, 'up', 2), (2, 0, 'down', 5)])
+def test_cross_fit_matches_quadrature(l, lp, part, k3p):
+    med = Medium(W.CROSS_D, W.CROSS_K)
+    zext = W.CROSS_ZEXT
+    zc = float(np.mean(zext[lp]))
+    wmin = W_min(med, l, part, zext)
+    A, Z, _ = fit_cross(med, l, lp, part, zc, k3p, wmin, n_images=16)
+    r = np.r_[0.3, -0.2, np.mean(zext[l]) + 0.1]
+    rp = np.r_[-0.1, 0.4, zc]
+    ref = reaction_derivative(med, l, lp, r, rp, k3p=k3p, part=part)
+    got = image_sum(med, l, part, A, Z, wmin, *r, rp[0], rp[1])
+    assert abs(got - ref) <= 1e-6 * abs(ref), (got, ref)
+
+
+def test_cross_direct_homogeneous_is_free_space():
+    med = Medium(W.CROSS_D, [3.0, 3.0, 3.0])
+    src = np.array([R_B, R_C])
+    tgt = np.array([R_A, R_A + 0.05, R_C + np.r_[0.3, 0.0, 0.1]])
+    q = np.array([1.0 + 0.5j, -0.3 + 0.2j])
+    got = CrossDirect(med, W.CROSS_ZEXT, n_images=16).potential(src, q, tgt)
+    ref = np.zeros(len(tgt), complex)
+    lay_s, lay_t = med.layer_of(src[:, 2]), med.layer_of(tgt[:, 2])
+    for i in range(len(tgt)):
+        for j in range(len(src)):
+            if lay_s[j] != lay_t[i]:
+                R = np.linalg.norm(tgt[i] - src[j])
+                ref[i] += q[j] * np.exp(3j * R) / (3j * R)
+    assert np.max(np.abs(got - ref)) <= 1e-8 * np.max(np.abs(ref))
+
+
+@pytest.fixture(scope="module")
+def slabs():
+    w = W.cross_layer_slabs(120, 0, 5, seed=0)
+    med = Medium(w.interfaces, w.k)
+    img = ImageTable(med, w.zext, n_images=w.n_images)
+    ref = direct_sum(med, img, w.src, w.q, w.src) + \
+        CrossDirect(med, w.zext, n_images=w.n_images).potential(w.src, w.q, w.src)
+    return w, med, img, ref
+
+
+def test_cross_layer_fmm_error_falls_with_p(slabs):
+    w, med, img, ref = slabs
+    errs = []
+    for p in (2, 4, 6):
+        f = TEFMM(med, img, p, w.leaf_cap, n_images=w.n_images).setup(w.src, w.src)
+        assert any(a != b for (a, b) in f.lists), "workload has no cross-layer component"
+        phi = f.evaluate(w.q)
+        errs.append(np.linalg.norm(phi - ref) / np.linalg.norm(ref))
+    assert all(b < 0.2 * a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 2e-3, errs
+
+
+def test_cross_layer_fmm_detects_planted_sign_error(slabs, monkeypatch):
+    """Drop the (-1)^{g3} of the down-going cross-layer tables: the error grows."""
+    w, med, img, ref = slabs
+    import oracle.tefmm as T
+    good = TEFMM(med, img, 4, w.leaf_cap, n_images=w.n_images).setup(w.src, w.src).evaluate(w.q)
+    e_good = np.linalg.norm(good - ref) / np.linalg.norm(ref)
+    real_tables = T.TEFMM._cross_tables
+
+    def planted(self, lt, ls, lev, key):
+        tab = real_tables(self, lt, ls, lev, key)
+        # undo the (-1)^{g3} of the down-going part by recomputing it without the sign
+        import oracle.cross as xl
+        from oracle.derivs import taylor_h0, multi_indices
+        tr, p = self.tr, self.p
+        dix, diy, izt, izs = key
+        h = tr.side / float(1 << lev)
+        zt = tr.lo[2] + (izt + 0.5) * h
+        mi2 = multi_indices(2 * p)
+        odd3 = (-1.0) ** mi2[:, 2]
+        if 'down' in xl.directions(self.med, lt):
+            wmin = xl.W_min(self.med, lt, 'down', self.zext)
+            W0 = float(xl.W_of(self.med, lt, 'down', zt))
+            for k3p in range(p + 1):
+                A, Z = self.cross_image(lt, ls, 'down', lev, izs, k3p)
+                if len(A) == 0:
+                    continue
+                t = taylor_h0(np.full(len(A), dix * h), np.full(len(A), diy * h),
+                              W0 - wmin - np.asarray(Z), self.med.k[lt], 2 * p)
+                s = (np.asarray(A)[:, None] * t).sum(0)
+                tab[k3p] += s - odd3 * s
+        return tab
+    monkeypatch.setattr(T.TEFMM, "_cross_tables", planted)
+    bad = TEFMM(med, img, 4, w.leaf_cap, n_images=w.n_images).setup(w.src, w.src).evaluate(w.q)
+    e_bad = np.linalg.norm(bad - ref) / np.linalg.norm(ref)
+    assert e_bad > 20 * e_good, (e_bad, e_good)
+
+
+def test_homogeneous_multi_layer_fmm_is_free_space():
+    w = W.cross_layer_slabs(60, 0, 5, seed=2, k=[3.0, 3.0, 3.0])
+    med = Medium(w.interfaces, w.k)
+    img = ImageTable(med, w.zext, n_images=w.n_images)
+    pts = w.src
+    d = pts[:, None, :] - pts[None, :, :]
+    R = np.sqrt((d ** 2).sum(-1))
+    np.fill_diagonal(R, 1.0)
+    G = np.exp(3j * R) / (3j * R)
+    np.fill_diagonal(G, 0.0)
+    ref = G @ w.q
+    errs = []
+    for p in (3, 6):
+        phi = TEFMM(med, img, p, w.leaf_cap, n_images=w.n_images).setup(pts, pts).evaluate(w.q)
+        errs.append(np.linalg.norm(phi - ref) / np.linalg.norm(ref))
+    assert errs[1] < 0.1 * errs[0] and errs[1] < 1e-3, errs
+
+
+def test_cross_split_rule_lists_partition_pairs():
+    w = W.cross_layer_slabs(80, 0, 5, seed=1)
+    med = Medium(w.interfaces, w.k)
+    tr = Trees(med, w.src, w.src, w.leaf_cap)
+    ns = len(w.src)
+    cover = np.zeros((ns, ns), dtype=np.int64)
+    for lt in range(3):
+        for ls in range(3):
+            V, P = build_lists(tr, lt, ls)
+            if lt != ls:
+                assert not P, "cross-layer pair left to the near field"
+            for t, lst in V.items():
+                for s in lst:
+                    assert not tr.adjacent(t, s)
+                    cover[np.ix_(tr.tperm[tr.t0[t]:tr.t1[t]], tr.sperm[tr.s0[s]:tr.s1[s]])] += 1
+            for t, lst in P.items():
+                for s in lst:
+                    cover[np.ix_(tr.tperm[tr.t0[t]:tr.t1[t]], tr.sperm[tr.s0[s]:tr.s1[s]])] += 1
+    assert np.all(cover == 1), (cover.min(), cover.max())
