@@ -84,6 +84,11 @@ typedef struct {
     double ms_near;        /* L2P + P2P                                               */
     double fit_max_resid;  /* worst DCIM fit residual on the samples (relative)       */
     int64_t n_launches;    /* kernels of this library launched by this plan so far    */
+    int n_cross_tables;    /* last eval: cross-layer derivative tables (l != l')      */
+    int n_cross_fits;      /* cross-layer DCIM fits cached by the plan                */
+    int n_cross_fits_last; /* cross-layer fits computed by the last eval (cache misses) */
+    double ms_cross_fit;   /* host time of those fits                                 */
+    double fit_max_resid_cross; /* worst cross-layer fit residual (relative)          */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,
@@ -175,6 +180,23 @@ int tefmm_export_lists(tefmm_plan plan, int64_t *n_v, int64_t *n_near, int *v_pt
  * evaluation: host arrays [n_nodes * n_coeffs * 2] in graded multi-index order
  * (n = 0..p; k1 = n..0; k2 = n-k1..0; k3 = n-k1-k2).  NULL skips one. */
 int tefmm_export_expansions(tefmm_plan plan, double *alpha, double *beta);
+
+/* Cross-layer DCIM images held by the plan (Sec. 3.2: one fit of the
+ * k3'-th z'-derivative density per target layer l, source layer l', part
+ * (0 up-going, W = z - d_l; 1 down-going, W = d_{l-1} - z), octree level,
+ * source z-box index iz_s and k3' = 0..p; the source z-centre is
+ * lo_z + (iz_s + 1/2) side / 2^level of the last evaluation's root cube).
+ * Fitted on demand by tefmm_eval and cached until the root cube's z-origin
+ * or side changes.
+ *   n_fits (out)        number of cached fits; with the other pointers all
+ *                       NULL only this is returned;
+ *   keys (out)          host int[6*n_fits]: (l, l', part, level, iz_s, k3');
+ *   counts (out)        host int[n_fits]: images of each fit (<= 32);
+ *   A, Z (out)          host double[2*32*n_fits]: image j of fit i at
+ *                       [2*(32*i + j)] (real, imaginary).
+ * Any of keys/counts/A/Z may be NULL.  Errors: INVALID_ARG. */
+int tefmm_plan_cross_images(tefmm_plan plan, int *n_fits, int *keys, int *counts, double *A,
+                            double *Z);
 
 /* ---- fit without device allocation -------------------------------------
  * The paper has no counterpart to this call; it is a convenience of this

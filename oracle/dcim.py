@@ -46,7 +46,7 @@ def default_T0(med: Medium, l):
 ABS_TOL = 1e-14
 
 
-CANCEL = 1e6
+CANCEL = 1e4     # largest image term on the sampled paths / largest sample
 
 
 def _hankel_svd(y):
@@ -124,8 +124,10 @@ def fit_two_level(F, k, T0, T1=10.0, n=101, n_images=8, m1=None, rel_tol=1e-12):
     # Only images with Re Z < 0 are kept: the Sommerfeld identity that turns an
     # image into h0 at the complex distance W - W_min - Z needs Re(W - W_min - Z)
     # > 0 for every W >= W_min.  A model order is accepted only if no image term
-    # exceeds CANCEL times the sampled data on either path (no catastrophic
-    # cancellation between images), and among the accepted orders the one with
+    # exceeds CANCEL times the sampled data on either path: the image sums then
+    # lose at most four digits to cancellation, so two FP64 evaluations of the
+    # same images agree to ~1e-12 (with 1e6 they differed by 1e-10); among the
+    # accepted orders the one with
     # the smallest sample residual is taken (level 1: on C_ap1; level 2: of all
     # images on both paths), since an ill-conditioned pencil at a high order
     # can give a poor fit.  These are readings; the paper does not discuss

@@ -48,6 +48,7 @@ def build(force=False, verbose=False, extra=()):
         return LIB
     os.makedirs(OBJ_DIR, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+             "-Xcompiler", "-ffp-contract=off",
                     "-I", os.path.join(ROOT, "include"), "-I", CSRC] + list(extra)
     objs = []
 

@@ -57,13 +57,16 @@ extern "C" int tefmm_eval(tefmm_plan P, int64_t ns, const double *sx, const doub
     TRY(lists_build(P, st));
     TRY(check_flags(P, st));
     TRY(m2l_prepare(P, st));
+    TRY(cross_prepare(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[1], st));
     TRY(upward_pass(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[2], st));
     TRY(m2l_tables(P, st));
+    TRY(cross_tables(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[3], st));
     if (P->opt.precision == TEFMM_MIXED) TRY(m2l_apply_tc(P, st));
     else TRY(m2l_apply(P, st));
+    TRY(cross_apply(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[4], st));
     TRY(downward_pass(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[5], st));
@@ -117,6 +120,11 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
     o->n_images_total = (int)P->A.size();
     o->fit_max_resid = P->fit_max_resid;
     o->n_launches = P->launches;
+    o->n_cross_tables = P->n_xtables;
+    o->n_cross_fits = (int)P->xcache.size();
+    o->n_cross_fits_last = P->n_xfits_last;
+    o->ms_cross_fit = P->ms_xfit;
+    o->fit_max_resid_cross = P->fit_max_resid_cross;
     if (P->n_nodes > 0 && cudaEventQuery(P->ev[6]) == cudaSuccess) {
         o->ms_tree = elapsed(P->ev[0], P->ev[1]);
         o->ms_upward = elapsed(P->ev[1], P->ev[2]);

@@ -1,0 +1,386 @@
+// Cross-layer reaction components (Sec. 3.2): target layer l != source layer l'.
+//
+// The component's z'-dependence cannot be folded into an image distance, so
+// the paper expands it in z' about the source box centre z_c: for each source
+// z-centre and each k3' = 0..p the density's k3'-th z'-derivative (divided by
+// k3'!) is fitted by the two-level DCIM in the target layer's k_lz,
+//   d^{k3'}_{z'} u / k3'! ~= sum_j A_j h0(k_l sqrt(rho^2 + (W - W_min - Z_j)^2)),
+// with W = z - d_l for the up-going part (present for l < L) and
+// W = d_{l-1} - z for the down-going part (present for l > 0).  The M2L of a cross pair is then
+//   beta_k += sum_k' alpha_k' (-1)^{k1'+k2'} C(k1+k1',k1) C(k2+k2',k2)
+//             sz^{k3} T^{(k3')}_{(k1+k1', k2+k2', k3)},
+//   T^{(k3')}_g = sum_dir sum_j A_j D^g h0(k_l R_j) / g!   at (dx h, dy h, W(z_t) - W_min - Z_j),
+// sz = +1 (up) / -1 (down, folded into the table as (-1)^{g3}).
+// One table per key (level, l, l', dx, dy, iz_t, iz_s) holds T^{(k3')} for all
+// k3' (orders 2p - k3'), packed slice after slice.
+//
+// The fits depend only on the geometry of the root cube (through z_c), so they
+// are cached in the plan and refitted only when the cube's z-origin or side
+// changes (the paper precomputes them once, 2^H (p+1) per component).
+#include <chrono>
+#include <set>
+
+#include "ops_common.cuh"
+
+namespace {
+
+struct XGeom {
+    double d[TEFMM_MAX_LAYERS];
+    double wmin[2 * TEFMM_MAX_LAYERS];   // [layer][dir]
+    cplx k[TEFMM_MAX_LAYERS];
+};
+
+__host__ __device__ inline int slice_off(int p, int k3p) {
+    int o = 0;
+    for (int j = 0; j < k3p; ++j) o += ncoef(2 * p - j);
+    return o;
+}
+
+// first cross-layer table and first cross-layer chunk (keys are sorted, kind 2 last)
+__global__ void k_first_cross(int ntab, const uint64_t *__restrict__ tkey, int64_t nch,
+                              const int *__restrict__ chunk_table, int *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < ntab) {
+        bool x = (tkey[i] >> 62) == 2, xp = i > 0 && (tkey[i - 1] >> 62) == 2;
+        if (x && !xp) out[0] = (int)i;
+    }
+    if (i < nch) {
+        bool x = (tkey[chunk_table[i]] >> 62) == 2;
+        bool xp = i > 0 && (tkey[chunk_table[i - 1]] >> 62) == 2;
+        if (x && !xp) out[1] = (int)i;
+    }
+}
+
+// T^{(k3')} slice of one cross table: grid (tables, p + 1)
+__global__ void k_xtables(int nx, const uint64_t *__restrict__ keys, Cube cb, int p,
+                          const int *__restrict__ mi_g, XGeom geo, const int2 *__restrict__ xrange,
+                          const cplx *__restrict__ xA, const cplx *__restrict__ xZ, int NX,
+                          cplx *__restrict__ xt) {
+    int tb = blockIdx.x, k3p = blockIdx.y;
+    if (tb >= nx || k3p > p) return;
+    const int P2 = 2 * p - k3p, n2 = ncoef(P2), nfull = ncoef(2 * p);
+    extern __shared__ double sm[];
+    cplx *a = (cplx *)sm;
+    cplx *b = a + nfull;
+    cplx *acc = b + nfull;
+    int *mi = (int *)(acc + nfull);
+    for (int g = threadIdx.x; g < 3 * n2; g += blockDim.x) mi[g] = mi_g[g];
+    for (int g = threadIdx.x; g < n2; g += blockDim.x) acc[g] = mkc(0, 0);
+    __syncthreads();
+    const XKey x = xkey_decode(keys[tb]);
+    const double h = box_h(cb.side, x.level);
+    const double X = (double)x.dx * h, Y = (double)x.dy * h;
+    const double zt = centre(cb.lo[2], x.izt, h);
+    const cplx k = geo.k[x.lt];
+    for (int dir = 0; dir < 2; ++dir) {
+        int2 r = xrange[((int64_t)tb * 2 + dir) * (p + 1) + k3p];
+        if (r.y == 0) continue;
+        double W0 = dir == 0 ? zt - geo.d[x.lt] : geo.d[x.lt - 1] - zt;
+        double Wr = W0 - geo.wmin[2 * x.lt + dir];
+        for (int j = r.x; j < r.x + r.y; ++j) {
+            cplx Wj = mkc(Wr - xZ[j].x, -xZ[j].y);
+            recur_accumulate(P2, n2, mi, k, X, Y, Wj, xA[j], dir == 1, a, b, acc);
+        }
+    }
+    cplx *dst = xt + (int64_t)tb * NX + slice_off(p, k3p);
+    for (int g = threadIdx.x; g < n2; g += blockDim.x) dst[g] = acc[g];
+}
+
+// Cross-layer M2L, FP64: one CTA per chunk of pairs of one cross key, one
+// thread per output coefficient k; the k' sum walks the k3' slices.
+constexpr int CHX = 16;
+
+__global__ void k_m2l_x(int c0, int nch, const int *__restrict__ chunk_start,
+                        const int *__restrict__ chunk_table, const int *__restrict__ chunk_cnt,
+                        int first_table, const cplx *__restrict__ xt, int NX,
+                        const int *__restrict__ items, const int *__restrict__ pair_t,
+                        const int *__restrict__ v_src, int p, int np,
+                        const unsigned short *__restrict__ xg, const double *__restrict__ xcf,
+                        const int *__restrict__ kp_order, const int *__restrict__ kp_grp,
+                        const cplx *__restrict__ alpha, cplx *__restrict__ beta) {
+    int c = c0 + blockIdx.x;
+    if (blockIdx.x >= nch) return;
+    extern __shared__ double sm[];
+    cplx *tab = (cplx *)sm;                       // [ncoef(2p)]
+    cplx *al = tab + ncoef(2 * p);                // [CHX][np]
+    __shared__ int tgt[CHX];
+    const int tb = chunk_table[c] - first_table;
+    const int cnt = chunk_cnt[c], st = chunk_start[c];
+    const int k = threadIdx.x;
+    const cplx *T = xt + (int64_t)tb * NX;
+    for (int qb = 0; qb < cnt; qb += CHX) {
+        const int nq = min(CHX, cnt - qb);
+        __syncthreads();
+        for (int q = 0; q < nq; ++q) {
+            int e = items[st + qb + q] >> 1;
+            if (threadIdx.x == 0) tgt[q] = pair_t[e];
+            int s = v_src[e];
+            for (int kk = threadIdx.x; kk < np; kk += blockDim.x) al[q * np + kk] = alpha[(int64_t)s * np + kk];
+        }
+        cplx acc[CHX];
+#pragma unroll
+        for (int q = 0; q < CHX; ++q) acc[q] = mkc(0, 0);
+        int off = 0;
+        for (int k3p = 0; k3p <= p; ++k3p) {
+            const int n2 = ncoef(2 * p - k3p);
+            __syncthreads();
+            for (int g = threadIdx.x; g < n2; g += blockDim.x) tab[g] = T[off + g];
+            __syncthreads();
+            off += n2;
+            if (k >= np) continue;
+            for (int i = kp_grp[k3p]; i < kp_grp[k3p + 1]; ++i) {
+                const int kp = kp_order[i];
+                const double cf = xcf[(int64_t)kp * np + k];
+                cplx hv = tab[xg[(int64_t)kp * np + k]];
+                hv.x *= cf;
+                hv.y *= cf;
+#pragma unroll
+                for (int q = 0; q < CHX; ++q) {
+                    if (q < nq) {
+                        cplx a = al[q * np + kp];
+                        acc[q].x += hv.x * a.x - hv.y * a.y;
+                        acc[q].y += hv.x * a.y + hv.y * a.x;
+                    }
+                }
+            }
+        }
+        if (k < np) {
+#pragma unroll
+            for (int q = 0; q < CHX; ++q) {
+                if (q < nq) {
+                    double *dst = (double *)&beta[(int64_t)tgt[q] * np + k];
+                    atomicAdd(dst, acc[q].x);
+                    atomicAdd(dst + 1, acc[q].y);
+                }
+            }
+        }
+    }
+}
+
+XGeom geometry(const tefmm_plan_s *P) {
+    XGeom g{};
+    for (int l = 0; l < TEFMM_MAX_LAYERS; ++l) {
+        g.d[l] = l < P->nL - 1 ? P->d[l] : 0.0;
+        g.k[l] = l < P->nL ? P->k[l] : mkc(1, 0);
+        for (int dir = 0; dir < 2; ++dir) {
+            bool present = l < P->nL && (dir == 0 ? l < P->nL - 1 : l > 0);
+            g.wmin[2 * l + dir] = present ? cross_wmin(P, l, dir) : 0.0;
+        }
+    }
+    return g;
+}
+
+// cross-layer M2L maps: xg[k'][k] = index of (k1+k1', k2+k2', k3) within the
+// k3' slice, xcf[k'][k] = (-1)^{k1'+k2'} C(k1+k1',k1) C(k2+k2',k2); k' ordered by k3'
+int build_maps(tefmm_plan_s *P) {
+    const int p = P->p, np = P->np;
+    if (P->d_xG.p && P->d_xoff.p && P->d_xcf.cap >= (size_t)np * np * 8) return TEFMM_OK;
+    std::vector<int> mi(3 * np);
+    int t = 0;
+    for (int n = 0; n <= p; ++n)
+        for (int k1 = n; k1 >= 0; --k1)
+            for (int k2 = n - k1; k2 >= 0; --k2) {
+                mi[3 * t] = k1;
+                mi[3 * t + 1] = k2;
+                mi[3 * t + 2] = n - k1 - k2;
+                ++t;
+            }
+    auto comb = [](int n, int k) {
+        double r = 1.0;
+        for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+        return r;
+    };
+    std::vector<unsigned short> G((size_t)np * np);
+    std::vector<double> cf((size_t)np * np);
+    for (int kp = 0; kp < np; ++kp)
+        for (int k = 0; k < np; ++k) {
+            int g1 = mi[3 * k] + mi[3 * kp], g2 = mi[3 * k + 1] + mi[3 * kp + 1], g3 = mi[3 * k + 2];
+            G[(size_t)kp * np + k] = (unsigned short)midx(g1, g2, g3);
+            double s = ((mi[3 * kp] + mi[3 * kp + 1]) & 1) ? -1.0 : 1.0;
+            cf[(size_t)kp * np + k] = s * comb(g1, mi[3 * k]) * comb(g2, mi[3 * k + 1]);
+        }
+    std::vector<int> ord, grp(p + 2, 0);
+    for (int k3p = 0; k3p <= p; ++k3p) {
+        grp[k3p] = (int)ord.size();
+        for (int kp = 0; kp < np; ++kp)
+            if (mi[3 * kp + 2] == k3p) ord.push_back(kp);
+    }
+    grp[p + 1] = (int)ord.size();
+    std::vector<int> og(ord);
+    og.insert(og.end(), grp.begin(), grp.end());
+    TRY(dbuf_ensure(P->d_xG, G.size() * 2));
+    TRY(dbuf_ensure(P->d_xcf, cf.size() * 8));
+    TRY(dbuf_ensure(P->d_xoff, og.size() * 4));
+    CUDA_TRY(cudaMemcpy(P->d_xG.p, G.data(), G.size() * 2, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(P->d_xcf.p, cf.data(), cf.size() * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(P->d_xoff.p, og.data(), og.size() * 4, cudaMemcpyHostToDevice));
+    return TEFMM_OK;
+}
+
+}  // namespace
+
+double cross_wmin(const tefmm_plan_s *P, int lt, int dir) {
+    const double zlo = P->opt.zext[2 * lt], zhi = P->opt.zext[2 * lt + 1];
+    return dir == 0 ? zlo - P->d[lt] : P->d[lt - 1] - zhi;
+}
+
+int cross_prepare(tefmm_plan_s *P, cudaStream_t st) {
+    P->n_xtables = 0;
+    P->n_xfits_last = 0;
+    P->ms_xfit = 0;
+    if (P->nL < 2 || P->n_tables == 0) return TEFMM_OK;
+    int h[2] = {P->n_tables, (int)P->n_chunks};
+    TRY(dbuf_ensure(P->counters, 64));
+    int *dcnt = dp<int>(P->counters) + 4;
+    CUDA_TRY(cudaMemcpyAsync(dcnt, h, 8, cudaMemcpyHostToDevice, st));
+    int64_t n = std::max<int64_t>(P->n_tables, P->n_chunks);
+    k_first_cross<<<grid_for(n, 256), 256, 0, st>>>(P->n_tables, dp<uint64_t>(P->table_slot),
+                                                    P->n_chunks, dp<int>(P->chunk_key), dcnt);
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(h, dcnt, 8, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    P->x_first_table = h[0];
+    P->x_first_chunk = h[1];
+    const int nx = P->n_tables - h[0];
+    if (nx == 0) return TEFMM_OK;
+    P->n_xtables = nx;
+    std::vector<uint64_t> keys(nx);
+    CUDA_TRY(cudaMemcpy(keys.data(), dp<uint64_t>(P->table_slot) + h[0], (size_t)nx * 8,
+                        cudaMemcpyDeviceToHost));
+    // the fits depend on the root cube through the source z-centres
+    if (P->lo[2] != P->xgeo_lo || P->side != P->xgeo_side) {
+        P->xcache.clear();
+        P->xA.clear();
+        P->xZ.clear();
+        P->x_uploaded = 0;
+        P->fit_max_resid_cross = 0;
+        P->xgeo_lo = P->lo[2];
+        P->xgeo_side = P->side;
+    }
+    const int p = P->p;
+    std::vector<CrossFitKey> miss;
+    std::set<CrossFitKey> pending;
+    for (uint64_t key : keys) {
+        XKey x = xkey_decode(key);
+        for (int dir = 0; dir < 2; ++dir) {
+            if (dir == 0 ? x.lt >= P->nL - 1 : x.lt == 0) continue;
+            for (int k3p = 0; k3p <= p; ++k3p) {
+                CrossFitKey c{x.lt, x.ls, dir, x.level, x.izs, k3p};
+                if (P->xcache.count(c) || pending.count(c)) continue;
+                pending.insert(c);
+                miss.push_back(c);
+            }
+        }
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    const size_t BATCH = 4096;
+    for (size_t i = 0; i < miss.size(); i += BATCH) {
+        std::vector<CrossFitKey> part(miss.begin() + i, miss.begin() + std::min(miss.size(), i + BATCH));
+        TRY(fit_cross_jobs(P, part, st));
+    }
+    P->n_xfits_last = (int)miss.size();
+    P->ms_xfit = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (P->xA.size() != P->x_uploaded || !P->d_xA.p) {
+        size_t ni = P->xA.size();
+        TRY(dbuf_ensure(P->d_xA, (ni + 1) * sizeof(cplx)));
+        TRY(dbuf_ensure(P->d_xZ, (ni + 1) * sizeof(cplx)));
+        if (ni) {
+            CUDA_TRY(cudaMemcpy(P->d_xA.p, P->xA.data(), ni * sizeof(cplx), cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(P->d_xZ.p, P->xZ.data(), ni * sizeof(cplx), cudaMemcpyHostToDevice));
+        }
+        P->x_uploaded = ni;
+    }
+    std::vector<int2> rng((size_t)nx * 2 * (p + 1), make_int2(0, 0));
+    for (int tb = 0; tb < nx; ++tb) {
+        XKey x = xkey_decode(keys[tb]);
+        for (int dir = 0; dir < 2; ++dir) {
+            if (dir == 0 ? x.lt >= P->nL - 1 : x.lt == 0) continue;
+            for (int k3p = 0; k3p <= p; ++k3p) {
+                auto it = P->xcache.find(CrossFitKey{x.lt, x.ls, dir, x.level, x.izs, k3p});
+                if (it == P->xcache.end()) return TEFMM_ERR_FIT_FAILED;
+                rng[((size_t)tb * 2 + dir) * (p + 1) + k3p] = make_int2(it->second.first, it->second.count);
+            }
+        }
+    }
+    TRY(dbuf_ensure(P->d_xrange, rng.size() * sizeof(int2)));
+    CUDA_TRY(cudaMemcpy(P->d_xrange.p, rng.data(), rng.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    TRY(build_maps(P));
+    P->NX = slice_off(p, p + 1);
+    return TEFMM_OK;
+}
+
+int cross_tables(tefmm_plan_s *P, cudaStream_t st) {
+    const int nx = P->n_xtables;
+    if (nx == 0) return TEFMM_OK;
+    TRY(dbuf_ensure(P->xtables, (size_t)nx * P->NX * sizeof(cplx)));
+    const int nfull = P->np2;
+    size_t sm = 3 * (size_t)nfull * sizeof(cplx) + 3 * (size_t)nfull * sizeof(int);
+    CUDA_TRY(cudaFuncSetAttribute(k_xtables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid((unsigned)nx, (unsigned)(P->p + 1));
+    k_xtables<<<grid, 256, sm, st>>>(nx, dp<uint64_t>(P->table_slot) + P->x_first_table, cube_of(P),
+                                     P->p, dp<int>(P->d_mi), geometry(P), dp<int2>(P->d_xrange),
+                                     dp<cplx>(P->d_xA), dp<cplx>(P->d_xZ), P->NX, dp<cplx>(P->xtables));
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+int cross_apply(tefmm_plan_s *P, cudaStream_t st) {
+    const int nch = (int)(P->n_chunks - P->x_first_chunk);
+    if (P->n_xtables == 0 || nch <= 0) return TEFMM_OK;
+    const int np = P->np;
+    const int nthr = (np + 31) / 32 * 32;
+    size_t sm = (size_t)P->np2 * sizeof(cplx) + (size_t)CHX * np * sizeof(cplx);
+    CUDA_TRY(cudaFuncSetAttribute(k_m2l_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int *og = dp<int>(P->d_xoff);
+    k_m2l_x<<<nch, nthr, sm, st>>>((int)P->x_first_chunk, nch, dp<int>(P->chunk_start),
+                                   dp<int>(P->chunk_key), dp<int>(P->chunk_cnt), P->x_first_table,
+                                   dp<cplx>(P->xtables), P->NX, dp<int>(P->pair_idx_sorted),
+                                   dp<int>(P->pair_t), dp<int>(P->v_src), P->p, np,
+                                   dp<unsigned short>(P->d_xG), dp<double>(P->d_xcf), og, og + np,
+                                   dp<cplx>(P->alpha), dp<cplx>(P->beta));
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+void cross_release(tefmm_plan_s *P) {
+    DBuf *b[] = {&P->d_xA, &P->d_xZ, &P->d_xrange, &P->d_tslot, &P->xtables,
+                 &P->d_xG, &P->d_xcf, &P->d_xexp, &P->d_xoff, &P->tc_xcf};
+    for (DBuf *x : b) dbuf_free(*x);
+}
+
+extern "C" int tefmm_plan_cross_images(tefmm_plan P, int *n_fits, int *keys, int *counts, double *A,
+                                       double *Z) {
+    if (!P || !n_fits) return TEFMM_ERR_INVALID_ARG;
+    *n_fits = (int)P->xcache.size();
+    if (!keys && !counts && !A && !Z) return TEFMM_OK;
+    int i = 0;
+    for (const auto &e : P->xcache) {
+        const CrossFitKey &c = e.first;
+        const CrossFitVal &v = e.second;
+        if (keys) {
+            int *o = keys + 6 * i;
+            o[0] = c.lt;
+            o[1] = c.ls;
+            o[2] = c.dir;
+            o[3] = c.level;
+            o[4] = c.izs;
+            o[5] = c.k3p;
+        }
+        if (counts) counts[i] = v.count;
+        for (int j = 0; j < v.count; ++j) {
+            if (A) {
+                A[2 * (TEFMM_MAX_IMG * i + j)] = P->xA[v.first + j].x;
+                A[2 * (TEFMM_MAX_IMG * i + j) + 1] = P->xA[v.first + j].y;
+            }
+            if (Z) {
+                Z[2 * (TEFMM_MAX_IMG * i + j)] = P->xZ[v.first + j].x;
+                Z[2 * (TEFMM_MAX_IMG * i + j) + 1] = P->xZ[v.first + j].y;
+            }
+        }
+        ++i;
+    }
+    return TEFMM_OK;
+}

@@ -25,7 +25,7 @@ constexpr int MAXM = TEFMM_MAX_IMG;  // images per fit (both levels)
 constexpr int MAXLS = 24;            // images per level
 constexpr double REL_TOL = 1e-12;
 constexpr double ABS_TOL = 1e-14;
-constexpr double CANCEL = 1e6;     // largest image term / largest sample
+constexpr double CANCEL = 1e4;     // largest image term / largest sample
 
 struct FitJob {
     int layer, tag, nL;
@@ -513,19 +513,47 @@ __host__ __device__ __forceinline__ cplx path2(cplx k, double T0, double dt2, in
     return cmul(k, mkc(1.0 - t / T0, t));                              // C_ap2
 }
 
-// no image term above CANCEL times the largest sample on either path
-__host__ __device__ bool small_terms(const cplx *A, const cplx *Z, int m, cplx k, double T0, double dt1,
-                            double dt2, int N, double scale) {
-    for (int j = 0; j < m; ++j)
-        for (int i = 0; i < N; ++i) {
-            cplx e1 = cmul(A[j], cexp_(cmul(mkc(0, -1), cmul(path1(k, T0, dt1, i), Z[j]))));
-            cplx e2 = cmul(A[j], cexp_(cmul(mkc(0, -1), cmul(path2(k, T0, dt2, i), Z[j]))));
-            if (!(cabs_(e1) <= CANCEL * scale) || !(cabs_(e2) <= CANCEL * scale)) return false;
-        }
-    return true;
+__device__ __forceinline__ double finite_or_inf(double v) { return v <= 1.7e308 ? v : INFINITY; }
+
+__device__ double block_max(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    for (int w = 0; w < nw; ++w) r = fmax(r, red[w]);
+    return r;
 }
 
-__global__ void k_fit(const FitJob *jobs, int njobs, cplx *outA, cplx *outZ, int *outN,
+// Candidate images CA/CZ (nc) on top of fixed images FA/FZ (nf), every thread
+// of the block: the largest candidate term on both paths (tmax) and the
+// largest residual against the samples (rmax; path 1 only unless both_paths).
+// A NaN or infinity anywhere gives +inf.
+__device__ void cand_eval(const cplx *FA, const cplx *FZ, int nf, const cplx *CA, const cplx *CZ, int nc,
+                          cplx k, double T0, double dt1, double dt2, int N, const cplx *y1,
+                          const cplx *y2, bool both_paths, double *red, double &tmax, double &rmax) {
+    double tm = 0.0, rm = 0.0;
+    for (int n = threadIdx.x; n < 2 * N; n += blockDim.x) {
+        const int lev = n / N, i = n % N;
+        const cplx kz = lev == 0 ? path1(k, T0, dt1, i) : path2(k, T0, dt2, i);
+        const cplx mikz = cmul(mkc(0, -1), kz);
+        cplx ap = mkc(0, 0);
+        for (int j = 0; j < nc; ++j) {
+            cplx e = cmul(CA[j], cexp_(cmul(mikz, CZ[j])));
+            tm = fmax(tm, finite_or_inf(cabs_(e)));
+            ap = cadd(ap, e);
+        }
+        if (lev == 0 || both_paths) {
+            for (int j = 0; j < nf; ++j) ap = cadd(ap, cmul(FA[j], cexp_(cmul(mikz, FZ[j]))));
+            rm = fmax(rm, finite_or_inf(cabs_(csub(ap, lev == 0 ? y1[i] : y2[i]))));
+        }
+    }
+    tmax = block_max(tm, red);
+    rmax = block_max(rm, red);
+}
+
+__global__ void __launch_bounds__(512) k_fit(const FitJob *jobs, int njobs, cplx *outA, cplx *outZ, int *outN,
                       double *outRes) {
     int jb = blockIdx.x;
     if (jb >= njobs) return;
@@ -555,33 +583,44 @@ __global__ void k_fit(const FitJob *jobs, int njobs, cplx *outA, cplx *outZ, int
         for (int i = 0; i < N; ++i) sc = fmax(sc, fmax(cabs_(y1[i]), cabs_(y2[i])));
         scale = sc;
     }
-    // level 1 (a model order is accepted only if its image terms stay below
-    // CANCEL times the samples on both paths)
+    // level 1: among the model orders whose image terms stay below CANCEL
+    // times the samples on both paths, the one with the smallest residual on
+    // C_ap1 (ties: the larger order)
+    __shared__ cplx cA[MAXLS], cZ[MAXLS];
+    __shared__ int cw, cap;
+    __shared__ double bres, red[32];
     for (int i = threadIdx.x; i < N; i += blockDim.x) S.res[i] = y1[i];
     __syncthreads();
     gpof_svd(S, N);
     if (threadIdx.x == 0) {
-        int cap = min(S.m, min(J.n_images / 2, MAXLS));
+        cap = min(S.m, min(J.n_images / 2, MAXLS));
         n1 = 0;
-        for (int m = cap; m >= 1; --m) {
-            int w = gpof_order(S, N, m, true, c1);
-            if (w == 0) continue;
-            cplx A[MAXLS], Z[MAXLS];
-            for (int j = 0; j < w; ++j) {
-                Z[j] = cdiv(clog_(S.zp[j]), c1);                                // z = e^{k dt1 Z}
-                A[j] = cmul(S.bb[j], cexp_(cscale(cmul(k, Z[j]), -T0)));       // A = b e^{-k T0 Z}
-            }
-            if (small_terms(A, Z, w, k, T0, dt1, dt2, N, scale)) {
-                for (int j = 0; j < w; ++j) {
-                    A1[j] = A[j];
-                    Z1[j] = Z[j];
-                }
-                n1 = w;
-                break;
-            }
-        }
+        bres = INFINITY;
     }
     __syncthreads();
+    for (int m = cap; m >= 1; --m) {
+        if (threadIdx.x == 0) {
+            cw = gpof_order(S, N, m, true, c1);
+            for (int j = 0; j < cw; ++j) {
+                cZ[j] = cdiv(clog_(S.zp[j]), c1);                               // z = e^{k dt1 Z}
+                cA[j] = cmul(S.bb[j], cexp_(cscale(cmul(k, cZ[j]), -T0)));      // A = b e^{-k T0 Z}
+            }
+        }
+        __syncthreads();
+        if (cw > 0) {
+            double tmax, rmax;
+            cand_eval(nullptr, nullptr, 0, cA, cZ, cw, k, T0, dt1, dt2, N, y1, y2, false, red, tmax, rmax);
+            if (threadIdx.x == 0 && tmax <= CANCEL * scale && rmax < bres) {
+                for (int j = 0; j < cw; ++j) {
+                    A1[j] = cA[j];
+                    Z1[j] = cZ[j];
+                }
+                n1 = cw;
+                bres = rmax;
+            }
+        }
+        __syncthreads();
+    }
     // level 2 on the residual
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         cplx kz = path2(k, T0, dt2, i);
@@ -592,30 +631,49 @@ __global__ void k_fit(const FitJob *jobs, int njobs, cplx *outA, cplx *outZ, int
     }
     __syncthreads();
     gpof_svd(S, N);
+    // level 2: same rule, residual of all images on both paths
+    __shared__ cplx bA[MAXLS], bZ[MAXLS];
+    __shared__ int n2;
     if (threadIdx.x == 0) {
-        int cap = min(S.m, min(J.n_images - n1, MAXLS));
+        cap = min(S.m, min(J.n_images - n1, MAXLS));
+        n2 = 0;
+        bres = INFINITY;
+    }
+    __syncthreads();
+    for (int m = cap; m >= 1; --m) {
+        if (threadIdx.x == 0) {
+            cw = gpof_order(S, N, m, false, c2);
+            for (int j = 0; j < cw; ++j) {
+                cZ[j] = cdiv(clog_(S.zp[j]), c2);
+                cA[j] = cmul(S.bb[j], cexp_(cmul(mkc(0, 1), cmul(k, cZ[j]))));   // A = b e^{ikZ}
+            }
+        }
+        __syncthreads();
+        if (cw > 0) {
+            double tmax, rmax;
+            cand_eval(A1, Z1, n1, cA, cZ, cw, k, T0, dt1, dt2, N, y1, y2, true, red, tmax, rmax);
+            if (threadIdx.x == 0 && tmax <= CANCEL * scale && rmax < bres) {
+                for (int j = 0; j < cw; ++j) {
+                    bA[j] = cA[j];
+                    bZ[j] = cZ[j];
+                }
+                n2 = cw;
+                bres = rmax;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
         int tot = 0;
         for (int j = 0; j < n1; ++j) {
             outA[jb * MAXM + tot] = A1[j];
             outZ[jb * MAXM + tot] = Z1[j];
             ++tot;
         }
-        for (int m = cap; m >= 1; --m) {
-            int w = gpof_order(S, N, m, false, c2);
-            if (w == 0) continue;
-            cplx A[MAXLS], Z[MAXLS];
-            for (int j = 0; j < w; ++j) {
-                Z[j] = cdiv(clog_(S.zp[j]), c2);
-                A[j] = cmul(S.bb[j], cexp_(cmul(mkc(0, 1), cmul(k, Z[j]))));   // A = b e^{ikZ}
-            }
-            if (small_terms(A, Z, w, k, T0, dt1, dt2, N, scale)) {
-                for (int j = 0; j < w; ++j) {
-                    outA[jb * MAXM + tot] = A[j];
-                    outZ[jb * MAXM + tot] = Z[j];
-                    ++tot;
-                }
-                break;
-            }
+        for (int j = 0; j < n2; ++j) {
+            outA[jb * MAXM + tot] = bA[j];
+            outZ[jb * MAXM + tot] = bZ[j];
+            ++tot;
         }
         outN[jb] = tot;
         // residual on both paths, relative to the largest sample
@@ -883,6 +941,83 @@ extern "C" int tefmm_fit_images_noalloc(int n_layers, const double *interfaces, 
             Z[2 * (i * MAXM + j)] = hZ[jb * MAXM + j].x;
             Z[2 * (i * MAXM + j) + 1] = hZ[jb * MAXM + j].y;
         }
+    }
+    return TEFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cross-layer fits (Sec. 3.2: one DCIM fit per source z-centre and k3', for a
+// component whose source and target layers differ).  Runs the fit kernel on
+// the given jobs and appends the images to the plan's cross-layer pool.
+int fit_cross_jobs(tefmm_plan_s *P, const std::vector<CrossFitKey> &keys, cudaStream_t st) {
+    const int nj = (int)keys.size();
+    if (nj == 0) return TEFMM_OK;
+    if (P->nL > 8 || P->opt.n_samples > MAXN) return TEFMM_ERR_NOT_IMPLEMENTED;
+    double kmax = 0;
+    for (int l = 0; l < P->nL; ++l) kmax = fmax(kmax, P->k[l].x);
+    std::vector<FitJob> jobs(nj);
+    for (int i = 0; i < nj; ++i) {
+        const CrossFitKey &c = keys[i];
+        FitJob J{};
+        J.mode = 1;
+        J.layer = c.lt;
+        J.src_layer = c.ls;
+        J.dir = c.dir;
+        J.k3p = c.k3p;
+        J.nL = P->nL;
+        for (int m = 0; m < TEFMM_MAX_LAYERS; ++m) {
+            J.d[m] = m < P->nL - 1 ? P->d[m] : 0.0;
+            J.k[m] = m < P->nL ? P->k[m] : mkc(1, 0);
+        }
+        double h = P->side / (double)(1 << c.level);
+        J.zc = P->lo[2] + ((double)c.izs + 0.5) * h;
+        J.zmin = cross_wmin(P, c.lt, c.dir);
+        double kl = P->k[c.lt].x;
+        J.T0 = P->opt.T0 > 0 ? P->opt.T0 : sqrt(fmax(((kmax + 0.8) / kl) * ((kmax + 0.8) / kl) - 1.0, 1e-6));
+        J.T1 = P->opt.T1;
+        J.n = P->opt.n_samples;
+        J.n_images = P->opt.n_images;
+        jobs[i] = J;
+    }
+    FitJob *djobs = nullptr;
+    cplx *dA = nullptr, *dZ = nullptr;
+    int *dN = nullptr;
+    double *dR = nullptr;
+    CUDA_TRY(cudaMalloc(&djobs, nj * sizeof(FitJob)));
+    CUDA_TRY(cudaMalloc(&dA, (size_t)nj * MAXM * sizeof(cplx)));
+    CUDA_TRY(cudaMalloc(&dZ, (size_t)nj * MAXM * sizeof(cplx)));
+    CUDA_TRY(cudaMalloc(&dN, nj * sizeof(int)));
+    CUDA_TRY(cudaMalloc(&dR, nj * sizeof(double)));
+    CUDA_TRY(cudaMemcpyAsync(djobs, jobs.data(), nj * sizeof(FitJob), cudaMemcpyHostToDevice, st));
+    size_t sm = sizeof(GpofSmem);
+    CUDA_TRY(cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fit<<<nj, 512, sm, st>>>(djobs, nj, dA, dZ, dN, dR);
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    std::vector<cplx> hA((size_t)nj * MAXM), hZ((size_t)nj * MAXM);
+    std::vector<int> hN(nj);
+    std::vector<double> hR(nj);
+    CUDA_TRY(cudaMemcpyAsync(hA.data(), dA, hA.size() * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hZ.data(), dZ, hZ.size() * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hN.data(), dN, nj * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(hR.data(), dR, nj * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(djobs);
+    cudaFree(dA);
+    cudaFree(dZ);
+    cudaFree(dN);
+    cudaFree(dR);
+    for (int i = 0; i < nj; ++i) {
+        if (!(hR[i] == hR[i])) return TEFMM_ERR_FIT_FAILED;
+        CrossFitVal v;
+        v.first = (int)P->xA.size();
+        v.count = hN[i];
+        for (int j = 0; j < hN[i]; ++j) {
+            P->xA.push_back(hA[(size_t)i * MAXM + j]);
+            P->xZ.push_back(hZ[(size_t)i * MAXM + j]);
+        }
+        P->xcache[keys[i]] = v;
+        P->fit_max_resid_cross = fmax(P->fit_max_resid_cross, hR[i]);
     }
     return TEFMM_OK;
 }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <map>
 #include <vector>
 
 #include "tefmm.h"
@@ -103,6 +104,23 @@ struct DevTerm {           // POD copy for kernels
     int first, count, layer, tag;
 };
 
+// cross-layer fit: (target layer, source layer, direction 0 up / 1 down,
+// level, source z-index, k3') -> images in the plan's cross-layer pool
+struct CrossFitKey {
+    int lt, ls, dir, level, izs, k3p;
+    bool operator<(const CrossFitKey &o) const {
+        if (lt != o.lt) return lt < o.lt;
+        if (ls != o.ls) return ls < o.ls;
+        if (dir != o.dir) return dir < o.dir;
+        if (level != o.level) return level < o.level;
+        if (izs != o.izs) return izs < o.izs;
+        return k3p < o.k3p;
+    }
+};
+struct CrossFitVal {
+    int first, count;
+};
+
 // ---------------------------------------------------------------- plan
 struct tefmm_plan_s {
     int nL = 0;
@@ -134,7 +152,7 @@ struct tefmm_plan_s {
     DBuf item_node, item_flag, item_scan, cnt_s, cnt_t;
     DBuf sx, sy, sz, sq, tx, ty, tz, perm_s, perm_t;
     DBuf n_layer, n_level, n_ix, n_iy, n_iz, n_parent, n_cfirst, n_nchild, n_s0, n_s1, n_t0,
-        n_t1, n_i0, n_i1, n_split;
+        n_t1, n_i0, n_i1, n_split, n_key;
     DBuf bbox, flags, counters;
     int n_nodes = 0, n_levels = 0;
     std::vector<int> level_off;   // node range per level: [level_off[l], level_off[l+1])
@@ -155,6 +173,19 @@ struct tefmm_plan_s {
     int n_tables = 0;
     int64_t n_chunks = 0;
     int chunk_pairs = 16;     // pairs per M2L work chunk (FP64 SIMT: 16, tensor cores: 128)
+
+    // cross-layer components: fitted images (cached per root-cube geometry),
+    // per-table image ranges and tables
+    std::map<CrossFitKey, CrossFitVal> xcache;
+    std::vector<cplx> xA, xZ;
+    double xgeo_lo = 0.0, xgeo_side = -1.0;
+    double fit_max_resid_cross = 0.0;
+    DBuf d_xA, d_xZ, d_xrange, d_tslot, xtables, d_xG, d_xcf, d_xexp, d_xoff, tc_xcf;
+    int NX = 0, n_xtables = 0, n_xfits_last = 0;
+    int x_first_table = 0;        // cross-layer tables are [x_first_table, n_tables)
+    int64_t x_first_chunk = 0;    // cross-layer chunks are [x_first_chunk, n_chunks)
+    size_t x_uploaded = 0;        // images of the pool on the device
+    double ms_xfit = 0;           // host time of the cross-layer fits of the last eval
 
     // tensor-core M2L buffers (mixed form)
     DBuf tc_ah, tc_al, tc_bt, tc_cfA, tc_cfB;
@@ -217,3 +248,10 @@ int plan_upload_images(tefmm_plan_s *P);
 int plan_build_operator_tables(tefmm_plan_s *P);
 // fit.cu
 int plan_fit_images(tefmm_plan_s *P, cudaStream_t st);
+int fit_cross_jobs(tefmm_plan_s *P, const std::vector<CrossFitKey> &keys, cudaStream_t st);
+// cross.cu
+double cross_wmin(const tefmm_plan_s *P, int lt, int dir);
+int cross_prepare(tefmm_plan_s *P, cudaStream_t st);
+int cross_tables(tefmm_plan_s *P, cudaStream_t st);
+int cross_apply(tefmm_plan_s *P, cudaStream_t st);
+void cross_release(tefmm_plan_s *P);

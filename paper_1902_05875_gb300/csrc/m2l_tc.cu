@@ -314,7 +314,8 @@ int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st) {
     const int Ntot = Ncta * nsplit;
     TRY(dbuf_ensure(P->beta, (size_t)nn * np * sizeof(cplx)));
     CUDA_TRY(cudaMemsetAsync(P->beta.p, 0, (size_t)nn * np * sizeof(cplx), st));
-    if (P->n_chunks == 0) return TEFMM_OK;
+    const int nch = (int)P->x_first_chunk;    // same-layer chunks (cross-layer ones follow)
+    if (nch == 0) return TEFMM_OK;
     TRY(dbuf_ensure(P->tc_ah, (size_t)nn * Kpad * 4));
     TRY(dbuf_ensure(P->tc_al, (size_t)nn * Kpad * 4));
     TRY(dbuf_ensure(P->tc_bt, (size_t)nn * Ntot * 4));
@@ -335,7 +336,7 @@ int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st) {
                                       dp<cplx>(P->alpha), dp<float>(P->tc_ah), dp<float>(P->tc_al));
     P->launches++;
     TcArgs a;
-    a.nchunks = (int)P->n_chunks;
+    a.nchunks = nch;
     a.chunk_start = dp<int>(P->chunk_start);
     a.chunk_table = dp<int>(P->chunk_key);
     a.chunk_cnt = dp<int>(P->chunk_cnt);
@@ -361,7 +362,7 @@ int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st) {
     a.flags = dp<int>(P->flags);
     size_t sm = 2 * (size_t)(2 * TM * KC * 4 + 2 * Ncta * KC * 4) + (size_t)P->np2 * sizeof(float2);
     CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid((unsigned)P->n_chunks, (unsigned)nsplit);
+    dim3 grid((unsigned)nch, (unsigned)nsplit);
     k_m2l_tc<<<grid, NTHR, sm, st>>>(a);
     P->launches++;
     k_fold_beta<<<nn, 128, 0, st>>>(nn, dp<int>(P->n_level), P->side, np, Ntot, dp<int>(P->d_mi),

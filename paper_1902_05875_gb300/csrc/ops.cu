@@ -212,10 +212,15 @@ __global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pa
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= nv) return;
     int t = pair_t[e], s = v_src[e];
-    int l = T.level[t], lay = T.layer[t];
+    int l = T.level[t], lay = T.layer[t], lays = T.layer[s];
     int dx = T.ix[t] - T.ix[s], dy = T.iy[t] - T.iy[s], dz = T.iz[t] - T.iz[s];
-    keys[2 * e] = m2l_key(0, l, lay, dx, dy, dz + 3);
-    keys[2 * e + 1] = has_A[lay] ? m2l_key(1, l, lay, dx, dy, T.iz[t] + T.iz[s]) : ~0ULL;
+    if (lay != lays) {          // cross-layer component: one table per (z_t, z_s)
+        keys[2 * e] = xkey(l, lay, lays, dx, dy, T.iz[t], T.iz[s]);
+        keys[2 * e + 1] = ~0ULL;
+    } else {
+        keys[2 * e] = m2l_key(0, l, lay, dx, dy, dz + 3);
+        keys[2 * e + 1] = has_A[lay] ? m2l_key(1, l, lay, dx, dy, T.iz[t] + T.iz[s]) : ~0ULL;
+    }
     vals[2 * e] = (int)(2 * e);
     vals[2 * e + 1] = (int)(2 * e + 1);
 }
@@ -274,67 +279,6 @@ __global__ void k_chunk_cnt(int nchunks, int64_t nvalid, const int *__restrict__
     int end = (c + 1 < nchunks) ? chunk_start[c + 1] : (int)nvalid;
     int cnt = end - chunk_start[c];
     chunk_cnt[c] = cnt < chsize ? cnt : chsize;
-}
-
-// ------------------------------------------------------------------ derivative tables
-// One derivative table per key: sum over the key's images of
-// A_j D^g h0(k R_j) / g!, |g| <= 2p, by the recurrence (Sec. 3.2)
-//   |g| R^2 a_g + (2|g|-1) sum_i x_i a_{g-e_i} + (|g|-1) sum_i a_{g-2e_i}
-//       = i k sum_i (x_i b_{g-e_i} + b_{g-2e_i}),
-//   |g| b_g = i k sum_i (x_i a_{g-e_i} + a_{g-2e_i}),
-// a_0 = e^{ikR}/R, b_0 = e^{ikR}, D^g h0 / g! = a_g / (ik).
-__device__ void recur_accumulate(int P2, int np2, const int *mi, cplx k, double X, double Y, cplx W,
-                                 cplx coef, bool flip3, cplx *a, cplx *b, cplx *acc) {
-    if (threadIdx.x == 0) {
-        cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
-        cplx R = csqrt_p(R2);
-        cplx ikR = cmul(mkc(-k.y, k.x), R);
-        cplx e = cexp_(ikR);
-        a[0] = cdiv(e, R);
-        b[0] = e;
-    }
-    __syncthreads();
-    cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
-    cplx ik = mkc(-k.y, k.x);
-    for (int n = 1; n <= P2; ++n) {
-        int first = n * (n + 1) * (n + 2) / 6, last = (n + 1) * (n + 2) * (n + 3) / 6;
-        for (int g = first + threadIdx.x; g < last; g += blockDim.x) {
-            int kk[3] = {mi[3 * g], mi[3 * g + 1], mi[3 * g + 2]};
-            cplx xs[3] = {mkc(X, 0), mkc(Y, 0), W};
-            cplx sa1 = mkc(0, 0), sa2 = mkc(0, 0), sb = mkc(0, 0);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if (kk[i] >= 1) {
-                    int m[3] = {kk[0], kk[1], kk[2]};
-                    m[i] -= 1;
-                    int j = midx(m[0], m[1], m[2]);
-                    sa1 = cadd(sa1, cmul(xs[i], a[j]));
-                    sb = cadd(sb, cmul(xs[i], b[j]));
-                }
-                if (kk[i] >= 2) {
-                    int m[3] = {kk[0], kk[1], kk[2]};
-                    m[i] -= 2;
-                    int j = midx(m[0], m[1], m[2]);
-                    sa2 = cadd(sa2, a[j]);
-                    sb = cadd(sb, b[j]);
-                }
-            }
-            cplx bg = cscale(cmul(ik, cadd(sa1, sa2)), 1.0 / n);
-            cplx num = csub(csub(cmul(ik, sb), cscale(sa1, 2.0 * n - 1.0)), cscale(sa2, n - 1.0));
-            cplx ag = cdiv(num, cscale(R2, (double)n));
-            a[g] = ag;
-            b[g] = bg;
-        }
-        __syncthreads();
-    }
-    // acc += coef * a / (ik) * (-1)^{g3 if flip3}
-    cplx c2 = cdiv(coef, ik);
-    for (int g = threadIdx.x; g < np2; g += blockDim.x) {
-        cplx v = cmul(c2, a[g]);
-        if (flip3 && (mi[3 * g + 2] & 1)) v = mkc(-v.x, -v.y);
-        acc[g] = cadd(acc[g], v);
-    }
-    __syncthreads();
 }
 
 __global__ void k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube cb, int P2, int np2,
@@ -617,6 +561,8 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     const int64_t nv = P->n_v;
     P->n_tables = 0;
     P->n_chunks = 0;
+    P->x_first_table = 0;
+    P->x_first_chunk = 0;
     if (nv == 0) return TEFMM_OK;
     const int64_t ni = 2 * nv;
     TRY(dbuf_ensure(P->pair_slot, ni * 8));
@@ -687,16 +633,19 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
                                                     P->chunk_pairs);
     P->launches++;
     CUDA_TRY(cudaGetLastError());
+    P->x_first_table = P->n_tables;     // narrowed by cross_prepare when cross keys exist
+    P->x_first_chunk = P->n_chunks;
     return TEFMM_OK;
 }
 
 int m2l_tables(tefmm_plan_s *P, cudaStream_t st) {
-    if (P->n_tables == 0) return TEFMM_OK;
+    const int ntab = P->x_first_table;        // same-layer tables (cross-layer ones follow)
+    if (ntab == 0) return TEFMM_OK;
     const int np2 = P->np2;
-    TRY(dbuf_ensure(P->tables, (size_t)P->n_tables * np2 * sizeof(cplx)));
+    TRY(dbuf_ensure(P->tables, (size_t)ntab * np2 * sizeof(cplx)));
     size_t sm = 3 * (size_t)np2 * sizeof(cplx) + 3 * (size_t)np2 * sizeof(int);
     CUDA_TRY(cudaFuncSetAttribute(k_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_tables<<<P->n_tables, 256, sm, st>>>(P->n_tables, dp<uint64_t>(P->table_slot), cube_of(P),
+    k_tables<<<ntab, 256, sm, st>>>(ntab, dp<uint64_t>(P->table_slot), cube_of(P),
                                            2 * P->p, np2, dp<int>(P->d_mi), img_view(P),
                                            dp<cplx>(P->tables));
     P->launches++;
@@ -708,11 +657,12 @@ int m2l_apply(tefmm_plan_s *P, cudaStream_t st) {
     const int nn = P->n_nodes, np = P->np;
     TRY(dbuf_ensure(P->beta, (size_t)nn * np * sizeof(cplx)));
     CUDA_TRY(cudaMemsetAsync(P->beta.p, 0, (size_t)nn * np * sizeof(cplx), st));
-    if (P->n_chunks == 0) return TEFMM_OK;
+    const int nch = (int)P->x_first_chunk;    // same-layer chunks (cross-layer ones follow)
+    if (nch == 0) return TEFMM_OK;
     size_t sm = (size_t)P->np2 * sizeof(cplx) + (size_t)CH * np * sizeof(cplx);
     CUDA_TRY(cudaFuncSetAttribute(k_m2l_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_m2l_fp64<<<(int)P->n_chunks, 256, sm, st>>>(
-        (int)P->n_chunks, dp<int>(P->chunk_start), dp<int>(P->chunk_key), dp<int>(P->chunk_cnt),
+    k_m2l_fp64<<<nch, 256, sm, st>>>(
+        nch, dp<int>(P->chunk_start), dp<int>(P->chunk_key), dp<int>(P->chunk_cnt),
         dp<uint64_t>(P->table_slot), dp<cplx>(P->tables), dp<int>(P->pair_idx_sorted),
         dp<int>(P->pair_t), dp<int>(P->v_src), np, P->np2, dp<unsigned short>(P->d_m2l_g),
         dp<double>(P->d_m2l_cB), dp<double>(P->d_m2l_cA), dp<cplx>(P->alpha), dp<cplx>(P->beta));

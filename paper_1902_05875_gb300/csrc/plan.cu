@@ -206,7 +206,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
                    &P->item_scan, &P->cnt_s, &P->cnt_t, &P->sx, &P->sy, &P->sz, &P->sq, &P->tx,
                    &P->ty, &P->tz, &P->perm_s, &P->perm_t, &P->n_layer, &P->n_level, &P->n_ix,
                    &P->n_iy, &P->n_iz, &P->n_parent, &P->n_cfirst, &P->n_nchild, &P->n_s0,
-                   &P->n_s1, &P->n_t0, &P->n_t1, &P->n_i0, &P->n_i1, &P->n_split, &P->bbox,
+                   &P->n_s1, &P->n_t0, &P->n_t1, &P->n_i0, &P->n_i1, &P->n_split, &P->n_key, &P->bbox,
                    &P->flags, &P->counters, &P->C_list, &P->C_cnt, &P->D_list, &P->D_cnt,
                    &P->X_list, &P->X_cnt, &P->V_tmp, &P->V_cnt, &P->v_ptr, &P->v_src,
                    &P->near_ptr, &P->near_src, &P->near_tmp, &P->near_cnt, &P->alpha, &P->beta,
@@ -215,6 +215,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
                    &P->chunk_start, &P->chunk_cnt, &P->tables, &P->table_slot, &P->seg_tmp,
                    &P->h_in, &P->h_out, &P->tc_ah, &P->tc_al, &P->tc_bt, &P->tc_cfA, &P->tc_cfB};
     for (DBuf *b : all) dbuf_free(*b);
+    cross_release(P);
     for (int i = 0; i < 8; ++i)
         if (P->ev[i]) cudaEventDestroy(P->ev[i]);
     delete P;

@@ -5,8 +5,10 @@
 // cube; integer coordinates i = min(floor(((x - lo)/side) * 2^20), 2^20 - 1)
 // with correctly rounded double operations (no FMA); 60-bit Morton codes with
 // the layer in bits 60..63; a box is split while max(#sources, #targets) >
-// leaf_cap; only boxes that hold a point exist; nodes are numbered
-// level-major, by (level, layer, Morton prefix).
+// leaf_cap, or while a box of the same level in another layer's tree is
+// adjacent to it (so that boxes of different layers never meet in a near-field
+// list); only boxes that hold a point exist; nodes are numbered level-major,
+// by (level, layer, Morton prefix).
 //
 // Lists: the dual-tree traversal of (target tree, source tree) that for a
 // single tree is the classic adaptive U/V/W/X construction; V pairs go to M2L,
@@ -252,6 +254,64 @@ __global__ void k_node_ranges(int off, int cnt, int64_t nitems, int l, int leaf_
     if (par >= 0) {
         if (j == 0 || n_parent[c - 1] != par) n_cfirst[par] = c;
         atomicAdd(&n_nchild[par], 1);
+    }
+}
+
+// Cross-layer split rule: a box that is not split by the leaf-size rule is
+// still split while a box of another layer's tree at the same level is
+// adjacent to it (and level < max_level).  Level nodes are ordered by
+// (layer, prefix); n_key holds (layer << 60 | prefix) for a binary search.
+__global__ void k_level_keys(int off, int cnt, int l, const int *__restrict__ n_i0,
+                             const uint64_t *__restrict__ keys, uint64_t *__restrict__ nkey) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cnt) return;
+    nkey[j] = prefix_at(keys[n_i0[off + j]], l);
+}
+
+__device__ __forceinline__ bool find_key(const uint64_t *nkey, int cnt, uint64_t k) {
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (nkey[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < cnt && nkey[lo] == k;
+}
+
+__device__ __forceinline__ uint64_t morton3(int ix, int iy, int iz, int l) {
+    uint64_t m = 0;
+    for (int b = 0; b < l; ++b) {
+        m |= (uint64_t)((ix >> b) & 1) << (3 * b + 2);
+        m |= (uint64_t)((iy >> b) & 1) << (3 * b + 1);
+        m |= (uint64_t)((iz >> b) & 1) << (3 * b);
+    }
+    return m;
+}
+
+__global__ void k_cross_split(int off, int cnt, int l, int nL, int max_level,
+                              const uint64_t *__restrict__ nkey, const int *__restrict__ n_layer,
+                              const int *__restrict__ n_ix, const int *__restrict__ n_iy,
+                              const int *__restrict__ n_iz, int *n_split, int *nsplit_count) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cnt || l >= max_level) return;
+    int c = off + j;
+    if (n_split[c]) return;
+    int lay = n_layer[c], ix = n_ix[c], iy = n_iy[c], iz = n_iz[c];
+    int side = 1 << l;
+    for (int ob = 0; ob < nL; ++ob) {
+        if (ob == lay) continue;
+        for (int dx = -1; dx <= 1; ++dx)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dz = -1; dz <= 1; ++dz) {
+                    int x = ix + dx, y = iy + dy, z = iz + dz;
+                    if (x < 0 || y < 0 || z < 0 || x >= side || y >= side || z >= side) continue;
+                    uint64_t k = ((uint64_t)ob << 60) | morton3(x, y, z, l);
+                    if (find_key(nkey, cnt, k)) {
+                        n_split[c] = 1;
+                        atomicAdd(nsplit_count, 1);
+                        return;
+                    }
+                }
     }
 }
 
@@ -658,6 +718,17 @@ int tree_build(tefmm_plan_s *P, const double *sx, const double *sy, const double
             dp<int>(P->n_split), dp<int>(P->n_cfirst), dp<int>(P->n_nchild),
             dp<int>(P->counters));
         P->launches++;
+        if (P->nL > 1) {
+            TRY(dbuf_ensure(P->n_key, (size_t)cnt * 8));
+            k_level_keys<<<grid_for(cnt, 256), 256, 0, st>>>((int)total, cnt, l, dp<int>(P->n_i0), keys,
+                                                             dp<uint64_t>(P->n_key));
+            P->launches++;
+            k_cross_split<<<grid_for(cnt, 128), 128, 0, st>>>(
+                (int)total, cnt, l, P->nL, max_level, dp<uint64_t>(P->n_key), dp<int>(P->n_layer),
+                dp<int>(P->n_ix), dp<int>(P->n_iy), dp<int>(P->n_iz), dp<int>(P->n_split),
+                dp<int>(P->counters));
+            P->launches++;
+        }
         int nsplit = 0;
         CUDA_TRY(cudaMemcpyAsync(&nsplit, P->counters.p, 4, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -733,10 +804,6 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
     if (nn > 0) {
         k_csr_fill<<<nn, 64, 0, st>>>(nn, dp<int>(P->V_cnt), dp<int>(P->V_tmp), P->cap_V,
                                       dp<int>(P->v_ptr), dp<int>(P->v_src), dp<int>(P->pair_t));
-        P->launches++;
-        k_layer_mismatch<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_layer),
-                                                            dp<int>(P->v_ptr), dp<int>(P->v_src),
-                                                            dp<int>(P->flags));
         P->launches++;
         k_layer_mismatch<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_layer),
                                                             dp<int>(P->near_ptr),

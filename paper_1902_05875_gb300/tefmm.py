@@ -34,14 +34,17 @@ class Stats(ctypes.Structure):
                 ("ms_tree", ctypes.c_double), ("ms_upward", ctypes.c_double),
                 ("ms_tables", ctypes.c_double), ("ms_m2l", ctypes.c_double),
                 ("ms_downward", ctypes.c_double), ("ms_near", ctypes.c_double),
-                ("fit_max_resid", ctypes.c_double), ("n_launches", ctypes.c_int64)]
+                ("fit_max_resid", ctypes.c_double), ("n_launches", ctypes.c_int64),
+                ("n_cross_tables", ctypes.c_int), ("n_cross_fits", ctypes.c_int),
+                ("n_cross_fits_last", ctypes.c_int), ("ms_cross_fit", ctypes.c_double),
+                ("fit_max_resid_cross", ctypes.c_double)]
 
 
 EXPORTED = [
     "tefmm_default_options", "tefmm_plan_create", "tefmm_plan_destroy", "tefmm_eval",
     "tefmm_eval_host", "tefmm_get_stats", "tefmm_status_string", "tefmm_plan_image_counts",
     "tefmm_plan_get_images", "tefmm_plan_set_images", "tefmm_export_tree", "tefmm_export_lists",
-    "tefmm_export_expansions", "tefmm_fit_images_noalloc",
+    "tefmm_export_expansions", "tefmm_fit_images_noalloc", "tefmm_plan_cross_images",
 ]
 
 _lib = None
@@ -273,6 +276,26 @@ class Plan:
         _check(self.lib.tefmm_export_lists(self.h, None, None, _iptr(vp), _iptr(vs), _iptr(npp),
                                            _iptr(ns_)), "export_lists")
         return vp, vs[:nv.value], npp, ns_[:nn_.value]
+
+    def cross_images(self):
+        """Cached cross-layer fits: {(l, l', 'up'|'down', level, iz_s, k3'): (A, Z)}."""
+        n = ctypes.c_int()
+        _check(self.lib.tefmm_plan_cross_images(self.h, ctypes.byref(n), None, None, None, None),
+               "cross_images")
+        m = n.value
+        keys = np.zeros(6 * max(m, 1), np.int32)
+        cnt = np.zeros(max(m, 1), np.int32)
+        A = np.zeros(2 * 32 * max(m, 1), np.float64)
+        Z = np.zeros(2 * 32 * max(m, 1), np.float64)
+        _check(self.lib.tefmm_plan_cross_images(self.h, ctypes.byref(n), _iptr(keys), _iptr(cnt),
+                                                _dptr(A), _dptr(Z)), "cross_images")
+        out = {}
+        for i in range(m):
+            lt, ls, d, lev, izs, k3p = (int(v) for v in keys[6 * i:6 * i + 6])
+            j = 32 * i + np.arange(cnt[i])
+            out[(lt, ls, 'up' if d == 0 else 'down', lev, izs, k3p)] = (
+                A[2 * j] + 1j * A[2 * j + 1], Z[2 * j] + 1j * Z[2 * j + 1])
+        return out
 
     def export_expansions(self):
         n = self.stats()["n_nodes"]
