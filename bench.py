@@ -1,11 +1,22 @@
 """Benchmark of the layered-media TE-FMM matrix-vector product.
 
 One step = one full ``tefmm_eval`` (Morton sort, octrees, lists, P2M/M2M,
-derivative tables, M2L, L2L, L2P and near field) over the whole particle set,
-inputs resident in HBM.  Prints one JSON line (rank 0).
+derivative tables, M2L, L2L, L2P and near field, all nine layer-pair
+components) over the whole particle set, inputs resident in HBM.  The DCIM
+fits are plan state: the same-layer ones are made at plan creation and the
+cross-layer ones on the first evaluation for a root cube (warm-up), then
+cached.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload NAME] [--precision fp64|mixed]
+                  [--workload NAME] [--precision fp64|mixed] [--no-fp64-form]
+                  [--accuracy-samples S]
+
+Besides the timed form (mixed by default) the line carries the FP64 form's
+time on the same workload (one step), the relative L2 difference between the
+two forms over all targets, and both forms' relative L2 error against the
+oracle's FP64 direct sum at S sampled targets (same-layer images plus the
+cross-layer field by one DCIM fit per target); the time of that direct sum
+is the CPU baseline.
 
 Multi-GPU: the path does not shard (one matvec per GPU); N ranks run N
 independent replicas of the same workload ("replicas only"); value sums the
@@ -27,16 +38,22 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "FMM matvec interactions/s (N_t*N_s per matvec time)"
+METRIC = ("FMM matvec interactions/s (N_t*N_s per matvec time) at N=2M, mixed vs FP64 form, "
+          "rel L2 err vs FP64 direct sum")
 UNIT = "interactions/s"
 
+
+def _wl(name):
+    from paper_1902_05875_gb300 import workloads as W
+    return getattr(W, name)()
+
+
 WORKLOADS = {
-    "three_layer_middle_n200k_p8": lambda: __import__(
-        "paper_1902_05875_gb300.workloads", fromlist=["x"]).cfg_fp64_200k(),
-    "three_layer_middle_n2000_p6": lambda: __import__(
-        "paper_1902_05875_gb300.workloads", fromlist=["x"]).cfg_small(),
+    "three_layer_slabs_n2M_p10": lambda: _wl("cfg_mixed_2m"),
+    "three_layer_middle_n200k_p8": lambda: _wl("cfg_fp64_200k"),
+    "three_layer_middle_n2000_p6": lambda: _wl("cfg_small"),
 }
-DEFAULT_WORKLOAD = "three_layer_middle_n200k_p8"
+DEFAULT_WORKLOAD = "three_layer_slabs_n2M_p10"
 
 
 def peaks():
@@ -120,28 +137,38 @@ def clocks_stop(p, path, gpu_index):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(w, seconds=12.0, timer=time.perf_counter):
-    """The oracle's FP64 direct sum (C, OpenMP, all host cores) on a bounded
-    sample of targets against every source of the workload."""
+def direct_at(w, tgt_idx):
+    """The oracle's FP64 direct sum at the given targets against every source:
+    same-layer part (free space + DCIM images, C/OpenMP) plus the cross-layer
+    part by reciprocity (one DCIM fit per target, C/OpenMP).  Returns
+    (phi, seconds)."""
     from oracle.medium import Medium
     from oracle.dcim import ImageTable
-    from oracle.direct import direct_sum
+    from oracle.direct import direct_sum, cross_sum_by_reciprocity
     med = Medium(w.interfaces, w.k)
     img = ImageTable(med, w.zext, n_images=w.n_images)
+    tgt = w.src[tgt_idx]
+    t0 = time.perf_counter()
+    phi = direct_sum(med, img, w.src, w.q, tgt)
+    if med.n_layers > 1:
+        phi = phi + cross_sum_by_reciprocity(med, w.zext, w.src, w.q, tgt, n_images=w.n_images)
+    return phi, time.perf_counter() - t0
+
+
+def cpu_baseline_from(n_t, n_s, seconds, name):
+    return {"value": n_t * n_s / seconds, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 direct sum (C/OpenMP; cross-layer part by one DCIM fit per target) "
+                      f"for {n_t} sampled targets x all {n_s} sources of {name}, {seconds:.1f} s"}
+
+
+def cpu_baseline(w, seconds=12.0):
+    """The oracle's direct sum on a bounded sample of targets (about `seconds`)."""
     rng = np.random.default_rng(123)
-    n = 8
-    t0 = timer()
-    direct_sum(med, img, w.src, w.q, w.src[rng.choice(len(w.src), n, replace=False)])
-    dt = max(timer() - t0, 1e-3)
-    n = int(max(8, min(len(w.src), n * seconds / dt)))
-    tgt = w.src[rng.choice(len(w.src), n, replace=False)]
-    t0 = timer()
-    direct_sum(med, img, w.src, w.q, tgt)
-    dt = timer() - t0
-    cores = os.cpu_count()
-    return {"value": n * len(w.src) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 direct sum (C/OpenMP) for {n} sampled targets x all {len(w.src)} "
-                      f"sources of {w.name}, {dt:.1f} s"}
+    n = 4
+    _, dt = direct_at(w, rng.choice(len(w.src), n, replace=False))
+    n = int(max(4, min(len(w.src), n * seconds / max(dt, 1e-3))))
+    _, dt = direct_at(w, rng.choice(len(w.src), n, replace=False))
+    return cpu_baseline_from(n, len(w.src), dt, w.name)
 
 
 def run_reference(args, w):
@@ -169,6 +196,27 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(plan, torch, x, y, z, q, out, flush, steps):
+    """Per-step device time (CUDA events on the launching stream, L2 flushed
+    before each step) and the plan's per-phase times."""
+    times = []
+    phase = {k: [] for k in ("ms_tree", "ms_upward", "ms_tables", "ms_m2l", "ms_downward", "ms_near",
+                             "ms_cross_tables", "ms_cross_m2l")}
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.eval(x, y, z, q, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        st = plan.stats()
+        for k in phase:
+            phase[k].append(st[k])
+    return times, {k: float(np.mean(v)) for k, v in phase.items()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,6 +226,10 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the FP64-form step that the mixed form is compared with")
+    ap.add_argument("--accuracy-samples", type=int, default=100,
+                    help="targets of the oracle direct sum for the accuracy check (0: none)")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]()
     if args.impl == "reference":
@@ -195,9 +247,12 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1902_05875_gb300 import tefmm
-    prec = tefmm.MIXED if args.precision == "mixed" else tefmm.FP64
-    plan = tefmm.Plan(w.interfaces, w.k, p=w.p, leaf_cap=w.leaf_cap, n_images=w.n_images, zext=w.zext,
-                      precision=prec)
+    mixed = args.precision == "mixed"
+
+    def make(prec):
+        return tefmm.Plan(w.interfaces, w.k, p=w.p, leaf_cap=w.leaf_cap, n_images=w.n_images,
+                          zext=w.zext, precision=prec)
+    plan = make(tefmm.MIXED if mixed else tefmm.FP64)
     x, y, z = [torch.tensor(np.ascontiguousarray(w.src[:, i]), device=dev) for i in range(3)]
     q = torch.tensor(w.q, device=dev)
     out = torch.empty(len(w.src), dtype=torch.complex128, device=dev)
@@ -213,21 +268,8 @@ def main():
 
     launches0 = plan.stats()["n_launches"]
     cp, cpath = clocks_start()
-    times = []
-    phase = {k: [] for k in ("ms_tree", "ms_upward", "ms_tables", "ms_m2l", "ms_downward", "ms_near")}
     barrier()
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        plan.eval(x, y, z, q, out=out)
-        e1.record()
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-        st = plan.stats()
-        for k in phase:
-            phase[k].append(st[k])
+    times, ph = timed_steps(plan, torch, x, y, z, q, out, flush, args.steps)
     barrier()
     clocks = clocks_stop(cp, cpath, local)
     launches = plan.stats()["n_launches"] - launches0
@@ -239,6 +281,7 @@ def main():
     N = len(w.src)
     value = world * N * N / (ms * 1e-3)
     st = plan.stats()
+    phi = out.cpu().numpy()
 
     # e2e: host buffers through tefmm_eval_host, copies inside the timed region
     pin = {k: torch.tensor(np.ascontiguousarray(a)).pin_memory() for k, a in
@@ -256,14 +299,12 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     e2e_ms = float(np.mean(e2e_t)) * 1e3
 
-    # roofline of the dominant kernel (each timed phase is one kernel)
+    # roofline of the dominant phase
     pk, pk_src = peaks()
-    ph = {k: float(np.mean(v)) for k, v in phase.items()}
-    dom = max(("ms_near", "ms_m2l", "ms_tables"), key=lambda k: ph[k])
+    dom = max(("ms_near", "ms_m2l", "ms_tables", "ms_upward", "ms_downward"), key=lambda k: ph[k])
     imgs = plan.images()
-    n_img_layer = sum(len(t["A"]) for t in imgs if t["layer"] == 1)
+    n_img_layer = max(sum(len(t["A"]) for t in imgs if t["layer"] == l) for l in range(len(w.k)))
     np_ = plan.np
-    mixed = args.precision == "mixed"
     if dom == "ms_near":
         if mixed:
             flops = st["n_p2p_pairs"] * (FLOPS32_FREE + FLOPS32_IMAGE * n_img_layer)
@@ -276,32 +317,43 @@ def main():
     elif dom == "ms_m2l":
         flops = 2 * st["n_v_pairs"] * 8 * np_ * np_
         if mixed:
-            kern = "k_m2l_tc (tcgen05 kind::tf32, 3xTF32 split, key-grouped M2L)"
+            kern = "k_m2l_tc (tcgen05 kind::tf32, 3xTF32 split, key-grouped M2L, same- and cross-layer)"
             peak = pk["bf16_tflops"] * TF32_OVER_BF16
             bound, psrc = "tensor", f"TF32 = {pk_src} BF16 burst x 1.1/2.25"
         else:
             kern = "k_m2l_fp64 (key-grouped complex M2L contraction)"
             peak, bound, psrc = FP64_PEAK_TFLOPS, "alu", "nominal GB300 FP64 (no measured FP64 figure)"
-    else:
+    elif dom == "ms_tables":
         np2 = (2 * w.p + 1) * (2 * w.p + 2) * (2 * w.p + 3) // 6
         flops = st["n_tables"] * (n_img_layer + 1) * np2 * 40
-        kern = "k_tables (derivative recurrence, FP64)"
+        kern = "k_tables + k_xtables (derivative recurrence, FP64)"
+        peak, bound, psrc = FP64_PEAK_TFLOPS, "alu", "nominal GB300 FP64 (no measured FP64 figure)"
+    else:
+        # M2M / L2L: per child-parent pair, sum over k' <= k of the binomial shift (8 flops per
+        # complex multiply-add), counted as 8 * n_p * n_p / 4 (the triangular fraction)
+        flops = st["n_nodes"] * 8 * np_ * np_ / 4
+        kern = "k_m2m / k_l2l (binomial shifts, FP64)"
         peak, bound, psrc = FP64_PEAK_TFLOPS, "alu", "nominal GB300 FP64 (no measured FP64 figure)"
     ach = flops / (ph[dom] * 1e-3) / 1e12
-    roof = {"kernel": kern, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": TRAFFIC.get((kern.split()[0], w.name)),
+    roof = {"kernel": kern, "phase": dom, "bound": bound, "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "traffic": TRAFFIC.get((kern.split()[0], w.name)),
             "peak_source": psrc}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+tf32x3/f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": N, "p": w.p, "leaf_cap": w.leaf_cap, "n_images": w.n_images,
-                   "precision": args.precision, "l2": "flushed (256 MB write) between timed steps",
+                   "layers": len(w.k), "precision": args.precision,
+                   "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "phases_ms": ph,
         "counts": {"nodes": st["n_nodes"], "levels": st["n_levels"], "v_pairs": st["n_v_pairs"],
                    "p2p_pairs": st["n_p2p_pairs"], "tables": st["n_tables"],
+                   "cross_tables": st["n_cross_tables"], "cross_fits": st["n_cross_fits"],
                    "images_total": st["n_images_total"]},
+        "fits": {"same_layer_max_resid": st["fit_max_resid"],
+                 "cross_layer_max_resid": st["fit_max_resid_cross"],
+                 "cross_layer_fit_ms_first_eval": "see warm-up (cached afterwards)"},
         "roofline": roof,
         "e2e": {"value": world * N * N / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(N * 40), "d2h_bytes_per_step": int(N * 16),
@@ -310,7 +362,34 @@ def main():
         "clocks": clocks,
         "peaks_source": pk_src,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    del plan
+    torch.cuda.empty_cache()
+    phi64 = None
+    if rank == 0 and mixed and not args.no_fp64_form:
+        p64 = make(tefmm.FP64)
+        out64 = torch.empty_like(out)
+        p64.eval(x, y, z, q, out=out64)
+        torch.cuda.synchronize()
+        t64, ph64 = timed_steps(p64, torch, x, y, z, q, out64, flush, 1)
+        phi64 = out64.cpu().numpy()
+        line["fp64_form"] = {"ms_per_step": float(np.mean(t64)), "value": N * N / (np.mean(t64) * 1e-3),
+                             "unit": UNIT, "phases_ms": ph64, "steps": 1,
+                             "speedup_mixed_over_fp64": float(np.mean(t64)) / ms}
+        line["accuracy"] = {"mixed_vs_fp64_form_rel_l2": float(np.linalg.norm(phi - phi64) /
+                                                                np.linalg.norm(phi64))}
+        del p64
+        torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and args.accuracy_samples > 0:
+        idx = np.random.default_rng(2024).choice(N, min(N, args.accuracy_samples), replace=False)
+        ref, dt = direct_at(w, idx)
+        acc = line.setdefault("accuracy", {})
+        acc["samples"] = int(len(idx))
+        acc[f"{args.precision}_vs_direct_rel_l2"] = float(np.linalg.norm(phi[idx] - ref) / np.linalg.norm(ref))
+        if phi64 is not None:
+            acc["fp64_vs_direct_rel_l2"] = float(np.linalg.norm(phi64[idx] - ref) / np.linalg.norm(ref))
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_from(len(idx), N, dt, w.name)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu_baseline" not in line:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)

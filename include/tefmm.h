@@ -89,6 +89,8 @@ typedef struct {
     int n_cross_fits_last; /* cross-layer fits computed by the last eval (cache misses) */
     double ms_cross_fit;   /* host time of those fits                                 */
     double fit_max_resid_cross; /* worst cross-layer fit residual (relative)          */
+    double ms_cross_tables; /* part of ms_tables spent on cross-layer tables          */
+    double ms_cross_m2l;   /* part of ms_m2l spent on cross-layer translations        */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,

@@ -66,16 +66,49 @@ def source_part(med: Medium, l, lp, direction, zp, k3p, krho):
     return out / math.factorial(k3p)
 
 
+RETRY_RESID = 1e-2
+
+
+def source_distance(med: Medium, lp, zc):
+    """Distance from z' = zc to the nearest interface of the source layer l'."""
+    ds = []
+    if lp > 0:
+        ds.append(med.d[lp - 1] - zc)
+    if lp < med.L:
+        ds.append(zc - med.d[lp])
+    return min(ds)
+
+
+def extended_T1(k, T0, k3p, d_eff):
+    """First-level path length reaching past the peak of |k_z|^{k3'} e^{-|k_z| d_eff}
+    (at |k_z| = k3'/d_eff) by five decay lengths: |k| (T0 + T1) = (k3' + 5) / d_eff."""
+    return (k3p + 5.0) / d_eff / abs(k) - T0
+
+
 def fit_cross(med: Medium, l, lp, direction, zc, k3p, wmin, n_images=8, T1=10.0, n_samples=101,
               T0=None, m1=None, rel_tol=1e-12):
-    """Images (A, Z, info) of Theta^{k3'} for source z-centre zc (Steps 1-2)."""
+    """Images (A, Z, info) of Theta^{k3'} for source z-centre zc (Steps 1-2).
+
+    Reading: when the fit on the given paths leaves a residual above
+    RETRY_RESID of the largest sample, the first-level path is lengthened to
+    extended_T1 and the fit repeated.  Theta^{k3'} grows like |k_z|^{k3'}
+    e^{-|k_z| d_eff} along C_ap1 (d_eff = W_min + the source's distance to its
+    nearest interface); with a large k3' and a small d_eff the fixed path ends
+    before the function has peaked and no image set fits the samples.
+    """
     kl = med.k[l]
     t0 = default_T0(med, l) if T0 is None else T0
 
     def F(kz):
         krho = np.sqrt(kl * kl - kz * kz)
         return source_part(med, l, lp, direction, zc, k3p, krho) * np.exp(1j * kz * wmin)
-    return fit_two_level(F, kl, t0, T1, n_samples, n_images, m1, rel_tol)
+    A, Z, info = fit_two_level(F, kl, t0, T1, n_samples, n_images, m1, rel_tol)
+    if max(info['resid1'], info['resid2']) > RETRY_RESID * info['scale']:
+        T1x = extended_T1(kl, t0, k3p, wmin + source_distance(med, lp, zc))
+        if T1x > T1:
+            A, Z, info = fit_two_level(F, kl, t0, T1x, n_samples, n_images, m1, rel_tol)
+            info['T1'] = T1x
+    return A, Z, info
 
 
 def image_sum(med: Medium, l, direction, A, Z, wmin, x, y, z, xp, yp):

@@ -65,3 +65,52 @@ void oracle_direct_sum(int64_t ns, const double *sx, const double *sy, const dou
         phi[2 * i + 1] = cimag(acc);
     }
 }
+
+/*
+ * Cross-layer part of Phi at each target by reciprocity (Sec. 3.2 fits, one per
+ * target).  For a target r_i in layer l and sources in layer l' != l,
+ *   u_{l l'}(r_i; r') = (k_l' / k_l)^2 u_{l' l}(r'; r_i),
+ * and u_{l' l}(r'; r_i) (the field in layer l' of a source at r_i) is the
+ * image sum  sum_m A_m h0(k_l' sqrt(rho^2 + (W(z') - W_min - Z_m)^2)),
+ * W(z') = z' - d_l' (up-going part) or d_{l'-1} - z' (down-going part).
+ * Fit f of target i (fit_first[i] <= f < fit_first[i+1]) applies to the
+ * sources of layer fit_layer[f] with part fit_part[f] (0 up, 1 down), shift
+ * fit_wmin[f], factor fit_fre + i fit_fim, images img_first[f] .. img_first[f+1].
+ */
+void oracle_cross_sum(int64_t ns, const double *sx, const double *sy, const double *sz,
+                      const double *q, const int *slay,
+                      int64_t nt, const double *tx, const double *ty,
+                      const int64_t *fit_first, const int *fit_layer, const int *fit_part,
+                      const double *fit_wmin, const double *fit_fre, const double *fit_fim,
+                      const int64_t *img_first, const double *are, const double *aim,
+                      const double *zre, const double *zim,
+                      const double *kre, const double *kim, const double *d, double *phi)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < nt; ++i) {
+        double complex acc = 0.0;
+        for (int64_t f = fit_first[i]; f < fit_first[i + 1]; ++f) {
+            const int lp = fit_layer[f];
+            const double complex k = kre[lp] + I * kim[lp];
+            const double complex fac = fit_fre[f] + I * fit_fim[f];
+            double complex part = 0.0;
+            for (int64_t j = 0; j < ns; ++j) {
+                if (slay[j] != lp) continue;
+                const double complex qj = q[2 * j] + I * q[2 * j + 1];
+                const double dx = tx[i] - sx[j], dy = ty[i] - sy[j];
+                const double rho2 = dx * dx + dy * dy;
+                const double W = fit_part[f] == 0 ? sz[j] - d[lp] : d[lp - 1] - sz[j];
+                double complex s = 0.0;
+                for (int64_t m = img_first[f]; m < img_first[f + 1]; ++m) {
+                    const double complex w = W - fit_wmin[f] - (zre[m] + I * zim[m]);
+                    const double complex R = csqrt(rho2 + w * w);
+                    s += (are[m] + I * aim[m]) * h0c(k * R);
+                }
+                part += qj * s;
+            }
+            acc += fac * part;
+        }
+        phi[2 * i] = creal(acc);
+        phi[2 * i + 1] = cimag(acc);
+    }
+}

@@ -76,3 +76,61 @@ def direct_sum(med, images, src, q, tgt, include_free=True, include_reaction=Tru
         ctypes.c_int(1 if include_free else 0), ctypes.c_int(1 if include_reaction else 0),
         _p(phi, ctypes.c_double))
     return phi[0::2] + 1j * phi[1::2]
+
+
+def cross_sum_by_reciprocity(med, zext, src, q, tgt, n_images=16, **fit_kw):
+    """Cross-layer part of Phi at the targets, one DCIM fit per target
+    (``oracle_cross_sum`` in ``direct.c``): the plain definition for large
+    source counts, where one fit per source point is out of reach."""
+    from .cross import directions, fit_cross, W_min
+    lib = _load()
+    lib.oracle_cross_sum.restype = None
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+    qi = np.ascontiguousarray(np.stack([np.real(q), np.imag(q)], -1).reshape(-1), dtype=np.float64)
+    slay = np.ascontiguousarray(med.layer_of(src[:, 2]), dtype=np.int32)
+    tlay = med.layer_of(tgt[:, 2])
+    if np.any(slay < 0) or np.any(tlay < 0):
+        raise ValueError("point on an interface")
+    present = set(int(v) for v in np.unique(slay))
+    fit_first = [0]
+    fl, fp, fw, fre, fim, img_first, A_all, Z_all = [], [], [], [], [], [0], [], []
+    for i in range(len(tgt)):
+        l = int(tlay[i])
+        for lp in sorted(present):
+            if lp == l:
+                continue
+            for part in directions(med, lp):
+                wmin = W_min(med, lp, part, zext)
+                A, Z, _ = fit_cross(med, lp, l, part, float(tgt[i, 2]), 0, wmin, n_images, **fit_kw)
+                fac = (med.k[lp] / med.k[l]) ** 2
+                fl.append(lp)
+                fp.append(0 if part == 'up' else 1)
+                fw.append(wmin)
+                fre.append(fac.real)
+                fim.append(fac.imag)
+                A_all.extend(A)
+                Z_all.extend(Z)
+                img_first.append(len(A_all))
+        fit_first.append(len(fl))
+    i64 = lambda v: np.ascontiguousarray(np.array(v, dtype=np.int64))
+    i32 = lambda v: np.ascontiguousarray(np.array(v, dtype=np.int32))
+    f64 = lambda v: np.ascontiguousarray(np.array(v, dtype=np.float64).reshape(-1))
+    A_all = np.array(A_all, dtype=complex)
+    Z_all = np.array(Z_all, dtype=complex)
+    arrs = dict(ff=i64(fit_first), fl=i32(fl), fp=i32(fp), fw=f64(fw), fre=f64(fre), fim=f64(fim),
+                imf=i64(img_first), are=f64(A_all.real), aim=f64(A_all.imag), zre=f64(Z_all.real),
+                zim=f64(Z_all.imag), kre=f64(med.k.real), kim=f64(med.k.imag),
+                d=f64(np.concatenate([med.d, [0.0]])))
+    phi = np.zeros(2 * tgt.shape[0], dtype=np.float64)
+    sx, sy, sz = [np.ascontiguousarray(src[:, i]) for i in range(3)]
+    tx, ty = [np.ascontiguousarray(tgt[:, i]) for i in range(2)]
+    D, L = ctypes.c_double, ctypes.c_int64
+    lib.oracle_cross_sum(
+        ctypes.c_int64(src.shape[0]), _p(sx, D), _p(sy, D), _p(sz, D), _p(qi, D),
+        _p(slay, ctypes.c_int), ctypes.c_int64(tgt.shape[0]), _p(tx, D), _p(ty, D),
+        _p(arrs['ff'], L), _p(arrs['fl'], ctypes.c_int), _p(arrs['fp'], ctypes.c_int),
+        _p(arrs['fw'], D), _p(arrs['fre'], D), _p(arrs['fim'], D), _p(arrs['imf'], L),
+        _p(arrs['are'], D), _p(arrs['aim'], D), _p(arrs['zre'], D), _p(arrs['zim'], D),
+        _p(arrs['kre'], D), _p(arrs['kim'], D), _p(arrs['d'], D), _p(phi, D))
+    return phi[0::2] + 1j * phi[1::2]

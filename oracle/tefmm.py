@@ -46,7 +46,13 @@ Readings where the paper is silent (all stated the same way for the CUDA path):
   D_r^k D_r'^k' u / (k! k'!) = (-1)^{k1'+k2'} C(k1+k1',k1) C(k2+k2',k2)
                                sz^{k3} T^{(k3')}_{(k1+k1', k2+k2', k3)},
   T^{(k3')}_g = sum_j A_j D^g h0(k_l R_j) / g! at (X0, Y0, W(z_t) - W_min - Z_j),
-  sz = +1 (up), -1 (down).  Cross-layer near-field pairs are not supported
+  sz = +1 (up), -1 (down).  Reading: the z-centres z_c (source) and z_t
+  (target) of a cross-layer translation are the box centres clamped to the
+  layer's particle slab; the source moments are shifted there exactly (M2M
+  in z) and the resulting local expansion is shifted back to the box centre
+  (L2L in z).  A box of one layer's tree can have its centre outside the
+  layer (it straddles an interface); at such a z_c the fitted function grows
+  like e^{|k_z| (z_c - d)} along the first DCIM path and cannot be fitted.  Cross-layer near-field pairs are not supported
   (leaves must be small enough that boxes of different layers are never
   adjacent).
 """
@@ -539,11 +545,18 @@ class TEFMM:
             beta[n] += ops.l2l(beta[par], tr.center(n) - tr.center(par))
         return beta
 
+    def cross_centre(self, layer, lev, iz):
+        """z of a box's cross-layer expansion centre: its centre clamped to the
+        layer's particle slab (zlo, zhi)."""
+        h = self.tr.side / float(1 << lev)
+        zc = self.tr.lo[2] + (iz + 0.5) * h
+        zlo, zhi = self.zext[layer]
+        return min(max(zc, zlo), zhi)
+
     def cross_image(self, lt, ls, direction, lev, izs, k3p):
         key = (lt, ls, direction, lev, izs, k3p)
         if key not in self.cross_images:
-            h = self.tr.side / float(1 << lev)
-            zc = self.tr.lo[2] + (izs + 0.5) * h
+            zc = self.cross_centre(ls, lev, izs)
             wmin = xl.W_min(self.med, lt, direction, self.zext)
             A, Z, _ = xl.fit_cross(self.med, lt, ls, direction, zc, k3p, wmin, self.n_images)
             self.cross_images[key] = (A, Z)
@@ -555,7 +568,7 @@ class TEFMM:
         dix, diy, izt, izs = key
         h = tr.side / float(1 << lev)
         X0, Y0 = dix * h, diy * h
-        zt = tr.lo[2] + (izt + 0.5) * h
+        zt = self.cross_centre(lt, lev, izt)
         mi2 = multi_indices(2 * p)
         odd3 = (-1.0) ** mi2[:, 2]
         T = np.zeros((p + 1, len(mi2)), dtype=complex)
@@ -586,7 +599,13 @@ class TEFMM:
             H = cx * T[k3p[None, :], gx]
             t = np.array([a for a, _ in lst])
             s_ = np.array([b for _, b in lst])
-            np.add.at(beta, t, alpha[s_] @ H.T)
+            # moments about the source's cross-layer centre, M2L into locals
+            # about the target's cross-layer centre, re-expanded at the box centre
+            zs, zsc = tr.center(s_[0])[2], self.cross_centre(ls, lev, izs)
+            zt, ztc = tr.center(t[0])[2], self.cross_centre(lt, lev, izt)
+            a_sh = np.array([ops.m2m(alpha[j], np.array([0.0, 0.0, zs - zsc])) for j in s_])
+            loc = a_sh @ H.T
+            np.add.at(beta, t, np.array([ops.l2l(b, np.array([0.0, 0.0, zt - ztc])) for b in loc]))
 
     # -- near field ----------------------------------------------------------
     def _kernel_same_layer(self, l, tpts, spts):

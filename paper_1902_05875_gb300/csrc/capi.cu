@@ -62,10 +62,12 @@ extern "C" int tefmm_eval(tefmm_plan P, int64_t ns, const double *sx, const doub
     TRY(upward_pass(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[2], st));
     TRY(m2l_tables(P, st));
+    CUDA_TRY(cudaEventRecord(P->ev[7], st));
     TRY(cross_tables(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[3], st));
     if (P->opt.precision == TEFMM_MIXED) TRY(m2l_apply_tc(P, st));
     else TRY(m2l_apply(P, st));
+    CUDA_TRY(cudaEventRecord(P->ev[8], st));
     TRY(cross_apply(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[4], st));
     TRY(downward_pass(P, st));
@@ -132,6 +134,8 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
         o->ms_m2l = elapsed(P->ev[3], P->ev[4]);
         o->ms_downward = elapsed(P->ev[4], P->ev[5]);
         o->ms_near = elapsed(P->ev[5], P->ev[6]);
+        o->ms_cross_tables = elapsed(P->ev[7], P->ev[3]);
+        o->ms_cross_m2l = elapsed(P->ev[8], P->ev[4]);
     }
     return TEFMM_OK;
 }

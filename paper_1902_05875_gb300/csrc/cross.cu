@@ -14,6 +14,14 @@
 // One table per key (level, l, l', dx, dy, iz_t, iz_s) holds T^{(k3')} for all
 // k3' (orders 2p - k3'), packed slice after slice.
 //
+// The z-centres of a cross-layer translation are the box centres clamped to
+// the layer's particle slab (a box of one layer's tree may straddle an
+// interface, and at a source centre outside its layer the fitted function
+// grows along the first DCIM path).  The source moments are shifted to the
+// clamped centre exactly (a z-only M2M), the translation produces locals
+// about the target's clamped centre, and these are re-expanded at the box
+// centre (a z-only L2L) and added to the box's locals.
+//
 // The fits depend only on the geometry of the root cube (through z_c), so they
 // are cached in the plan and refitted only when the cube's z-origin or side
 // changes (the paper precomputes them once, 2^H (p+1) per component).
@@ -27,8 +35,83 @@ namespace {
 struct XGeom {
     double d[TEFMM_MAX_LAYERS];
     double wmin[2 * TEFMM_MAX_LAYERS];   // [layer][dir]
+    double zlo[TEFMM_MAX_LAYERS], zhi[TEFMM_MAX_LAYERS];   // particle slab of each layer
     cplx k[TEFMM_MAX_LAYERS];
 };
+
+// cross-layer expansion centre in z: the box centre clamped to the layer's slab
+__host__ __device__ inline double xcentre(double c, double zlo, double zhi) {
+    return fmin(fmax(c, zlo), zhi);
+}
+
+// moments about the cross-layer centre: alpha*_k = sum_{j3<=k3} C(k3,j3) dz^{k3-j3}
+// alpha_(k1,k2,j3), dz = box centre - cross-layer centre (exact shift in z)
+__global__ void k_xshift_alpha(int nn, TreeArrays T, Cube cb, XGeom geo, int p, int np,
+                               const int *__restrict__ mi, const cplx *__restrict__ alpha,
+                               cplx *__restrict__ alpha_x) {
+    int node = blockIdx.x;
+    if (node >= nn) return;
+    const int lay = T.layer[node];
+    const double h = box_h(cb.side, T.level[node]);
+    const double zc = centre(cb.lo[2], T.iz[node], h);
+    const double dz = zc - xcentre(zc, geo.zlo[lay], geo.zhi[lay]);
+    __shared__ double pw[32];
+    if (threadIdx.x == 0) {
+        double v = 1.0;
+        for (int e = 0; e <= p; ++e) {
+            pw[e] = v;
+            v *= dz;
+        }
+    }
+    __syncthreads();
+    const cplx *a = alpha + (int64_t)node * np;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const int k1 = mi[3 * k], k2 = mi[3 * k + 1], k3 = mi[3 * k + 2];
+        cplx s = mkc(0, 0);
+        for (int j3 = 0; j3 <= k3; ++j3) {
+            const double b = binom(k3, j3) * pw[k3 - j3];
+            const cplx x = a[midx(k1, k2, j3)];
+            s.x += b * x.x;
+            s.y += b * x.y;
+        }
+        alpha_x[(int64_t)node * np + k] = s;
+    }
+}
+
+// locals about the cross-layer centre, re-expanded at the box centre and added:
+// beta_k += sum_{j3>=k3} C(j3,k3) dz^{j3-k3} beta*_(k1,k2,j3), dz = box centre - cross centre
+__global__ void k_xshift_beta(int nn, TreeArrays T, Cube cb, XGeom geo, int p, int np,
+                              const int *__restrict__ mi, const cplx *__restrict__ beta_x,
+                              cplx *__restrict__ beta) {
+    int node = blockIdx.x;
+    if (node >= nn || T.t1[node] <= T.t0[node]) return;
+    const int lay = T.layer[node];
+    const double h = box_h(cb.side, T.level[node]);
+    const double zc = centre(cb.lo[2], T.iz[node], h);
+    const double dz = zc - xcentre(zc, geo.zlo[lay], geo.zhi[lay]);
+    __shared__ double pw[32];
+    if (threadIdx.x == 0) {
+        double v = 1.0;
+        for (int e = 0; e <= p; ++e) {
+            pw[e] = v;
+            v *= dz;
+        }
+    }
+    __syncthreads();
+    const cplx *bx = beta_x + (int64_t)node * np;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        const int k1 = mi[3 * k], k2 = mi[3 * k + 1], k3 = mi[3 * k + 2];
+        cplx s = mkc(0, 0);
+        for (int j3 = k3; k1 + k2 + j3 <= p; ++j3) {
+            const double b = binom(j3, k3) * pw[j3 - k3];
+            const cplx x = bx[midx(k1, k2, j3)];
+            s.x += b * x.x;
+            s.y += b * x.y;
+        }
+        cplx v = beta[(int64_t)node * np + k];
+        beta[(int64_t)node * np + k] = mkc(v.x + s.x, v.y + s.y);
+    }
+}
 
 __host__ __device__ inline int slice_off(int p, int k3p) {
     int o = 0;
@@ -70,7 +153,7 @@ __global__ void k_xtables(int nx, const uint64_t *__restrict__ keys, Cube cb, in
     const XKey x = xkey_decode(keys[tb]);
     const double h = box_h(cb.side, x.level);
     const double X = (double)x.dx * h, Y = (double)x.dy * h;
-    const double zt = centre(cb.lo[2], x.izt, h);
+    const double zt = xcentre(centre(cb.lo[2], x.izt, h), geo.zlo[x.lt], geo.zhi[x.lt]);
     const cplx k = geo.k[x.lt];
     for (int dir = 0; dir < 2; ++dir) {
         int2 r = xrange[((int64_t)tb * 2 + dir) * (p + 1) + k3p];
@@ -162,6 +245,8 @@ XGeom geometry(const tefmm_plan_s *P) {
     for (int l = 0; l < TEFMM_MAX_LAYERS; ++l) {
         g.d[l] = l < P->nL - 1 ? P->d[l] : 0.0;
         g.k[l] = l < P->nL ? P->k[l] : mkc(1, 0);
+        g.zlo[l] = l < P->nL ? P->opt.zext[2 * l] : 0.0;
+        g.zhi[l] = l < P->nL ? P->opt.zext[2 * l + 1] : 0.0;
         for (int dir = 0; dir < 2; ++dir) {
             bool present = l < P->nL && (dir == 0 ? l < P->nL - 1 : l > 0);
             g.wmin[2 * l + dir] = present ? cross_wmin(P, l, dir) : 0.0;
@@ -208,6 +293,18 @@ int build_maps(tefmm_plan_s *P) {
     grp[p + 1] = (int)ord.size();
     std::vector<int> og(ord);
     og.insert(og.end(), grp.begin(), grp.end());
+    // tensor-core form: index into the packed slices and FP32 coefficients (exact)
+    std::vector<unsigned short> Gs((size_t)np * np);
+    std::vector<float> cf32((size_t)np * np);
+    for (int kp = 0; kp < np; ++kp)
+        for (int k = 0; k < np; ++k) {
+            Gs[(size_t)kp * np + k] = (unsigned short)(slice_off(p, mi[3 * kp + 2]) + G[(size_t)kp * np + k]);
+            cf32[(size_t)kp * np + k] = (float)cf[(size_t)kp * np + k];
+        }
+    TRY(dbuf_ensure(P->tc_xgs, Gs.size() * 2));
+    TRY(dbuf_ensure(P->tc_xcf32, cf32.size() * 4));
+    CUDA_TRY(cudaMemcpy(P->tc_xgs.p, Gs.data(), Gs.size() * 2, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(P->tc_xcf32.p, cf32.data(), cf32.size() * 4, cudaMemcpyHostToDevice));
     TRY(dbuf_ensure(P->d_xG, G.size() * 2));
     TRY(dbuf_ensure(P->d_xcf, cf.size() * 8));
     TRY(dbuf_ensure(P->d_xoff, og.size() * 4));
@@ -334,20 +431,41 @@ int cross_apply(tefmm_plan_s *P, cudaStream_t st) {
     size_t sm = (size_t)P->np2 * sizeof(cplx) + (size_t)CHX * np * sizeof(cplx);
     CUDA_TRY(cudaFuncSetAttribute(k_m2l_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int *og = dp<int>(P->d_xoff);
-    k_m2l_x<<<nch, nthr, sm, st>>>((int)P->x_first_chunk, nch, dp<int>(P->chunk_start),
+    const int nn = P->n_nodes;
+    const size_t nb = (size_t)nn * np * sizeof(cplx);
+    TRY(dbuf_ensure(P->xalpha, nb));
+    TRY(dbuf_ensure(P->xbeta, nb));
+    CUDA_TRY(cudaMemsetAsync(P->xbeta.p, 0, nb, st));
+    const TreeArrays T = tree_arrays(P);
+    const Cube cb = cube_of(P);
+    const XGeom geo = geometry(P);
+    k_xshift_alpha<<<nn, 128, 0, st>>>(nn, T, cb, geo, P->p, np, dp<int>(P->d_mi), dp<cplx>(P->alpha),
+                                       dp<cplx>(P->xalpha));
+    P->launches++;
+    if (P->opt.precision == TEFMM_MIXED && m2l_tc_smem(np, P->NX) <= 227 * 1024) {
+        // mixed form: the cross-layer contraction on the tensor cores (3xTF32)
+        TRY(m2l_apply_tc_cross(P, st, dp<cplx>(P->xalpha), dp<cplx>(P->xbeta),
+                               dp<unsigned short>(P->tc_xgs), dp<float>(P->tc_xcf32)));
+    } else {
+        k_m2l_x<<<nch, nthr, sm, st>>>((int)P->x_first_chunk, nch, dp<int>(P->chunk_start),
                                    dp<int>(P->chunk_key), dp<int>(P->chunk_cnt), P->x_first_table,
                                    dp<cplx>(P->xtables), P->NX, dp<int>(P->pair_idx_sorted),
                                    dp<int>(P->pair_t), dp<int>(P->v_src), P->p, np,
                                    dp<unsigned short>(P->d_xG), dp<double>(P->d_xcf), og, og + np,
-                                   dp<cplx>(P->alpha), dp<cplx>(P->beta));
+                                   dp<cplx>(P->xalpha), dp<cplx>(P->xbeta));
+        P->launches++;
+    }
+    k_xshift_beta<<<nn, 128, 0, st>>>(nn, T, cb, geo, P->p, np, dp<int>(P->d_mi), dp<cplx>(P->xbeta),
+                                      dp<cplx>(P->beta));
     P->launches++;
     CUDA_TRY(cudaGetLastError());
     return TEFMM_OK;
 }
 
 void cross_release(tefmm_plan_s *P) {
-    DBuf *b[] = {&P->d_xA, &P->d_xZ, &P->d_xrange, &P->d_tslot, &P->xtables,
-                 &P->d_xG, &P->d_xcf, &P->d_xexp, &P->d_xoff, &P->tc_xcf};
+    DBuf *b[] = {&P->d_xA, &P->d_xZ, &P->d_xrange, &P->d_tslot, &P->xtables, &P->d_xG,
+                 &P->d_xcf, &P->d_xexp, &P->d_xoff, &P->tc_xcf, &P->xalpha, &P->xbeta,
+                 &P->tc_xah, &P->tc_xal, &P->tc_xbt, &P->tc_xgs, &P->tc_xcf32};
     for (DBuf *x : b) dbuf_free(*x);
 }
 

@@ -26,6 +26,7 @@ constexpr int MAXLS = 24;            // images per level
 constexpr double REL_TOL = 1e-12;
 constexpr double ABS_TOL = 1e-14;
 constexpr double CANCEL = 1e4;     // largest image term / largest sample
+constexpr double RETRY_RESID = 1e-2;   // cross-layer fit residual that triggers a longer path
 
 struct FitJob {
     int layer, tag, nL;
@@ -969,8 +970,10 @@ int fit_cross_jobs(tefmm_plan_s *P, const std::vector<CrossFitKey> &keys, cudaSt
             J.d[m] = m < P->nL - 1 ? P->d[m] : 0.0;
             J.k[m] = m < P->nL ? P->k[m] : mkc(1, 0);
         }
+        // source z-centre: the box centre clamped to the source layer's slab
         double h = P->side / (double)(1 << c.level);
-        J.zc = P->lo[2] + ((double)c.izs + 0.5) * h;
+        double zc = P->lo[2] + ((double)c.izs + 0.5) * h;
+        J.zc = fmin(fmax(zc, P->opt.zext[2 * c.ls]), P->opt.zext[2 * c.ls + 1]);
         J.zmin = cross_wmin(P, c.lt, c.dir);
         double kl = P->k[c.lt].x;
         J.T0 = P->opt.T0 > 0 ? P->opt.T0 : sqrt(fmax(((kmax + 0.8) / kl) * ((kmax + 0.8) / kl) - 1.0, 1e-6));
@@ -997,11 +1000,59 @@ int fit_cross_jobs(tefmm_plan_s *P, const std::vector<CrossFitKey> &keys, cudaSt
     std::vector<cplx> hA((size_t)nj * MAXM), hZ((size_t)nj * MAXM);
     std::vector<int> hN(nj);
     std::vector<double> hR(nj);
-    CUDA_TRY(cudaMemcpyAsync(hA.data(), dA, hA.size() * sizeof(cplx), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(hZ.data(), dZ, hZ.size() * sizeof(cplx), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(hN.data(), dN, nj * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaMemcpyAsync(hR.data(), dR, nj * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
+    auto fetch = [&]() -> int {
+        CUDA_TRY(cudaMemcpyAsync(hA.data(), dA, hA.size() * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(hZ.data(), dZ, hZ.size() * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(hN.data(), dN, nj * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(hR.data(), dR, nj * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return TEFMM_OK;
+    };
+    TRY(fetch());
+    // Fits whose residual exceeds RETRY_RESID of the largest sample are
+    // repeated on a first-level path that reaches past the peak of
+    // |k_z|^{k3'} e^{-|k_z| d_eff}: |k| (T0 + T1) = (k3' + 5) / d_eff, with
+    // d_eff = W_min + the source centre's distance to its nearest interface.
+    std::vector<int> redo;
+    for (int i = 0; i < nj; ++i) {
+        if (!(hR[i] > RETRY_RESID)) continue;
+        FitJob &J = jobs[i];
+        double ds = 1e300;
+        if (J.src_layer > 0) ds = fmin(ds, J.d[J.src_layer - 1] - J.zc);
+        if (J.src_layer < J.nL - 1) ds = fmin(ds, J.zc - J.d[J.src_layer]);
+        const cplx kl = J.k[J.layer];
+        const double T1x = (J.k3p + 5.0) / (J.zmin + ds) / hypot(kl.x, kl.y) - J.T0;
+        if (T1x > J.T1) {
+            J.T1 = T1x;
+            redo.push_back(i);
+        }
+    }
+    if (!redo.empty()) {
+        const int nr = (int)redo.size();
+        std::vector<FitJob> rj(nr);
+        for (int i = 0; i < nr; ++i) rj[i] = jobs[redo[i]];
+        CUDA_TRY(cudaMemcpyAsync(djobs, rj.data(), nr * sizeof(FitJob), cudaMemcpyHostToDevice, st));
+        k_fit<<<nr, 512, sm, st>>>(djobs, nr, dA, dZ, dN, dR);
+        P->launches++;
+        CUDA_TRY(cudaGetLastError());
+        std::vector<cplx> rA((size_t)nr * MAXM), rZ((size_t)nr * MAXM);
+        std::vector<int> rN(nr);
+        std::vector<double> rR(nr);
+        CUDA_TRY(cudaMemcpyAsync(rA.data(), dA, rA.size() * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(rZ.data(), dZ, rZ.size() * sizeof(cplx), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(rN.data(), dN, nr * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(rR.data(), dR, nr * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        for (int i = 0; i < nr; ++i) {
+            const int j = redo[i];
+            for (int m = 0; m < MAXM; ++m) {
+                hA[(size_t)j * MAXM + m] = rA[(size_t)i * MAXM + m];
+                hZ[(size_t)j * MAXM + m] = rZ[(size_t)i * MAXM + m];
+            }
+            hN[j] = rN[i];
+            hR[j] = rR[i];
+        }
+    }
     cudaFree(djobs);
     cudaFree(dA);
     cudaFree(dZ);

@@ -181,6 +181,8 @@ struct tefmm_plan_s {
     double xgeo_lo = 0.0, xgeo_side = -1.0;
     double fit_max_resid_cross = 0.0;
     DBuf d_xA, d_xZ, d_xrange, d_tslot, xtables, d_xG, d_xcf, d_xexp, d_xoff, tc_xcf;
+    DBuf xalpha, xbeta;   // moments / locals about the cross-layer centres
+    DBuf tc_xah, tc_xal, tc_xbt, tc_xgs, tc_xcf32;   // tensor-core cross-layer M2L
     int NX = 0, n_xtables = 0, n_xfits_last = 0;
     int x_first_table = 0;        // cross-layer tables are [x_first_table, n_tables)
     int64_t x_first_chunk = 0;    // cross-layer chunks are [x_first_chunk, n_chunks)
@@ -195,7 +197,7 @@ struct tefmm_plan_s {
     DBuf h_in, h_out;
 
     // timing
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[12] = {};
     double ms_tree = 0, ms_upward = 0, ms_tables = 0, ms_m2l = 0, ms_downward = 0, ms_near = 0;
     int64_t launches = 0;    // kernels of this library launched so far
 };
@@ -238,6 +240,9 @@ int m2l_tables(tefmm_plan_s *P, cudaStream_t st);
 int m2l_apply(tefmm_plan_s *P, cudaStream_t st);
 // m2l_tc.cu
 int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st);
+int m2l_apply_tc_cross(tefmm_plan_s *P, cudaStream_t st, const cplx *alpha_x, cplx *beta_x,
+                       const unsigned short *xgs, const float *xcf);
+size_t m2l_tc_smem(int np, int tab_entries);
 void m2l_tc_geometry(int np, int *Kpad, int *Ncta, int *nsplit, int *nblk);
 int downward_pass(tefmm_plan_s *P, cudaStream_t st);
 int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st);

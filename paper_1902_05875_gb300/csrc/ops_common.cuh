@@ -122,7 +122,9 @@ __device__ inline void recur_accumulate(int P2, int np2, const int *mi, cplx k, 
     __syncthreads();
     cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
     cplx ik = mkc(-k.y, k.x);
+    const cplx iR2 = cdiv(mkc(1, 0), R2);
     for (int n = 1; n <= P2; ++n) {
+        const double inv_n = 1.0 / n;
         int first = n * (n + 1) * (n + 2) / 6, last = (n + 1) * (n + 2) * (n + 3) / 6;
         for (int g = first + threadIdx.x; g < last; g += blockDim.x) {
             int kk[3] = {mi[3 * g], mi[3 * g + 1], mi[3 * g + 2]};
@@ -145,9 +147,9 @@ __device__ inline void recur_accumulate(int P2, int np2, const int *mi, cplx k, 
                     sb = cadd(sb, b[j]);
                 }
             }
-            cplx bg = cscale(cmul(ik, cadd(sa1, sa2)), 1.0 / n);
+            cplx bg = cscale(cmul(ik, cadd(sa1, sa2)), inv_n);
             cplx num = csub(csub(cmul(ik, sb), cscale(sa1, 2.0 * n - 1.0)), cscale(sa2, n - 1.0));
-            cplx ag = cdiv(num, cscale(R2, (double)n));
+            cplx ag = cscale(cmul(num, iR2), inv_n);
             a[g] = ag;
             b[g] = bg;
         }

@@ -188,7 +188,7 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
     }
     if (r == TEFMM_OK) r = plan_upload_images(P);
     if (r == TEFMM_OK)
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 12; ++i)
             if (cudaEventCreate(&P->ev[i]) != cudaSuccess) r = TEFMM_ERR_CUDA;
     if (r != TEFMM_OK) {
         tefmm_plan_destroy(P);
@@ -216,7 +216,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
                    &P->h_in, &P->h_out, &P->tc_ah, &P->tc_al, &P->tc_bt, &P->tc_cfA, &P->tc_cfB};
     for (DBuf *b : all) dbuf_free(*b);
     cross_release(P);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 12; ++i)
         if (P->ev[i]) cudaEventDestroy(P->ev[i]);
     delete P;
     return TEFMM_OK;

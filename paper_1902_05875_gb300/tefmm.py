@@ -37,7 +37,8 @@ class Stats(ctypes.Structure):
                 ("fit_max_resid", ctypes.c_double), ("n_launches", ctypes.c_int64),
                 ("n_cross_tables", ctypes.c_int), ("n_cross_fits", ctypes.c_int),
                 ("n_cross_fits_last", ctypes.c_int), ("ms_cross_fit", ctypes.c_double),
-                ("fit_max_resid_cross", ctypes.c_double)]
+                ("fit_max_resid_cross", ctypes.c_double), ("ms_cross_tables", ctypes.c_double),
+                ("ms_cross_m2l", ctypes.c_double)]
 
 
 EXPORTED = [

@@ -102,6 +102,7 @@ def cfg_fp64_200k():
 
 
 def cfg_mixed_2m():
-    """2M points over three layers, k = (2, 3, 4 + 0.01i), p = 10, leaf cap 64."""
-    return three_layer_slabs(2_000_000, 10, 64, seed=0, n_images=8,
+    """2M points over three layers, k = (2, 3, 4 + 0.01i), p = 10, leaf cap 64,
+    16 images per fit (the cross-layer fits need them for ~1e-7 accuracy)."""
+    return three_layer_slabs(2_000_000, 10, 64, seed=0, n_images=16,
                              name="three_layer_slabs_n2M_p10")

@@ -96,7 +96,7 @@ def test_cross_device_fits_against_quadrature():
     for i in rng.choice(len(keys), min(12, len(keys)), replace=False):
         lt, ls, part, lev, izs, k3p = keys[i]
         A, Z = xi[keys[i]]
-        zc = lo[2] + (izs + 0.5) * side / 2 ** lev
+        zc = min(max(lo[2] + (izs + 0.5) * side / 2 ** lev, w.zext[ls][0]), w.zext[ls][1])
         wmin = W_min(med, lt, part, w.zext)
         r = np.r_[0.3, -0.2, np.mean(w.zext[lt])]
         rp = np.r_[-0.1, 0.2, zc]

@@ -28,7 +28,7 @@ import pytest
 from oracle.medium import Medium
 from oracle.dcim import ImageTable
 from oracle.cross import CrossDirect, fit_cross, image_sum, W_min
-from oracle.direct import direct_sum
+from oracle.direct import direct_sum, cross_sum_by_reciprocity
 from oracle.sommerfeld import reaction_derivative
 from oracle.tefmm import TEFMM, Trees, build_lists
 from paper_1902_05875_gb300 import workloads as W
@@ -185,3 +185,14 @@ def test_cross_split_rule_lists_partition_pairs():
                 for s in lst:
                     cover[np.ix_(tr.tperm[tr.t0[t]:tr.t1[t]], tr.sperm[tr.s0[s]:tr.s1[s]])] += 1
     assert np.all(cover == 1), (cover.min(), cover.max())
+
+
+def test_cross_sum_by_reciprocity_matches_per_source_fits():
+    """One fit per target (reciprocity) and one fit per source give the same
+    cross-layer field (up to the fits' accuracy)."""
+    w = W.cross_layer_slabs(25, 0, 5, seed=5)
+    med = Medium(w.interfaces, w.k)
+    tgt = w.src[::4]
+    a = CrossDirect(med, w.zext, n_images=16).potential(w.src, w.q, tgt)
+    b = cross_sum_by_reciprocity(med, w.zext, w.src, w.q, tgt, n_images=16)
+    assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(a), np.linalg.norm(a - b) / np.linalg.norm(a)
