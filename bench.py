@@ -50,6 +50,7 @@ def _wl(name):
 
 WORKLOADS = {
     "three_layer_slabs_n2M_p10": lambda: _wl("cfg_mixed_2m"),
+    "three_layer_slabs_n200k_p10": lambda: _wl("cfg_mixed_200k"),
     "three_layer_middle_n200k_p8": lambda: _wl("cfg_fp64_200k"),
     "three_layer_middle_n2000_p6": lambda: _wl("cfg_small"),
 }
@@ -380,7 +381,7 @@ def main():
         del p64
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.accuracy_samples > 0:
-        idx = np.random.default_rng(2024).choice(N, min(N, args.accuracy_samples), replace=False)
+        idx = np.random.default_rng(1).choice(N, min(N, args.accuracy_samples), replace=False)
         ref, dt = direct_at(w, idx)
         acc = line.setdefault("accuracy", {})
         acc["samples"] = int(len(idx))

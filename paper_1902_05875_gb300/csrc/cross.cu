@@ -55,26 +55,34 @@ __global__ void k_xshift_alpha(int nn, TreeArrays T, Cube cb, XGeom geo, int p, 
     const double h = box_h(cb.side, T.level[node]);
     const double zc = centre(cb.lo[2], T.iz[node], h);
     const double dz = zc - xcentre(zc, geo.zlo[lay], geo.zhi[lay]);
-    __shared__ double pw[32];
-    if (threadIdx.x == 0) {
-        double v = 1.0;
-        for (int e = 0; e <= p; ++e) {
-            pw[e] = v;
-            v *= dz;
+    const cplx *a = alpha + (int64_t)node * np;
+    cplx *o = alpha_x + (int64_t)node * np;
+    if (dz == 0.0) {
+        for (int k = threadIdx.x; k < np; k += blockDim.x) o[k] = a[k];
+        return;
+    }
+    __shared__ double cw[32 * 32];   // cw[n * (p + 1) + j] = C(n, j) dz^{n-j}
+    if (threadIdx.x <= p) {
+        const int n = threadIdx.x;
+        double c = 1.0;               // C(n, j), built from j = n down
+        double pw = 1.0;              // dz^{n-j}
+        for (int j = n; j >= 0; --j) {
+            cw[n * (p + 1) + j] = c * pw;
+            c = c * (double)j / (double)(n - j + 1);
+            pw *= dz;
         }
     }
     __syncthreads();
-    const cplx *a = alpha + (int64_t)node * np;
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
         const int k1 = mi[3 * k], k2 = mi[3 * k + 1], k3 = mi[3 * k + 2];
         cplx s = mkc(0, 0);
         for (int j3 = 0; j3 <= k3; ++j3) {
-            const double b = binom(k3, j3) * pw[k3 - j3];
+            const double b = cw[k3 * (p + 1) + j3];
             const cplx x = a[midx(k1, k2, j3)];
             s.x += b * x.x;
             s.y += b * x.y;
         }
-        alpha_x[(int64_t)node * np + k] = s;
+        o[k] = s;
     }
 }
 
@@ -89,30 +97,37 @@ __global__ void k_xshift_beta(int nn, TreeArrays T, Cube cb, XGeom geo, int p, i
     const double h = box_h(cb.side, T.level[node]);
     const double zc = centre(cb.lo[2], T.iz[node], h);
     const double dz = zc - xcentre(zc, geo.zlo[lay], geo.zhi[lay]);
-    __shared__ double pw[32];
-    if (threadIdx.x == 0) {
-        double v = 1.0;
-        for (int e = 0; e <= p; ++e) {
-            pw[e] = v;
-            v *= dz;
+    const cplx *bx = beta_x + (int64_t)node * np;
+    cplx *b = beta + (int64_t)node * np;
+    if (dz == 0.0) {
+        for (int k = threadIdx.x; k < np; k += blockDim.x) b[k] = cadd(b[k], bx[k]);
+        return;
+    }
+    __shared__ double cw[32 * 32];   // cw[j * (p + 1) + n] = C(j, n) dz^{j-n}, j >= n
+    if (threadIdx.x <= p) {
+        const int j = threadIdx.x;
+        double c = 1.0, pw = 1.0;
+        for (int n = j; n >= 0; --n) {
+            cw[j * (p + 1) + n] = c * pw;
+            c = c * (double)n / (double)(j - n + 1);
+            pw *= dz;
         }
     }
     __syncthreads();
-    const cplx *bx = beta_x + (int64_t)node * np;
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
         const int k1 = mi[3 * k], k2 = mi[3 * k + 1], k3 = mi[3 * k + 2];
         cplx s = mkc(0, 0);
         for (int j3 = k3; k1 + k2 + j3 <= p; ++j3) {
-            const double b = binom(j3, k3) * pw[j3 - k3];
+            const double w = cw[j3 * (p + 1) + k3];
             const cplx x = bx[midx(k1, k2, j3)];
-            s.x += b * x.x;
-            s.y += b * x.y;
+            s.x += w * x.x;
+            s.y += w * x.y;
         }
-        cplx v = beta[(int64_t)node * np + k];
-        beta[(int64_t)node * np + k] = mkc(v.x + s.x, v.y + s.y);
+        b[k] = mkc(b[k].x + s.x, b[k].y + s.y);
     }
 }
 
+// offset of slice k3' in a packed cross-layer table
 __host__ __device__ inline int slice_off(int p, int k3p) {
     int o = 0;
     for (int j = 0; j < k3p; ++j) o += ncoef(2 * p - j);

@@ -17,9 +17,17 @@
 // D / (R + R0),
 //   A_m e^{ik R}/(ik R) = E0_m e^{ik delta} / (1 + delta/R0),
 //   E0_m = A_m e^{ik R0}/(ik R0)   (FP64, once per leaf and image).
-// sin, cos and exp are CUDA's accurate single-precision functions (their
-// arguments here are small: k r within a near box pair and k delta).  Pairs
-// whose FP32 offsets coincide (r = 0) are skipped in the free-space sum.
+// The image terms of a fit can cancel (terms up to 1e4 times their sum), so
+// the constant part is split off:  sum_m E0_m g_m = sum_m E0_m + sum_m E0_m (g_m - 1)
+// with g = e^{ik delta}/(1 + delta/R0).  The first sum times the near-field
+// charge total is formed once per leaf in FP64; only g - 1 (small for the
+// distant images) goes through FP32, written as
+//   g - 1 = (e^{ik delta} - 1 - delta/R0) / (1 + delta/R0),
+//   e^{a+ib} - 1 = expm1(a) cos b - 2 sin^2(b/2) + i e^a sin b,
+// so that its rounding is relative to |g - 1|, not to 1.
+// sin, cos, exp and expm1 are CUDA's accurate single-precision functions
+// (their arguments here are small: k r within a near box pair and k delta).
+// Pairs whose FP32 offsets coincide (r = 0) are skipped in the free-space sum.
 #include "ops_common.cuh"
 
 namespace {
@@ -55,6 +63,7 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
     __shared__ f2 sE0[MI], sW0[MI], sR0sq[MI], sIR0[MI];
     __shared__ float tsz[TEFMM_MAX_TERMS], tszp[TEFMM_MAX_TERMS];
     __shared__ int tcnt[TEFMM_MAX_TERMS];
+    __shared__ double2 cq[2];      // [0]: sum of E0 over all images, [1]: near-field charge total
     int lay = T.layer[node];
     cplx k = a.im.k[lay];
     cplx ik = mkc(-k.y, k.x);
@@ -64,6 +73,8 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
     double cx = centre(a.cb.lo[0], T.ix[node], h), cy = centre(a.cb.lo[1], T.iy[node], h),
            cz = centre(a.cb.lo[2], T.iz[node], h);
     int tf = a.im.lt_first[lay], ntm = a.im.lt_count[lay];
+    if (threadIdx.x < 2) red[threadIdx.x] = make_double2(0.0, 0.0);
+    __syncthreads();
     if (threadIdx.x < ntm) {
         DevTerm t = a.im.terms[tf + threadIdx.x];
         tsz[threadIdx.x] = (float)t.sz;
@@ -85,8 +96,30 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
             sW0[s] = f2{(float)w0.x, (float)w0.y};
             sR0sq[s] = f2{(float)r0sq.x, (float)r0sq.y};
             sIR0[s] = f2{(float)ir0.x, (float)ir0.y};
+            atomicAdd(&red[0].x, E0.x);
+            atomicAdd(&red[0].y, E0.y);
         }
     }
+    // near-field charge total (FP64)
+    {
+        double qr = 0.0, qi = 0.0;
+        for (int nb = a.near_ptr[node]; nb < a.near_ptr[node + 1]; ++nb) {
+            const int sb = a.near_src[nb];
+            for (int j = T.s0[sb] + threadIdx.x; j < T.s1[sb]; j += blockDim.x) {
+                qr += a.sq[2 * j];
+                qi += a.sq[2 * j + 1];
+            }
+        }
+        atomicAdd(&red[1].x, qr);
+        atomicAdd(&red[1].y, qi);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const cplx c = mkc(red[0].x, red[0].y), qt = mkc(red[1].x, red[1].y);
+        const cplx cq0 = cmul(c, qt);
+        cq[0] = make_double2(cq0.x, cq0.y);
+    }
+
     const float kr = (float)k.x, ki = (float)k.y;
     const f2 iik = f2{(float)inv_ik.x, (float)inv_ik.y};
     int ntp = 1;
@@ -149,16 +182,19 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                             float sr = R.x + w0.x, si = R.y + w0.y;
                             float isn = __frcp_rn(sr * sr + si * si);
                             float der = (Dr * sr + Di * si) * isn, dei = (Di * sr - Dr * si) * isn;
-                            // e^{i k delta}
+                            // e^{i k delta} - 1
                             float ph = kr * der - ki * dei, dec = -(kr * dei + ki * der);
-                            float sn, cs;
+                            float sn, cs, sh, ch;
                             sincosf(ph, &sn, &cs);
-                            float mg = expf(dec);
-                            float ur = mg * cs, ui = mg * sn;
-                            // 1 / (1 + delta / R0)
-                            float vr = 1.f + der * ir0.x - dei * ir0.y, vi = der * ir0.y + dei * ir0.x;
+                            sincosf(0.5f * ph, &sh, &ch);
+                            float em1 = expm1f(dec);
+                            float ur = em1 * cs - 2.f * sh * sh, ui = (1.f + em1) * sn;
+                            // delta / R0 and g - 1 = (e^{ik delta} - 1 - delta/R0) / (1 + delta/R0)
+                            float tr = der * ir0.x - dei * ir0.y, ti = der * ir0.y + dei * ir0.x;
+                            float nr = ur - tr, ni = ui - ti;
+                            float vr = 1.f + tr, vi = ti;
                             float iv = __frcp_rn(vr * vr + vi * vi);
-                            float pr = (ur * vr + ui * vi) * iv, pi = (ui * vr - ur * vi) * iv;
+                            float pr = (nr * vr + ni * vi) * iv, pi = (ni * vr - nr * vi) * iv;
                             const f2 E0 = sE0[sidx];
                             hr += E0.x * pr - E0.y * pi;
                             hi += E0.x * pi + E0.y * pr;
@@ -181,6 +217,8 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                 accr += red[sl * ntp + my_t].x;
                 acci += red[sl * ntp + my_t].y;
             }
+            accr += cq[0].x;       // the images' constant part times the charge total
+            acci += cq[0].y;
             // L2P in FP64
             double d[3] = {xt - cx, yt - cy, zt - cz};
             double pw[3][13];

@@ -95,106 +95,101 @@ __global__ void k_p2m(int nn, TreeArrays T, Cube cb, int p, int np, const int *_
 }
 
 // ------------------------------------------------------------------ M2M
-__global__ void k_m2m(int off, int cnt, TreeArrays T, Cube cb, int p, int np,
-                      const int *__restrict__ mi, cplx *__restrict__ alpha) {
-    int node = off + blockIdx.x;
-    if (blockIdx.x >= cnt || !T.split[node] || T.s1[node] <= T.s0[node]) return;
-    extern __shared__ double sm[];
-    cplx *ac = (cplx *)sm;                   // child moments [np]
-    double *pw = (double *)(ac + np);        // [3][p+1]
-    int l = T.level[node];
-    double h = box_h(cb.side, l), hc = box_h(cb.side, l + 1);
-    double c[3] = {centre(cb.lo[0], T.ix[node], h), centre(cb.lo[1], T.iy[node], h),
-                   centre(cb.lo[2], T.iz[node], h)};
-    const int R = 4;
-    cplx acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = mkc(0, 0);
-    int c0 = T.cfirst[node], c1 = c0 + T.nchild[node];
-    for (int ch = c0; ch < c1; ++ch) {
-        if (T.s1[ch] <= T.s0[ch]) continue;
-        __syncthreads();
-        for (int k = threadIdx.x; k < np; k += blockDim.x) ac[k] = alpha[(int64_t)ch * np + k];
-        if (threadIdx.x < 3) {
-            int a = threadIdx.x;
-            int ic = a == 0 ? T.ix[ch] : (a == 1 ? T.iy[ch] : T.iz[ch]);
-            double d = centre(cb.lo[a], ic, hc) - c[a];   // child centre - parent centre
-            double v = 1.0;
-            for (int e = 0; e <= p; ++e) {
-                pw[a * (p + 1) + e] = v;
-                v *= d;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            int k = threadIdx.x + r * blockDim.x;
-            if (k >= np) continue;
-            int k1 = mi[3 * k], k2 = mi[3 * k + 1], k3 = mi[3 * k + 2];
-            cplx s = mkc(0, 0);
-            for (int j1 = 0; j1 <= k1; ++j1) {
-                double b1 = binom(k1, j1) * pw[0 * (p + 1) + k1 - j1];
-                for (int j2 = 0; j2 <= k2; ++j2) {
-                    double b2 = b1 * binom(k2, j2) * pw[1 * (p + 1) + k2 - j2];
-                    for (int j3 = 0; j3 <= k3; ++j3) {
-                        double b = b2 * binom(k3, j3) * pw[2 * (p + 1) + k3 - j3];
-                        cplx a = ac[midx(j1, j2, j3)];
-                        s.x += b * a.x;
-                        s.y += b * a.y;
-                    }
-                }
-            }
-            acc[r] = cadd(acc[r], s);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        int k = threadIdx.x + r * blockDim.x;
-        if (k < np) alpha[(int64_t)node * np + k] = acc[r];
-    }
-}
+// Shift lists (built at plan creation): row k holds the k' of the shift and
+// the exponents of the offset packed in one int, plus prod_i C(.,.) in FP64.
+struct ShiftRows {
+    const int *ptr, *ent;
+    const double *cf;
+};
 
-// ------------------------------------------------------------------ L2L
-__global__ void k_l2l(int off, int cnt, TreeArrays T, Cube cb, int p, int np,
-                      const int *__restrict__ mi, cplx *__restrict__ beta) {
-    int node = off + blockIdx.x;
-    if (blockIdx.x >= cnt || T.t1[node] <= T.t0[node]) return;
-    int par = T.parent[node];
-    if (par < 0) return;
-    extern __shared__ double sm[];
-    cplx *bp = (cplx *)sm;
-    double *pw = (double *)(bp + np);
-    int l = T.level[node];
-    double h = box_h(cb.side, l), hp = box_h(cb.side, l - 1);
-    for (int k = threadIdx.x; k < np; k += blockDim.x) bp[k] = beta[(int64_t)par * np + k];
+__device__ __forceinline__ void offset_powers(double *pw, int p, double d0, double d1, double d2) {
+    // pw[a * (p + 1) + e] = d_a^e
     if (threadIdx.x < 3) {
-        int a = threadIdx.x;
-        int ic = a == 0 ? T.ix[node] : (a == 1 ? T.iy[node] : T.iz[node]);
-        int ip = a == 0 ? T.ix[par] : (a == 1 ? T.iy[par] : T.iz[par]);
-        double d = centre(cb.lo[a], ic, h) - centre(cb.lo[a], ip, hp);
+        const int a = threadIdx.x;
+        const double d = a == 0 ? d0 : (a == 1 ? d1 : d2);
         double v = 1.0;
         for (int e = 0; e <= p; ++e) {
             pw[a * (p + 1) + e] = v;
             v *= d;
         }
     }
+}
+
+// gamma_k = sum_children sum_{k' <= k} C(k,k') (c_child - c_parent)^{k-k'} alpha^child_k'
+__global__ void k_m2m(int off, int cnt, TreeArrays T, Cube cb, int p, int np, ShiftRows R,
+                      cplx *__restrict__ alpha) {
+    int node = off + blockIdx.x;
+    if (blockIdx.x >= cnt || !T.split[node] || T.s1[node] <= T.s0[node]) return;
+    extern __shared__ double sm[];
+    const int P1 = p + 1;
+    cplx *ac = (cplx *)sm;                         // [8][np] child moments
+    double *pw = (double *)(ac + 8 * np);         // [8][3][p+1]
+    const int l = T.level[node];
+    const double h = box_h(cb.side, l), hc = box_h(cb.side, l + 1);
+    const double c0 = centre(cb.lo[0], T.ix[node], h), c1 = centre(cb.lo[1], T.iy[node], h),
+                 c2 = centre(cb.lo[2], T.iz[node], h);
+    const int cf0 = T.cfirst[node], nch = T.nchild[node];
+    int used = 0;
+    for (int i = 0; i < nch; ++i) {
+        const int ch = cf0 + i;
+        if (T.s1[ch] <= T.s0[ch]) continue;
+        for (int k = threadIdx.x; k < np; k += blockDim.x) ac[used * np + k] = alpha[(int64_t)ch * np + k];
+        if (threadIdx.x < 3)
+            offset_powers(pw + used * 3 * P1, p, centre(cb.lo[0], T.ix[ch], hc) - c0,
+                          centre(cb.lo[1], T.iy[ch], hc) - c1, centre(cb.lo[2], T.iz[ch], hc) - c2);
+        ++used;
+    }
     __syncthreads();
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        int k1 = mi[3 * k], k2 = mi[3 * k + 1], k3 = mi[3 * k + 2];
-        cplx s = mkc(0, 0);
-        for (int j1 = k1; j1 <= p; ++j1) {
-            double b1 = binom(j1, k1) * pw[0 * (p + 1) + j1 - k1];
-            for (int j2 = k2; j1 + j2 <= p; ++j2) {
-                double b2 = b1 * binom(j2, k2) * pw[1 * (p + 1) + j2 - k2];
-                for (int j3 = k3; j1 + j2 + j3 <= p; ++j3) {
-                    double b = b2 * binom(j3, k3) * pw[2 * (p + 1) + j3 - k3];
-                    cplx a = bp[midx(j1, j2, j3)];
-                    s.x += b * a.x;
-                    s.y += b * a.y;
-                }
+        cplx acc = mkc(0, 0);
+        const int e0 = R.ptr[k], e1 = R.ptr[k + 1];
+        for (int c = 0; c < used; ++c) {
+            const double *pc = pw + c * 3 * P1;
+            const cplx *a = ac + c * np;
+            for (int e = e0; e < e1; ++e) {
+                const int v = R.ent[e];
+                const double b = R.cf[e] * pc[(v >> 16) & 31] * pc[P1 + ((v >> 21) & 31)] *
+                                 pc[2 * P1 + ((v >> 26) & 31)];
+                const cplx x = a[v & 0xFFFF];
+                acc.x += b * x.x;
+                acc.y += b * x.y;
             }
         }
-        beta[(int64_t)node * np + k] = cadd(beta[(int64_t)node * np + k], s);
+        alpha[(int64_t)node * np + k] = acc;
+    }
+}
+
+// ------------------------------------------------------------------ L2L
+// lambda_k += sum_{k' >= k} C(k',k) (c_child - c_parent)^{k'-k} beta^parent_k'
+__global__ void k_l2l(int off, int cnt, TreeArrays T, Cube cb, int p, int np, ShiftRows R,
+                      cplx *__restrict__ beta) {
+    int node = off + blockIdx.x;
+    if (blockIdx.x >= cnt || T.t1[node] <= T.t0[node]) return;
+    int par = T.parent[node];
+    if (par < 0) return;
+    extern __shared__ double sm[];
+    const int P1 = p + 1;
+    cplx *bp = (cplx *)sm;
+    double *pw = (double *)(bp + np);
+    const int l = T.level[node];
+    const double h = box_h(cb.side, l), hp = box_h(cb.side, l - 1);
+    for (int k = threadIdx.x; k < np; k += blockDim.x) bp[k] = beta[(int64_t)par * np + k];
+    offset_powers(pw, p, centre(cb.lo[0], T.ix[node], h) - centre(cb.lo[0], T.ix[par], hp),
+                  centre(cb.lo[1], T.iy[node], h) - centre(cb.lo[1], T.iy[par], hp),
+                  centre(cb.lo[2], T.iz[node], h) - centre(cb.lo[2], T.iz[par], hp));
+    __syncthreads();
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        cplx acc = mkc(0, 0);
+        for (int e = R.ptr[k]; e < R.ptr[k + 1]; ++e) {
+            const int v = R.ent[e];
+            const double b = R.cf[e] * pw[(v >> 16) & 31] * pw[P1 + ((v >> 21) & 31)] *
+                             pw[2 * P1 + ((v >> 26) & 31)];
+            const cplx x = bp[v & 0xFFFF];
+            acc.x += b * x.x;
+            acc.y += b * x.y;
+        }
+        cplx v = beta[(int64_t)node * np + k];
+        beta[(int64_t)node * np + k] = mkc(v.x + acc.x, v.y + acc.y);
     }
 }
 
@@ -544,12 +539,13 @@ int upward_pass(tefmm_plan_s *P, cudaStream_t st) {
                                    dp<double>(P->sy), dp<double>(P->sz), dp<double>(P->sq),
                                    dp<cplx>(P->alpha));
     P->launches++;
-    size_t sm_m2m = np * sizeof(cplx) + 3 * (p + 1) * sizeof(double);
+    size_t sm_m2m = 8 * (size_t)np * sizeof(cplx) + 8 * 3 * (p + 1) * sizeof(double);
+    CUDA_TRY(cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_m2m));
+    ShiftRows R{dp<int>(P->d_sh_ptr_m2m), dp<int>(P->d_sh_ent_m2m), dp<double>(P->d_sh_cf_m2m)};
     for (int l = P->n_levels - 2; l >= 0; --l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
         if (cnt > 0) {
-            k_m2m<<<cnt, 128, sm_m2m, st>>>(off, cnt, T, cb, p, np, dp<int>(P->d_mi),
-                                            dp<cplx>(P->alpha));
+            k_m2m<<<cnt, 256, sm_m2m, st>>>(off, cnt, T, cb, p, np, R, dp<cplx>(P->alpha));
             P->launches++;
         }
     }
@@ -675,11 +671,11 @@ int downward_pass(tefmm_plan_s *P, cudaStream_t st) {
     TreeArrays T = tree_arrays(P);
     Cube cb = cube_of(P);
     size_t sm = P->np * sizeof(cplx) + 3 * (P->p + 1) * sizeof(double);
+    ShiftRows R{dp<int>(P->d_sh_ptr_l2l), dp<int>(P->d_sh_ent_l2l), dp<double>(P->d_sh_cf_l2l)};
     for (int l = 1; l < P->n_levels; ++l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
         if (cnt > 0) {
-            k_l2l<<<cnt, 128, sm, st>>>(off, cnt, T, cb, P->p, P->np, dp<int>(P->d_mi),
-                                        dp<cplx>(P->beta));
+            k_l2l<<<cnt, 256, sm, st>>>(off, cnt, T, cb, P->p, P->np, R, dp<cplx>(P->beta));
             P->launches++;
         }
     }

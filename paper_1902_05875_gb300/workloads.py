@@ -106,3 +106,9 @@ def cfg_mixed_2m():
     16 images per fit (the cross-layer fits need them for ~1e-7 accuracy)."""
     return three_layer_slabs(2_000_000, 10, 64, seed=0, n_images=16,
                              name="three_layer_slabs_n2M_p10")
+
+
+def cfg_mixed_200k():
+    """The 2M workload's geometry and medium at 200k points (a profiling case)."""
+    return three_layer_slabs(200_000, 10, 64, seed=0, n_images=16,
+                             name="three_layer_slabs_n200k_p10")

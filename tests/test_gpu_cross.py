@@ -133,7 +133,7 @@ def test_cross_mixed_close_to_fp64_form():
     b = gpu_eval(pmx, torch, w.src, w.q)
     err = np.linalg.norm(a - b) / np.linalg.norm(a)
     print(f'cross-layer mixed vs fp64 form: {err:.3e}')
-    assert err < 2e-6, err
+    assert err < 1.5e-6, err      # measured 7.2e-7
 
 
 def test_cross_fit_cache():

@@ -1,10 +1,13 @@
 """Mixed-precision form (``precision=MIXED``) against the FP64 oracle (``-m gpu``).
 
 The mixed form evaluates the near-field pairs in FP32 (FP64 per-target
-accumulation) and the M2L contractions on the tensor cores in 3xTF32 with FP32
-accumulation; tables, P2M/M2M/L2L and L2P stay in FP64.  Measured rounding
-of the mixed form: about 1e-6 relative, almost all of it from the FP32
-accumulation of the M2L contractions (K = 2 n_p terms per output).
+accumulation, the images' constant part in FP64) and the M2L contractions on
+the tensor cores in 3xTF32 with FP32 accumulation (highest orders first);
+tables, P2M/M2M/L2L and L2P stay in FP64.  Measured rounding of the mixed form
+on GB300: 8e-8 (2000 points, p = 6) and 1.8e-7 (3001 points, p = 5) against
+the FP64 form; at the 20k sampled targets 2.5e-7 against the direct sum (FP64
+form 1.8e-7), almost all of it from the FP32 accumulation of the M2L
+contractions.
 """
 import numpy as np
 import pytest
@@ -31,7 +34,7 @@ def test_mixed_close_to_fp64_form(w):
     b = gpu_eval(pmx, torch, w.src, w.q)
     err = np.linalg.norm(a - b) / np.linalg.norm(a)
     print(f'mixed vs fp64 form ({w.name}): {err:.3e}')
-    assert err < 2e-6, err
+    assert err < 5e-7, err
 
 
 def test_mixed_vs_direct_sum_at_sampled_targets():
@@ -76,7 +79,7 @@ def test_mixed_vs_direct_sum_at_sampled_targets():
     e_tot = np.linalg.norm(b[sel] - a[sel]) / np.linalg.norm(a[sel])
     e_near = np.linalg.norm(b[sel] - a[sel] - dm2l) / np.linalg.norm(a[sel])
     print(f'mixed - fp64 at samples: total {e_tot:.3e}, from M2L {e_m2l:.3e}, near field {e_near:.3e}')
-    assert emx < e64 + 1.5e-6, (emx, e64)
+    assert emx < e64 + 3e-7, (emx, e64)
 
 
 @pytest.mark.parametrize("w", [W.cfg_small(), W.middle_layer_uniform(20000, 8, 64, seed=7)],
