@@ -457,7 +457,7 @@ int cross_apply(tefmm_plan_s *P, cudaStream_t st) {
     k_xshift_alpha<<<nn, 128, 0, st>>>(nn, T, cb, geo, P->p, np, dp<int>(P->d_mi), dp<cplx>(P->alpha),
                                        dp<cplx>(P->xalpha));
     P->launches++;
-    if (P->opt.precision == TEFMM_MIXED && m2l_tc_smem(np, P->NX) <= 227 * 1024) {
+    if (P->opt.precision == TEFMM_MIXED && m2l_tc_smem(np, TC_MT_CROSS, P->NX) + 8 * 1024 <= 227 * 1024) {
         // mixed form: the cross-layer contraction on the tensor cores (3xTF32)
         TRY(m2l_apply_tc_cross(P, st, dp<cplx>(P->xalpha), dp<cplx>(P->xbeta),
                                dp<unsigned short>(P->tc_xgs), dp<float>(P->tc_xcf32)));

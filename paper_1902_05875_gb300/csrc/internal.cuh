@@ -176,7 +176,7 @@ struct tefmm_plan_s {
         pair_idx_sorted, chunk_key, chunk_start, chunk_cnt, tables, table_slot, seg_tmp;
     int n_tables = 0;
     int64_t n_chunks = 0;
-    int chunk_pairs = 16;     // pairs per M2L work chunk (FP64 SIMT: 16, tensor cores: 128)
+    int chunk_pairs = 16;     // pairs per M2L work chunk (FP64 SIMT: 16, tensor cores: 512)
 
     // cross-layer components: fitted images (cached per root-cube geometry),
     // per-table image ranges and tables
@@ -246,8 +246,10 @@ int m2l_apply(tefmm_plan_s *P, cudaStream_t st);
 int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st);
 int m2l_apply_tc_cross(tefmm_plan_s *P, cudaStream_t st, const cplx *alpha_x, cplx *beta_x,
                        const unsigned short *xgs, const float *xcf);
-size_t m2l_tc_smem(int np, int tab_entries);
-void m2l_tc_geometry(int np, int *Kpad, int *Ncta, int *nsplit, int *nblk);
+size_t m2l_tc_smem(int np, int MT, int tab_entries);
+void m2l_tc_geometry(int np, int MT, int *Kpad, int *Ncta, int *nsplit);
+#define TC_MT 4         // tiles of 128 pairs per pass, same-layer keys (128 output columns per CTA)
+#define TC_MT_CROSS 2   // cross-layer keys (256 output columns per CTA; larger table in smem)
 int downward_pass(tefmm_plan_s *P, cudaStream_t st);
 int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st);
 // near32.cu

@@ -42,12 +42,14 @@ struct TcArgs {
     const unsigned short *G;     // [k'][k]
     const float *cfA, *cfB;      // [k'][k] coefficients with signs
     const int *mi;
-    int np, np2, Kpad, Ncta, Ntot, nblk;
+    int np, np2, Kpad, Ncta, Ntot, nblk;   // nblk: unused (1)
     double side;
     int *flags;
     // table layout: tables + (tb - tab_base) * tab_stride; xmode: cross-layer
     // tables (p + 1 slices of orders 2p - k3', entry scaled by h^{|g| + k3'})
     int tab_base, tab_stride, xmode, p;
+    int MT;                      // tiles of 128 pairs per pass (MT * Ncta = 512 TMEM columns)
+    int nsplit;                  // column slices per chunk
 };
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -87,20 +89,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
+// One CTA: one chunk of up to chunk_pairs pairs of one key, and one slice of
+// NC output columns.  The chunk is taken in passes of MT tiles of TM = 128
+// pairs; TMEM holds one 128 x NC FP32 accumulator per tile (MT * NC = 512
+// columns).  Every K slice of W^T (NC x 16, generated from the table once per
+// pass) therefore serves MT * 128 pairs.
 __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
-    const int c = blockIdx.x;
-    const int half = blockIdx.y;
+    // 1-D grid: the nsplit column slices of one chunk are adjacent blocks, so
+    // they run together and share the chunk's moment rows through L2
+    const int c = blockIdx.x / a.nsplit;
+    const int slice = blockIdx.x % a.nsplit;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int MT = a.MT, NC = a.Ncta;
     extern __shared__ __align__(1024) unsigned char smem[];
-    // layout: [2 buffers][Xh | Xl | Wh | Wl] then table
-    const int xbytes = TM * KC * 4;
-    const int wbytes = a.Ncta * KC * 4;
+    // layout: [2 buffers][Xh (MT tiles) | Xl (MT tiles) | Wh | Wl] then table
+    const int tbytes = TM * KC * 4;                 // one X tile
+    const int xbytes = MT * tbytes;
+    const int wbytes = NC * KC * 4;
     const int bufbytes = 2 * xbytes + 2 * wbytes;
     unsigned char *buf0 = smem;
     float2 *tab = (float2 *)(smem + 2 * bufbytes);
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_src[TM], s_tgt[TM];
+    __shared__ int s_src[4 * TM], s_tgt[4 * TM];
     __shared__ int s_fail;
 
     const int tb = a.chunk_table[c];
@@ -113,16 +124,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     const float *cf = kind == 0 ? a.cfB : a.cfA;
 
     if (tid == 0) s_fail = 0;
-    if (tid < TM) {
-        if (tid < cnt) {
-            int e = a.items[st + tid] >> 1;
-            s_src[tid] = a.v_src[e];
-            s_tgt[tid] = a.pair_t[e];
-        } else {
-            s_src[tid] = -1;
-            s_tgt[tid] = -1;
-        }
-    }
     // scaled table T~_g = T_g h^{|g|} in FP32 (cross-layer: h^{|g| + k3'} in slice k3')
     {
         const cplx *T = a.tables + (int64_t)(tb - a.tab_base) * a.tab_stride;
@@ -154,116 +155,138 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    const int nblk = a.nblk, blkN = a.Ncta / nblk;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(blkN >> 3) << 17) |
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NC >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
     const int nk = a.Kpad / KC;
     const int np = a.np;
-    const int n0 = half * a.Ncta;       // first output column of this CTA
+    const int n0 = slice * NC;             // first output column of this CTA
     bool ok = true;
+    int gch = 0;                           // K chunks issued so far (all passes): buffer and phase
 
-    for (int ch = 0; ch < nk; ++ch) {
-        const int b = ch & 1;
-        unsigned char *buf = buf0 + b * bufbytes;
-        unsigned char *Xh = buf, *Xl = buf + xbytes, *Wh = buf + 2 * xbytes, *Wl = buf + 2 * xbytes + wbytes;
-        if (ch >= 2) {
-            if (!mbar_wait(su32(&mbar[b]), ((ch - 2) >> 1) & 1)) ok = false;
-        }
-        const int c0 = ch * KC;
-        // X^T slice: rows = pairs, 16 K columns, hi and lo (16-byte pieces)
-        for (int i = tid; i < TM * 4 * 2; i += NTHR) {
-            int part = i / (TM * 4), rem = i % (TM * 4);
-            int r = rem >> 2, q = rem & 3;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            int s = s_src[r];
-            if (s >= 0) {
-                const float *srcp = (part == 0 ? a.ah : a.al) + (int64_t)s * a.Kpad + c0 + 4 * q;
-                v = *reinterpret_cast<const float4 *>(srcp);
+    for (int pb = 0; pb < cnt; pb += MT * TM) {
+        const int npair = min(MT * TM, cnt - pb);
+        const int ntile = (npair + TM - 1) / TM;
+        for (int r = tid; r < MT * TM; r += NTHR) {
+            if (r < npair) {
+                int e = a.items[st + pb + r] >> 1;
+                s_src[r] = a.v_src[e];
+                s_tgt[r] = a.pair_t[e];
+            } else {
+                s_src[r] = -1;
+                s_tgt[r] = -1;
             }
-            *reinterpret_cast<float4 *>((part == 0 ? Xh : Xl) + koff(r, 4 * q)) = v;
         }
-        // W^T slice: rows = output columns n, 16 K columns
-        for (int i = tid; i < a.Ncta * KC; i += NTHR) {
-            int nl = i / KC, kk = i % KC;
-            int n = n0 + nl, col = c0 + kk;
-            float w = 0.f;
-            if (n < 2 * np && col < 2 * np) {
-                int k = n < np ? n : n - np, po = n < np ? 0 : 1;
-                int kp = np - 1 - (col >> 1), pi = col & 1;     // K order: see kcol()
-                int64_t o = (int64_t)kp * np + k;
-                float cfv = cf[o];
-                float2 t = tab[a.G[o]];
-                float hr = cfv * t.x, hi = cfv * t.y;
-                // [[Re H, -Im H], [Im H, Re H]]
-                w = (po == pi) ? hr : (po == 0 ? -hi : hi);
-            }
-            float wh = tf32_rn(w);
-            float wl = tf32_rn(w - wh);
-            *reinterpret_cast<float *>(Wh + koff(nl, kk)) = wh;
-            *reinterpret_cast<float *>(Wl + koff(nl, kk)) = wl;
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            for (int j = 0; j < KC / 8; ++j) {
-                for (int bl = 0; bl < nblk; ++bl) {
-                    uint32_t d = tmem + (uint32_t)(bl * blkN);
-                    uint32_t wo = (uint32_t)(bl * blkN / 8) * 512 + j * 256;
-                    uint64_t dxh = sdesc(su32(Xh) + j * 256), dxl = sdesc(su32(Xl) + j * 256);
-                    uint64_t dwh = sdesc(su32(Wh) + wo), dwl = sdesc(su32(Wl) + wo);
-                    uint32_t acc0 = (ch > 0 || j > 0) ? 1u : 0u;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                 :: "r"(d), "l"(dxh), "l"(dwh), "r"(idesc), "r"(acc0));
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                 :: "r"(d), "l"(dxh), "l"(dwl), "r"(idesc), "r"(1u));
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                 :: "r"(d), "l"(dxl), "l"(dwh), "r"(idesc), "r"(1u));
+        for (int ch = 0; ch < nk; ++ch, ++gch) {
+            const int b = gch & 1;
+            unsigned char *buf = buf0 + b * bufbytes;
+            unsigned char *Xh = buf, *Xl = buf + xbytes, *Wh = buf + 2 * xbytes, *Wl = buf + 2 * xbytes + wbytes;
+            if (gch >= 2) {
+                if (!mbar_wait(su32(&mbar[b]), ((gch - 2) >> 1) & 1)) ok = false;
+            }
+            const int c0 = ch * KC;
+            // X^T slices: rows = pairs (tile by tile), 16 K columns, hi and lo;
+            // asynchronous 16-byte copies (rows without a pair are zero-filled),
+            // in flight while W^T is generated
+            for (int i = tid; i < ntile * TM * 4 * 2; i += NTHR) {
+                const int part = i / (ntile * TM * 4), rem = i % (ntile * TM * 4);
+                const int r = rem >> 2, q = rem & 3;
+                const int s = s_src[r];
+                const float *srcp = s >= 0 ? (part == 0 ? a.ah : a.al) + (int64_t)s * a.Kpad + c0 + 4 * q : a.ah;
+                const uint32_t dst = su32((part == 0 ? Xh : Xl) + (r / TM) * tbytes + koff(r % TM, 4 * q));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                             :: "r"(dst), "l"(srcp), "r"(s >= 0 ? 16 : 0) : "memory");
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            // W^T slice: rows = output columns n, 16 K columns; consecutive threads
+            // take consecutive rows so that the coefficient loads are contiguous in k
+#pragma unroll 4
+            for (int i = tid; i < NC * KC; i += NTHR) {
+                const int kk = i / NC, nl = i % NC;
+                const int n = n0 + nl, col = c0 + kk;
+                float w = 0.f;
+                if (n < 2 * np && col < 2 * np) {
+                    const int k = n < np ? n : n - np, po = n < np ? 0 : 1;
+                    const int kp = np - 1 - (col >> 1), pi = col & 1;     // K order: see kcol()
+                    const int64_t o = (int64_t)kp * np + k;
+                    const float cfv = __ldg(cf + o);
+                    const float2 t = tab[__ldg(a.G + o)];
+                    const float hr = cfv * t.x, hi = cfv * t.y;
+                    // [[Re H, -Im H], [Im H, Re H]]
+                    w = (po == pi) ? hr : (po == 0 ? -hi : hi);
+                }
+                const float wh = tf32_rn(w);
+                *reinterpret_cast<float *>(Wh + koff(nl, kk)) = wh;
+                *reinterpret_cast<float *>(Wl + koff(nl, kk)) = tf32_rn(w - wh);
+            }
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                for (int mt = 0; mt < ntile; ++mt) {
+                    const uint32_t d = tmem + (uint32_t)(mt * NC);
+                    for (int j = 0; j < KC / 8; ++j) {
+                        const uint64_t dxh = sdesc(su32(Xh + mt * tbytes) + j * 256);
+                        const uint64_t dxl = sdesc(su32(Xl + mt * tbytes) + j * 256);
+                        const uint64_t dwh = sdesc(su32(Wh) + j * 256), dwl = sdesc(su32(Wl) + j * 256);
+                        const uint32_t acc0 = (ch > 0 || j > 0) ? 1u : 0u;
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                     :: "r"(d), "l"(dxh), "l"(dwh), "r"(idesc), "r"(acc0));
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                     :: "r"(d), "l"(dxh), "l"(dwl), "r"(idesc), "r"(1u));
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                     :: "r"(d), "l"(dxl), "l"(dwh), "r"(idesc), "r"(1u));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(su32(&mbar[b])) : "memory");
+            }
+        }
+        // the last commit covers every MMA issued before it
+        if (!mbar_wait(su32(&mbar[(gch - 1) & 1]), ((gch - 1) >> 1) & 1)) ok = false;
+        if (!ok) atomicExch(&s_fail, 1);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!s_fail) {
+            // epilogue: warp w reads TMEM lanes 32*(w%4).., column half w/4 of each tile
+            const int row = (warp & 3) * 32 + lane;
+            const int chalf = warp >> 2;
+            const int colw = NC / 2;
+            for (int mt = 0; mt < ntile; ++mt) {
+                const int t = s_tgt[mt * TM + row];
+                for (int cc = chalf * colw; cc < (chalf + 1) * colw; cc += 16) {
+                    uint32_t r[16];
+                    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * NC + cc);
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                                 : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (t >= 0) {
+                        float *dst = a.bt + (int64_t)t * a.Ntot + n0 + cc;
+                        for (int q = 0; q < 16; q += 4) {
+                            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                                         :: "l"(dst + q), "f"(__uint_as_float(r[q])), "f"(__uint_as_float(r[q + 1])),
+                                            "f"(__uint_as_float(r[q + 2])), "f"(__uint_as_float(r[q + 3]))
+                                         : "memory");
+                        }
+                    }
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(su32(&mbar[b])) : "memory");
         }
+        // TMEM reads of this pass done before the next pass's MMAs overwrite it
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (s_fail) break;
     }
-    // the last commit covers every MMA issued before it
-    if (!mbar_wait(su32(&mbar[(nk - 1) & 1]), ((nk - 1) >> 1) & 1)) ok = false;
-    if (!ok) atomicExch(&s_fail, 1);
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!s_fail) {
-        // epilogue: warp w reads TMEM lanes 32*(w%4).., column half w/4
-        const int row = (warp & 3) * 32 + lane;
-        const int chalf = warp >> 2;
-        const int colw = a.Ncta / 2;
-        const int t = s_tgt[row];
-        for (int cc = chalf * colw; cc < (chalf + 1) * colw; cc += 16) {
-            uint32_t r[16];
-            uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cc;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                           "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                           "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (t >= 0) {
-                float *dst = a.bt + (int64_t)t * a.Ntot + n0 + cc;
-                for (int q = 0; q < 16; q += 4) {
-                    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
-                                 :: "l"(dst + q), "f"(__uint_as_float(r[q])), "f"(__uint_as_float(r[q + 1])),
-                                    "f"(__uint_as_float(r[q + 2])), "f"(__uint_as_float(r[q + 3]))
-                                 : "memory");
-                }
-            }
-        }
-    } else if (tid == 0) {
-        atomicOr(a.flags, FLAG_CHECK);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    if (s_fail && tid == 0) atomicOr(a.flags, FLAG_CHECK);
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
     }
@@ -314,15 +337,13 @@ __global__ void k_fold_beta(int nn, const int *__restrict__ level, double side, 
 
 }  // namespace
 
-// column geometry of the tensor-core M2L for order p
-void m2l_tc_geometry(int np, int *Kpad, int *Ncta, int *nsplit, int *nblk) {
-    int R = 2 * np;
+// column geometry of the tensor-core M2L: K padded to 16; NC = 512 / MT output
+// columns per CTA; nsplit CTAs per chunk cover the 2 n_p output columns
+void m2l_tc_geometry(int np, int MT, int *Kpad, int *Ncta, int *nsplit) {
+    const int R = 2 * np;
     *Kpad = (R + KC - 1) / KC * KC;
-    int ns = (R + 479) / 480;
-    int nc = ((R + ns - 1) / ns + 31) / 32 * 32;
-    *nsplit = ns;
-    *Ncta = nc;
-    *nblk = nc > 256 ? 2 : 1;
+    *Ncta = 512 / MT;
+    *nsplit = (R + *Ncta - 1) / *Ncta;
 }
 
 namespace {
@@ -331,10 +352,10 @@ namespace {
 int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alpha, cplx *beta_out,
               const cplx *tables, int tab_base, int tab_stride, int xmode,
               const unsigned short *G, const float *cfA, const float *cfB, size_t tab_bytes,
-              DBuf &ah, DBuf &al, DBuf &bt) {
+              DBuf &ah, DBuf &al, DBuf &bt, int MT) {
     const int nn = P->n_nodes, np = P->np;
-    int Kpad, Ncta, nsplit, nblk;
-    m2l_tc_geometry(np, &Kpad, &Ncta, &nsplit, &nblk);
+    int Kpad, Ncta, nsplit;
+    m2l_tc_geometry(np, MT, &Kpad, &Ncta, &nsplit);
     const int Ntot = Ncta * nsplit;
     TRY(dbuf_ensure(ah, (size_t)nn * Kpad * 4));
     TRY(dbuf_ensure(al, (size_t)nn * Kpad * 4));
@@ -365,16 +386,18 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
     a.Kpad = Kpad;
     a.Ncta = Ncta;
     a.Ntot = Ntot;
-    a.nblk = nblk;
+    a.nblk = 1;
+    a.MT = MT;
     a.side = P->side;
     a.flags = dp<int>(P->flags);
     a.tab_base = tab_base;
     a.tab_stride = tab_stride;
     a.xmode = xmode;
     a.p = P->p;
-    size_t sm = 2 * (size_t)(2 * TM * KC * 4 + 2 * Ncta * KC * 4) + tab_bytes;
+    size_t sm = m2l_tc_smem(np, MT, 0) + tab_bytes;
     CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid((unsigned)nch, (unsigned)nsplit);
+    a.nsplit = nsplit;
+    dim3 grid((unsigned)((int64_t)nch * nsplit));
     k_m2l_tc<<<grid, NTHR, sm, st>>>(a);
     P->launches++;
     k_fold_beta<<<nn, 128, 0, st>>>(nn, dp<int>(P->n_level), P->side, np, Ntot, dp<int>(P->d_mi),
@@ -386,11 +409,12 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
 
 }  // namespace
 
-// shared memory of the tensor-core M2L for a table of tab_entries complex entries
-size_t m2l_tc_smem(int np, int tab_entries) {
-    int Kpad, Ncta, nsplit, nblk;
-    m2l_tc_geometry(np, &Kpad, &Ncta, &nsplit, &nblk);
-    return 2 * (size_t)(2 * TM * KC * 4 + 2 * Ncta * KC * 4) + (size_t)tab_entries * sizeof(float2);
+// shared memory of the tensor-core M2L with MT tiles per pass and a table of
+// tab_entries complex entries
+size_t m2l_tc_smem(int np, int MT, int tab_entries) {
+    int Kpad, Ncta, nsplit;
+    m2l_tc_geometry(np, MT, &Kpad, &Ncta, &nsplit);
+    return 2 * (size_t)(2 * MT * TM * KC * 4 + 2 * Ncta * KC * 4) + (size_t)tab_entries * sizeof(float2);
 }
 
 int m2l_apply_tc_cross(tefmm_plan_s *P, cudaStream_t st, const cplx *alpha_x, cplx *beta_x,
@@ -398,7 +422,8 @@ int m2l_apply_tc_cross(tefmm_plan_s *P, cudaStream_t st, const cplx *alpha_x, cp
     const int c0 = (int)P->x_first_chunk, nch = (int)(P->n_chunks - P->x_first_chunk);
     if (nch <= 0) return TEFMM_OK;
     return tc_launch(P, st, c0, nch, alpha_x, beta_x, dp<cplx>(P->xtables), P->x_first_table, P->NX, 1,
-                     xgs, xcf, xcf, (size_t)P->NX * sizeof(float2), P->tc_xah, P->tc_xal, P->tc_xbt);
+                     xgs, xcf, xcf, (size_t)P->NX * sizeof(float2), P->tc_xah, P->tc_xal, P->tc_xbt,
+                     TC_MT_CROSS);
 }
 
 int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st) {
@@ -421,5 +446,6 @@ int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st) {
     }
     return tc_launch(P, st, 0, nch, dp<cplx>(P->alpha), dp<cplx>(P->beta), dp<cplx>(P->tables), 0,
                      P->np2, 0, dp<unsigned short>(P->d_m2l_g), dp<float>(P->tc_cfA),
-                     dp<float>(P->tc_cfB), (size_t)P->np2 * sizeof(float2), P->tc_ah, P->tc_al, P->tc_bt);
+                     dp<float>(P->tc_cfB), (size_t)P->np2 * sizeof(float2), P->tc_ah, P->tc_al, P->tc_bt,
+                     TC_MT);
 }

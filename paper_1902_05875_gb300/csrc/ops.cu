@@ -605,7 +605,7 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     k_seg_start<<<grid_for(ni, 256), 256, 0, st>>>(ni, head, seg, keys, dp<int>(P->keyslot_flag),
                                                    dp<uint64_t>(P->table_slot));
     P->launches++;
-    P->chunk_pairs = (P->opt.precision == TEFMM_MIXED) ? 128 : CH;
+    P->chunk_pairs = (P->opt.precision == TEFMM_MIXED) ? 128 * TC_MT : CH;
     k_chunk_heads<<<grid_for(ni, 256), 256, 0, st>>>(ni, keys, seg, dp<int>(P->keyslot_flag), chead,
                                                      P->chunk_pairs);
     P->launches++;
