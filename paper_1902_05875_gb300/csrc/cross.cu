@@ -457,7 +457,7 @@ int cross_apply(tefmm_plan_s *P, cudaStream_t st) {
     k_xshift_alpha<<<nn, 128, 0, st>>>(nn, T, cb, geo, P->p, np, dp<int>(P->d_mi), dp<cplx>(P->alpha),
                                        dp<cplx>(P->xalpha));
     P->launches++;
-    if (P->opt.precision == TEFMM_MIXED && m2l_tc_smem(np, TC_MT_CROSS, P->NX) + 8 * 1024 <= 227 * 1024) {
+    if (P->opt.precision == TEFMM_MIXED && (size_t)P->NX * sizeof(double) <= 200 * 1024) {
         // mixed form: the cross-layer contraction on the tensor cores (3xTF32)
         TRY(m2l_apply_tc_cross(P, st, dp<cplx>(P->xalpha), dp<cplx>(P->xbeta),
                                dp<unsigned short>(P->tc_xgs), dp<float>(P->tc_xcf32)));
@@ -480,7 +480,7 @@ int cross_apply(tefmm_plan_s *P, cudaStream_t st) {
 void cross_release(tefmm_plan_s *P) {
     DBuf *b[] = {&P->d_xA, &P->d_xZ, &P->d_xrange, &P->d_tslot, &P->xtables, &P->d_xG,
                  &P->d_xcf, &P->d_xexp, &P->d_xoff, &P->tc_xcf, &P->xalpha, &P->xbeta,
-                 &P->tc_xah, &P->tc_xal, &P->tc_xbt, &P->tc_xgs, &P->tc_xcf32};
+                 &P->tc_xah, &P->tc_xal, &P->tc_xbt, &P->tc_xgs, &P->tc_xcf32, &P->tc_xW};
     for (DBuf *x : b) dbuf_free(*x);
 }
 

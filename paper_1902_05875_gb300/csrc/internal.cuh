@@ -186,7 +186,7 @@ struct tefmm_plan_s {
     double fit_max_resid_cross = 0.0;
     DBuf d_xA, d_xZ, d_xrange, d_tslot, xtables, d_xG, d_xcf, d_xexp, d_xoff, tc_xcf;
     DBuf xalpha, xbeta;   // moments / locals about the cross-layer centres
-    DBuf tc_xah, tc_xal, tc_xbt, tc_xgs, tc_xcf32;   // tensor-core cross-layer M2L
+    DBuf tc_xah, tc_xal, tc_xbt, tc_xgs, tc_xcf32, tc_xW;   // tensor-core cross-layer M2L
     int NX = 0, n_xtables = 0, n_xfits_last = 0;
     int x_first_table = 0;        // cross-layer tables are [x_first_table, n_tables)
     int64_t x_first_chunk = 0;    // cross-layer chunks are [x_first_chunk, n_chunks)
@@ -194,7 +194,7 @@ struct tefmm_plan_s {
     double ms_xfit = 0;           // host time of the cross-layer fits of the last eval
 
     // tensor-core M2L buffers (mixed form)
-    DBuf tc_ah, tc_al, tc_bt, tc_cfA, tc_cfB;
+    DBuf tc_ah, tc_al, tc_bt, tc_cfA, tc_cfB, tc_W;   // tc_W: precomputed W^T blocks
     int tc_cf_np = 0;
 
     // host staging for tefmm_eval_host

@@ -21,6 +21,8 @@
 // LBO = 128 B between K-neighbours, SBO = 512 B between 8-row groups).
 // Every wait is bounded; on a timeout the CTA raises a flag, skips its output
 // and still releases its TMEM.
+#include <algorithm>
+
 #include "ops_common.cuh"
 
 namespace {
@@ -29,6 +31,7 @@ constexpr int TM = 128;      // pairs per CTA (MMA M)
 constexpr int KC = 16;       // K elements per chunk
 constexpr int NTHR = 256;
 constexpr long SPIN_LIMIT = 4000000;
+constexpr size_t W_BATCH_BYTES = (size_t)2 << 30;   // W^T blocks held at once
 
 struct TcArgs {
     int nchunks;
@@ -45,11 +48,13 @@ struct TcArgs {
     int np, np2, Kpad, Ncta, Ntot, nblk;   // nblk: unused (1)
     double side;
     int *flags;
-    // table layout: tables + (tb - tab_base) * tab_stride; xmode: cross-layer
-    // tables (p + 1 slices of orders 2p - k3', entry scaled by h^{|g| + k3'})
-    int tab_base, tab_stride, xmode, p;
+    // table of key tb: tables + (tb - tab_origin) * tab_stride; W^T blocks of the
+    // keys tab_base.. of this launch (k_wgen); xmode: cross-layer tables (p + 1
+    // slices of orders 2p - k3', entry scaled by h^{|g| + k3'})
+    int tab_origin, tab_base, tab_stride, xmode, p;
     int MT;                      // tiles of 128 pairs per pass (MT * Ncta = 512 TMEM columns)
     int nsplit;                  // column slices per chunk
+    const float *W;              // precomputed W^T blocks (k_wgen)
 };
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -89,44 +94,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// One CTA: one chunk of up to chunk_pairs pairs of one key, and one slice of
-// NC output columns.  The chunk is taken in passes of MT tiles of TM = 128
-// pairs; TMEM holds one 128 x NC FP32 accumulator per tile (MT * NC = 512
-// columns).  Every K slice of W^T (NC x 16, generated from the table once per
-// pass) therefore serves MT * 128 pairs.
-__global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
-    // 1-D grid: the nsplit column slices of one chunk are adjacent blocks, so
-    // they run together and share the chunk's moment rows through L2
-    const int c = blockIdx.x / a.nsplit;
-    const int slice = blockIdx.x % a.nsplit;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int MT = a.MT, NC = a.Ncta;
+// W^T blocks of one key, one column slice and one K chunk: NC x 16 TF32 hi
+// values in the K-major core-matrix layout of koff(), then the lo values;
+// block (key - tab_base, slice, ch) at W + ((tbl * nsplit + slice) * nk + ch) * 2 * NC * KC.
+// One CTA per (key, slice): the scaled table T~_g = T_g h^{|g|} (cross-layer:
+// h^{|g| + k3'} in slice k3') goes to shared memory in FP32 and every entry
+// of the real form [[Re H, -Im H], [Im H, Re H]] of the slice is generated once.
+__global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__restrict__ W) {
+    const int tbl = blockIdx.x / a.nsplit, slice = blockIdx.x % a.nsplit;
+    if (tbl >= ntab) return;
+    const int tid = threadIdx.x;
+    const int NC = a.Ncta, np = a.np, nk = a.Kpad / KC;
     extern __shared__ __align__(1024) unsigned char smem[];
-    // layout: [2 buffers][Xh (MT tiles) | Xl (MT tiles) | Wh | Wl] then table
-    const int tbytes = TM * KC * 4;                 // one X tile
-    const int xbytes = MT * tbytes;
-    const int wbytes = NC * KC * 4;
-    const int bufbytes = 2 * xbytes + 2 * wbytes;
-    unsigned char *buf0 = smem;
-    float2 *tab = (float2 *)(smem + 2 * bufbytes);
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ uint32_t tmem_base;
-    __shared__ int s_src[4 * TM], s_tgt[4 * TM];
-    __shared__ int s_fail;
-
-    const int tb = a.chunk_table[c];
-    const int cnt = a.chunk_cnt[c];
-    const int st = a.chunk_start[c];
+    float2 *tab = (float2 *)smem;
+    const int tb = a.tab_base + tbl;
     const uint64_t key = a.table_key[tb];
     const int kind = (int)(key >> 62);
     const int lev = (int)((key >> 57) & 31);
     const double h = a.side / (double)(1 << lev);
     const float *cf = kind == 0 ? a.cfB : a.cfA;
-
-    if (tid == 0) s_fail = 0;
-    // scaled table T~_g = T_g h^{|g|} in FP32 (cross-layer: h^{|g| + k3'} in slice k3')
     {
-        const cplx *T = a.tables + (int64_t)(tb - a.tab_base) * a.tab_stride;
+        const cplx *T = a.tables + (int64_t)(tb - a.tab_origin) * a.tab_stride;
         const int nsl = a.xmode ? a.p + 1 : 1;
         int off = 0;
         for (int k3p = 0; k3p < nsl; ++k3p) {
@@ -141,14 +129,76 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
             off += n2;
         }
     }
+    __syncthreads();
+    const int n0 = slice * NC;
+    for (int ch = 0; ch < nk; ++ch) {
+        float *blk = W + (((int64_t)tbl * a.nsplit + slice) * nk + ch) * (2 * NC * KC);
+        const int c0 = ch * KC;
+        for (int i = tid; i < NC * KC; i += NTHR) {
+            const int kk = i / NC, nl = i % NC;
+            const int n = n0 + nl, col = c0 + kk;
+            float w = 0.f;
+            if (n < 2 * np && col < 2 * np) {
+                const int k = n < np ? n : n - np, po = n < np ? 0 : 1;
+                const int kp = np - 1 - (col >> 1), pi = col & 1;     // K order: see kcol()
+                const int64_t o = (int64_t)kp * np + k;
+                const float cfv = __ldg(cf + o);
+                const float2 t = tab[__ldg(a.G + o)];
+                const float hr = cfv * t.x, hi = cfv * t.y;
+                w = (po == pi) ? hr : (po == 0 ? -hi : hi);
+            }
+            const float wh = tf32_rn(w);
+            const int e = koff(nl, kk) >> 2;
+            blk[e] = wh;
+            blk[NC * KC + e] = tf32_rn(w - wh);
+        }
+    }
+}
+
+// One CTA: one chunk of up to chunk_pairs pairs of one key, and one slice of
+// NC output columns.  The chunk is taken in passes of MT tiles of TM = 128
+// pairs; TMEM holds one 128 x NC FP32 accumulator per tile (MT * NC = 512
+// columns), so every W^T block brought in serves MT * 128 pairs.  Per K chunk:
+// thread 0 copies the W^T block (hi and lo, one bulk copy completing on an
+// mbarrier), all threads copy the pairs' moment rows (16-byte asynchronous
+// copies), then thread 0 issues 3 MMAs per tile and K step (hi.hi, hi.lo,
+// lo.hi) and commits them to the buffer's mbarrier.  Two buffers alternate.
+__global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
+    // 1-D grid: the nsplit column slices of one chunk are adjacent blocks, so
+    // they run together and share the chunk's moment rows through L2
+    const int c = blockIdx.x / a.nsplit;
+    const int slice = blockIdx.x % a.nsplit;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int MT = a.MT, NC = a.Ncta;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    // layout: [2 buffers][Xh (MT tiles) | Xl (MT tiles) | Wh | Wl]
+    const int tbytes = TM * KC * 4;                 // one X tile
+    const int xbytes = MT * tbytes;
+    const int wbytes = NC * KC * 4;
+    const int bufbytes = 2 * xbytes + 2 * wbytes;
+    unsigned char *buf0 = smem;
+    __shared__ __align__(8) uint64_t mbar[2], wbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_src[4 * TM], s_tgt[4 * TM];
+    __shared__ int s_fail;
+
+    const int tb = a.chunk_table[c];
+    const int cnt = a.chunk_cnt[c];
+    const int st = a.chunk_start[c];
+    const int nk = a.Kpad / KC;
+    const float *Wkey = a.W + ((int64_t)(tb - a.tab_base) * a.nsplit + slice) * nk * (2 * NC * KC);
+
+    if (tid == 0) s_fail = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(su32(&tmem_base)), "r"(512));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&mbar[1])));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&mbar[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&wbar[i])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -157,8 +207,6 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NC >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
-    const int nk = a.Kpad / KC;
-    const int np = a.np;
     const int n0 = slice * NC;             // first output column of this CTA
     bool ok = true;
     int gch = 0;                           // K chunks issued so far (all passes): buffer and phase
@@ -180,14 +228,23 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
         for (int ch = 0; ch < nk; ++ch, ++gch) {
             const int b = gch & 1;
             unsigned char *buf = buf0 + b * bufbytes;
-            unsigned char *Xh = buf, *Xl = buf + xbytes, *Wh = buf + 2 * xbytes, *Wl = buf + 2 * xbytes + wbytes;
+            unsigned char *Xh = buf, *Xl = buf + xbytes, *Wh = buf + 2 * xbytes;
             if (gch >= 2) {
                 if (!mbar_wait(su32(&mbar[b]), ((gch - 2) >> 1) & 1)) ok = false;
             }
             const int c0 = ch * KC;
+            if (tid == 0) {
+                // W^T block (hi then lo) by one bulk copy completing on wbar[b]
+                const uint32_t bytes = 2u * (uint32_t)wbytes;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                             :: "r"(su32(&wbar[b])), "r"(bytes) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(su32(Wh)), "l"(Wkey + (int64_t)ch * (2 * NC * KC)), "r"(bytes),
+                                "r"(su32(&wbar[b]))
+                             : "memory");
+            }
             // X^T slices: rows = pairs (tile by tile), 16 K columns, hi and lo;
-            // asynchronous 16-byte copies (rows without a pair are zero-filled),
-            // in flight while W^T is generated
+            // 16-byte asynchronous copies, rows without a pair zero-filled
             for (int i = tid; i < ntile * TM * 4 * 2; i += NTHR) {
                 const int part = i / (ntile * TM * 4), rem = i % (ntile * TM * 4);
                 const int r = rem >> 2, q = rem & 3;
@@ -198,28 +255,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
                              :: "r"(dst), "l"(srcp), "r"(s >= 0 ? 16 : 0) : "memory");
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
-            // W^T slice: rows = output columns n, 16 K columns; consecutive threads
-            // take consecutive rows so that the coefficient loads are contiguous in k
-#pragma unroll 4
-            for (int i = tid; i < NC * KC; i += NTHR) {
-                const int kk = i / NC, nl = i % NC;
-                const int n = n0 + nl, col = c0 + kk;
-                float w = 0.f;
-                if (n < 2 * np && col < 2 * np) {
-                    const int k = n < np ? n : n - np, po = n < np ? 0 : 1;
-                    const int kp = np - 1 - (col >> 1), pi = col & 1;     // K order: see kcol()
-                    const int64_t o = (int64_t)kp * np + k;
-                    const float cfv = __ldg(cf + o);
-                    const float2 t = tab[__ldg(a.G + o)];
-                    const float hr = cfv * t.x, hi = cfv * t.y;
-                    // [[Re H, -Im H], [Im H, Re H]]
-                    w = (po == pi) ? hr : (po == 0 ? -hi : hi);
-                }
-                const float wh = tf32_rn(w);
-                *reinterpret_cast<float *>(Wh + koff(nl, kk)) = wh;
-                *reinterpret_cast<float *>(Wl + koff(nl, kk)) = tf32_rn(w - wh);
-            }
             asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (!mbar_wait(su32(&wbar[b]), (gch >> 1) & 1)) ok = false;
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
             if (tid == 0) {
@@ -229,7 +266,7 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
                     for (int j = 0; j < KC / 8; ++j) {
                         const uint64_t dxh = sdesc(su32(Xh + mt * tbytes) + j * 256);
                         const uint64_t dxl = sdesc(su32(Xl + mt * tbytes) + j * 256);
-                        const uint64_t dwh = sdesc(su32(Wh) + j * 256), dwl = sdesc(su32(Wl) + j * 256);
+                        const uint64_t dwh = sdesc(su32(Wh) + j * 256), dwl = sdesc(su32(Wh + wbytes) + j * 256);
                         const uint32_t acc0 = (ch > 0 || j > 0) ? 1u : 0u;
                         asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                                      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
@@ -285,6 +322,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (s_fail) break;
+    }
+    // no bulk copy of this CTA may still be landing in its shared memory
+    for (int b = 0; b < 2 && b < gch; ++b) {
+        const int last = gch - 1 - ((gch - 1 - b) & 1);      // last chunk that used buffer b
+        mbar_wait(su32(&wbar[b]), (last >> 1) & 1);
     }
     if (s_fail && tid == 0) atomicOr(a.flags, FLAG_CHECK);
     if (warp == 0) {
@@ -350,9 +392,9 @@ namespace {
 
 // launch: split moments, tensor-core contraction of chunks [c0, c0 + nch), fold into beta_out
 int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alpha, cplx *beta_out,
-              const cplx *tables, int tab_base, int tab_stride, int xmode,
+              const cplx *tables, int tab_origin, int tab_first, int ntab, int tab_stride, int xmode,
               const unsigned short *G, const float *cfA, const float *cfB, size_t tab_bytes,
-              DBuf &ah, DBuf &al, DBuf &bt, int MT) {
+              DBuf &ah, DBuf &al, DBuf &bt, DBuf &Wbuf, int MT) {
     const int nn = P->n_nodes, np = P->np;
     int Kpad, Ncta, nsplit;
     m2l_tc_geometry(np, MT, &Kpad, &Ncta, &nsplit);
@@ -390,16 +432,45 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
     a.MT = MT;
     a.side = P->side;
     a.flags = dp<int>(P->flags);
-    a.tab_base = tab_base;
+    a.tab_origin = tab_origin;
+    a.tab_base = tab_first;
     a.tab_stride = tab_stride;
     a.xmode = xmode;
     a.p = P->p;
-    size_t sm = m2l_tc_smem(np, MT, 0) + tab_bytes;
-    CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     a.nsplit = nsplit;
-    dim3 grid((unsigned)((int64_t)nch * nsplit));
-    k_m2l_tc<<<grid, NTHR, sm, st>>>(a);
-    P->launches++;
+    // keys in batches whose W^T blocks fit in W_BATCH_BYTES; chunks are sorted
+    // by key, so a batch of keys is a contiguous range of chunks
+    const int nk = Kpad / KC;
+    const size_t wkey = (size_t)nsplit * nk * 2 * Ncta * KC * sizeof(float);
+    const int kb = (int)std::max<size_t>(1, std::min<size_t>((size_t)ntab, W_BATCH_BYTES / wkey));
+    TRY(dbuf_ensure(Wbuf, (size_t)kb * wkey));
+    a.W = dp<float>(Wbuf);
+    std::vector<int> ctab(nch);
+    CUDA_TRY(cudaMemcpyAsync(ctab.data(), dp<int>(P->chunk_key) + c0, (size_t)nch * 4,
+                             cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaFuncSetAttribute(k_wgen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_bytes));
+    const size_t sm = m2l_tc_smem(np, MT, 0);
+    CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int cb = 0;
+    for (int t0 = tab_first; t0 < tab_first + ntab; t0 += kb) {
+        const int t1 = std::min(t0 + kb, tab_first + ntab);
+        int ce = cb;
+        while (ce < nch && ctab[ce] < t1) ++ce;
+        a.tab_base = t0;
+        k_wgen<<<(unsigned)((int64_t)(t1 - t0) * nsplit), NTHR, tab_bytes, st>>>(a, t1 - t0, dp<float>(Wbuf));
+        P->launches++;
+        if (ce > cb) {
+            TcArgs b = a;
+            b.chunk_start = a.chunk_start + cb;
+            b.chunk_table = a.chunk_table + cb;
+            b.chunk_cnt = a.chunk_cnt + cb;
+            b.nchunks = ce - cb;
+            k_m2l_tc<<<(unsigned)((int64_t)(ce - cb) * nsplit), NTHR, sm, st>>>(b);
+            P->launches++;
+        }
+        cb = ce;
+    }
     k_fold_beta<<<nn, 128, 0, st>>>(nn, dp<int>(P->n_level), P->side, np, Ntot, dp<int>(P->d_mi),
                                     dp<float>(bt), beta_out);
     P->launches++;
@@ -421,9 +492,9 @@ int m2l_apply_tc_cross(tefmm_plan_s *P, cudaStream_t st, const cplx *alpha_x, cp
                        const unsigned short *xgs, const float *xcf) {
     const int c0 = (int)P->x_first_chunk, nch = (int)(P->n_chunks - P->x_first_chunk);
     if (nch <= 0) return TEFMM_OK;
-    return tc_launch(P, st, c0, nch, alpha_x, beta_x, dp<cplx>(P->xtables), P->x_first_table, P->NX, 1,
-                     xgs, xcf, xcf, (size_t)P->NX * sizeof(float2), P->tc_xah, P->tc_xal, P->tc_xbt,
-                     TC_MT_CROSS);
+    return tc_launch(P, st, c0, nch, alpha_x, beta_x, dp<cplx>(P->xtables), P->x_first_table,
+                     P->x_first_table, P->n_xtables, P->NX, 1, xgs, xcf, xcf, (size_t)P->NX * sizeof(float2),
+                     P->tc_xah, P->tc_xal, P->tc_xbt, P->tc_xW, TC_MT_CROSS);
 }
 
 int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st) {
@@ -444,8 +515,8 @@ int m2l_apply_tc(tefmm_plan_s *P, cudaStream_t st) {
         CUDA_TRY(cudaMemcpy(P->tc_cfB.p, fb.data(), fb.size() * 4, cudaMemcpyHostToDevice));
         P->tc_cf_np = np;
     }
-    return tc_launch(P, st, 0, nch, dp<cplx>(P->alpha), dp<cplx>(P->beta), dp<cplx>(P->tables), 0,
-                     P->np2, 0, dp<unsigned short>(P->d_m2l_g), dp<float>(P->tc_cfA),
+    return tc_launch(P, st, 0, nch, dp<cplx>(P->alpha), dp<cplx>(P->beta), dp<cplx>(P->tables), 0, 0,
+                     P->x_first_table, P->np2, 0, dp<unsigned short>(P->d_m2l_g), dp<float>(P->tc_cfA),
                      dp<float>(P->tc_cfB), (size_t)P->np2 * sizeof(float2), P->tc_ah, P->tc_al, P->tc_bt,
-                     TC_MT);
+                     P->tc_W, TC_MT);
 }
