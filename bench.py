@@ -80,9 +80,10 @@ FLOPS_FREE = 22
 
 # mixed form: FP32 flops per pair evaluation in k_near_fp32, counted from its
 # formulas (image term relative to the leaf-centre reference: D 5, complex sqrt
-# 12, delta 10, e^{ik delta} 8, 1/(1+delta/R0) 10, times E0 and accumulate 8;
+# 12, delta 10, e^{ik delta} - 1 from expm1/sin/cos 10, delta/R0 and the
+# numerator 6, division by 1 + delta/R0 10, times E0 and accumulate 8;
 # free-space term 20)
-FLOPS32_IMAGE = 53
+FLOPS32_IMAGE = 61
 FLOPS32_FREE = 20
 # FP32 SIMT peak derived from the unit counts and the maximum clock:
 # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz
