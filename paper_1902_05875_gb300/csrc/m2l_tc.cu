@@ -28,7 +28,8 @@
 namespace {
 
 constexpr int TM = 128;      // pairs per CTA (MMA M)
-constexpr int KC = 16;       // K elements per chunk
+constexpr int KC = 8;        // K elements per pipeline stage (one MMA K step)
+constexpr int NST = 4;       // pipeline stages (shared-memory buffers)
 constexpr int NTHR = 256;
 constexpr long SPIN_LIMIT = 4000000;
 constexpr size_t W_BATCH_BYTES = (size_t)2 << 30;   // W^T blocks held at once
@@ -52,9 +53,10 @@ struct TcArgs {
     // keys tab_base.. of this launch (k_wgen); xmode: cross-layer tables (p + 1
     // slices of orders 2p - k3', entry scaled by h^{|g| + k3'})
     int tab_origin, tab_base, tab_stride, xmode, p;
-    int MT;                      // tiles of 128 pairs per pass (MT * Ncta = 512 TMEM columns)
+    int MT;                      // tiles of 128 pairs per pass (MT * Ncta <= 512 TMEM columns)
     int nsplit;                  // column slices per chunk
     const float *W;              // precomputed W^T blocks (k_wgen)
+    int tcols;                   // TMEM columns allocated (power of 2 >= MT * Ncta)
 };
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -62,7 +64,7 @@ __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvt
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
     d |= (uint64_t)(128 >> 4) << 16;   // LBO
-    d |= (uint64_t)(512 >> 4) << 32;   // SBO
+    d |= (uint64_t)(256 >> 4) << 32;   // SBO: 8 rows x KC 4-byte elements
     d |= (uint64_t)1 << 46;            // descriptor version
     return d;
 }
@@ -73,9 +75,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 // collects the small terms before the large ones; this ordering measured
 // 2.5x less accumulation error than the graded order.
 //
-// byte offset of (row r, k) in a K-major no-swizzle tile with KC columns
+// byte offset of (row r, k) in a K-major no-swizzle tile with KC = 8 columns:
+// 8-row x 16-byte core matrices, LBO = 128 B between the two K halves,
+// SBO = 256 B between 8-row groups
 __device__ __forceinline__ int koff(int r, int k) {
-    return (r >> 3) * 512 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+    return (r >> 3) * 256 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
 }
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -157,12 +161,14 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
 
 // One CTA: one chunk of up to chunk_pairs pairs of one key, and one slice of
 // NC output columns.  The chunk is taken in passes of MT tiles of TM = 128
-// pairs; TMEM holds one 128 x NC FP32 accumulator per tile (MT * NC = 512
-// columns), so every W^T block brought in serves MT * 128 pairs.  Per K chunk:
-// thread 0 copies the W^T block (hi and lo, one bulk copy completing on an
-// mbarrier), all threads copy the pairs' moment rows (16-byte asynchronous
-// copies), then thread 0 issues 3 MMAs per tile and K step (hi.hi, hi.lo,
-// lo.hi) and commits them to the buffer's mbarrier.  Two buffers alternate.
+// pairs; TMEM holds one 128 x NC FP32 accumulator per tile (MT * NC <= 512
+// columns), so every W^T block brought in serves MT * 128 pairs.  The K
+// dimension runs through a ring of NST shared-memory stages of KC = 8: the
+// copies of stage c + NST - 1 (one bulk copy of the W^T block completing on an
+// mbarrier, 16-byte asynchronous copies of the pairs' moment rows) are issued
+// as soon as the MMAs of stage c - 1 have finished, so three stages of copies
+// are in flight while the tensor core works.  Thread 0 issues 3 MMAs per tile
+// (hi.hi, hi.lo, lo.hi) and commits them to the stage's mbarrier.
 __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     // 1-D grid: the nsplit column slices of one chunk are adjacent blocks, so
     // they run together and share the chunk's moment rows through L2
@@ -171,13 +177,12 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int MT = a.MT, NC = a.Ncta;
     extern __shared__ __align__(1024) unsigned char smem[];
-    // layout: [2 buffers][Xh (MT tiles) | Xl (MT tiles) | Wh | Wl]
+    // layout: [NST stages][Xh (MT tiles) | Xl (MT tiles) | Wh | Wl]
     const int tbytes = TM * KC * 4;                 // one X tile
     const int xbytes = MT * tbytes;
     const int wbytes = NC * KC * 4;
-    const int bufbytes = 2 * xbytes + 2 * wbytes;
-    unsigned char *buf0 = smem;
-    __shared__ __align__(8) uint64_t mbar[2], wbar[2];
+    const int stbytes = 2 * xbytes + 2 * wbytes;
+    __shared__ __align__(8) uint64_t mbar[NST], wbar[NST];
     __shared__ uint32_t tmem_base;
     __shared__ int s_src[4 * TM], s_tgt[4 * TM];
     __shared__ int s_fail;
@@ -191,11 +196,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     if (tid == 0) s_fail = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(su32(&tmem_base)), "r"(512));
+                     :: "r"(su32(&tmem_base)), "r"(a.tcols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NST; ++i) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&mbar[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&wbar[i])));
         }
@@ -209,7 +214,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
                            ((uint32_t)(TM >> 4) << 24);
     const int n0 = slice * NC;             // first output column of this CTA
     bool ok = true;
-    int gch = 0;                           // K chunks issued so far (all passes): buffer and phase
+    int gbase = 0;                         // global index of the pass's first K stage
+    int gissued = 0;                       // K stages whose copies were issued (all passes)
 
     for (int pb = 0; pb < cnt; pb += MT * TM) {
         const int npair = min(MT * TM, cnt - pb);
@@ -225,29 +231,28 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
             }
         }
         __syncthreads();
-        for (int ch = 0; ch < nk; ++ch, ++gch) {
-            const int b = gch & 1;
-            unsigned char *buf = buf0 + b * bufbytes;
-            unsigned char *Xh = buf, *Xl = buf + xbytes, *Wh = buf + 2 * xbytes;
-            if (gch >= 2) {
-                if (!mbar_wait(su32(&mbar[b]), ((gch - 2) >> 1) & 1)) ok = false;
+        // copies of K stage kc of this pass into buffer g % NST (g = gbase + kc),
+        // once the MMAs that last read that buffer (stage g - NST) are done
+        auto issue = [&](int kc) {
+            const int g = gbase + kc, sb = g % NST;
+            if (g >= NST) {
+                if (!mbar_wait(su32(&mbar[sb]), ((g - NST) / NST) & 1)) ok = false;
             }
-            const int c0 = ch * KC;
+            unsigned char *buf = smem + sb * stbytes;
+            unsigned char *Xh = buf, *Xl = buf + xbytes, *Wh = buf + 2 * xbytes;
             if (tid == 0) {
-                // W^T block (hi then lo) by one bulk copy completing on wbar[b]
                 const uint32_t bytes = 2u * (uint32_t)wbytes;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                             :: "r"(su32(&wbar[b])), "r"(bytes) : "memory");
+                             :: "r"(su32(&wbar[sb])), "r"(bytes) : "memory");
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             :: "r"(su32(Wh)), "l"(Wkey + (int64_t)ch * (2 * NC * KC)), "r"(bytes),
-                                "r"(su32(&wbar[b]))
+                             :: "r"(su32(Wh)), "l"(Wkey + (int64_t)kc * (2 * NC * KC)), "r"(bytes),
+                                "r"(su32(&wbar[sb]))
                              : "memory");
             }
-            // X^T slices: rows = pairs (tile by tile), 16 K columns, hi and lo;
-            // 16-byte asynchronous copies, rows without a pair zero-filled
-            for (int i = tid; i < ntile * TM * 4 * 2; i += NTHR) {
-                const int part = i / (ntile * TM * 4), rem = i % (ntile * TM * 4);
-                const int r = rem >> 2, q = rem & 3;
+            const int c0 = kc * KC;
+            for (int i = tid; i < ntile * TM * 2 * 2; i += NTHR) {
+                const int part = i / (ntile * TM * 2), rem = i % (ntile * TM * 2);
+                const int r = rem >> 1, q = rem & 1;
                 const int s = s_src[r];
                 const float *srcp = s >= 0 ? (part == 0 ? a.ah : a.al) + (int64_t)s * a.Kpad + c0 + 4 * q : a.ah;
                 const uint32_t dst = su32((part == 0 ? Xh : Xl) + (r / TM) * tbytes + koff(r % TM, 4 * q));
@@ -255,36 +260,46 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
                              :: "r"(dst), "l"(srcp), "r"(s >= 0 ? 16 : 0) : "memory");
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-            if (!mbar_wait(su32(&wbar[b]), (gch >> 1) & 1)) ok = false;
+            ++gissued;
+        };
+        for (int kc = 0; kc < NST - 1 && kc < nk; ++kc) issue(kc);
+        for (int kc = 0; kc < nk; ++kc) {
+            const int g = gbase + kc, sb = g % NST;
+            // this stage's moment rows: the later stages of this pass may stay in flight
+            const int pending = min(nk - kc - 1, NST - 2);
+            if (pending >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+            else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
+            if (!mbar_wait(su32(&wbar[sb]), (g / NST) & 1)) ok = false;
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
+                unsigned char *buf = smem + sb * stbytes;
+                const uint64_t dwh = sdesc(su32(buf + 2 * xbytes)), dwl = sdesc(su32(buf + 2 * xbytes + wbytes));
+                const uint32_t acc0 = kc > 0 ? 1u : 0u;
                 for (int mt = 0; mt < ntile; ++mt) {
                     const uint32_t d = tmem + (uint32_t)(mt * NC);
-                    for (int j = 0; j < KC / 8; ++j) {
-                        const uint64_t dxh = sdesc(su32(Xh + mt * tbytes) + j * 256);
-                        const uint64_t dxl = sdesc(su32(Xl + mt * tbytes) + j * 256);
-                        const uint64_t dwh = sdesc(su32(Wh) + j * 256), dwl = sdesc(su32(Wh + wbytes) + j * 256);
-                        const uint32_t acc0 = (ch > 0 || j > 0) ? 1u : 0u;
-                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                     :: "r"(d), "l"(dxh), "l"(dwh), "r"(idesc), "r"(acc0));
-                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                     :: "r"(d), "l"(dxh), "l"(dwl), "r"(idesc), "r"(1u));
-                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                     :: "r"(d), "l"(dxl), "l"(dwh), "r"(idesc), "r"(1u));
-                    }
+                    const uint64_t dxh = sdesc(su32(buf + mt * tbytes));
+                    const uint64_t dxl = sdesc(su32(buf + xbytes + mt * tbytes));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                 :: "r"(d), "l"(dxh), "l"(dwh), "r"(idesc), "r"(acc0));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                 :: "r"(d), "l"(dxh), "l"(dwl), "r"(idesc), "r"(1u));
+                    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                 :: "r"(d), "l"(dxl), "l"(dwh), "r"(idesc), "r"(1u));
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(su32(&mbar[b])) : "memory");
+                             :: "r"(su32(&mbar[sb])) : "memory");
             }
+            if (kc + NST - 1 < nk) issue(kc + NST - 1);
         }
+        gbase += nk;
         // the last commit covers every MMA issued before it
-        if (!mbar_wait(su32(&mbar[(gch - 1) & 1]), ((gch - 1) >> 1) & 1)) ok = false;
+        if (!mbar_wait(su32(&mbar[(gbase - 1) % NST]), ((gbase - 1) / NST) & 1)) ok = false;
         if (!ok) atomicExch(&s_fail, 1);
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
@@ -324,13 +339,15 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
         if (s_fail) break;
     }
     // no bulk copy of this CTA may still be landing in its shared memory
-    for (int b = 0; b < 2 && b < gch; ++b) {
-        const int last = gch - 1 - ((gch - 1 - b) & 1);      // last chunk that used buffer b
-        mbar_wait(su32(&wbar[b]), (last >> 1) & 1);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    for (int sb = 0; sb < NST; ++sb) {
+        if (sb >= gissued) break;
+        const int last = sb + (gissued - 1 - sb) / NST * NST;     // last stage that used buffer sb
+        mbar_wait(su32(&wbar[sb]), (last / NST) & 1);
     }
     if (s_fail && tid == 0) atomicOr(a.flags, FLAG_CHECK);
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(a.tcols));
     }
 }
 
@@ -379,13 +396,16 @@ __global__ void k_fold_beta(int nn, const int *__restrict__ level, double side, 
 
 }  // namespace
 
-// column geometry of the tensor-core M2L: K padded to 16; NC = 512 / MT output
-// columns per CTA; nsplit CTAs per chunk cover the 2 n_p output columns
+// column geometry of the tensor-core M2L: K padded to 16; the 2 n_p output
+// columns are cut into nsplit = ceil(2 n_p / 256) slices of Ncta columns
+// (a multiple of 32, at most 256: the MMA's N, and 16-column TMEM loads per
+// half of the epilogue warps)
 void m2l_tc_geometry(int np, int MT, int *Kpad, int *Ncta, int *nsplit) {
     const int R = 2 * np;
-    *Kpad = (R + KC - 1) / KC * KC;
-    *Ncta = 512 / MT;
-    *nsplit = (R + *Ncta - 1) / *Ncta;
+    (void)MT;
+    *Kpad = (R + 15) / 16 * 16;
+    *nsplit = (R + 255) / 256;
+    *Ncta = ((R + *nsplit - 1) / *nsplit + 31) / 32 * 32;
 }
 
 namespace {
@@ -399,6 +419,10 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
     int Kpad, Ncta, nsplit;
     m2l_tc_geometry(np, MT, &Kpad, &Ncta, &nsplit);
     const int Ntot = Ncta * nsplit;
+    // MMA shape M = 128, N = Ncta (multiple of 16, at most 256); MT accumulators in TMEM
+    if (Ncta > 256 || Ncta % 32 != 0 || MT < 1 || MT > 4 || MT * Ncta > 512) return TEFMM_ERR_INVALID_ARG;
+    int tcols = 32;
+    while (tcols < MT * Ncta) tcols <<= 1;
     TRY(dbuf_ensure(ah, (size_t)nn * Kpad * 4));
     TRY(dbuf_ensure(al, (size_t)nn * Kpad * 4));
     TRY(dbuf_ensure(bt, (size_t)nn * Ntot * 4));
@@ -438,6 +462,7 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
     a.xmode = xmode;
     a.p = P->p;
     a.nsplit = nsplit;
+    a.tcols = tcols;
     // keys in batches whose W^T blocks fit in W_BATCH_BYTES; chunks are sorted
     // by key, so a batch of keys is a contiguous range of chunks
     const int nk = Kpad / KC;
@@ -485,7 +510,7 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
 size_t m2l_tc_smem(int np, int MT, int tab_entries) {
     int Kpad, Ncta, nsplit;
     m2l_tc_geometry(np, MT, &Kpad, &Ncta, &nsplit);
-    return 2 * (size_t)(2 * MT * TM * KC * 4 + 2 * Ncta * KC * 4) + (size_t)tab_entries * sizeof(float2);
+    return NST * (size_t)(2 * MT * TM * KC * 4 + 2 * Ncta * KC * 4) + (size_t)tab_entries * sizeof(float2);
 }
 
 int m2l_apply_tc_cross(tefmm_plan_s *P, cudaStream_t st, const cplx *alpha_x, cplx *beta_x,
