@@ -198,6 +198,83 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+BATCHED = "batched_256_instances_p6"
+
+
+def run_batched(args):
+    """The batched workload: 256 independent two- or three-layer instances
+    (N log-uniform in [1k, 64k], about 3.8M points in all), mixed form, p = 6,
+    leaf caps chosen by the library's autotuner, evaluated together by
+    tefmm_eval_batched.  value = sum of N_i^2 per batch time."""
+    import torch
+    from paper_1902_05875_gb300 import tefmm
+    from paper_1902_05875_gb300 import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            ws = W.batched_instances(256)
+            cb = cpu_baseline(ws[0], seconds=10.0)
+            print(json.dumps({"impl": "reference", "metric": METRIC_BATCH, "value": cb["value"],
+                              "unit": UNIT, "n_gpus": args.gpus, "steps": 1, "warmup": 0,
+                              "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                              "config": {"workload": BATCHED, "sample": "instance 0"},
+                              "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT,
+                                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ws = W.batched_instances(256)
+    t0 = time.perf_counter()
+    plans = [tefmm.Plan(w.interfaces, w.k, p=w.p, leaf_cap=w.leaf_cap, n_images=w.n_images, zext=w.zext,
+                        precision=tefmm.MIXED) for w in ws]
+    plan_s = time.perf_counter() - t0
+    inst = []
+    for w in ws:
+        x, y, z = [torch.tensor(np.ascontiguousarray(w.src[:, i]), device=dev) for i in range(3)]
+        q = torch.tensor(w.q, device=dev)
+        inst.append((x, y, z, q, torch.empty(len(w.src), dtype=torch.complex128, device=dev)))
+    t0 = time.perf_counter()
+    st = tefmm.eval_batched(plans, inst)            # first call: autotuner and cross-layer fits
+    torch.cuda.synchronize()
+    first_s = time.perf_counter() - t0
+    assert all(v == 0 for v in st), st
+    for _ in range(max(3, args.warmup) - 1):
+        tefmm.eval_batched(plans, inst)
+    torch.cuda.synchronize()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    cp, cpath = clocks_start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tefmm.eval_batched(plans, inst)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = clocks_stop(cp, cpath, local)
+    ms = float(np.mean(times))
+    inter = float(sum(len(w.src) ** 2 for w in ws))
+    caps = [pl.stats()["leaf_cap_used"] for pl in plans]
+    line = {"metric": METRIC_BATCH, "value": world * inter / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+tf32x3/f64", "data": "synthetic",
+            "config": {"workload": BATCHED, "instances": len(ws), "points": int(sum(len(w.src) for w in ws)),
+                       "p": 6, "n_images": ws[0].n_images, "precision": "mixed",
+                       "leaf_caps": {str(c): caps.count(c) for c in sorted(set(caps))},
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "plan_s": plan_s, "first_batch_s_incl_autotune_and_fits": first_s,
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+METRIC_BATCH = "batched TE-FMM matvec interactions/s (sum of N_i^2 per batch time), 256 instances"
+
+
 def timed_steps(plan, torch, x, y, z, q, out, flush, steps):
     """Per-step device time (CUDA events on the launching stream, L2 flushed
     before each step) and the plan's per-phase times."""
@@ -225,7 +302,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + [BATCHED])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--no-fp64-form", action="store_true",
@@ -233,6 +310,9 @@ def main():
     ap.add_argument("--accuracy-samples", type=int, default=100,
                     help="targets of the oracle direct sum for the accuracy check (0: none)")
     args = ap.parse_args()
+    if args.workload == BATCHED:
+        run_batched(args)
+        return
     w = WORKLOADS[args.workload]()
     if args.impl == "reference":
         run_reference(args, w)

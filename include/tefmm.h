@@ -57,7 +57,9 @@ typedef struct tefmm_plan_s *tefmm_plan;
 
 typedef struct {
     int p;                 /* Taylor order (|k| <= p), 1..12                          */
-    int leaf_cap;          /* split a box while max(#sources, #targets) > leaf_cap    */
+    int leaf_cap;          /* split a box while max(#sources, #targets) > leaf_cap;
+                              0: autotuned on the first evaluation (the fastest of
+                              16, 32, 64, 128, 256 by CUDA-event timing)              */
     int max_level;         /* deepest octree level, 1..20                             */
     int precision;         /* TEFMM_FP64 or TEFMM_MIXED                               */
     int n_images;          /* DCIM images per fitted term (<= 32; <= 24 per level)    */
@@ -91,6 +93,9 @@ typedef struct {
     double fit_max_resid_cross; /* worst cross-layer fit residual (relative)          */
     double ms_cross_tables; /* part of ms_tables spent on cross-layer tables          */
     double ms_cross_m2l;   /* part of ms_m2l spent on cross-layer translations        */
+    int leaf_cap_used;     /* leaf cap of the last evaluation (the autotuner's choice
+                              when the plan was made with leaf_cap = 0)               */
+    double ms_autotune;    /* time of the autotuner's trial evaluations               */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,
@@ -128,6 +133,28 @@ int tefmm_plan_destroy(tefmm_plan plan);
 int tefmm_eval(tefmm_plan plan, int64_t ns, const double *d_sx, const double *d_sy,
                const double *d_sz, const double *d_q, int64_t nt, const double *d_tx,
                const double *d_ty, const double *d_tz, double *d_phi, void *stream);
+
+/* One instance of a batch: device arrays as for tefmm_eval; tx == NULL means
+ * the targets are the sources (then nt, ty, tz are ignored). */
+typedef struct {
+    int64_t ns;
+    const double *sx, *sy, *sz, *q;
+    int64_t nt;
+    const double *tx, *ty, *tz;
+    double *phi;
+} tefmm_batch_item;
+
+/* Batched matrix-vector products of n independent instances (the batched
+ * workload of many small layered media; the paper evaluates one medium at a
+ * time).  plans[i] holds instance i's medium and options (distinct plans; a
+ * plan may appear once), items[i] its particles and output.  The instances
+ * run concurrently on n_workers (<= 0: 8) internal streams, each driven by a
+ * host thread; the work is ordered after the caller's stream at entry and the
+ * caller's stream waits for all of it at exit.  status (optional, host int[n])
+ * receives each instance's result.  Returns the first error of any instance,
+ * INVALID_ARG for bad arguments, CUDA for stream/event failures. */
+int tefmm_eval_batched(int n, tefmm_plan *plans, const tefmm_batch_item *items, int n_workers,
+                       void *stream, int *status);
 
 /* Same as tefmm_eval with HOST arrays: copies the inputs to plan-owned device
  * buffers, evaluates, copies Phi back, and synchronises the stream. */

@@ -32,14 +32,53 @@ float elapsed(cudaEvent_t a, cudaEvent_t b) {
 }
 }  // namespace
 
+namespace {
+int eval_once(tefmm_plan P, int64_t ns, const double *sx, const double *sy, const double *sz,
+              const double *q, int64_t nt, const double *tx, const double *ty, const double *tz,
+              double *phi, cudaStream_t st);
+}
+
+// Leaf-cap autotuner: with leaf_cap = 0 the first evaluation tries each cap of
+// TUNE_CAPS (the trade between near-field pairs and M2L translations depends on
+// p, the images per term, the precision and the particle distribution), times
+// each trial with CUDA events, keeps the fastest for the plan's lifetime and
+// evaluates once more with it.
 extern "C" int tefmm_eval(tefmm_plan P, int64_t ns, const double *sx, const double *sy,
                           const double *sz, const double *q, int64_t nt, const double *tx,
                           const double *ty, const double *tz, double *phi, void *stream) {
     if (!P || ns < 0 || nt < 0 || ns > (1LL << 30) || nt > (1LL << 30)) return TEFMM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P->leaf_cap_eff == 0 && ns > 0 && nt > 0) {
+        static const int TUNE_CAPS[] = {16, 32, 64, 128, 256};
+        float best = 1e30f;
+        int best_cap = 64;
+        for (int cap : TUNE_CAPS) {
+            P->leaf_cap_eff = cap;
+            float ms = 0.f;
+            CUDA_TRY(cudaEventRecord(P->ev[9], st));
+            int r = eval_once(P, ns, sx, sy, sz, q, nt, tx, ty, tz, phi, st);
+            CUDA_TRY(cudaEventRecord(P->ev[10], st));
+            CUDA_TRY(cudaEventSynchronize(P->ev[10]));
+            CUDA_TRY(cudaEventElapsedTime(&ms, P->ev[9], P->ev[10]));
+            if (r != TEFMM_OK) continue;       // e.g. a cap that leaves cross-layer near pairs
+            P->ms_autotune += ms;
+            if (ms < best) {
+                best = ms;
+                best_cap = cap;
+            }
+        }
+        P->leaf_cap_eff = best_cap;
+    }
+    return eval_once(P, ns, sx, sy, sz, q, nt, tx, ty, tz, phi, st);
+}
+
+namespace {
+int eval_once(tefmm_plan P, int64_t ns, const double *sx, const double *sy, const double *sz,
+              const double *q, int64_t nt, const double *tx, const double *ty, const double *tz,
+              double *phi, cudaStream_t st) {
     if (nt > 0 && !phi) return TEFMM_ERR_INVALID_ARG;
     if (ns > 0 && (!sx || !sy || !sz || !q)) return TEFMM_ERR_INVALID_ARG;
     if (nt > 0 && (!tx || !ty || !tz)) return TEFMM_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
     if (ns == 0 || nt == 0) {
         if (nt > 0) {
             k_zero<<<grid_for(2 * nt, 256), 256, 0, st>>>(2 * nt, phi);
@@ -78,6 +117,7 @@ extern "C" int tefmm_eval(tefmm_plan P, int64_t ns, const double *sx, const doub
     CUDA_TRY(cudaGetLastError());
     return TEFMM_OK;
 }
+}  // namespace
 
 extern "C" int tefmm_eval_host(tefmm_plan P, int64_t ns, const double *sx, const double *sy,
                                const double *sz, const double *q, int64_t nt, const double *tx,
@@ -137,6 +177,8 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
         o->ms_cross_tables = elapsed(P->ev[7], P->ev[3]);
         o->ms_cross_m2l = elapsed(P->ev[8], P->ev[4]);
     }
+    o->leaf_cap_used = P->leaf_cap_eff;
+    o->ms_autotune = P->ms_autotune;
     return TEFMM_OK;
 }
 

@@ -428,7 +428,7 @@ int cross_tables(tefmm_plan_s *P, cudaStream_t st) {
     TRY(dbuf_ensure(P->xtables, (size_t)nx * P->NX * sizeof(cplx)));
     const int nfull = P->np2;
     size_t sm = 3 * (size_t)nfull * sizeof(cplx) + 3 * (size_t)nfull * sizeof(int);
-    CUDA_TRY(cudaFuncSetAttribute(k_xtables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    TRY(smem_optin(k_xtables));
     dim3 grid((unsigned)nx, (unsigned)(P->p + 1));
     k_xtables<<<grid, 256, sm, st>>>(nx, dp<uint64_t>(P->table_slot) + P->x_first_table, cube_of(P),
                                      P->p, dp<int>(P->d_mi), geometry(P), dp<int2>(P->d_xrange),
@@ -444,7 +444,7 @@ int cross_apply(tefmm_plan_s *P, cudaStream_t st) {
     const int np = P->np;
     const int nthr = (np + 31) / 32 * 32;
     size_t sm = (size_t)P->np2 * sizeof(cplx) + (size_t)CHX * np * sizeof(cplx);
-    CUDA_TRY(cudaFuncSetAttribute(k_m2l_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    TRY(smem_optin(k_m2l_x));
     const int *og = dp<int>(P->d_xoff);
     const int nn = P->n_nodes;
     const size_t nb = (size_t)nn * np * sizeof(cplx);

@@ -129,6 +129,8 @@ struct tefmm_plan_s {
     tefmm_options opt{};
     int p = 0, np = 0, np2 = 0;
     int device = 0;
+    int leaf_cap_eff = 64;        // leaf cap in use (0 until the autotuner has chosen one)
+    double ms_autotune = 0;       // time of the autotuner's trial evaluations
 
     // images (host mirror + device copy)
     std::vector<TermDesc> terms;
@@ -222,6 +224,23 @@ struct tefmm_plan_s {
         int _r = (expr);                  \
         if (_r != TEFMM_OK) return _r;    \
     } while (0)
+
+// Raise a kernel's dynamic shared-memory limit to the most the device allows
+// beside the kernel's static shared memory.  Every call sets the same value,
+// so plans evaluated concurrently from several host threads (batched
+// evaluation) cannot lower the limit under one another's launches.
+template <class F>
+static inline int smem_optin(F *func) {
+    int dev = 0, mx = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, (const void *)func) != cudaSuccess ||
+        cudaFuncSetAttribute((const void *)func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             mx - (int)fa.sharedSizeBytes) != cudaSuccess)
+        return TEFMM_ERR_CUDA;
+    return TEFMM_OK;
+}
 
 static inline int grid_for(int64_t n, int block) {
     int64_t g = (n + block - 1) / block;

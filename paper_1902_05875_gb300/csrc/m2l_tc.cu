@@ -32,7 +32,8 @@ constexpr int KC = 8;        // K elements per pipeline stage (one MMA K step)
 constexpr int NST = 4;       // pipeline stages (shared-memory buffers)
 constexpr int NTHR = 256;
 constexpr long SPIN_LIMIT = 4000000;
-constexpr size_t W_BATCH_BYTES = (size_t)2 << 30;   // W^T blocks held at once
+constexpr size_t W_BATCH_BYTES = (size_t)2 << 30;   // W^T blocks held at once, at most
+constexpr size_t W_BATCH_MIN = (size_t)64 << 20;    // ... and at least (unless fewer are needed)
 
 struct TcArgs {
     int nchunks;
@@ -467,16 +468,20 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
     // by key, so a batch of keys is a contiguous range of chunks
     const int nk = Kpad / KC;
     const size_t wkey = (size_t)nsplit * nk * 2 * Ncta * KC * sizeof(float);
-    const int kb = (int)std::max<size_t>(1, std::min<size_t>((size_t)ntab, W_BATCH_BYTES / wkey));
+    // a quarter of what all keys need, within [W_BATCH_MIN, W_BATCH_BYTES]: large
+    // problems take few batches, and many plans alive at once (batched
+    // evaluation) do not each hold gigabytes
+    const size_t wcap = std::min(W_BATCH_BYTES, std::max(W_BATCH_MIN, (size_t)ntab * wkey / 4));
+    const int kb = (int)std::max<size_t>(1, std::min<size_t>((size_t)ntab, wcap / wkey));
     TRY(dbuf_ensure(Wbuf, (size_t)kb * wkey));
     a.W = dp<float>(Wbuf);
     std::vector<int> ctab(nch);
     CUDA_TRY(cudaMemcpyAsync(ctab.data(), dp<int>(P->chunk_key) + c0, (size_t)nch * 4,
                              cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    CUDA_TRY(cudaFuncSetAttribute(k_wgen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab_bytes));
+    TRY(smem_optin(k_wgen));
     const size_t sm = m2l_tc_smem(np, MT, 0);
-    CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    TRY(smem_optin(k_m2l_tc));
     int cb = 0;
     for (int t0 = tab_first; t0 < tab_first + ntab; t0 += kb) {
         const int t1 = std::min(t0 + kb, tab_first + ntab);

@@ -540,7 +540,7 @@ int upward_pass(tefmm_plan_s *P, cudaStream_t st) {
                                    dp<cplx>(P->alpha));
     P->launches++;
     size_t sm_m2m = 8 * (size_t)np * sizeof(cplx) + 8 * 3 * (p + 1) * sizeof(double);
-    CUDA_TRY(cudaFuncSetAttribute(k_m2m, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_m2m));
+    TRY(smem_optin(k_m2m));
     ShiftRows R{dp<int>(P->d_sh_ptr_m2m), dp<int>(P->d_sh_ent_m2m), dp<double>(P->d_sh_cf_m2m)};
     for (int l = P->n_levels - 2; l >= 0; --l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
@@ -640,7 +640,7 @@ int m2l_tables(tefmm_plan_s *P, cudaStream_t st) {
     const int np2 = P->np2;
     TRY(dbuf_ensure(P->tables, (size_t)ntab * np2 * sizeof(cplx)));
     size_t sm = 3 * (size_t)np2 * sizeof(cplx) + 3 * (size_t)np2 * sizeof(int);
-    CUDA_TRY(cudaFuncSetAttribute(k_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    TRY(smem_optin(k_tables));
     k_tables<<<ntab, 256, sm, st>>>(ntab, dp<uint64_t>(P->table_slot), cube_of(P),
                                            2 * P->p, np2, dp<int>(P->d_mi), img_view(P),
                                            dp<cplx>(P->tables));
@@ -656,7 +656,7 @@ int m2l_apply(tefmm_plan_s *P, cudaStream_t st) {
     const int nch = (int)P->x_first_chunk;    // same-layer chunks (cross-layer ones follow)
     if (nch == 0) return TEFMM_OK;
     size_t sm = (size_t)P->np2 * sizeof(cplx) + (size_t)CH * np * sizeof(cplx);
-    CUDA_TRY(cudaFuncSetAttribute(k_m2l_fp64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    TRY(smem_optin(k_m2l_fp64));
     k_m2l_fp64<<<nch, 256, sm, st>>>(
         nch, dp<int>(P->chunk_start), dp<int>(P->chunk_key), dp<int>(P->chunk_cnt),
         dp<uint64_t>(P->table_slot), dp<cplx>(P->tables), dp<int>(P->pair_idx_sorted),

@@ -194,7 +194,7 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
     tefmm_options o;
     if (opt) o = *opt;
     else tefmm_default_options(&o);
-    if (o.p < 1 || o.p > 12 || o.leaf_cap < 1 || o.max_level < 1 || o.max_level > TEFMM_NBITS ||
+    if (o.p < 1 || o.p > 12 || o.leaf_cap < 0 || o.max_level < 1 || o.max_level > TEFMM_NBITS ||
         o.n_images < 0 || o.n_images > TEFMM_MAX_IMG || o.n_samples < 8 || o.n_samples > 127 ||
         !(o.T1 > 0) || (o.precision != TEFMM_FP64 && o.precision != TEFMM_MIXED))
         return TEFMM_ERR_INVALID_ARG;
@@ -210,6 +210,7 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
         if (l < n_layers - 1 && o.zext[2 * l] < interfaces[l]) return TEFMM_ERR_INVALID_ARG;
     }
     tefmm_plan_s *P = new tefmm_plan_s();
+    P->leaf_cap_eff = o.leaf_cap;      // 0: chosen by the autotuner on the first evaluation
     P->nL = n_layers;
     for (int m = 0; m < n_layers - 1; ++m) P->d[m] = interfaces[m];
     for (int l = 0; l < n_layers; ++l) P->k[l] = mkc(k_re[l], k_im[l]);

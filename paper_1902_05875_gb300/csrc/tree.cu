@@ -712,7 +712,7 @@ int tree_build(tefmm_plan_s *P, const double *sx, const double *sy, const double
         P->launches++;
         CUDA_TRY(cudaMemsetAsync(P->counters.p, 0, 4, st));
         k_node_ranges<<<grid_for(cnt, 256), 256, 0, st>>>(
-            (int)total, cnt, nitems, l, P->opt.leaf_cap, max_level, dp<int>(P->n_i0),
+            (int)total, cnt, nitems, l, P->leaf_cap_eff, max_level, dp<int>(P->n_i0),
             dp<int>(P->n_parent), dp<int>(P->cnt_s), nullptr, shared, dp<int>(P->n_i1),
             dp<int>(P->n_s0), dp<int>(P->n_s1), dp<int>(P->n_t0), dp<int>(P->n_t1),
             dp<int>(P->n_split), dp<int>(P->n_cfirst), dp<int>(P->n_nchild),

@@ -38,7 +38,8 @@ class Stats(ctypes.Structure):
                 ("n_cross_tables", ctypes.c_int), ("n_cross_fits", ctypes.c_int),
                 ("n_cross_fits_last", ctypes.c_int), ("ms_cross_fit", ctypes.c_double),
                 ("fit_max_resid_cross", ctypes.c_double), ("ms_cross_tables", ctypes.c_double),
-                ("ms_cross_m2l", ctypes.c_double)]
+                ("ms_cross_m2l", ctypes.c_double), ("leaf_cap_used", ctypes.c_int),
+                ("ms_autotune", ctypes.c_double)]
 
 
 EXPORTED = [
@@ -46,6 +47,7 @@ EXPORTED = [
     "tefmm_eval_host", "tefmm_get_stats", "tefmm_status_string", "tefmm_plan_image_counts",
     "tefmm_plan_get_images", "tefmm_plan_set_images", "tefmm_export_tree", "tefmm_export_lists",
     "tefmm_export_expansions", "tefmm_fit_images_noalloc", "tefmm_plan_cross_images",
+    "tefmm_eval_batched",
 ]
 
 _lib = None
@@ -85,6 +87,8 @@ def load(build_if_needed=True):
     lib.tefmm_export_tree.argtypes = [P, I, I64, I64] + [I] * 12
     lib.tefmm_export_lists.argtypes = [P, I64, I64, I, I, I, I]
     lib.tefmm_export_expansions.argtypes = [P, D, D]
+    lib.tefmm_eval_batched.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                       ctypes.POINTER(BatchItem), ctypes.c_int, P, I]
     lib.tefmm_fit_images_noalloc.argtypes = [ctypes.c_int, D, D, D, ctypes.POINTER(Options), P,
                                              I, I, I, I, D, D]
     for name in EXPORTED:
@@ -121,6 +125,36 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int64), ("sx", ctypes.c_void_p), ("sy", ctypes.c_void_p),
+                ("sz", ctypes.c_void_p), ("q", ctypes.c_void_p), ("nt", ctypes.c_int64),
+                ("tx", ctypes.c_void_p), ("ty", ctypes.c_void_p), ("tz", ctypes.c_void_p),
+                ("phi", ctypes.c_void_p)]
+
+
+def eval_batched(plans, instances, n_workers=8, stream=None):
+    """``tefmm_eval_batched``: plans[i] evaluates instances[i] = (sx, sy, sz, q, out),
+    contiguous CUDA tensors (float64 coordinates, complex128 charges and output;
+    targets are the sources).  Returns the per-instance status list."""
+    lib = load()
+    n = len(plans)
+    items = (BatchItem * max(n, 1))()
+    keep = []
+    for i, (sx, sy, sz, q, out) in enumerate(instances):
+        for a in (sx, sy, sz):
+            if not (a.is_cuda and a.is_contiguous()):
+                raise ValueError("coordinates must be contiguous CUDA tensors")
+        vp = lambda t: t.data_ptr()
+        items[i] = BatchItem(sx.numel(), vp(sx), vp(sy), vp(sz), vp(q), sx.numel(), None, None, None,
+                             vp(out))
+        keep.append((sx, sy, sz, q, out))
+    hs = (ctypes.c_void_p * max(n, 1))(*[pl.h.value for pl in plans])
+    st = (ctypes.c_int * max(n, 1))()
+    _check(lib.tefmm_eval_batched(n, hs, items, int(n_workers), _stream_handle(stream), st),
+           "tefmm_eval_batched")
+    return list(st[:n])
 
 
 class Plan:

@@ -112,3 +112,34 @@ def cfg_mixed_200k():
     """The 2M workload's geometry and medium at 200k points (a profiling case)."""
     return three_layer_slabs(200_000, 10, 64, seed=0, n_images=16,
                              name="three_layer_slabs_n200k_p10")
+
+
+def batched_instances(n_inst, p=6, seed=2, n_min=1000, n_max=64000, n_images=8, leaf_cap=0):
+    """Independent two- or three-layer instances (the batched workload): layer
+    count 2 or 3 with equal probability; interface depths uniform in [-2, 0],
+    sorted, a middle layer at least 0.3 thick (rejection); real k per layer
+    uniform in [1, 4]; N log-uniform in [n_min, n_max], split equally over the
+    layers, uniform in [-1,1]^2 x slabs 0.1 inside each layer (outer slabs 1.0
+    thick); complex charges.  leaf_cap = 0 asks the library's autotuner."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_inst):
+        nl = int(rng.integers(2, 4))
+        while True:
+            d = np.sort(rng.uniform(-2.0, 0.0, nl - 1))[::-1]
+            if nl == 2 or d[0] - d[1] >= 0.3:
+                break
+        k = list(rng.uniform(1.0, 4.0, nl))
+        n = int(np.exp(rng.uniform(np.log(n_min), np.log(n_max))))
+        zext = []
+        for l in range(nl):
+            top = d[l - 1] - 0.1 if l > 0 else d[0] + 1.1
+            bot = d[l] + 0.1 if l < nl - 1 else d[-1] - 1.1
+            zext.append((float(bot), float(top)))
+        counts = [n // nl + (1 if l < n % nl else 0) for l in range(nl)]
+        src = np.concatenate([rng.uniform([-1.0, -1.0, a], [1.0, 1.0, b], size=(c, 3))
+                              for (a, b), c in zip(zext, counts)], 0)
+        q = _charges(rng, len(src))
+        out.append(Workload(f"batch{i}_L{nl}_n{n}", list(map(float, d)), k, zext, src, q, p, leaf_cap,
+                            n_images))
+    return out
