@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <math.h>
 #include <stdio.h>
 
 #include <map>
@@ -130,6 +131,7 @@ struct tefmm_plan_s {
     int p = 0, np = 0, np2 = 0;
     int device = 0;
     int leaf_cap_eff = 64;        // leaf cap in use (0 until the autotuner has chosen one)
+    double HX = INFINITY;         // box size above which stacked cross-layer boxes are paired, not translated
     double ms_autotune = 0;       // time of the autotuner's trial evaluations
 
     // images (host mirror + device copy)

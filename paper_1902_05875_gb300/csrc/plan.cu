@@ -211,6 +211,16 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
     }
     tefmm_plan_s *P = new tefmm_plan_s();
     P->leaf_cap_eff = o.leaf_cap;      // 0: chosen by the autotuner on the first evaluation
+    // HX = 2 min over interfaces of (gap above + gap below) between the particle
+    // slabs and the interface; interfaces without a gap do not count
+    {
+        double gmin = INFINITY;
+        for (int m = 0; m + 1 < n_layers; ++m) {
+            const double gm = (o.zext[2 * m] - interfaces[m]) + (interfaces[m] - o.zext[2 * (m + 1) + 1]);
+            if (gm > 0.0 && gm < gmin) gmin = gm;
+        }
+        P->HX = gmin < INFINITY ? 2.0 * gmin : INFINITY;
+    }
     P->nL = n_layers;
     for (int m = 0; m < n_layers - 1; ++m) P->d[m] = interfaces[m];
     for (int l = 0; l < n_layers; ++l) P->k[l] = mkc(k_re[l], k_im[l]);

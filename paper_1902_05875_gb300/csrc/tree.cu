@@ -369,9 +369,17 @@ __global__ void k_lists_root(int nroots, NodeView N, int *C_list, int *C_cnt, in
     V_cnt[t] = 0;
 }
 
+// Cross-layer admissibility: at a level whose box size exceeds HX (coarse != 0),
+// two split boxes of different layers stacked within one box horizontally are
+// paired like adjacent boxes (their children are paired) instead of translated.
+__device__ __forceinline__ bool cross_colleague(const NodeView &N, int t, int c, int coarse) {
+    if (!coarse || N.layer[t] == N.layer[c] || !N.split[t] || !N.split[c]) return false;
+    return abs(N.ix[t] - N.ix[c]) <= 1 && abs(N.iy[t] - N.iy[c]) <= 1;
+}
+
 __global__ void k_lists_level(int off, int cnt, NodeView N, int *C_list, int *C_cnt, int capC,
                               int *D_list, int *D_cnt, int capD, int *X_list, int *X_cnt, int capX,
-                              int *V_list, int *V_cnt, int capV, int *flags) {
+                              int *V_list, int *V_cnt, int capV, int *flags, int coarse) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cnt) return;
     int t = off + j;
@@ -390,7 +398,7 @@ __global__ void k_lists_level(int off, int cnt, NodeView N, int *C_list, int *C_
                 int c0 = N.cfirst[s], c1 = c0 + N.nchild[s];
                 for (int c = c0; c < c1; ++c) {
                     if (N.s1[c] <= N.s0[c]) continue;
-                    if (adjacent(N, t, c)) {
+                    if (adjacent(N, t, c) || cross_colleague(N, t, c, coarse)) {
                         if (nc < capC) Cl[nc++] = c; else ovf = true;
                     } else {
                         if (nv < capV) Vl[nv++] = c; else ovf = true;
@@ -743,8 +751,11 @@ int tree_build(tefmm_plan_s *P, const double *sx, const double *sy, const double
 
 int lists_build(tefmm_plan_s *P, cudaStream_t st) {
     const int nn = P->n_nodes;
-    P->cap_C = 27 * P->nL;
-    P->cap_V = 189 * P->nL;
+    // stacked cross-layer colleagues (at most 128 per other layer) and their
+    // children in the V lists; overflow is reported (LIST_OVERFLOW)
+    const bool xrule = P->nL > 1 && P->HX < INFINITY;
+    P->cap_C = 27 * P->nL + (xrule ? 128 * (P->nL - 1) : 0);
+    P->cap_V = 189 * P->nL + (xrule ? 1024 * (P->nL - 1) : 0);
     P->cap_D = 128;
     P->cap_X = 27 * P->nL + 128;
     TRY(dbuf_ensure(P->C_list, (size_t)nn * P->cap_C * 4));
@@ -768,7 +779,8 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
         k_lists_level<<<grid_for(cnt, 128), 128, 0, st>>>(
             off, cnt, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C, dp<int>(P->D_list),
             dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X,
-            dp<int>(P->V_tmp), dp<int>(P->V_cnt), P->cap_V, dp<int>(P->flags));
+            dp<int>(P->V_tmp), dp<int>(P->V_cnt), P->cap_V, dp<int>(P->flags),
+            (P->nL > 1 && P->side / (double)(1 << l) > P->HX) ? 1 : 0);
         P->launches++;
     }
     for (int l = 0; l < P->n_levels; ++l) {

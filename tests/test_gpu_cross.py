@@ -154,3 +154,32 @@ def test_cross_fit_cache():
     gpu_eval(plan, torch, src, q)
     s3 = plan.stats()
     assert s3["n_cross_fits_last"] > 0
+
+
+def test_stacked_cross_rule_tree_lists_and_fp64_parity():
+    """Slabs 0.1 from the interfaces (HX = 0.4): the stacked cross-layer
+    admissibility rule is active; trees and lists stay bit-exact and the FP64
+    form matches the oracle's TE-FMM given the plan's cross-layer fits."""
+    torch = need_gpu()
+    w = W.three_layer_slabs(240, 3, 8, seed=4, half_width=0.5, n_images=16)
+    med, img = oracle_images(w)
+    plan = make_plan(w)
+    push_images(plan, img)
+    phi = gpu_eval(plan, torch, w.src, w.q)
+    f = TEFMM(med, img, w.p, w.leaf_cap, cross_images=dict(plan.cross_images()),
+              n_images=w.n_images).setup(w.src, w.src)
+    tr = f.tr
+    assert abs(tr.HX - 0.4) < 1e-12
+    g = plan.export_tree()
+    assert g["n_nodes"] == tr.n_nodes
+    for key, ref in (("layer", tr.layer), ("level", tr.level), ("ix", tr.ix), ("iy", tr.iy),
+                     ("iz", tr.iz), ("parent", tr.parent), ("s0", tr.s0), ("t1", tr.t1)):
+        assert np.array_equal(g[key].astype(np.int64), np.asarray(ref, dtype=np.int64)), key
+    vp, vs, npp, ns_ = plan.export_lists()
+    (rvp, rvs), (rnp, rns) = oracle_lists_csr(tr, f.lists, tr.n_nodes)
+    assert np.array_equal(vp, rvp) and np.array_equal(vs, rvs)
+    assert np.array_equal(npp, rnp) and np.array_equal(ns_, rns)
+    ref = f.evaluate(w.q)
+    err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    print(f'stacked cross rule, FP64 form vs oracle TE-FMM: {err:.3e}')
+    assert err <= FP64_TOL, err

@@ -19,8 +19,10 @@ What fixes them independently of the oracle's own formulas:
   (same-layer images + per-source-point cross-layer fits), with an error that
   falls as p rises; a planted sign error in the down-going cross-layer tables
   is detected;
-* the cross-layer split rule: no cross-layer pair is left to the near field,
-  and the lists still cover every (target, source) pair exactly once.
+* the cross-layer split rule and the stacked cross-layer admissibility rule:
+  no cross-layer pair is left to the near field, and the lists still cover
+  every (target, source) pair exactly once; on slabs 0.1 from the interfaces
+  the admissibility rule lowers the cross-layer error by two orders.
 """
 import numpy as np
 import pytest
@@ -166,10 +168,21 @@ def test_homogeneous_multi_layer_fmm_is_free_space():
     assert errs[1] < 0.1 * errs[0] and errs[1] < 1e-3, errs
 
 
-def test_cross_split_rule_lists_partition_pairs():
-    w = W.cross_layer_slabs(80, 0, 5, seed=1)
+@pytest.mark.parametrize("case", ["wide_gaps", "slabs_near_interfaces"])
+def test_cross_split_rule_lists_partition_pairs(case):
+    """The lists cover every (target, source) pair once; with slabs 0.1 from
+    the interfaces the stacked cross-layer admissibility rule is active (HX = 0.4
+    < the box size at levels 0-3) and must keep that property."""
+    if case == "wide_gaps":
+        w = W.cross_layer_slabs(80, 0, 5, seed=1)
+    else:
+        w = W.three_layer_slabs(300, 0, 8, seed=3, half_width=0.5)
     med = Medium(w.interfaces, w.k)
-    tr = Trees(med, w.src, w.src, w.leaf_cap)
+    tr = Trees(med, w.src, w.src, w.leaf_cap, zext=w.zext)
+    if case != "wide_gaps":
+        assert abs(tr.HX - 0.4) < 1e-12
+        assert any(tr.cross_colleague(a, b) for a in range(tr.n_nodes) for b in range(tr.n_nodes)
+                   if tr.level[a] == tr.level[b] and tr.level[a] <= 3)
     ns = len(w.src)
     cover = np.zeros((ns, ns), dtype=np.int64)
     for lt in range(3):
@@ -179,7 +192,7 @@ def test_cross_split_rule_lists_partition_pairs():
                 assert not P, "cross-layer pair left to the near field"
             for t, lst in V.items():
                 for s in lst:
-                    assert not tr.adjacent(t, s)
+                    assert not tr.adjacent(t, s) and not tr.cross_colleague(t, s)
                     cover[np.ix_(tr.tperm[tr.t0[t]:tr.t1[t]], tr.sperm[tr.s0[s]:tr.s1[s]])] += 1
             for t, lst in P.items():
                 for s in lst:
@@ -196,3 +209,31 @@ def test_cross_sum_by_reciprocity_matches_per_source_fits():
     a = CrossDirect(med, w.zext, n_images=16).potential(w.src, w.q, tgt)
     b = cross_sum_by_reciprocity(med, w.zext, w.src, w.q, tgt, n_images=16)
     assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(a), np.linalg.norm(a - b) / np.linalg.norm(a)
+
+
+@pytest.mark.slow
+def test_stacked_cross_pairs_rule_improves_accuracy():
+    """Slabs 0.1 from the interfaces, p = 3: taking stacked coarse cross-layer
+    pairs as translations (HX = inf) vs pairing their children (HX = 0.4)."""
+    import oracle.tefmm as T
+    w = W.three_layer_slabs(180, 3, 8, seed=4, half_width=0.5)
+    med = Medium(w.interfaces, w.k)
+    img = ImageTable(med, w.zext, n_images=16)
+    ref = direct_sum(med, img, w.src, w.q, w.src) + \
+        CrossDirect(med, w.zext, n_images=16).potential(w.src, w.q, w.src)
+    errs = {}
+    for name, lim in (("rule", None), ("no_rule", np.inf)):
+        f = TEFMM(med, img, 3, w.leaf_cap, n_images=16)
+        if lim is not None:
+            orig = T.cross_box_limit
+            T.cross_box_limit = lambda med_, zext_: lim
+            try:
+                f.setup(w.src, w.src)
+            finally:
+                T.cross_box_limit = orig
+        else:
+            f.setup(w.src, w.src)
+        phi = f.evaluate(w.q)
+        errs[name] = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    print(errs)
+    assert errs["rule"] < 0.2 * errs["no_rule"], errs
