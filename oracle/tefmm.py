@@ -30,7 +30,7 @@ Readings where the paper is silent (all stated the same way for the CUDA path):
   keeps leaves of different layers apart, so that every cross-layer
   interaction is an M2L (V-list) pair.
 * Cross-layer admissibility (a reading): two split boxes of different layers
-  at a level where the box size exceeds HX (= 2 min over interfaces of the
+  at a level where the box size exceeds HX (= 4 min over interfaces of the
   summed gaps between the particle slabs and the interface), horizontally
   within one box of each other (|dx|, |dy| <= 1), are not translated but
   treated like adjacent boxes (their children are paired).  Such vertically
@@ -98,7 +98,7 @@ def morton_decode(prefix, level):
 
 
 def cross_box_limit(med, zext):
-    """HX = 2 min over interfaces of (gap of the slab above + gap of the slab below),
+    """HX = 4 min over interfaces of (gap of the slab above + gap of the slab below),
     the gaps between the particle slabs (zext) and the interface; interfaces with
     no gap are skipped; +inf when no interface counts (or no zext)."""
     if zext is None or med.n_layers < 2:
@@ -108,7 +108,7 @@ def cross_box_limit(med, zext):
         gm = (float(zext[m][0]) - float(med.d[m])) + (float(med.d[m]) - float(zext[m + 1][1]))
         if gm > 0.0:
             g.append(gm)
-    return 2.0 * min(g) if g else np.inf
+    return 4.0 * min(g) if g else np.inf
 
 
 def root_cube(points):

@@ -211,7 +211,7 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
     }
     tefmm_plan_s *P = new tefmm_plan_s();
     P->leaf_cap_eff = o.leaf_cap;      // 0: chosen by the autotuner on the first evaluation
-    // HX = 2 min over interfaces of (gap above + gap below) between the particle
+    // HX = 4 min over interfaces of (gap above + gap below) between the particle
     // slabs and the interface; interfaces without a gap do not count
     {
         double gmin = INFINITY;
@@ -219,7 +219,7 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
             const double gm = (o.zext[2 * m] - interfaces[m]) + (interfaces[m] - o.zext[2 * (m + 1) + 1]);
             if (gm > 0.0 && gm < gmin) gmin = gm;
         }
-        P->HX = gmin < INFINITY ? 2.0 * gmin : INFINITY;
+        P->HX = gmin < INFINITY ? 4.0 * gmin : INFINITY;
     }
     P->nL = n_layers;
     for (int m = 0; m < n_layers - 1; ++m) P->d[m] = interfaces[m];

@@ -157,7 +157,7 @@ def test_cross_fit_cache():
 
 
 def test_stacked_cross_rule_tree_lists_and_fp64_parity():
-    """Slabs 0.1 from the interfaces (HX = 0.4): the stacked cross-layer
+    """Slabs 0.1 from the interfaces (HX = 0.8): the stacked cross-layer
     admissibility rule is active; trees and lists stay bit-exact and the FP64
     form matches the oracle's TE-FMM given the plan's cross-layer fits."""
     torch = need_gpu()
@@ -169,7 +169,7 @@ def test_stacked_cross_rule_tree_lists_and_fp64_parity():
     f = TEFMM(med, img, w.p, w.leaf_cap, cross_images=dict(plan.cross_images()),
               n_images=w.n_images).setup(w.src, w.src)
     tr = f.tr
-    assert abs(tr.HX - 0.4) < 1e-12
+    assert abs(tr.HX - 0.8) < 1e-12
     g = plan.export_tree()
     assert g["n_nodes"] == tr.n_nodes
     for key, ref in (("layer", tr.layer), ("level", tr.level), ("ix", tr.ix), ("iy", tr.iy),

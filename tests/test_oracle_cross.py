@@ -171,8 +171,8 @@ def test_homogeneous_multi_layer_fmm_is_free_space():
 @pytest.mark.parametrize("case", ["wide_gaps", "slabs_near_interfaces"])
 def test_cross_split_rule_lists_partition_pairs(case):
     """The lists cover every (target, source) pair once; with slabs 0.1 from
-    the interfaces the stacked cross-layer admissibility rule is active (HX = 0.4
-    < the box size at levels 0-3) and must keep that property."""
+    the interfaces the stacked cross-layer admissibility rule is active (HX = 0.8
+    < the box size at levels 0-2) and must keep that property."""
     if case == "wide_gaps":
         w = W.cross_layer_slabs(80, 0, 5, seed=1)
     else:
@@ -180,9 +180,9 @@ def test_cross_split_rule_lists_partition_pairs(case):
     med = Medium(w.interfaces, w.k)
     tr = Trees(med, w.src, w.src, w.leaf_cap, zext=w.zext)
     if case != "wide_gaps":
-        assert abs(tr.HX - 0.4) < 1e-12
+        assert abs(tr.HX - 0.8) < 1e-12
         assert any(tr.cross_colleague(a, b) for a in range(tr.n_nodes) for b in range(tr.n_nodes)
-                   if tr.level[a] == tr.level[b] and tr.level[a] <= 3)
+                   if tr.level[a] == tr.level[b] and tr.level[a] <= 2)
     ns = len(w.src)
     cover = np.zeros((ns, ns), dtype=np.int64)
     for lt in range(3):
@@ -214,7 +214,7 @@ def test_cross_sum_by_reciprocity_matches_per_source_fits():
 @pytest.mark.slow
 def test_stacked_cross_pairs_rule_improves_accuracy():
     """Slabs 0.1 from the interfaces, p = 3: taking stacked coarse cross-layer
-    pairs as translations (HX = inf) vs pairing their children (HX = 0.4)."""
+    pairs as translations (HX = inf) vs pairing their children (HX = 0.8)."""
     import oracle.tefmm as T
     w = W.three_layer_slabs(180, 3, 8, seed=4, half_width=0.5)
     med = Medium(w.interfaces, w.k)
