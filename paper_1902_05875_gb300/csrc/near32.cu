@@ -24,6 +24,7 @@
 // distant images) goes through FP32, written as
 //   g - 1 = (e^{ik delta} - 1 - delta/R0) / (1 + delta/R0),
 //   e^{a+ib} - 1 = expm1(a) cos b - 2 sin^2(b/2) + i e^a sin b,
+// (one sincos of b/2: sin b = 2 sin(b/2) cos(b/2), cos b - 1 = -2 sin^2(b/2)),
 // so that its rounding is relative to |g - 1|, not to 1.
 // sin, cos, exp and expm1 are CUDA's accurate single-precision functions
 // (their arguments here are small: k r within a near box pair and k delta).
@@ -184,11 +185,12 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                             float der = (Dr * sr + Di * si) * isn, dei = (Di * sr - Dr * si) * isn;
                             // e^{i k delta} - 1
                             float ph = kr * der - ki * dei, dec = -(kr * dei + ki * der);
-                            float sn, cs, sh, ch;
-                            sincosf(ph, &sn, &cs);
+                            // half-angle: sin ph = 2 s c, cos ph = 1 - 2 s^2 (one sincos)
+                            float sh, ch;
                             sincosf(0.5f * ph, &sh, &ch);
+                            const float sn = 2.f * sh * ch, cm1 = -2.f * sh * sh;   // cos ph - 1
                             float em1 = expm1f(dec);
-                            float ur = em1 * cs - 2.f * sh * sh, ui = (1.f + em1) * sn;
+                            float ur = em1 * (1.f + cm1) + cm1, ui = (1.f + em1) * sn;
                             // delta / R0 and g - 1 = (e^{ik delta} - 1 - delta/R0) / (1 + delta/R0)
                             float tr = der * ir0.x - dei * ir0.y, ti = der * ir0.y + dei * ir0.x;
                             float nr = ur - tr, ni = ui - ti;
