@@ -430,7 +430,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single"},
         "phases_ms": ph,
         "counts": {"nodes": st["n_nodes"], "levels": st["n_levels"], "v_pairs": st["n_v_pairs"],
-                   "p2p_pairs": st["n_p2p_pairs"], "tables": st["n_tables"],
+                   "p2p_pairs": st["n_p2p_pairs"], "tables": st["n_tables"], "tables_built": st["n_tables_built"],
                    "cross_tables": st["n_cross_tables"], "cross_fits": st["n_cross_fits"],
                    "images_total": st["n_images_total"]},
         "fits": {"same_layer_max_resid": st["fit_max_resid"],

@@ -96,6 +96,9 @@ typedef struct {
     int leaf_cap_used;     /* leaf cap of the last evaluation (the autotuner's choice
                               when the plan was made with leaf_cap = 0)               */
     double ms_autotune;    /* time of the autotuner's trial evaluations               */
+    int n_tables_built;    /* last eval: tables computed by the recurrence; the other
+                              n_tables - n_tables_built are copied from one of these by
+                              the reflection x -> -x, y -> -y and swap x <-> y symmetry */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,

@@ -179,6 +179,7 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
     }
     o->leaf_cap_used = P->leaf_cap_eff;
     o->ms_autotune = P->ms_autotune;
+    o->n_tables_built = P->n_tables_built;
     return TEFMM_OK;
 }
 

@@ -127,13 +127,6 @@ __global__ void k_xshift_beta(int nn, TreeArrays T, Cube cb, XGeom geo, int p, i
     }
 }
 
-// offset of slice k3' in a packed cross-layer table
-__host__ __device__ inline int slice_off(int p, int k3p) {
-    int o = 0;
-    for (int j = 0; j < k3p; ++j) o += ncoef(2 * p - j);
-    return o;
-}
-
 // first cross-layer table and first cross-layer chunk (keys are sorted, kind 2 last)
 __global__ void k_first_cross(int ntab, const uint64_t *__restrict__ tkey, int64_t nch,
                               const int *__restrict__ chunk_table, int *out) {
@@ -153,9 +146,10 @@ __global__ void k_first_cross(int ntab, const uint64_t *__restrict__ tkey, int64
 __global__ void k_xtables(int nx, const uint64_t *__restrict__ keys, Cube cb, int p,
                           const int *__restrict__ mi_g, XGeom geo, const int2 *__restrict__ xrange,
                           const cplx *__restrict__ xA, const cplx *__restrict__ xZ, int NX,
-                          cplx *__restrict__ xt) {
+                          const int *__restrict__ rep_code, int first, cplx *__restrict__ xt) {
     int tb = blockIdx.x, k3p = blockIdx.y;
     if (tb >= nx || k3p > p) return;
+    if ((rep_code[first + tb] >> 3) != first + tb) return;   // copied by symmetry
     const int P2 = 2 * p - k3p, n2 = ncoef(P2), nfull = ncoef(2 * p);
     extern __shared__ double sm[];
     cplx *a = (cplx *)sm;
@@ -432,10 +426,11 @@ int cross_tables(tefmm_plan_s *P, cudaStream_t st) {
     dim3 grid((unsigned)nx, (unsigned)(P->p + 1));
     k_xtables<<<grid, 256, sm, st>>>(nx, dp<uint64_t>(P->table_slot) + P->x_first_table, cube_of(P),
                                      P->p, dp<int>(P->d_mi), geometry(P), dp<int2>(P->d_xrange),
-                                     dp<cplx>(P->d_xA), dp<cplx>(P->d_xZ), P->NX, dp<cplx>(P->xtables));
+                                     dp<cplx>(P->d_xA), dp<cplx>(P->d_xZ), P->NX,
+                                     dp<int>(P->table_rep), P->x_first_table, dp<cplx>(P->xtables));
     P->launches++;
     CUDA_TRY(cudaGetLastError());
-    return TEFMM_OK;
+    return tables_expand(P, P->x_first_table, nx, P->p + 1, dp<cplx>(P->xtables), P->NX, st);
 }
 
 int cross_apply(tefmm_plan_s *P, cudaStream_t st) {

@@ -178,7 +178,9 @@ struct tefmm_plan_s {
     // M2L grouping and tables
     DBuf keyslot_flag, keyslot_table, pair_t, pair_s, pair_slot, pair_slot_sorted, pair_idx,
         pair_idx_sorted, chunk_key, chunk_start, chunk_cnt, tables, table_slot, seg_tmp;
+    DBuf table_rep;           // per table: representative * 8 + symmetry code
     int n_tables = 0;
+    int n_tables_built = 0;   // tables computed by the recurrence (the rest by symmetry)
     int64_t n_chunks = 0;
     int chunk_pairs = 16;     // pairs per M2L work chunk (FP64 SIMT: 16, tensor cores: 512)
 
@@ -283,6 +285,8 @@ int plan_fit_images(tefmm_plan_s *P, cudaStream_t st);
 int fit_cross_jobs(tefmm_plan_s *P, const std::vector<CrossFitKey> &keys, cudaStream_t st);
 // cross.cu
 double cross_wmin(const tefmm_plan_s *P, int lt, int dir);
+int tables_expand(tefmm_plan_s *P, int first, int ntab, int nslices, cplx *tabs, int64_t stride,
+                  cudaStream_t st);
 int cross_prepare(tefmm_plan_s *P, cudaStream_t st);
 int cross_tables(tefmm_plan_s *P, cudaStream_t st);
 int cross_apply(tefmm_plan_s *P, cudaStream_t st);

@@ -240,6 +240,69 @@ __global__ void k_seg_start(int64_t n, const int *__restrict__ head, const int *
     table_key[s] = keys[i];
 }
 
+// Symmetry of the derivative tables.  A table takes D^g / g! of a function of
+// (x^2 + y^2, z) at (X, Y) = (dx h, dy h); the key's other fields do not
+// involve dx, dy.  Hence for signs sx, sy:
+//   T(sx X, sy Y)[g1, g2, g3] = sx^g1 sy^g2 T(X, Y)[g1, g2, g3],
+//   T(Y, X)[g1, g2, g3]       = T(X, Y)[g2, g1, g3].
+// Of the (up to eight) keys that differ only by these maps, the first in key
+// order (its representative) is computed by the recurrence and the others are
+// copied from it.  rep_code[i] = rep * 8 + code, code bit 0: sx = -1, bit 1:
+// sy = -1, bit 2: swapped, so that T_i[g] = sx^g1 sy^g2 T_rep[g or (g2, g1, g3)].
+// The sign flips reproduce the recurrence's own result bit for bit; the swap
+// changes its rounding only (the x and y terms are summed in the other order).
+__global__ void k_table_rep(int ntab, const uint64_t *__restrict__ keys, int *__restrict__ rep_code,
+                            int *__restrict__ nrep) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntab) return;
+    const uint64_t key = keys[i];
+    const int dx = (int)((key >> 50) & 7) - 3, dy = (int)((key >> 47) & 7) - 3;
+    const uint64_t base = key & ~(63ULL << 47);
+    int rep = i, rdx = dx, rdy = dy;
+    for (int v = 1; v < 8; ++v) {
+        int a = (v & 4) ? dy : dx, b = (v & 4) ? dx : dy;
+        if (v & 1) a = -a;
+        if (v & 2) b = -b;
+        const uint64_t kv = base | ((uint64_t)(a + 3) << 50) | ((uint64_t)(b + 3) << 47);
+        int lo = 0, hi = rep;   // keys are sorted: search the ones before the current representative
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (keys[mid] < kv) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo < rep && keys[lo] == kv) {
+            rep = lo;
+            rdx = a;
+            rdy = b;
+        }
+    }
+    int code;
+    if (abs(dx) == abs(rdx) && abs(dy) == abs(rdy)) code = (dx != rdx) | ((dy != rdy) << 1);
+    else code = 4 | (dx != rdy) | ((dy != rdx) << 1);
+    rep_code[i] = rep * 8 + code;
+    if (rep == i) atomicAdd(nrep, 1);
+}
+
+// copy the tables [first, first + ntab) that are not representatives from
+// their representative: grid (ntab, slices), slice s holds ncoef(2p - s) entries
+__global__ void k_table_expand(int ntab, int first, const int *__restrict__ rep_code,
+                               const int *__restrict__ mi, int p, cplx *__restrict__ tabs, int64_t stride) {
+    const int t = blockIdx.x, s = blockIdx.y;
+    if (t >= ntab) return;
+    const int rc = rep_code[first + t];
+    const int rep = (rc >> 3) - first, code = rc & 7;
+    if (rep == t) return;
+    const int n = ncoef(2 * p - s), off = slice_off(p, s);
+    const cplx *src = tabs + (int64_t)rep * stride + off;
+    cplx *dst = tabs + (int64_t)t * stride + off;
+    for (int g = threadIdx.x; g < n; g += blockDim.x) {
+        const int g1 = mi[3 * g], g2 = mi[3 * g + 1], g3 = mi[3 * g + 2];
+        const cplx v = src[(code & 4) ? midx(g2, g1, g3) : g];
+        const bool neg = ((code & 1) && (g1 & 1)) != ((code & 2) && (g2 & 1));
+        dst[g] = neg ? mkc(-v.x, -v.y) : v;
+    }
+}
+
 __global__ void k_chunk_heads(int64_t n, const uint64_t *__restrict__ keys,
                               const int *__restrict__ seg_incl, const int *__restrict__ seg_start,
                               int *__restrict__ chead, int chsize) {
@@ -277,9 +340,10 @@ __global__ void k_chunk_cnt(int nchunks, int64_t nvalid, const int *__restrict__
 }
 
 __global__ void k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube cb, int P2, int np2,
-                         const int *__restrict__ mi_g, ImgView im, cplx *__restrict__ tables) {
+                         const int *__restrict__ mi_g, ImgView im, const int *__restrict__ rep_code,
+                         cplx *__restrict__ tables) {
     int tb = blockIdx.x;
-    if (tb >= ntab) return;
+    if (tb >= ntab || (rep_code[tb] >> 3) != tb) return;   // copied by symmetry
     extern __shared__ double sm[];
     cplx *a = (cplx *)sm;
     cplx *b = a + np2;
@@ -556,6 +620,7 @@ int upward_pass(tefmm_plan_s *P, cudaStream_t st) {
 int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     const int64_t nv = P->n_v;
     P->n_tables = 0;
+    P->n_tables_built = 0;
     P->n_chunks = 0;
     P->x_first_table = 0;
     P->x_first_chunk = 0;
@@ -605,6 +670,11 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     k_seg_start<<<grid_for(ni, 256), 256, 0, st>>>(ni, head, seg, keys, dp<int>(P->keyslot_flag),
                                                    dp<uint64_t>(P->table_slot));
     P->launches++;
+    TRY(dbuf_ensure(P->table_rep, (size_t)(nseg + 1) * 4));
+    CUDA_TRY(cudaMemsetAsync(dp<int>(P->counters) + 2, 0, 4, st));
+    k_table_rep<<<grid_for(nseg, 256), 256, 0, st>>>(nseg, dp<uint64_t>(P->table_slot),
+                                                     dp<int>(P->table_rep), dp<int>(P->counters) + 2);
+    P->launches++;
     P->chunk_pairs = (P->opt.precision == TEFMM_MIXED) ? 128 * TC_MT : CH;
     k_chunk_heads<<<grid_for(ni, 256), 256, 0, st>>>(ni, keys, seg, dp<int>(P->keyslot_flag), chead,
                                                      P->chunk_pairs);
@@ -614,6 +684,7 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     int nch = 0, nvalid_i = 0;
     CUDA_TRY(cudaMemcpyAsync(&nch, dp<int>(P->keyslot_table) + ni - 1, 4, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaMemcpyAsync(&nvalid_i, P->counters.p, 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&P->n_tables_built, dp<int>(P->counters) + 2, 4, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     P->n_chunks = nch;
     TRY(dbuf_ensure(P->chunk_start, (size_t)(nch + 1) * 4));
@@ -643,7 +714,17 @@ int m2l_tables(tefmm_plan_s *P, cudaStream_t st) {
     TRY(smem_optin(k_tables));
     k_tables<<<ntab, 256, sm, st>>>(ntab, dp<uint64_t>(P->table_slot), cube_of(P),
                                            2 * P->p, np2, dp<int>(P->d_mi), img_view(P),
-                                           dp<cplx>(P->tables));
+                                           dp<int>(P->table_rep), dp<cplx>(P->tables));
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return tables_expand(P, 0, ntab, 1, dp<cplx>(P->tables), np2, st);
+}
+
+int tables_expand(tefmm_plan_s *P, int first, int ntab, int nslices, cplx *tabs, int64_t stride,
+                  cudaStream_t st) {
+    if (ntab == 0) return TEFMM_OK;
+    k_table_expand<<<dim3((unsigned)ntab, (unsigned)nslices), 256, 0, st>>>(
+        ntab, first, dp<int>(P->table_rep), dp<int>(P->d_mi), P->p, tabs, stride);
     P->launches++;
     CUDA_TRY(cudaGetLastError());
     return TEFMM_OK;

@@ -81,6 +81,14 @@ inline Cube cube_of(tefmm_plan_s *P) {
 }
 
 
+// offset of slice k3' in a packed cross-layer table (slice k3' holds the
+// ncoef(2p - k3') derivatives of order <= 2p - k3'); a same-layer table is slice 0
+__host__ __device__ inline int slice_off(int p, int k3p) {
+    int o = 0;
+    for (int j = 0; j < k3p; ++j) o += ncoef(2 * p - j);
+    return o;
+}
+
 // Cross-layer M2L key (kind 2): level(5) lt(4) dx+3(3) dy+3(3) ls(4) iz_t(20) iz_s(20).
 // Same-layer keys (kinds 0 and 1) sort before it.
 __host__ __device__ inline uint64_t xkey(int l, int lt, int ls, int dx, int dy, int izt, int izs) {

@@ -259,7 +259,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
                    &P->near_ptr, &P->near_src, &P->near_tmp, &P->near_cnt, &P->alpha, &P->beta,
                    &P->keyslot_flag, &P->keyslot_table, &P->pair_t, &P->pair_s, &P->pair_slot,
                    &P->pair_slot_sorted, &P->pair_idx, &P->pair_idx_sorted, &P->chunk_key,
-                   &P->chunk_start, &P->chunk_cnt, &P->tables, &P->table_slot, &P->seg_tmp,
+                   &P->chunk_start, &P->chunk_cnt, &P->tables, &P->table_slot, &P->seg_tmp, &P->table_rep,
                    &P->h_in, &P->h_out, &P->tc_ah, &P->tc_al, &P->tc_bt, &P->tc_cfA, &P->tc_cfB, &P->tc_W};
     for (DBuf *b : all) dbuf_free(*b);
     cross_release(P);

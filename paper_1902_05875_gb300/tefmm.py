@@ -39,7 +39,7 @@ class Stats(ctypes.Structure):
                 ("n_cross_fits_last", ctypes.c_int), ("ms_cross_fit", ctypes.c_double),
                 ("fit_max_resid_cross", ctypes.c_double), ("ms_cross_tables", ctypes.c_double),
                 ("ms_cross_m2l", ctypes.c_double), ("leaf_cap_used", ctypes.c_int),
-                ("ms_autotune", ctypes.c_double)]
+                ("ms_autotune", ctypes.c_double), ("n_tables_built", ctypes.c_int)]
 
 
 EXPORTED = [

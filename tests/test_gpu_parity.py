@@ -71,6 +71,9 @@ def test_fp64_fmm_matches_oracle_fmm(w):
     ref = f.evaluate(w.q)
     err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
     assert err <= FP64_TOL, err
+    # most tables come from a reflected or swapped key's table (x <-> -x, y <-> -y, x <-> y)
+    st = plan.stats()
+    assert 0 < st["n_tables_built"] < st["n_tables"], st
 
 
 def test_distinct_targets_and_ragged_sizes():

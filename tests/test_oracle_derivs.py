@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 from scipy.signal import convolve
 
-from oracle.derivs import taylor_phi, multi_indices, index_map
+from oracle.derivs import taylor_phi, taylor_h0, multi_indices, index_map
 
 
 def _series_phi(x, k, P):
@@ -119,3 +119,24 @@ def test_first_and_second_derivatives_finite_difference():
         m2[i] = 2
         assert abs(a[im[tuple(m1)]] - d1) < 1e-7
         assert abs(a[im[tuple(m2)]] - d2) < 1e-5
+
+
+def test_reflection_and_swap_symmetry():
+    """D^g / g! of a function of (x^2 + y^2, z): reflecting x (or y) flips the
+    sign of the entries with odd g1 (g2), swapping x and y swaps g1 and g2.
+    The device path builds one table per class of keys related by these maps
+    and copies the rest."""
+    P = 8
+    k = 2.0 + 0.3j
+    X, Y, W = 0.7, -0.4, 0.9 - 0.35j
+    mi = multi_indices(P)
+    im = index_map(P)
+    T = taylor_h0(X, Y, W, k, P)
+    g1, g2 = mi[:, 0], mi[:, 1]
+    for sx in (1, -1):
+        for sy in (1, -1):
+            R = taylor_h0(sx * X, sy * Y, W, k, P)
+            assert np.allclose(R, T * sx ** g1 * sy ** g2, rtol=1e-13, atol=0)
+            S = taylor_h0(sx * Y, sy * X, W, k, P)
+            perm = [im[(int(b), int(a), int(c))] for a, b, c in mi]
+            assert np.allclose(S, T[perm] * sx ** g1 * sy ** g2, rtol=1e-13, atol=0)
