@@ -29,7 +29,7 @@ namespace {
 
 constexpr int TM = 128;      // pairs per CTA (MMA M)
 constexpr int KC = 8;        // K elements per pipeline stage (one MMA K step)
-constexpr int NST = 4;       // pipeline stages (shared-memory buffers)
+constexpr int NST = 5;       // pipeline stages (shared-memory buffers)
 constexpr int NTHR = 256;
 constexpr long SPIN_LIMIT = 4000000;
 constexpr size_t W_BATCH_BYTES = (size_t)2 << 30;   // W^T blocks held at once, at most
@@ -160,17 +160,41 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
     }
 }
 
+// wait until at most n of this thread's cp.async groups are pending
+__device__ __forceinline__ void cp_async_wait(int n) {
+    if (n <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    else if (n == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else if (n == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+    else asm volatile("cp.async.wait_group 3;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
+}
+
 // One CTA: one chunk of up to chunk_pairs pairs of one key, and one slice of
-// NC output columns.  The chunk is taken in passes of MT tiles of TM = 128
-// pairs; TMEM holds one 128 x NC FP32 accumulator per tile (MT * NC <= 512
-// columns), so every W^T block brought in serves MT * 128 pairs.  The K
-// dimension runs through a ring of NST shared-memory stages of KC = 8: the
-// copies of stage c + NST - 1 (one bulk copy of the W^T block completing on an
-// mbarrier, 16-byte asynchronous copies of the pairs' moment rows) are issued
-// as soon as the MMAs of stage c - 1 have finished, so three stages of copies
-// are in flight while the tensor core works.  Thread 0 issues 3 MMAs per tile
-// (hi.hi, hi.lo, lo.hi) and commits them to the stage's mbarrier.
-__global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
+// NC output columns, taken in passes of MT tiles of TM = 128 pairs; TMEM holds
+// one 128 x NC FP32 accumulator per tile (MT * NC <= 512 columns).  The K
+// dimension runs through a ring of NST shared-memory stages of KC = 8,
+// warp-specialised:
+//  * warps 0-7 (producers): for stage g they wait until the MMAs that last
+//    read the stage's buffer are done (empty[g % NST], committed by the MMA
+//    warp), thread 0 starts the bulk copy of the W^T block (completing on
+//    wbar), and every thread issues its two 16-byte copies of moment rows
+//    (addresses fixed per pass).  LAG stages later the thread waits for its
+//    own copies, fences them for the tensor core (async proxy) and arrives on
+//    full[g % NST];
+//  * warp 8, lane 0 (MMA issuer): waits full and wbar of stage g, issues the
+//    3 MMAs per tile (hi.hi, hi.lo, lo.hi) and commits them to empty.
+// After a pass the producers wait for the last commit and move the
+// accumulators out of TMEM (the epilogue).  Every wait is bounded; on a
+// timeout the CTA raises a flag, skips its output, waits for its copies and
+// MMAs in flight (again bounded) and releases its TMEM.
+constexpr int NPROD = 256;              // producer / epilogue threads
+constexpr int NTHR_TC = NPROD + 32;     // + the MMA warp
+constexpr int LAG = 2;                  // stages a producer keeps in flight before arriving
+
+__global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
     // 1-D grid: the nsplit column slices of one chunk are adjacent blocks, so
     // they run together and share the chunk's moment rows through L2
     const int c = blockIdx.x / a.nsplit;
@@ -183,10 +207,10 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     const int xbytes = MT * tbytes;
     const int wbytes = NC * KC * 4;
     const int stbytes = 2 * xbytes + 2 * wbytes;
-    __shared__ __align__(8) uint64_t mbar[NST], wbar[NST];
+    __shared__ __align__(8) uint64_t full[NST], empty[NST], wbar[NST];
     __shared__ uint32_t tmem_base;
     __shared__ int s_src[4 * TM], s_tgt[4 * TM];
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_issued, s_committed;
 
     const int tb = a.chunk_table[c];
     const int cnt = a.chunk_cnt[c];
@@ -194,7 +218,11 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     const int nk = a.Kpad / KC;
     const float *Wkey = a.W + ((int64_t)(tb - a.tab_base) * a.nsplit + slice) * nk * (2 * NC * KC);
 
-    if (tid == 0) s_fail = 0;
+    if (tid == 0) {
+        s_fail = 0;
+        s_issued = 0;        // stages whose W^T copy was started
+        s_committed = -1;    // last stage whose MMAs were committed
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(su32(&tmem_base)), "r"(a.tcols));
@@ -202,7 +230,8 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     }
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&mbar[i])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(su32(&full[i])), "r"(NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&empty[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&wbar[i])));
         }
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -214,14 +243,12 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NC >> 3) << 17) |
                            ((uint32_t)(TM >> 4) << 24);
     const int n0 = slice * NC;             // first output column of this CTA
-    bool ok = true;
     int gbase = 0;                         // global index of the pass's first K stage
-    int gissued = 0;                       // K stages whose copies were issued (all passes)
 
     for (int pb = 0; pb < cnt; pb += MT * TM) {
         const int npair = min(MT * TM, cnt - pb);
         const int ntile = (npair + TM - 1) / TM;
-        for (int r = tid; r < MT * TM; r += NTHR) {
+        for (int r = tid; r < MT * TM; r += NTHR_TC) {
             if (r < npair) {
                 int e = a.items[st + pb + r] >> 1;
                 s_src[r] = a.v_src[e];
@@ -232,49 +259,65 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
             }
         }
         __syncthreads();
-        // copies of K stage kc of this pass into buffer g % NST (g = gbase + kc),
-        // once the MMAs that last read that buffer (stage g - NST) are done
-        auto issue = [&](int kc) {
-            const int g = gbase + kc, sb = g % NST;
-            if (g >= NST) {
-                if (!mbar_wait(su32(&mbar[sb]), ((g - NST) / NST) & 1)) ok = false;
+        if (warp < NPROD / 32) {
+            // ---------------------------------------------------------- producers
+            // thread t copies 16 bytes (4 K values) q = t & 1 of row t >> 1 of every
+            // tile, hi and lo: source addresses advance by KC floats per stage
+            const int q = tid & 1, r = tid >> 1;
+            bool okp = true;
+            for (int kc = 0; kc < nk && okp; ++kc) {
+                const int g = gbase + kc, sb = g % NST;
+                if (g >= NST && !mbar_wait(su32(&empty[sb]), ((g - NST) / NST) & 1)) okp = false;
+                if (!okp || *(volatile int *)&s_fail) {
+                    okp = false;
+                    break;
+                }
+                unsigned char *buf = smem + sb * stbytes;
+                if (tid == 0) {
+                    const uint32_t bytes = 2u * (uint32_t)wbytes;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                                 :: "r"(su32(&wbar[sb])), "r"(bytes) : "memory");
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 :: "r"(su32(buf + 2 * xbytes)), "l"(Wkey + (int64_t)kc * (2 * NC * KC)),
+                                    "r"(bytes), "r"(su32(&wbar[sb]))
+                                 : "memory");
+                    s_issued = g + 1;
+                }
+                for (int mt = 0; mt < ntile; ++mt) {
+                    const int s = s_src[mt * TM + r];
+                    const int64_t so = (int64_t)(s >= 0 ? s : 0) * a.Kpad + kc * KC + 4 * q;
+                    const uint32_t dst = su32(buf + mt * tbytes + koff(r, 4 * q));
+                    const uint32_t sz = s >= 0 ? 16u : 0u;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                 :: "r"(dst), "l"(a.ah + so), "r"(sz) : "memory");
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                 :: "r"(dst + (uint32_t)xbytes), "l"(a.al + so), "r"(sz) : "memory");
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+                if (kc >= LAG) {
+                    cp_async_wait(LAG);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(su32(&full[(g - LAG) % NST]));
+                }
             }
-            unsigned char *buf = smem + sb * stbytes;
-            unsigned char *Xh = buf, *Xl = buf + xbytes, *Wh = buf + 2 * xbytes;
-            if (tid == 0) {
-                const uint32_t bytes = 2u * (uint32_t)wbytes;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                             :: "r"(su32(&wbar[sb])), "r"(bytes) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             :: "r"(su32(Wh)), "l"(Wkey + (int64_t)kc * (2 * NC * KC)), "r"(bytes),
-                                "r"(su32(&wbar[sb]))
-                             : "memory");
+            if (okp) {
+                // the last LAG stages of the pass
+                for (int kc = max(nk - LAG, 0); kc < nk; ++kc) {
+                    cp_async_wait(nk - 1 - kc);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_arrive(su32(&full[(gbase + kc) % NST]));
+                }
+            } else {
+                atomicExch(&s_fail, 1);
             }
-            const int c0 = kc * KC;
-            for (int i = tid; i < ntile * TM * 2 * 2; i += NTHR) {
-                const int part = i / (ntile * TM * 2), rem = i % (ntile * TM * 2);
-                const int r = rem >> 1, q = rem & 1;
-                const int s = s_src[r];
-                const float *srcp = s >= 0 ? (part == 0 ? a.ah : a.al) + (int64_t)s * a.Kpad + c0 + 4 * q : a.ah;
-                const uint32_t dst = su32((part == 0 ? Xh : Xl) + (r / TM) * tbytes + koff(r % TM, 4 * q));
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                             :: "r"(dst), "l"(srcp), "r"(s >= 0 ? 16 : 0) : "memory");
-            }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            ++gissued;
-        };
-        for (int kc = 0; kc < NST - 1 && kc < nk; ++kc) issue(kc);
-        for (int kc = 0; kc < nk; ++kc) {
-            const int g = gbase + kc, sb = g % NST;
-            // this stage's moment rows: the later stages of this pass may stay in flight
-            const int pending = min(nk - kc - 1, NST - 2);
-            if (pending >= 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
-            else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
-            else asm volatile("cp.async.wait_group 0;" ::: "memory");
-            if (!mbar_wait(su32(&wbar[sb]), (g / NST) & 1)) ok = false;
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
-            if (tid == 0) {
+        } else if (lane == 0) {
+            // ----------------------------------------------------------- MMA issuer
+            for (int kc = 0; kc < nk; ++kc) {
+                const int g = gbase + kc, sb = g % NST;
+                if (!mbar_wait(su32(&full[sb]), (g / NST) & 1) || !mbar_wait(su32(&wbar[sb]), (g / NST) & 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 unsigned char *buf = smem + sb * stbytes;
                 const uint64_t dwh = sdesc(su32(buf + 2 * xbytes)), dwl = sdesc(su32(buf + 2 * xbytes + wbytes));
@@ -294,40 +337,42 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
                                  :: "r"(d), "l"(dxl), "l"(dwh), "r"(idesc), "r"(1u));
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(su32(&mbar[sb])) : "memory");
+                             :: "r"(su32(&empty[sb])) : "memory");
+                s_committed = g;
             }
-            if (kc + NST - 1 < nk) issue(kc + NST - 1);
         }
         gbase += nk;
-        // the last commit covers every MMA issued before it
-        if (!mbar_wait(su32(&mbar[(gbase - 1) % NST]), ((gbase - 1) / NST) & 1)) ok = false;
-        if (!ok) atomicExch(&s_fail, 1);
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!s_fail) {
-            // epilogue: warp w reads TMEM lanes 32*(w%4).., column half w/4 of each tile
-            const int row = (warp & 3) * 32 + lane;
-            const int chalf = warp >> 2;
-            const int colw = NC / 2;
-            for (int mt = 0; mt < ntile; ++mt) {
-                const int t = s_tgt[mt * TM + row];
-                for (int cc = chalf * colw; cc < (chalf + 1) * colw; cc += 16) {
-                    uint32_t r[16];
-                    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * NC + cc);
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                                 : "r"(taddr));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-                    if (t >= 0) {
-                        float *dst = a.bt + (int64_t)t * a.Ntot + n0 + cc;
-                        for (int q = 0; q < 16; q += 4) {
-                            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
-                                         :: "l"(dst + q), "f"(__uint_as_float(r[q])), "f"(__uint_as_float(r[q + 1])),
-                                            "f"(__uint_as_float(r[q + 2])), "f"(__uint_as_float(r[q + 3]))
-                                         : "memory");
+        if (warp < NPROD / 32) {
+            // ------------------------------------------------------------ epilogue
+            // the last commit covers every MMA of the pass
+            const int gl = gbase - 1;
+            bool ok = !*(volatile int *)&s_fail && mbar_wait(su32(&empty[gl % NST]), (gl / NST) & 1);
+            if (!ok) atomicExch(&s_fail, 1);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (ok) {
+                // warp w reads TMEM lanes 32*(w%4).., column half w/4 of each tile
+                const int row = (warp & 3) * 32 + lane;
+                const int chalf = warp >> 2;
+                const int colw = NC / 2;
+                for (int mt = 0; mt < ntile; ++mt) {
+                    const int t = s_tgt[mt * TM + row];
+                    for (int cc = chalf * colw; cc < (chalf + 1) * colw; cc += 16) {
+                        uint32_t v[16];
+                        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(mt * NC + cc);
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                                       "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                                       "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                                     : "r"(taddr));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;");
+                        if (t >= 0) {
+                            float *dst = a.bt + (int64_t)t * a.Ntot + n0 + cc;
+                            for (int qq = 0; qq < 16; qq += 4) {
+                                asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                                             :: "l"(dst + qq), "f"(__uint_as_float(v[qq])), "f"(__uint_as_float(v[qq + 1])),
+                                                "f"(__uint_as_float(v[qq + 2])), "f"(__uint_as_float(v[qq + 3]))
+                                             : "memory");
+                            }
                         }
                     }
                 }
@@ -339,13 +384,21 @@ __global__ void __launch_bounds__(NTHR, 1) k_m2l_tc(TcArgs a) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (s_fail) break;
     }
-    // no bulk copy of this CTA may still be landing in its shared memory
+    // nothing of this CTA may still be landing in its shared memory or running
+    // on its TMEM: the moment-row copies, the W^T bulk copies, the MMAs
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    for (int sb = 0; sb < NST; ++sb) {
-        if (sb >= gissued) break;
-        const int last = sb + (gissued - 1 - sb) / NST * NST;     // last stage that used buffer sb
-        mbar_wait(su32(&wbar[sb]), (last / NST) & 1);
+    if (tid == 0) {
+        const int gissued = s_issued;
+        for (int sb = 0; sb < NST && sb < gissued; ++sb) {
+            const int last = sb + (gissued - 1 - sb) / NST * NST;     // last stage that used buffer sb
+            mbar_wait(su32(&wbar[sb]), (last / NST) & 1);
+        }
+        const int gc = s_committed;
+        if (gc >= 0) mbar_wait(su32(&empty[gc % NST]), (gc / NST) & 1);
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
     if (s_fail && tid == 0) atomicOr(a.flags, FLAG_CHECK);
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(a.tcols));
@@ -496,7 +549,7 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
             b.chunk_table = a.chunk_table + cb;
             b.chunk_cnt = a.chunk_cnt + cb;
             b.nchunks = ce - cb;
-            k_m2l_tc<<<(unsigned)((int64_t)(ce - cb) * nsplit), NTHR, sm, st>>>(b);
+            k_m2l_tc<<<(unsigned)((int64_t)(ce - cb) * nsplit), NTHR_TC, sm, st>>>(b);
             P->launches++;
         }
         cb = ce;
