@@ -185,11 +185,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 //    own copies, fences them for the tensor core (async proxy) and arrives on
 //    full[g % NST];
 //  * warp 8, lane 0 (MMA issuer): waits full and wbar of stage g, issues the
-//    3 MMAs per tile (hi.hi, hi.lo, lo.hi) and commits them to empty.
-// After a pass the producers wait for the last commit and move the
-// accumulators out of TMEM (the epilogue).  Every wait is bounded; on a
-// timeout the CTA raises a flag, skips its output, waits for its copies and
-// MMAs in flight (again bounded) and releases its TMEM.
+//    3 MMAs per tile (hi.hi, hi.lo, lo.hi) and commits them to empty; after
+//    the pass's last stage it also commits to done (one phase per pass).
+// Warps 0-7 wait on done and move the accumulators out of TMEM (the
+// epilogue).  Every wait is bounded; on a timeout the CTA raises a flag, skips
+// its output, waits for its copies and MMAs in flight (again bounded) and
+// releases its TMEM.
 constexpr int NPROD = 256;              // producer / epilogue threads
 constexpr int NTHR_TC = NPROD + 32;     // + the MMA warp
 constexpr int LAG = 2;                  // stages a producer keeps in flight before arriving
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
     const int xbytes = MT * tbytes;
     const int wbytes = NC * KC * 4;
     const int stbytes = 2 * xbytes + 2 * wbytes;
-    __shared__ __align__(8) uint64_t full[NST], empty[NST], wbar[NST];
+    __shared__ __align__(8) uint64_t full[NST], empty[NST], wbar[NST], done;
     __shared__ uint32_t tmem_base;
     __shared__ int s_src[4 * TM], s_tgt[4 * TM];
     __shared__ int s_fail, s_issued, s_committed;
@@ -234,6 +235,8 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&empty[i])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&wbar[i])));
         }
+        // done: one phase per pass, completed by the commit after the pass's last MMAs
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(su32(&done)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -244,6 +247,7 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
                            ((uint32_t)(TM >> 4) << 24);
     const int n0 = slice * NC;             // first output column of this CTA
     int gbase = 0;                         // global index of the pass's first K stage
+    int npass = 0;                         // passes completed (phase of done)
 
     for (int pb = 0; pb < cnt; pb += MT * TM) {
         const int npair = min(MT * TM, cnt - pb);
@@ -339,14 +343,17 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              :: "r"(su32(&empty[sb])) : "memory");
                 s_committed = g;
+                if (kc == nk - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(su32(&done)) : "memory");
             }
         }
+        __syncwarp();
         gbase += nk;
         if (warp < NPROD / 32) {
             // ------------------------------------------------------------ epilogue
-            // the last commit covers every MMA of the pass
-            const int gl = gbase - 1;
-            bool ok = !*(volatile int *)&s_fail && mbar_wait(su32(&empty[gl % NST]), (gl / NST) & 1);
+            // the pass's last commit (to done) covers every MMA of the pass
+            bool ok = !*(volatile int *)&s_fail && mbar_wait(su32(&done), npass & 1);
             if (!ok) atomicExch(&s_fail, 1);
             asm volatile("tcgen05.fence::after_thread_sync;");
             if (ok) {
@@ -382,6 +389,7 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
+        ++npass;
         if (s_fail) break;
     }
     // nothing of this CTA may still be landing in its shared memory or running
