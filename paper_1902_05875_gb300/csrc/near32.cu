@@ -42,10 +42,10 @@ __device__ __forceinline__ f2 csqrt32(float x, float y) {
     if (r == 0.f) return f2{0.f, 0.f};
     if (x >= 0.f) {
         float t = sqrtf(0.5f * (r + x));
-        return f2{t, y / (2.f * t)};
+        return f2{t, 0.5f * y * __frcp_rn(t)};
     }
     float t = sqrtf(0.5f * (r - x));
-    return f2{fabsf(y) / (2.f * t), copysignf(t, y)};
+    return f2{0.5f * fabsf(y) * __frcp_rn(t), copysignf(t, y)};
 }
 
 __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
@@ -123,14 +123,17 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
 
     const float kr = (float)k.x, ki = (float)k.y;
     const f2 iik = f2{(float)inv_ik.x, (float)inv_ik.y};
-    int ntp = 1;
-    while (ntp < nt && ntp < 128) ntp <<= 1;
-    int nslice = 128 / ntp;
-    int my_t = threadIdx.x % ntp, slice = threadIdx.x / ntp;
+    // thread -> (target, source slice): ntp = min(nt, 128) targets at a time,
+    // nslice = 128 / ntp slices of the sources; the 128 - ntp * nslice
+    // remaining threads only help with the loads
+    const int ntp = min(nt, 128);
+    const int nslice = 128 / ntp;
+    const int my_t = threadIdx.x % ntp, slice = threadIdx.x / ntp;
+    const bool in_grid = slice < nslice;
     int nb0 = a.near_ptr[node], nb1 = a.near_ptr[node + 1];
     for (int tbase = 0; tbase < nt; tbase += ntp) {
         int ti = tbase + my_t;
-        bool active = ti < nt;
+        bool active = in_grid && ti < nt;
         double xt = 0, yt = 0, zt = 0;
         if (active) {
             xt = a.tx[t0 + ti];
