@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
     __shared__ float xs[TILE], ys[TILE], zs[TILE];
     __shared__ f2 qs[TILE];
     __shared__ double2 red[128];
-    __shared__ f2 sE0[MI], sW0[MI], sR0sq[MI], sIR0[MI];
+    // per image: (w0, R0^2) and (1/R0, E0), FP32, two 16-byte loads per pair
+    __shared__ float4 sWR[MI], sIE[MI];
     __shared__ float tsz[TEFMM_MAX_TERMS], tszp[TEFMM_MAX_TERMS];
     __shared__ int tcnt[TEFMM_MAX_TERMS];
     __shared__ double2 cq[2];      // [0]: sum of E0 over all images, [1]: near-field charge total
@@ -93,10 +94,8 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
             cplx r0sq = cmul(w0, w0);
             cplx ir0 = cdiv(mkc(1, 0), w0);
             int s = ti * TEFMM_MAX_IMG + j;
-            sE0[s] = f2{(float)E0.x, (float)E0.y};
-            sW0[s] = f2{(float)w0.x, (float)w0.y};
-            sR0sq[s] = f2{(float)r0sq.x, (float)r0sq.y};
-            sIR0[s] = f2{(float)ir0.x, (float)ir0.y};
+            sWR[s] = make_float4((float)w0.x, (float)w0.y, (float)r0sq.x, (float)r0sq.y);
+            sIE[s] = make_float4((float)ir0.x, (float)ir0.y, (float)E0.x, (float)E0.y);
             atomicAdd(&red[0].x, E0.x);
             atomicAdd(&red[0].y, E0.y);
         }
@@ -178,7 +177,8 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                         const float dw = tsz[tm] * zf + tszp[tm] * zs[j];   // w - w0 (real)
                         for (int m = 0; m < tcnt[tm]; ++m) {
                             const int sidx = tm * TEFMM_MAX_IMG + m;
-                            const f2 w0 = sW0[sidx], r0s = sR0sq[sidx], ir0 = sIR0[sidx];
+                            const float4 wr = sWR[sidx];
+                            const f2 w0 = f2{wr.x, wr.y}, r0s = f2{wr.z, wr.w};
                             // D = rho^2 + dw (2 w0 + dw)
                             float Dr = rho2 + dw * (2.f * w0.x + dw), Di = dw * 2.f * w0.y;
                             // R = sqrt(R0^2 + D) (principal), delta = D / (R + R0)
@@ -195,14 +195,14 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                             float em1 = expm1f(dec);
                             float ur = em1 * (1.f + cm1) + cm1, ui = (1.f + em1) * sn;
                             // delta / R0 and g - 1 = (e^{ik delta} - 1 - delta/R0) / (1 + delta/R0)
-                            float tr = der * ir0.x - dei * ir0.y, ti = der * ir0.y + dei * ir0.x;
+                            const float4 ie = sIE[sidx];
+                            float tr = der * ie.x - dei * ie.y, ti = der * ie.y + dei * ie.x;
                             float nr = ur - tr, ni = ui - ti;
                             float vr = 1.f + tr, vi = ti;
                             float iv = __frcp_rn(vr * vr + vi * vi);
                             float pr = (nr * vr + ni * vi) * iv, pi = (ni * vr - nr * vi) * iv;
-                            const f2 E0 = sE0[sidx];
-                            hr += E0.x * pr - E0.y * pi;
-                            hi += E0.x * pi + E0.y * pr;
+                            hr += ie.z * pr - ie.w * pi;
+                            hi += ie.z * pi + ie.w * pr;
                         }
                     }
                     gr += q.x * hr - q.y * hi;
