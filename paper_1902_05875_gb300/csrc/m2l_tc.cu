@@ -135,27 +135,46 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
         }
     }
     __syncthreads();
+    // one thread per 16-byte chunk of the layout (row nl, K values 4 cg .. 4 cg + 3):
+    // the chunk's two source coefficients k' (real and imaginary column each)
+    // need two table lookups, and its hi and lo parts are one 16-byte store each
     const int n0 = slice * NC;
     for (int ch = 0; ch < nk; ++ch) {
         float *blk = W + (((int64_t)tbl * a.nsplit + slice) * nk + ch) * (2 * NC * KC);
         const int c0 = ch * KC;
-        for (int i = tid; i < NC * KC; i += NTHR) {
-            const int kk = i / NC, nl = i % NC;
-            const int n = n0 + nl, col = c0 + kk;
-            float w = 0.f;
-            if (n < 2 * np && col < 2 * np) {
+        for (int j = tid; j < 2 * NC; j += NTHR) {
+            const int cg = j >= NC ? 1 : 0, nl = j - cg * NC;
+            const int n = n0 + nl;
+            float w[4] = {0.f, 0.f, 0.f, 0.f};
+            if (n < 2 * np) {
                 const int k = n < np ? n : n - np, po = n < np ? 0 : 1;
-                const int kp = np - 1 - (col >> 1), pi = col & 1;     // K order: see kcol()
-                const int64_t o = (int64_t)kp * np + k;
-                const float cfv = __ldg(cf + o);
-                const float2 t = tab[__ldg(a.G + o)];
-                const float hr = cfv * t.x, hi = cfv * t.y;
-                w = (po == pi) ? hr : (po == 0 ? -hi : hi);
+#pragma unroll
+                for (int hp = 0; hp < 2; ++hp) {
+                    const int col = c0 + 4 * cg + 2 * hp;          // real column of k'; col + 1 imaginary
+                    if (col < 2 * np) {
+                        const int kp = np - 1 - (col >> 1);         // K order: see kcol()
+                        const int64_t o = (int64_t)kp * np + k;
+                        const float cfv = __ldg(cf + o);
+                        const float2 t = tab[__ldg(a.G + o)];
+                        const float hr = cfv * t.x, hi = cfv * t.y;
+                        // row part po, column parts 0 and 1 of [[Re H, -Im H], [Im H, Re H]]
+                        w[2 * hp] = po == 0 ? hr : hi;
+                        w[2 * hp + 1] = po == 0 ? -hi : hr;
+                    }
+                }
             }
-            const float wh = tf32_rn(w);
-            const int e = koff(nl, kk) >> 2;
-            blk[e] = wh;
-            blk[NC * KC + e] = tf32_rn(w - wh);
+            float4 wh, wl;
+            wh.x = tf32_rn(w[0]);
+            wh.y = tf32_rn(w[1]);
+            wh.z = tf32_rn(w[2]);
+            wh.w = tf32_rn(w[3]);
+            wl.x = tf32_rn(w[0] - wh.x);
+            wl.y = tf32_rn(w[1] - wh.y);
+            wl.z = tf32_rn(w[2] - wh.z);
+            wl.w = tf32_rn(w[3] - wh.w);
+            const int e = koff(nl, 4 * cg) >> 2;
+            *(float4 *)(blk + e) = wh;
+            *(float4 *)(blk + NC * KC + e) = wl;
         }
     }
 }
