@@ -151,7 +151,6 @@ struct tefmm_plan_s {
     // shift lists of M2M / L2L: row k of M2M lists the k' <= k, row k of L2L
     // the k' >= k; entry = (k', exponents of the offset packed 8 bits each)
     // and the binomial prod_i C(max, min)
-    DBuf d_sh_ptr_m2m, d_sh_ent_m2m, d_sh_cf_m2m, d_sh_ptr_l2l, d_sh_ent_l2l, d_sh_cf_l2l;
 
     // workspace of the last evaluation
     int64_t ns = 0, nt = 0, nitems = 0;

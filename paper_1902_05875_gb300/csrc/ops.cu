@@ -94,102 +94,163 @@ __global__ void k_p2m(int nn, TreeArrays T, Cube cb, int p, int np, const int *_
     }
 }
 
-// ------------------------------------------------------------------ M2M
-// Shift lists (built at plan creation): row k holds the k' of the shift and
-// the exponents of the offset packed in one int, plus prod_i C(.,.) in FP64.
-struct ShiftRows {
-    const int *ptr, *ent;
-    const double *cf;
-};
+// ------------------------------------------------------------------ M2M / L2L
+// A Taylor shift by an offset d factors over the three axes,
+//   C(k, j) d^{k - j} = prod_a C(k_a, j_a) d_a^{k_a - j_a},
+// so the multi-index shift is three one-dimensional shifts, applied one axis
+// after the other (each of at most p + 1 terms per coefficient); the
+// intermediate coefficients keep total degree <= p.
+constexpr int SH_KPT = 2;   // coefficients per thread (256 threads, n_p <= 512)
 
-__device__ __forceinline__ void offset_powers(double *pw, int p, double d0, double d1, double d2) {
-    // pw[a * (p + 1) + e] = d_a^e
-    if (threadIdx.x < 3) {
-        const int a = threadIdx.x;
-        const double d = a == 0 ? d0 : (a == 1 ? d1 : d2);
-        double v = 1.0;
-        for (int e = 0; e <= p; ++e) {
-            pw[a * (p + 1) + e] = v;
-            v *= d;
+// cw[(a * (p + 1) + n) * (p + 1) + j] = C(n, j) d_a^{n - j}, 0 <= j <= n <= p
+__device__ __forceinline__ void shift_coeffs(double *cw, int p, double d0, double d1, double d2) {
+    const int P1 = p + 1;
+    for (int t = threadIdx.x; t < 3 * P1; t += blockDim.x) {
+        const int ax = t / P1, n = t % P1;
+        const double d = ax == 0 ? d0 : (ax == 1 ? d1 : d2);
+        double c = 1.0, pw = 1.0;            // C(n, j), d^{n - j}, from j = n down
+        for (int j = n; j >= 0; --j) {
+            cw[(ax * P1 + n) * P1 + j] = c * pw;
+            c = c * (double)j / (double)(n - j + 1);
+            pw *= d;
         }
     }
 }
 
+// one axis of the upward shift: out_k = sum_{j_a <= k_a} C(k_a, j_a) d_a^{k_a - j_a} in_{k with k_a = j_a}
+__device__ __forceinline__ cplx shift_up_axis(int ax, const int kk[3], const double *cw, int P1, const cplx *in) {
+    cplx acc = mkc(0, 0);
+    int m[3] = {kk[0], kk[1], kk[2]};
+    const double *row = cw + (ax * P1 + kk[ax]) * P1;
+    for (int j = 0; j <= kk[ax]; ++j) {
+        m[ax] = j;
+        const double c = row[j];
+        const cplx x = in[midx(m[0], m[1], m[2])];
+        acc.x += c * x.x;
+        acc.y += c * x.y;
+    }
+    return acc;
+}
+
+// one axis of the downward shift: out_k = sum_{j_a >= k_a, |m| <= p} C(j_a, k_a) d_a^{j_a - k_a} in_{k with k_a = j_a}
+__device__ __forceinline__ cplx shift_down_axis(int ax, const int kk[3], const double *cw, int p, const cplx *in) {
+    const int P1 = p + 1;
+    cplx acc = mkc(0, 0);
+    int m[3] = {kk[0], kk[1], kk[2]};
+    const int jmax = p - (kk[0] + kk[1] + kk[2] - kk[ax]);
+    for (int j = kk[ax]; j <= jmax; ++j) {
+        m[ax] = j;
+        const double c = cw[(ax * P1 + j) * P1 + kk[ax]];
+        const cplx x = in[midx(m[0], m[1], m[2])];
+        acc.x += c * x.x;
+        acc.y += c * x.y;
+    }
+    return acc;
+}
+
 // gamma_k = sum_children sum_{k' <= k} C(k,k') (c_child - c_parent)^{k-k'} alpha^child_k'
-__global__ void k_m2m(int off, int cnt, TreeArrays T, Cube cb, int p, int np, ShiftRows R,
+__global__ void k_m2m(int off, int cnt, TreeArrays T, Cube cb, int p, int np, const int *__restrict__ mi,
                       cplx *__restrict__ alpha) {
     int node = off + blockIdx.x;
     if (blockIdx.x >= cnt || !T.split[node] || T.s1[node] <= T.s0[node]) return;
     extern __shared__ double sm[];
     const int P1 = p + 1;
-    cplx *ac = (cplx *)sm;                         // [8][np] child moments
-    double *pw = (double *)(ac + 8 * np);         // [8][3][p+1]
+    cplx *s0 = (cplx *)sm, *s1 = s0 + np;
+    double *cw = (double *)(s1 + np);                 // [3][p+1][p+1]
     const int l = T.level[node];
     const double h = box_h(cb.side, l), hc = box_h(cb.side, l + 1);
     const double c0 = centre(cb.lo[0], T.ix[node], h), c1 = centre(cb.lo[1], T.iy[node], h),
                  c2 = centre(cb.lo[2], T.iz[node], h);
-    const int cf0 = T.cfirst[node], nch = T.nchild[node];
-    int used = 0;
-    for (int i = 0; i < nch; ++i) {
-        const int ch = cf0 + i;
-        if (T.s1[ch] <= T.s0[ch]) continue;
-        for (int k = threadIdx.x; k < np; k += blockDim.x) ac[used * np + k] = alpha[(int64_t)ch * np + k];
-        if (threadIdx.x < 3)
-            offset_powers(pw + used * 3 * P1, p, centre(cb.lo[0], T.ix[ch], hc) - c0,
-                          centre(cb.lo[1], T.iy[ch], hc) - c1, centre(cb.lo[2], T.iz[ch], hc) - c2);
-        ++used;
+    int kk[SH_KPT][3];
+    cplx acc[SH_KPT];
+#pragma unroll
+    for (int i = 0; i < SH_KPT; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        for (int ax = 0; ax < 3; ++ax) kk[i][ax] = k < np ? mi[3 * k + ax] : 0;
+        acc[i] = mkc(0, 0);
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        cplx acc = mkc(0, 0);
-        const int e0 = R.ptr[k], e1 = R.ptr[k + 1];
-        for (int c = 0; c < used; ++c) {
-            const double *pc = pw + c * 3 * P1;
-            const cplx *a = ac + c * np;
-            for (int e = e0; e < e1; ++e) {
-                const int v = R.ent[e];
-                const double b = R.cf[e] * pc[(v >> 16) & 31] * pc[P1 + ((v >> 21) & 31)] *
-                                 pc[2 * P1 + ((v >> 26) & 31)];
-                const cplx x = a[v & 0xFFFF];
-                acc.x += b * x.x;
-                acc.y += b * x.y;
+    const int cf0 = T.cfirst[node], nch = T.nchild[node];
+    for (int c = 0; c < nch; ++c) {
+        const int ch = cf0 + c;
+        if (T.s1[ch] <= T.s0[ch]) continue;
+        __syncthreads();                              // the previous child is done with s0, cw
+        for (int k = threadIdx.x; k < np; k += blockDim.x) s0[k] = alpha[(int64_t)ch * np + k];
+        shift_coeffs(cw, p, centre(cb.lo[0], T.ix[ch], hc) - c0, centre(cb.lo[1], T.iy[ch], hc) - c1,
+                     centre(cb.lo[2], T.iz[ch], hc) - c2);
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < SH_KPT; ++i) {
+            const int k = threadIdx.x + i * blockDim.x;
+            if (k < np) s1[k] = shift_up_axis(0, kk[i], cw, P1, s0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < SH_KPT; ++i) {
+            const int k = threadIdx.x + i * blockDim.x;
+            if (k < np) s0[k] = shift_up_axis(1, kk[i], cw, P1, s1);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < SH_KPT; ++i) {
+            const int k = threadIdx.x + i * blockDim.x;
+            if (k < np) {
+                const cplx v = shift_up_axis(2, kk[i], cw, P1, s0);
+                acc[i].x += v.x;
+                acc[i].y += v.y;
             }
         }
-        alpha[(int64_t)node * np + k] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < SH_KPT; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        if (k < np) alpha[(int64_t)node * np + k] = acc[i];
     }
 }
 
 // ------------------------------------------------------------------ L2L
 // lambda_k += sum_{k' >= k} C(k',k) (c_child - c_parent)^{k'-k} beta^parent_k'
-__global__ void k_l2l(int off, int cnt, TreeArrays T, Cube cb, int p, int np, ShiftRows R,
+__global__ void k_l2l(int off, int cnt, TreeArrays T, Cube cb, int p, int np, const int *__restrict__ mi,
                       cplx *__restrict__ beta) {
     int node = off + blockIdx.x;
     if (blockIdx.x >= cnt || T.t1[node] <= T.t0[node]) return;
     int par = T.parent[node];
     if (par < 0) return;
     extern __shared__ double sm[];
-    const int P1 = p + 1;
-    cplx *bp = (cplx *)sm;
-    double *pw = (double *)(bp + np);
+    cplx *s0 = (cplx *)sm, *s1 = s0 + np;
+    double *cw = (double *)(s1 + np);
     const int l = T.level[node];
     const double h = box_h(cb.side, l), hp = box_h(cb.side, l - 1);
-    for (int k = threadIdx.x; k < np; k += blockDim.x) bp[k] = beta[(int64_t)par * np + k];
-    offset_powers(pw, p, centre(cb.lo[0], T.ix[node], h) - centre(cb.lo[0], T.ix[par], hp),
-                  centre(cb.lo[1], T.iy[node], h) - centre(cb.lo[1], T.iy[par], hp),
-                  centre(cb.lo[2], T.iz[node], h) - centre(cb.lo[2], T.iz[par], hp));
+    for (int k = threadIdx.x; k < np; k += blockDim.x) s0[k] = beta[(int64_t)par * np + k];
+    shift_coeffs(cw, p, centre(cb.lo[0], T.ix[node], h) - centre(cb.lo[0], T.ix[par], hp),
+                 centre(cb.lo[1], T.iy[node], h) - centre(cb.lo[1], T.iy[par], hp),
+                 centre(cb.lo[2], T.iz[node], h) - centre(cb.lo[2], T.iz[par], hp));
+    int kk[SH_KPT][3];
+#pragma unroll
+    for (int i = 0; i < SH_KPT; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        for (int ax = 0; ax < 3; ++ax) kk[i][ax] = k < np ? mi[3 * k + ax] : 0;
+    }
     __syncthreads();
-    for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        cplx acc = mkc(0, 0);
-        for (int e = R.ptr[k]; e < R.ptr[k + 1]; ++e) {
-            const int v = R.ent[e];
-            const double b = R.cf[e] * pw[(v >> 16) & 31] * pw[P1 + ((v >> 21) & 31)] *
-                             pw[2 * P1 + ((v >> 26) & 31)];
-            const cplx x = bp[v & 0xFFFF];
-            acc.x += b * x.x;
-            acc.y += b * x.y;
+#pragma unroll
+    for (int i = 0; i < SH_KPT; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        if (k < np) s1[k] = shift_down_axis(0, kk[i], cw, p, s0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SH_KPT; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        if (k < np) s0[k] = shift_down_axis(1, kk[i], cw, p, s1);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SH_KPT; ++i) {
+        const int k = threadIdx.x + i * blockDim.x;
+        if (k < np) {
+            const cplx v = shift_down_axis(2, kk[i], cw, p, s0);
+            cplx b = beta[(int64_t)node * np + k];
+            beta[(int64_t)node * np + k] = mkc(b.x + v.x, b.y + v.y);
         }
-        cplx v = beta[(int64_t)node * np + k];
-        beta[(int64_t)node * np + k] = mkc(v.x + acc.x, v.y + acc.y);
     }
 }
 
@@ -603,13 +664,13 @@ int upward_pass(tefmm_plan_s *P, cudaStream_t st) {
                                    dp<double>(P->sy), dp<double>(P->sz), dp<double>(P->sq),
                                    dp<cplx>(P->alpha));
     P->launches++;
-    size_t sm_m2m = 8 * (size_t)np * sizeof(cplx) + 8 * 3 * (p + 1) * sizeof(double);
+    if (np > SH_KPT * 256) return TEFMM_ERR_INVALID_ARG;
+    const size_t sm_m2m = 2 * (size_t)np * sizeof(cplx) + 3 * (size_t)(p + 1) * (p + 1) * sizeof(double);
     TRY(smem_optin(k_m2m));
-    ShiftRows R{dp<int>(P->d_sh_ptr_m2m), dp<int>(P->d_sh_ent_m2m), dp<double>(P->d_sh_cf_m2m)};
     for (int l = P->n_levels - 2; l >= 0; --l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
         if (cnt > 0) {
-            k_m2m<<<cnt, 256, sm_m2m, st>>>(off, cnt, T, cb, p, np, R, dp<cplx>(P->alpha));
+            k_m2m<<<cnt, 256, sm_m2m, st>>>(off, cnt, T, cb, p, np, dp<int>(P->d_mi), dp<cplx>(P->alpha));
             P->launches++;
         }
     }
@@ -751,12 +812,12 @@ int m2l_apply(tefmm_plan_s *P, cudaStream_t st) {
 int downward_pass(tefmm_plan_s *P, cudaStream_t st) {
     TreeArrays T = tree_arrays(P);
     Cube cb = cube_of(P);
-    size_t sm = P->np * sizeof(cplx) + 3 * (P->p + 1) * sizeof(double);
-    ShiftRows R{dp<int>(P->d_sh_ptr_l2l), dp<int>(P->d_sh_ent_l2l), dp<double>(P->d_sh_cf_l2l)};
+    if (P->np > SH_KPT * 256) return TEFMM_ERR_INVALID_ARG;
+    const size_t sm = 2 * (size_t)P->np * sizeof(cplx) + 3 * (size_t)(P->p + 1) * (P->p + 1) * sizeof(double);
     for (int l = 1; l < P->n_levels; ++l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
         if (cnt > 0) {
-            k_l2l<<<cnt, 256, sm, st>>>(off, cnt, T, cb, P->p, P->np, R, dp<cplx>(P->beta));
+            k_l2l<<<cnt, 256, sm, st>>>(off, cnt, T, cb, P->p, P->np, dp<int>(P->d_mi), dp<cplx>(P->beta));
             P->launches++;
         }
     }

@@ -72,41 +72,6 @@ int plan_build_operator_tables(tefmm_plan_s *P) {
     CUDA_TRY(cudaMemcpy(P->d_m2l_g.p, G.data(), G.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(P->d_m2l_cB.p, cB.data(), cB.size() * sizeof(double), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(P->d_m2l_cA.p, cA.data(), cA.size() * sizeof(double), cudaMemcpyHostToDevice));
-    // M2M rows: k' <= k componentwise, coefficient C(k, k'), offset exponent k - k';
-    // L2L rows: k' >= k, |k'| <= p, coefficient C(k', k), offset exponent k' - k
-    for (int pass = 0; pass < 2; ++pass) {
-        std::vector<int> ptr(np + 1, 0), ent;
-        std::vector<double> cf;
-        for (int k = 0; k < np; ++k) {
-            const int a1 = mi[3 * k], a2 = mi[3 * k + 1], a3 = mi[3 * k + 2];
-            for (int kp = 0; kp < np; ++kp) {
-                const int b1 = mi[3 * kp], b2 = mi[3 * kp + 1], b3 = mi[3 * kp + 2];
-                int e1, e2, e3;
-                double c;
-                if (pass == 0) {
-                    if (b1 > a1 || b2 > a2 || b3 > a3) continue;
-                    e1 = a1 - b1, e2 = a2 - b2, e3 = a3 - b3;
-                    c = comb(a1, b1) * comb(a2, b2) * comb(a3, b3);
-                } else {
-                    if (b1 < a1 || b2 < a2 || b3 < a3) continue;
-                    e1 = b1 - a1, e2 = b2 - a2, e3 = b3 - a3;
-                    c = comb(b1, a1) * comb(b2, a2) * comb(b3, a3);
-                }
-                ent.push_back(kp | (e1 << 16) | (e2 << 21) | (e3 << 26));
-                cf.push_back(c);
-            }
-            ptr[k + 1] = (int)ent.size();
-        }
-        DBuf &dp_ = pass == 0 ? P->d_sh_ptr_m2m : P->d_sh_ptr_l2l;
-        DBuf &de = pass == 0 ? P->d_sh_ent_m2m : P->d_sh_ent_l2l;
-        DBuf &dc = pass == 0 ? P->d_sh_cf_m2m : P->d_sh_cf_l2l;
-        TRY(dbuf_ensure(dp_, ptr.size() * 4));
-        TRY(dbuf_ensure(de, ent.size() * 4));
-        TRY(dbuf_ensure(dc, cf.size() * 8));
-        CUDA_TRY(cudaMemcpy(dp_.p, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(de.p, ent.data(), ent.size() * 4, cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(dc.p, cf.data(), cf.size() * 8, cudaMemcpyHostToDevice));
-    }
     return TEFMM_OK;
 }
 
@@ -247,8 +212,7 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
 extern "C" int tefmm_plan_destroy(tefmm_plan P) {
     if (!P) return TEFMM_OK;
     DBuf *all[] = {&P->d_terms, &P->d_A, &P->d_Z, &P->d_k, &P->d_mi, &P->d_m2l_g, &P->d_m2l_cB,
-                   &P->d_m2l_cA, &P->d_binom, &P->d_sh_ptr_m2m, &P->d_sh_ent_m2m, &P->d_sh_cf_m2m,
-                   &P->d_sh_ptr_l2l, &P->d_sh_ent_l2l, &P->d_sh_cf_l2l, &P->keys_in, &P->keys_out, &P->vals_in,
+                   &P->d_m2l_cA, &P->d_binom, &P->keys_in, &P->keys_out, &P->vals_in,
                    &P->vals_out, &P->cub_tmp, &P->scan_tmp, &P->item_node, &P->item_flag,
                    &P->item_scan, &P->cnt_s, &P->cnt_t, &P->sx, &P->sy, &P->sz, &P->sq, &P->tx,
                    &P->ty, &P->tz, &P->perm_s, &P->perm_t, &P->n_layer, &P->n_level, &P->n_ix,
