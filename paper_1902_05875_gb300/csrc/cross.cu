@@ -143,20 +143,18 @@ __global__ void k_first_cross(int ntab, const uint64_t *__restrict__ tkey, int64
 }
 
 // T^{(k3')} slice of one cross table: grid (tables, p + 1)
-__global__ void k_xtables(int nx, const uint64_t *__restrict__ keys, Cube cb, int p,
-                          const int *__restrict__ mi_g, XGeom geo, const int2 *__restrict__ xrange,
+__global__ void __launch_bounds__(256, 4) k_xtables(int nx, const uint64_t *__restrict__ keys, Cube cb, int p, XGeom geo,
+                          const int2 *__restrict__ xrange,
                           const cplx *__restrict__ xA, const cplx *__restrict__ xZ, int NX,
                           const int *__restrict__ rep_code, int first, cplx *__restrict__ xt) {
     int tb = blockIdx.x, k3p = blockIdx.y;
     if (tb >= nx || k3p > p) return;
     if ((rep_code[first + tb] >> 3) != first + tb) return;   // copied by symmetry
-    const int P2 = 2 * p - k3p, n2 = ncoef(P2), nfull = ncoef(2 * p);
+    const int P2 = 2 * p - k3p, n2 = ncoef(P2), cmax = tri(P2 + 1);
     extern __shared__ double sm[];
-    cplx *a = (cplx *)sm;
-    cplx *b = a + nfull;
-    cplx *acc = b + nfull;
-    int *mi = (int *)(acc + nfull);
-    for (int g = threadIdx.x; g < 3 * n2; g += blockDim.x) mi[g] = mi_g[g];
+    cplx *a = (cplx *)sm;                                     // [3][cmax] ring of orders
+    cplx *b = a + 3 * cmax;
+    cplx *acc = xt + (int64_t)tb * NX + slice_off(p, k3p);   // the slice accumulates in place
     for (int g = threadIdx.x; g < n2; g += blockDim.x) acc[g] = mkc(0, 0);
     __syncthreads();
     const XKey x = xkey_decode(keys[tb]);
@@ -171,11 +169,9 @@ __global__ void k_xtables(int nx, const uint64_t *__restrict__ keys, Cube cb, in
         double Wr = W0 - geo.wmin[2 * x.lt + dir];
         for (int j = r.x; j < r.x + r.y; ++j) {
             cplx Wj = mkc(Wr - xZ[j].x, -xZ[j].y);
-            recur_accumulate(P2, n2, mi, k, X, Y, Wj, xA[j], dir == 1, a, b, acc);
+            recur_accumulate(P2, cmax, k, X, Y, Wj, xA[j], dir == 1, a, b, acc);
         }
     }
-    cplx *dst = xt + (int64_t)tb * NX + slice_off(p, k3p);
-    for (int g = threadIdx.x; g < n2; g += blockDim.x) dst[g] = acc[g];
 }
 
 // Cross-layer M2L, FP64: one CTA per chunk of pairs of one cross key, one
@@ -420,12 +416,11 @@ int cross_tables(tefmm_plan_s *P, cudaStream_t st) {
     const int nx = P->n_xtables;
     if (nx == 0) return TEFMM_OK;
     TRY(dbuf_ensure(P->xtables, (size_t)nx * P->NX * sizeof(cplx)));
-    const int nfull = P->np2;
-    size_t sm = 3 * (size_t)nfull * sizeof(cplx) + 3 * (size_t)nfull * sizeof(int);
+    const size_t sm = 6 * (size_t)tri(2 * P->p + 1) * sizeof(cplx);
     TRY(smem_optin(k_xtables));
     dim3 grid((unsigned)nx, (unsigned)(P->p + 1));
     k_xtables<<<grid, 256, sm, st>>>(nx, dp<uint64_t>(P->table_slot) + P->x_first_table, cube_of(P),
-                                     P->p, dp<int>(P->d_mi), geometry(P), dp<int2>(P->d_xrange),
+                                     P->p, geometry(P), dp<int2>(P->d_xrange),
                                      dp<cplx>(P->d_xA), dp<cplx>(P->d_xZ), P->NX,
                                      dp<int>(P->table_rep), P->x_first_table, dp<cplx>(P->xtables));
     P->launches++;

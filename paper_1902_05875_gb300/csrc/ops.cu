@@ -400,17 +400,15 @@ __global__ void k_chunk_cnt(int nchunks, int64_t nvalid, const int *__restrict__
     chunk_cnt[c] = cnt < chsize ? cnt : chsize;
 }
 
-__global__ void k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube cb, int P2, int np2,
-                         const int *__restrict__ mi_g, ImgView im, const int *__restrict__ rep_code,
-                         cplx *__restrict__ tables) {
+__global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube cb, int P2, int np2,
+                         ImgView im, const int *__restrict__ rep_code, cplx *__restrict__ tables) {
     int tb = blockIdx.x;
     if (tb >= ntab || (rep_code[tb] >> 3) != tb) return;   // copied by symmetry
     extern __shared__ double sm[];
-    cplx *a = (cplx *)sm;
-    cplx *b = a + np2;
-    cplx *acc = b + np2;
-    int *mi = (int *)(acc + np2);
-    for (int g = threadIdx.x; g < 3 * np2; g += blockDim.x) mi[g] = mi_g[g];
+    const int cmax = tri(P2 + 1);            // entries of the largest order
+    cplx *a = (cplx *)sm;                    // [3][cmax] ring of orders
+    cplx *b = a + 3 * cmax;
+    cplx *acc = tables + (int64_t)tb * np2;  // the table accumulates in place
     for (int g = threadIdx.x; g < np2; g += blockDim.x) acc[g] = mkc(0, 0);
     __syncthreads();
     uint64_t key = table_key[tb];
@@ -426,14 +424,14 @@ __global__ void k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube 
     int tf = im.lt_first[lay], tc = im.lt_count[lay];
     if (kind == 0) {
         double dz = (double)(w - 3) * h;
-        recur_accumulate(P2, np2, mi, k, X, Y, mkc(dz, 0), mkc(1, 0), false, a, b, acc);
+        recur_accumulate(P2, cmax, k, X, Y, mkc(dz, 0), mkc(1, 0), false, a, b, acc);
         for (int ti = tf; ti < tf + tc; ++ti) {
             DevTerm t = im.terms[ti];
             if (t.tag != 2 && t.tag != 3) continue;
             double W0 = __dadd_rn(__dmul_rn(t.sz, dz), t.c);
             for (int j = t.first; j < t.first + t.count; ++j) {
                 cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
-                recur_accumulate(P2, np2, mi, k, X, Y, Wj, im.A[j], t.tag == 3, a, b, acc);
+                recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 3, a, b, acc);
             }
         }
     } else {
@@ -444,11 +442,10 @@ __global__ void k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube 
             double W0 = __dadd_rn(__dmul_rn(t.sz, zsum), t.c);
             for (int j = t.first; j < t.first + t.count; ++j) {
                 cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
-                recur_accumulate(P2, np2, mi, k, X, Y, Wj, im.A[j], t.tag == 1, a, b, acc);
+                recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 1, a, b, acc);
             }
         }
     }
-    for (int g = threadIdx.x; g < np2; g += blockDim.x) tables[(int64_t)tb * np2 + g] = acc[g];
 }
 
 // ------------------------------------------------------------------ M2L apply (FP64)
@@ -771,11 +768,10 @@ int m2l_tables(tefmm_plan_s *P, cudaStream_t st) {
     if (ntab == 0) return TEFMM_OK;
     const int np2 = P->np2;
     TRY(dbuf_ensure(P->tables, (size_t)ntab * np2 * sizeof(cplx)));
-    size_t sm = 3 * (size_t)np2 * sizeof(cplx) + 3 * (size_t)np2 * sizeof(int);
+    const size_t sm = 6 * (size_t)tri(2 * P->p + 1) * sizeof(cplx);
     TRY(smem_optin(k_tables));
-    k_tables<<<ntab, 256, sm, st>>>(ntab, dp<uint64_t>(P->table_slot), cube_of(P),
-                                           2 * P->p, np2, dp<int>(P->d_mi), img_view(P),
-                                           dp<int>(P->table_rep), dp<cplx>(P->tables));
+    k_tables<<<ntab, 256, sm, st>>>(ntab, dp<uint64_t>(P->table_slot), cube_of(P), 2 * P->p, np2,
+                                    img_view(P), dp<int>(P->table_rep), dp<cplx>(P->tables));
     P->launches++;
     CUDA_TRY(cudaGetLastError());
     return tables_expand(P, 0, ntab, 1, dp<cplx>(P->tables), np2, st);

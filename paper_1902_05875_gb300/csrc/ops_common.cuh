@@ -112,64 +112,76 @@ __host__ __device__ inline XKey xkey_decode(uint64_t k) {
 
 // ------------------------------------------------------------------ derivative tables
 // One derivative table per key: sum over the key's images of
-// A_j D^g h0(k R_j) / g!, |g| <= 2p, by the recurrence (Sec. 3.2)
+// A_j D^g h0(k R_j) / g!, |g| <= P2, by the recurrence (Sec. 3.2)
 //   |g| R^2 a_g + (2|g|-1) sum_i x_i a_{g-e_i} + (|g|-1) sum_i a_{g-2e_i}
 //       = i k sum_i (x_i b_{g-e_i} + b_{g-2e_i}),
 //   |g| b_g = i k sum_i (x_i a_{g-e_i} + a_{g-2e_i}),
 // a_0 = e^{ikR}/R, b_0 = e^{ikR}, D^g h0 / g! = a_g / (ik).
-__device__ inline void recur_accumulate(int P2, int np2, const int *mi, cplx k, double X, double Y, cplx W,
-                                 cplx coef, bool flip3, cplx *a, cplx *b, cplx *acc) {
+// Order n needs orders n-1 and n-2 only, so a and b live in shared memory as
+// a ring of three orders (slot n mod 3, each ncoef-level wide: cmax entries).
+// Within order n the graded index of g = (k1, k2, k3) is
+// loc(g) = T(k2 + k3) + k3, T(x) = x (x + 1) / 2 (so g = n(n+1)(n+2)/6 + loc(g)).
+// The thread that computes a_g adds coef a_g / (ik) (times (-1)^{g3} if flip3)
+// to the table entry dst[g] itself: the table is the accumulator.
+__host__ __device__ inline int tri(int x) { return x * (x + 1) / 2; }
+
+__device__ inline void recur_accumulate(int P2, int cmax, cplx k, double X, double Y, cplx W, cplx coef,
+                                        bool flip3, cplx *a, cplx *b, cplx *dst) {
+    const cplx ik = mkc(-k.y, k.x);
+    const cplx c2 = cdiv(coef, ik);
     if (threadIdx.x == 0) {
         cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
         cplx R = csqrt_p(R2);
-        cplx ikR = cmul(mkc(-k.y, k.x), R);
+        cplx ikR = cmul(ik, R);
         cplx e = cexp_(ikR);
-        a[0] = cdiv(e, R);
+        const cplx a0 = cdiv(e, R);
+        a[0] = a0;
         b[0] = e;
+        dst[0] = cadd(dst[0], cmul(c2, a0));
     }
     __syncthreads();
-    cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
-    cplx ik = mkc(-k.y, k.x);
+    const cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
     const cplx iR2 = cdiv(mkc(1, 0), R2);
+    const cplx xs[3] = {mkc(X, 0), mkc(Y, 0), W};
     for (int n = 1; n <= P2; ++n) {
         const double inv_n = 1.0 / n;
-        int first = n * (n + 1) * (n + 2) / 6, last = (n + 1) * (n + 2) * (n + 3) / 6;
-        for (int g = first + threadIdx.x; g < last; g += blockDim.x) {
-            int kk[3] = {mi[3 * g], mi[3 * g + 1], mi[3 * g + 2]};
-            cplx xs[3] = {mkc(X, 0), mkc(Y, 0), W};
+        const int first = n * (n + 1) * (n + 2) / 6, cnt = tri(n + 1);
+        cplx *an = a + (n % 3) * cmax, *bn = b + (n % 3) * cmax;
+        const cplx *a1 = a + ((n + 2) % 3) * cmax, *b1 = b + ((n + 2) % 3) * cmax;   // order n - 1
+        const cplx *a2 = a + ((n + 1) % 3) * cmax, *b2 = b + ((n + 1) % 3) * cmax;   // order n - 2
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            // (k1, k2, k3) of local index i: i = T(s) + k3 with s = k2 + k3
+            int s = (int)((sqrtf(8.f * (float)i + 1.f) - 1.f) * 0.5f);
+            while (tri(s + 1) <= i) ++s;
+            while (tri(s) > i) --s;
+            const int k3 = i - tri(s), k2 = s - k3, k1 = n - s;
+            const int kk[3] = {k1, k2, k3};
             cplx sa1 = mkc(0, 0), sa2 = mkc(0, 0), sb = mkc(0, 0);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                if (kk[i] >= 1) {
-                    int m[3] = {kk[0], kk[1], kk[2]};
-                    m[i] -= 1;
-                    int j = midx(m[0], m[1], m[2]);
-                    sa1 = cadd(sa1, cmul(xs[i], a[j]));
-                    sb = cadd(sb, cmul(xs[i], b[j]));
+            for (int d = 0; d < 3; ++d) {
+                if (kk[d] >= 1) {
+                    int m2 = kk[1] - (d == 1), m3 = kk[2] - (d == 2);
+                    const int j = tri(m2 + m3) + m3;
+                    sa1 = cadd(sa1, cmul(xs[d], a1[j]));
+                    sb = cadd(sb, cmul(xs[d], b1[j]));
                 }
-                if (kk[i] >= 2) {
-                    int m[3] = {kk[0], kk[1], kk[2]};
-                    m[i] -= 2;
-                    int j = midx(m[0], m[1], m[2]);
-                    sa2 = cadd(sa2, a[j]);
-                    sb = cadd(sb, b[j]);
+                if (kk[d] >= 2) {
+                    int m2 = kk[1] - 2 * (d == 1), m3 = kk[2] - 2 * (d == 2);
+                    const int j = tri(m2 + m3) + m3;
+                    sa2 = cadd(sa2, a2[j]);
+                    sb = cadd(sb, b2[j]);
                 }
             }
-            cplx bg = cscale(cmul(ik, cadd(sa1, sa2)), inv_n);
-            cplx num = csub(csub(cmul(ik, sb), cscale(sa1, 2.0 * n - 1.0)), cscale(sa2, n - 1.0));
-            cplx ag = cscale(cmul(num, iR2), inv_n);
-            a[g] = ag;
-            b[g] = bg;
+            const cplx bg = cscale(cmul(ik, cadd(sa1, sa2)), inv_n);
+            const cplx num = csub(csub(cmul(ik, sb), cscale(sa1, 2.0 * n - 1.0)), cscale(sa2, n - 1.0));
+            const cplx ag = cscale(cmul(num, iR2), inv_n);
+            an[i] = ag;
+            bn[i] = bg;
+            cplx v = cmul(c2, ag);
+            if (flip3 && (k3 & 1)) v = mkc(-v.x, -v.y);
+            dst[first + i] = cadd(dst[first + i], v);
         }
         __syncthreads();
     }
-    // acc += coef * a / (ik) * (-1)^{g3 if flip3}
-    cplx c2 = cdiv(coef, ik);
-    for (int g = threadIdx.x; g < np2; g += blockDim.x) {
-        cplx v = cmul(c2, a[g]);
-        if (flip3 && (mi[3 * g + 2] & 1)) v = mkc(-v.x, -v.y);
-        acc[g] = cadd(acc[g], v);
-    }
-    __syncthreads();
 }
 
