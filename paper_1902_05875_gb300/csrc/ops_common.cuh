@@ -142,7 +142,6 @@ __device__ inline void recur_accumulate(int P2, int cmax, cplx k, double X, doub
     __syncthreads();
     const cplx R2 = mkc(X * X + Y * Y + W.x * W.x - W.y * W.y, 2.0 * W.x * W.y);
     const cplx iR2 = cdiv(mkc(1, 0), R2);
-    const cplx xs[3] = {mkc(X, 0), mkc(Y, 0), W};
     for (int n = 1; n <= P2; ++n) {
         const double inv_n = 1.0 / n;
         const int first = n * (n + 1) * (n + 2) / 6, cnt = tri(n + 1);
@@ -162,8 +161,14 @@ __device__ inline void recur_accumulate(int P2, int cmax, cplx k, double X, doub
                 if (kk[d] >= 1) {
                     int m2 = kk[1] - (d == 1), m3 = kk[2] - (d == 2);
                     const int j = tri(m2 + m3) + m3;
-                    sa1 = cadd(sa1, cmul(xs[d], a1[j]));
-                    sb = cadd(sb, cmul(xs[d], b1[j]));
+                    if (d < 2) {   // x and y offsets are real: scale instead of a complex product
+                        const double xd = d == 0 ? X : Y;
+                        sa1 = cadd(sa1, cscale(a1[j], xd));
+                        sb = cadd(sb, cscale(b1[j], xd));
+                    } else {
+                        sa1 = cadd(sa1, cmul(W, a1[j]));
+                        sb = cadd(sb, cmul(W, b1[j]));
+                    }
                 }
                 if (kk[d] >= 2) {
                     int m2 = kk[1] - 2 * (d == 1), m3 = kk[2] - 2 * (d == 2);
