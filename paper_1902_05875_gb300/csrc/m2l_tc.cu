@@ -30,6 +30,7 @@ namespace {
 constexpr int TM = 128;      // pairs per CTA (MMA M)
 constexpr int KC = 8;        // K elements per pipeline stage (one MMA K step)
 constexpr int NST = 5;       // pipeline stages (shared-memory buffers)
+constexpr int NMAX = 256;    // widest output slice (the MMA's N for M = 128)
 constexpr int NTHR = 256;
 constexpr long SPIN_LIMIT = 4000000;
 constexpr size_t W_BATCH_BYTES = (size_t)2 << 30;   // W^T blocks held at once, at most
@@ -213,6 +214,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 constexpr int NPROD = 256;              // producer / epilogue threads
 constexpr int NTHR_TC = NPROD + 32;     // + the MMA warp
 constexpr int LAG = 2;                  // stages a producer keeps in flight before arriving
+static_assert(LAG < NST, "a producer must arrive for a stage before it waits for that stage's buffer");
 
 __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
     // 1-D grid: the nsplit column slices of one chunk are adjacent blocks, so
@@ -478,14 +480,14 @@ __global__ void k_fold_beta(int nn, const int *__restrict__ level, double side, 
 }  // namespace
 
 // column geometry of the tensor-core M2L: K padded to 16; the 2 n_p output
-// columns are cut into nsplit = ceil(2 n_p / 256) slices of Ncta columns
-// (a multiple of 32, at most 256: the MMA's N, and 16-column TMEM loads per
-// half of the epilogue warps)
+// columns are cut into nsplit = ceil(2 n_p / NMAX) slices of Ncta columns
+// (a multiple of 32, at most NMAX <= 256: the MMA's N, and 16-column TMEM
+// loads per half of the epilogue warps)
 void m2l_tc_geometry(int np, int MT, int *Kpad, int *Ncta, int *nsplit) {
     const int R = 2 * np;
     (void)MT;
     *Kpad = (R + 15) / 16 * 16;
-    *nsplit = (R + 255) / 256;
+    *nsplit = (R + NMAX - 1) / NMAX;
     *Ncta = ((R + *nsplit - 1) / *nsplit + 31) / 32 * 32;
 }
 
