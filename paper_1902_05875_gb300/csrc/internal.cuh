@@ -147,10 +147,6 @@ struct tefmm_plan_s {
     DBuf d_m2l_g;     // uint16 [np*np]  index of k+k' (layout [k'][k])
     DBuf d_m2l_cB;    // double [np*np]  C(k+k',k) (-1)^{k1'+k2'} (-1)^{k3'}  ([k'][k])
     DBuf d_m2l_cA;    // double [np*np]  C(k+k',k) (-1)^{k1'+k2'}            ([k'][k])
-    DBuf d_binom;     // double [(2p+1)^2]
-    // shift lists of M2M / L2L: row k of M2M lists the k' <= k, row k of L2L
-    // the k' >= k; entry = (k', exponents of the offset packed 8 bits each)
-    // and the binomial prod_i C(max, min)
 
     // workspace of the last evaluation
     int64_t ns = 0, nt = 0, nitems = 0;

@@ -11,14 +11,15 @@
 // Precision: FP32 values split into TF32 hi/lo parts; three tcgen05.mma
 // kind::tf32 products (hi.hi + hi.lo + lo.hi) accumulate in FP32 in TMEM.
 //
-// Kernel layout: one CTA per chunk of <= 128 pairs of one key (M = 128 rows of
-// TMEM = pairs) and one slice of the output columns (N <= 512 TMEM columns).
-// The K dimension (2np, padded to 16) is walked in chunks of 16: all 256
-// threads generate the W^T slice from the table and gather the X^T slice into
-// one of two shared-memory buffers while the tensor core works on the other;
-// thread 0 issues the MMAs and commits them to the buffer's mbarrier.
+// Kernel layout (k_wgen, k_m2l_tc below): k_wgen writes W^T per key and
+// output slice in the MMA's shared-memory operand layout (TF32 hi and lo);
+// k_m2l_tc takes one chunk of <= 128 pairs of one key (M = 128 rows of TMEM =
+// pairs) and one slice of N <= 256 output columns, and walks K (2np, padded
+// to 16) in stages of 8 through a 5-stage shared-memory ring filled by
+// producer warps (bulk copy of the W^T block, 16-byte copies of the pairs'
+// moment rows) and drained by one MMA-issuing thread.
 // Operands are K-major without swizzle (8-row x 16-byte core matrices,
-// LBO = 128 B between K-neighbours, SBO = 512 B between 8-row groups).
+// LBO = 128 B between K-neighbours, SBO = 256 B between 8-row groups).
 // Every wait is bounded; on a timeout the CTA raises a flag, skips its output
 // and still releases its TMEM.
 #include <algorithm>
