@@ -29,7 +29,8 @@
 namespace {
 
 constexpr int TM = 128;      // pairs per CTA (MMA M)
-constexpr int KC = 8;        // K elements per pipeline stage (one MMA K step)
+constexpr int KC = 8;        // K elements per pipeline stage (KC / 8 MMA K steps)
+static_assert(KC % 8 == 0 && KC <= 32, "a stage holds whole MMA K steps of 8");
 constexpr int NST = 5;       // pipeline stages (shared-memory buffers)
 constexpr int NMAX = 256;    // widest output slice (the MMA's N for M = 128)
 constexpr int NTHR = 256;
@@ -67,7 +68,7 @@ __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvt
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
     d |= (uint64_t)(128 >> 4) << 16;   // LBO
-    d |= (uint64_t)(256 >> 4) << 32;   // SBO: 8 rows x KC 4-byte elements
+    d |= (uint64_t)((8 * KC * 4) >> 4) << 32;   // SBO: 8 rows x KC 4-byte elements
     d |= (uint64_t)1 << 46;            // descriptor version
     return d;
 }
@@ -78,11 +79,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 // collects the small terms before the large ones; this ordering measured
 // 2.5x less accumulation error than the graded order.
 //
-// byte offset of (row r, k) in a K-major no-swizzle tile with KC = 8 columns:
-// 8-row x 16-byte core matrices, LBO = 128 B between the two K halves,
-// SBO = 256 B between 8-row groups
+// byte offset of (row r, k) in a K-major no-swizzle tile with KC columns:
+// 8-row x 16-byte core matrices, LBO = 128 B between K-neighbouring core
+// matrices, SBO = 32 KC B between 8-row groups; one MMA K step (8 values)
+// spans two core matrices, so step s of a stage starts 256 s bytes in
 __device__ __forceinline__ int koff(int r, int k) {
-    return (r >> 3) * 256 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+    return (r >> 3) * (32 * KC) + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
 }
 
 __device__ __forceinline__ float tf32_rn(float x) {
@@ -101,7 +103,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     return false;
 }
 
-// W^T blocks of one key, one column slice and one K chunk: NC x 16 TF32 hi
+// W^T blocks of one key, one column slice and one K chunk: NC x KC TF32 hi
 // values in the K-major core-matrix layout of koff(), then the lo values;
 // block (key - tab_base, slice, ch) at W + ((tbl * nsplit + slice) * nk + ch) * 2 * NC * KC.
 // One CTA per (key, slice): the scaled table T~_g = T_g h^{|g|} (cross-layer:
@@ -144,8 +146,8 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
     for (int ch = 0; ch < nk; ++ch) {
         float *blk = W + (((int64_t)tbl * a.nsplit + slice) * nk + ch) * (2 * NC * KC);
         const int c0 = ch * KC;
-        for (int j = tid; j < 2 * NC; j += NTHR) {
-            const int cg = j >= NC ? 1 : 0, nl = j - cg * NC;
+        for (int j = tid; j < (KC / 4) * NC; j += NTHR) {
+            const int cg = j / NC, nl = j - cg * NC;
             const int n = n0 + nl;
             float w[4] = {0.f, 0.f, 0.f, 0.f};
             if (n < 2 * np) {
@@ -196,7 +198,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // One CTA: one chunk of up to chunk_pairs pairs of one key, and one slice of
 // NC output columns, taken in passes of MT tiles of TM = 128 pairs; TMEM holds
 // one 128 x NC FP32 accumulator per tile (MT * NC <= 512 columns).  The K
-// dimension runs through a ring of NST shared-memory stages of KC = 8,
+// dimension runs through a ring of NST shared-memory stages of KC values,
 // warp-specialised:
 //  * warps 0-7 (producers): for stage g they wait until the MMAs that last
 //    read the stage's buffer are done (empty[g % NST], committed by the MMA
@@ -287,8 +289,9 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
         __syncthreads();
         if (warp < NPROD / 32) {
             // ---------------------------------------------------------- producers
-            // thread t copies 16 bytes (4 K values) q = t & 1 of row t >> 1 of every
-            // tile, hi and lo: source addresses advance by KC floats per stage
+            // thread t copies the 16-byte chunks (4 K values each) q, q + 2, .. (q = t & 1)
+            // of row t >> 1 of every tile, hi and lo: source addresses advance by KC
+            // floats per stage
             const int q = tid & 1, r = tid >> 1;
             bool okp = true;
             for (int kc = 0; kc < nk && okp; ++kc) {
@@ -311,13 +314,16 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
                 }
                 for (int mt = 0; mt < ntile; ++mt) {
                     const int s = s_src[mt * TM + r];
-                    const int64_t so = (int64_t)(s >= 0 ? s : 0) * a.Kpad + kc * KC + 4 * q;
-                    const uint32_t dst = su32(buf + mt * tbytes + koff(r, 4 * q));
                     const uint32_t sz = s >= 0 ? 16u : 0u;
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                                 :: "r"(dst), "l"(a.ah + so), "r"(sz) : "memory");
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                                 :: "r"(dst + (uint32_t)xbytes), "l"(a.al + so), "r"(sz) : "memory");
+#pragma unroll
+                    for (int cq = q; cq < KC / 4; cq += 2) {
+                        const int64_t so = (int64_t)(s >= 0 ? s : 0) * a.Kpad + kc * KC + 4 * cq;
+                        const uint32_t dst = su32(buf + mt * tbytes + koff(r, 4 * cq));
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                     :: "r"(dst), "l"(a.ah + so), "r"(sz) : "memory");
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                     :: "r"(dst + (uint32_t)xbytes), "l"(a.al + so), "r"(sz) : "memory");
+                    }
                 }
                 asm volatile("cp.async.commit_group;" ::: "memory");
                 if (kc >= LAG) {
@@ -346,12 +352,14 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 unsigned char *buf = smem + sb * stbytes;
-                const uint64_t dwh = sdesc(su32(buf + 2 * xbytes)), dwl = sdesc(su32(buf + 2 * xbytes + wbytes));
-                const uint32_t acc0 = kc > 0 ? 1u : 0u;
+                for (int ks = 0; ks < KC / 8; ++ks) {
+                const uint32_t ko = 256u * (uint32_t)ks;       // K step ks of the stage
+                const uint64_t dwh = sdesc(su32(buf + 2 * xbytes) + ko), dwl = sdesc(su32(buf + 2 * xbytes + wbytes) + ko);
+                const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
                 for (int mt = 0; mt < ntile; ++mt) {
                     const uint32_t d = tmem + (uint32_t)(mt * NC);
-                    const uint64_t dxh = sdesc(su32(buf + mt * tbytes));
-                    const uint64_t dxl = sdesc(su32(buf + xbytes + mt * tbytes));
+                    const uint64_t dxh = sdesc(su32(buf + mt * tbytes) + ko);
+                    const uint64_t dxl = sdesc(su32(buf + xbytes + mt * tbytes) + ko);
                     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
                                  :: "r"(d), "l"(dxh), "l"(dwh), "r"(idesc), "r"(acc0));
@@ -361,6 +369,7 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
                     asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
                                  :: "r"(d), "l"(dxl), "l"(dwh), "r"(idesc), "r"(1u));
+                }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              :: "r"(su32(&empty[sb])) : "memory");
