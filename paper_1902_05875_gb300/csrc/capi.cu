@@ -115,7 +115,9 @@ int eval_once(tefmm_plan P, int64_t ns, const double *sx, const double *sy, cons
     else TRY(near_field(P, phi, st));
     CUDA_TRY(cudaEventRecord(P->ev[6], st));
     CUDA_TRY(cudaGetLastError());
-    return TEFMM_OK;
+    // flags raised after the list checks (M2L key range, bounded waits of the
+    // tensor-core kernel) are reported by this call, before the next one resets them
+    return check_flags(P, st);
 }
 }  // namespace
 

@@ -264,13 +264,17 @@ __device__ __forceinline__ uint64_t m2l_key(int kind, int l, int lay, int dx, in
 
 __global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pair_t,
                             const int *__restrict__ v_src, const int *__restrict__ has_A,
-                            uint64_t *__restrict__ keys, int *__restrict__ vals) {
+                            uint64_t *__restrict__ keys, int *__restrict__ vals, int *flags) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= nv) return;
     int t = pair_t[e], s = v_src[e];
     int l = T.level[t], lay = T.layer[t], lays = T.layer[s];
     int dx = T.ix[t] - T.ix[s], dy = T.iy[t] - T.iy[s], dz = T.iz[t] - T.iz[s];
-    if (lay != lays) {          // cross-layer component: one table per (z_t, z_s)
+    // a V pair lies within the parent's neighbourhood: offsets fit the keys' 3-bit fields
+    if (abs(dx) > 3 || abs(dy) > 3 || (lay == lays && abs(dz) > 3)) {
+        atomicOr(flags, FLAG_CHECK);
+        keys[2 * e] = keys[2 * e + 1] = ~0ULL;
+    } else if (lay != lays) {          // cross-layer component: one table per (z_t, z_s)
         keys[2 * e] = xkey(l, lay, lays, dx, dy, T.iz[t], T.iz[s]);
         keys[2 * e + 1] = ~0ULL;
     } else {
@@ -697,7 +701,7 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     TreeArrays T = tree_arrays(P);
     k_m2l_items<<<grid_for(nv, 256), 256, 0, st>>>(nv, T, dp<int>(P->pair_t), dp<int>(P->v_src),
                                                    dp<int>(P->seg_tmp), dp<uint64_t>(P->pair_slot),
-                                                   dp<int>(P->pair_idx));
+                                                   dp<int>(P->pair_idx), dp<int>(P->flags));
     P->launches++;
     size_t bytes = 0;
     cub::DeviceRadixSort::SortPairs(nullptr, bytes, dp<uint64_t>(P->pair_slot),
