@@ -132,7 +132,10 @@ int tefmm_plan_destroy(tefmm_plan plan);
  *                       sources" case (self pairs skipped in free space only);
  *   d_phi               output potentials (device, 2*nt doubles), overwritten.
  * Errors: INVALID_ARG, POINT_ON_INTERFACE, OUT_OF_DOMAIN, OOM, CUDA,
- *         LIST_OVERFLOW, DEVICE_CHECK.  ns == 0 or nt == 0 writes zeros. */
+ *         LIST_OVERFLOW, DEVICE_CHECK (an M2L pair offset outside the key
+ *         range, or a bounded device wait that ran out).  The call returns
+ *         when the result is complete on the stream, with any device-detected
+ *         error of this evaluation.  ns == 0 or nt == 0 writes zeros. */
 int tefmm_eval(tefmm_plan plan, int64_t ns, const double *d_sx, const double *d_sy,
                const double *d_sz, const double *d_q, int64_t nt, const double *d_tx,
                const double *d_ty, const double *d_tz, double *d_phi, void *stream);
