@@ -157,6 +157,32 @@ def direct_at(w, tgt_idx):
     return phi, time.perf_counter() - t0
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' values of x (the job's time is its slowest
+    replica's); x itself when not distributed."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, interactions, ms):
+    """Whole-job throughput of `world` independent replicas, each doing
+    `interactions` pair interactions, over the slowest replica's time."""
+    return world * float(interactions) / (ms * 1e-3)
+
+
+def init_ranks(world, backend="nccl"):
+    """Process group of a multi-rank run (None for one rank)."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend)
+    return dist
+
+
 def cpu_baseline_from(n_t, n_s, seconds, name):
     return {"value": n_t * n_s / seconds, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"FP64 direct sum (C/OpenMP; cross-layer part by one DCIM fit per target) "
@@ -223,6 +249,7 @@ def run_batched(args):
                               "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT,
                                                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
+    dist = init_ranks(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ws = W.batched_instances(256)
@@ -245,6 +272,9 @@ def run_batched(args):
     torch.cuda.synchronize()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     cp, cpath = clocks_start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
     times = []
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -255,11 +285,13 @@ def run_batched(args):
         e1.record()
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    if dist is not None:
+        dist.barrier()
     clocks = clocks_stop(cp, cpath, local)
-    ms = float(np.mean(times))
+    ms = max_over_ranks(float(np.mean(times)), dist, dev)
     inter = float(sum(len(w.src) ** 2 for w in ws))
     caps = [pl.stats()["leaf_cap_used"] for pl in plans]
-    line = {"metric": METRIC_BATCH, "value": world * inter / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+    line = {"metric": METRIC_BATCH, "value": replica_value(world, inter, ms), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+tf32x3/f64", "data": "synthetic",
             "config": {"workload": BATCHED, "instances": len(ws), "points": int(sum(len(w.src) for w in ws)),
@@ -270,6 +302,8 @@ def run_batched(args):
             "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 METRIC_BATCH = "batched TE-FMM matvec interactions/s (sum of N_i^2 per batch time), 256 instances"
@@ -322,10 +356,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    dist = init_ranks(world)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1902_05875_gb300 import tefmm
@@ -355,13 +386,9 @@ def main():
     barrier()
     clocks = clocks_stop(cp, cpath, local)
     launches = plan.stats()["n_launches"] - launches0
-    ms = float(np.mean(times))
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), dist, dev)
     N = len(w.src)
-    value = world * N * N / (ms * 1e-3)
+    value = replica_value(world, N * N, ms)
     st = plan.stats()
     phi = out.cpu().numpy()
 
