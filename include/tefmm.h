@@ -140,6 +140,25 @@ int tefmm_eval(tefmm_plan plan, int64_t ns, const double *d_sx, const double *d_
                const double *d_sz, const double *d_q, int64_t nt, const double *d_tx,
                const double *d_ty, const double *d_tz, double *d_phi, void *stream);
 
+/* Geometry once, charges many times: the repeated matrix-vector products of an
+ * iterative solver (Sec. 1 motivates the FMM as the matvec of such solvers).
+ * tefmm_set_points builds, for the given points, everything of tefmm_eval
+ * that does not depend on the charges: trees, lists, M2L keys, cross-layer
+ * fits and derivative tables (arguments as tefmm_eval without d_q and d_phi).
+ * tefmm_apply then evaluates the potentials of charges d_q (device, 2*ns
+ * doubles, interleaved, in the order of the set_points sources) into d_phi
+ * (device, 2*nt doubles, target order), running only P2M, M2M, M2L, L2L, L2P
+ * and the near field.  The points are not copied from the caller again; the
+ * plan keeps its own sorted copy.  tefmm_eval also leaves the plan ready for
+ * tefmm_apply on its points; tefmm_plan_set_images invalidates it.
+ * Errors: as tefmm_eval; tefmm_apply returns INVALID_ARG when the plan has no
+ * points.  A plan made with leaf_cap = 0 uses the cap its autotuner chose in
+ * an earlier tefmm_eval, else 64.  No counterpart in the paper's code. */
+int tefmm_set_points(tefmm_plan plan, int64_t ns, const double *d_sx, const double *d_sy,
+                     const double *d_sz, int64_t nt, const double *d_tx, const double *d_ty,
+                     const double *d_tz, void *stream);
+int tefmm_apply(tefmm_plan plan, const double *d_q, double *d_phi, void *stream);
+
 /* One instance of a batch: device arrays as for tefmm_eval; tx == NULL means
  * the targets are the sources (then nt, ty, tz are ignored). */
 typedef struct {

@@ -25,6 +25,16 @@ __global__ void k_zero(int64_t n, double *a) {
     if (i < n) a[i] = 0.0;
 }
 
+// charges into the plan's source order: sq[pos] = q[perm_s[pos]]
+__global__ void k_gather_q(int64_t ns, const int *__restrict__ perm_s, const double *__restrict__ q,
+                           double *__restrict__ sq) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const int64_t v = perm_s[i];
+    sq[2 * i] = q[2 * v];
+    sq[2 * i + 1] = q[2 * v + 1];
+}
+
 float elapsed(cudaEvent_t a, cudaEvent_t b) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, a, b);
@@ -36,6 +46,12 @@ namespace {
 int eval_once(tefmm_plan P, int64_t ns, const double *sx, const double *sy, const double *sz,
               const double *q, int64_t nt, const double *tx, const double *ty, const double *tz,
               double *phi, cudaStream_t st);
+int geometry(tefmm_plan P, int64_t ns, const double *sx, const double *sy, const double *sz,
+             const double *q, int64_t nt, const double *tx, const double *ty, const double *tz,
+             cudaStream_t st);
+int charge_phases(tefmm_plan P, double *phi, cudaStream_t st);
+int tables(tefmm_plan P, cudaStream_t st);
+int zero_output(int64_t nt, double *phi, cudaStream_t st, tefmm_plan P);
 }
 
 // Leaf-cap autotuner: with leaf_cap = 0 the first evaluation tries each cap of
@@ -72,24 +88,57 @@ extern "C" int tefmm_eval(tefmm_plan P, int64_t ns, const double *sx, const doub
     return eval_once(P, ns, sx, sy, sz, q, nt, tx, ty, tz, phi, st);
 }
 
-namespace {
-int eval_once(tefmm_plan P, int64_t ns, const double *sx, const double *sy, const double *sz,
-              const double *q, int64_t nt, const double *tx, const double *ty, const double *tz,
-              double *phi, cudaStream_t st) {
-    if (nt > 0 && !phi) return TEFMM_ERR_INVALID_ARG;
-    if (ns > 0 && (!sx || !sy || !sz || !q)) return TEFMM_ERR_INVALID_ARG;
+// Geometry once, charges many times (an iterative solver's matrix-vector
+// products): set_points builds the trees, lists, M2L keys, cross-layer fits
+// and derivative tables of the points; apply then runs only the phases that
+// depend on the charges.  A plan made with leaf_cap = 0 uses the cap its
+// autotuner chose in an earlier tefmm_eval, else 64.
+extern "C" int tefmm_set_points(tefmm_plan P, int64_t ns, const double *sx, const double *sy,
+                                const double *sz, int64_t nt, const double *tx, const double *ty,
+                                const double *tz, void *stream) {
+    if (!P || ns < 0 || nt < 0 || ns > (1LL << 30) || nt > (1LL << 30)) return TEFMM_ERR_INVALID_ARG;
+    if (ns > 0 && (!sx || !sy || !sz)) return TEFMM_ERR_INVALID_ARG;
     if (nt > 0 && (!tx || !ty || !tz)) return TEFMM_ERR_INVALID_ARG;
-    if (ns == 0 || nt == 0) {
-        if (nt > 0) {
-            k_zero<<<grid_for(2 * nt, 256), 256, 0, st>>>(2 * nt, phi);
-            P->launches++;
-        }
-        CUDA_TRY(cudaGetLastError());
-        return TEFMM_OK;
-    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P->leaf_cap_eff == 0) P->leaf_cap_eff = 64;
+    TRY(geometry(P, ns, sx, sy, sz, nullptr, nt, tx, ty, tz, st));
+    if (ns == 0 || nt == 0) return TEFMM_OK;
+    TRY(tables(P, st));
+    P->geom_ready = true;
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_apply(tefmm_plan P, const double *q, double *phi, void *stream) {
+    if (!P || !P->geom_ready) return TEFMM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (P->ns == 0 || P->nt == 0) return zero_output(P->nt, phi, st, P);
+    if (!q || !phi) return TEFMM_ERR_INVALID_ARG;
+    CUDA_TRY(cudaEventRecord(P->ev[0], st));
+    k_gather_q<<<grid_for(P->ns, 256), 256, 0, st>>>(P->ns, dp<int>(P->perm_s), q, dp<double>(P->sq));
+    P->launches++;
+    CUDA_TRY(cudaEventRecord(P->ev[1], st));
+    TRY(upward_pass(P, st));
+    // no tables to build: ev[2], ev[7] and ev[3] mark an empty phase
+    CUDA_TRY(cudaEventRecord(P->ev[2], st));
+    CUDA_TRY(cudaEventRecord(P->ev[7], st));
+    CUDA_TRY(cudaEventRecord(P->ev[3], st));
+    return charge_phases(P, phi, st);
+}
+
+namespace {
+// tree, lists, M2L keys, cross-layer fits (ev[0] .. ev[1]); with q == nullptr
+// the sorted charges are left alone (set_points)
+int geometry(tefmm_plan P, int64_t ns, const double *sx, const double *sy, const double *sz,
+             const double *q, int64_t nt, const double *tx, const double *ty, const double *tz,
+             cudaStream_t st) {
+    P->geom_ready = false;
     P->ns = ns;
     P->nt = nt;
     P->shared_pts = (tx == sx && ty == sy && tz == sz && nt == ns);
+    if (ns == 0 || nt == 0) {
+        P->geom_ready = true;
+        return TEFMM_OK;
+    }
     CUDA_TRY(cudaEventRecord(P->ev[0], st));
     TRY(tree_build(P, sx, sy, sz, q, tx, ty, tz, st));
     TRY(check_flags(P, st));
@@ -98,12 +147,22 @@ int eval_once(tefmm_plan P, int64_t ns, const double *sx, const double *sy, cons
     TRY(m2l_prepare(P, st));
     TRY(cross_prepare(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[1], st));
-    TRY(upward_pass(P, st));
+    return TEFMM_OK;
+}
+
+// derivative tables (ev[2] .. ev[3], cross-layer from ev[7])
+int tables(tefmm_plan P, cudaStream_t st) {
     CUDA_TRY(cudaEventRecord(P->ev[2], st));
     TRY(m2l_tables(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[7], st));
     TRY(cross_tables(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[3], st));
+    return TEFMM_OK;
+}
+
+// M2L, L2L, L2P and near field for the sorted charges (ev[3] .. ev[6]), then
+// the device flags of the whole evaluation
+int charge_phases(tefmm_plan P, double *phi, cudaStream_t st) {
     if (P->opt.precision == TEFMM_MIXED) TRY(m2l_apply_tc(P, st));
     else TRY(m2l_apply(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[8], st));
@@ -118,6 +177,30 @@ int eval_once(tefmm_plan P, int64_t ns, const double *sx, const double *sy, cons
     // flags raised after the list checks (M2L key range, bounded waits of the
     // tensor-core kernel) are reported by this call, before the next one resets them
     return check_flags(P, st);
+}
+
+int zero_output(int64_t nt, double *phi, cudaStream_t st, tefmm_plan P) {
+    if (nt > 0) {
+        k_zero<<<grid_for(2 * nt, 256), 256, 0, st>>>(2 * nt, phi);
+        P->launches++;
+    }
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
+int eval_once(tefmm_plan P, int64_t ns, const double *sx, const double *sy, const double *sz,
+              const double *q, int64_t nt, const double *tx, const double *ty, const double *tz,
+              double *phi, cudaStream_t st) {
+    if (nt > 0 && !phi) return TEFMM_ERR_INVALID_ARG;
+    if (ns > 0 && (!sx || !sy || !sz || !q)) return TEFMM_ERR_INVALID_ARG;
+    if (nt > 0 && (!tx || !ty || !tz)) return TEFMM_ERR_INVALID_ARG;
+    TRY(geometry(P, ns, sx, sy, sz, q, nt, tx, ty, tz, st));
+    if (ns == 0 || nt == 0) return zero_output(nt, phi, st, P);
+    TRY(upward_pass(P, st));
+    TRY(tables(P, st));
+    TRY(charge_phases(P, phi, st));
+    P->geom_ready = true;
+    return TEFMM_OK;
 }
 }  // namespace
 

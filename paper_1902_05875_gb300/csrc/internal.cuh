@@ -151,6 +151,7 @@ struct tefmm_plan_s {
     // workspace of the last evaluation
     int64_t ns = 0, nt = 0, nitems = 0;
     bool shared_pts = false;
+    bool geom_ready = false;   // tree, lists and tables match the last points (eval or set_points)
     DBuf keys_in, keys_out, vals_in, vals_out, cub_tmp, scan_tmp;
     DBuf item_node, item_flag, item_scan, cnt_s, cnt_t;
     DBuf sx, sy, sz, sq, tx, ty, tz, perm_s, perm_t;

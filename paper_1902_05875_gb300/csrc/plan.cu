@@ -278,6 +278,7 @@ extern "C" int tefmm_plan_set_images(tefmm_plan P, const int *term_count, const 
         tot += term_count[i];
     }
     if (tot > 0 && (!A || !Z)) return TEFMM_ERR_INVALID_ARG;
+    P->geom_ready = false;      // the derivative tables depend on the images
     P->A.assign(tot, mkc(0, 0));
     P->Z.assign(tot, mkc(0, 0));
     int f = 0;

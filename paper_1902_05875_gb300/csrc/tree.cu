@@ -143,8 +143,10 @@ __global__ void k_gather(int64_t nitems, int64_t ns, bool shared, const int *__r
         osx[pos] = sx[v];
         osy[pos] = sy[v];
         osz[pos] = sz[v];
-        oq[2 * pos] = q[2 * v];
-        oq[2 * pos + 1] = q[2 * v + 1];
+        if (q) {                      // no charges when only the geometry is built
+            oq[2 * pos] = q[2 * v];
+            oq[2 * pos + 1] = q[2 * v + 1];
+        }
         perm_s[pos] = v;
     } else {
         int64_t pos = i - cnt_s[i];

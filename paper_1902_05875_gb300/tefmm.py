@@ -15,6 +15,7 @@ import numpy as np
 from . import _build
 
 OK = 0
+ERR_INVALID_ARG = -1
 _STATUS = {}
 
 FP64 = 0
@@ -47,7 +48,7 @@ EXPORTED = [
     "tefmm_eval_host", "tefmm_get_stats", "tefmm_status_string", "tefmm_plan_image_counts",
     "tefmm_plan_get_images", "tefmm_plan_set_images", "tefmm_export_tree", "tefmm_export_lists",
     "tefmm_export_expansions", "tefmm_fit_images_noalloc", "tefmm_plan_cross_images",
-    "tefmm_eval_batched",
+    "tefmm_eval_batched", "tefmm_set_points", "tefmm_apply",
 ]
 
 _lib = None
@@ -78,6 +79,8 @@ def load(build_if_needed=True):
     lib.tefmm_plan_destroy.argtypes = [P]
     lib.tefmm_eval.argtypes = [P, i64, P, P, P, P, i64, P, P, P, P, P]
     lib.tefmm_eval_host.argtypes = [P, i64, D, D, D, D, i64, D, D, D, D, P]
+    lib.tefmm_set_points.argtypes = [P, i64, P, P, P, i64, P, P, P, P]
+    lib.tefmm_apply.argtypes = [P, P, P, P]
     lib.tefmm_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
     lib.tefmm_status_string.argtypes = [ctypes.c_int]
     lib.tefmm_status_string.restype = ctypes.c_char_p
@@ -213,11 +216,43 @@ class Plan:
         if q.dtype != torch.complex128 or not q.is_cuda or not q.is_contiguous():
             raise ValueError("q must be a contiguous complex128 CUDA tensor")
         ns, nt = sx.numel(), tx.numel()
+        self._n_targets = nt
         if out is None:
             out = torch.empty(nt, dtype=torch.complex128, device=sx.device)
         vp = lambda t: ctypes.c_void_p(t.data_ptr())
         _check(self.lib.tefmm_eval(self.h, ns, vp(sx), vp(sy), vp(sz), vp(q), nt, vp(tx), vp(ty),
                                    vp(tz), vp(out), _stream_handle(stream)), "tefmm_eval")
+        return out
+
+    def set_points(self, sx, sy, sz, tx=None, ty=None, tz=None, stream=None):
+        """``tefmm_set_points``: build the charge-independent part (trees, lists,
+        keys, fits, tables) for these points; targets default to the sources."""
+        import torch
+        shared = tx is None
+        if shared:
+            tx, ty, tz = sx, sy, sz
+        for a in (sx, sy, sz, tx, ty, tz):
+            if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous():
+                raise ValueError("coordinates must be contiguous float64 CUDA tensors")
+        vp = lambda t: ctypes.c_void_p(t.data_ptr())
+        self._n_targets = tx.numel()
+        self._device = sx.device
+        _check(self.lib.tefmm_set_points(self.h, sx.numel(), vp(sx), vp(sy), vp(sz), tx.numel(), vp(tx),
+                                         vp(ty), vp(tz), _stream_handle(stream)), "tefmm_set_points")
+
+    def apply(self, q, out=None, stream=None):
+        """``tefmm_apply``: potentials of charges q (contiguous complex128 CUDA
+        tensor, source order) on the points of the last set_points / eval."""
+        import torch
+        if q.dtype != torch.complex128 or not q.is_cuda or not q.is_contiguous():
+            raise ValueError("q must be a contiguous complex128 CUDA tensor")
+        if out is None:
+            n = getattr(self, "_n_targets", None)
+            if n is None:
+                raise RuntimeError("apply() needs set_points() or eval() first")
+            out = torch.empty(n, dtype=torch.complex128, device=q.device)
+        vp = lambda t: ctypes.c_void_p(t.data_ptr())
+        _check(self.lib.tefmm_apply(self.h, vp(q), vp(out), _stream_handle(stream)), "tefmm_apply")
         return out
 
     def eval_host(self, src, q, tgt=None, stream=None):
