@@ -1,0 +1,66 @@
+"""Host-side helpers of bench.py that decide whether a run is valid (no GPU):
+the clock record taken during the timed region, and the CPU-baseline line."""
+import os
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+class _FakeSampler:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def _record(lines):
+    f = tempfile.NamedTemporaryFile("w", suffix=".csv", delete=False)
+    f.write("\n".join(lines) + "\n")
+    f.close()
+    return f.name
+
+
+def test_clock_record_median_max_and_reasons():
+    import bench
+    # index, clocks.sm, clocks.max.sm, power, active, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    path = _record([
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "1, 900, 2070, 300.0, 0x8, Active, Not Active, Not Active, Not Active",   # another GPU
+        "garbage line",
+    ])
+    c = bench.clocks_stop(_FakeSampler(), path, 0)
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"]          # kept and noted; GPU 1's slowdown ignored
+    assert not os.path.exists(path)
+
+
+def test_clock_record_flags_hardware_slowdown():
+    import bench
+    path = _record([
+        "2, 1500, 2070, 800.0, 0x8, Active, Active, Not Active, Not Active",
+        "2, 1490, 2070, 800.0, 0x8, Active, Not Active, Not Active, Not Active",
+    ])
+    c = bench.clocks_stop(_FakeSampler(), path, 2)
+    assert set(c["reasons"]) == {"hw_slowdown", "hw_thermal_slowdown"}
+    assert c["sm_mhz"] == pytest.approx(1495.0)
+
+
+def test_clock_record_without_sampler():
+    import bench
+    c = bench.clocks_stop(None, None, 0)
+    assert c["sm_mhz"] is None and c["reasons"]
+
+
+def test_cpu_baseline_line():
+    import bench
+    cb = bench.cpu_baseline_from(100, 2_000_000, 40.0, "w")
+    assert cb["kind"] == "oracle" and cb["unit"] == bench.UNIT
+    assert cb["value"] == pytest.approx(100 * 2e6 / 40.0)
+    assert cb["cores"] == os.cpu_count()
