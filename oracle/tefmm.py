@@ -130,11 +130,15 @@ def int_coords(xyz, lo, side):
 class Trees:
     """Per-layer octrees in a common root cube (see module docstring)."""
 
-    def __init__(self, med, src, tgt, leaf_cap, max_level=NBITS, cube=None, zext=None):
+    def __init__(self, med, src, tgt, leaf_cap, max_level=NBITS, cube=None, zext=None, kh_max=None):
         self.med = med
         allp = np.concatenate([src, tgt], 0)
         self.lo, self.side = root_cube(allp) if cube is None else cube
         self.HX = cross_box_limit(med, zext)
+        # wavenumber admissibility (off unless kh_max is given): on levels whose box
+        # size h has k_max h > kh_max, pairs of split boxes are refined, not translated
+        self.kh_max = kh_max
+        self.kmax = max(abs(complex(k)) for k in med.k)
         self.leaf_cap = leaf_cap
         self.max_level = max_level
         self.slay = med.layer_of(src[:, 2])
@@ -246,6 +250,16 @@ class Trees:
             return False
         return max(abs(int(self.ix[a]) - int(self.ix[b])), abs(int(self.iy[a]) - int(self.iy[b]))) <= 1
 
+    def coarse_colleague(self, a, b):
+        """Same-level split boxes on a level where the Taylor expansions would
+        span k_max h > kh_max: their children are paired instead (no translation)."""
+        if self.kh_max is None:
+            return False
+        la = int(self.level[a])
+        if la != int(self.level[b]) or self.is_leaf[a] or self.is_leaf[b]:
+            return False
+        return self.kmax * self.side / float(1 << la) > self.kh_max
+
     def adjacent(self, a, b):
         la, lb = int(self.level[a]), int(self.level[b])
         if la > lb:
@@ -323,7 +337,7 @@ def build_lists(tr: Trees, lt, ls):
         else:
             for ct in ch_t(t):
                 for cs in ch_s(s):
-                    if tr.adjacent(ct, cs) or tr.cross_colleague(ct, cs):
+                    if tr.adjacent(ct, cs) or tr.cross_colleague(ct, cs) or tr.coarse_colleague(ct, cs):
                         stack.append((ct, cs))
                     else:
                         add(V, ct, cs)
@@ -436,8 +450,9 @@ class TEFMM:
     """Algorithm 1 + the component loop, for every (target layer, source layer)."""
 
     def __init__(self, med, images, p, leaf_cap, max_level=NBITS, cube=None, zext=None,
-                 cross_images=None, n_images=None):
+                 cross_images=None, n_images=None, kh_max=None):
         self.med = med
+        self.kh_max = kh_max
         self.images = images
         self.zext = zext if zext is not None else (images.zext if images is not None else None)
         # cross-layer images: dict (lt, ls, direction, level, izs, k3p) -> (A, Z);
@@ -454,7 +469,7 @@ class TEFMM:
         self.src = np.asarray(src, float)
         self.tgt = np.asarray(tgt, float)
         self.tr = Trees(self.med, self.src, self.tgt, self.leaf_cap, self.max_level, self.cube,
-                        self.zext)
+                        self.zext, kh_max=self.kh_max)
         self.lists = {}
         for lt in range(self.med.n_layers):
             for ls in range(self.med.n_layers):
