@@ -246,11 +246,14 @@ class Plan:
         import torch
         if q.dtype != torch.complex128 or not q.is_cuda or not q.is_contiguous():
             raise ValueError("q must be a contiguous complex128 CUDA tensor")
+        n = getattr(self, "_n_targets", None)
         if out is None:
-            n = getattr(self, "_n_targets", None)
             if n is None:
                 raise RuntimeError("apply() needs set_points() or eval() first")
             out = torch.empty(n, dtype=torch.complex128, device=q.device)
+        elif out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous() or \
+                (n is not None and out.numel() != n):
+            raise ValueError("out must be a contiguous complex128 CUDA tensor with one entry per target")
         vp = lambda t: ctypes.c_void_p(t.data_ptr())
         _check(self.lib.tefmm_apply(self.h, vp(q), vp(out), _stream_handle(stream)), "tefmm_apply")
         return out

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -42,3 +44,15 @@ def test_default_options_without_gpu():
 def test_built_for_sm103a():
     from paper_1902_05875_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+
+
+def test_apply_binding_checks_arguments_without_gpu():
+    """set_points / apply refuse host tensors before calling the library."""
+    torch = pytest.importorskip("torch")
+    from paper_1902_05875_gb300 import tefmm
+    plan = object.__new__(tefmm.Plan)          # argument checks only: no device plan
+    x = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        tefmm.Plan.set_points(plan, x, x, x)
+    with pytest.raises(ValueError):
+        tefmm.Plan.apply(plan, torch.zeros(4, dtype=torch.complex128))
