@@ -157,6 +157,24 @@ def direct_at(w, tgt_idx):
     return phi, time.perf_counter() - t0
 
 
+def err_stats(phi, ref, layer=None):
+    """The paper's error measures (Sec. 4): Err_2 = sqrt(sum |ref - phi|^2 / sum |ref|^2)
+    and Err_max = max_i |ref_i - phi_i| / |ref_i|, over all sampled targets and,
+    given each target's layer, per layer."""
+    phi = np.asarray(phi)
+    ref = np.asarray(ref)
+    e = np.abs(phi - ref)
+
+    def one(m):
+        return {"rel_l2": float(np.sqrt(np.sum(e[m] ** 2) / np.sum(np.abs(ref[m]) ** 2))),
+                "max_rel": float(np.max(e[m] / np.abs(ref[m])))}
+    out = one(np.ones(len(ref), dtype=bool))
+    if layer is not None:
+        layer = np.asarray(layer)
+        out["per_layer"] = {str(int(l)): one(layer == l) for l in np.unique(layer)}
+    return out
+
+
 def max_over_ranks(x, dist, device):
     """The largest of the ranks' values of x (the job's time is its slowest
     replica's); x itself when not distributed."""
@@ -494,8 +512,12 @@ def main():
         acc = line.setdefault("accuracy", {})
         acc["samples"] = int(len(idx))
         acc[f"{args.precision}_vs_direct_rel_l2"] = float(np.linalg.norm(phi[idx] - ref) / np.linalg.norm(ref))
+        from oracle.medium import Medium
+        lay = Medium(w.interfaces, w.k).layer_of(w.src[idx, 2])
+        acc[f"{args.precision}_vs_direct"] = err_stats(phi[idx], ref, lay)
         if phi64 is not None:
             acc["fp64_vs_direct_rel_l2"] = float(np.linalg.norm(phi64[idx] - ref) / np.linalg.norm(ref))
+            acc["fp64_vs_direct"] = err_stats(phi64[idx], ref, lay)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_from(len(idx), N, dt, w.name)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and "cpu_baseline" not in line:

@@ -64,3 +64,17 @@ def test_cpu_baseline_line():
     assert cb["kind"] == "oracle" and cb["unit"] == bench.UNIT
     assert cb["value"] == pytest.approx(100 * 2e6 / 40.0)
     assert cb["cores"] == os.cpu_count()
+
+
+def test_err_stats_follow_the_papers_measures():
+    """Err_2 and Err_max (Sec. 4), overall and per layer, on a hand-made case."""
+    import numpy as np
+    import bench
+    ref = np.array([1.0, 2.0j, -2.0, 4.0])
+    phi = ref + np.array([0.1, 0.0, 0.2j, 0.0])
+    s = bench.err_stats(phi, ref, [0, 0, 1, 1])
+    assert s["rel_l2"] == pytest.approx(np.sqrt((0.01 + 0.04) / (1 + 4 + 4 + 16)))
+    assert s["max_rel"] == pytest.approx(0.1)              # 0.1 / 1 beats 0.2 / 2
+    assert s["per_layer"]["0"]["rel_l2"] == pytest.approx(np.sqrt(0.01 / 5))
+    assert s["per_layer"]["1"]["max_rel"] == pytest.approx(0.1)
+    assert s["per_layer"]["1"]["rel_l2"] == pytest.approx(np.sqrt(0.04 / 20))
