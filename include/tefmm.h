@@ -53,6 +53,12 @@ extern "C" {
 #define TEFMM_FP64 0   /* every step in FP64                                          */
 #define TEFMM_MIXED 1  /* M2L on tensor cores and P2P in FP32; FP64 tables and sums   */
 
+#define TEFMM_ALG_RECURRENCE 1 /* Algorithm 1: DCIM images + derivative recurrence (Sec. 3.3) */
+#define TEFMM_ALG_TABLES 2     /* Algorithm 2/3 (Sec. 4): symmetric-derivative tables          */
+
+#define TEFMM_SPLIT_TF32X3 0   /* mixed form: FP32 operands split hi + lo in TF32, three products
+                                  (hi*hi + hi*lo + lo*hi) with FP32 accumulation                */
+
 typedef struct tefmm_plan_s *tefmm_plan;
 
 typedef struct {
@@ -67,8 +73,25 @@ typedef struct {
     double T1;             /* length of the first-level path (Sec. 3.3 uses 10)       */
     double T0;             /* second-level path; <= 0: sqrt(((max Re k + 0.8)/Re k_l)^2 - 1) */
     double zext[2 * 16];   /* per layer (zlo, zhi): z-range of the particles, used for
-                              the DCIM shift zeta_min (Sec. 3.2, z_min); a point outside
+                              the DCIM shift zeta_min (Sec. 3.3, z_min); a point outside
                               its layer's range is TEFMM_ERR_OUT_OF_DOMAIN             */
+    double kh_max;         /* wavenumber admissibility: on octree levels whose box size h
+                              has max_l |k_l| h > kh_max, two split boxes are not
+                              translated (M2L) but their children are paired, so every
+                              translation spans k h <= kh_max (the truncated Taylor
+                              series of e^{ikR}/R of Sec. 3.1 converges slowly for
+                              large k h); <= 0 turns the rule off.  Default 3.5.  The
+                              first translating level may pair boxes at most 15 apart:
+                              a medium that needs more coarse levels returns
+                              TEFMM_ERR_NOT_IMPLEMENTED from the evaluation.          */
+    int algorithm;         /* TEFMM_ALG_RECURRENCE (default); TEFMM_ALG_TABLES is not
+                              built: TEFMM_ERR_NOT_IMPLEMENTED                         */
+    int split;             /* tensor-core split of the mixed form: TEFMM_SPLIT_TF32X3
+                              (the only one built; others TEFMM_ERR_NOT_IMPLEMENTED)  */
+    int scale_output;      /* 0 (default): potentials in the paper's normalisation
+                              (Sec. 3.1: free term h0(k|r - r'|), factor i k_l/(4 pi)
+                              omitted); 1: every potential multiplied by i k_l/(4 pi)
+                              of its target's layer l                                  */
 } tefmm_options;
 
 typedef struct {
@@ -102,18 +125,20 @@ typedef struct {
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,
- * 8 images, 101 samples, T1 = 10, T0 = formula, zext = whole layers. */
+ * 8 images, 101 samples, T1 = 10, T0 = formula, zext = whole layers,
+ * kh_max = 3.5, algorithm 1, TF32x3 split, unscaled output. */
 int tefmm_default_options(tefmm_options *opt);
 
 /* Create a plan for a layered medium (Sec. 2.1) and fit its DCIM images
- * (Sec. 3.2, Steps 1-2) on the device.
+ * (Sec. 3.3, Steps 1-2) on the device.
  *   n_layers        1..8;
  *   interfaces      host array [n_layers-1], strictly decreasing;
  *   k_re, k_im      host arrays [n_layers], k_im >= 0;
  *   opt             host struct (NULL = defaults);
  *   stream          cudaStream_t used for the fits;
  *   out             receives the plan.
- * Errors: INVALID_ARG, OOM, CUDA, FIT_FAILED. */
+ * Errors: INVALID_ARG, OOM, CUDA, FIT_FAILED, NOT_IMPLEMENTED (algorithm or
+ * split not built). */
 int tefmm_plan_create(int n_layers, const double *interfaces, const double *k_re,
                       const double *k_im, const tefmm_options *opt, void *stream,
                       tefmm_plan *out);
@@ -251,6 +276,20 @@ int tefmm_export_expansions(tefmm_plan plan, double *alpha, double *beta);
  * Any of keys/counts/A/Z may be NULL.  Errors: INVALID_ARG. */
 int tefmm_plan_cross_images(tefmm_plan plan, int *n_fits, int *keys, int *counts, double *A,
                             double *Z);
+
+/* Replace or add cross-layer fits in the plan's cache (the inverse of
+ * tefmm_plan_cross_images, same layouts): fit i with key keys[6*i..6*i+5] =
+ * (l, l', part, level, iz_s, k3') takes the counts[i] images at
+ * A[2*(32*i + j)], Z[2*(32*i + j)].  The fits describe the source z-centre of
+ * the root cube of the plan's last evaluation (or set_points): an evaluation
+ * with a different root cube z-origin or side discards the cache.  The next
+ * tefmm_eval / tefmm_set_points rebuilds the cross-layer tables from them
+ * (tefmm_apply is refused until then).  The parity tests use it to run the
+ * device on the oracle's fits; the paper has no counterpart.
+ * Errors: INVALID_ARG (a key outside the plan's layers, parts, p or levels, or
+ * more than 32 images). */
+int tefmm_plan_set_cross_images(tefmm_plan plan, int n_fits, const int *keys, const int *counts,
+                                const double *A, const double *Z);
 
 /* ---- fit without device allocation -------------------------------------
  * The paper has no counterpart to this call; it is a convenience of this

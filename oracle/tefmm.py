@@ -74,6 +74,9 @@ from .derivs import multi_indices, index_map, n_coeffs, taylor_h0
 from . import cross as xl
 
 NBITS = 20
+# wavenumber admissibility bound (see Trees): on levels where k_max h > KH_MAX,
+# split boxes are paired instead of translated; None turns the rule off
+KH_MAX = 3.5
 
 
 def morton_encode(ix, iy, iz):
@@ -130,12 +133,12 @@ def int_coords(xyz, lo, side):
 class Trees:
     """Per-layer octrees in a common root cube (see module docstring)."""
 
-    def __init__(self, med, src, tgt, leaf_cap, max_level=NBITS, cube=None, zext=None, kh_max=None):
+    def __init__(self, med, src, tgt, leaf_cap, max_level=NBITS, cube=None, zext=None, kh_max=KH_MAX):
         self.med = med
         allp = np.concatenate([src, tgt], 0)
         self.lo, self.side = root_cube(allp) if cube is None else cube
         self.HX = cross_box_limit(med, zext)
-        # wavenumber admissibility (off unless kh_max is given): on levels whose box
+        # wavenumber admissibility (kh_max None or <= 0: off): on levels whose box
         # size h has k_max h > kh_max, pairs of split boxes are refined, not translated
         self.kh_max = kh_max
         self.kmax = max(abs(complex(k)) for k in med.k)
@@ -253,7 +256,7 @@ class Trees:
     def coarse_colleague(self, a, b):
         """Same-level split boxes on a level where the Taylor expansions would
         span k_max h > kh_max: their children are paired instead (no translation)."""
-        if self.kh_max is None:
+        if self.kh_max is None or self.kh_max <= 0:
             return False
         la = int(self.level[a])
         if la != int(self.level[b]) or self.is_leaf[a] or self.is_leaf[b]:
@@ -450,7 +453,7 @@ class TEFMM:
     """Algorithm 1 + the component loop, for every (target layer, source layer)."""
 
     def __init__(self, med, images, p, leaf_cap, max_level=NBITS, cube=None, zext=None,
-                 cross_images=None, n_images=None, kh_max=None):
+                 cross_images=None, n_images=None, kh_max=KH_MAX):
         self.med = med
         self.kh_max = kh_max
         self.images = images

@@ -132,12 +132,12 @@ __global__ void k_first_cross(int ntab, const uint64_t *__restrict__ tkey, int64
                               const int *__restrict__ chunk_table, int *out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < ntab) {
-        bool x = (tkey[i] >> 62) == 2, xp = i > 0 && (tkey[i - 1] >> 62) == 2;
+        bool x = key_kind(tkey[i]) == 2, xp = i > 0 && key_kind(tkey[i - 1]) == 2;
         if (x && !xp) out[0] = (int)i;
     }
     if (i < nch) {
-        bool x = (tkey[chunk_table[i]] >> 62) == 2;
-        bool xp = i > 0 && (tkey[chunk_table[i - 1]] >> 62) == 2;
+        bool x = key_kind(tkey[chunk_table[i]]) == 2;
+        bool xp = i > 0 && key_kind(tkey[chunk_table[i - 1]]) == 2;
         if (x && !xp) out[1] = (int)i;
     }
 }
@@ -505,5 +505,31 @@ extern "C" int tefmm_plan_cross_images(tefmm_plan P, int *n_fits, int *keys, int
         }
         ++i;
     }
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_plan_set_cross_images(tefmm_plan P, int n_fits, const int *keys, const int *counts,
+                                           const double *A, const double *Z) {
+    if (!P || n_fits < 0 || (n_fits > 0 && (!keys || !counts || !A || !Z))) return TEFMM_ERR_INVALID_ARG;
+    for (int i = 0; i < n_fits; ++i) {
+        const int *k = keys + 6 * i;
+        const int lt = k[0], ls = k[1], dir = k[2], lev = k[3], izs = k[4], k3p = k[5];
+        if (lt < 0 || lt >= P->nL || ls < 0 || ls >= P->nL || lt == ls || (dir != 0 && dir != 1) ||
+            (dir == 0 && lt >= P->nL - 1) || (dir == 1 && lt == 0) || lev < 0 || lev > TEFMM_NBITS ||
+            izs < 0 || izs >= (1 << lev) || k3p < 0 || k3p > P->p || counts[i] < 0 ||
+            counts[i] > TEFMM_MAX_IMG)
+            return TEFMM_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < n_fits; ++i) {
+        const int *k = keys + 6 * i;
+        CrossFitVal v{(int)P->xA.size(), counts[i]};
+        for (int j = 0; j < counts[i]; ++j) {
+            P->xA.push_back(mkc(A[2 * (TEFMM_MAX_IMG * i + j)], A[2 * (TEFMM_MAX_IMG * i + j) + 1]));
+            P->xZ.push_back(mkc(Z[2 * (TEFMM_MAX_IMG * i + j)], Z[2 * (TEFMM_MAX_IMG * i + j) + 1]));
+        }
+        P->xcache[CrossFitKey{k[0], k[1], k[2], k[3], k[4], k[5]}] = v;
+    }
+    P->x_uploaded = (size_t)-1;   // the device pool is copied again by the next evaluation
+    P->geom_ready = false;        // tables of the imported fits are built by the next evaluation
     return TEFMM_OK;
 }

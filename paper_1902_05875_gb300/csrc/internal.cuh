@@ -132,6 +132,7 @@ struct tefmm_plan_s {
     int device = 0;
     int leaf_cap_eff = 64;        // leaf cap in use (0 until the autotuner has chosen one)
     double HX = INFINITY;         // box size above which stacked cross-layer boxes are paired, not translated
+    double kmax = 0.0;            // max over layers of |k_l| (wavenumber admissibility)
     double ms_autotune = 0;       // time of the autotuner's trial evaluations
 
     // images (host mirror + device copy)
@@ -166,7 +167,7 @@ struct tefmm_plan_s {
     DBuf C_list, C_cnt, D_list, D_cnt, X_list, X_cnt, V_tmp, V_cnt;
     DBuf v_ptr, v_src, near_ptr, near_src, near_tmp, near_cnt;
     int64_t n_v = 0, n_near = 0, n_p2p_pairs = 0;
-    int cap_C = 0, cap_V = 0, cap_D = 64, cap_X = 0, cap_near = 0;
+    int cap_D = 64, cap_X = 0;
 
     // expansions
     DBuf alpha, beta;

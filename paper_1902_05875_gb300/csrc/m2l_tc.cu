@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
     float2 *tab = (float2 *)smem;
     const int tb = a.tab_base + tbl;
     const uint64_t key = a.table_key[tb];
-    const int kind = (int)(key >> 62);
-    const int lev = (int)((key >> 57) & 31);
+    const int kind = key_kind(key);
+    const int lev = key_level(key);
     const double h = a.side / (double)(1 << lev);
     const float *cf = kind == 0 ? a.cfB : a.cfA;
     {

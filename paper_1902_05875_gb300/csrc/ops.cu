@@ -255,13 +255,7 @@ __global__ void k_l2l(int off, int cnt, TreeArrays T, Cube cb, int p, int np, co
 }
 
 // ------------------------------------------------------------------ M2L keys
-// key layout (64 bits): kind(2) level(5) layer(4) dx+3(3) dy+3(3) w(22)
-//   kind 0 = B (w = dz + 3), kind 1 = A (w = iz_t + iz_s)
-__device__ __forceinline__ uint64_t m2l_key(int kind, int l, int lay, int dx, int dy, int w) {
-    return ((uint64_t)kind << 62) | ((uint64_t)l << 57) | ((uint64_t)lay << 53) |
-           ((uint64_t)(dx + 3) << 50) | ((uint64_t)(dy + 3) << 47) | (uint64_t)w;
-}
-
+// (layout and field accessors in ops_common.cuh)
 __global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pair_t,
                             const int *__restrict__ v_src, const int *__restrict__ has_A,
                             uint64_t *__restrict__ keys, int *__restrict__ vals, int *flags) {
@@ -270,16 +264,17 @@ __global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pa
     int t = pair_t[e], s = v_src[e];
     int l = T.level[t], lay = T.layer[t], lays = T.layer[s];
     int dx = T.ix[t] - T.ix[s], dy = T.iy[t] - T.iy[s], dz = T.iz[t] - T.iz[s];
-    // a V pair lies within the parent's neighbourhood: offsets fit the keys' 3-bit fields
-    if (abs(dx) > 3 || abs(dy) > 3 || (lay == lays && abs(dz) > 3)) {
+    // offsets must fit the keys' fields (a V pair lies within the neighbourhood of
+    // its parent's colleagues; wavenumber-coarse levels widen that neighbourhood)
+    if (abs(dx) > KEY_OFF || abs(dy) > KEY_OFF || (lay == lays && abs(dz) > KEY_OFF)) {
         atomicOr(flags, FLAG_CHECK);
         keys[2 * e] = keys[2 * e + 1] = ~0ULL;
     } else if (lay != lays) {          // cross-layer component: one table per (z_t, z_s)
         keys[2 * e] = xkey(l, lay, lays, dx, dy, T.iz[t], T.iz[s]);
         keys[2 * e + 1] = ~0ULL;
     } else {
-        keys[2 * e] = m2l_key(0, l, lay, dx, dy, dz + 3);
-        keys[2 * e + 1] = has_A[lay] ? m2l_key(1, l, lay, dx, dy, T.iz[t] + T.iz[s]) : ~0ULL;
+        keys[2 * e] = m2l_key(0, l, lay, dx, dy, (uint64_t)(dz + KEY_OFF));
+        keys[2 * e + 1] = has_A[lay] ? m2l_key(1, l, lay, dx, dy, (uint64_t)(T.iz[t] + T.iz[s])) : ~0ULL;
     }
     vals[2 * e] = (int)(2 * e);
     vals[2 * e + 1] = (int)(2 * e + 1);
@@ -321,14 +316,13 @@ __global__ void k_table_rep(int ntab, const uint64_t *__restrict__ keys, int *__
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ntab) return;
     const uint64_t key = keys[i];
-    const int dx = (int)((key >> 50) & 7) - 3, dy = (int)((key >> 47) & 7) - 3;
-    const uint64_t base = key & ~(63ULL << 47);
+    const int dx = key_dx(key), dy = key_dy(key);
     int rep = i, rdx = dx, rdy = dy;
     for (int v = 1; v < 8; ++v) {
         int a = (v & 4) ? dy : dx, b = (v & 4) ? dx : dy;
         if (v & 1) a = -a;
         if (v & 2) b = -b;
-        const uint64_t kv = base | ((uint64_t)(a + 3) << 50) | ((uint64_t)(b + 3) << 47);
+        const uint64_t kv = key_with_dxdy(key, a, b);
         int lo = 0, hi = rep;   // keys are sorted: search the ones before the current representative
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -416,18 +410,18 @@ __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__r
     for (int g = threadIdx.x; g < np2; g += blockDim.x) acc[g] = mkc(0, 0);
     __syncthreads();
     uint64_t key = table_key[tb];
-    int kind = (int)(key >> 62);
-    int l = (int)((key >> 57) & 31);
-    int lay = (int)((key >> 53) & 15);
-    int dx = (int)((key >> 50) & 7) - 3;
-    int dy = (int)((key >> 47) & 7) - 3;
-    int w = (int)(key & ((1ULL << 47) - 1));
+    int kind = key_kind(key);
+    int l = key_level(key);
+    int lay = key_layer(key);
+    int dx = key_dx(key);
+    int dy = key_dy(key);
+    int w = (int)key_w(key);
     double h = box_h(cb.side, l);
     double X = (double)dx * h, Y = (double)dy * h;
     cplx k = im.k[lay];
     int tf = im.lt_first[lay], tc = im.lt_count[lay];
     if (kind == 0) {
-        double dz = (double)(w - 3) * h;
+        double dz = (double)(w - KEY_OFF) * h;
         recur_accumulate(P2, cmax, k, X, Y, mkc(dz, 0), mkc(1, 0), false, a, b, acc);
         for (int ti = tf; ti < tf + tc; ++ti) {
             DevTerm t = im.terms[ti];
@@ -470,7 +464,7 @@ __global__ void k_m2l_fp64(int nchunks, const int *__restrict__ chunk_start,
     int tb = chunk_table[c];
     int cnt = chunk_cnt[c];
     int st = chunk_start[c];
-    int kind = (int)(table_key[tb] >> 62);
+    int kind = key_kind(table_key[tb]);
     const double *coef = kind == 0 ? cB : cA;
     for (int g = threadIdx.x; g < np2; g += blockDim.x) tab[g] = tables[(int64_t)tb * np2 + g];
     for (int q = 0; q < cnt; ++q) {

@@ -89,22 +89,43 @@ __host__ __device__ inline int slice_off(int p, int k3p) {
     return o;
 }
 
-// Cross-layer M2L key (kind 2): level(5) lt(4) dx+3(3) dy+3(3) ls(4) iz_t(20) iz_s(20).
-// Same-layer keys (kinds 0 and 1) sort before it.
+// M2L keys (64 bits): kind(2) level(5) target layer(3) dx+15(5) dy+15(5) w(44).
+//   kind 0 = B (same layer; w = dz + 15),
+//   kind 1 = A (same layer; w = iz_t + iz_s),
+//   kind 2 = cross layer (w = source layer(3) iz_t(20) iz_s(20)); sorts last.
+// dx, dy, dz are the target-minus-source box offsets of a V pair.  With
+// wavenumber admissibility the first translating level can pair boxes up to
+// 2^level - 1 apart, so the offset fields hold |d| <= KEY_OFF.
+#define KEY_OFF 15
+__host__ __device__ inline uint64_t m2l_key(int kind, int l, int lay, int dx, int dy, uint64_t w) {
+    return ((uint64_t)kind << 62) | ((uint64_t)l << 57) | ((uint64_t)lay << 54) |
+           ((uint64_t)(dx + KEY_OFF) << 49) | ((uint64_t)(dy + KEY_OFF) << 44) | w;
+}
+__host__ __device__ inline int key_kind(uint64_t k) { return (int)(k >> 62); }
+__host__ __device__ inline int key_level(uint64_t k) { return (int)((k >> 57) & 31); }
+__host__ __device__ inline int key_layer(uint64_t k) { return (int)((k >> 54) & 7); }
+__host__ __device__ inline int key_dx(uint64_t k) { return (int)((k >> 49) & 31) - KEY_OFF; }
+__host__ __device__ inline int key_dy(uint64_t k) { return (int)((k >> 44) & 31) - KEY_OFF; }
+__host__ __device__ inline uint64_t key_w(uint64_t k) { return k & ((1ULL << 44) - 1); }
+// the same key with other horizontal offsets
+__host__ __device__ inline uint64_t key_with_dxdy(uint64_t k, int dx, int dy) {
+    return (k & ~(1023ULL << 44)) | ((uint64_t)(dx + KEY_OFF) << 49) | ((uint64_t)(dy + KEY_OFF) << 44);
+}
+
+// Cross-layer M2L key: kind 2, w = ls(3) iz_t(20) iz_s(20).
 __host__ __device__ inline uint64_t xkey(int l, int lt, int ls, int dx, int dy, int izt, int izs) {
-    return (2ULL << 62) | ((uint64_t)l << 57) | ((uint64_t)lt << 53) | ((uint64_t)(dx + 3) << 50) |
-           ((uint64_t)(dy + 3) << 47) | ((uint64_t)ls << 40) | ((uint64_t)izt << 20) | (uint64_t)izs;
+    return m2l_key(2, l, lt, dx, dy, ((uint64_t)ls << 40) | ((uint64_t)izt << 20) | (uint64_t)izs);
 }
 struct XKey {
     int level, lt, ls, dx, dy, izt, izs;
 };
 __host__ __device__ inline XKey xkey_decode(uint64_t k) {
     XKey x;
-    x.level = (int)((k >> 57) & 31);
-    x.lt = (int)((k >> 53) & 15);
-    x.dx = (int)((k >> 50) & 7) - 3;
-    x.dy = (int)((k >> 47) & 7) - 3;
-    x.ls = (int)((k >> 40) & 15);
+    x.level = key_level(k);
+    x.lt = key_layer(k);
+    x.dx = key_dx(k);
+    x.dy = key_dy(k);
+    x.ls = (int)((k >> 40) & 7);
     x.izt = (int)((k >> 20) & 0xFFFFF);
     x.izs = (int)(k & 0xFFFFF);
     return x;

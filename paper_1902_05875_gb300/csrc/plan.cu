@@ -144,6 +144,10 @@ extern "C" int tefmm_default_options(tefmm_options *opt) {
         opt->zext[2 * l] = NAN;
         opt->zext[2 * l + 1] = NAN;
     }
+    opt->kh_max = 3.5;
+    opt->algorithm = TEFMM_ALG_RECURRENCE;
+    opt->split = TEFMM_SPLIT_TF32X3;
+    opt->scale_output = 0;
     return TEFMM_OK;
 }
 
@@ -161,8 +165,11 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
     else tefmm_default_options(&o);
     if (o.p < 1 || o.p > 12 || o.leaf_cap < 0 || o.max_level < 1 || o.max_level > TEFMM_NBITS ||
         o.n_images < 0 || o.n_images > TEFMM_MAX_IMG || o.n_samples < 8 || o.n_samples > 127 ||
-        !(o.T1 > 0) || (o.precision != TEFMM_FP64 && o.precision != TEFMM_MIXED))
+        !(o.T1 > 0) || (o.precision != TEFMM_FP64 && o.precision != TEFMM_MIXED) ||
+        isnan(o.kh_max) || (o.scale_output != 0 && o.scale_output != 1) ||
+        (o.algorithm != TEFMM_ALG_RECURRENCE && o.algorithm != TEFMM_ALG_TABLES))
         return TEFMM_ERR_INVALID_ARG;
+    if (o.algorithm != TEFMM_ALG_RECURRENCE || o.split != TEFMM_SPLIT_TF32X3) return TEFMM_ERR_NOT_IMPLEMENTED;
     // default particle ranges: the whole layer (top/bottom: one unit beyond the interface)
     for (int l = 0; l < n_layers; ++l) {
         double top = (l == 0) ? (n_layers > 1 ? interfaces[0] + 1.0 : 1.0) : interfaces[l - 1];
@@ -188,7 +195,10 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
     }
     P->nL = n_layers;
     for (int m = 0; m < n_layers - 1; ++m) P->d[m] = interfaces[m];
-    for (int l = 0; l < n_layers; ++l) P->k[l] = mkc(k_re[l], k_im[l]);
+    for (int l = 0; l < n_layers; ++l) {
+        P->k[l] = mkc(k_re[l], k_im[l]);
+        P->kmax = fmax(P->kmax, hypot(k_re[l], k_im[l]));
+    }
     P->opt = o;
     P->p = o.p;
     cudaGetDevice(&P->device);

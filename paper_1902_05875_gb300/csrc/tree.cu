@@ -19,6 +19,10 @@
 //   V(t): children of C(parent) boxes that are not adjacent to t.
 #include <cub/cub.cuh>
 
+#include <string.h>
+
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace {
@@ -322,6 +326,22 @@ struct NodeView {
     const int *layer, *level, *ix, *iy, *iz, *parent, *cfirst, *nchild, *s0, *s1, *t0, *t1, *split;
 };
 
+// Per-level rows of the C (colleague) and V (M2L) work lists: node t of level l
+// owns cap[l] entries at base[l] + (t - off[l]) * cap[l].  Coarse levels of the
+// wavenumber rule pair every split box of a level, so their rows (and the V rows
+// of the level below) are as wide as the level; the others stay neighbourhood-sized.
+struct ListLayout {
+    int off[TEFMM_NBITS + 2];
+    int ccap[TEFMM_NBITS + 1], vcap[TEFMM_NBITS + 1];
+    long long cbase[TEFMM_NBITS + 1], vbase[TEFMM_NBITS + 1];
+};
+__device__ __forceinline__ long long c_row(const ListLayout &Ly, int l, int t) {
+    return Ly.cbase[l] + (long long)(t - Ly.off[l]) * Ly.ccap[l];
+}
+__device__ __forceinline__ long long v_row(const ListLayout &Ly, int l, int t) {
+    return Ly.vbase[l] + (long long)(t - Ly.off[l]) * Ly.vcap[l];
+}
+
 __device__ __forceinline__ bool adjacent(const NodeView &N, int a, int b) {
     int la = N.level[a], lb = N.level[b];
     int ax = N.ix[a], ay = N.iy[a], az = N.iz[a];
@@ -356,14 +376,14 @@ __device__ __forceinline__ void isort(int *a, int n) {
 }
 
 // level 0: C(root_t) = every root that holds sources
-__global__ void k_lists_root(int nroots, NodeView N, int *C_list, int *C_cnt, int capC, int *D_cnt,
+__global__ void k_lists_root(int nroots, NodeView N, ListLayout Ly, int *C_list, int *C_cnt, int *D_cnt,
                              int *X_cnt, int *V_cnt) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nroots) return;
     int n = 0;
     if (N.t1[t] > N.t0[t]) {
         for (int s = 0; s < nroots; ++s)
-            if (N.s1[s] > N.s0[s]) C_list[(int64_t)t * capC + n++] = s;
+            if (N.s1[s] > N.s0[s]) C_list[c_row(Ly, 0, t) + n++] = s;
     }
     C_cnt[t] = n;
     D_cnt[t] = 0;
@@ -379,28 +399,37 @@ __device__ __forceinline__ bool cross_colleague(const NodeView &N, int t, int c,
     return abs(N.ix[t] - N.ix[c]) <= 1 && abs(N.iy[t] - N.iy[c]) <= 1;
 }
 
-__global__ void k_lists_level(int off, int cnt, NodeView N, int *C_list, int *C_cnt, int capC,
+// Wavenumber admissibility: on a level whose Taylor expansions would span
+// k_max h > kh_max (kcoarse != 0), two split boxes are not translated; their
+// children are paired instead, whatever their distance.
+__device__ __forceinline__ bool coarse_colleague(const NodeView &N, int t, int c, int kcoarse) {
+    return kcoarse && N.split[t] && N.split[c];
+}
+
+__global__ void k_lists_level(int off, int cnt, int l, NodeView N, ListLayout Ly, int *C_list, int *C_cnt,
                               int *D_list, int *D_cnt, int capD, int *X_list, int *X_cnt, int capX,
-                              int *V_list, int *V_cnt, int capV, int *flags, int coarse) {
+                              int *V_list, int *V_cnt, int *flags, int coarse, int kcoarse) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cnt) return;
     int t = off + j;
     int nc = 0, nd = 0, nx = 0, nv = 0;
     if (N.t1[t] > N.t0[t]) {
+        const int capC = Ly.ccap[l], capV = Ly.vcap[l];
         int P = N.parent[t];
-        int *Cl = C_list + (int64_t)t * capC;
+        int *Cl = C_list + c_row(Ly, l, t);
         int *Dl = D_list + (int64_t)t * capD;
         int *Xl = X_list + (int64_t)t * capX;
-        int *Vl = V_list + (int64_t)t * capV;
+        int *Vl = V_list + v_row(Ly, l, t);
         bool ovf = false;
-        const int *CP = C_list + (int64_t)P * capC;
+        const int *CP = C_list + c_row(Ly, l - 1, P);
         for (int a = 0; a < C_cnt[P]; ++a) {
             int s = CP[a];
             if (N.split[s]) {
                 int c0 = N.cfirst[s], c1 = c0 + N.nchild[s];
                 for (int c = c0; c < c1; ++c) {
                     if (N.s1[c] <= N.s0[c]) continue;
-                    if (adjacent(N, t, c) || cross_colleague(N, t, c, coarse)) {
+                    if (adjacent(N, t, c) || cross_colleague(N, t, c, coarse) ||
+                        coarse_colleague(N, t, c, kcoarse)) {
                         if (nc < capC) Cl[nc++] = c; else ovf = true;
                     } else {
                         if (nv < capV) Vl[nv++] = c; else ovf = true;
@@ -438,7 +467,7 @@ __global__ void k_lists_level(int off, int cnt, NodeView N, int *C_list, int *C_
 // there) and X of t and of every ancestor.  Two passes: with out == nullptr
 // only the count is written; otherwise the list is written at out[ptr[t]..]
 // and sorted.
-__global__ void k_near(int off, int cnt, NodeView N, const int *C_list, const int *C_cnt, int capC,
+__global__ void k_near(int off, int cnt, int l, NodeView N, ListLayout Ly, const int *C_list, const int *C_cnt,
                        const int *D_list, const int *D_cnt, int capD, const int *X_list,
                        const int *X_cnt, int capX, const int *ptr, int *out, int *near_cnt,
                        int *flags) {
@@ -451,7 +480,7 @@ __global__ void k_near(int off, int cnt, NodeView N, const int *C_list, const in
         bool ovf = false;
         int stack[160];
         int sp = 0;
-        const int *Cl = C_list + (int64_t)t * capC;
+        const int *Cl = C_list + c_row(Ly, l, t);
         for (int a = 0; a < C_cnt[t]; ++a) {
             int s = Cl[a];
             if (!N.split[s]) {
@@ -492,15 +521,17 @@ __global__ void k_near(int off, int cnt, NodeView N, const int *C_list, const in
     if (!out) near_cnt[t] = n;
 }
 
-__global__ void k_csr_fill(int n_nodes, const int *__restrict__ cnt, const int *__restrict__ tmp,
-                           int cap, const int *__restrict__ ptr, int *__restrict__ out,
-                           int *__restrict__ out_t) {
-    int t = blockIdx.x;
-    if (t >= n_nodes) return;
-    int c = cnt[t], base = ptr[t];
+__global__ void k_csr_fill(int off, int cnt, int l, ListLayout Ly, const int *__restrict__ vcnt,
+                           const int *__restrict__ tmp, const int *__restrict__ ptr,
+                           int *__restrict__ out, int *__restrict__ out_t) {
+    int j = blockIdx.x;
+    if (j >= cnt) return;
+    int t = off + j;
+    int c = vcnt[t], base = ptr[t];
+    const int *row = tmp + v_row(Ly, l, t);
     for (int a = threadIdx.x; a < c; a += blockDim.x) {
-        out[base + a] = tmp[(int64_t)t * cap + a];
-        if (out_t) out_t[base + a] = t;
+        out[base + a] = row[a];
+        out_t[base + a] = t;
     }
 }
 
@@ -751,44 +782,66 @@ int tree_build(tefmm_plan_s *P, const double *sx, const double *sy, const double
     return TEFMM_OK;
 }
 
+// level l is coarse for the wavenumber rule when k_max h_l > kh_max (kh_max > 0)
+static bool kh_coarse(const tefmm_plan_s *P, int l) {
+    return P->opt.kh_max > 0.0 && P->kmax * (P->side / (double)(1 << l)) > P->opt.kh_max;
+}
+
 int lists_build(tefmm_plan_s *P, cudaStream_t st) {
     const int nn = P->n_nodes;
+    const int NL = P->n_levels;
     // stacked cross-layer colleagues (at most 128 per other layer) and their
     // children in the V lists; overflow is reported (LIST_OVERFLOW)
     const bool xrule = P->nL > 1 && P->HX < INFINITY;
-    P->cap_C = 27 * P->nL + (xrule ? 128 * (P->nL - 1) : 0);
-    P->cap_V = 189 * P->nL + (xrule ? 1024 * (P->nL - 1) : 0);
+    const int capC_near = 27 * P->nL + (xrule ? 128 * (P->nL - 1) : 0);
     P->cap_D = 128;
     P->cap_X = 27 * P->nL + 128;
-    TRY(dbuf_ensure(P->C_list, (size_t)nn * P->cap_C * 4));
+    ListLayout Ly;
+    memset(&Ly, 0, sizeof(Ly));
+    long long ctot = 0, vtot = 0;
+    for (int l = 0; l <= NL; ++l) Ly.off[l] = P->level_off[l];
+    for (int l = 0; l < NL; ++l) {
+        const int cnt = P->level_off[l + 1] - P->level_off[l];
+        Ly.ccap[l] = (l == 0 || kh_coarse(P, l)) ? cnt : std::min(cnt, capC_near);
+        Ly.vcap[l] = l == 0 ? 0 : std::min(cnt, 8 * Ly.ccap[l - 1]);
+        Ly.cbase[l] = ctot;
+        Ly.vbase[l] = vtot;
+        ctot += (long long)cnt * Ly.ccap[l];
+        vtot += (long long)cnt * Ly.vcap[l];
+    }
+    TRY(dbuf_ensure(P->C_list, (size_t)ctot * 4));
     TRY(dbuf_ensure(P->C_cnt, (size_t)nn * 4));
     TRY(dbuf_ensure(P->D_list, (size_t)nn * P->cap_D * 4));
     TRY(dbuf_ensure(P->D_cnt, (size_t)nn * 4));
     TRY(dbuf_ensure(P->X_list, (size_t)nn * P->cap_X * 4));
     TRY(dbuf_ensure(P->X_cnt, (size_t)nn * 4));
-    TRY(dbuf_ensure(P->V_tmp, (size_t)nn * P->cap_V * 4));
+    TRY(dbuf_ensure(P->V_tmp, (size_t)vtot * 4));
     TRY(dbuf_ensure(P->V_cnt, (size_t)(nn + 1) * 4));
     TRY(dbuf_ensure(P->near_cnt, (size_t)(nn + 1) * 4));
     CUDA_TRY(cudaMemsetAsync(P->V_cnt.p, 0, (size_t)(nn + 1) * 4, st));
     CUDA_TRY(cudaMemsetAsync(P->near_cnt.p, 0, (size_t)(nn + 1) * 4, st));
+    // the first translating level below a coarse level l pairs boxes up to
+    // 2^(l+1) - 1 apart; the M2L keys hold offsets up to 15
+    for (int l = 1; l + 1 < NL; ++l)
+        if (kh_coarse(P, l) && (1 << (l + 1)) - 1 > 15) return TEFMM_ERR_NOT_IMPLEMENTED;
     NodeView N = node_view(P);
     int nroots = P->level_off[1];
-    k_lists_root<<<1, 32, 0, st>>>(nroots, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C,
-                                   dp<int>(P->D_cnt), dp<int>(P->X_cnt), dp<int>(P->V_cnt));
+    k_lists_root<<<1, 32, 0, st>>>(nroots, N, Ly, dp<int>(P->C_list), dp<int>(P->C_cnt), dp<int>(P->D_cnt),
+                                   dp<int>(P->X_cnt), dp<int>(P->V_cnt));
     P->launches++;
-    for (int l = 1; l < P->n_levels; ++l) {
+    for (int l = 1; l < NL; ++l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
         k_lists_level<<<grid_for(cnt, 128), 128, 0, st>>>(
-            off, cnt, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C, dp<int>(P->D_list),
+            off, cnt, l, N, Ly, dp<int>(P->C_list), dp<int>(P->C_cnt), dp<int>(P->D_list),
             dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X,
-            dp<int>(P->V_tmp), dp<int>(P->V_cnt), P->cap_V, dp<int>(P->flags),
-            (P->nL > 1 && P->side / (double)(1 << l) > P->HX) ? 1 : 0);
+            dp<int>(P->V_tmp), dp<int>(P->V_cnt), dp<int>(P->flags),
+            (P->nL > 1 && P->side / (double)(1 << l) > P->HX) ? 1 : 0, kh_coarse(P, l) ? 1 : 0);
         P->launches++;
     }
-    for (int l = 0; l < P->n_levels; ++l) {
+    for (int l = 0; l < NL; ++l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
         k_near<<<grid_for(cnt, 64), 64, 0, st>>>(
-            off, cnt, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C, dp<int>(P->D_list),
+            off, cnt, l, N, Ly, dp<int>(P->C_list), dp<int>(P->C_cnt), dp<int>(P->D_list),
             dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X, nullptr,
             nullptr, dp<int>(P->near_cnt), dp<int>(P->flags));
         P->launches++;
@@ -807,18 +860,22 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
     TRY(dbuf_ensure(P->v_src, (size_t)(P->n_v + 1) * 4));
     TRY(dbuf_ensure(P->pair_t, (size_t)(P->n_v + 1) * 4));
     TRY(dbuf_ensure(P->near_src, (size_t)(P->n_near + 1) * 4));
-    for (int l = 0; l < P->n_levels; ++l) {
+    for (int l = 0; l < NL; ++l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
         k_near<<<grid_for(cnt, 64), 64, 0, st>>>(
-            off, cnt, N, dp<int>(P->C_list), dp<int>(P->C_cnt), P->cap_C, dp<int>(P->D_list),
+            off, cnt, l, N, Ly, dp<int>(P->C_list), dp<int>(P->C_cnt), dp<int>(P->D_list),
             dp<int>(P->D_cnt), P->cap_D, dp<int>(P->X_list), dp<int>(P->X_cnt), P->cap_X,
             dp<int>(P->near_ptr), dp<int>(P->near_src), nullptr, dp<int>(P->flags));
         P->launches++;
     }
-    if (nn > 0) {
-        k_csr_fill<<<nn, 64, 0, st>>>(nn, dp<int>(P->V_cnt), dp<int>(P->V_tmp), P->cap_V,
-                                      dp<int>(P->v_ptr), dp<int>(P->v_src), dp<int>(P->pair_t));
+    for (int l = 1; l < NL; ++l) {
+        int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
+        if (cnt == 0) continue;
+        k_csr_fill<<<cnt, 64, 0, st>>>(off, cnt, l, Ly, dp<int>(P->V_cnt), dp<int>(P->V_tmp),
+                                       dp<int>(P->v_ptr), dp<int>(P->v_src), dp<int>(P->pair_t));
         P->launches++;
+    }
+    if (nn > 0) {
         k_layer_mismatch<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_layer),
                                                             dp<int>(P->near_ptr),
                                                             dp<int>(P->near_src), dp<int>(P->flags));

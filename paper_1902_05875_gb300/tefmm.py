@@ -25,7 +25,9 @@ MIXED = 1
 class Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("max_level", ctypes.c_int),
                 ("precision", ctypes.c_int), ("n_images", ctypes.c_int), ("n_samples", ctypes.c_int),
-                ("T1", ctypes.c_double), ("T0", ctypes.c_double), ("zext", ctypes.c_double * 32)]
+                ("T1", ctypes.c_double), ("T0", ctypes.c_double), ("zext", ctypes.c_double * 32),
+                ("kh_max", ctypes.c_double), ("algorithm", ctypes.c_int), ("split", ctypes.c_int),
+                ("scale_output", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -48,7 +50,7 @@ EXPORTED = [
     "tefmm_eval_host", "tefmm_get_stats", "tefmm_status_string", "tefmm_plan_image_counts",
     "tefmm_plan_get_images", "tefmm_plan_set_images", "tefmm_export_tree", "tefmm_export_lists",
     "tefmm_export_expansions", "tefmm_fit_images_noalloc", "tefmm_plan_cross_images",
-    "tefmm_eval_batched", "tefmm_set_points", "tefmm_apply",
+    "tefmm_eval_batched", "tefmm_set_points", "tefmm_apply", "tefmm_plan_set_cross_images",
 ]
 
 _lib = None
@@ -90,6 +92,7 @@ def load(build_if_needed=True):
     lib.tefmm_export_tree.argtypes = [P, I, I64, I64] + [I] * 12
     lib.tefmm_export_lists.argtypes = [P, I64, I64, I, I, I, I]
     lib.tefmm_export_expansions.argtypes = [P, D, D]
+    lib.tefmm_plan_set_cross_images.argtypes = [P, ctypes.c_int, I, I, D, D]
     lib.tefmm_eval_batched.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                        ctypes.POINTER(BatchItem), ctypes.c_int, P, I]
     lib.tefmm_fit_images_noalloc.argtypes = [ctypes.c_int, D, D, D, ctypes.POINTER(Options), P,
@@ -164,7 +167,8 @@ class Plan:
     """A layered medium plus its DCIM images (``tefmm_plan_create``)."""
 
     def __init__(self, interfaces, k, p=6, leaf_cap=64, max_level=20, precision=FP64,
-                 n_images=8, n_samples=101, T1=10.0, T0=0.0, zext=None, stream=None):
+                 n_images=8, n_samples=101, T1=10.0, T0=0.0, zext=None, kh_max=3.5,
+                 scale_output=False, stream=None):
         lib = load()
         self.lib = lib
         k = np.asarray(k, dtype=complex).reshape(-1)
@@ -177,6 +181,8 @@ class Plan:
         opt.precision = int(precision)
         opt.n_images, opt.n_samples = int(n_images), int(n_samples)
         opt.T1, opt.T0 = float(T1), float(T0)
+        opt.kh_max = 0.0 if kh_max is None else float(kh_max)
+        opt.scale_output = 1 if scale_output else 0
         if zext is not None:
             for l, (a, b) in enumerate(zext):
                 opt.zext[2 * l] = float(a)
@@ -369,6 +375,28 @@ class Plan:
             out[(lt, ls, 'up' if d == 0 else 'down', lev, izs, k3p)] = (
                 A[2 * j] + 1j * A[2 * j + 1], Z[2 * j] + 1j * Z[2 * j + 1])
         return out
+
+    def set_cross_images(self, fits):
+        """``tefmm_plan_set_cross_images``: fits {(l, l', 'up'|'down', level, iz_s, k3'): (A, Z)}
+        (the layout of cross_images()) replace or join the plan's cached cross-layer fits."""
+        items = list(fits.items())
+        m = len(items)
+        keys = np.zeros(6 * max(m, 1), np.int32)
+        cnt = np.zeros(max(m, 1), np.int32)
+        A = np.zeros(2 * 32 * max(m, 1), np.float64)
+        Z = np.zeros(2 * 32 * max(m, 1), np.float64)
+        for i, ((lt, ls, d, lev, izs, k3p), (a, z)) in enumerate(items):
+            a = np.asarray(a, complex)
+            z = np.asarray(z, complex)
+            if len(a) != len(z) or len(a) > 32:
+                raise ValueError("at most 32 images per fit, A and Z of equal length")
+            keys[6 * i:6 * i + 6] = (lt, ls, 0 if d == 'up' else 1, lev, izs, k3p)
+            cnt[i] = len(a)
+            j = 32 * i + np.arange(len(a))
+            A[2 * j], A[2 * j + 1] = a.real, a.imag
+            Z[2 * j], Z[2 * j + 1] = z.real, z.imag
+        _check(self.lib.tefmm_plan_set_cross_images(self.h, m, _iptr(keys), _iptr(cnt), _dptr(A), _dptr(Z)),
+               "set_cross_images")
 
     def export_expansions(self):
         n = self.stats()["n_nodes"]

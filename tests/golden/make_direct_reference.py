@@ -1,0 +1,49 @@
+"""Writes the FP64 direct-sum reference of the 2M three-slab workload at 1000
+sampled targets (``direct_three_layer_slabs_n2M_1000.txt``).
+
+The values come from the oracle alone (``oracle.direct``: same-layer part by
+the DCIM images of ``oracle.dcim``, cross-layer part by one DCIM fit per
+target); the workload is the seeded input generator's.  The sample is 1000
+targets drawn without replacement by numpy ``default_rng(1)``.  Each output
+line is ``index re im`` (17 significant digits).  Run from the repository root:
+
+    python tests/golden/make_direct_reference.py [n_targets]
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "direct_three_layer_slabs_n2M_{n}.txt")
+
+
+def main(n=1000):
+    from paper_1902_05875_gb300 import workloads
+    from oracle.medium import Medium
+    from oracle.dcim import ImageTable
+    from oracle.direct import direct_sum, cross_sum_by_reciprocity
+    w = workloads.cfg_mixed_2m()
+    idx = np.random.default_rng(1).choice(len(w.src), n, replace=False)
+    med = Medium(w.interfaces, w.k)
+    img = ImageTable(med, w.zext, n_images=w.n_images)
+    tgt = w.src[idx]
+    t0 = time.perf_counter()
+    phi = direct_sum(med, img, w.src, w.q, tgt)
+    phi = phi + cross_sum_by_reciprocity(med, w.zext, w.src, w.q, tgt, n_images=w.n_images)
+    dt = time.perf_counter() - t0
+    with open(OUT.format(n=n), "w") as f:
+        f.write(f"# FP64 direct sum (oracle) of {w.name} at {n} targets, default_rng(1); "
+                f"index re im; {dt:.0f} s on {os.cpu_count()} cores\n")
+        for i, v in zip(idx, phi):
+            f.write(f"{int(i)} {v.real:.17g} {v.imag:.17g}\n")
+    print(OUT.format(n=n), f"{dt:.1f} s")
+
+
+if __name__ == "__main__":
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 1000)
