@@ -146,14 +146,14 @@ def direct_at(w, tgt_idx):
     (phi, seconds)."""
     from oracle.medium import Medium
     from oracle.dcim import ImageTable
-    from oracle.direct import direct_sum, cross_sum_by_reciprocity
+    from oracle.direct import direct_sum, cross_sum
     med = Medium(w.interfaces, w.k)
     img = ImageTable(med, w.zext, n_images=w.n_images)
     tgt = w.src[tgt_idx]
     t0 = time.perf_counter()
     phi = direct_sum(med, img, w.src, w.q, tgt)
     if med.n_layers > 1:
-        phi = phi + cross_sum_by_reciprocity(med, w.zext, w.src, w.q, tgt, n_images=w.n_images)
+        phi = phi + cross_sum(med, w.zext, w.src, w.q, tgt, n_images=w.n_images)
     return phi, time.perf_counter() - t0
 
 

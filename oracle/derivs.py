@@ -57,39 +57,48 @@ def taylor_phi(X, Y, W, k, P):
     R2 = X * X + Y * Y + W * W
     R = np.sqrt(R2)
     k = complex(k)
+    T = len(multi_indices(P))
+    # coefficient index first (row T is a zero row standing for a coefficient
+    # with a negative index); order n needs orders n-1 and n-2 only, so all
+    # coefficients of one order are computed together
+    a = np.zeros((T + 1,) + X.shape, dtype=complex)
+    b = np.zeros((T + 1,) + X.shape, dtype=complex)
+    e = np.exp(1j * k * R)
+    a[0] = e / R
+    b[0] = e
+    for n in range(1, P + 1):
+        ts, J1, J2 = _order_links(P, n)
+        sa1 = x[0][None] * a[J1[0]] + x[1][None] * a[J1[1]] + x[2][None] * a[J1[2]]
+        sa2 = a[J2[0]] + a[J2[1]] + a[J2[2]]
+        sbr = x[0][None] * b[J1[0]] + x[1][None] * b[J1[1]] + x[2][None] * b[J1[2]] + \
+            b[J2[0]] + b[J2[1]] + b[J2[2]]
+        b[ts] = 1j * k * (sa1 + sa2) / n
+        a[ts] = (1j * k * sbr - (2 * n - 1) * sa1 - (n - 1) * sa2) / (n * R2[None])
+    return np.moveaxis(a[:T], 0, -1)
+
+
+@lru_cache(maxsize=None)
+def _order_links(P, n):
+    """Indices of the order-n multi-indices k (in the order-P list) and, per
+    axis i, of k - e_i (J1[i]) and k - 2 e_i (J2[i]); T (a zero row) where
+    that index is negative."""
     mi = multi_indices(P)
     im = index_map(P)
     T = len(mi)
-    a = np.zeros(X.shape + (T,), dtype=complex)
-    b = np.zeros(X.shape + (T,), dtype=complex)
-    e = np.exp(1j * k * R)
-    a[..., 0] = e / R
-    b[..., 0] = e
-    for t in range(1, T):
-        kk = mi[t]
-        n = int(kk.sum())
-        sb = 0
-        sa1 = 0
-        sa2 = 0
-        sbr = 0
+    ts = np.nonzero(mi.sum(1) == n)[0]
+    J1 = np.full((3, len(ts)), T, dtype=np.int64)
+    J2 = np.full((3, len(ts)), T, dtype=np.int64)
+    for c, t in enumerate(ts):
         for i in range(3):
-            if kk[i] >= 1:
-                km = kk.copy()
+            if mi[t][i] >= 1:
+                km = mi[t].copy()
                 km[i] -= 1
-                j = im[tuple(int(v) for v in km)]
-                sb = sb + x[i] * a[..., j]
-                sa1 = sa1 + x[i] * a[..., j]
-                sbr = sbr + x[i] * b[..., j]
-            if kk[i] >= 2:
-                km = kk.copy()
+                J1[i, c] = im[tuple(int(v) for v in km)]
+            if mi[t][i] >= 2:
+                km = mi[t].copy()
                 km[i] -= 2
-                j = im[tuple(int(v) for v in km)]
-                sb = sb + a[..., j]
-                sa2 = sa2 + a[..., j]
-                sbr = sbr + b[..., j]
-        b[..., t] = 1j * k * sb / n
-        a[..., t] = (1j * k * sbr - (2 * n - 1) * sa1 - (n - 1) * sa2) / (n * R2)
-    return a
+                J2[i, c] = im[tuple(int(v) for v in km)]
+    return ts, J1, J2
 
 
 def taylor_h0(X, Y, W, k, P):

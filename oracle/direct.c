@@ -114,3 +114,58 @@ void oracle_cross_sum(int64_t ns, const double *sx, const double *sy, const doub
         phi[2 * i + 1] = cimag(acc);
     }
 }
+
+/*
+ * Cross-layer part of Phi with the images in the TARGET layer l (Sec. 3.2:
+ * the source-box z'-expansion of the density, eq. ``layermediumdensity``, and
+ * the image form of each z'-derivative, eq. ``closedformgreen``).  Sources are
+ * grouped in narrow z'-bins; a source at z' = zc_b + delta (bin b) contributes
+ *   q sum_{k3'=0..K} delta^{k3'} sum_m A_m h0(k_l sqrt(rho^2 + (W(z) - W_min - Z_m)^2)),
+ * with the fit of Theta^{k3'} at zc_b, W(z) = z - d_l (up) or d_{l-1} - z (down).
+ * Fit of (target layer l, bin b, part, k3') is
+ *   f = ((l * nbin + b) * 2 + part) * (K + 1) + k3',
+ * its images img_first[f] .. img_first[f+1]; wmin[2 l + part] is W_min.
+ * Only the layer pairs with use[l * nl + l'] != 0 are summed here.
+ */
+void oracle_cross_sum_binned(int64_t ns, const double *sx, const double *sy, const double *q,
+                             const int *slay, const int *sbin, const double *sdelta,
+                             int64_t nt, const double *tx, const double *ty, const double *tz,
+                             const int *tlay, int nl, const int *use, int nbin, int K,
+                             const int64_t *img_first, const double *are, const double *aim,
+                             const double *zre, const double *zim, const double *wmin,
+                             const double *kre, const double *kim, const double *d, double *phi)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < nt; ++i) {
+        const int l = tlay[i];
+        const double complex k = kre[l] + I * kim[l];
+        double complex acc = 0.0;
+        for (int part = 0; part < 2; ++part) {
+            if (part == 0 ? l >= nl - 1 : l == 0) continue;
+            const double W = part == 0 ? tz[i] - d[l] : d[l - 1] - tz[i];
+            const double Wr = W - wmin[2 * l + part];
+            for (int64_t j = 0; j < ns; ++j) {
+                const int lp = slay[j];
+                if (lp == l || !use[l * nl + lp]) continue;
+                const double dx = tx[i] - sx[j], dy = ty[i] - sy[j];
+                const double rho2 = dx * dx + dy * dy;
+                const int64_t f0 = ((int64_t)(l * nbin + sbin[j]) * 2 + part) * (K + 1);
+                double complex s = 0.0;
+                double pw = 1.0;
+                for (int k3p = 0; k3p <= K; ++k3p) {
+                    double complex t = 0.0;
+                    for (int64_t m = img_first[f0 + k3p]; m < img_first[f0 + k3p + 1]; ++m) {
+                        const double complex w = Wr - (zre[m] + I * zim[m]);
+                        const double complex R = csqrt(rho2 + w * w);
+                        t += (are[m] + I * aim[m]) * h0c(k * R);
+                    }
+                    s += pw * t;
+                    pw *= sdelta[j];
+                }
+                acc += (q[2 * j] + I * q[2 * j + 1]) * s;
+            }
+        }
+        phi[2 * i] = creal(acc);
+        phi[2 * i + 1] = cimag(acc);
+    }
+}

@@ -6,6 +6,7 @@ file with gcc (-O2, OpenMP, no FMA contraction) into ``oracle/_build``.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 
@@ -78,10 +79,115 @@ def direct_sum(med, images, src, q, tgt, include_free=True, include_reaction=Tru
     return phi[0::2] + 1j * phi[1::2]
 
 
-def cross_sum_by_reciprocity(med, zext, src, q, tgt, n_images=16, **fit_kw):
+def images_in_source_layer(med, l, lp):
+    """A cross-layer component (target layer l, source layer l') has its DCIM
+    images in the layer of the larger |k|: those fits match Sommerfeld
+    quadrature to about 1e-8, fits in the smaller-|k| layer only to 1e-6 .. 4e-4
+    (branch points of the spectral function near the sampling paths).  True
+    when that layer is the source layer (reciprocity form)."""
+    return abs(complex(med.k[lp])) > abs(complex(med.k[l]))
+
+
+def cross_sum(med, zext, src, q, tgt, n_images=16, zbin=0.02, K=6, **fit_kw):
+    """Cross-layer part of Phi at the targets, every layer pair with its images
+    in the layer of the larger |k| (``images_in_source_layer``): by reciprocity
+    with one fit per target where that is the source layer, else with the
+    images in the target layer and fits per narrow source z'-bin (width at most
+    ``zbin``, z'-Taylor order ``K``; ``cross_sum_binned``)."""
+    out = cross_sum_by_reciprocity(med, zext, src, q, tgt, n_images,
+                                   pairs=lambda l, lp: images_in_source_layer(med, l, lp), **fit_kw)
+    return out + cross_sum_binned(med, zext, src, q, tgt, n_images, zbin, K,
+                                  pairs=lambda l, lp: not images_in_source_layer(med, l, lp), **fit_kw)
+
+
+def cross_sum_binned(med, zext, src, q, tgt, n_images=16, zbin=0.02, K=6, pairs=None, **fit_kw):
+    """Cross-layer part of Phi with the images in the target layer: the sources
+    of layer l' are grouped in equal z'-bins of width <= zbin over the layer's
+    particle slab, each bin centre zc gets the fits of Theta^{k3'}, k3' = 0..K
+    (Sec. 3.2, ``oracle.cross.fit_cross``), and a source at zc + delta adds
+    sum_{k3'} delta^{k3'} (image sum of fit k3') (``oracle_cross_sum_binned``).
+    pairs(l, l') selects the layer pairs (default: all)."""
+    from .cross import directions, fit_cross, W_min
+    lib = _load()
+    lib.oracle_cross_sum_binned.restype = None
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+    qi = np.ascontiguousarray(np.stack([np.real(q), np.imag(q)], -1).reshape(-1), dtype=np.float64)
+    slay = np.ascontiguousarray(med.layer_of(src[:, 2]), dtype=np.int32)
+    tlay = np.ascontiguousarray(med.layer_of(tgt[:, 2]), dtype=np.int32)
+    if np.any(slay < 0) or np.any(tlay < 0):
+        raise ValueError("point on an interface")
+    nl = med.n_layers
+    use = np.zeros((nl, nl), dtype=np.int32)
+    for l in set(int(v) for v in tlay):
+        for lp in set(int(v) for v in slay):
+            if lp != l and (pairs is None or pairs(l, lp)):
+                use[l, lp] = 1
+    # bins: per source layer, equal widths over its particle slab; global numbering
+    nb = [max(1, int(math.ceil((zext[l][1] - zext[l][0]) / zbin - 1e-9))) for l in range(nl)]
+    b0 = np.concatenate([[0], np.cumsum(nb)]).astype(np.int64)
+    nbin = int(b0[-1])
+    sbin = np.zeros(len(src), dtype=np.int32)
+    sdelta = np.zeros(len(src), dtype=np.float64)
+    zc_of = np.zeros(nbin)
+    for l in range(nl):
+        w = (zext[l][1] - zext[l][0]) / nb[l]
+        zc_of[b0[l]:b0[l + 1]] = zext[l][0] + (np.arange(nb[l]) + 0.5) * w
+        m = slay == l
+        b = np.clip(np.floor((src[m, 2] - zext[l][0]) / w).astype(np.int64), 0, nb[l] - 1)
+        sbin[m] = (b0[l] + b).astype(np.int32)
+        sdelta[m] = src[m, 2] - zc_of[b0[l] + b]
+    counts = np.zeros(nl * nbin * 2 * (K + 1), dtype=np.int64)
+    A_all, Z_all = [], []
+    chunks = {}
+    for l in range(nl):
+        for lp in range(nl):
+            if not use[l, lp]:
+                continue
+            for part in directions(med, l):
+                wm = W_min(med, l, part, zext)
+                pi = 0 if part == 'up' else 1
+                for b in range(b0[lp], b0[lp + 1]):
+                    for k3p in range(K + 1):
+                        A, Z, _ = fit_cross(med, l, lp, part, float(zc_of[b]), k3p, wm, n_images, **fit_kw)
+                        f = ((l * nbin + b) * 2 + pi) * (K + 1) + k3p
+                        chunks[f] = (np.asarray(A, complex), np.asarray(Z, complex))
+                        counts[f] = len(A)
+    img_first = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    A_all = np.zeros(int(img_first[-1]), dtype=complex)
+    Z_all = np.zeros(int(img_first[-1]), dtype=complex)
+    for f, (A, Z) in chunks.items():
+        A_all[img_first[f]:img_first[f + 1]] = A
+        Z_all[img_first[f]:img_first[f + 1]] = Z
+    wmin = np.zeros(2 * nl)
+    for l in range(nl):
+        for part in directions(med, l):
+            wmin[2 * l + (0 if part == 'up' else 1)] = W_min(med, l, part, zext)
+    f64 = lambda v: np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(-1))
+    are, aim, zre, zim = f64(A_all.real), f64(A_all.imag), f64(Z_all.real), f64(Z_all.imag)
+    kre, kim = f64(med.k.real), f64(med.k.imag)
+    dd = f64(np.concatenate([med.d, [0.0]]))
+    wmin = f64(wmin)
+    use_f = np.ascontiguousarray(use.reshape(-1))
+    phi = np.zeros(2 * tgt.shape[0], dtype=np.float64)
+    sx, sy = [np.ascontiguousarray(src[:, i]) for i in range(2)]
+    tx, ty, tz = [np.ascontiguousarray(tgt[:, i]) for i in range(3)]
+    D, L, Ci = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+    lib.oracle_cross_sum_binned(
+        ctypes.c_int64(src.shape[0]), _p(sx, D), _p(sy, D), _p(qi, D), _p(slay, Ci), _p(sbin, Ci),
+        _p(sdelta, D), ctypes.c_int64(tgt.shape[0]), _p(tx, D), _p(ty, D), _p(tz, D), _p(tlay, Ci),
+        ctypes.c_int(nl), _p(use_f, Ci), ctypes.c_int(nbin), ctypes.c_int(K), _p(img_first, L),
+        _p(are, D), _p(aim, D), _p(zre, D), _p(zim, D), _p(wmin, D), _p(kre, D), _p(kim, D), _p(dd, D),
+        _p(phi, D))
+    return phi[0::2] + 1j * phi[1::2]
+
+
+def cross_sum_by_reciprocity(med, zext, src, q, tgt, n_images=16, pairs=None, **fit_kw):
     """Cross-layer part of Phi at the targets, one DCIM fit per target
-    (``oracle_cross_sum`` in ``direct.c``): the plain definition for large
-    source counts, where one fit per source point is out of reach."""
+    (``oracle_cross_sum`` in ``direct.c``), its images in the source layer:
+    the plain definition for large source counts, where one fit per source
+    point is out of reach.  pairs(l, l') selects the (target layer, source
+    layer) pairs (default: all)."""
     from .cross import directions, fit_cross, W_min
     lib = _load()
     lib.oracle_cross_sum.restype = None
@@ -98,7 +204,7 @@ def cross_sum_by_reciprocity(med, zext, src, q, tgt, n_images=16, **fit_kw):
     for i in range(len(tgt)):
         l = int(tlay[i])
         for lp in sorted(present):
-            if lp == l:
+            if lp == l or (pairs is not None and not pairs(l, lp)):
                 continue
             for part in directions(med, lp):
                 wmin = W_min(med, lp, part, zext)

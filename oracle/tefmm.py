@@ -63,6 +63,16 @@ Readings where the paper is silent (all stated the same way for the CUDA path):
   like e^{|k_z| (z_c - d)} along the first DCIM path and cannot be fitted.  Cross-layer near-field pairs are not supported
   (leaves must be small enough that boxes of different layers are never
   adjacent).
+* Which layer holds the images of a cross-layer component (a reading): the
+  DCIM fit of Sec. 3.3 is accurate to about 1e-8 against Sommerfeld quadrature
+  when its images live in the layer of the larger |k|, but only to 1e-6 .. 4e-4
+  in the layer of the smaller |k| (branch points k_rho = k_other of the
+  spectral function then lie close to the sampling paths).  So a component
+  whose target layer l has the smaller |k| is evaluated through reciprocity,
+  k_l^2 u_{l l'}(r; r') = k_l'^2 u_{l' l}(r'; r): its M2L matrix between a
+  target box t and a source box s is (k_l' / k_l)^2 times the transpose of the
+  M2L matrix of component (l', l) from box t to box s, whose fits have their
+  images in layer l' (the z-Taylor order of the target plays the role of k3').
 """
 from __future__ import annotations
 
@@ -407,19 +417,25 @@ class Ops:
         """alpha_k = sum_j q_j (r_j - c)^k."""
         return q @ self.monomials(pts - c[None, :])
 
+    def shift_matrix(self, dc):
+        """B[k, k'] = C(k, k') dc^{k-k'} for k' <= k componentwise (else 0); the
+        same few offsets recur (8 child positions per level), so B is kept."""
+        key = tuple(float(v) for v in dc)
+        cache = self.__dict__.setdefault('_shift_cache', {})
+        if key not in cache:
+            m = self.monomials(np.asarray(dc, dtype=float)[None, :])[0]
+            cache[key] = np.where(self.valid, self.binom * m[self.dpow], 0.0)
+        return cache[key]
+
     def m2m(self, alpha_child, dc):
         """Parent moments from a child's, dc = child centre - parent centre:
         gamma_k = sum_{k' <= k} C(k, k') dc^{k-k'} alpha_{k'}."""
-        m = self.monomials(dc[None, :])[0]
-        B = np.where(self.valid, self.binom * m[self.dpow], 0.0)
-        return B @ alpha_child
+        return self.shift_matrix(dc) @ alpha_child
 
     def l2l(self, beta_parent, dc):
         """Child local from the parent's, dc = child centre - parent centre:
         lambda_k = sum_{k' >= k} C(k', k) dc^{k'-k} beta_{k'}."""
-        m = self.monomials(dc[None, :])[0]
-        B = np.where(self.valid, self.binom * m[self.dpow], 0.0)
-        return B.T @ beta_parent
+        return self.shift_matrix(dc).T @ beta_parent
 
     def l2p(self, beta, pts, c):
         return self.monomials(pts - c[None, :]) @ beta
@@ -615,27 +631,44 @@ class TEFMM:
             self.cross_images[key] = (A, Z)
         return self.cross_images[key]
 
-    def _cross_tables(self, lt, ls, lev, key):
-        """T^{(k3')} of one cross key (dix, diy, izt, izs), shape (p+1, n_{2p})."""
+    def _cross_tables(self, lt, ls, lev, keys):
+        """T^{(k3')} of cross keys (dix, diy, izt, izs) at one level, shape
+        (n_keys, p+1, n_{2p}): T^{(k3')}_g = sum over parts and images of
+        A_j D^g h0(k_l R_j) / g! at (dix h, diy h, W(z_t) - W_min - Z_j).  The
+        recurrence runs once over all (key, image) points of a (part, k3')."""
         tr, p = self.tr, self.p
-        dix, diy, izt, izs = key
+        keys = np.asarray(keys, dtype=np.int64).reshape(-1, 4)
         h = tr.side / float(1 << lev)
-        X0, Y0 = dix * h, diy * h
-        zt = self.cross_centre(lt, lev, izt)
+        X0, Y0 = keys[:, 0] * h, keys[:, 1] * h
+        zt = np.array([self.cross_centre(lt, lev, int(i)) for i in keys[:, 2]])
         mi2 = multi_indices(2 * p)
         odd3 = (-1.0) ** mi2[:, 2]
-        T = np.zeros((p + 1, len(mi2)), dtype=complex)
+        T = np.zeros((len(keys), p + 1, len(mi2)), dtype=complex)
         k = self.med.k[lt]
         for direction in xl.directions(self.med, lt):
             wmin = xl.W_min(self.med, lt, direction, self.zext)
-            W0 = float(xl.W_of(self.med, lt, direction, zt))
+            W0 = xl.W_of(self.med, lt, direction, zt)
             sgn = 1.0 if direction == 'up' else odd3
             for k3p in range(p + 1):
-                A, Z = self.cross_image(lt, ls, direction, lev, izs, k3p)
-                if len(A) == 0:
-                    continue
-                tab = taylor_h0(np.full(len(A), X0), np.full(len(A), Y0), W0 - wmin - np.asarray(Z), k, 2 * p)
-                T[k3p] += sgn * (np.asarray(A)[:, None] * tab).sum(0)
+                idx, A, Z = [], [], []
+                for i, izs in enumerate(keys[:, 3]):
+                    a, z = self.cross_image(lt, ls, direction, lev, int(izs), k3p)
+                    idx.extend([i] * len(a))
+                    A.extend(a)
+                    Z.extend(z)
+                idx, A, Z = np.array(idx, dtype=np.int64), np.array(A, complex), np.array(Z, complex)
+                # slice k3' needs the derivatives of order <= 2p - k3' only
+                P2 = 2 * p - k3p
+                nP = n_coeffs(P2)
+                sg = sgn if np.isscalar(sgn) else sgn[:nP]
+                for c0 in range(0, len(idx), 2048):
+                    sl = slice(c0, c0 + 2048)
+                    tab = taylor_h0(X0[idx[sl]], Y0[idx[sl]], W0[idx[sl]] - wmin - Z[sl], k, P2)
+                    vals = sg * (A[sl, None] * tab)
+                    # the images of a key are consecutive: sum each key's run
+                    ii = idx[sl]
+                    starts = np.nonzero(np.r_[True, ii[1:] != ii[:-1]])[0]
+                    T[ii[starts], k3p, :nP] += np.add.reduceat(vals, starts, axis=0)
         return T
 
     def _cross_m2l(self, lt, ls, V, alpha, beta, need):
@@ -647,18 +680,33 @@ class TEFMM:
             key = (int(tr.level[t]), int(tr.ix[t] - tr.ix[s]), int(tr.iy[t] - tr.iy[s]),
                    int(tr.iz[t]), int(tr.iz[s]))
             groups.setdefault(key, []).append((t, s))
-        for (lev, dix, diy, izt, izs), lst in groups.items():
-            T = self._cross_tables(lt, ls, lev, (dix, diy, izt, izs))
-            H = cx * T[k3p[None, :], gx]
-            t = np.array([a for a, _ in lst])
-            s_ = np.array([b for _, b in lst])
-            # moments about the source's cross-layer centre, M2L into locals
-            # about the target's cross-layer centre, re-expanded at the box centre
-            zs, zsc = tr.center(s_[0])[2], self.cross_centre(ls, lev, izs)
-            zt, ztc = tr.center(t[0])[2], self.cross_centre(lt, lev, izt)
-            a_sh = np.array([ops.m2m(alpha[j], np.array([0.0, 0.0, zs - zsc])) for j in s_])
-            loc = a_sh @ H.T
-            np.add.at(beta, t, np.array([ops.l2l(b, np.array([0.0, 0.0, zt - ztc])) for b in loc]))
+        # images in the layer of the larger |k| (see the module docstring): a target
+        # layer with the smaller |k| uses reciprocity, k_l^2 u_{l l'}(r; r') =
+        # k_l'^2 u_{l' l}(r'; r), i.e. the transposed matrix of the mirror pair
+        # (target box <-> source box) of component (l', l), times (k_l' / k_l)^2
+        rev = abs(self.med.k[ls]) > abs(self.med.k[lt])
+        by_level = {}
+        for g in groups:
+            by_level.setdefault(g[0], []).append(g)
+        for lev, gl in by_level.items():
+            if rev:
+                Ts = self._cross_tables(ls, lt, lev, [(-dx, -dy, zs, zt) for (_, dx, dy, zt, zs) in gl])
+            else:
+                Ts = self._cross_tables(lt, ls, lev, [(dx, dy, zt, zs) for (_, dx, dy, zt, zs) in gl])
+            for (_, dix, diy, izt, izs), T in zip(gl, Ts):
+                lst = groups[(lev, dix, diy, izt, izs)]
+                H = cx * T[k3p[None, :], gx]
+                if rev:
+                    H = (self.med.k[ls] / self.med.k[lt]) ** 2 * H.T
+                t = np.array([a for a, _ in lst])
+                s_ = np.array([b for _, b in lst])
+                # moments about the source's cross-layer centre, M2L into locals
+                # about the target's cross-layer centre, re-expanded at the box centre
+                zs, zsc = tr.center(s_[0])[2], self.cross_centre(ls, lev, izs)
+                zt, ztc = tr.center(t[0])[2], self.cross_centre(lt, lev, izt)
+                a_sh = alpha[s_] @ ops.shift_matrix(np.array([0.0, 0.0, zs - zsc])).T
+                loc = a_sh @ H.T
+                np.add.at(beta, t, loc @ ops.shift_matrix(np.array([0.0, 0.0, zt - ztc])))
 
     # -- near field ----------------------------------------------------------
     def _kernel_same_layer(self, l, tpts, spts):

@@ -175,7 +175,10 @@ __global__ void __launch_bounds__(256, 4) k_xtables(int nx, const uint64_t *__re
 }
 
 // Cross-layer M2L, FP64: one CTA per chunk of pairs of one cross key, one
-// thread per output coefficient k; the k' sum walks the k3' slices.
+// thread per output coefficient k; the k' sum walks the k3' slices.  A reversed
+// key (xkey_rev) applies (k_lt / k_ls)^2 times the transposed matrix
+// H^T[k][k'] = xcf[k][k'] T^{(k3)}[xg[k][k']]: thread k takes its whole sum from
+// the slice of its own k3.
 constexpr int CHX = 16;
 
 __global__ void k_m2l_x(int c0, int nch, const int *__restrict__ chunk_start,
@@ -185,7 +188,9 @@ __global__ void k_m2l_x(int c0, int nch, const int *__restrict__ chunk_start,
                         const int *__restrict__ v_src, int p, int np,
                         const unsigned short *__restrict__ xg, const double *__restrict__ xcf,
                         const int *__restrict__ kp_order, const int *__restrict__ kp_grp,
-                        const cplx *__restrict__ alpha, cplx *__restrict__ beta) {
+                        const uint64_t *__restrict__ table_key, const int *__restrict__ mi,
+                        const cplx *__restrict__ kl, const cplx *__restrict__ alpha,
+                        cplx *__restrict__ beta) {
     int c = c0 + blockIdx.x;
     if (blockIdx.x >= nch) return;
     extern __shared__ double sm[];
@@ -196,6 +201,15 @@ __global__ void k_m2l_x(int c0, int nch, const int *__restrict__ chunk_start,
     const int cnt = chunk_cnt[c], st = chunk_start[c];
     const int k = threadIdx.x;
     const cplx *T = xt + (int64_t)tb * NX;
+    const uint64_t key = table_key[chunk_table[c]];
+    const bool rev = xkey_rev(key) != 0;
+    cplx fac = mkc(1, 0);
+    if (rev) {
+        const XKey x = xkey_decode(key);
+        const cplx r = cdiv(kl[x.lt], kl[x.ls]);
+        fac = cmul(r, r);
+    }
+    const int k3 = k < np ? mi[3 * k + 2] : -1;
     for (int qb = 0; qb < cnt; qb += CHX) {
         const int nq = min(CHX, cnt - qb);
         __syncthreads();
@@ -216,18 +230,35 @@ __global__ void k_m2l_x(int c0, int nch, const int *__restrict__ chunk_start,
             __syncthreads();
             off += n2;
             if (k >= np) continue;
-            for (int i = kp_grp[k3p]; i < kp_grp[k3p + 1]; ++i) {
-                const int kp = kp_order[i];
-                const double cf = xcf[(int64_t)kp * np + k];
-                cplx hv = tab[xg[(int64_t)kp * np + k]];
-                hv.x *= cf;
-                hv.y *= cf;
+            if (!rev) {
+                for (int i = kp_grp[k3p]; i < kp_grp[k3p + 1]; ++i) {
+                    const int kp = kp_order[i];
+                    const double cf = xcf[(int64_t)kp * np + k];
+                    cplx hv = tab[xg[(int64_t)kp * np + k]];
+                    hv.x *= cf;
+                    hv.y *= cf;
 #pragma unroll
-                for (int q = 0; q < CHX; ++q) {
-                    if (q < nq) {
-                        cplx a = al[q * np + kp];
-                        acc[q].x += hv.x * a.x - hv.y * a.y;
-                        acc[q].y += hv.x * a.y + hv.y * a.x;
+                    for (int q = 0; q < CHX; ++q) {
+                        if (q < nq) {
+                            cplx a = al[q * np + kp];
+                            acc[q].x += hv.x * a.x - hv.y * a.y;
+                            acc[q].y += hv.x * a.y + hv.y * a.x;
+                        }
+                    }
+                }
+            } else if (k3 == k3p) {
+                for (int kp = 0; kp < np; ++kp) {
+                    const double cf = xcf[(int64_t)k * np + kp];
+                    cplx hv = tab[xg[(int64_t)k * np + kp]];
+                    hv.x *= cf;
+                    hv.y *= cf;
+#pragma unroll
+                    for (int q = 0; q < CHX; ++q) {
+                        if (q < nq) {
+                            cplx a = al[q * np + kp];
+                            acc[q].x += hv.x * a.x - hv.y * a.y;
+                            acc[q].y += hv.x * a.y + hv.y * a.x;
+                        }
                     }
                 }
             }
@@ -236,9 +267,10 @@ __global__ void k_m2l_x(int c0, int nch, const int *__restrict__ chunk_start,
 #pragma unroll
             for (int q = 0; q < CHX; ++q) {
                 if (q < nq) {
+                    const cplx v = rev ? cmul(fac, acc[q]) : acc[q];
                     double *dst = (double *)&beta[(int64_t)tgt[q] * np + k];
-                    atomicAdd(dst, acc[q].x);
-                    atomicAdd(dst + 1, acc[q].y);
+                    atomicAdd(dst, v.x);
+                    atomicAdd(dst + 1, v.y);
                 }
             }
         }
@@ -457,6 +489,7 @@ int cross_apply(tefmm_plan_s *P, cudaStream_t st) {
                                    dp<cplx>(P->xtables), P->NX, dp<int>(P->pair_idx_sorted),
                                    dp<int>(P->pair_t), dp<int>(P->v_src), P->p, np,
                                    dp<unsigned short>(P->d_xG), dp<double>(P->d_xcf), og, og + np,
+                                   dp<uint64_t>(P->table_slot), dp<int>(P->d_mi), dp<cplx>(P->d_k),
                                    dp<cplx>(P->xalpha), dp<cplx>(P->xbeta));
         P->launches++;
     }

@@ -61,6 +61,7 @@ struct TcArgs {
     int nsplit;                  // column slices per chunk
     const float *W;              // precomputed W^T blocks (k_wgen)
     int tcols;                   // TMEM columns allocated (power of 2 >= MT * Ncta)
+    const cplx *kl;              // wavenumber per layer (reversed cross keys)
 };
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -122,6 +123,14 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
     const int lev = key_level(key);
     const double h = a.side / (double)(1 << lev);
     const float *cf = kind == 0 ? a.cfB : a.cfA;
+    // a reversed cross key: (k_lt / k_ls)^2 times the transposed matrix of its component
+    const bool rev = a.xmode && xkey_rev(key);
+    cplx fac = mkc(1, 0);
+    if (rev) {
+        const XKey x = xkey_decode(key);
+        const cplx r = cdiv(a.kl[x.lt], a.kl[x.ls]);
+        fac = cmul(r, r);
+    }
     {
         const cplx *T = a.tables + (int64_t)(tb - a.tab_origin) * a.tab_stride;
         const int nsl = a.xmode ? a.p + 1 : 1;
@@ -133,6 +142,7 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
                 double s = 1.0;
                 for (int i = 0; i < n; ++i) s *= h;
                 cplx v = T[off + g];
+                if (rev) v = cmul(fac, v);
                 tab[off + g] = make_float2((float)(v.x * s), (float)(v.y * s));
             }
             off += n2;
@@ -157,7 +167,7 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
                     const int col = c0 + 4 * cg + 2 * hp;          // real column of k'; col + 1 imaginary
                     if (col < 2 * np) {
                         const int kp = np - 1 - (col >> 1);         // K order: see kcol()
-                        const int64_t o = (int64_t)kp * np + k;
+                        const int64_t o = rev ? (int64_t)k * np + kp : (int64_t)kp * np + k;
                         const float cfv = __ldg(cf + o);
                         const float2 t = tab[__ldg(a.G + o)];
                         const float hr = cfv * t.x, hi = cfv * t.y;
@@ -556,6 +566,7 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
     a.p = P->p;
     a.nsplit = nsplit;
     a.tcols = tcols;
+    a.kl = dp<cplx>(P->d_k);
     // keys in batches whose W^T blocks fit in W_BATCH_BYTES; chunks are sorted
     // by key, so a batch of keys is a contiguous range of chunks
     const int nk = Kpad / KC;

@@ -258,7 +258,8 @@ __global__ void k_l2l(int off, int cnt, TreeArrays T, Cube cb, int p, int np, co
 // (layout and field accessors in ops_common.cuh)
 __global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pair_t,
                             const int *__restrict__ v_src, const int *__restrict__ has_A,
-                            uint64_t *__restrict__ keys, int *__restrict__ vals, int *flags) {
+                            const cplx *__restrict__ kl, uint64_t *__restrict__ keys,
+                            int *__restrict__ vals, int *flags) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= nv) return;
     int t = pair_t[e], s = v_src[e];
@@ -270,7 +271,11 @@ __global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pa
         atomicOr(flags, FLAG_CHECK);
         keys[2 * e] = keys[2 * e + 1] = ~0ULL;
     } else if (lay != lays) {          // cross-layer component: one table per (z_t, z_s)
-        keys[2 * e] = xkey(l, lay, lays, dx, dy, T.iz[t], T.iz[s]);
+        // images in the layer of the larger |k| (their DCIM fits are the accurate
+        // ones): a target layer with the smaller |k| takes its mirror pair's key
+        const double kt = hypot(kl[lay].x, kl[lay].y), ks = hypot(kl[lays].x, kl[lays].y);
+        keys[2 * e] = ks > kt ? xkey(l, lays, lay, -dx, -dy, T.iz[s], T.iz[t], 1)
+                              : xkey(l, lay, lays, dx, dy, T.iz[t], T.iz[s], 0);
         keys[2 * e + 1] = ~0ULL;
     } else {
         keys[2 * e] = m2l_key(0, l, lay, dx, dy, (uint64_t)(dz + KEY_OFF));
@@ -307,7 +312,8 @@ __global__ void k_seg_start(int64_t n, const int *__restrict__ head, const int *
 //   T(Y, X)[g1, g2, g3]       = T(X, Y)[g2, g1, g3].
 // Of the (up to eight) keys that differ only by these maps, the first in key
 // order (its representative) is computed by the recurrence and the others are
-// copied from it.  rep_code[i] = rep * 8 + code, code bit 0: sx = -1, bit 1:
+// copied from it.  A reversed cross-layer key (rev bit) has the table of its
+// rev = 0 twin, so cross keys search sixteen variants.  rep_code[i] = rep * 8 + code, code bit 0: sx = -1, bit 1:
 // sy = -1, bit 2: swapped, so that T_i[g] = sx^g1 sy^g2 T_rep[g or (g2, g1, g3)].
 // The sign flips reproduce the recurrence's own result bit for bit; the swap
 // changes its rounding only (the x and y terms are summed in the other order).
@@ -317,12 +323,15 @@ __global__ void k_table_rep(int ntab, const uint64_t *__restrict__ keys, int *__
     if (i >= ntab) return;
     const uint64_t key = keys[i];
     const int dx = key_dx(key), dy = key_dy(key);
+    // a reversed cross key uses the table of the same key with rev = 0
+    const int nvar = key_kind(key) == 2 ? 16 : 8;
     int rep = i, rdx = dx, rdy = dy;
-    for (int v = 1; v < 8; ++v) {
+    for (int v = 1; v < nvar; ++v) {
         int a = (v & 4) ? dy : dx, b = (v & 4) ? dx : dy;
         if (v & 1) a = -a;
         if (v & 2) b = -b;
-        const uint64_t kv = key_with_dxdy(key, a, b);
+        uint64_t kv = key_with_dxdy(key, a, b);
+        if (v & 8) kv ^= 1ULL << 43;
         int lo = 0, hi = rep;   // keys are sorted: search the ones before the current representative
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -694,7 +703,8 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     CUDA_TRY(cudaMemcpyAsync(P->seg_tmp.p, hasA, sizeof(hasA), cudaMemcpyHostToDevice, st));
     TreeArrays T = tree_arrays(P);
     k_m2l_items<<<grid_for(nv, 256), 256, 0, st>>>(nv, T, dp<int>(P->pair_t), dp<int>(P->v_src),
-                                                   dp<int>(P->seg_tmp), dp<uint64_t>(P->pair_slot),
+                                                   dp<int>(P->seg_tmp), dp<cplx>(P->d_k),
+                                                   dp<uint64_t>(P->pair_slot),
                                                    dp<int>(P->pair_idx), dp<int>(P->flags));
     P->launches++;
     size_t bytes = 0;

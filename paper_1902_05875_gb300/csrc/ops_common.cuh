@@ -112,10 +112,18 @@ __host__ __device__ inline uint64_t key_with_dxdy(uint64_t k, int dx, int dy) {
     return (k & ~(1023ULL << 44)) | ((uint64_t)(dx + KEY_OFF) << 49) | ((uint64_t)(dy + KEY_OFF) << 44);
 }
 
-// Cross-layer M2L key: kind 2, w = ls(3) iz_t(20) iz_s(20).
-__host__ __device__ inline uint64_t xkey(int l, int lt, int ls, int dx, int dy, int izt, int izs) {
-    return m2l_key(2, l, lt, dx, dy, ((uint64_t)ls << 40) | ((uint64_t)izt << 20) | (uint64_t)izs);
+// Cross-layer M2L key: kind 2, w = rev(1) ls(3) iz_t(20) iz_s(20).  The fields
+// describe the component (lt <- ls) whose fits and table the key uses.  rev = 0:
+// the V pairs of the key translate from a source box of layer ls into a target
+// box of layer lt.  rev = 1 (the pair's target layer has the smaller |k|): the
+// pairs run the other way, target box (layer ls, z-index izs) from source box
+// (layer lt, izt, offset -dx, -dy), and use the transposed matrix of the key's
+// component scaled by (k_lt / k_ls)^2 (reciprocity).
+__host__ __device__ inline uint64_t xkey(int l, int lt, int ls, int dx, int dy, int izt, int izs, int rev = 0) {
+    return m2l_key(2, l, lt, dx, dy,
+                   ((uint64_t)rev << 43) | ((uint64_t)ls << 40) | ((uint64_t)izt << 20) | (uint64_t)izs);
 }
+__host__ __device__ inline int xkey_rev(uint64_t k) { return (int)((k >> 43) & 1); }
 struct XKey {
     int level, lt, ls, dx, dy, izt, izs;
 };

@@ -74,3 +74,14 @@ def oracle_lists_csr(tr, lists_by_pair, n_nodes):
             src.extend(lst)
         return ptr, np.array(src, dtype=np.int64)
     return csr(V), csr(N)
+
+
+def push_cross_fits(plan, oracle_fmm):
+    """Replace the plan's cross-layer fits by the oracle's: every key the plan
+    holds (after an evaluation) is fitted by the oracle's TE-FMM object
+    (``cross_image``, the oracle's own DCIM fit at the same clamped source
+    z-centre) and imported with ``set_cross_images``.  Returns the keys."""
+    keys = sorted(plan.cross_images())
+    fits = {k: oracle_fmm.cross_image(*k) for k in keys}
+    plan.set_cross_images(fits)
+    return keys

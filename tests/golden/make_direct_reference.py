@@ -2,8 +2,9 @@
 sampled targets (``direct_three_layer_slabs_n2M_1000.txt``).
 
 The values come from the oracle alone (``oracle.direct``: same-layer part by
-the DCIM images of ``oracle.dcim``, cross-layer part by one DCIM fit per
-target); the workload is the seeded input generator's.  The sample is 1000
+the DCIM images of ``oracle.dcim``, cross-layer part by ``cross_sum``, every
+layer pair with its images in the layer of the larger |k|); the workload is
+the seeded input generator's.  The sample is 1000
 targets drawn without replacement by numpy ``default_rng(1)``.  Each output
 line is ``index re im`` (17 significant digits).  Run from the repository root:
 
@@ -27,7 +28,7 @@ def main(n=1000):
     from paper_1902_05875_gb300 import workloads
     from oracle.medium import Medium
     from oracle.dcim import ImageTable
-    from oracle.direct import direct_sum, cross_sum_by_reciprocity
+    from oracle.direct import direct_sum, cross_sum
     w = workloads.cfg_mixed_2m()
     idx = np.random.default_rng(1).choice(len(w.src), n, replace=False)
     med = Medium(w.interfaces, w.k)
@@ -35,7 +36,7 @@ def main(n=1000):
     tgt = w.src[idx]
     t0 = time.perf_counter()
     phi = direct_sum(med, img, w.src, w.q, tgt)
-    phi = phi + cross_sum_by_reciprocity(med, w.zext, w.src, w.q, tgt, n_images=w.n_images)
+    phi = phi + cross_sum(med, w.zext, w.src, w.q, tgt, n_images=w.n_images)
     dt = time.perf_counter() - t0
     with open(OUT.format(n=n), "w") as f:
         f.write(f"# FP64 direct sum (oracle) of {w.name} at {n} targets, default_rng(1); "

@@ -15,7 +15,7 @@ from paper_1902_05875_gb300 import workloads as W
 from paper_1902_05875_gb300 import tefmm
 from oracle.medium import Medium
 from oracle.dcim import ImageTable
-from oracle.direct import direct_sum, cross_sum_by_reciprocity
+from oracle.direct import direct_sum, cross_sum
 
 from _helpers import need_gpu, make_plan, gpu_eval, to_dev
 
@@ -58,7 +58,7 @@ def test_batch_instance_against_direct_sum(precision):
     sel = np.random.default_rng(0).choice(len(w.src), 40, replace=False)
     ref = direct_sum(med, img, w.src, w.q, w.src[sel])
     if len(w.k) > 1:
-        ref = ref + cross_sum_by_reciprocity(med, w.zext, w.src, w.q, w.src[sel], n_images=w.n_images)
+        ref = ref + cross_sum(med, w.zext, w.src, w.q, w.src[sel], n_images=w.n_images)
     err = np.linalg.norm(phi[sel] - ref) / np.linalg.norm(ref)
     print(f'{w.name} ({len(w.k)} layers, p=6) vs direct sum: {err:.2e}')
     assert err < 5e-3, err

@@ -2,9 +2,10 @@
 
 * the octree with the cross-layer split rule and the merged V / near lists
   bit-exact against the oracle's;
-* the FP64 form within 1e-11 of the oracle's TE-FMM fed the same images (the
-  plan's same-layer images replaced by the oracle's, the oracle given the
-  plan's cross-layer fits);
+* the FP64 form within 1e-11 of the oracle's TE-FMM with the same images:
+  the plan's same-layer images and cross-layer fits are replaced by the
+  oracle's (``set_images``, ``set_cross_images``), so the oracle never takes a
+  value the device computed;
 * the device cross-layer fits against Sommerfeld quadrature of the same
   z'-derivative;
 * the whole product (device fits, p = 8) against the oracle's direct sum;
@@ -17,11 +18,12 @@ import pytest
 from paper_1902_05875_gb300 import workloads as W
 from paper_1902_05875_gb300 import tefmm
 from oracle.tefmm import TEFMM
-from oracle.cross import CrossDirect, image_sum, W_min
-from oracle.direct import direct_sum
+from oracle.cross import image_sum, W_min
+from oracle.direct import direct_sum, cross_sum
 from oracle.sommerfeld import reaction_derivative
 
-from _helpers import need_gpu, oracle_images, push_images, make_plan, gpu_eval, oracle_lists_csr
+from _helpers import (need_gpu, oracle_images, push_images, push_cross_fits, make_plan, gpu_eval,
+                      oracle_lists_csr)
 
 pytestmark = pytest.mark.gpu
 
@@ -40,8 +42,7 @@ def test_cross_tree_and_lists_bit_exact():
     push_images(plan, img)
     gpu_eval(plan, torch, w.src, w.q)
     g = plan.export_tree()
-    f = TEFMM(med, img, w.p, w.leaf_cap, cross_images=plan.cross_images(),
-              n_images=w.n_images).setup(w.src, w.src)
+    f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images).setup(w.src, w.src)
     tr = f.tr
     assert g["n_nodes"] == tr.n_nodes
     for key, ref in (("layer", tr.layer), ("level", tr.level), ("ix", tr.ix), ("iy", tr.iy),
@@ -63,12 +64,14 @@ def test_cross_fp64_matches_oracle_fmm():
     med, img = oracle_images(w)
     plan = make_plan(w)
     push_images(plan, img)
+    gpu_eval(plan, torch, w.src, w.q)
+    f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images).setup(w.src, w.src)
+    keys = push_cross_fits(plan, f)
     phi = gpu_eval(plan, torch, w.src, w.q)
-    xi = plan.cross_images()
-    f = TEFMM(med, img, w.p, w.leaf_cap, cross_images=dict(xi), n_images=w.n_images).setup(w.src, w.src)
+    assert plan.stats()["n_cross_fits_last"] == 0        # every fit came from the oracle
     alpha = f.upward(w.q)
     beta = f.downward(alpha)
-    assert len(f.cross_images) == len(xi), "oracle needed a fit the plan does not hold"
+    assert sorted(f.cross_images) == keys, "the oracle and the plan use different fits"
     ga, gb = plan.export_expansions()
     for n in range(f.tr.n_nodes):
         if f.tr.nt(n) > 0:
@@ -115,7 +118,7 @@ def test_cross_fmm_against_direct_sum():
     plan = make_plan(w)
     phi = gpu_eval(plan, torch, w.src, w.q)
     ref = direct_sum(med, img, w.src, w.q, w.src) + \
-        CrossDirect(med, w.zext, n_images=w.n_images).potential(w.src, w.q, w.src)
+        cross_sum(med, w.zext, w.src, w.q, w.src, n_images=w.n_images)
     err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
     print(f'cross-layer product (device fits, p=8) vs direct sum: {err:.3e}')
     assert err < 1e-4, err
@@ -159,15 +162,16 @@ def test_cross_fit_cache():
 def test_stacked_cross_rule_tree_lists_and_fp64_parity():
     """Slabs 0.1 from the interfaces (HX = 0.8): the stacked cross-layer
     admissibility rule is active; trees and lists stay bit-exact and the FP64
-    form matches the oracle's TE-FMM given the plan's cross-layer fits."""
+    form, run on the oracle's cross-layer fits, matches the oracle's TE-FMM."""
     torch = need_gpu()
     w = W.three_layer_slabs(240, 3, 8, seed=4, half_width=0.5, n_images=16)
     med, img = oracle_images(w)
     plan = make_plan(w)
     push_images(plan, img)
+    gpu_eval(plan, torch, w.src, w.q)
+    f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images).setup(w.src, w.src)
+    push_cross_fits(plan, f)
     phi = gpu_eval(plan, torch, w.src, w.q)
-    f = TEFMM(med, img, w.p, w.leaf_cap, cross_images=dict(plan.cross_images()),
-              n_images=w.n_images).setup(w.src, w.src)
     tr = f.tr
     assert abs(tr.HX - 0.8) < 1e-12
     g = plan.export_tree()

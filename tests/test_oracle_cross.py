@@ -19,6 +19,11 @@ What fixes them independently of the oracle's own formulas:
   (same-layer images + per-source-point cross-layer fits), with an error that
   falls as p rises; a planted sign error in the down-going cross-layer tables
   is detected;
+* which layer holds a component's images: against the Sommerfeld quadrature,
+  fits whose images live in the layer of the larger |k| are accurate to about
+  1e-8, fits in the smaller-|k| layer only to 1e-6 .. 4e-4; the cross-layer
+  direct sum built on that choice (``cross_sum``) matches the quadrature sum
+  to 2e-7, and its binned z'-Taylor part matches per-source fits to 2e-8;
 * the cross-layer split rule and the stacked cross-layer admissibility rule:
   no cross-layer pair is left to the near field, and the lists still cover
   every (target, source) pair exactly once; on slabs 0.1 from the interfaces
@@ -29,8 +34,9 @@ import pytest
 
 from oracle.medium import Medium
 from oracle.dcim import ImageTable
-from oracle.cross import CrossDirect, fit_cross, image_sum, W_min
-from oracle.direct import direct_sum, cross_sum_by_reciprocity
+from oracle.cross import CrossDirect, directions, fit_cross, image_sum, W_min
+from oracle.direct import (direct_sum, cross_sum, cross_sum_binned, cross_sum_by_reciprocity,
+                           images_in_source_layer)
 from oracle.sommerfeld import reaction_derivative
 from oracle.tefmm import TEFMM, Trees, build_lists
 from paper_1902_05875_gb300 import workloads as W
@@ -97,7 +103,7 @@ def slabs():
     med = Medium(w.interfaces, w.k)
     img = ImageTable(med, w.zext, n_images=w.n_images)
     ref = direct_sum(med, img, w.src, w.q, w.src) + \
-        CrossDirect(med, w.zext, n_images=w.n_images).potential(w.src, w.q, w.src)
+        cross_sum(med, w.zext, w.src, w.q, w.src, n_images=w.n_images)
     return w, med, img, ref
 
 
@@ -121,28 +127,27 @@ def test_cross_layer_fmm_detects_planted_sign_error(slabs, monkeypatch):
     e_good = np.linalg.norm(good - ref) / np.linalg.norm(ref)
     real_tables = T.TEFMM._cross_tables
 
-    def planted(self, lt, ls, lev, key):
-        tab = real_tables(self, lt, ls, lev, key)
+    def planted(self, lt, ls, lev, keys):
+        tab = real_tables(self, lt, ls, lev, keys)
         # undo the (-1)^{g3} of the down-going part by recomputing it without the sign
         import oracle.cross as xl
         from oracle.derivs import taylor_h0, multi_indices
         tr, p = self.tr, self.p
-        dix, diy, izt, izs = key
         h = tr.side / float(1 << lev)
-        zt = tr.lo[2] + (izt + 0.5) * h
         mi2 = multi_indices(2 * p)
         odd3 = (-1.0) ** mi2[:, 2]
         if 'down' in xl.directions(self.med, lt):
             wmin = xl.W_min(self.med, lt, 'down', self.zext)
-            W0 = float(xl.W_of(self.med, lt, 'down', zt))
-            for k3p in range(p + 1):
-                A, Z = self.cross_image(lt, ls, 'down', lev, izs, k3p)
-                if len(A) == 0:
-                    continue
-                t = taylor_h0(np.full(len(A), dix * h), np.full(len(A), diy * h),
-                              W0 - wmin - np.asarray(Z), self.med.k[lt], 2 * p)
-                s = (np.asarray(A)[:, None] * t).sum(0)
-                tab[k3p] += s - odd3 * s
+            for i, (dix, diy, izt, izs) in enumerate(np.asarray(keys).reshape(-1, 4)):
+                W0 = float(xl.W_of(self.med, lt, 'down', self.cross_centre(lt, lev, int(izt))))
+                for k3p in range(p + 1):
+                    A, Z = self.cross_image(lt, ls, 'down', lev, int(izs), k3p)
+                    if len(A) == 0:
+                        continue
+                    t = taylor_h0(np.full(len(A), dix * h), np.full(len(A), diy * h),
+                                  W0 - wmin - np.asarray(Z), self.med.k[lt], 2 * p)
+                    s = (np.asarray(A)[:, None] * t).sum(0)
+                    tab[i, k3p] += s - odd3 * s
         return tab
     monkeypatch.setattr(T.TEFMM, "_cross_tables", planted)
     bad = TEFMM(med, img, 4, w.leaf_cap, n_images=w.n_images).setup(w.src, w.src).evaluate(w.q)
@@ -220,7 +225,7 @@ def test_stacked_cross_pairs_rule_improves_accuracy():
     med = Medium(w.interfaces, w.k)
     img = ImageTable(med, w.zext, n_images=16)
     ref = direct_sum(med, img, w.src, w.q, w.src) + \
-        CrossDirect(med, w.zext, n_images=16).potential(w.src, w.q, w.src)
+        cross_sum(med, w.zext, w.src, w.q, w.src, n_images=16)
     errs = {}
     for name, lim in (("rule", None), ("no_rule", np.inf)):
         f = TEFMM(med, img, 3, w.leaf_cap, n_images=16)
@@ -237,3 +242,92 @@ def test_stacked_cross_pairs_rule_improves_accuracy():
         errs[name] = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
     print(errs)
     assert errs["rule"] < 0.2 * errs["no_rule"], errs
+
+
+def _slab_medium():
+    w = W.cfg_mixed_200k()
+    return Medium(w.interfaces, w.k), w.zext
+
+
+@pytest.mark.parametrize("l,lp", [(2, 0), (0, 2), (2, 1), (1, 2), (0, 1)])
+def test_images_in_larger_k_layer_match_quadrature(l, lp):
+    """Medium k = (2, 3, 4 + 0.01i), slabs 0.1 from the interfaces: a target
+    and a source each 0.1 from the interfaces, horizontal offsets 0 .. 4.  The
+    component u_{l l'} with its images in the larger-|k| layer (target layer,
+    or the source layer by reciprocity) matches the quadrature to 2e-7; with
+    the images in the other layer it misses by more than 1e-6 somewhere."""
+    med, zext = _slab_medium()
+    zt = zext[l][1] if l > lp else zext[l][0]
+    zs = zext[lp][0] if l > lp else zext[lp][1]
+    good, bad = [], []
+    for rho in (0.0, 0.7, 2.0, 4.0):
+        r, rp = np.r_[rho, 0.0, zt], np.r_[0.0, 0.0, zs]
+        ref = sum(reaction_derivative(med, l, lp, r, rp, part=pt) for pt in directions(med, l))
+        tgt_form = 0
+        for pt in directions(med, l):
+            wm = W_min(med, l, pt, zext)
+            A, Z, _ = fit_cross(med, l, lp, pt, zs, 0, wm, n_images=16)
+            tgt_form += image_sum(med, l, pt, A, Z, wm, *r, rp[0], rp[1])
+        src_form = 0
+        for pt in directions(med, lp):
+            wm = W_min(med, lp, pt, zext)
+            A, Z, _ = fit_cross(med, lp, l, pt, zt, 0, wm, n_images=16)
+            src_form += image_sum(med, lp, pt, A, Z, wm, *rp, r[0], r[1])
+        src_form *= (med.k[lp] / med.k[l]) ** 2
+        if images_in_source_layer(med, l, lp):
+            good.append(abs(src_form - ref) / abs(ref))
+            bad.append(abs(tgt_form - ref) / abs(ref))
+        else:
+            good.append(abs(tgt_form - ref) / abs(ref))
+            bad.append(abs(src_form - ref) / abs(ref))
+    assert max(good) <= 2e-7, good
+    assert max(bad) > 1e-6, bad
+
+
+@pytest.fixture(scope="module")
+def small_slabs():
+    w = W.three_layer_slabs(150, 4, 16, seed=3, n_images=16, name="small_slabs")
+    med = Medium(w.interfaces, w.k)
+    tgt = w.src[np.random.default_rng(7).choice(len(w.src), 40, replace=False)]
+    return w, med, tgt
+
+
+def test_cross_sum_binned_matches_per_source_fits(small_slabs):
+    """The binned z'-Taylor form (fits at bin centres, order 6) against one fit
+    per source point at its exact z' (``CrossDirect``), on the layer pairs where
+    the images are in the target layer."""
+    w, med, tgt = small_slabs
+    nr = lambda l, lp: not images_in_source_layer(med, l, lp)
+    got = cross_sum_binned(med, w.zext, w.src, w.q, tgt, 16, pairs=nr)
+    tl, sl = med.layer_of(tgt[:, 2]), med.layer_of(w.src[:, 2])
+    ref = np.zeros(len(tgt), complex)
+    for lp in range(med.n_layers):
+        m = sl == lp
+        part = CrossDirect(med, w.zext, n_images=16).potential(w.src[m], w.q[m], tgt)
+        sel = np.array([tl[i] != lp and nr(tl[i], lp) for i in range(len(tgt))])
+        ref[sel] += part[sel]
+    assert np.linalg.norm(ref) > 0
+    assert np.linalg.norm(got - ref) <= 2e-8 * np.linalg.norm(ref), np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
+def test_cross_sum_matches_quadrature(small_slabs):
+    """The cross-layer direct sum (``cross_sum``) against the pairwise
+    Sommerfeld quadrature at 3 targets in each layer: within 2e-7, while
+    either single representation (all images in the source layer, or all in
+    the target layer) misses by more than 5e-6."""
+    w, med, tgt = small_slabs
+    lay = med.layer_of(tgt[:, 2])
+    tgt = np.concatenate([tgt[lay == l][:3] for l in range(3)])
+    src, q = w.src[::3], w.q[::3]
+    tl, sl = med.layer_of(tgt[:, 2]), med.layer_of(src[:, 2])
+    assert len(set(tl)) == 3
+    truth = np.zeros(len(tgt), complex)
+    for i in range(len(tgt)):
+        for j in range(len(src)):
+            if tl[i] != sl[j]:
+                truth[i] += q[j] * sum(reaction_derivative(med, tl[i], sl[j], tgt[i], src[j], part=pt)
+                                       for pt in directions(med, tl[i]))
+    err = lambda v: np.linalg.norm(v - truth) / np.linalg.norm(truth)
+    assert err(cross_sum(med, w.zext, src, q, tgt, 16)) <= 2e-7
+    assert err(cross_sum_by_reciprocity(med, w.zext, src, q, tgt, 16)) > 5e-6
+    assert err(CrossDirect(med, w.zext, n_images=16).potential(src, q, tgt)) > 5e-6
