@@ -122,6 +122,13 @@ typedef struct {
     int n_tables_built;    /* last eval: tables computed by the recurrence; the other
                               n_tables - n_tables_built are copied from one of these by
                               the reflection x -> -x, y -> -y and swap x <-> y symmetry */
+    int64_t n_m2l_items;   /* last eval: translation matrices applied, same-layer (up to
+                              two per V pair: the B and the A table)                  */
+    int64_t n_m2l_items_cross; /* ... cross-layer (one per cross-layer V pair)        */
+    double ms_m2l_kernel;  /* mixed form: device time of the tensor-core contraction
+                              kernels alone (CUDA events around each launch)          */
+    int n_m2l_kernel_launches; /* ... and their number                               */
+    int64_t n_p2p_pairs_layer[8]; /* near-field particle pairs by target layer        */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,
@@ -295,12 +302,13 @@ int tefmm_plan_set_cross_images(tefmm_plan plan, int n_fits, const int *keys, co
  * The paper has no counterpart to this call; it is a convenience of this
  * library.  It runs the same device DCIM fit as tefmm_plan_create (same
  * images, same order of terms as tefmm_plan_get_images) for callers that
- * cannot allocate device memory at that point: code running inside a stream
- * capture, code whose device memory is owned by a pre-sized pool allocator, or
- * latency-critical paths that must avoid an allocation's implicit device
- * synchronisation.  It calls no cudaMalloc/cudaFree: its scratch is a fixed
- * array of about 46 KB inside the library, held by every device that loads the
- * library until the process exits.
+ * cannot allocate device memory at that point: code whose device memory is
+ * owned by a pre-sized pool allocator (where a stray cudaMalloc can fail or
+ * fragment the pool), or latency-critical paths that must avoid an
+ * allocation's implicit device synchronisation.  It calls no
+ * cudaMalloc/cudaFree: its scratch is a fixed array of about 46 KB inside the
+ * library, held by every device that loads the library until the process
+ * exits.
  *   n_layers, interfaces, k_re, k_im, opt   as for tefmm_plan_create;
  *   stream                                  cudaStream_t for the fit; the call
  *                                           synchronises it before returning;
@@ -310,7 +318,9 @@ int tefmm_plan_set_cross_images(tefmm_plan plan, int n_fits, const int *keys, co
  *   A, Z (out)                              host double[2*32*4*n_layers]: the images
  *                                           of term t at A[2*(32*t + j)], j < term_count[t].
  * The first call on a device looks up the array's device address and should
- * come before any stream capture.  Calls share the array: calls that overlap
+ * come before any stream capture; the address is kept for the process, so a
+ * caller that resets the device (cudaDeviceReset) must not call this entry
+ * point on that device afterwards.  Calls share the array: calls that overlap
  * on the GPU race and must be serialised by the caller.  Sizes beyond the
  * array (more than 32 fits, n_samples > 127, n_images > 32) return
  * TEFMM_ERR_INVALID_ARG; other errors as tefmm_plan_create. */

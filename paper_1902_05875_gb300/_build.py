@@ -45,6 +45,7 @@ def up_to_date():
 
 def build(force=False, verbose=False, extra=()):
     if not force and up_to_date():
+        build_peaks()
         return LIB
     os.makedirs(OBJ_DIR, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -70,7 +71,25 @@ def build(force=False, verbose=False, extra=()):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    build_peaks(force)
     return LIB
+
+
+PEAKS_SRC = os.path.join(HERE, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(OUT_DIR, "libtefmm_peaks.so")
+
+
+def build_peaks(force=False):
+    """The arithmetic-peak measurement library of the benchmark (peaks/peaks.cu)."""
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= os.path.getmtime(PEAKS_SRC):
+        return PEAKS_LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    cmd = [nvcc()] + ARCH + ["-O3", "-Xcompiler", "-fPIC", "-shared", "-o", PEAKS_LIB + ".tmp", PEAKS_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(PEAKS_LIB + ".tmp", PEAKS_LIB)
+    return PEAKS_LIB
 
 
 if __name__ == "__main__":

@@ -163,6 +163,7 @@ int tables(tefmm_plan P, cudaStream_t st) {
 // M2L, L2L, L2P and near field for the sorted charges (ev[3] .. ev[6]), then
 // the device flags of the whole evaluation
 int charge_phases(tefmm_plan P, double *phi, cudaStream_t st) {
+    P->kev_used = 0;
     if (P->opt.precision == TEFMM_MIXED) TRY(m2l_apply_tc(P, st));
     else TRY(m2l_apply(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[8], st));
@@ -262,6 +263,12 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
         o->ms_cross_tables = elapsed(P->ev[7], P->ev[3]);
         o->ms_cross_m2l = elapsed(P->ev[8], P->ev[4]);
     }
+    o->n_m2l_items = P->n_items - P->n_items_cross;
+    o->n_m2l_items_cross = P->n_items_cross;
+    o->n_m2l_kernel_launches = P->kev_used / 2;
+    if (P->kev_used > 0 && cudaEventQuery(P->kev[P->kev_used - 1]) == cudaSuccess)
+        for (int i = 0; i + 1 < P->kev_used; i += 2) o->ms_m2l_kernel += elapsed(P->kev[i], P->kev[i + 1]);
+    for (int l = 0; l < 8; ++l) o->n_p2p_pairs_layer[l] = P->p2p_by_layer[l];
     o->leaf_cap_used = P->leaf_cap_eff;
     o->ms_autotune = P->ms_autotune;
     o->n_tables_built = P->n_tables_built;
@@ -311,5 +318,15 @@ extern "C" int tefmm_export_expansions(tefmm_plan P, double *alpha, double *beta
     size_t n = (size_t)P->n_nodes * P->np * sizeof(cplx);
     if (alpha && n) CUDA_TRY(cudaMemcpy(alpha, P->alpha.p, n, cudaMemcpyDeviceToHost));
     if (beta && n) CUDA_TRY(cudaMemcpy(beta, P->beta.p, n, cudaMemcpyDeviceToHost));
+    return TEFMM_OK;
+}
+
+int kernel_event(tefmm_plan_s *P, cudaStream_t st) {
+    if (P->kev_used == (int)P->kev.size()) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        P->kev.push_back(e);
+    }
+    CUDA_TRY(cudaEventRecord(P->kev[P->kev_used++], st));
     return TEFMM_OK;
 }

@@ -378,6 +378,11 @@ int cross_prepare(tefmm_plan_s *P, cudaStream_t st) {
     P->x_first_chunk = h[1];
     const int nx = P->n_tables - h[0];
     if (nx == 0) return TEFMM_OK;
+    if (P->x_first_chunk < P->n_chunks) {   // items from the first cross-layer chunk on are cross-layer
+        int first_item = 0;
+        CUDA_TRY(cudaMemcpy(&first_item, dp<int>(P->chunk_start) + P->x_first_chunk, 4, cudaMemcpyDeviceToHost));
+        P->n_items_cross = P->n_items - first_item;
+    }
     P->n_xtables = nx;
     std::vector<uint64_t> keys(nx);
     CUDA_TRY(cudaMemcpy(keys.data(), dp<uint64_t>(P->table_slot) + h[0], (size_t)nx * 8,

@@ -12,6 +12,7 @@
 // V2^H V1 (V1^H V1)^{-1} (Hessenberg reduction + shifted QR), and the
 // amplitudes by Householder least squares.  The first level keeps only
 // decaying poles; the second level fits what the first leaves on C_ap2.
+#include <mutex>
 #include <math.h>
 
 #include "internal.cuh"
@@ -779,20 +780,22 @@ int plan_fit_images(tefmm_plan_s *P, cudaStream_t st) {
 // tefmm_fit_images_noalloc: the device DCIM fit without any device allocation.
 //
 // Some callers cannot call cudaMalloc at the point where they need the images
-// of a medium: code that runs while a stream is being captured into a CUDA
-// graph (an allocation there breaks the capture), frameworks that hand all
-// device memory to their own pool allocator up front, and latency-sensitive
-// loops that must not hit the implicit device-wide synchronisation of an
-// allocation.  This entry point runs the same fit kernel as
+// of a medium: frameworks that hand all device memory to their own pool
+// allocator up front (a stray cudaMalloc can fail or fragment that pool), and
+// latency-sensitive loops that must not hit the implicit device-wide
+// synchronisation of an allocation.  This entry point runs the same fit kernel as
 // tefmm_plan_create, with its job descriptors and per-fit results held in the
 // fixed array below instead of freshly allocated scratch; the caller passes
 // the medium in and receives the images in its own host arrays.
 //
 // The array lives in this library's module and is held by every device that
 // loads the library until the process exits.  Its device address is looked up
-// once per device (cudaGetSymbolAddress, with that device current) on the
+// once per device (cudaGetSymbolAddress, with that device current, under a
+// mutex so that concurrent first calls do not race on the lookup) on the
 // first call made on that device; that first call should therefore come
-// before any stream capture.  All calls share the array: two calls whose work
+// before any stream capture.  The address is kept for the process: a caller
+// that resets the device (cudaDeviceReset) must not call this entry point on
+// that device afterwards.  All calls share the array: two calls whose work
 // overlaps on the GPU (different streams or host threads) race on it, so such
 // calls must be serialised by the caller.
 namespace {
@@ -832,6 +835,7 @@ static __device__ __align__(256) unsigned char g_fit_scratch[sizeof(NoAllocScrat
 
 static void *g_fit_scratch_addr[64];
 static bool g_fit_scratch_ready[64];
+static std::mutex g_fit_scratch_mutex;
 
 extern "C" int tefmm_fit_images_noalloc(int n_layers, const double *interfaces, const double *k_re,
                                         const double *k_im, const tefmm_options *opt, void *stream,
@@ -909,13 +913,18 @@ extern "C" int tefmm_fit_images_noalloc(int n_layers, const double *interfaces, 
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return TEFMM_ERR_INVALID_ARG;
-    if (!g_fit_scratch_ready[dev]) {
-        void *ptr = nullptr;
-        CUDA_TRY(cudaGetSymbolAddress(&ptr, g_fit_scratch));
-        g_fit_scratch_addr[dev] = ptr;
-        g_fit_scratch_ready[dev] = true;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_fit_scratch_mutex);
+        if (!g_fit_scratch_ready[dev]) {
+            void *ptr = nullptr;
+            CUDA_TRY(cudaGetSymbolAddress(&ptr, g_fit_scratch));
+            g_fit_scratch_addr[dev] = ptr;
+            g_fit_scratch_ready[dev] = true;
+        }
+        scratch = g_fit_scratch_addr[dev];
     }
-    NoAllocScratch *S = reinterpret_cast<NoAllocScratch *>(g_fit_scratch_addr[dev]);
+    NoAllocScratch *S = reinterpret_cast<NoAllocScratch *>(scratch);
     CUDA_TRY(cudaMemcpyAsync(S->jobs, jobs, nj * sizeof(FitJob), cudaMemcpyHostToDevice, st));
     // counts and residuals start at zero; images are written up to the counts
     CUDA_TRY(cudaMemsetAsync(S->N, 0, sizeof(S->N), st));

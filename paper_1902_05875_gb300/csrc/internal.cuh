@@ -205,6 +205,10 @@ struct tefmm_plan_s {
 
     // timing
     cudaEvent_t ev[12] = {};
+    std::vector<cudaEvent_t> kev;   // pairs of events around the tensor-core M2L launches
+    int kev_used = 0;               // events recorded by the last evaluation
+    int64_t n_items = 0, n_items_cross = 0;   // M2L items (one per translation matrix applied)
+    int64_t p2p_by_layer[8] = {};             // near-field particle pairs per target layer
     double ms_tree = 0, ms_upward = 0, ms_tables = 0, ms_m2l = 0, ms_downward = 0, ms_near = 0;
     int64_t launches = 0;    // kernels of this library launched so far
 };
@@ -257,6 +261,7 @@ int tree_build(tefmm_plan_s *P, const double *sx, const double *sy, const double
                cudaStream_t st);
 int lists_build(tefmm_plan_s *P, cudaStream_t st);
 int check_flags(tefmm_plan_s *P, cudaStream_t st);
+int kernel_event(tefmm_plan_s *P, cudaStream_t st);   // record the next timing event
 // ops.cu
 int upward_pass(tefmm_plan_s *P, cudaStream_t st);
 int m2l_prepare(tefmm_plan_s *P, cudaStream_t st);

@@ -599,8 +599,10 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
             b.chunk_table = a.chunk_table + cb;
             b.chunk_cnt = a.chunk_cnt + cb;
             b.nchunks = ce - cb;
+            TRY(kernel_event(P, st));
             k_m2l_tc<<<(unsigned)((int64_t)(ce - cb) * nsplit), NTHR_TC, sm, st>>>(b);
             P->launches++;
+            TRY(kernel_event(P, st));
         }
         cb = ce;
     }

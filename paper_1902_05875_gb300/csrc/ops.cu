@@ -761,6 +761,8 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
                                                 dp<int>(P->chunk_cnt), nch);
     P->launches++;
     const int64_t nvalid = nvalid_i;
+    P->n_items = nvalid;
+    P->n_items_cross = 0;
     k_chunk_cnt<<<grid_for(nch, 256), 256, 0, st>>>(nch, nvalid, dp<int>(P->chunk_start),
                                                     dp<int>(P->chunk_key), dp<int>(P->chunk_cnt),
                                                     P->chunk_pairs);

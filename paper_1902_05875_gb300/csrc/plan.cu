@@ -239,6 +239,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
     cross_release(P);
     for (int i = 0; i < 12; ++i)
         if (P->ev[i]) cudaEventDestroy(P->ev[i]);
+    for (cudaEvent_t e : P->kev) cudaEventDestroy(e);
     delete P;
     return TEFMM_OK;
 }

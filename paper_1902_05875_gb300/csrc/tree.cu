@@ -535,10 +535,12 @@ __global__ void k_csr_fill(int off, int cnt, int l, ListLayout Ly, const int *__
     }
 }
 
+// near-field particle pairs: out[0] in all, out[1 + l] with targets in layer l
 __global__ void k_count_pairs(int n_nodes, const int *__restrict__ near_ptr,
                               const int *__restrict__ near_src, const int *__restrict__ s0,
                               const int *__restrict__ s1, const int *__restrict__ t0,
-                              const int *__restrict__ t1, unsigned long long *out) {
+                              const int *__restrict__ t1, const int *__restrict__ layer,
+                              unsigned long long *out) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_nodes) return;
     unsigned long long acc = 0;
@@ -547,7 +549,10 @@ __global__ void k_count_pairs(int n_nodes, const int *__restrict__ near_ptr,
         int s = near_src[a];
         acc += (unsigned long long)nt * (unsigned long long)(s1[s] - s0[s]);
     }
-    if (acc) atomicAdd(out, acc);
+    if (acc) {
+        atomicAdd(out, acc);
+        atomicAdd(out + 1 + (layer[t] & 7), acc);
+    }
 }
 
 __global__ void k_layer_mismatch(int n_nodes, const int *__restrict__ layer,
@@ -881,17 +886,18 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
                                                             dp<int>(P->near_src), dp<int>(P->flags));
         P->launches++;
     }
-    TRY(dbuf_ensure(P->counters, 64));
-    CUDA_TRY(cudaMemsetAsync(P->counters.p, 0, 8, st));
+    TRY(dbuf_ensure(P->counters, 128));
+    CUDA_TRY(cudaMemsetAsync(P->counters.p, 0, 72, st));
     if (nn > 0) {
         k_count_pairs<<<grid_for(nn, 128), 128, 0, st>>>(
             nn, dp<int>(P->near_ptr), dp<int>(P->near_src), dp<int>(P->n_s0), dp<int>(P->n_s1),
-            dp<int>(P->n_t0), dp<int>(P->n_t1), dp<unsigned long long>(P->counters));
+            dp<int>(P->n_t0), dp<int>(P->n_t1), dp<int>(P->n_layer), dp<unsigned long long>(P->counters));
         P->launches++;
     }
-    unsigned long long np2p = 0;
-    CUDA_TRY(cudaMemcpyAsync(&np2p, P->counters.p, 8, cudaMemcpyDeviceToHost, st));
+    unsigned long long np2p[9] = {};
+    CUDA_TRY(cudaMemcpyAsync(np2p, P->counters.p, 72, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    P->n_p2p_pairs = (int64_t)np2p;
+    P->n_p2p_pairs = (int64_t)np2p[0];
+    for (int l = 0; l < 8; ++l) P->p2p_by_layer[l] = (int64_t)np2p[1 + l];
     return TEFMM_OK;
 }

@@ -42,7 +42,10 @@ class Stats(ctypes.Structure):
                 ("n_cross_fits_last", ctypes.c_int), ("ms_cross_fit", ctypes.c_double),
                 ("fit_max_resid_cross", ctypes.c_double), ("ms_cross_tables", ctypes.c_double),
                 ("ms_cross_m2l", ctypes.c_double), ("leaf_cap_used", ctypes.c_int),
-                ("ms_autotune", ctypes.c_double), ("n_tables_built", ctypes.c_int)]
+                ("ms_autotune", ctypes.c_double), ("n_tables_built", ctypes.c_int),
+                ("n_m2l_items", ctypes.c_int64), ("n_m2l_items_cross", ctypes.c_int64),
+                ("ms_m2l_kernel", ctypes.c_double), ("n_m2l_kernel_launches", ctypes.c_int),
+                ("n_p2p_pairs_layer", ctypes.c_int64 * 8)]
 
 
 EXPORTED = [
@@ -222,12 +225,18 @@ class Plan:
         if q.dtype != torch.complex128 or not q.is_cuda or not q.is_contiguous():
             raise ValueError("q must be a contiguous complex128 CUDA tensor")
         ns, nt = sx.numel(), tx.numel()
-        self._n_targets = nt
+        if sy.numel() != ns or sz.numel() != ns or ty.numel() != nt or tz.numel() != nt:
+            raise ValueError("coordinate arrays of one point set must have equal lengths")
+        if q.numel() != ns:
+            raise ValueError("q must have one entry per source")
         if out is None:
             out = torch.empty(nt, dtype=torch.complex128, device=sx.device)
+        elif out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous() or out.numel() != nt:
+            raise ValueError("out must be a contiguous complex128 CUDA tensor with one entry per target")
         vp = lambda t: ctypes.c_void_p(t.data_ptr())
         _check(self.lib.tefmm_eval(self.h, ns, vp(sx), vp(sy), vp(sz), vp(q), nt, vp(tx), vp(ty),
                                    vp(tz), vp(out), _stream_handle(stream)), "tefmm_eval")
+        self._n_sources, self._n_targets = ns, nt
         return out
 
     def set_points(self, sx, sy, sz, tx=None, ty=None, tz=None, stream=None):
@@ -240,11 +249,14 @@ class Plan:
         for a in (sx, sy, sz, tx, ty, tz):
             if a.dtype != torch.float64 or not a.is_cuda or not a.is_contiguous():
                 raise ValueError("coordinates must be contiguous float64 CUDA tensors")
+        ns, nt = sx.numel(), tx.numel()
+        if sy.numel() != ns or sz.numel() != ns or ty.numel() != nt or tz.numel() != nt:
+            raise ValueError("coordinate arrays of one point set must have equal lengths")
         vp = lambda t: ctypes.c_void_p(t.data_ptr())
-        self._n_targets = tx.numel()
-        self._device = sx.device
-        _check(self.lib.tefmm_set_points(self.h, sx.numel(), vp(sx), vp(sy), vp(sz), tx.numel(), vp(tx),
+        self._n_sources = self._n_targets = None      # unknown until the call succeeds
+        _check(self.lib.tefmm_set_points(self.h, ns, vp(sx), vp(sy), vp(sz), nt, vp(tx),
                                          vp(ty), vp(tz), _stream_handle(stream)), "tefmm_set_points")
+        self._n_sources, self._n_targets = ns, nt
 
     def apply(self, q, out=None, stream=None):
         """``tefmm_apply``: potentials of charges q (contiguous complex128 CUDA
@@ -253,9 +265,12 @@ class Plan:
         if q.dtype != torch.complex128 or not q.is_cuda or not q.is_contiguous():
             raise ValueError("q must be a contiguous complex128 CUDA tensor")
         n = getattr(self, "_n_targets", None)
+        ns = getattr(self, "_n_sources", None)
+        if n is None or ns is None:
+            raise RuntimeError("apply() needs a successful set_points() or eval() first")
+        if q.numel() != ns:
+            raise ValueError("q must have one entry per source of the last set_points() / eval()")
         if out is None:
-            if n is None:
-                raise RuntimeError("apply() needs set_points() or eval() first")
             out = torch.empty(n, dtype=torch.complex128, device=q.device)
         elif out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous() or \
                 (n is not None and out.numel() != n):
@@ -286,7 +301,9 @@ class Plan:
     def stats(self):
         s = Stats()
         _check(self.lib.tefmm_get_stats(self.h, ctypes.byref(s)), "tefmm_get_stats")
-        return {f: getattr(s, f) for f, _ in Stats._fields_}
+        out = {f: getattr(s, f) for f, _ in Stats._fields_}
+        out["n_p2p_pairs_layer"] = list(s.n_p2p_pairs_layer)
+        return out
 
     def images(self):
         nt_ = ctypes.c_int()

@@ -58,16 +58,36 @@ def test_clock_record_without_sampler():
     assert c["sm_mhz"] is None and c["reasons"]
 
 
-def test_cpu_baseline_line():
+def test_cpu_baseline_line(monkeypatch):
+    """The CPU baseline line is the oracle TE-FMM sample's throughput with the
+    cores it used (CPU time over wall time)."""
     import bench
-    cb = bench.cpu_baseline_from(100, 2_000_000, 40.0, "w")
+    monkeypatch.setattr(bench, "oracle_fmm_sample", lambda w, n, warm=True: (20.0, 1.5, "sample", n * 2000))
+    cb = bench.cpu_baseline(None, n_targets=2)
     assert cb["kind"] == "oracle" and cb["unit"] == bench.UNIT
-    assert cb["value"] == pytest.approx(100 * 2e6 / 40.0)
-    assert cb["cores"] == os.cpu_count()
+    assert cb["value"] == pytest.approx(2 * 2000 / 20.0)
+    assert cb["cores"] == 1.5 and cb["sample"] == "sample"
+
+
+def test_stored_direct_sum_reference():
+    """The stored 1000-target direct sum of the 2M workload: default_rng(1)'s
+    sample of the 2M points, finite non-zero values, read in order."""
+    import numpy as np
+    import bench
+
+    class Wk:
+        name = "three_layer_slabs_n2M_p10"
+        src = np.zeros((2_000_000, 3))
+    idx, ref, where = bench.reference_at(Wk, 1000)
+    assert where.startswith("tests")
+    assert np.array_equal(idx, np.random.default_rng(1).choice(2_000_000, 1000, replace=False))
+    assert np.all(np.isfinite(ref)) and np.all(np.abs(ref) > 0)
+    idx2, ref2, _ = bench.reference_at(Wk, 100)
+    assert np.array_equal(idx2, idx[:100]) and np.array_equal(ref2, ref[:100])
 
 
 def test_err_stats_follow_the_papers_measures():
-    """Err_2 and Err_max (Sec. 4), overall and per layer, on a hand-made case."""
+    """Err_2 and Err_max (Sec. 5), overall and per layer, on a hand-made case."""
     import numpy as np
     import bench
     ref = np.array([1.0, 2.0j, -2.0, 4.0])

@@ -56,3 +56,44 @@ def test_apply_binding_checks_arguments_without_gpu():
         tefmm.Plan.set_points(plan, x, x, x)
     with pytest.raises(ValueError):
         tefmm.Plan.apply(plan, torch.zeros(4, dtype=torch.complex128))
+
+
+class _FakeCuda:
+    """Stands in for a contiguous CUDA tensor (dtype, length) so that the
+    binding's argument checks run on a machine without a GPU."""
+
+    def __init__(self, dtype, n):
+        self.dtype, self.n, self.is_cuda, self.device = dtype, n, True, "cuda:0"
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self.n
+
+    def data_ptr(self):
+        raise AssertionError("the library must not be called")
+
+
+def test_eval_and_apply_refuse_wrong_lengths_without_gpu():
+    """eval() and apply() check that q has one entry per source and out one
+    per target before the library is called (a short array would be read or
+    written past its end on the device)."""
+    torch = pytest.importorskip("torch")
+    from paper_1902_05875_gb300 import tefmm
+    plan = object.__new__(tefmm.Plan)
+    f64 = lambda n: _FakeCuda(torch.float64, n)
+    c128 = lambda n: _FakeCuda(torch.complex128, n)
+    with pytest.raises(ValueError):
+        tefmm.Plan.eval(plan, f64(5), f64(5), f64(5), c128(4))                     # short q
+    with pytest.raises(ValueError):
+        tefmm.Plan.eval(plan, f64(5), f64(5), f64(5), c128(5), out=c128(4))        # short out
+    with pytest.raises(ValueError):
+        tefmm.Plan.eval(plan, f64(5), f64(5), f64(5), c128(5), f64(3), f64(3), f64(2))
+    with pytest.raises(RuntimeError):
+        tefmm.Plan.apply(plan, c128(5))                                            # no points yet
+    plan._n_sources, plan._n_targets = 5, 3
+    with pytest.raises(ValueError):
+        tefmm.Plan.apply(plan, c128(4))                                            # short q
+    with pytest.raises(ValueError):
+        tefmm.Plan.apply(plan, c128(5), out=c128(5))                               # out of the wrong length
