@@ -49,6 +49,8 @@ extern "C" {
 #define TEFMM_ERR_LIST_OVERFLOW (-7)      /* an interaction list exceeded its capacity   */
 #define TEFMM_ERR_NOT_IMPLEMENTED (-8)    /* configuration not supported by this build   */
 #define TEFMM_ERR_DEVICE_CHECK (-9)       /* a device-side consistency check failed      */
+#define TEFMM_ERR_TIMEOUT (-10)           /* a bounded device wait ran out (the kernel
+                                             skipped its output and released its TMEM)  */
 
 #define TEFMM_FP64 0   /* every step in FP64                                          */
 #define TEFMM_MIXED 1  /* M2L on tensor cores and P2P in FP32; FP64 tables and sums   */
@@ -165,7 +167,8 @@ int tefmm_plan_destroy(tefmm_plan plan);
  *   d_phi               output potentials (device, 2*nt doubles), overwritten.
  * Errors: INVALID_ARG, POINT_ON_INTERFACE, OUT_OF_DOMAIN, OOM, CUDA,
  *         LIST_OVERFLOW, DEVICE_CHECK (an M2L pair offset outside the key
- *         range, or a bounded device wait that ran out).  The call returns
+ *         range), TIMEOUT (a bounded device wait of the tensor-core M2L ran
+ *         out), NOT_IMPLEMENTED (wavenumber rule needing offsets above 15).  The call returns
  *         when the result is complete on the stream, with any device-detected
  *         error of this evaluation.  ns == 0 or nt == 0 writes zeros. */
 int tefmm_eval(tefmm_plan plan, int64_t ns, const double *d_sx, const double *d_sy,
@@ -212,6 +215,34 @@ typedef struct {
  * INVALID_ARG for bad arguments, CUDA for stream/event failures. */
 int tefmm_eval_batched(int n, tefmm_plan *plans, const tefmm_batch_item *items, int n_workers,
                        void *stream, int *status);
+
+/* Device-detected errors of the plan's work so far (reads the plan's device
+ * flags, synchronising the stream): the status tefmm_eval / tefmm_apply would
+ * have returned.  Work captured into a CUDA graph cannot report them when it
+ * runs; read them with this call after the graph has run.  Flags accumulate
+ * from the plan's last tefmm_eval / tefmm_set_points on.  No counterpart in
+ * the paper. */
+int tefmm_plan_status(tefmm_plan plan, void *stream);
+
+/* Batch graph: the charge phases of n plans (tefmm_apply of plans[i] with
+ * device charges q[i] and potentials phi[i], each plan on the points of its
+ * last tefmm_set_points or tefmm_eval) captured once into one CUDA graph, each
+ * plan a parallel branch, and replayed with one cudaGraphLaunch per batch:
+ * the batched workload of many independent media run as a single launch.
+ * create runs one tefmm_apply per plan on ``stream`` first (buffers are sized
+ * outside the capture), then captures on ``stream`` (relaxed mode).  The
+ * pointers q[i] and phi[i] are baked into the graph: write new charges into
+ * the same buffers before each launch.  Plans must be distinct and must not be
+ * used by other calls while the graph exists (tefmm_set_points or tefmm_eval
+ * on one of them invalidates the graph).  Errors found on the device are read
+ * with tefmm_plan_status.  No counterpart in the paper.
+ * Errors: INVALID_ARG (n <= 0, NULL, a plan without points, a repeated plan),
+ * CUDA, and the errors of tefmm_apply. */
+typedef struct tefmm_batch_graph_s *tefmm_batch_graph;
+int tefmm_batch_graph_create(int n, tefmm_plan *plans, const double *const *q, double *const *phi,
+                             void *stream, tefmm_batch_graph *out);
+int tefmm_batch_graph_launch(tefmm_batch_graph graph, void *stream);
+int tefmm_batch_graph_destroy(tefmm_batch_graph graph);
 
 /* Same as tefmm_eval with HOST arrays: copies the inputs to plan-owned device
  * buffers, evaluates, copies Phi back, and synchronises the stream. */
@@ -297,6 +328,23 @@ int tefmm_plan_cross_images(tefmm_plan plan, int *n_fits, int *keys, int *counts
  * more than 32 images). */
 int tefmm_plan_set_cross_images(tefmm_plan plan, int n_fits, const int *keys, const int *counts,
                                 const double *A, const double *Z);
+
+/* ---- test hooks for the error paths --------------------------------------
+ * No counterpart in the paper; used by the tests.
+ * tefmm_debug_inject(kind, n): make the n-th (n >= 1) device allocation
+ * (kind TEFMM_INJECT_ALLOC, returned as TEFMM_ERR_OOM) or the n-th batch of
+ * DCIM fits (kind TEFMM_INJECT_FIT: plan creation's same-layer fits or an
+ * evaluation's cross-layer fits, returned as TEFMM_ERR_FIT_FAILED) made by
+ * the library from now on fail, once; kind 0 clears both.  Process-wide.
+ * tefmm_debug_wait_probe(plan, ms, stream): one kernel waits, bounded by ms
+ * milliseconds of device time (1..2000), on an mbarrier that nothing
+ * completes; it raises the plan's timeout flag, and the call returns
+ * TEFMM_ERR_TIMEOUT, the status a run-out wait of the tensor-core M2L gives.
+ * Errors: INVALID_ARG. */
+#define TEFMM_INJECT_ALLOC 1
+#define TEFMM_INJECT_FIT 2
+int tefmm_debug_inject(int kind, int n);
+int tefmm_debug_wait_probe(tefmm_plan plan, int ms, void *stream);
 
 /* ---- fit without device allocation -------------------------------------
  * The paper has no counterpart to this call; it is a convenience of this

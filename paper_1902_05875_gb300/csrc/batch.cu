@@ -69,3 +69,88 @@ extern "C" int tefmm_eval_batched(int n, tefmm_plan *plans, const tefmm_batch_it
     }
     return err;
 }
+
+// ---------------------------------------------------------------------------
+// Batch graph: the charge phases (tefmm_apply) of many plans, each on the
+// points of its last tefmm_set_points, captured once into one CUDA graph and
+// then replayed by a single cudaGraphLaunch per batch.  Each plan's apply is
+// its own branch of the graph (forked from and joined to the caller's
+// stream), so the instances' kernels overlap on the GPU as one launch.
+struct tefmm_batch_graph_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    std::vector<tefmm_plan> plans;
+};
+
+static void batch_graph_free(tefmm_batch_graph_s *G) {
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    for (cudaEvent_t e : G->events) cudaEventDestroy(e);
+    for (cudaStream_t s : G->streams) cudaStreamDestroy(s);
+    delete G;
+}
+
+extern "C" int tefmm_batch_graph_create(int n, tefmm_plan *plans, const double *const *q, double *const *phi,
+                                        void *stream, tefmm_batch_graph *out) {
+    if (!out || n <= 0 || !plans || !q || !phi) return TEFMM_ERR_INVALID_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i] || !plans[i]->geom_ready || !q[i] || !phi[i]) return TEFMM_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return TEFMM_ERR_INVALID_ARG;   // a plan is not shared
+    }
+    cudaStream_t cs = (cudaStream_t)stream;
+    // one apply per plan outside the capture: sizes its buffers (no allocation
+    // may happen inside a capture) and checks that it runs
+    for (int i = 0; i < n; ++i) TRY(tefmm_apply(plans[i], q[i], phi[i], stream));
+    tefmm_batch_graph_s *G = new tefmm_batch_graph_s();
+    G->plans.assign(plans, plans + n);
+    int err = TEFMM_OK;
+    G->streams.resize(n, nullptr);
+    G->events.resize(n + 1, nullptr);
+    for (int i = 0; i < n && err == TEFMM_OK; ++i)
+        if (cudaStreamCreateWithFlags(&G->streams[i], cudaStreamNonBlocking) != cudaSuccess) err = TEFMM_ERR_CUDA;
+    for (int i = 0; i <= n && err == TEFMM_OK; ++i)
+        if (cudaEventCreateWithFlags(&G->events[i], cudaEventDisableTiming) != cudaSuccess) err = TEFMM_ERR_CUDA;
+    if (err != TEFMM_OK) {
+        batch_graph_free(G);
+        return err;
+    }
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        batch_graph_free(G);
+        return TEFMM_ERR_CUDA;
+    }
+    if (cudaEventRecord(G->events[n], cs) != cudaSuccess) err = TEFMM_ERR_CUDA;
+    for (int i = 0; i < n && err == TEFMM_OK; ++i) {
+        if (cudaStreamWaitEvent(G->streams[i], G->events[n], 0) != cudaSuccess) err = TEFMM_ERR_CUDA;
+        if (err == TEFMM_OK) err = tefmm_apply(plans[i], q[i], phi[i], G->streams[i]);
+        if (err == TEFMM_OK && (cudaEventRecord(G->events[i], G->streams[i]) != cudaSuccess ||
+                                cudaStreamWaitEvent(cs, G->events[i], 0) != cudaSuccess))
+            err = TEFMM_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    G->graph = graph;
+    if (err == TEFMM_OK && ec != cudaSuccess) err = TEFMM_ERR_CUDA;
+    if (err == TEFMM_OK && cudaGraphInstantiate(&G->exec, G->graph, 0) != cudaSuccess) err = TEFMM_ERR_CUDA;
+    if (err != TEFMM_OK) {
+        cudaGetLastError();
+        batch_graph_free(G);
+        return err;
+    }
+    *out = G;
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_batch_graph_launch(tefmm_batch_graph G, void *stream) {
+    if (!G || !G->exec) return TEFMM_ERR_INVALID_ARG;
+    CUDA_TRY(cudaGraphLaunch(G->exec, (cudaStream_t)stream));
+    return TEFMM_OK;
+}
+
+extern "C" int tefmm_batch_graph_destroy(tefmm_batch_graph G) {
+    if (G) batch_graph_free(G);
+    return TEFMM_OK;
+}

@@ -15,6 +15,7 @@ extern "C" const char *tefmm_status_string(int s) {
         case TEFMM_ERR_LIST_OVERFLOW: return "interaction list capacity exceeded";
         case TEFMM_ERR_NOT_IMPLEMENTED: return "configuration not implemented";
         case TEFMM_ERR_DEVICE_CHECK: return "device-side check failed";
+        case TEFMM_ERR_TIMEOUT: return "a bounded device wait ran out";
         default: return "unknown status";
     }
 }
@@ -176,7 +177,12 @@ int charge_phases(tefmm_plan P, double *phi, cudaStream_t st) {
     CUDA_TRY(cudaEventRecord(P->ev[6], st));
     CUDA_TRY(cudaGetLastError());
     // flags raised after the list checks (M2L key range, bounded waits of the
-    // tensor-core kernel) are reported by this call, before the next one resets them
+    // tensor-core kernel) are reported by this call, before the next one resets
+    // them; work queued into a stream capture cannot wait for them, and
+    // tefmm_plan_status reads them after the graph has run
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return TEFMM_OK;
     return check_flags(P, st);
 }
 
@@ -329,4 +335,44 @@ int kernel_event(tefmm_plan_s *P, cudaStream_t st) {
     }
     CUDA_TRY(cudaEventRecord(P->kev[P->kev_used++], st));
     return TEFMM_OK;
+}
+
+extern "C" int tefmm_plan_status(tefmm_plan P, void *stream) {
+    if (!P) return TEFMM_ERR_INVALID_ARG;
+    if (!P->flags.p) return TEFMM_OK;
+    return check_flags(P, (cudaStream_t)stream);
+}
+
+namespace {
+// a bounded wait on an mbarrier that nothing completes: the wait runs out after
+// `ms` milliseconds of device time (%globaltimer) and raises FLAG_TIMEOUT
+__global__ void k_wait_probe(int *flags, unsigned long long ms) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(b));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (;;) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     "selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(b) : "memory");
+        if (ok) return;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > ms * 1000000ULL) break;
+    }
+    atomicOr(flags, FLAG_TIMEOUT);
+}
+}  // namespace
+
+extern "C" int tefmm_debug_wait_probe(tefmm_plan P, int ms, void *stream) {
+    if (!P || ms < 1 || ms > 2000) return TEFMM_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(dbuf_ensure(P->flags, 64));
+    CUDA_TRY(cudaMemsetAsync(P->flags.p, 0, 64, st));
+    k_wait_probe<<<1, 32, 0, st>>>(dp<int>(P->flags), (unsigned long long)ms);
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return check_flags(P, st);
 }

@@ -761,6 +761,7 @@ int plan_fit_images(tefmm_plan_s *P, cudaStream_t st) {
     cudaFree(dZ);
     cudaFree(dN);
     cudaFree(dR);
+    if (inject_fit_failure()) return TEFMM_ERR_FIT_FAILED;
     for (size_t i = 0; i < P->terms.size(); ++i) {
         int jb = job_of[i];
         TermDesc &t = P->terms[i];
@@ -1067,6 +1068,7 @@ int fit_cross_jobs(tefmm_plan_s *P, const std::vector<CrossFitKey> &keys, cudaSt
     cudaFree(dZ);
     cudaFree(dN);
     cudaFree(dR);
+    if (inject_fit_failure()) return TEFMM_ERR_FIT_FAILED;
     for (int i = 0; i < nj; ++i) {
         if (!(hR[i] == hR[i])) return TEFMM_ERR_FIT_FAILED;
         CrossFitVal v;

@@ -22,6 +22,7 @@
 #define FLAG_LIST_OVERFLOW 4
 #define FLAG_CROSS_LAYER 8
 #define FLAG_CHECK 16
+#define FLAG_TIMEOUT 32         // a bounded device wait ran out
 
 // ---------------------------------------------------------------- complex
 struct cplx {
@@ -88,6 +89,9 @@ struct DBuf {
     size_t cap = 0;
 };
 int dbuf_ensure(DBuf &b, size_t bytes);   // grow (contents not preserved)
+// test hooks (tefmm_debug_inject): true when the next allocation / fit is to fail
+bool inject_alloc_failure();
+bool inject_fit_failure();
 void dbuf_free(DBuf &b);
 
 template <class T>
@@ -179,6 +183,7 @@ struct tefmm_plan_s {
     int n_tables = 0;
     int n_tables_built = 0;   // tables computed by the recurrence (the rest by symmetry)
     int64_t n_chunks = 0;
+    std::vector<int> chunk_key_host;   // mixed form: chunk -> table, copied when the geometry is built
     int chunk_pairs = 16;     // pairs per M2L work chunk (FP64 SIMT: 16, tensor cores: 512)
 
     // cross-layer components: fitted images (cached per root-cube geometry),

@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(NTHR_TC, 1) k_m2l_tc(TcArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (s_fail && tid == 0) atomicOr(a.flags, FLAG_CHECK);
+    if (s_fail && tid == 0) atomicOr(a.flags, FLAG_TIMEOUT);   // only a bounded wait sets s_fail
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(a.tcols));
     }
@@ -578,10 +578,8 @@ int tc_launch(tefmm_plan_s *P, cudaStream_t st, int c0, int nch, const cplx *alp
     const int kb = (int)std::max<size_t>(1, std::min<size_t>((size_t)ntab, wcap / wkey));
     TRY(dbuf_ensure(Wbuf, (size_t)kb * wkey));
     a.W = dp<float>(Wbuf);
-    std::vector<int> ctab(nch);
-    CUDA_TRY(cudaMemcpyAsync(ctab.data(), dp<int>(P->chunk_key) + c0, (size_t)nch * 4,
-                             cudaMemcpyDeviceToHost, st));
-    CUDA_TRY(cudaStreamSynchronize(st));
+    if ((int64_t)P->chunk_key_host.size() < (int64_t)c0 + nch) return TEFMM_ERR_DEVICE_CHECK;
+    const int *ctab = P->chunk_key_host.data() + c0;    // host copy made with the geometry
     TRY(smem_optin(k_wgen));
     const size_t sm = m2l_tc_smem(np, MT, 0);
     TRY(smem_optin(k_m2l_tc));

@@ -770,6 +770,15 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     CUDA_TRY(cudaGetLastError());
     P->x_first_table = P->n_tables;     // narrowed by cross_prepare when cross keys exist
     P->x_first_chunk = P->n_chunks;
+    // the tensor-core M2L launches key batches by chunk ranges: their host copy
+    // is taken here, once per geometry, so that later applies need no host wait
+    P->chunk_key_host.clear();
+    if (P->opt.precision == TEFMM_MIXED && nch > 0) {
+        P->chunk_key_host.resize(nch);
+        CUDA_TRY(cudaMemcpyAsync(P->chunk_key_host.data(), P->chunk_key.p, (size_t)nch * 4,
+                                 cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
     return TEFMM_OK;
 }
 

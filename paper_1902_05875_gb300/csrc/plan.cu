@@ -2,7 +2,37 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "internal.cuh"
+
+// Fault injection for the tests of the error paths (tefmm_debug_inject):
+// countdowns of device allocations and of DCIM fit batches; the one that
+// reaches zero fails.  -1 / 0: nothing injected.
+static std::atomic<int> g_inject_alloc{0}, g_inject_fit{0};
+
+static bool countdown_hits(std::atomic<int> &c) {
+    int v = c.load();
+    while (v > 0) {
+        if (c.compare_exchange_weak(v, v - 1)) return v == 1;
+    }
+    return false;
+}
+bool inject_alloc_failure() { return countdown_hits(g_inject_alloc); }
+bool inject_fit_failure() { return countdown_hits(g_inject_fit); }
+
+extern "C" int tefmm_debug_inject(int kind, int n) {
+    if (kind == 0) {
+        g_inject_alloc = 0;
+        g_inject_fit = 0;
+        return TEFMM_OK;
+    }
+    if (n < 1) return TEFMM_ERR_INVALID_ARG;
+    if (kind == TEFMM_INJECT_ALLOC) g_inject_alloc = n;
+    else if (kind == TEFMM_INJECT_FIT) g_inject_fit = n;
+    else return TEFMM_ERR_INVALID_ARG;
+    return TEFMM_OK;
+}
 
 int dbuf_ensure(DBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -10,6 +40,7 @@ int dbuf_ensure(DBuf &b, size_t bytes) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
+    if (inject_alloc_failure()) return TEFMM_ERR_OOM;
     size_t cap = bytes + bytes / 4 + 256;
     cudaError_t e = cudaMalloc(&b.p, cap);
     if (e != cudaSuccess) {

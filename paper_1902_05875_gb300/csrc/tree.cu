@@ -591,6 +591,7 @@ int grow_nodes(tefmm_plan_s *P, int64_t need, int64_t have, cudaStream_t st) {
         if (b->cap >= (size_t)need * sizeof(int)) continue;
         size_t ncap = (size_t)(need * 2) * sizeof(int);
         void *np_ = nullptr;
+        if (inject_alloc_failure()) return TEFMM_ERR_OOM;
         CUDA_TRY(cudaMalloc(&np_, ncap));
         if (have > 0 && b->p) CUDA_TRY(cudaMemcpyAsync(np_, b->p, have * sizeof(int), cudaMemcpyDeviceToDevice, st));
         CUDA_TRY(cudaStreamSynchronize(st));
@@ -629,6 +630,7 @@ int check_flags(tefmm_plan_s *P, cudaStream_t st) {
     if (f & FLAG_OUT_OF_DOMAIN) return TEFMM_ERR_OUT_OF_DOMAIN;
     if (f & FLAG_LIST_OVERFLOW) return TEFMM_ERR_LIST_OVERFLOW;
     if (f & FLAG_CROSS_LAYER) return TEFMM_ERR_NOT_IMPLEMENTED;
+    if (f & FLAG_TIMEOUT) return TEFMM_ERR_TIMEOUT;
     if (f & FLAG_CHECK) return TEFMM_ERR_DEVICE_CHECK;
     return TEFMM_OK;
 }

@@ -16,6 +16,11 @@ from . import _build
 
 OK = 0
 ERR_INVALID_ARG = -1
+ERR_OOM = -4
+ERR_FIT_FAILED = -6
+ERR_TIMEOUT = -10
+INJECT_ALLOC = 1
+INJECT_FIT = 2
 _STATUS = {}
 
 FP64 = 0
@@ -54,6 +59,8 @@ EXPORTED = [
     "tefmm_plan_get_images", "tefmm_plan_set_images", "tefmm_export_tree", "tefmm_export_lists",
     "tefmm_export_expansions", "tefmm_fit_images_noalloc", "tefmm_plan_cross_images",
     "tefmm_eval_batched", "tefmm_set_points", "tefmm_apply", "tefmm_plan_set_cross_images",
+    "tefmm_plan_status", "tefmm_batch_graph_create", "tefmm_batch_graph_launch", "tefmm_batch_graph_destroy",
+    "tefmm_debug_inject", "tefmm_debug_wait_probe",
 ]
 
 _lib = None
@@ -96,6 +103,14 @@ def load(build_if_needed=True):
     lib.tefmm_export_lists.argtypes = [P, I64, I64, I, I, I, I]
     lib.tefmm_export_expansions.argtypes = [P, D, D]
     lib.tefmm_plan_set_cross_images.argtypes = [P, ctypes.c_int, I, I, D, D]
+    lib.tefmm_plan_status.argtypes = [P, P]
+    lib.tefmm_debug_inject.argtypes = [ctypes.c_int, ctypes.c_int]
+    lib.tefmm_debug_wait_probe.argtypes = [P, ctypes.c_int, P]
+    lib.tefmm_batch_graph_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                             P, ctypes.POINTER(P)]
+    lib.tefmm_batch_graph_launch.argtypes = [P, P]
+    lib.tefmm_batch_graph_destroy.argtypes = [P]
     lib.tefmm_eval_batched.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
                                        ctypes.POINTER(BatchItem), ctypes.c_int, P, I]
     lib.tefmm_fit_images_noalloc.argtypes = [ctypes.c_int, D, D, D, ctypes.POINTER(Options), P,
@@ -164,6 +179,47 @@ def eval_batched(plans, instances, n_workers=8, stream=None):
     _check(lib.tefmm_eval_batched(n, hs, items, int(n_workers), _stream_handle(stream), st),
            "tefmm_eval_batched")
     return list(st[:n])
+
+
+class BatchGraph:
+    """``tefmm_batch_graph_create``: the charge phases (apply) of several plans,
+    each on the points of its last set_points / eval, captured into one CUDA
+    graph; ``launch()`` replays the whole batch with one graph launch.  qs[i]
+    and phis[i] are contiguous complex128 CUDA tensors that stay bound to the
+    graph: write new charges into qs[i] in place between launches."""
+
+    def __init__(self, plans, qs, phis, stream=None):
+        import torch
+        self.lib = load()
+        n = len(plans)
+        for q, phi, pl in zip(qs, phis, plans):
+            for t in (q, phi):
+                if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+                    raise ValueError("charges and potentials must be contiguous complex128 CUDA tensors")
+            if q.numel() != getattr(pl, "_n_sources", None) or phi.numel() != getattr(pl, "_n_targets", None):
+                raise ValueError("q and phi must match the plan's last set_points() / eval()")
+        self._keep = (list(plans), list(qs), list(phis))
+        hp = (ctypes.c_void_p * n)(*[pl.h.value for pl in plans])
+        hq = (ctypes.c_void_p * n)(*[q.data_ptr() for q in qs])
+        hphi = (ctypes.c_void_p * n)(*[phi.data_ptr() for phi in phis])
+        h = ctypes.c_void_p()
+        _check(self.lib.tefmm_batch_graph_create(n, hp, hq, hphi, _stream_handle(stream), ctypes.byref(h)),
+               "tefmm_batch_graph_create")
+        self.h = h
+
+    def launch(self, stream=None):
+        _check(self.lib.tefmm_batch_graph_launch(self.h, _stream_handle(stream)), "tefmm_batch_graph_launch")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.tefmm_batch_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:
@@ -297,6 +353,10 @@ class Plan:
                "tefmm_eval_host")
         return phi[0::2] + 1j * phi[1::2]
 
+    def status(self, stream=None):
+        """``tefmm_plan_status``: raises if the plan's device work so far flagged an error."""
+        _check(self.lib.tefmm_plan_status(self.h, _stream_handle(stream)), "tefmm_plan_status")
+
     # -- inspection ----------------------------------------------------------
     def stats(self):
         s = Stats()
@@ -421,3 +481,9 @@ class Plan:
         b = np.zeros(2 * n * self.np, np.float64)
         _check(self.lib.tefmm_export_expansions(self.h, _dptr(a), _dptr(b)), "export_expansions")
         return (a[0::2] + 1j * a[1::2]).reshape(n, self.np), (b[0::2] + 1j * b[1::2]).reshape(n, self.np)
+
+
+def debug_inject(kind, n=1):
+    """``tefmm_debug_inject`` (test hook): the n-th device allocation (INJECT_ALLOC)
+    or DCIM fit batch (INJECT_FIT) from now on fails once; kind 0 clears."""
+    _check(load().tefmm_debug_inject(int(kind), int(n)), "tefmm_debug_inject")

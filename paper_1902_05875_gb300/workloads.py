@@ -143,3 +143,60 @@ def batched_instances(n_inst, p=6, seed=2, n_min=1000, n_max=64000, n_images=8, 
         out.append(Workload(f"batch{i}_L{nl}_n{n}", list(map(float, d)), k, zext, src, q, p, leaf_cap,
                             n_images))
     return out
+
+
+def multi_layer_slabs(n_per_layer, n_layers, p, leaf_cap, seed=0, n_images=16, name=None):
+    """n_layers layers (2..8) with interfaces at 0, -1, -2, ..., real
+    wavenumbers 1.5, 2.0, 2.5, ... from the top; n_per_layer uniform points per
+    layer in [-0.6,0.6]^2 x a slab 0.2 inside each interface (outer slabs 0.6
+    thick), top layer first."""
+    rng = np.random.default_rng(seed)
+    d = [0.0] + [-float(m) for m in range(1, n_layers - 1)]
+    k = [1.5 + 0.5 * l for l in range(n_layers)]
+    zext = []
+    for l in range(n_layers):
+        top = d[l - 1] - 0.2 if l > 0 else d[0] + 0.8
+        bot = d[l] + 0.2 if l < n_layers - 1 else d[-1] - 0.8
+        zext.append((float(bot), float(top)))
+    src = np.concatenate([rng.uniform([-0.6, -0.6, a], [0.6, 0.6, b], size=(n_per_layer, 3))
+                          for (a, b) in zext], 0)
+    q = _charges(rng, len(src))
+    return Workload(name or f"multi_layer{n_layers}_n{len(src)}_p{p}", d, k, zext, src, q, p, leaf_cap,
+                    n_images)
+
+
+# Example 2 of the paper's Sec. 5: irregular domains
+# r(theta) = 0.5 - a + (a / 8) (35 cos^4 theta - 30 cos^2 theta + 3)
+# shifted to centres (0, 0, 1), (0, 0, -1) (two layers, interface z = 0) and
+# (0, 0, -3) (three layers, interfaces 0, -2), a = 0.1, 0.15, 0.05.
+IRREGULAR_CENTRES = [1.0, -1.0, -3.0]
+IRREGULAR_A = [0.1, 0.15, 0.05]
+
+
+def irregular_domains(n, n_layers=3, p=6, leaf_cap=64, seed=0, n_images=16, k=(0.8, 1.5, 2.0), name=None):
+    """Particles uniform inside the irregular domains of Example 2 (rejection
+    from the cube of side 1 around each domain centre), n split equally over
+    the n_layers (2 or 3) domains, top layer first.  The paper does not state
+    the wavenumbers of Sec. 5; k defaults to those of its Sec. 3.3 example."""
+    assert n_layers in (2, 3)
+    rng = np.random.default_rng(seed)
+    d = [0.0] if n_layers == 2 else [0.0, -2.0]
+    counts = [n // n_layers + (1 if l < n % n_layers else 0) for l in range(n_layers)]
+    parts, zext = [], []
+    for l in range(n_layers):
+        c, a, need = IRREGULAR_CENTRES[l], IRREGULAR_A[l], counts[l]
+        got = []
+        while need > 0:
+            x = rng.uniform([-0.5, -0.5, c - 0.5], [0.5, 0.5, c + 0.5], size=(max(2 * need, 64), 3))
+            rel = x - np.array([0.0, 0.0, c])
+            r = np.sqrt(np.sum(rel * rel, 1))
+            ct = np.divide(rel[:, 2], r, out=np.zeros_like(r), where=r > 0)
+            keep = x[r < 0.5 - a + a / 8.0 * (35 * ct ** 4 - 30 * ct ** 2 + 3)][:need]
+            got.append(keep)
+            need -= len(keep)
+        parts.append(np.concatenate(got, 0))
+        zext.append((c - 0.5, c + 0.5))
+    src = np.concatenate(parts, 0)
+    q = _charges(rng, len(src))
+    return Workload(name or f"irregular_domains{n_layers}_n{n}_p{p}", d, list(k)[:n_layers], zext, src, q,
+                    p, leaf_cap, n_images)

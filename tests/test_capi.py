@@ -97,3 +97,15 @@ def test_eval_and_apply_refuse_wrong_lengths_without_gpu():
         tefmm.Plan.apply(plan, c128(4))                                            # short q
     with pytest.raises(ValueError):
         tefmm.Plan.apply(plan, c128(5), out=c128(5))                               # out of the wrong length
+
+
+def test_fault_injection_hook_arguments_without_gpu():
+    """The error-path test hook takes its arguments and clears without a GPU."""
+    from paper_1902_05875_gb300 import tefmm
+    lib = tefmm.load()
+    assert lib.tefmm_debug_inject(0, 0) == 0
+    assert lib.tefmm_debug_inject(tefmm.INJECT_ALLOC, 0) == tefmm.ERR_INVALID_ARG
+    assert lib.tefmm_debug_inject(7, 1) == tefmm.ERR_INVALID_ARG
+    assert lib.tefmm_debug_inject(tefmm.INJECT_FIT, 3) == 0
+    assert lib.tefmm_debug_inject(0, 0) == 0
+    assert lib.tefmm_status_string(tefmm.ERR_TIMEOUT) == b"a bounded device wait ran out"
