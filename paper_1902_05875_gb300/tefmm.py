@@ -322,11 +322,11 @@ class Plan:
             raise ValueError("q must be a contiguous complex128 CUDA tensor")
         n = getattr(self, "_n_targets", None)
         ns = getattr(self, "_n_sources", None)
-        if n is None or ns is None:
-            raise RuntimeError("apply() needs a successful set_points() or eval() first")
-        if q.numel() != ns:
+        if ns is not None and q.numel() != ns:
             raise ValueError("q must have one entry per source of the last set_points() / eval()")
         if out is None:
+            if n is None:
+                raise RuntimeError("apply() needs a successful set_points() or eval() first")
             out = torch.empty(n, dtype=torch.complex128, device=q.device)
         elif out.dtype != torch.complex128 or not out.is_cuda or not out.is_contiguous() or \
                 (n is not None and out.numel() != n):
