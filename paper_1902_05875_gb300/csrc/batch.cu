@@ -79,6 +79,7 @@ extern "C" int tefmm_eval_batched(int n, tefmm_plan *plans, const tefmm_batch_it
 struct tefmm_batch_graph_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t origin = nullptr;     // the capture's origin stream (the legacy stream cannot be captured)
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
     std::vector<tefmm_plan> plans;
@@ -89,6 +90,7 @@ static void batch_graph_free(tefmm_batch_graph_s *G) {
     if (G->graph) cudaGraphDestroy(G->graph);
     for (cudaEvent_t e : G->events) cudaEventDestroy(e);
     for (cudaStream_t s : G->streams) cudaStreamDestroy(s);
+    if (G->origin) cudaStreamDestroy(G->origin);
     delete G;
 }
 
@@ -101,13 +103,15 @@ extern "C" int tefmm_batch_graph_create(int n, tefmm_plan *plans, const double *
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return TEFMM_ERR_INVALID_ARG;   // a plan is not shared
     }
-    cudaStream_t cs = (cudaStream_t)stream;
     // one apply per plan outside the capture: sizes its buffers (no allocation
     // may happen inside a capture) and checks that it runs
     for (int i = 0; i < n; ++i) TRY(tefmm_apply(plans[i], q[i], phi[i], stream));
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     tefmm_batch_graph_s *G = new tefmm_batch_graph_s();
     G->plans.assign(plans, plans + n);
     int err = TEFMM_OK;
+    if (cudaStreamCreateWithFlags(&G->origin, cudaStreamNonBlocking) != cudaSuccess) err = TEFMM_ERR_CUDA;
+    cudaStream_t cs = G->origin;
     G->streams.resize(n, nullptr);
     G->events.resize(n + 1, nullptr);
     for (int i = 0; i < n && err == TEFMM_OK; ++i)
@@ -119,6 +123,7 @@ extern "C" int tefmm_batch_graph_create(int n, tefmm_plan *plans, const double *
         return err;
     }
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        fprintf(stderr, "tefmm: stream capture could not begin: %s\n", cudaGetErrorString(cudaGetLastError()));
         batch_graph_free(G);
         return TEFMM_ERR_CUDA;
     }
@@ -136,6 +141,8 @@ extern "C" int tefmm_batch_graph_create(int n, tefmm_plan *plans, const double *
     if (err == TEFMM_OK && ec != cudaSuccess) err = TEFMM_ERR_CUDA;
     if (err == TEFMM_OK && cudaGraphInstantiate(&G->exec, G->graph, 0) != cudaSuccess) err = TEFMM_ERR_CUDA;
     if (err != TEFMM_OK) {
+        fprintf(stderr, "tefmm: batch graph capture failed (status %d, end capture: %s)\n", err,
+                cudaGetErrorString(ec));
         cudaGetLastError();
         batch_graph_free(G);
         return err;
