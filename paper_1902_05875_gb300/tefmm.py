@@ -178,6 +178,8 @@ def eval_batched(plans, instances, n_workers=8, stream=None):
     st = (ctypes.c_int * max(n, 1))()
     _check(lib.tefmm_eval_batched(n, hs, items, int(n_workers), _stream_handle(stream), st),
            "tefmm_eval_batched")
+    for pl, (sx, *_rest) in zip(plans, instances):     # the plans now hold these points
+        pl._n_sources = pl._n_targets = sx.numel()
     return list(st[:n])
 
 
