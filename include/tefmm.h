@@ -2,7 +2,7 @@
  * tefmm.h -- C ABI of the GB300 Taylor-expansion FMM for the 3-D Helmholtz
  * equation in layered media (Wang, Zhang, Cai: arXiv 1902.05875).
  *
- * The library computes the matrix-vector product of the paper's Sec. 3.1,
+ * The library computes the matrix-vector product of the paper's Sec. 3.2,
  * eq. ``totalinteraction``:
  *
  *   Phi_l(r_i) = sum_{j in layer l, r_j != r_i} q_j h0(k_l |r_i - r_j|)
@@ -11,7 +11,7 @@
  * with h0(z) = e^{iz}/(iz) and the factor i k_l / (4 pi) omitted (Sec. 3.1),
  * by the TE-FMM of Algorithm 1 applied to every component of the heterogeneous
  * loop that follows it (Sec. 3.3).  The reaction components are represented by
- * discrete complex images (Sec. 3.2, eq. ``closedformgreen``) fitted at plan
+ * discrete complex images (Sec. 3.3, eq. ``closedformgreen``) fitted at plan
  * time.  Everything below these calls runs in this library's own CUDA kernels.
  *
  * Conventions shared by every call
@@ -155,7 +155,7 @@ int tefmm_plan_create(int n_layers, const double *interfaces, const double *k_re
 /* Release a plan and everything it owns.  NULL is accepted. */
 int tefmm_plan_destroy(tefmm_plan plan);
 
-/* The matrix-vector product (Sec. 3.1, eq. ``totalinteraction``; Algorithm 1
+/* The matrix-vector product (Sec. 3.2, eq. ``totalinteraction``; Algorithm 1
  * for every component).  Builds the octrees and lists for the given points,
  * then runs the upward pass, the M2L translations, the downward pass, L2P and
  * the near field.
@@ -260,7 +260,7 @@ const char *tefmm_status_string(int status);
  * Images are described per (layer, term): term tags 0 = up-up, 1 = down-down,
  * 2 = up-down, 3 = down-up.  A same-layer reaction term is written with a real
  * image distance zeta = sz*z + szp*z' + c (> 0 inside the layer) and contributes
- * sum_j A_j h0(k_l sqrt(rho^2 + (zeta - zeta_min - Z_j)^2)) (Sec. 3.2, Step 3,
+ * sum_j A_j h0(k_l sqrt(rho^2 + (zeta - zeta_min - Z_j)^2)) (Sec. 3.3, Step 3,
  * eq. ``closedformgreen`` with the density's reflection exponentials folded
  * into zeta).  For each term: sz, szp, c, zeta_min and its images (A_j, Z_j).
  */
@@ -298,7 +298,7 @@ int tefmm_export_lists(tefmm_plan plan, int64_t *n_v, int64_t *n_near, int *v_pt
  * (n = 0..p; k1 = n..0; k2 = n-k1..0; k3 = n-k1-k2).  NULL skips one. */
 int tefmm_export_expansions(tefmm_plan plan, double *alpha, double *beta);
 
-/* Cross-layer DCIM images held by the plan (Sec. 3.2: one fit of the
+/* Cross-layer DCIM images held by the plan (Sec. 3.3: one fit of the
  * k3'-th z'-derivative density per target layer l, source layer l', part
  * (0 up-going, W = z - d_l; 1 down-going, W = d_{l-1} - z), octree level,
  * source z-box index iz_s and k3' = 0..p; the source z-centre is

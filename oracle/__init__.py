@@ -10,12 +10,12 @@ The oracle is a plain, slow, readable restatement of the paper:
 * ``medium``      -- layered medium, the k_z branch, the interface problem for
                      the densities sigma (Sec. 2, Appendix A);
 * ``sommerfeld``  -- contour quadrature of Sommerfeld integrals and their
-                     derivatives (Sec. 2, eqs. for u^up/u^down, Sec. 3.2);
-* ``dcim``        -- two-level DCIM sampling and GPOF fits (Sec. 3.2, Steps 1-3);
+                     derivatives (Sec. 2, eqs. for u^up/u^down, Sec. 3.3);
+* ``dcim``        -- two-level DCIM sampling and GPOF fits (Sec. 3.3, Steps 1-3);
 * ``derivs``      -- the Cartesian recurrence for D^k e^{ikR}/R at complex R
-                     (Sec. 3.2, eq. ``recurrsion``, corrected form);
+                     (Sec. 3.3, eq. ``recurrsion``, corrected form);
 * ``direct``      -- FP64 direct sum of the DCIM-approximated layered Green's
-                     function (Sec. 3.1, eq. ``totalinteraction``), in C;
+                     function (Sec. 3.2, eq. ``totalinteraction``), in C;
 * ``tefmm``       -- the CPU TE-FMM (Algorithms 1 and 2 of Sec. 3).
 
 It shares no code with the CUDA path.

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Follows Sec. 3.2 of the paper for a component whose source and target lie in
+Follows Sec. 3.2-3.3 of the paper for a component whose source and target lie in
 different layers:
 
 * the z'-derivatives of the density, eq. ``layermediumdensity``:
@@ -11,7 +11,7 @@ different layers:
 * Theta^{k3'}(k_rho, z') = e^{i k_lz W_min} d^{k3'}_{z'} sigma~ / k3'!, fitted
   by the two-level DCIM in the target layer's variable k_lz (Steps 1-2), one fit
   per source z-centre and k3' (the "2^H (p+1)" precomputed approximations at the
-  end of Sec. 3.2);
+  end of Sec. 3.3);
 * d^{k3'}_{z'} u / k3'! ~= sum_j A_j h0(k_l sqrt(rho^2 + (W - W_min - Z_j)^2)),
   eq. ``closedformgreen``, with the target distance W = z - d_l for the up-going
   part and W = d_{l-1} - z for the down-going part (W > 0 in layer l).

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Follows Sec. 3.2, Steps 1-3 (eqs. ``compleximageapp`` and
+Follows Sec. 3.3, Steps 1-3 (eqs. ``compleximageapp`` and
 ``closedformgreen``):
 
 * Step 1: sample the density on two paths in the k_lz plane,

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Sec. 3.2, eq. ``recurrsion``: with x = r - r' (third component possibly
+Sec. 3.3, eq. ``recurrsion``: with x = r - r' (third component possibly
 complex, an image point), phi = e^{ikR}/R, psi = e^{ikR}, R = sqrt(x.x)
 (principal branch), a_k = D^k phi / k!, b_k = D^k psi / k!.
 

@@ -4,11 +4,11 @@
  * TEST INFRASTRUCTURE ONLY: used by the tests and the CPU baseline, never by
  * the CUDA library.
  *
- * Sec. 3.1, eq. ``totalinteraction``: for a target r_i in layer l,
+ * Sec. 3.2, eq. ``totalinteraction``: for a target r_i in layer l,
  *   Phi(r_i) = sum_{j in layer l, r_j != r_i} q_j h0(k_l |r_i - r_j|)
  *            + sum_{l'} sum_j q_j (u^up_{l l'} + u^down_{l l'})(r_i, r_j),
  * with the factor i k_l / (4 pi) omitted (Sec. 3.1) and h0(z) = e^{iz}/(iz).
- * The same-layer reaction field is the DCIM image sum of Sec. 3.2, Step 3
+ * The same-layer reaction field is the DCIM image sum of Sec. 3.3, Step 3
  * (eq. ``closedformgreen``), written with the image distance
  *   zeta = sz*z + szp*z' + c,   R_j = sqrt(rho^2 + (zeta - zeta_min - Z_j)^2),
  * each image contributing A_j h0(k_l R_j).  The self pair is excluded from the
@@ -67,7 +67,7 @@ void oracle_direct_sum(int64_t ns, const double *sx, const double *sy, const dou
 }
 
 /*
- * Cross-layer part of Phi at each target by reciprocity (Sec. 3.2 fits, one per
+ * Cross-layer part of Phi at each target by reciprocity (Sec. 3.3 fits, one per
  * target).  For a target r_i in layer l and sources in layer l' != l,
  *   u_{l l'}(r_i; r') = (k_l' / k_l)^2 u_{l' l}(r'; r_i),
  * and u_{l' l}(r'; r_i) (the field in layer l' of a source at r_i) is the
@@ -116,7 +116,7 @@ void oracle_cross_sum(int64_t ns, const double *sx, const double *sy, const doub
 }
 
 /*
- * Cross-layer part of Phi with the images in the TARGET layer l (Sec. 3.2:
+ * Cross-layer part of Phi with the images in the TARGET layer l (Sec. 3.3:
  * the source-box z'-expansion of the density, eq. ``layermediumdensity``, and
  * the image form of each z'-derivative, eq. ``closedformgreen``).  Sources are
  * grouped in narrow z'-bins; a source at z' = zc_b + delta (bin b) contributes

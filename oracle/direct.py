@@ -104,7 +104,7 @@ def cross_sum_binned(med, zext, src, q, tgt, n_images=16, zbin=0.02, K=6, pairs=
     """Cross-layer part of Phi with the images in the target layer: the sources
     of layer l' are grouped in equal z'-bins of width <= zbin over the layer's
     particle slab, each bin centre zc gets the fits of Theta^{k3'}, k3' = 0..K
-    (Sec. 3.2, ``oracle.cross.fit_cross``), and a source at zc + delta adds
+    (Sec. 3.3, ``oracle.cross.fit_cross``), and a source at zc + delta adds
     sum_{k3'} delta^{k3'} (image sum of fit k3') (``oracle_cross_sum_binned``).
     pairs(l, l') selects the layer pairs (default: all)."""
     from .cross import directions, fit_cross, W_min

@@ -11,7 +11,7 @@ factor i k_l / (4 pi) omitted as in Sec. 3.1, so that
 with sigma~^up = S2 sigma^{uu} + S1 sigma^{ud}, sigma~^down = S2 sigma^{du} +
 S1 sigma^{dd}, S1 = e^{i k_l'z (d_{l'-1} - z')}, S2 = e^{i k_l'z (z' - d_l')}.
 
-Derivatives (Sec. 3.2 and Sec. 4.3): d/dz acts on the target exponential,
+Derivatives (Sec. 3.3 and Sec. 4.2): d/dz acts on the target exponential,
 d/dz' on S1, S2 (eq. ``layermediumdensity``), and the in-plane operator uses
 (d/dx + i d/dy)^s J0(k_rho rho) = (-k_rho)^s J_s(k_rho rho) e^{i s theta}.
 
@@ -134,7 +134,7 @@ def reaction_derivative(med: Medium, l, lp, r, rp, s=0, k3=0, k3p=0, part='both'
 def free_space_by_quadrature(k, r, rp, **path_kw):
     """h0(k|r - r'|) = (1/k) int k_rho J0(k_rho rho) e^{i k_z |z - z'|}/k_z dk_rho.
 
-    The Sommerfeld identity of Sec. 3.2, evaluated numerically (homogeneous
+    The Sommerfeld identity of Sec. 3.3, evaluated numerically (homogeneous
     medium check of the quadrature path).
     """
     r = np.asarray(r, float)

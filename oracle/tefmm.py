@@ -8,9 +8,9 @@ Follows Sec. 3 of the paper:
   ``taylorexplocxclfree``), M2M by the binomial shift (eqs. ``LETOLEmat``,
   ``TETartoTETar``), L2L (eq. ``freeletole``), and the box-to-box translation
   L_k^{k'} = D_r^k D_{r'}^{k'} h0 / (k! k'!).
-* Sec. 3.1 (layered media): the same M2M/L2L, and the layered M2L of eq.
+* Sec. 3.2 (layered media): the same M2M/L2L, and the layered M2L of eq.
   ``tesourceboxtotargetbox`` with D_r^k D_{r'}^{k'} u / (k! k'!).
-* Sec. 3.2: DCIM images and the derivative recurrence (``oracle.derivs``).
+* Sec. 3.3: DCIM images and the derivative recurrence (``oracle.derivs``).
 * Algorithm 1 (upward pass, downward pass with L2L and M2L, L2P, near-field
   direct sum) and the component loop of the heterogeneous algorithm that
   follows it (free space for l = l', up/down reaction components).
@@ -47,7 +47,7 @@ Readings where the paper is silent (all stated the same way for the CUDA path):
   where a_g = D^g f / g!, C(k+k', k) = prod_i (k_i+k'_i)!/(k_i! k'_i!).
   Offsets of M2L pairs are taken from integer box coordinates:
   X0 = di_x * (side / 2^l), and zt_c + zs_c = 2 lo_z + (i_t + i_s + 1) * (side / 2^l).
-* Cross-layer components (target layer l != source layer l', Sec. 3.2): per
+* Cross-layer components (target layer l != source layer l', Sec. 3.2-3.3): per
   source z-centre z_c and k3' = 0..p the images of Theta^{k3'} (``oracle.cross``)
   give d^{k3'}_{z'} u / k3'! as image Hankel functions of (X, Y, W), W = z - d_l
   (up) or d_{l-1} - z (down); hence
@@ -519,7 +519,7 @@ class TEFMM:
                         alpha[n] += ops.m2m(alpha[ch], tr.center(ch) - c)
         return alpha
 
-    # -- derivative tables (Sec. 3.2) ---------------------------------------
+    # -- derivative tables (Sec. 3.3) ---------------------------------------
     def _tables(self, l, lev, keysB, keysA):
         """Combined tables per key at one level of layer l.
 

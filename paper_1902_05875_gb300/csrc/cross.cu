@@ -1,4 +1,4 @@
-// Cross-layer reaction components (Sec. 3.2): target layer l != source layer l'.
+// Cross-layer reaction components (Sec. 3.2-3.3): target layer l != source layer l'.
 //
 // The component's z'-dependence cannot be folded into an image distance, so
 // the paper expands it in z' about the source box centre z_c: for each source

@@ -1,4 +1,4 @@
-// Plan-time DCIM fits on the device (Sec. 3.2, Steps 1-2), one CTA per fit.
+// Plan-time DCIM fits on the device (Sec. 3.3, Steps 1-2), one CTA per fit.
 //
 // Step 1 samples, on the two paths of the k_lz plane
 //   C_ap1: k_lz = i k_l (T0 + t), 0 <= t <= T1;   C_ap2: k_lz = k_l (1 - t/T0 + i t), 0 <= t <= T0,
@@ -957,7 +957,7 @@ extern "C" int tefmm_fit_images_noalloc(int n_layers, const double *interfaces, 
 }
 
 // ---------------------------------------------------------------------------
-// Cross-layer fits (Sec. 3.2: one DCIM fit per source z-centre and k3', for a
+// Cross-layer fits (Sec. 3.3: one DCIM fit per source z-centre and k3', for a
 // component whose source and target layers differ).  Runs the fit kernel on
 // the given jobs and appends the images to the plan's cross-layer pool.
 int fit_cross_jobs(tefmm_plan_s *P, const std::vector<CrossFitKey> &keys, cudaStream_t st) {

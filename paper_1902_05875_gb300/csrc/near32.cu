@@ -3,7 +3,7 @@
 //
 // For a target leaf, every source box of its near list contributes
 //   q_j [ e^{ik r}/(ik r)  (free space, skipped for coincident points)
-//       + sum_tau sum_m A_m e^{ik R_m}/(ik R_m) ]  (DCIM images, Sec. 3.2 Step 3)
+//       + sum_tau sum_m A_m e^{ik R_m}/(ik R_m) ]  (DCIM images, Sec. 3.3 Step 3)
 // with R_m = sqrt(rho^2 + w_m^2), w_m = zeta_tau(z, z') - zeta_min - Z_m.
 // Coordinates enter as FP32 offsets from the target leaf's centre (each
 // offset formed in FP64); every pair is evaluated in FP32; the sum over one

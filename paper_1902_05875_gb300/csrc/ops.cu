@@ -5,7 +5,7 @@
 //   M2L   beta_k += sum_k' alpha_k' D_r^k D_r'^k' u / (k! k'!)     (eq. tesourceboxtotargetbox)
 //   L2L   lambda_k = sum_{k'>=k} C(k',k) (c~ - c)^{k'-k} beta_k'   (eq. freeletole)
 //   L2P   Phi(r) += sum_k beta_k (r - c)^k                         (eq. taylorexploc2ld)
-//   P2P   free-space h0 plus the DCIM image sum (Sec. 3.2, eq. closedformgreen)
+//   P2P   free-space h0 plus the DCIM image sum (Sec. 3.3, eq. closedformgreen)
 //
 // M2L follows the per-key batching of Sec. 3.2 (the derivative tables depend
 // only on the box centres): V pairs are grouped by a key, one derivative table

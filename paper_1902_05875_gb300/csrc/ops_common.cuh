@@ -141,7 +141,7 @@ __host__ __device__ inline XKey xkey_decode(uint64_t k) {
 
 // ------------------------------------------------------------------ derivative tables
 // One derivative table per key: sum over the key's images of
-// A_j D^g h0(k R_j) / g!, |g| <= P2, by the recurrence (Sec. 3.2)
+// A_j D^g h0(k R_j) / g!, |g| <= P2, by the recurrence (Sec. 3.3)
 //   |g| R^2 a_g + (2|g|-1) sum_i x_i a_{g-e_i} + (|g|-1) sum_i a_{g-2e_i}
 //       = i k sum_i (x_i b_{g-e_i} + b_{g-2e_i}),
 //   |g| b_g = i k sum_i (x_i a_{g-e_i} + a_{g-2e_i}),

@@ -1,4 +1,4 @@
-"""Pins of the oracle's cross-layer components (Sec. 3.2, target layer l differs
+"""Pins of the oracle's cross-layer components (Sec. 3.2-3.3, target layer l differs
 from source layer l').
 
 What fixes them independently of the oracle's own formulas:

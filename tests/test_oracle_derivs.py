@@ -1,4 +1,4 @@
-"""Pins of the derivative recurrence (Sec. 3.2, corrected eq. ``recurrsion``).
+"""Pins of the derivative recurrence (Sec. 3.3, corrected eq. ``recurrsion``).
 
 Independent references: the closed-form Taylor series on the z axis, an
 independent truncated multivariate power-series evaluation of e^{ikR}/R

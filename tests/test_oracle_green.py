@@ -5,9 +5,9 @@
 * Appendix A closed forms (two layers; three layers, source in the middle):
   the numeric interface solve must reproduce them.
 * Homogeneous medium: no reflection, unit transmission; the Sommerfeld identity
-  (Sec. 3.2) must give h0.
+  (Sec. 3.3) must give h0.
 * GPOF recovers a known sum of exponentials; the DCIM image sum approaches
-  the quadrature truth as the number of images grows (Sec. 3.2, Steps 1-3).
+  the quadrature truth as the number of images grows (Sec. 3.3, Steps 1-3).
 * Reciprocity inside one layer: u(r, r') = u(r', r).
 """
 import math
