@@ -90,6 +90,12 @@ typedef struct {
                               built: TEFMM_ERR_NOT_IMPLEMENTED                         */
     int split;             /* tensor-core split of the mixed form: TEFMM_SPLIT_TF32X3
                               (the only one built; others TEFMM_ERR_NOT_IMPLEMENTED)  */
+    int far_of_near;       /* 1 (default): for two adjacent leaves of one level, the DCIM
+                              images far from both (-Re Z_j >= 10^(10/(p+1)) sqrt(3) h)
+                              are translated by M2L (through the tensor cores in the
+                              mixed form) instead of summed pair by pair; the free-space
+                              term and the near images stay in P2P.  0: every image in
+                              P2P.                                                     */
     int scale_output;      /* 0 (default): potentials in the paper's normalisation
                               (Sec. 3.1: free term h0(k|r - r'|), factor i k_l/(4 pi)
                               omitted); 1: every potential multiplied by i k_l/(4 pi)
@@ -131,11 +137,12 @@ typedef struct {
                               kernels alone (CUDA events around each launch)          */
     int n_m2l_kernel_launches; /* ... and their number                               */
     int64_t n_p2p_pairs_layer[8]; /* near-field particle pairs by target layer        */
+    int64_t n_fon_pairs;   /* last eval: leaf pairs whose far images went through M2L */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,
  * 8 images, 101 samples, T1 = 10, T0 = formula, zext = whole layers,
- * kh_max = 3.5, algorithm 1, TF32x3 split, unscaled output. */
+ * kh_max = 3.5, far_of_near = 1, algorithm 1, TF32x3 split, unscaled output. */
 int tefmm_default_options(tefmm_options *opt);
 
 /* Create a plan for a layered medium (Sec. 2.1) and fit its DCIM images

@@ -63,6 +63,16 @@ Readings where the paper is silent (all stated the same way for the CUDA path):
   like e^{|k_z| (z_c - d)} along the first DCIM path and cannot be fitted.  Cross-layer near-field pairs are not supported
   (leaves must be small enough that boxes of different layers are never
   adjacent).
+* Far-of-near (a reading of the precision pattern the method is built for):
+  for a pair of adjacent leaves of one level l, an image j of a same-layer
+  term whose depth satisfies -Re Z_j >= kappa_p sqrt(3) h_l, kappa_p =
+  10^(10/(p+1)), is far from both leaves (their points lie within sqrt(3) h_l
+  of each other's centres in the combined displacement), so its part of the
+  pair's field is a smooth function that a Taylor translation of order p
+  carries to about kappa_p^-(p+1) = 1e-10 of itself.  Those images go through
+  M2L between the two leaves (tables of the far images only, no free-space
+  term); the free-space term and the nearer images stay in the direct sum.
+  Pairs of leaves of different levels (and W/X pairs) keep every image direct.
 * Which layer holds the images of a cross-layer component (a reading): the
   DCIM fit of Sec. 3.3 is accurate to about 1e-8 against Sommerfeld quadrature
   when its images live in the layer of the larger |k|, but only to 1e-6 .. 4e-4
@@ -108,6 +118,12 @@ def morton_decode(prefix, level):
         iy |= ((p >> np.uint64(3 * b + 1)) & np.uint64(1)).astype(np.int64) << b
         ix |= ((p >> np.uint64(3 * b + 2)) & np.uint64(1)).astype(np.int64) << b
     return ix, iy, iz
+
+
+def fon_threshold(p, side, lev):
+    """Depth beyond which an image is far for a pair of adjacent leaves of
+    level lev (see the far-of-near reading): kappa_p sqrt(3) h."""
+    return 10.0 ** (10.0 / (p + 1)) * math.sqrt(3.0) * (side / float(1 << lev))
 
 
 def cross_box_limit(med, zext):
@@ -469,9 +485,10 @@ class TEFMM:
     """Algorithm 1 + the component loop, for every (target layer, source layer)."""
 
     def __init__(self, med, images, p, leaf_cap, max_level=NBITS, cube=None, zext=None,
-                 cross_images=None, n_images=None, kh_max=KH_MAX):
+                 cross_images=None, n_images=None, kh_max=KH_MAX, far_of_near=True):
         self.med = med
         self.kh_max = kh_max
+        self.far_of_near = far_of_near
         self.images = images
         self.zext = zext if zext is not None else (images.zext if images is not None else None)
         # cross-layer images: dict (lt, ls, direction, level, izs, k3p) -> (A, Z);
@@ -520,11 +537,13 @@ class TEFMM:
         return alpha
 
     # -- derivative tables (Sec. 3.3) ---------------------------------------
-    def _tables(self, l, lev, keysB, keysA):
+    def _tables(self, l, lev, keysB, keysA, far_thr=None):
         """Combined tables per key at one level of layer l.
 
         keysB: (n, 3) integer offsets (dix, diy, diz) -> B = free + ud + (-1)^{g3} du
         keysA: (n, 3) (dix, diy, izt + izs)           -> A = uu + (-1)^{g3} dd
+        With far_thr (far-of-near pairs): no free-space term, and only the
+        images with -Re Z >= far_thr.
         """
         tr = self.tr
         P2 = 2 * self.p
@@ -539,13 +558,16 @@ class TEFMM:
             X0 = keysB[:, 0] * h
             Y0 = keysB[:, 1] * h
             dz = keysB[:, 2] * h
-            TB += taylor_h0(X0, Y0, dz.astype(complex), k, P2)
+            if far_thr is None:
+                TB += taylor_h0(X0, Y0, dz.astype(complex), k, P2)
             for tag, sgn in (('ud', None), ('du', odd3)):
                 if tag not in terms:
                     continue
                 t = terms[tag]
                 W0 = t['sz'] * dz + t['c']          # sz z_t + szp z_s + c with szp = -sz
                 for A, Z in zip(t['A'], t['Z']):
+                    if far_thr is not None and not (-Z.real >= far_thr):
+                        continue
                     tab = A * taylor_h0(X0, Y0, W0 - t['zeta_min'] - Z, k, P2)
                     TB += tab if sgn is None else tab * sgn[None, :]
         if len(keysA):
@@ -558,6 +580,8 @@ class TEFMM:
                 t = terms[tag]
                 W0 = t['sz'] * zsum + t['c']        # sz = szp for these terms
                 for A, Z in zip(t['A'], t['Z']):
+                    if far_thr is not None and not (-Z.real >= far_thr):
+                        continue
                     tab = A * taylor_h0(X0, Y0, W0 - t['zeta_min'] - Z, k, P2)
                     TA += tab if sgn is None else tab * sgn[None, :]
         return TB, TA
@@ -576,14 +600,33 @@ class TEFMM:
                 while a >= 0:
                     need.add(a)
                     a = tr.parent[a]
-        for (lt, ls), (V, _) in self.lists.items():
+        for (lt, ls), (V, P2P) in self.lists.items():
             if lt != ls:
                 self._cross_m2l(lt, ls, V, alpha, beta, need)
                 continue
-            # group V pairs by level
+            # group V pairs by level; far-of-near pairs (adjacent leaves of one
+            # level) translate their far images only
             pairs = [(t, s) for t, lst in V.items() for s in lst if need is None or t in need]
-            if not pairs:
+            self._same_layer_m2l(lt, pairs, alpha, beta, None)
+            if self.far_of_near and self.images is not None:
+                fon = [(t, s) for t, lst in P2P.items() for s in lst
+                       if tr.level[s] == tr.level[t] and (need is None or t in need)]
+                self._same_layer_m2l(lt, fon, alpha, beta, True)
+        order = np.argsort(tr.level, kind='stable')
+        for n in order:
+            par = tr.parent[n]
+            if par < 0 or tr.nt(n) == 0:
                 continue
+            if need is not None and n not in need:
+                continue
+            beta[n] += ops.l2l(beta[par], tr.center(n) - tr.center(par))
+        return beta
+
+    def _same_layer_m2l(self, l, pairs, alpha, beta, fon):
+        """M2L of same-layer box pairs, grouped by level and key; fon: the
+        far-of-near tables (far images only) of adjacent leaf pairs."""
+        tr, ops = self.tr, self.ops
+        if pairs:
             pairs = np.array(pairs, dtype=np.int64)
             for lev in np.unique(tr.level[pairs[:, 0]]):
                 sel = pairs[tr.level[pairs[:, 0]] == lev]
@@ -592,7 +635,8 @@ class TEFMM:
                 kA = np.stack([tr.ix[t] - tr.ix[s], tr.iy[t] - tr.iy[s], tr.iz[t] + tr.iz[s]], 1)
                 uB, invB = np.unique(kB, axis=0, return_inverse=True)
                 uA, invA = np.unique(kA, axis=0, return_inverse=True)
-                TB, TA = self._tables(lt, int(lev), uB, uA)
+                thr = fon_threshold(self.p, tr.side, int(lev)) if fon else None
+                TB, TA = self._tables(l, int(lev), uB, uA, far_thr=thr)
                 zero = np.zeros(TB.shape[1], dtype=complex)
                 invB = invB.reshape(-1)
                 invA = invA.reshape(-1)
@@ -604,15 +648,6 @@ class TEFMM:
                     m = invA == i
                     contrib[m] += alpha[s[m]] @ ops.m2l_matrix(TA[i], zero).T
                 np.add.at(beta, t, contrib)
-        order = np.argsort(tr.level, kind='stable')
-        for n in order:
-            par = tr.parent[n]
-            if par < 0 or tr.nt(n) == 0:
-                continue
-            if need is not None and n not in need:
-                continue
-            beta[n] += ops.l2l(beta[par], tr.center(n) - tr.center(par))
-        return beta
 
     def cross_centre(self, layer, lev, iz):
         """z of a box's cross-layer expansion centre: its centre clamped to the
@@ -709,8 +744,10 @@ class TEFMM:
                 np.add.at(beta, t, loc @ ops.shift_matrix(np.array([0.0, 0.0, zt - ztc])))
 
     # -- near field ----------------------------------------------------------
-    def _kernel_same_layer(self, l, tpts, spts):
-        """free h0 (skip identical coordinates) + DCIM images, (nt, ns) matrix."""
+    def _kernel_same_layer(self, l, tpts, spts, far_thr=None):
+        """free h0 (skip identical coordinates) + DCIM images, (nt, ns) matrix;
+        with far_thr (a far-of-near pair) the images with -Re Z >= far_thr are
+        left out (they went through M2L)."""
         k = self.med.k[l]
         dx = tpts[:, None, 0] - spts[None, :, 0]
         dy = tpts[:, None, 1] - spts[None, :, 1]
@@ -720,9 +757,19 @@ class TEFMM:
             (tpts[:, None, 2] == spts[None, :, 2])
         with np.errstate(divide='ignore', invalid='ignore'):
             G = np.where(same, 0.0, np.exp(1j * k * r) / (1j * k * np.where(same, 1.0, r)))
-        if self.images is not None:
+        if self.images is not None and far_thr is None:
             G = G + self.images.reaction(l, tpts[:, None, 0], tpts[:, None, 1], tpts[:, None, 2],
                                          spts[None, :, 0], spts[None, :, 1], spts[None, :, 2])
+        elif self.images is not None:
+            rho2 = dx * dx + dy * dy
+            for t in self.images.terms[l]:
+                zeta = t['sz'] * tpts[:, None, 2] + t['szp'] * spts[None, :, 2] + t['c']
+                for A, Z in zip(t['A'], t['Z']):
+                    if -Z.real >= far_thr:
+                        continue
+                    w = zeta - t['zeta_min'] - Z
+                    R = np.sqrt(rho2 + w * w)
+                    G = G + A * np.exp(1j * k * R) / (1j * k * R)
         return G
 
     def evaluate(self, q, target_index=None):
@@ -760,7 +807,9 @@ class TEFMM:
                     continue
                 for s in P2P[t]:
                     s0, s1 = tr.s0[s], tr.s1[s]
-                    G = self._kernel_same_layer(l, pts, sp[s0:s1])
+                    thr = (fon_threshold(self.p, tr.side, int(tr.level[t]))
+                           if self.far_of_near and tr.level[s] == tr.level[t] else None)
+                    G = self._kernel_same_layer(l, pts, sp[s0:s1], far_thr=thr)
                     val = val + G @ qs[s0:s1]
             phi_sorted[idx] = val
         out = np.zeros(len(tp), dtype=complex)

@@ -275,6 +275,7 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
     if (P->kev_used > 0 && cudaEventQuery(P->kev[P->kev_used - 1]) == cudaSuccess)
         for (int i = 0; i + 1 < P->kev_used; i += 2) o->ms_m2l_kernel += elapsed(P->kev[i], P->kev[i + 1]);
     for (int l = 0; l < 8; ++l) o->n_p2p_pairs_layer[l] = P->p2p_by_layer[l];
+    o->n_fon_pairs = P->n_fon;
     o->leaf_cap_used = P->leaf_cap_eff;
     o->ms_autotune = P->ms_autotune;
     o->n_tables_built = P->n_tables_built;

@@ -127,17 +127,17 @@ __global__ void k_xshift_beta(int nn, TreeArrays T, Cube cb, XGeom geo, int p, i
     }
 }
 
-// first cross-layer table and first cross-layer chunk (keys are sorted, kind 2 last)
+// first cross-layer table and first cross-layer chunk (keys are sorted, kind 3 last)
 __global__ void k_first_cross(int ntab, const uint64_t *__restrict__ tkey, int64_t nch,
                               const int *__restrict__ chunk_table, int *out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < ntab) {
-        bool x = key_kind(tkey[i]) == 2, xp = i > 0 && key_kind(tkey[i - 1]) == 2;
+        bool x = key_is_cross(tkey[i]), xp = i > 0 && key_is_cross(tkey[i - 1]);
         if (x && !xp) out[0] = (int)i;
     }
     if (i < nch) {
-        bool x = key_kind(tkey[chunk_table[i]]) == 2;
-        bool xp = i > 0 && key_kind(tkey[chunk_table[i - 1]]) == 2;
+        bool x = key_is_cross(tkey[chunk_table[i]]);
+        bool xp = i > 0 && key_is_cross(tkey[chunk_table[i - 1]]);
         if (x && !xp) out[1] = (int)i;
     }
 }

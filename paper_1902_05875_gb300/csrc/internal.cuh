@@ -171,6 +171,8 @@ struct tefmm_plan_s {
     DBuf C_list, C_cnt, D_list, D_cnt, X_list, X_cnt, V_tmp, V_cnt;
     DBuf v_ptr, v_src, near_ptr, near_src, near_tmp, near_cnt;
     int64_t n_v = 0, n_near = 0, n_p2p_pairs = 0;
+    int64_t n_fon = 0;            // far-of-near pairs (same-level adjacent leaves), after the V pairs
+    DBuf fon_cnt, fon_ptr;
     int cap_D = 64, cap_X = 0;
 
     // expansions

@@ -119,10 +119,9 @@ __global__ void __launch_bounds__(NTHR) k_wgen(TcArgs a, int ntab, float *__rest
     float2 *tab = (float2 *)smem;
     const int tb = a.tab_base + tbl;
     const uint64_t key = a.table_key[tb];
-    const int kind = key_kind(key);
     const int lev = key_level(key);
     const double h = a.side / (double)(1 << lev);
-    const float *cf = kind == 0 ? a.cfB : a.cfA;
+    const float *cf = key_is_B(key) ? a.cfB : a.cfA;
     // a reversed cross key: (k_lt / k_ls)^2 times the transposed matrix of its component
     const bool rev = a.xmode && xkey_rev(key);
     cplx fac = mkc(1, 0);

@@ -64,8 +64,9 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
     // per image: (w0, R0^2) and (1/R0, E0), FP32, two 16-byte loads per pair
     __shared__ float4 sWR[MI], sIE[MI];
     __shared__ float tsz[TEFMM_MAX_TERMS], tszp[TEFMM_MAX_TERMS];
-    __shared__ int tcnt[TEFMM_MAX_TERMS];
-    __shared__ double2 cq[2];      // [0]: sum of E0 over all images, [1]: near-field charge total
+    __shared__ int tcnt[TEFMM_MAX_TERMS], tncnt[TEFMM_MAX_TERMS];   // images / near images per term
+    __shared__ int slot[MI];       // image j of term ti at slot[ti * MAX_IMG + j]: near images first
+    __shared__ double2 cq[2];      // [0]: the images' constant part times the charges it applies to
     int lay = T.layer[node];
     cplx k = a.im.k[lay];
     cplx ik = mkc(-k.y, k.x);
@@ -75,15 +76,25 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
     double cx = centre(a.cb.lo[0], T.ix[node], h), cy = centre(a.cb.lo[1], T.iy[node], h),
            cz = centre(a.cb.lo[2], T.iz[node], h);
     int tf = a.im.lt_first[lay], ntm = a.im.lt_count[lay];
-    if (threadIdx.x < 2) red[threadIdx.x] = make_double2(0.0, 0.0);
-    __syncthreads();
+    // far-of-near: for a same-level near leaf the images with -Re Z >= thr went through M2L
+    const double thr = a.fon.on ? a.fon.thr[T.level[node]] : INFINITY;
+    if (threadIdx.x < 4) red[threadIdx.x] = make_double2(0.0, 0.0);
     if (threadIdx.x < ntm) {
         DevTerm t = a.im.terms[tf + threadIdx.x];
         tsz[threadIdx.x] = (float)t.sz;
         tszp[threadIdx.x] = (float)t.szp;
         tcnt[threadIdx.x] = t.count;
+        int nn_ = 0;                     // near images take the first slots, far ones the rest
+        for (int j = 0; j < t.count; ++j)
+            if (!(-a.im.Z[t.first + j].x >= thr)) slot[threadIdx.x * TEFMM_MAX_IMG + j] = nn_++;
+        tncnt[threadIdx.x] = nn_;
+        int nf_ = nn_;
+        for (int j = 0; j < t.count; ++j)
+            if (-a.im.Z[t.first + j].x >= thr) slot[threadIdx.x * TEFMM_MAX_IMG + j] = nf_++;
     }
-    // per-image reference at the leaf centre (FP64)
+    __syncthreads();
+    // per-image reference at the leaf centre (FP64); constant parts: red[0] near
+    // images, red[2] far images
     for (int ti = 0; ti < ntm; ++ti) {
         DevTerm t = a.im.terms[tf + ti];
         for (int j = threadIdx.x; j < t.count; j += blockDim.x) {
@@ -93,30 +104,41 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
             cplx E0 = cmul(cmul(a.im.A[t.first + j], inv_ik), cdiv(e, w0));
             cplx r0sq = cmul(w0, w0);
             cplx ir0 = cdiv(mkc(1, 0), w0);
-            int s = ti * TEFMM_MAX_IMG + j;
+            int s = ti * TEFMM_MAX_IMG + slot[ti * TEFMM_MAX_IMG + j];
             sWR[s] = make_float4((float)w0.x, (float)w0.y, (float)r0sq.x, (float)r0sq.y);
             sIE[s] = make_float4((float)ir0.x, (float)ir0.y, (float)E0.x, (float)E0.y);
-            atomicAdd(&red[0].x, E0.x);
-            atomicAdd(&red[0].y, E0.y);
+            const int rc = (-Z.x >= thr) ? 2 : 0;
+            atomicAdd(&red[rc].x, E0.x);
+            atomicAdd(&red[rc].y, E0.y);
         }
     }
-    // near-field charge total (FP64)
+    // near-field charge totals (FP64): red[1] all near boxes, red[3] same-level leaves
     {
-        double qr = 0.0, qi = 0.0;
+        double qr = 0.0, qi = 0.0, sr = 0.0, si = 0.0;
         for (int nb = a.near_ptr[node]; nb < a.near_ptr[node + 1]; ++nb) {
             const int sb = a.near_src[nb];
+            const bool same = T.level[sb] == T.level[node];
             for (int j = T.s0[sb] + threadIdx.x; j < T.s1[sb]; j += blockDim.x) {
                 qr += a.sq[2 * j];
                 qi += a.sq[2 * j + 1];
+                if (same) {
+                    sr += a.sq[2 * j];
+                    si += a.sq[2 * j + 1];
+                }
             }
         }
         atomicAdd(&red[1].x, qr);
         atomicAdd(&red[1].y, qi);
+        atomicAdd(&red[3].x, sr);
+        atomicAdd(&red[3].y, si);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const cplx c = mkc(red[0].x, red[0].y), qt = mkc(red[1].x, red[1].y);
-        const cplx cq0 = cmul(c, qt);
+        // near images apply to every near box; far images only to the boxes of other levels
+        const cplx cn = mkc(red[0].x, red[0].y), cf = mkc(red[2].x, red[2].y);
+        const cplx qt = mkc(red[1].x, red[1].y);
+        const cplx qo = a.fon.on ? csub(qt, mkc(red[3].x, red[3].y)) : qt;
+        const cplx cq0 = cadd(cmul(cn, qt), cmul(cf, qo));
         cq[0] = make_double2(cq0.x, cq0.y);
     }
 
@@ -145,6 +167,7 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
         for (int nb = nb0; nb < nb1; ++nb) {
             int s = a.near_src[nb];
             int s0 = T.s0[s], s1 = T.s1[s];
+            const bool fon_pair = a.fon.on && T.level[s] == l;   // far images already in M2L
             for (int base = s0; base < s1; base += TILE) {
                 int cnt = min(TILE, s1 - base);
                 __syncthreads();
@@ -175,7 +198,8 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                     float hr = 0.f, hi = 0.f;
                     for (int tm = 0; tm < ntm; ++tm) {
                         const float dw = tsz[tm] * zf + tszp[tm] * zs[j];   // w - w0 (real)
-                        for (int m = 0; m < tcnt[tm]; ++m) {
+                        const int lim = fon_pair ? tncnt[tm] : tcnt[tm];
+                        for (int m = 0; m < lim; ++m) {
                             const int sidx = tm * TEFMM_MAX_IMG + m;
                             const float4 wr = sWR[sidx];
                             const f2 w0 = f2{wr.x, wr.y}, r0s = f2{wr.z, wr.w};
@@ -241,6 +265,12 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                 accr += b.x * m;
                 acci += b.y * m;
             }
+            if (a.scale) {                // i k / (4 pi)
+                const double sr = -k.y / (4.0 * M_PI), si = k.x / (4.0 * M_PI);
+                const double vr = accr * sr - acci * si, vi = accr * si + acci * sr;
+                accr = vr;
+                acci = vi;
+            }
             int out = a.perm_t[t0 + ti];
             a.phi[2 * out] = accr;
             a.phi[2 * out + 1] = acci;
@@ -269,6 +299,8 @@ int near_field_fp32(tefmm_plan_s *P, double *phi, cudaStream_t st) {
     a.perm_t = P->shared_pts ? dp<int>(P->perm_s) : dp<int>(P->perm_t);
     a.beta = dp<cplx>(P->beta);
     a.im = img_view(P);
+    a.fon = fon_thresholds(P);
+    a.scale = P->opt.scale_output;
     a.phi = phi;
     k_near_fp32<<<P->n_nodes, 128, 0, st>>>(P->n_nodes, a);
     P->launches++;

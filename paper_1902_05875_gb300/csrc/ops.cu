@@ -256,7 +256,10 @@ __global__ void k_l2l(int off, int cnt, TreeArrays T, Cube cb, int p, int np, co
 
 // ------------------------------------------------------------------ M2L keys
 // (layout and field accessors in ops_common.cuh)
-__global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pair_t,
+// has_A[16]: a layer with up-up or down-down images; fonB / fonA [16][21]: a
+// layer with far images of its B' / A' terms at a level (far-of-near pairs
+// e >= nv_v come after the V pairs)
+__global__ void k_m2l_items(int64_t nv, int64_t nv_v, TreeArrays T, const int *__restrict__ pair_t,
                             const int *__restrict__ v_src, const int *__restrict__ has_A,
                             const cplx *__restrict__ kl, uint64_t *__restrict__ keys,
                             int *__restrict__ vals, int *flags) {
@@ -265,6 +268,20 @@ __global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pa
     int t = pair_t[e], s = v_src[e];
     int l = T.level[t], lay = T.layer[t], lays = T.layer[s];
     int dx = T.ix[t] - T.ix[s], dy = T.iy[t] - T.iy[s], dz = T.iz[t] - T.iz[s];
+    vals[2 * e] = (int)(2 * e);
+    vals[2 * e + 1] = (int)(2 * e + 1);
+    if (e >= nv_v) {                   // far-of-near pair of adjacent leaves of level l
+        const int *fonB = has_A + TEFMM_MAX_LAYERS, *fonA = fonB + TEFMM_MAX_LAYERS * (TEFMM_NBITS + 1);
+        const int li = lay * (TEFMM_NBITS + 1) + l;
+        if (abs(dx) > 1 || abs(dy) > 1 || abs(dz) > 1 || lay != lays) {
+            atomicOr(flags, FLAG_CHECK);
+            keys[2 * e] = keys[2 * e + 1] = ~0ULL;
+            return;
+        }
+        keys[2 * e] = fonB[li] ? fon_key(l, lay, dx, dy, 0, (uint64_t)(dz + KEY_OFF)) : ~0ULL;
+        keys[2 * e + 1] = fonA[li] ? fon_key(l, lay, dx, dy, 1, (uint64_t)(T.iz[t] + T.iz[s])) : ~0ULL;
+        return;
+    }
     // offsets must fit the keys' fields (a V pair lies within the neighbourhood of
     // its parent's colleagues; wavenumber-coarse levels widen that neighbourhood)
     if (abs(dx) > KEY_OFF || abs(dy) > KEY_OFF || (lay == lays && abs(dz) > KEY_OFF)) {
@@ -281,8 +298,6 @@ __global__ void k_m2l_items(int64_t nv, TreeArrays T, const int *__restrict__ pa
         keys[2 * e] = m2l_key(0, l, lay, dx, dy, (uint64_t)(dz + KEY_OFF));
         keys[2 * e + 1] = has_A[lay] ? m2l_key(1, l, lay, dx, dy, (uint64_t)(T.iz[t] + T.iz[s])) : ~0ULL;
     }
-    vals[2 * e] = (int)(2 * e);
-    vals[2 * e + 1] = (int)(2 * e + 1);
 }
 
 __global__ void k_heads(int64_t n, const uint64_t *__restrict__ keys, int *__restrict__ head,
@@ -324,7 +339,7 @@ __global__ void k_table_rep(int ntab, const uint64_t *__restrict__ keys, int *__
     const uint64_t key = keys[i];
     const int dx = key_dx(key), dy = key_dy(key);
     // a reversed cross key uses the table of the same key with rev = 0
-    const int nvar = key_kind(key) == 2 ? 16 : 8;
+    const int nvar = key_is_cross(key) ? 16 : 8;
     int rep = i, rdx = dx, rdy = dy;
     for (int v = 1; v < nvar; ++v) {
         int a = (v & 4) ? dy : dx, b = (v & 4) ? dx : dy;
@@ -408,7 +423,7 @@ __global__ void k_chunk_cnt(int nchunks, int64_t nvalid, const int *__restrict__
 }
 
 __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube cb, int P2, int np2,
-                         ImgView im, const int *__restrict__ rep_code, cplx *__restrict__ tables) {
+                         ImgView im, FonThr fon, const int *__restrict__ rep_code, cplx *__restrict__ tables) {
     int tb = blockIdx.x;
     if (tb >= ntab || (rep_code[tb] >> 3) != tb) return;   // copied by symmetry
     extern __shared__ double sm[];
@@ -441,7 +456,7 @@ __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__r
                 recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 3, a, b, acc);
             }
         }
-    } else {
+    } else if (kind == 1) {
         double zsum = __dadd_rn(2.0 * cb.lo[2], __dmul_rn((double)(w + 1), h));
         for (int ti = tf; ti < tf + tc; ++ti) {
             DevTerm t = im.terms[ti];
@@ -450,6 +465,36 @@ __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__r
             for (int j = t.first; j < t.first + t.count; ++j) {
                 cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
                 recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 1, a, b, acc);
+            }
+        }
+    } else {
+        // far-of-near (kind 2): the far images only, no free-space term
+        const int sub = (int)((key >> 43) & 1);
+        const int ww = (int)(key_w(key) & ((1ULL << 43) - 1));
+        const double thr = fon.thr[l];
+        if (sub == 0) {
+            double dz = (double)(ww - KEY_OFF) * h;
+            for (int ti = tf; ti < tf + tc; ++ti) {
+                DevTerm t = im.terms[ti];
+                if (t.tag != 2 && t.tag != 3) continue;
+                double W0 = __dadd_rn(__dmul_rn(t.sz, dz), t.c);
+                for (int j = t.first; j < t.first + t.count; ++j) {
+                    if (!(-im.Z[j].x >= thr)) continue;
+                    cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
+                    recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 3, a, b, acc);
+                }
+            }
+        } else {
+            double zsum = __dadd_rn(2.0 * cb.lo[2], __dmul_rn((double)(ww + 1), h));
+            for (int ti = tf; ti < tf + tc; ++ti) {
+                DevTerm t = im.terms[ti];
+                if (t.tag != 0 && t.tag != 1) continue;
+                double W0 = __dadd_rn(__dmul_rn(t.sz, zsum), t.c);
+                for (int j = t.first; j < t.first + t.count; ++j) {
+                    if (!(-im.Z[j].x >= thr)) continue;
+                    cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
+                    recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 1, a, b, acc);
+                }
             }
         }
     }
@@ -473,8 +518,7 @@ __global__ void k_m2l_fp64(int nchunks, const int *__restrict__ chunk_start,
     int tb = chunk_table[c];
     int cnt = chunk_cnt[c];
     int st = chunk_start[c];
-    int kind = key_kind(table_key[tb]);
-    const double *coef = kind == 0 ? cB : cA;
+    const double *coef = key_is_B(table_key[tb]) ? cB : cA;
     for (int g = threadIdx.x; g < np2; g += blockDim.x) tab[g] = tables[(int64_t)tb * np2 + g];
     for (int q = 0; q < cnt; ++q) {
         int item = sorted_vals[st + q];
@@ -577,6 +621,8 @@ __global__ void k_near_fp64(int nn, NearArgs a) {
         for (int nb = nb0; nb < nb1; ++nb) {
             int s = a.near_src[nb];
             int s0 = T.s0[s], s1 = T.s1[s];
+            // a same-level adjacent leaf: its far images went through M2L
+            const double thr = (a.fon.on && T.level[s] == l) ? a.fon.thr[l] : INFINITY;
             for (int base = s0; base < s1; base += TILE) {
                 int cnt = min(TILE, s1 - base);
                 __syncthreads();
@@ -602,6 +648,7 @@ __global__ void k_near_fp64(int nn, NearArgs a) {
                             double zeta = tgeo[tm][0] * zt + tgeo[tm][1] * zs[j] + tgeo[tm][2] - tgeo[tm][3];
                             for (int m = 0; m < tcnt[tm]; ++m) {
                                 cplx Z = imgZ[tm * TEFMM_MAX_IMG + m];
+                                if (-Z.x >= thr) continue;
                                 cplx w = mkc(zeta - Z.x, -Z.y);
                                 cplx R = csqrt_p(mkc(rho2 + w.x * w.x - w.y * w.y, 2.0 * w.x * w.y));
                                 gi = cadd(gi, cmul(imgA[tm * TEFMM_MAX_IMG + m], eikr_over_r(ik, R)));
@@ -637,6 +684,7 @@ __global__ void k_near_fp64(int nn, NearArgs a) {
                 loc.y += b.y * m;
             }
             tot = cadd(tot, loc);
+            if (a.scale) tot = cmul(tot, mkc(-k.y / (4.0 * M_PI), k.x / (4.0 * M_PI)));   // i k / (4 pi)
             int out = a.perm_t[t0 + ti];
             a.phi[2 * out] = tot.x;
             a.phi[2 * out + 1] = tot.y;
@@ -683,7 +731,7 @@ int upward_pass(tefmm_plan_s *P, cudaStream_t st) {
 }
 
 int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
-    const int64_t nv = P->n_v;
+    const int64_t nv = P->n_v + P->n_fon;
     P->n_tables = 0;
     P->n_tables_built = 0;
     P->n_chunks = 0;
@@ -695,14 +743,22 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
     TRY(dbuf_ensure(P->pair_slot_sorted, ni * 8));
     TRY(dbuf_ensure(P->pair_idx, ni * 4));
     TRY(dbuf_ensure(P->pair_idx_sorted, ni * 4));
-    // has_A per layer: any up-up or down-down term with images
-    int hasA[TEFMM_MAX_LAYERS] = {0};
-    for (auto &t : P->terms)
+    // has_A per layer: any up-up or down-down term with images; per (layer,
+    // level): far images of the B' (up-down, down-up) and A' terms
+    constexpr int NLV = TEFMM_NBITS + 1;
+    std::vector<int> flagsA(TEFMM_MAX_LAYERS * (1 + 2 * NLV), 0);
+    int *hasA = flagsA.data(), *fonB = hasA + TEFMM_MAX_LAYERS, *fonA = fonB + TEFMM_MAX_LAYERS * NLV;
+    const FonThr ft = fon_thresholds(P);
+    for (auto &t : P->terms) {
         if ((t.tag == 0 || t.tag == 1) && t.count > 0) hasA[t.layer] = 1;
-    TRY(dbuf_ensure(P->seg_tmp, sizeof(hasA)));
-    CUDA_TRY(cudaMemcpyAsync(P->seg_tmp.p, hasA, sizeof(hasA), cudaMemcpyHostToDevice, st));
+        for (int lv = 0; lv < NLV; ++lv)
+            for (int j = t.first; j < t.first + t.count; ++j)
+                if (-P->Z[j].x >= ft.thr[lv]) (t.tag >= 2 ? fonB : fonA)[t.layer * NLV + lv] = 1;
+    }
+    TRY(dbuf_ensure(P->seg_tmp, flagsA.size() * sizeof(int)));
+    CUDA_TRY(cudaMemcpyAsync(P->seg_tmp.p, flagsA.data(), flagsA.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     TreeArrays T = tree_arrays(P);
-    k_m2l_items<<<grid_for(nv, 256), 256, 0, st>>>(nv, T, dp<int>(P->pair_t), dp<int>(P->v_src),
+    k_m2l_items<<<grid_for(nv, 256), 256, 0, st>>>(nv, P->n_v, T, dp<int>(P->pair_t), dp<int>(P->v_src),
                                                    dp<int>(P->seg_tmp), dp<cplx>(P->d_k),
                                                    dp<uint64_t>(P->pair_slot),
                                                    dp<int>(P->pair_idx), dp<int>(P->flags));
@@ -790,7 +846,7 @@ int m2l_tables(tefmm_plan_s *P, cudaStream_t st) {
     const size_t sm = 6 * (size_t)tri(2 * P->p + 1) * sizeof(cplx);
     TRY(smem_optin(k_tables));
     k_tables<<<ntab, 256, sm, st>>>(ntab, dp<uint64_t>(P->table_slot), cube_of(P), 2 * P->p, np2,
-                                    img_view(P), dp<int>(P->table_rep), dp<cplx>(P->tables));
+                                    img_view(P), fon_thresholds(P), dp<int>(P->table_rep), dp<cplx>(P->tables));
     P->launches++;
     CUDA_TRY(cudaGetLastError());
     return tables_expand(P, 0, ntab, 1, dp<cplx>(P->tables), np2, st);
@@ -859,6 +915,8 @@ int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st) {
     a.perm_t = P->shared_pts ? dp<int>(P->perm_s) : dp<int>(P->perm_t);
     a.beta = dp<cplx>(P->beta);
     a.im = img_view(P);
+    a.fon = fon_thresholds(P);
+    a.scale = P->opt.scale_output;
     a.phi = phi;
     k_near_fp64<<<P->n_nodes, 128, 0, st>>>(P->n_nodes, a);
     P->launches++;

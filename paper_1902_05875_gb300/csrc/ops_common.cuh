@@ -49,6 +49,26 @@ struct ImgView {
     const cplx *k;
 };
 
+// Far-of-near reading: for a pair of adjacent leaves of level l, image j of a
+// same-layer term is "far" when -Re Z_j >= thr[l] = kappa_p sqrt(3) h_l,
+// kappa_p = 10^(10/(p+1)) (the combined displacement of target and source from
+// their leaf centres is at most sqrt(3) h_l, so a Taylor expansion of that
+// image term to order p errs by about kappa_p^-(p+1) = 1e-10 of it).  Far
+// images of such pairs go through M2L (key kind 2), the others through P2P.
+struct FonThr {
+    double thr[TEFMM_NBITS + 1];
+    int on;
+};
+
+inline FonThr fon_thresholds(const tefmm_plan_s *P) {
+    FonThr f{};
+    f.on = P->opt.far_of_near ? 1 : 0;
+    const double kap = pow(10.0, 10.0 / (double)(P->p + 1));
+    for (int l = 0; l <= TEFMM_NBITS; ++l)
+        f.thr[l] = f.on ? kap * sqrt(3.0) * (P->side / (double)(1 << l)) : INFINITY;
+    return f;
+}
+
 struct NearArgs {
     TreeArrays T;
     Cube cb;
@@ -59,6 +79,8 @@ struct NearArgs {
     const int *perm_t;
     const cplx *beta;
     ImgView im;
+    FonThr fon;
+    int scale;                 // multiply each potential by i k_l / (4 pi) of its layer
     double *phi;
 };
 
@@ -92,7 +114,11 @@ __host__ __device__ inline int slice_off(int p, int k3p) {
 // M2L keys (64 bits): kind(2) level(5) target layer(3) dx+15(5) dy+15(5) w(44).
 //   kind 0 = B (same layer; w = dz + 15),
 //   kind 1 = A (same layer; w = iz_t + iz_s),
-//   kind 2 = cross layer (w = source layer(3) iz_t(20) iz_s(20)); sorts last.
+//   kind 2 = far-of-near pair of adjacent leaves of one level: w = sub(1) at
+//            bit 43 and, for sub 0 (B': far images of the up-down and down-up
+//            terms) dz + 15, for sub 1 (A': far images of up-up and down-down)
+//            iz_t + iz_s,
+//   kind 3 = cross layer (w = rev(1) source layer(3) iz_t(20) iz_s(20)); sorts last.
 // dx, dy, dz are the target-minus-source box offsets of a V pair.  With
 // wavenumber admissibility the first translating level can pair boxes up to
 // 2^level - 1 apart, so the offset fields hold |d| <= KEY_OFF.
@@ -107,12 +133,21 @@ __host__ __device__ inline int key_layer(uint64_t k) { return (int)((k >> 54) & 
 __host__ __device__ inline int key_dx(uint64_t k) { return (int)((k >> 49) & 31) - KEY_OFF; }
 __host__ __device__ inline int key_dy(uint64_t k) { return (int)((k >> 44) & 31) - KEY_OFF; }
 __host__ __device__ inline uint64_t key_w(uint64_t k) { return k & ((1ULL << 44) - 1); }
+__host__ __device__ inline bool key_is_cross(uint64_t k) { return key_kind(k) == 3; }
+// the key's table is a B table (free space, up-down, down-up; or B'), else an A table
+__host__ __device__ inline bool key_is_B(uint64_t k) {
+    const int c = key_kind(k);
+    return c == 0 || (c == 2 && !((k >> 43) & 1));
+}
+__host__ __device__ inline uint64_t fon_key(int l, int lay, int dx, int dy, int sub, uint64_t w) {
+    return m2l_key(2, l, lay, dx, dy, ((uint64_t)sub << 43) | w);
+}
 // the same key with other horizontal offsets
 __host__ __device__ inline uint64_t key_with_dxdy(uint64_t k, int dx, int dy) {
     return (k & ~(1023ULL << 44)) | ((uint64_t)(dx + KEY_OFF) << 49) | ((uint64_t)(dy + KEY_OFF) << 44);
 }
 
-// Cross-layer M2L key: kind 2, w = rev(1) ls(3) iz_t(20) iz_s(20).  The fields
+// Cross-layer M2L key: kind 3, w = rev(1) ls(3) iz_t(20) iz_s(20).  The fields
 // describe the component (lt <- ls) whose fits and table the key uses.  rev = 0:
 // the V pairs of the key translate from a source box of layer ls into a target
 // box of layer lt.  rev = 1 (the pair's target layer has the smaller |k|): the
@@ -120,7 +155,7 @@ __host__ __device__ inline uint64_t key_with_dxdy(uint64_t k, int dx, int dy) {
 // (layer lt, izt, offset -dx, -dy), and use the transposed matrix of the key's
 // component scaled by (k_lt / k_ls)^2 (reciprocity).
 __host__ __device__ inline uint64_t xkey(int l, int lt, int ls, int dx, int dy, int izt, int izs, int rev = 0) {
-    return m2l_key(2, l, lt, dx, dy,
+    return m2l_key(3, l, lt, dx, dy,
                    ((uint64_t)rev << 43) | ((uint64_t)ls << 40) | ((uint64_t)izt << 20) | (uint64_t)izs);
 }
 __host__ __device__ inline int xkey_rev(uint64_t k) { return (int)((k >> 43) & 1); }

@@ -176,6 +176,7 @@ extern "C" int tefmm_default_options(tefmm_options *opt) {
         opt->zext[2 * l + 1] = NAN;
     }
     opt->kh_max = 3.5;
+    opt->far_of_near = 1;
     opt->algorithm = TEFMM_ALG_RECURRENCE;
     opt->split = TEFMM_SPLIT_TF32X3;
     opt->scale_output = 0;
@@ -198,6 +199,7 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
         o.n_images < 0 || o.n_images > TEFMM_MAX_IMG || o.n_samples < 8 || o.n_samples > 127 ||
         !(o.T1 > 0) || (o.precision != TEFMM_FP64 && o.precision != TEFMM_MIXED) ||
         isnan(o.kh_max) || (o.scale_output != 0 && o.scale_output != 1) ||
+        (o.far_of_near != 0 && o.far_of_near != 1) ||
         (o.algorithm != TEFMM_ALG_RECURRENCE && o.algorithm != TEFMM_ALG_TABLES))
         return TEFMM_ERR_INVALID_ARG;
     if (o.algorithm != TEFMM_ALG_RECURRENCE || o.split != TEFMM_SPLIT_TF32X3) return TEFMM_ERR_NOT_IMPLEMENTED;

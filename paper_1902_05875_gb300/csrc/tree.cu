@@ -555,6 +555,30 @@ __global__ void k_count_pairs(int n_nodes, const int *__restrict__ near_ptr,
     }
 }
 
+// far-of-near pairs: the near-list entries of a target leaf that are leaves of
+// its own level (adjacent by construction)
+__global__ void k_fon_count(int n_nodes, const int *__restrict__ level, const int *__restrict__ ptr,
+                            const int *__restrict__ src, int *__restrict__ cnt) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes) return;
+    int c = 0;
+    for (int a = ptr[t]; a < ptr[t + 1]; ++a) c += level[src[a]] == level[t];
+    cnt[t] = c;
+}
+__global__ void k_fon_fill(int n_nodes, const int *__restrict__ level, const int *__restrict__ ptr,
+                           const int *__restrict__ src, const int *__restrict__ fptr, int64_t base,
+                           int *__restrict__ pair_t, int *__restrict__ pair_s) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes) return;
+    int64_t o = base + fptr[t];
+    for (int a = ptr[t]; a < ptr[t + 1]; ++a)
+        if (level[src[a]] == level[t]) {
+            pair_t[o] = t;
+            pair_s[o] = src[a];
+            ++o;
+        }
+}
+
 __global__ void k_layer_mismatch(int n_nodes, const int *__restrict__ layer,
                                  const int *__restrict__ ptr, const int *__restrict__ src,
                                  int *flags) {
@@ -864,8 +888,9 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
     CUDA_TRY(cudaStreamSynchronize(st));
     P->n_v = tot[0];
     P->n_near = tot[1];
-    TRY(dbuf_ensure(P->v_src, (size_t)(P->n_v + 1) * 4));
-    TRY(dbuf_ensure(P->pair_t, (size_t)(P->n_v + 1) * 4));
+    // V pairs, then (at most one per near entry) the far-of-near pairs
+    TRY(dbuf_ensure(P->v_src, (size_t)(P->n_v + P->n_near + 1) * 4));
+    TRY(dbuf_ensure(P->pair_t, (size_t)(P->n_v + P->n_near + 1) * 4));
     TRY(dbuf_ensure(P->near_src, (size_t)(P->n_near + 1) * 4));
     for (int l = 0; l < NL; ++l) {
         int off = P->level_off[l], cnt = P->level_off[l + 1] - off;
@@ -895,6 +920,26 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
             nn, dp<int>(P->near_ptr), dp<int>(P->near_src), dp<int>(P->n_s0), dp<int>(P->n_s1),
             dp<int>(P->n_t0), dp<int>(P->n_t1), dp<int>(P->n_layer), dp<unsigned long long>(P->counters));
         P->launches++;
+    }
+    P->n_fon = 0;
+    if (P->opt.far_of_near && nn > 0) {
+        TRY(dbuf_ensure(P->fon_cnt, (size_t)(nn + 1) * 4));
+        TRY(dbuf_ensure(P->fon_ptr, (size_t)(nn + 1) * 4));
+        CUDA_TRY(cudaMemsetAsync(P->fon_cnt.p, 0, (size_t)(nn + 1) * 4, st));
+        k_fon_count<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_level), dp<int>(P->near_ptr),
+                                                       dp<int>(P->near_src), dp<int>(P->fon_cnt));
+        P->launches++;
+        TRY(scan_excl(P, dp<int>(P->fon_cnt), dp<int>(P->fon_ptr), nn + 1, st));
+        int nf = 0;
+        CUDA_TRY(cudaMemcpyAsync(&nf, dp<int>(P->fon_ptr) + nn, 4, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        P->n_fon = nf;
+        if (nf > 0) {
+            k_fon_fill<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_level), dp<int>(P->near_ptr),
+                                                          dp<int>(P->near_src), dp<int>(P->fon_ptr), P->n_v,
+                                                          dp<int>(P->pair_t), dp<int>(P->v_src));
+            P->launches++;
+        }
     }
     unsigned long long np2p[9] = {};
     CUDA_TRY(cudaMemcpyAsync(np2p, P->counters.p, 72, cudaMemcpyDeviceToHost, st));

@@ -32,7 +32,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("n_images", ctypes.c_int), ("n_samples", ctypes.c_int),
                 ("T1", ctypes.c_double), ("T0", ctypes.c_double), ("zext", ctypes.c_double * 32),
                 ("kh_max", ctypes.c_double), ("algorithm", ctypes.c_int), ("split", ctypes.c_int),
-                ("scale_output", ctypes.c_int)]
+                ("far_of_near", ctypes.c_int), ("scale_output", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -50,7 +50,7 @@ class Stats(ctypes.Structure):
                 ("ms_autotune", ctypes.c_double), ("n_tables_built", ctypes.c_int),
                 ("n_m2l_items", ctypes.c_int64), ("n_m2l_items_cross", ctypes.c_int64),
                 ("ms_m2l_kernel", ctypes.c_double), ("n_m2l_kernel_launches", ctypes.c_int),
-                ("n_p2p_pairs_layer", ctypes.c_int64 * 8)]
+                ("n_p2p_pairs_layer", ctypes.c_int64 * 8), ("n_fon_pairs", ctypes.c_int64)]
 
 
 EXPORTED = [
@@ -229,7 +229,7 @@ class Plan:
 
     def __init__(self, interfaces, k, p=6, leaf_cap=64, max_level=20, precision=FP64,
                  n_images=8, n_samples=101, T1=10.0, T0=0.0, zext=None, kh_max=3.5,
-                 scale_output=False, stream=None):
+                 far_of_near=True, scale_output=False, stream=None):
         lib = load()
         self.lib = lib
         k = np.asarray(k, dtype=complex).reshape(-1)
@@ -244,6 +244,7 @@ class Plan:
         opt.T1, opt.T0 = float(T1), float(T0)
         opt.kh_max = 0.0 if kh_max is None else float(kh_max)
         opt.scale_output = 1 if scale_output else 0
+        opt.far_of_near = 1 if far_of_near else 0
         if zext is not None:
             for l, (a, b) in enumerate(zext):
                 opt.zext[2 * l] = float(a)

@@ -71,3 +71,21 @@ def test_bench_config_mixed_matches_oracle(case):
     print(f"p=10 three-slab, mixed form vs oracle TE-FMM at {len(idx)} targets: "
           f"rel L2 {err:.2e}, max rel {worst:.2e}")
     assert err <= 2e-6, err
+
+
+def test_far_of_near_changes_the_fp64_form_below_its_bound(case):
+    """The device's far-of-near path (far images of adjacent same-level leaf
+    pairs through M2L) against every image in P2P, FP64 form, same images:
+    the two agree far below the method's error (1e-8), and pairs were moved."""
+    torch = need_gpu()
+    w, med, img, f, idx = case
+    out = {}
+    for fon in (True, False):
+        plan = make_plan(w, far_of_near=fon)
+        push_images(plan, img)
+        out[fon] = gpu_eval(plan, torch, w.src, w.q)
+        if fon:
+            assert plan.stats()["n_fon_pairs"] > 0
+    err = np.linalg.norm(out[True] - out[False]) / np.linalg.norm(out[False])
+    print(f"far-of-near on vs off (FP64 form, p=10): {err:.2e}")
+    assert err <= 1e-8, err

@@ -199,3 +199,35 @@ def test_wavenumber_rule_refines_coarse_levels():
         for s in lst:
             cover[tr.t0[t]:tr.t1[t], tr.s0[s]:tr.s1[s]] += 1
     assert np.all(cover == 1)
+
+
+def test_far_of_near_keeps_the_error():
+    """The far-of-near reading moves the images of adjacent same-level leaf
+    pairs with -Re Z >= 10^(10/(p+1)) sqrt(3) h out of the direct sum and into
+    M2L; at p = 8 on a three-slab case with small leaves (so that such images
+    exist) the error against the direct sum stays that of the plain form
+    (within 1.5x plus 1e-9), and images and pairs were moved."""
+    from oracle.tefmm import fon_threshold
+    from oracle.direct import direct_sum, cross_sum
+    w = W.three_layer_slabs(900, 8, 6, seed=6, n_images=16, half_width=0.4)
+    med = Medium(w.interfaces, w.k)
+    img = ImageTable(med, w.zext, n_images=w.n_images)
+    idx = np.random.default_rng(2).choice(len(w.src), 30, replace=False)
+    ref = direct_sum(med, img, w.src, w.q, w.src[idx]) + cross_sum(med, w.zext, w.src, w.q, w.src[idx], 16)
+    err, moved = {}, 0
+    for fon in (False, True):
+        f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images, far_of_near=fon).setup(w.src, w.src)
+        phi = f.evaluate(w.q, target_index=idx)
+        err[fon] = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+        if fon:
+            tr = f.tr
+            for (lt, ls), (_, P2P) in f.lists.items():
+                if lt != ls:
+                    continue
+                for t, lst in P2P.items():
+                    thr = fon_threshold(w.p, tr.side, int(tr.level[t]))
+                    nfar = sum(int(np.sum(-np.real(tt['Z']) >= thr)) for tt in img.terms[lt])
+                    moved += nfar * sum(1 for s in lst if tr.level[s] == tr.level[t])
+    print(err, moved)
+    assert moved > 0
+    assert err[True] <= 1.5 * err[False] + 1e-9, err
