@@ -48,9 +48,9 @@ METRIC = ("FMM matvec interactions/s (N_t*N_s per matvec time) at N=2M, mixed vs
 UNIT = "interactions/s"
 
 
-def _wl(name):
+def _wl(fn, *args, **kw):
     from paper_1902_05875_gb300 import workloads as W
-    return getattr(W, name)()
+    return getattr(W, fn)(*args, **kw)
 
 
 WORKLOADS = {
@@ -58,12 +58,15 @@ WORKLOADS = {
     "three_layer_slabs_n200k_p10": lambda: _wl("cfg_mixed_200k"),
     "three_layer_middle_n200k_p8": lambda: _wl("cfg_fp64_200k"),
     "three_layer_middle_n2000_p6": lambda: _wl("cfg_small"),
+    # deep adaptive trees: 32 Gaussian clusters (sigma 0.05) in the middle layer, p = 8
+    "clustered_n16M_p8": lambda: _wl("clustered", 16_000_000, 8, 64, seed=0, n_images=16,
+                                     name="clustered_n16M_p8"),
 }
 # the paper's Example 2 (irregular domains, three layers), p = 6, for the time-vs-N check
 for _n, _tag in ((250_000, "250k"), (500_000, "500k"), (1_000_000, "1M"), (2_000_000, "2M")):
     WORKLOADS[f"irregular_domains3_n{_tag}_p6"] = (
-        lambda n=_n, tag=_tag: __import__("paper_1902_05875_gb300.workloads", fromlist=["x"]).irregular_domains(
-            n, 3, p=6, leaf_cap=64, seed=0, n_images=16, name=f"irregular_domains3_n{tag}_p6"))
+        lambda n=_n, tag=_tag: _wl("irregular_domains", n, 3, p=6, leaf_cap=64, seed=0, n_images=16,
+                                   name=f"irregular_domains3_n{tag}_p6"))
 DEFAULT_WORKLOAD = "three_layer_slabs_n2M_p10"
 
 

@@ -200,3 +200,18 @@ def irregular_domains(n, n_layers=3, p=6, leaf_cap=64, seed=0, n_images=16, k=(0
     q = _charges(rng, len(src))
     return Workload(name or f"irregular_domains{n_layers}_n{n}_p{p}", d, list(k)[:n_layers], zext, src, q,
                     p, leaf_cap, n_images)
+
+
+def clustered(n, p=8, leaf_cap=64, seed=0, n_images=16, n_clusters=32, sigma=0.05, name=None):
+    """n points from n_clusters Gaussian clusters (standard deviation sigma,
+    centres uniform in the middle slab [-1,1]^2 x [-1.1,-0.1] of the
+    three-layer medium of the small workload, points clipped to the slab):
+    an adaptive octree many levels deep in the clusters and shallow between them."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.array([-1.0, -1.0, -1.1]), np.array([1.0, 1.0, -0.1])
+    centres = rng.uniform(lo, hi, size=(n_clusters, 3))
+    which = rng.integers(0, n_clusters, n)
+    src = np.clip(centres[which] + sigma * rng.standard_normal((n, 3)), lo, hi)
+    q = _charges(rng, n)
+    return Workload(name or f"clustered_n{n}_p{p}", THREE_LAYER_D, THREE_LAYER_K, THREE_LAYER_ZEXT, src, q, p,
+                    leaf_cap, n_images)

@@ -76,3 +76,15 @@ def test_irregular_domains_mixed_against_direct_sum():
     err = np.linalg.norm(phi[idx] - ref) / np.linalg.norm(ref)
     print(f"irregular domains, 60k points, p=8, mixed form vs direct sum at 40 targets: {err:.2e}")
     assert err <= 1e-5, err
+
+
+def test_clustered_deep_tree_fp64_matches_oracle():
+    """32 Gaussian clusters (sigma 0.05) in the middle layer: an adaptive tree
+    several levels deeper in the clusters than between them, with W and X
+    pairs; trees, lists and the FP64 form against the oracle as above."""
+    w = W.clustered(1500, p=4, leaf_cap=12, seed=3, n_clusters=8)
+    err, f = _parity(w)
+    depth = int(f.tr.level.max())
+    print(f"clustered: depth {depth}, FP64 form vs oracle TE-FMM {err:.2e}")
+    assert depth >= 5
+    assert err <= 1e-11, err
