@@ -16,7 +16,12 @@ The oracle is a plain, slow, readable restatement of the paper:
                      (Sec. 3.3, eq. ``recurrsion``, corrected form);
 * ``direct``      -- FP64 direct sum of the DCIM-approximated layered Green's
                      function (Sec. 3.2, eq. ``totalinteraction``), in C;
-* ``tefmm``       -- the CPU TE-FMM (Algorithms 1 and 2 of Sec. 3).
+* ``cross``       -- cross-layer components and their image fits (Sec. 3.3);
+* ``alg2``        -- Algorithm 2's tables of Sommerfeld integrals on a grid,
+                     interpolated and assembled into Cartesian derivatives
+                     (Sec. 4.2, eqs. ``sysdifferential``, ``symmetricdetable``);
+* ``tefmm``       -- the CPU TE-FMM (Algorithm 1 and the component loop of
+                     Sec. 3, with Algorithm 2's tables as an option).
 
 It shares no code with the CUDA path.
 """

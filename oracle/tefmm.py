@@ -92,6 +92,7 @@ import numpy as np
 
 from .derivs import multi_indices, index_map, n_coeffs, taylor_h0
 from . import cross as xl
+from . import alg2 as a2
 
 NBITS = 20
 # wavenumber admissibility bound (see Trees): on levels where k_max h > KH_MAX,
@@ -485,10 +486,18 @@ class TEFMM:
     """Algorithm 1 + the component loop, for every (target layer, source layer)."""
 
     def __init__(self, med, images, p, leaf_cap, max_level=NBITS, cube=None, zext=None,
-                 cross_images=None, n_images=None, kh_max=KH_MAX, far_of_near=True):
+                 cross_images=None, n_images=None, kh_max=KH_MAX, far_of_near=True,
+                 algorithm=1, table_n=64):
         self.med = med
         self.kh_max = kh_max
-        self.far_of_near = far_of_near
+        # Algorithm 2 (Sec. 4.2): same-layer reaction derivatives from
+        # interpolated tables of Sommerfeld integrals (oracle.alg2) instead of
+        # complex images; the near field keeps the images, and far-of-near
+        # (which splits the image set) does not apply
+        self.algorithm = algorithm
+        self.table_n = table_n
+        self.alg2 = {}
+        self.far_of_near = far_of_near and algorithm == 1
         self.images = images
         self.zext = zext if zext is not None else (images.zext if images is not None else None)
         # cross-layer images: dict (lt, ls, direction, level, izs, k3p) -> (A, Z);
@@ -552,6 +561,8 @@ class TEFMM:
         mi2 = multi_indices(P2)
         odd3 = (-1.0) ** mi2[:, 2]
         terms = {t['tag']: t for t in self.images.terms[l]} if self.images is not None else {}
+        if self.algorithm == 2:
+            return self._tables_alg2(l, h, keysB, keysA, odd3)
         TB = np.zeros((len(keysB), len(mi2)), dtype=complex)
         TA = np.zeros((len(keysA), len(mi2)), dtype=complex)
         if len(keysB):
@@ -584,6 +595,58 @@ class TEFMM:
                         continue
                     tab = A * taylor_h0(X0, Y0, W0 - t['zeta_min'] - Z, k, P2)
                     TA += tab if sgn is None else tab * sgn[None, :]
+        return TB, TA
+
+    def alg2_tables(self, l):
+        """The Algorithm 2 tables of layer l, {tag: Alg2Table}, over the grid
+        ranges of all the layer's same-layer M2L pairs (built once)."""
+        if l not in self.alg2:
+            tr = self.tr
+            V = self.lists[(l, l)][0] if (l, l) in self.lists else {}
+            keys = []
+            for t, lst in V.items():
+                for s in lst:
+                    lev = int(tr.level[t])
+                    h = tr.side / float(1 << lev)
+                    keys.append((h, int(tr.ix[t] - tr.ix[s]), int(tr.iy[t] - tr.iy[s]), int(tr.iz[t] - tr.iz[s]),
+                                 2.0 * tr.lo[2] + (int(tr.iz[t] + tr.iz[s]) + 1) * h))
+            tabs = {}
+            if keys:
+                rho_max, rng = a2.layer_ranges(self.med, l, keys)
+                for tag, (lo, hi) in rng.items():
+                    tabs[tag] = a2.Alg2Table(a2.medium_T(self.med, l, tag, 2 * self.p), 2 * self.p,
+                                             rho_max, lo, hi, self.table_n)
+            self.alg2[l] = tabs
+        return self.alg2[l]
+
+    def _tables_alg2(self, l, h, keysB, keysA, odd3):
+        """_tables with the reaction part from the Algorithm 2 tables: the
+        same combinations (B = free + ud + (-1)^{g3} du, A = uu + (-1)^{g3} dd)
+        with each term's D^g F / g! interpolated at its image distance."""
+        P2 = 2 * self.p
+        k = self.med.k[l]
+        tabs = self.alg2_tables(l)
+        terms = {tag: (sz, c) for tag, sz, szp, c in self.med.same_layer_terms(l)}
+        n = len(multi_indices(P2))
+        TB = np.zeros((len(keysB), n), dtype=complex)
+        TA = np.zeros((len(keysA), n), dtype=complex)
+        for T, keys, tags in ((TB, keysB, ('ud', 'du')), (TA, keysA, ('uu', 'dd'))):
+            if not len(keys):
+                continue
+            X0 = keys[:, 0] * h
+            Y0 = keys[:, 1] * h
+            if T is TB:
+                zarg = keys[:, 2] * h
+                T += taylor_h0(X0, Y0, zarg.astype(complex), k, P2)
+            else:
+                zarg = 2.0 * self.tr.lo[2] + (keys[:, 2] + 1) * h
+            for tag in tags:
+                if tag not in terms:
+                    continue
+                sz, c = terms[tag]
+                sgn = odd3 if tag in ('du', 'dd') else 1.0
+                for i in range(len(keys)):
+                    T[i] += tabs[tag].derivatives(float(X0[i]), float(Y0[i]), sz * zarg[i] + c) * sgn
         return TB, TA
 
     # -- downward pass -------------------------------------------------------
