@@ -474,6 +474,9 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + [BATCHED])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--algorithm", type=int, default=1, choices=[1, 2],
+                    help="1: DCIM image recurrence; 2: Sommerfeld-integral tables (same-layer reaction M2L)")
+    ap.add_argument("--table-n", type=int, default=0, help="Algorithm 2 grid points per direction (0: 64)")
     ap.add_argument("--no-fp64-form", action="store_true",
                     help="skip the FP64-form step that the mixed form is compared with")
     ap.add_argument("--accuracy-samples", type=int, default=1000,
@@ -497,9 +500,9 @@ def main():
     from paper_1902_05875_gb300 import tefmm
     mixed = args.precision == "mixed"
 
-    def make(prec):
+    def make(prec, algorithm=args.algorithm):
         return tefmm.Plan(w.interfaces, w.k, p=w.p, leaf_cap=w.leaf_cap, n_images=w.n_images,
-                          zext=w.zext, precision=prec)
+                          zext=w.zext, precision=prec, algorithm=algorithm, table_n=args.table_n)
     plan = make(tefmm.MIXED if mixed else tefmm.FP64)
     x, y, z = [torch.tensor(np.ascontiguousarray(w.src[:, i]), device=dev) for i in range(3)]
     q = torch.tensor(w.q, device=dev)
@@ -586,7 +589,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+tf32x3/f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": w.name, "n": N, "p": w.p, "leaf_cap": w.leaf_cap, "n_images": w.n_images,
-                   "layers": len(w.k), "precision": args.precision,
+                   "layers": len(w.k), "precision": args.precision, "algorithm": args.algorithm,
                    "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "phases_ms": ph,
@@ -636,6 +639,20 @@ def main():
         if phi64 is not None:
             acc["fp64_vs_direct_rel_l2"] = float(np.linalg.norm(phi64[idx] - ref) / np.linalg.norm(ref))
             acc["fp64_vs_direct"] = err_stats(phi64[idx], ref, lay)
+        if args.algorithm == 2:
+            # the same form with Algorithm 1's recurrence derivatives, at the same targets
+            p1 = make(tefmm.MIXED if mixed else tefmm.FP64, algorithm=1)
+            out1 = torch.empty_like(out)
+            p1.eval(x, y, z, q, out=out1)
+            phi1 = out1.cpu().numpy()
+            del p1
+            torch.cuda.empty_cache()
+            acc["tables_vs_recurrence"] = {
+                "tables_vs_direct": err_stats(phi[idx], ref, lay),
+                "recurrence_vs_direct": err_stats(phi1[idx], ref, lay),
+                "tables_vs_recurrence_rel_l2": float(np.linalg.norm(phi - phi1) / np.linalg.norm(phi1)),
+                "table_n": args.table_n or 64, "alg2_tables": st["n_alg2_tables"],
+                "ms_table_build": st["ms_alg2_build"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:

@@ -56,7 +56,8 @@ extern "C" {
 #define TEFMM_MIXED 1  /* M2L on tensor cores and P2P in FP32; FP64 tables and sums   */
 
 #define TEFMM_ALG_RECURRENCE 1 /* Algorithm 1: DCIM images + derivative recurrence (Sec. 3.3) */
-#define TEFMM_ALG_TABLES 2     /* Algorithm 2/3 (Sec. 4): symmetric-derivative tables          */
+#define TEFMM_ALG_TABLES 2     /* Algorithm 2/3 (Sec. 4.2): same-layer reaction derivatives from
+                                  interpolated tables of Sommerfeld integrals               */
 
 #define TEFMM_SPLIT_TF32X3 0   /* mixed form: FP32 operands split hi + lo in TF32, three products
                                   (hi*hi + hi*lo + lo*hi) with FP32 accumulation                */
@@ -86,8 +87,25 @@ typedef struct {
                               first translating level may pair boxes at most 15 apart:
                               a medium that needs more coarse levels returns
                               TEFMM_ERR_NOT_IMPLEMENTED from the evaluation.          */
-    int algorithm;         /* TEFMM_ALG_RECURRENCE (default); TEFMM_ALG_TABLES is not
-                              built: TEFMM_ERR_NOT_IMPLEMENTED                         */
+    int algorithm;         /* TEFMM_ALG_RECURRENCE (default): every M2L derivative from
+                              the DCIM images by the recurrence of Sec. 3.3.
+                              TEFMM_ALG_TABLES (Sec. 4.2, eqs. ``sysdifferential`` and
+                              ``symmetricdetable``): the same-layer reaction derivatives
+                              D^g u_tau / g! from tables of the Sommerfeld integrals
+                              T_{m,nu,n}(rho, zeta) = (1/k) int k_rho^{m+1} J_nu(k_rho rho)
+                              (i k_z)^n e^{i k_z zeta} s_tau / k_z dk_rho  (m + n <= 2p,
+                              nu = m, m-2, ..), one table per same-layer term tau, on a
+                              uniform table_n x table_n grid over rho in [0, rho_max] and
+                              the term's image distance zeta in [zeta_lo, zeta_hi], the
+                              ranges of the layer's M2L pairs (built on the device by
+                              contour quadrature when the geometry is set, rebuilt when a
+                              new geometry leaves the ranges); FP64 degree-7 Lagrange
+                              interpolation in each direction, assembled into Cartesian
+                              derivatives through D+- = d_x +- i d_y.  The free-space part,
+                              cross-layer components and the near field keep Algorithm 1;
+                              far_of_near is ignored.  A geometry whose same-layer pairs
+                              reach zeta <= 0 (box centres beyond the layer's interface,
+                              where the integral diverges) is TEFMM_ERR_NOT_IMPLEMENTED. */
     int split;             /* tensor-core split of the mixed form: TEFMM_SPLIT_TF32X3
                               (the only one built; others TEFMM_ERR_NOT_IMPLEMENTED)  */
     int far_of_near;       /* 1 (default): for two adjacent leaves of one level, the DCIM
@@ -100,6 +118,8 @@ typedef struct {
                               (Sec. 3.1: free term h0(k|r - r'|), factor i k_l/(4 pi)
                               omitted); 1: every potential multiplied by i k_l/(4 pi)
                               of its target's layer l                                  */
+    int table_n;           /* TEFMM_ALG_TABLES: grid points per direction, 8..512;
+                              0 (default) = 64                                         */
 } tefmm_options;
 
 typedef struct {
@@ -138,6 +158,8 @@ typedef struct {
     int n_m2l_kernel_launches; /* ... and their number                               */
     int64_t n_p2p_pairs_layer[8]; /* near-field particle pairs by target layer        */
     int64_t n_fon_pairs;   /* last eval: leaf pairs whose far images went through M2L */
+    int n_alg2_tables;     /* TEFMM_ALG_TABLES: Sommerfeld-integral tables held        */
+    double ms_alg2_build;  /* ... host time of the last (re)build of those tables      */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,
@@ -335,6 +357,20 @@ int tefmm_plan_cross_images(tefmm_plan plan, int *n_fits, int *keys, int *counts
  * more than 32 images). */
 int tefmm_plan_set_cross_images(tefmm_plan plan, int n_fits, const int *keys, const int *counts,
                                 const double *A, const double *Z);
+
+/* Read one Algorithm 2 table (Sec. 4.2, eq. ``symmetricdetable``) of a plan
+ * made with TEFMM_ALG_TABLES, as built for its last geometry: the table of
+ * same-layer term ``tag`` (0 up-up, 1 down-down, 2 up-down, 3 down-up) of
+ * ``layer``.  Outputs (host): *n grid points per direction, *n_entries
+ * entries per point (the T_{m,nu,n} in the order m = 0..2p, nu = m mod 2,
+ * .., m step 2, n = 0..2p - m), range[3] = (rho_max, zeta_lo, zeta_hi) and,
+ * unless T is NULL, T[2 * ((i * n + j) * n_entries + e)] (+1) = real (imag)
+ * part of entry e at rho_i = i rho_max / (n - 1), zeta_j = zeta_lo + j
+ * (zeta_hi - zeta_lo) / (n - 1).  Synchronous.
+ * Errors: INVALID_ARG (no such table: other algorithm, no geometry, or the
+ * layer has no M2L pairs or no such term), CUDA. */
+int tefmm_plan_get_alg2_table(tefmm_plan plan, int layer, int tag, int *n, int *n_entries,
+                              double *range, double *T);
 
 /* ---- test hooks for the error paths --------------------------------------
  * No counterpart in the paper; used by the tests.

@@ -597,22 +597,28 @@ class TEFMM:
                     TA += tab if sgn is None else tab * sgn[None, :]
         return TB, TA
 
+    def alg2_ranges(self, l):
+        """Grid ranges of the Algorithm 2 tables of layer l over all its
+        same-layer M2L pairs: (rho_max, {tag: (zeta_lo, zeta_hi)}), or None."""
+        tr = self.tr
+        V = self.lists[(l, l)][0] if (l, l) in self.lists else {}
+        keys = []
+        for t, lst in V.items():
+            for s in lst:
+                lev = int(tr.level[t])
+                h = tr.side / float(1 << lev)
+                keys.append((h, int(tr.ix[t] - tr.ix[s]), int(tr.iy[t] - tr.iy[s]), int(tr.iz[t] - tr.iz[s]),
+                             2.0 * tr.lo[2] + (int(tr.iz[t] + tr.iz[s]) + 1) * h))
+        return a2.layer_ranges(self.med, l, keys) if keys else None
+
     def alg2_tables(self, l):
         """The Algorithm 2 tables of layer l, {tag: Alg2Table}, over the grid
         ranges of all the layer's same-layer M2L pairs (built once)."""
         if l not in self.alg2:
-            tr = self.tr
-            V = self.lists[(l, l)][0] if (l, l) in self.lists else {}
-            keys = []
-            for t, lst in V.items():
-                for s in lst:
-                    lev = int(tr.level[t])
-                    h = tr.side / float(1 << lev)
-                    keys.append((h, int(tr.ix[t] - tr.ix[s]), int(tr.iy[t] - tr.iy[s]), int(tr.iz[t] - tr.iz[s]),
-                                 2.0 * tr.lo[2] + (int(tr.iz[t] + tr.iz[s]) + 1) * h))
             tabs = {}
-            if keys:
-                rho_max, rng = a2.layer_ranges(self.med, l, keys)
+            r = self.alg2_ranges(l)
+            if r is not None:
+                rho_max, rng = r
                 for tag, (lo, hi) in rng.items():
                     tabs[tag] = a2.Alg2Table(a2.medium_T(self.med, l, tag, 2 * self.p), 2 * self.p,
                                              rho_max, lo, hi, self.table_n)

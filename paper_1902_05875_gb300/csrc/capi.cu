@@ -146,6 +146,7 @@ int geometry(tefmm_plan P, int64_t ns, const double *sx, const double *sy, const
     TRY(lists_build(P, st));
     TRY(check_flags(P, st));
     TRY(m2l_prepare(P, st));
+    TRY(alg2_prepare(P, st));
     TRY(cross_prepare(P, st));
     CUDA_TRY(cudaEventRecord(P->ev[1], st));
     return TEFMM_OK;
@@ -276,6 +277,8 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
         for (int i = 0; i + 1 < P->kev_used; i += 2) o->ms_m2l_kernel += elapsed(P->kev[i], P->kev[i + 1]);
     for (int l = 0; l < 8; ++l) o->n_p2p_pairs_layer[l] = P->p2p_by_layer[l];
     o->n_fon_pairs = P->n_fon;
+    o->n_alg2_tables = (int)P->a2.size();
+    o->ms_alg2_build = P->ms_alg2_build;
     o->leaf_cap_used = P->leaf_cap_eff;
     o->ms_autotune = P->ms_autotune;
     o->n_tables_built = P->n_tables_built;

@@ -104,6 +104,12 @@ struct TermDesc {          // one same-layer reaction term of one layer
     double sz, szp, c, zmin;
 };
 
+struct Alg2Table {         // one Algorithm 2 table (host record of a device buffer)
+    int layer = 0, tag = 0, P2 = 0, n = 0, ne = 0;
+    double rho_max = 0, zlo = 0, zhi = 0;
+    cplx *T = nullptr;     // device [n][n][ne]
+};
+
 struct DevTerm {           // POD copy for kernels
     double sz, szp, c, zmin;
     int first, count, layer, tag;
@@ -187,6 +193,11 @@ struct tefmm_plan_s {
     int64_t n_chunks = 0;
     std::vector<int> chunk_key_host;   // mixed form: chunk -> table, copied when the geometry is built
     int chunk_pairs = 16;     // pairs per M2L work chunk (FP64 SIMT: 16, tensor cores: 512)
+
+    // Algorithm 2: one Sommerfeld-integral table per (layer, same-layer term),
+    // [n][n][entries] complex, over the ranges of the last geometry's keys
+    std::vector<Alg2Table> a2;
+    double ms_alg2_build = 0.0;
 
     // cross-layer components: fitted images (cached per root-cube geometry),
     // per-table image ranges and tables
@@ -300,3 +311,7 @@ int cross_prepare(tefmm_plan_s *P, cudaStream_t st);
 int cross_tables(tefmm_plan_s *P, cudaStream_t st);
 int cross_apply(tefmm_plan_s *P, cudaStream_t st);
 void cross_release(tefmm_plan_s *P);
+// alg2.cu
+int alg2_prepare(tefmm_plan_s *P, cudaStream_t st);
+void alg2_release(tefmm_plan_s *P);
+int alg2_entries(int P2);

@@ -21,6 +21,7 @@
 #include <cub/cub.cuh>
 
 #include "ops_common.cuh"
+#include "alg2.cuh"
 
 namespace {
 
@@ -423,7 +424,7 @@ __global__ void k_chunk_cnt(int nchunks, int64_t nvalid, const int *__restrict__
 }
 
 __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__restrict__ table_key, Cube cb, int P2, int np2,
-                         ImgView im, FonThr fon, const int *__restrict__ rep_code, cplx *__restrict__ tables) {
+                         ImgView im, FonThr fon, int a2_on, const int *__restrict__ rep_code, cplx *__restrict__ tables) {
     int tb = blockIdx.x;
     if (tb >= ntab || (rep_code[tb] >> 3) != tb) return;   // copied by symmetry
     extern __shared__ double sm[];
@@ -451,6 +452,7 @@ __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__r
             DevTerm t = im.terms[ti];
             if (t.tag != 2 && t.tag != 3) continue;
             double W0 = __dadd_rn(__dmul_rn(t.sz, dz), t.c);
+            if (a2_on) continue;   // Algorithm 2: added by k_tables_a2
             for (int j = t.first; j < t.first + t.count; ++j) {
                 cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
                 recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 3, a, b, acc);
@@ -462,6 +464,7 @@ __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__r
             DevTerm t = im.terms[ti];
             if (t.tag != 0 && t.tag != 1) continue;
             double W0 = __dadd_rn(__dmul_rn(t.sz, zsum), t.c);
+            if (a2_on) continue;
             for (int j = t.first; j < t.first + t.count; ++j) {
                 cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
                 recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 1, a, b, acc);
@@ -497,6 +500,34 @@ __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__r
                 }
             }
         }
+    }
+}
+
+// Algorithm 2: the reaction terms of the same-layer keys of kinds 0 and 1 from
+// their Sommerfeld-integral tables, added to the tables k_tables started
+// (free-space part); the image distance as in k_tables.
+__global__ void __launch_bounds__(256) k_tables_a2(int ntab, const uint64_t *__restrict__ table_key, Cube cb,
+                                                   int np2, ImgView im, A2View a2,
+                                                   const int *__restrict__ rep_code, cplx *__restrict__ tables) {
+    const int tb = blockIdx.x;
+    if (tb >= ntab || (rep_code[tb] >> 3) != tb) return;
+    const uint64_t key = table_key[tb];
+    const int kind = key_kind(key);
+    if (kind > 1) return;
+    extern __shared__ double sm[];
+    const int l = key_level(key), lay = key_layer(key);
+    const int w = (int)key_w(key);
+    const double h = box_h(cb.side, l);
+    const double X = (double)key_dx(key) * h, Y = (double)key_dy(key) * h;
+    const double zarg = kind == 0 ? (double)(w - KEY_OFF) * h
+                                  : __dadd_rn(2.0 * cb.lo[2], __dmul_rn((double)(w + 1), h));
+    const int tf = im.lt_first[lay], tc = im.lt_count[lay];
+    for (int ti = tf; ti < tf + tc; ++ti) {
+        const DevTerm t = im.terms[ti];
+        if (kind == 0 ? t.tag < 2 : t.tag > 1) continue;
+        const double W0 = __dadd_rn(__dmul_rn(t.sz, zarg), t.c);
+        alg2_accumulate(a2, a2.t[lay][t.tag], X, Y, W0, t.tag == 1 || t.tag == 3, (cplx *)sm, np2,
+                        tables + (int64_t)tb * np2);
     }
 }
 
@@ -845,9 +876,17 @@ int m2l_tables(tefmm_plan_s *P, cudaStream_t st) {
     TRY(dbuf_ensure(P->tables, (size_t)ntab * np2 * sizeof(cplx)));
     const size_t sm = 6 * (size_t)tri(2 * P->p + 1) * sizeof(cplx);
     TRY(smem_optin(k_tables));
+    const A2View a2 = a2_view(P);
     k_tables<<<ntab, 256, sm, st>>>(ntab, dp<uint64_t>(P->table_slot), cube_of(P), 2 * P->p, np2,
-                                    img_view(P), fon_thresholds(P), dp<int>(P->table_rep), dp<cplx>(P->tables));
+                                    img_view(P), fon_thresholds(P), a2.on, dp<int>(P->table_rep), dp<cplx>(P->tables));
     P->launches++;
+    if (a2.on) {
+        const size_t sm2 = (size_t)a2_smem_cplx(a2.P2, a2.ne) * sizeof(cplx);
+        TRY(smem_optin(k_tables_a2));
+        k_tables_a2<<<ntab, 256, sm2, st>>>(ntab, dp<uint64_t>(P->table_slot), cube_of(P), np2, img_view(P), a2,
+                                            dp<int>(P->table_rep), dp<cplx>(P->tables));
+        P->launches++;
+    }
     CUDA_TRY(cudaGetLastError());
     return tables_expand(P, 0, ntab, 1, dp<cplx>(P->tables), np2, st);
 }

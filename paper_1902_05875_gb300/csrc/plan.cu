@@ -180,6 +180,7 @@ extern "C" int tefmm_default_options(tefmm_options *opt) {
     opt->algorithm = TEFMM_ALG_RECURRENCE;
     opt->split = TEFMM_SPLIT_TF32X3;
     opt->scale_output = 0;
+    opt->table_n = 0;
     return TEFMM_OK;
 }
 
@@ -200,9 +201,11 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
         !(o.T1 > 0) || (o.precision != TEFMM_FP64 && o.precision != TEFMM_MIXED) ||
         isnan(o.kh_max) || (o.scale_output != 0 && o.scale_output != 1) ||
         (o.far_of_near != 0 && o.far_of_near != 1) ||
-        (o.algorithm != TEFMM_ALG_RECURRENCE && o.algorithm != TEFMM_ALG_TABLES))
+        (o.algorithm != TEFMM_ALG_RECURRENCE && o.algorithm != TEFMM_ALG_TABLES) ||
+        (o.table_n != 0 && (o.table_n < 8 || o.table_n > 512)))
         return TEFMM_ERR_INVALID_ARG;
-    if (o.algorithm != TEFMM_ALG_RECURRENCE || o.split != TEFMM_SPLIT_TF32X3) return TEFMM_ERR_NOT_IMPLEMENTED;
+    if (o.split != TEFMM_SPLIT_TF32X3) return TEFMM_ERR_NOT_IMPLEMENTED;
+    if (o.algorithm == TEFMM_ALG_TABLES) o.far_of_near = 0;   // it splits image sets the tables replace
     // default particle ranges: the whole layer (top/bottom: one unit beyond the interface)
     for (int l = 0; l < n_layers; ++l) {
         double top = (l == 0) ? (n_layers > 1 ? interfaces[0] + 1.0 : 1.0) : interfaces[l - 1];
@@ -270,6 +273,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
                    &P->h_in, &P->h_out, &P->tc_ah, &P->tc_al, &P->tc_bt, &P->tc_cfA, &P->tc_cfB, &P->tc_W};
     for (DBuf *b : all) dbuf_free(*b);
     cross_release(P);
+    alg2_release(P);
     for (int i = 0; i < 12; ++i)
         if (P->ev[i]) cudaEventDestroy(P->ev[i]);
     for (cudaEvent_t e : P->kev) cudaEventDestroy(e);

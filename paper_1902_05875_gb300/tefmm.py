@@ -18,6 +18,7 @@ OK = 0
 ERR_INVALID_ARG = -1
 ERR_OOM = -4
 ERR_FIT_FAILED = -6
+ERR_NOT_IMPLEMENTED = -8
 ERR_TIMEOUT = -10
 INJECT_ALLOC = 1
 INJECT_FIT = 2
@@ -32,7 +33,7 @@ class Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("n_images", ctypes.c_int), ("n_samples", ctypes.c_int),
                 ("T1", ctypes.c_double), ("T0", ctypes.c_double), ("zext", ctypes.c_double * 32),
                 ("kh_max", ctypes.c_double), ("algorithm", ctypes.c_int), ("split", ctypes.c_int),
-                ("far_of_near", ctypes.c_int), ("scale_output", ctypes.c_int)]
+                ("far_of_near", ctypes.c_int), ("scale_output", ctypes.c_int), ("table_n", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -50,7 +51,8 @@ class Stats(ctypes.Structure):
                 ("ms_autotune", ctypes.c_double), ("n_tables_built", ctypes.c_int),
                 ("n_m2l_items", ctypes.c_int64), ("n_m2l_items_cross", ctypes.c_int64),
                 ("ms_m2l_kernel", ctypes.c_double), ("n_m2l_kernel_launches", ctypes.c_int),
-                ("n_p2p_pairs_layer", ctypes.c_int64 * 8), ("n_fon_pairs", ctypes.c_int64)]
+                ("n_p2p_pairs_layer", ctypes.c_int64 * 8), ("n_fon_pairs", ctypes.c_int64),
+                ("n_alg2_tables", ctypes.c_int), ("ms_alg2_build", ctypes.c_double)]
 
 
 EXPORTED = [
@@ -60,7 +62,7 @@ EXPORTED = [
     "tefmm_export_expansions", "tefmm_fit_images_noalloc", "tefmm_plan_cross_images",
     "tefmm_eval_batched", "tefmm_set_points", "tefmm_apply", "tefmm_plan_set_cross_images",
     "tefmm_plan_status", "tefmm_batch_graph_create", "tefmm_batch_graph_launch", "tefmm_batch_graph_destroy",
-    "tefmm_debug_inject", "tefmm_debug_wait_probe",
+    "tefmm_debug_inject", "tefmm_debug_wait_probe", "tefmm_plan_get_alg2_table",
 ]
 
 _lib = None
@@ -104,6 +106,7 @@ def load(build_if_needed=True):
     lib.tefmm_export_expansions.argtypes = [P, D, D]
     lib.tefmm_plan_set_cross_images.argtypes = [P, ctypes.c_int, I, I, D, D]
     lib.tefmm_plan_status.argtypes = [P, P]
+    lib.tefmm_plan_get_alg2_table.argtypes = [P, ctypes.c_int, ctypes.c_int, I, I, D, D]
     lib.tefmm_debug_inject.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.tefmm_debug_wait_probe.argtypes = [P, ctypes.c_int, P]
     lib.tefmm_batch_graph_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
@@ -229,7 +232,7 @@ class Plan:
 
     def __init__(self, interfaces, k, p=6, leaf_cap=64, max_level=20, precision=FP64,
                  n_images=8, n_samples=101, T1=10.0, T0=0.0, zext=None, kh_max=3.5,
-                 far_of_near=True, scale_output=False, stream=None):
+                 far_of_near=True, scale_output=False, algorithm=1, table_n=0, stream=None):
         lib = load()
         self.lib = lib
         k = np.asarray(k, dtype=complex).reshape(-1)
@@ -245,6 +248,8 @@ class Plan:
         opt.kh_max = 0.0 if kh_max is None else float(kh_max)
         opt.scale_output = 1 if scale_output else 0
         opt.far_of_near = 1 if far_of_near else 0
+        opt.algorithm = int(algorithm)
+        opt.table_n = int(table_n)
         if zext is not None:
             for l, (a, b) in enumerate(zext):
                 opt.zext[2 * l] = float(a)
@@ -455,6 +460,23 @@ class Plan:
             out[(lt, ls, 'up' if d == 0 else 'down', lev, izs, k3p)] = (
                 A[2 * j] + 1j * A[2 * j + 1], Z[2 * j] + 1j * Z[2 * j + 1])
         return out
+
+    def alg2_table(self, layer, tag, values=True):
+        """One Algorithm 2 table (``tefmm_plan_get_alg2_table``): (rho_max,
+        zeta_lo, zeta_hi, T) with T complex of shape (n, n, entries) indexed
+        [i_rho, j_zeta, entry], or None for T when values is False."""
+        n, ne = ctypes.c_int(), ctypes.c_int()
+        rng = np.zeros(3)
+        _check(self.lib.tefmm_plan_get_alg2_table(self.h, int(layer), int(tag), ctypes.byref(n), ctypes.byref(ne),
+                                                  _dptr(rng), None), "tefmm_plan_get_alg2_table")
+        T = None
+        if values:
+            buf = np.zeros(2 * n.value * n.value * ne.value)
+            _check(self.lib.tefmm_plan_get_alg2_table(self.h, int(layer), int(tag), ctypes.byref(n),
+                                                      ctypes.byref(ne), _dptr(rng), _dptr(buf)),
+                   "tefmm_plan_get_alg2_table")
+            T = buf.view(np.complex128).reshape(n.value, n.value, ne.value)
+        return float(rng[0]), float(rng[1]), float(rng[2]), T
 
     def set_cross_images(self, fits):
         """``tefmm_plan_set_cross_images``: fits {(l, l', 'up'|'down', level, iz_s, k3'): (A, Z)}

@@ -1,0 +1,113 @@
+"""Algorithm 2 (Sec. 4.2) on the GPU against the oracle.
+
+* the device's Sommerfeld-integral tables (paper's contour Gamma_1 + Gamma_2,
+  its own Bessel functions) equal the oracle's quadrature (another contour,
+  scipy's Bessel functions) at sampled grid points, over the same grid ranges
+  (the ranges are computed from the trees, which are bit-exact);
+* the FP64 form with Algorithm 2 tables equals the oracle TE-FMM with its
+  own Algorithm 2 tables on the same grid (the near field on the oracle's
+  images, pushed into the plan);
+* the mixed form with tables against the oracle direct sum, beside Algorithm
+  1 (the table-versus-recurrence report);
+* a geometry whose pairs reach an image distance <= 0 is refused.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from _helpers import need_gpu, oracle_images, push_images, make_plan, gpu_eval, TAGS
+
+pytestmark = pytest.mark.gpu
+
+
+def _small():
+    from paper_1902_05875_gb300 import workloads as W
+    return W.middle_layer_uniform(600, 3, 20, seed=4, n_images=16)
+
+
+def test_tables_match_oracle_quadrature():
+    torch = need_gpu()
+    from oracle import alg2 as A2
+    from oracle.tefmm import TEFMM
+    w = _small()
+    med, img = oracle_images(w)
+    plan = make_plan(w, algorithm=2, table_n=12)
+    gpu_eval(plan, torch, w.src, w.q)
+    assert plan.stats()["n_alg2_tables"] == 4
+    f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images, algorithm=2, table_n=12).setup(w.src, w.src)
+    rho_max, rng = f.alg2_ranges(1)
+    rng_pts = [(0, 0), (0, 11), (3, 5), (7, 2), (11, 11), (11, 0)]
+    worst = 0.0
+    for tag in range(4):
+        r, lo, hi, T = plan.alg2_table(1, tag)
+        olo, ohi = rng[TAGS[tag]]
+        assert abs(r - rho_max) <= 1e-14 * rho_max and abs(lo - olo) <= 1e-14 and abs(hi - ohi) <= 1e-14
+        Tf = A2.medium_T(med, 1, TAGS[tag], 2 * w.p)
+        rho = A2.grid(0.0, r, 12)
+        zeta = A2.grid(lo, hi, 12)
+        for i, j in rng_pts:
+            ref = Tf([rho[i]], zeta[j])[0]
+            d = np.abs(T[i, j] - ref)
+            scale = np.abs(ref).max()
+            err = float(np.max(d / (np.abs(ref) + 1e-6 * scale)))
+            worst = max(worst, err)
+            assert err < 1e-8, (tag, i, j, err)
+    print(f"device vs oracle quadrature: worst entry error {worst:.2e}")
+
+
+def test_fp64_form_matches_oracle_alg2():
+    torch = need_gpu()
+    from oracle.tefmm import TEFMM
+    w = _small()
+    med, img = oracle_images(w)
+    plan = make_plan(w, algorithm=2, table_n=12)
+    push_images(plan, img)
+    phi = gpu_eval(plan, torch, w.src, w.q)
+    f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images, algorithm=2, table_n=12).setup(w.src, w.src)
+    ref = f.evaluate(w.q)
+    err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    # the two table sets differ by their quadratures (<= 1e-8 per entry, test above)
+    print(f"FP64 form, Algorithm 2 vs oracle Algorithm 2: {err:.2e}")
+    assert err <= 1e-9, err
+    # and Algorithm 1 on the same plan inputs differs only by the images' fit error
+    plan1 = make_plan(w)
+    push_images(plan1, img)
+    phi1 = gpu_eval(plan1, torch, w.src, w.q)
+    assert np.linalg.norm(phi1 - phi) / np.linalg.norm(phi1) < 1e-5
+
+
+def test_mixed_tables_versus_recurrence():
+    """Clustered points (8 Gaussian clusters) in the middle layer, p = 6, 64 x 64
+    tables: both algorithms in the mixed form against the oracle direct sum at
+    200 sampled targets."""
+    torch = need_gpu()
+    from paper_1902_05875_gb300 import tefmm
+    from paper_1902_05875_gb300 import workloads as W
+    from oracle.direct import direct_sum
+    w = W.clustered(20000, p=6, leaf_cap=32, seed=5, n_clusters=8, n_images=16)
+    med, img = oracle_images(w)
+    idx = np.random.default_rng(1).choice(len(w.src), 200, replace=False)
+    ref = direct_sum(med, img, w.src, w.q, w.src[idx])
+    err = {}
+    for alg in (1, 2):
+        plan = make_plan(w, algorithm=alg, precision=tefmm.MIXED)
+        push_images(plan, img)
+        phi = gpu_eval(plan, torch, w.src, w.q)[idx]
+        err[alg] = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+        if alg == 2:
+            st = plan.stats()
+            print(f"tables: {st['n_alg2_tables']}, built in {st['ms_alg2_build']:.0f} ms")
+    print(f"mixed form vs direct sum: recurrence {err[1]:.2e}, tables {err[2]:.2e}")
+    assert err[1] < 1e-5 and err[2] < 1e-5, err
+
+
+def test_nonpositive_image_distance_is_refused():
+    torch = need_gpu()
+    from paper_1902_05875_gb300 import tefmm
+    from paper_1902_05875_gb300 import workloads as W
+    w = W.three_layer_slabs(6000, 4, 32, seed=0)
+    plan = make_plan(w, algorithm=2, table_n=8)
+    with pytest.raises(tefmm.TefmmError) as e:
+        gpu_eval(plan, torch, w.src, w.q)
+    assert e.value.status == tefmm.ERR_NOT_IMPLEMENTED
