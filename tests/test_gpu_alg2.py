@@ -52,7 +52,7 @@ def test_tables_match_oracle_quadrature():
             scale = np.abs(ref).max()
             err = float(np.max(d / (np.abs(ref) + 1e-6 * scale)))
             worst = max(worst, err)
-            assert err < 1e-8, (tag, i, j, err)
+            assert err < 1e-9, (tag, i, j, err)     # measured 7.7e-12
     print(f"device vs oracle quadrature: worst entry error {worst:.2e}")
 
 
@@ -67,9 +67,9 @@ def test_fp64_form_matches_oracle_alg2():
     f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images, algorithm=2, table_n=12).setup(w.src, w.src)
     ref = f.evaluate(w.q)
     err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
-    # the two table sets differ by their quadratures (<= 1e-8 per entry, test above)
+    # the two table sets differ by their quadratures (<= 1e-9 per entry, test above)
     print(f"FP64 form, Algorithm 2 vs oracle Algorithm 2: {err:.2e}")
-    assert err <= 1e-9, err
+    assert err <= 1e-11, err     # measured 9.9e-15
     # and Algorithm 1 on the same plan inputs differs only by the images' fit error
     plan1 = make_plan(w)
     push_images(plan1, img)
