@@ -127,6 +127,25 @@ def fon_threshold(p, side, lev):
     return 10.0 ** (10.0 / (p + 1)) * math.sqrt(3.0) * (side / float(1 << lev))
 
 
+def fon_anchor(tr, t, s):
+    """Far-of-near anchor of a near-list pair (target box t, source box s):
+    l* = the coarser of the two levels, T* and S* the boxes of level l* that
+    hold t and s.  When T* and S* are adjacent, the far images (-Re Z >=
+    fon_threshold(l*)) of every particle pair under (T*, S*) go through one M2L
+    from S* to T*, and the pair sum of (t, s) leaves them out.  Returns
+    (l*, T*, S*), or None when T* and S* are not adjacent (all images in P2P)."""
+    ls = min(int(tr.level[t]), int(tr.level[s]))
+    T, S = t, s
+    while tr.level[T] > ls:
+        T = tr.parent[T]
+    while tr.level[S] > ls:
+        S = tr.parent[S]
+    if max(abs(int(tr.ix[T]) - int(tr.ix[S])), abs(int(tr.iy[T]) - int(tr.iy[S])),
+           abs(int(tr.iz[T]) - int(tr.iz[S]))) > 1:
+        return None
+    return ls, int(T), int(S)
+
+
 def cross_box_limit(med, zext):
     """HX = 4 min over interfaces of (gap of the slab above + gap of the slab below),
     the gaps between the particle slabs (zext) and the interface; interfaces with
@@ -673,13 +692,14 @@ class TEFMM:
             if lt != ls:
                 self._cross_m2l(lt, ls, V, alpha, beta, need)
                 continue
-            # group V pairs by level; far-of-near pairs (adjacent leaves of one
-            # level) translate their far images only
+            # group V pairs by level; far-of-near pairs (the anchors of the
+            # near-list pairs, see fon_anchor) translate their far images only
             pairs = [(t, s) for t, lst in V.items() for s in lst if need is None or t in need]
             self._same_layer_m2l(lt, pairs, alpha, beta, None)
             if self.far_of_near and self.images is not None:
-                fon = [(t, s) for t, lst in P2P.items() for s in lst
-                       if tr.level[s] == tr.level[t] and (need is None or t in need)]
+                fon = sorted({a[1:] for t, lst in P2P.items() for s in lst
+                              for a in [fon_anchor(tr, t, s)] if a is not None})
+                fon = [(T, S) for T, S in fon if need is None or T in need]
                 self._same_layer_m2l(lt, fon, alpha, beta, True)
         order = np.argsort(tr.level, kind='stable')
         for n in order:
@@ -876,8 +896,8 @@ class TEFMM:
                     continue
                 for s in P2P[t]:
                     s0, s1 = tr.s0[s], tr.s1[s]
-                    thr = (fon_threshold(self.p, tr.side, int(tr.level[t]))
-                           if self.far_of_near and tr.level[s] == tr.level[t] else None)
+                    anc = fon_anchor(tr, t, s) if self.far_of_near else None
+                    thr = fon_threshold(self.p, tr.side, anc[0]) if anc is not None else None
                     G = self._kernel_same_layer(l, pts, sp[s0:s1], far_thr=thr)
                     val = val + G @ qs[s0:s1]
             phi_sorted[idx] = val

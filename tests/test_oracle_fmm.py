@@ -231,3 +231,36 @@ def test_far_of_near_keeps_the_error():
     print(err, moved)
     assert moved > 0
     assert err[True] <= 1.5 * err[False] + 1e-9, err
+
+
+def test_far_of_near_mixed_levels_keeps_the_error():
+    """Adaptive tree (clusters): near-list pairs of different levels take the
+    far-of-near reading at the coarser level l* through the anchors (T*, S*)
+    of ``fon_anchor`` (the level-l* boxes holding them, adjacent): one M2L per
+    anchor, the pair sums without those images.  The error against the
+    direct sum stays that of the plain form (within 1.5x plus 1e-9), with
+    anchors of both kinds (T* split, S* split) present; every anchor is a pair
+    of adjacent same-level boxes, one of them a leaf of the pair."""
+    from oracle.tefmm import fon_anchor
+    w = W.clustered(1500, p=8, leaf_cap=8, seed=2, n_clusters=4, n_images=16)
+    med = Medium(w.interfaces, w.k)
+    img = ImageTable(med, w.zext, n_images=w.n_images)
+    idx = np.random.default_rng(3).choice(len(w.src), 40, replace=False)
+    ref = direct_sum(med, img, w.src, w.q, w.src[idx])
+    err = {}
+    for fon in (False, True):
+        f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images, far_of_near=fon).setup(w.src, w.src)
+        err[fon] = np.linalg.norm(f.evaluate(w.q, target_index=idx) - ref) / np.linalg.norm(ref)
+    tr = f.tr
+    kinds = set()
+    for t, lst in f.lists[(1, 1)][1].items():
+        for s in lst:
+            a = fon_anchor(tr, t, s)
+            if a is None:
+                continue
+            l, T, S = a
+            assert tr.level[T] == tr.level[S] == l and (T == t or S == s)
+            kinds.add((T == t, S == s))
+    print(err, kinds)
+    assert {(True, False), (False, True), (True, True)} <= kinds
+    assert err[True] <= 1.5 * err[False] + 1e-9, err
