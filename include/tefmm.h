@@ -103,17 +103,22 @@ typedef struct {
                               interpolation in each direction, assembled into Cartesian
                               derivatives through D+- = d_x +- i d_y.  The free-space part,
                               cross-layer components and the near field keep Algorithm 1;
-                              far_of_near is ignored.  A geometry whose same-layer pairs
-                              reach zeta <= 0 (box centres beyond the layer's interface,
-                              where the integral diverges) is TEFMM_ERR_NOT_IMPLEMENTED. */
+                              far_of_near is ignored.  The integral converges for zeta > 0
+                              only: a key whose image distance lies below the term's
+                              smallest one over the layer's particle slab (zext; the
+                              DCIM shift zeta_min), i.e. box centres of a coarse level
+                              beyond the slab, keeps the images for that term and stays
+                              out of the grid ranges.                                  */
     int split;             /* tensor-core split of the mixed form: TEFMM_SPLIT_TF32X3
                               (the only one built; others TEFMM_ERR_NOT_IMPLEMENTED)  */
-    int far_of_near;       /* 1 (default): for two adjacent leaves of one level, the DCIM
-                              images far from both (-Re Z_j >= 10^(10/(p+1)) sqrt(3) h)
-                              are translated by M2L (through the tensor cores in the
-                              mixed form) instead of summed pair by pair; the free-space
-                              term and the near images stay in P2P.  0: every image in
-                              P2P.                                                     */
+    int far_of_near;       /* 1 (default): for a near-field pair of boxes (target t,
+                              source s) let l* be the coarser of their levels and T*, S*
+                              the level-l* boxes holding them; when T* and S* are
+                              adjacent, the DCIM images far from both (-Re Z_j >=
+                              10^(10/(p+1)) sqrt(3) h_{l*}) are translated by one M2L
+                              from S* to T* (through the tensor cores in the mixed
+                              form) instead of summed pair by pair; the free-space term
+                              and the near images stay in P2P.  0: every image in P2P. */
     int scale_output;      /* 0 (default): potentials in the paper's normalisation
                               (Sec. 3.1: free term h0(k|r - r'|), factor i k_l/(4 pi)
                               omitted); 1: every potential multiplied by i k_l/(4 pi)
@@ -160,6 +165,8 @@ typedef struct {
     int64_t n_fon_pairs;   /* last eval: leaf pairs whose far images went through M2L */
     int n_alg2_tables;     /* TEFMM_ALG_TABLES: Sommerfeld-integral tables held        */
     double ms_alg2_build;  /* ... host time of the last (re)build of those tables      */
+    int n_alg2_image_keys; /* ... (key, term) derivatives of the last geometry taken from
+                              the images instead (image distance below the slab's)   */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,

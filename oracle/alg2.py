@@ -33,8 +33,10 @@ Grid ranges (the "domain of interest" of Sec. 4.2): for the terms of layer l,
 rho_max is the largest horizontal offset of the layer's same-layer M2L pairs
 (all levels) and [zeta_lo, zeta_hi] the range of the term's image distance
 over those pairs, computed from the box indices as the M2L tables do.  The
-integral converges only for zeta > 0: a layer whose pairs reach zeta <= 0 (box
-centres beyond the layer's interface) is refused.
+integral converges only for zeta > 0, and box centres of coarse levels can lie
+beyond the layer's particle slab: a key whose image distance is below the
+term's smallest one over the slab (zeta_min, the DCIM shift) keeps the images
+of Algorithm 1 and stays out of the ranges.
 """
 from __future__ import annotations
 
@@ -175,25 +177,30 @@ def assemble(P2, Tvals, phi):
     return out
 
 
-def layer_ranges(med: Medium, l, keys):
+def layer_ranges(med: Medium, l, keys, floor):
     """Grid ranges of the terms of layer l from its same-layer M2L keys.
 
     keys: iterable of (h, dix, diy, diz, zsum) per translation, zsum the sum of
-    the two box centres' z.  Returns (rho_max, {tag: (zeta_lo, zeta_hi)}).
-    ud/du terms use zeta = sz dz + c (dz = diz h), uu/dd zeta = sz zsum + c."""
+    the two box centres' z.  ud/du terms use zeta = sz dz + c (dz = diz h),
+    uu/dd zeta = sz zsum + c.  floor: {tag: the term's smallest image distance
+    over the layer's particle slab (its DCIM shift zeta_min)}; a key below it
+    (box centres beyond the slab, where the integral may diverge) is left to
+    the images and does not count.  Returns (rho_max, {tag: (zeta_lo,
+    zeta_hi)}) over the keys that use the tables."""
     rho_max = 0.0
     rng = {}
     for h, dix, diy, diz, zsum in keys:
-        rho_max = max(rho_max, math.hypot(dix * h, diy * h))
+        rho = math.hypot(dix * h, diy * h)
         for tag, sz, szp, c in med.same_layer_terms(l):
             zeta = sz * (diz * h) + c if tag in ('ud', 'du') else sz * zsum + c
+            if not zeta >= floor[tag]:
+                continue
+            rho_max = max(rho_max, rho)
             lo, hi = rng.get(tag, (math.inf, -math.inf))
             rng[tag] = (min(lo, zeta), max(hi, zeta))
     if rho_max == 0.0:
         rho_max = 1.0
     for tag, (lo, hi) in rng.items():
-        if not lo > 0.0:
-            raise NotImplementedError(f"Algorithm 2: layer {l} term {tag} reaches image distance {lo} <= 0")
         if hi == lo:
             rng[tag] = (lo, lo + 1.0)
     return rho_max, rng

@@ -628,7 +628,8 @@ class TEFMM:
                 h = tr.side / float(1 << lev)
                 keys.append((h, int(tr.ix[t] - tr.ix[s]), int(tr.iy[t] - tr.iy[s]), int(tr.iz[t] - tr.iz[s]),
                              2.0 * tr.lo[2] + (int(tr.iz[t] + tr.iz[s]) + 1) * h))
-        return a2.layer_ranges(self.med, l, keys) if keys else None
+        floor = {t['tag']: t['zeta_min'] for t in self.images.terms[l]}
+        return a2.layer_ranges(self.med, l, keys, floor) if keys else None
 
     def alg2_tables(self, l):
         """The Algorithm 2 tables of layer l, {tag: Alg2Table}, over the grid
@@ -647,11 +648,13 @@ class TEFMM:
     def _tables_alg2(self, l, h, keysB, keysA, odd3):
         """_tables with the reaction part from the Algorithm 2 tables: the
         same combinations (B = free + ud + (-1)^{g3} du, A = uu + (-1)^{g3} dd)
-        with each term's D^g F / g! interpolated at its image distance."""
+        with each term's D^g F / g! interpolated at its image distance; a key
+        below the term's zeta_min (box centres beyond the particle slab) keeps
+        the term's images."""
         P2 = 2 * self.p
         k = self.med.k[l]
         tabs = self.alg2_tables(l)
-        terms = {tag: (sz, c) for tag, sz, szp, c in self.med.same_layer_terms(l)}
+        terms = {t['tag']: t for t in self.images.terms[l]}
         n = len(multi_indices(P2))
         TB = np.zeros((len(keysB), n), dtype=complex)
         TA = np.zeros((len(keysA), n), dtype=complex)
@@ -668,10 +671,16 @@ class TEFMM:
             for tag in tags:
                 if tag not in terms:
                     continue
-                sz, c = terms[tag]
+                t = terms[tag]
                 sgn = odd3 if tag in ('du', 'dd') else 1.0
                 for i in range(len(keys)):
-                    T[i] += tabs[tag].derivatives(float(X0[i]), float(Y0[i]), sz * zarg[i] + c) * sgn
+                    zeta = t['sz'] * zarg[i] + t['c']
+                    if zeta >= t['zeta_min']:
+                        T[i] += tabs[tag].derivatives(float(X0[i]), float(Y0[i]), zeta) * sgn
+                    else:
+                        for A, Z in zip(t['A'], t['Z']):
+                            T[i] += A * taylor_h0(X0[i:i + 1], Y0[i:i + 1], np.array([zeta - t['zeta_min'] - Z]),
+                                                  k, P2)[0] * sgn
         return TB, TA
 
     # -- downward pass -------------------------------------------------------

@@ -374,12 +374,13 @@ int alg2_prepare(tefmm_plan_s *P, cudaStream_t st) {
     const int L = P->nL;
     std::vector<double> rmax(L, 0.0), lo(4 * L, INFINITY), hi(4 * L, -INFINITY);
     std::vector<char> has(4 * L, 0);
+    int n_images = 0;
     for (uint64_t key : keys) {
         const int kind = key_kind(key);
         if (kind > 1) continue;            // far-of-near keys do not occur with tables
         const int l = key_layer(key), lev = key_level(key);
         const double h = P->side / (double)(1 << lev);
-        rmax[l] = fmax(rmax[l], hypot((double)key_dx(key) * h, (double)key_dy(key) * h));
+        const double rho = hypot((double)key_dx(key) * h, (double)key_dy(key) * h);
         const int w = (int)key_w(key);
         for (int ti = P->layer_term_first[l]; ti < P->layer_term_first[l] + P->layer_term_count[l]; ++ti) {
             const TermDesc &td = P->terms[ti];
@@ -387,23 +388,26 @@ int alg2_prepare(tefmm_plan_s *P, cudaStream_t st) {
             if (kind == 0 && td.tag >= 2) zeta = td.sz * ((double)(w - KEY_OFF) * h) + td.c;
             else if (kind == 1 && td.tag <= 1) zeta = td.sz * (2.0 * P->lo[2] + (double)(w + 1) * h) + td.c;
             else continue;
+            // below the term's smallest image distance over the particle slab
+            // (its DCIM shift: box centres beyond the slab) the key keeps the images
+            if (!(zeta >= td.zmin)) {
+                ++n_images;
+                continue;
+            }
             const int s = 4 * l + td.tag;
             has[s] = 1;
             lo[s] = fmin(lo[s], zeta);
             hi[s] = fmax(hi[s], zeta);
+            rmax[l] = fmax(rmax[l], rho);
         }
     }
+    P->n_alg2_image_keys = n_images;
     const int P2 = 2 * P->p, n = P->opt.table_n > 0 ? P->opt.table_n : 64;
     std::vector<Alg2Table> want;
     for (int l = 0; l < L; ++l)
         for (int tag = 0; tag < 4; ++tag) {
             const int s = 4 * l + tag;
             if (!has[s]) continue;
-            if (!(lo[s] > 0.0)) {
-                fprintf(stderr, "tefmm: Algorithm 2 needs image distances > 0; layer %d term %d reaches %g\n", l,
-                        tag, lo[s]);
-                return TEFMM_ERR_NOT_IMPLEMENTED;
-            }
             Alg2Table t;
             t.layer = l;
             t.tag = tag;

@@ -279,6 +279,7 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
     o->n_fon_pairs = P->n_fon;
     o->n_alg2_tables = (int)P->a2.size();
     o->ms_alg2_build = P->ms_alg2_build;
+    o->n_alg2_image_keys = P->n_alg2_image_keys;
     o->leaf_cap_used = P->leaf_cap_eff;
     o->ms_autotune = P->ms_autotune;
     o->n_tables_built = P->n_tables_built;

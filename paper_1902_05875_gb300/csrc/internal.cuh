@@ -178,7 +178,11 @@ struct tefmm_plan_s {
     DBuf v_ptr, v_src, near_ptr, near_src, near_tmp, near_cnt;
     int64_t n_v = 0, n_near = 0, n_p2p_pairs = 0;
     int64_t n_fon = 0;            // far-of-near pairs (same-level adjacent leaves), after the V pairs
-    DBuf fon_cnt, fon_ptr;
+    DBuf fon_cnt, fon_ptr, fon_key, fon_key_sorted;
+    DBuf near_fl;   // per near-list entry: far-of-near level l* of its anchor, or -1
+    // near-field work items (one CTA each): target leaf, chunk index, chunks of that leaf
+    DBuf nitem_cnt, nitem_pos, nitem_node, nitem_part, nitem_np;
+    int n_near_items = 0;
     int cap_D = 64, cap_X = 0;
 
     // expansions
@@ -198,6 +202,7 @@ struct tefmm_plan_s {
     // [n][n][entries] complex, over the ranges of the last geometry's keys
     std::vector<Alg2Table> a2;
     double ms_alg2_build = 0.0;
+    int n_alg2_image_keys = 0;   // (key, term) lookups of the last geometry left to the images
 
     // cross-layer components: fitted images (cached per root-cube geometry),
     // per-table image ranges and tables
@@ -291,6 +296,7 @@ int m2l_apply_tc_cross(tefmm_plan_s *P, cudaStream_t st, const cplx *alpha_x, cp
                        const unsigned short *xgs, const float *xcf);
 size_t m2l_tc_smem(int np, int MT, int tab_entries);
 void m2l_tc_geometry(int np, int MT, int *Kpad, int *Ncta, int *nsplit);
+#define NEAR_CHUNK 4096   // near sources per near-field work item
 #define TC_MT 1         // tiles of 128 pairs per pass, same-layer keys (two CTAs per SM)
 #define TC_MT_CROSS 1   // cross-layer keys
 int downward_pass(tefmm_plan_s *P, cudaStream_t st);

@@ -48,9 +48,13 @@ __device__ __forceinline__ f2 csqrt32(float x, float y) {
     return f2{0.5f * fabsf(y) * __frcp_rn(t), copysignf(t, y)};
 }
 
-__global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
-    int node = blockIdx.x;
-    if (node >= nn) return;
+__global__ void __launch_bounds__(128) k_near_fp32(int n_items, NearArgs a) {
+    // one work item: near sources [src_lo, src_hi) of the leaf's list; chunk 0
+    // also adds the constant part and the L2P
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
+    const int node = a.item_node[it], part = a.item_part[it], nparts = a.item_np[it];
+    const int64_t src_lo = (int64_t)part * NEAR_CHUNK, src_hi = src_lo + NEAR_CHUNK;
     const TreeArrays &T = a.T;
     if (T.split[node]) return;
     int t0 = T.t0[node], t1 = T.t1[node];
@@ -64,9 +68,14 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
     // per image: (w0, R0^2) and (1/R0, E0), FP32, two 16-byte loads per pair
     __shared__ float4 sWR[MI], sIE[MI];
     __shared__ float tsz[TEFMM_MAX_TERMS], tszp[TEFMM_MAX_TERMS];
-    __shared__ int tcnt[TEFMM_MAX_TERMS], tncnt[TEFMM_MAX_TERMS];   // images / near images per term
-    __shared__ int slot[MI];       // image j of term ti at slot[ti * MAX_IMG + j]: near images first
-    __shared__ double2 cq[2];      // [0]: the images' constant part times the charges it applies to
+    __shared__ int tcnt[TEFMM_MAX_TERMS];   // images per term
+    // images of term ti with -Re Z < thr[lv] (the ones a pair sum with
+    // far-of-near level lv evaluates), lv <= the leaf's level
+    __shared__ int ncnt[TEFMM_MAX_TERMS][TEFMM_NBITS + 1];
+    __shared__ int slot[MI];       // image j of term ti at slot[ti * MAX_IMG + j]: by -Re Z ascending
+    // near-field charge totals: [lv] entries with far-of-near level lv, [NBITS + 1] entries without
+    __shared__ double2 qlev[TEFMM_NBITS + 2];
+    __shared__ double2 cq[1];      // the images' constant part times the charges it applies to
     int lay = T.layer[node];
     cplx k = a.im.k[lay];
     cplx ik = mkc(-k.y, k.x);
@@ -76,25 +85,53 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
     double cx = centre(a.cb.lo[0], T.ix[node], h), cy = centre(a.cb.lo[1], T.iy[node], h),
            cz = centre(a.cb.lo[2], T.iz[node], h);
     int tf = a.im.lt_first[lay], ntm = a.im.lt_count[lay];
-    // far-of-near: for a same-level near leaf the images with -Re Z >= thr went through M2L
-    const double thr = a.fon.on ? a.fon.thr[T.level[node]] : INFINITY;
-    if (threadIdx.x < 4) red[threadIdx.x] = make_double2(0.0, 0.0);
+    for (int i = threadIdx.x; i < TEFMM_NBITS + 2; i += blockDim.x) qlev[i] = make_double2(0.0, 0.0);
+    if (threadIdx.x == 0) cq[0] = make_double2(0.0, 0.0);
     if (threadIdx.x < ntm) {
         DevTerm t = a.im.terms[tf + threadIdx.x];
         tsz[threadIdx.x] = (float)t.sz;
         tszp[threadIdx.x] = (float)t.szp;
         tcnt[threadIdx.x] = t.count;
-        int nn_ = 0;                     // near images take the first slots, far ones the rest
-        for (int j = 0; j < t.count; ++j)
-            if (!(-a.im.Z[t.first + j].x >= thr)) slot[threadIdx.x * TEFMM_MAX_IMG + j] = nn_++;
-        tncnt[threadIdx.x] = nn_;
-        int nf_ = nn_;
-        for (int j = 0; j < t.count; ++j)
-            if (-a.im.Z[t.first + j].x >= thr) slot[threadIdx.x * TEFMM_MAX_IMG + j] = nf_++;
+        // rank by depth -Re Z (ties by index; a NaN depth counts as near)
+        for (int j = 0; j < t.count; ++j) {
+            const double dj = -a.im.Z[t.first + j].x;
+            const double kj = dj == dj ? dj : -INFINITY;
+            int r = 0;
+            for (int i = 0; i < t.count; ++i) {
+                const double di = -a.im.Z[t.first + i].x;
+                const double ki_ = di == di ? di : -INFINITY;
+                r += (ki_ < kj) || (ki_ == kj && i < j);
+            }
+            slot[threadIdx.x * TEFMM_MAX_IMG + j] = r;
+        }
+        for (int lv = 0; lv <= l; ++lv) {
+            const double thr = a.fon.on ? a.fon.thr[lv] : INFINITY;
+            int c = 0;
+            for (int j = 0; j < t.count; ++j) c += !(-a.im.Z[t.first + j].x >= thr);
+            ncnt[threadIdx.x][lv] = c;
+        }
     }
     __syncthreads();
-    // per-image reference at the leaf centre (FP64); constant parts: red[0] near
-    // images, red[2] far images
+    // near-field charge totals (FP64) by far-of-near level (chunk 0 only)
+    for (int nb = a.near_ptr[node]; part == 0 && nb < a.near_ptr[node + 1]; ++nb) {
+        const int sb = a.near_src[nb];
+        const int fl = a.fon.on ? a.near_fl[nb] : -1;
+        double qr = 0.0, qi = 0.0;
+        bool any = false;
+        for (int j = T.s0[sb] + threadIdx.x; j < T.s1[sb]; j += blockDim.x) {
+            qr += a.sq[2 * j];
+            qi += a.sq[2 * j + 1];
+            any = true;
+        }
+        if (any) {
+            double2 *dst = &qlev[fl >= 0 ? fl : TEFMM_NBITS + 1];
+            atomicAdd(&dst->x, qr);
+            atomicAdd(&dst->y, qi);
+        }
+    }
+    __syncthreads();
+    // per-image reference at the leaf centre (FP64); the constant part E0 times
+    // the charge of the entries that evaluate the image
     for (int ti = 0; ti < ntm; ++ti) {
         DevTerm t = a.im.terms[tf + ti];
         for (int j = threadIdx.x; j < t.count; j += blockDim.x) {
@@ -104,43 +141,19 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
             cplx E0 = cmul(cmul(a.im.A[t.first + j], inv_ik), cdiv(e, w0));
             cplx r0sq = cmul(w0, w0);
             cplx ir0 = cdiv(mkc(1, 0), w0);
-            int s = ti * TEFMM_MAX_IMG + slot[ti * TEFMM_MAX_IMG + j];
+            const int r = slot[ti * TEFMM_MAX_IMG + j];
+            int s = ti * TEFMM_MAX_IMG + r;
             sWR[s] = make_float4((float)w0.x, (float)w0.y, (float)r0sq.x, (float)r0sq.y);
             sIE[s] = make_float4((float)ir0.x, (float)ir0.y, (float)E0.x, (float)E0.y);
-            const int rc = (-Z.x >= thr) ? 2 : 0;
-            atomicAdd(&red[rc].x, E0.x);
-            atomicAdd(&red[rc].y, E0.y);
+            cplx qw = mkc(qlev[TEFMM_NBITS + 1].x, qlev[TEFMM_NBITS + 1].y);
+            for (int lv = 0; lv <= l; ++lv)
+                if (r < ncnt[ti][lv]) qw = cadd(qw, mkc(qlev[lv].x, qlev[lv].y));
+            const cplx c = cmul(E0, qw);
+            atomicAdd(&cq[0].x, c.x);
+            atomicAdd(&cq[0].y, c.y);
         }
-    }
-    // near-field charge totals (FP64): red[1] all near boxes, red[3] same-level leaves
-    {
-        double qr = 0.0, qi = 0.0, sr = 0.0, si = 0.0;
-        for (int nb = a.near_ptr[node]; nb < a.near_ptr[node + 1]; ++nb) {
-            const int sb = a.near_src[nb];
-            const bool same = T.level[sb] == T.level[node];
-            for (int j = T.s0[sb] + threadIdx.x; j < T.s1[sb]; j += blockDim.x) {
-                qr += a.sq[2 * j];
-                qi += a.sq[2 * j + 1];
-                if (same) {
-                    sr += a.sq[2 * j];
-                    si += a.sq[2 * j + 1];
-                }
-            }
-        }
-        atomicAdd(&red[1].x, qr);
-        atomicAdd(&red[1].y, qi);
-        atomicAdd(&red[3].x, sr);
-        atomicAdd(&red[3].y, si);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // near images apply to every near box; far images only to the boxes of other levels
-        const cplx cn = mkc(red[0].x, red[0].y), cf = mkc(red[2].x, red[2].y);
-        const cplx qt = mkc(red[1].x, red[1].y);
-        const cplx qo = a.fon.on ? csub(qt, mkc(red[3].x, red[3].y)) : qt;
-        const cplx cq0 = cadd(cmul(cn, qt), cmul(cf, qo));
-        cq[0] = make_double2(cq0.x, cq0.y);
-    }
 
     const float kr = (float)k.x, ki = (float)k.y;
     const f2 iik = f2{(float)inv_ik.x, (float)inv_ik.y};
@@ -164,10 +177,19 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
         const float xf = (float)(xt - cx), yf = (float)(yt - cy), zf = (float)(zt - cz);
         double accr = 0.0, acci = 0.0;
         __syncthreads();
-        for (int nb = nb0; nb < nb1; ++nb) {
+        int64_t off = 0;           // near sources of the list before entry nb
+        for (int nb = nb0; nb < nb1 && off < src_hi; ++nb) {
             int s = a.near_src[nb];
             int s0 = T.s0[s], s1 = T.s1[s];
-            const bool fon_pair = a.fon.on && T.level[s] == l;   // far images already in M2L
+            const int64_t ns_e = s1 - s0;
+            // this item's part of the entry
+            const int b0 = (int)(s0 + max((int64_t)0, src_lo - off));
+            const int b1 = (int)(s0 + min(ns_e, src_hi - off));
+            off += ns_e;
+            if (b0 >= b1) continue;
+            s0 = b0;
+            s1 = b1;
+            const int fl = a.fon.on ? a.near_fl[nb] : -1;   // far images of the anchor already in M2L
             for (int base = s0; base < s1; base += TILE) {
                 int cnt = min(TILE, s1 - base);
                 __syncthreads();
@@ -198,7 +220,7 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                     float hr = 0.f, hi = 0.f;
                     for (int tm = 0; tm < ntm; ++tm) {
                         const float dw = tsz[tm] * zf + tszp[tm] * zs[j];   // w - w0 (real)
-                        const int lim = fon_pair ? tncnt[tm] : tcnt[tm];
+                        const int lim = fl >= 0 ? ncnt[tm][fl] : tcnt[tm];
                         for (int m = 0; m < lim; ++m) {
                             const int sidx = tm * TEFMM_MAX_IMG + m;
                             const float4 wr = sWR[sidx];
@@ -246,24 +268,26 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                 accr += red[sl * ntp + my_t].x;
                 acci += red[sl * ntp + my_t].y;
             }
-            accr += cq[0].x;       // the images' constant part times the charge total
-            acci += cq[0].y;
-            // L2P in FP64
-            double d[3] = {xt - cx, yt - cy, zt - cz};
-            double pw[3][13];
-            for (int e = 0; e < 3; ++e) {
-                double v = 1.0;
-                for (int qq = 0; qq <= a.p; ++qq) {
-                    pw[e][qq] = v;
-                    v *= d[e];
+            if (part == 0) {
+                accr += cq[0].x;       // the images' constant part times the charge total
+                acci += cq[0].y;
+                // L2P in FP64
+                double d[3] = {xt - cx, yt - cy, zt - cz};
+                double pw[3][13];
+                for (int e = 0; e < 3; ++e) {
+                    double v = 1.0;
+                    for (int qq = 0; qq <= a.p; ++qq) {
+                        pw[e][qq] = v;
+                        v *= d[e];
+                    }
                 }
-            }
-            const cplx *bt = a.beta + (int64_t)node * a.np;
-            for (int kk = 0; kk < a.np; ++kk) {
-                double m = pw[0][a.mi[3 * kk]] * pw[1][a.mi[3 * kk + 1]] * pw[2][a.mi[3 * kk + 2]];
-                cplx b = bt[kk];
-                accr += b.x * m;
-                acci += b.y * m;
+                const cplx *bt = a.beta + (int64_t)node * a.np;
+                for (int kk = 0; kk < a.np; ++kk) {
+                    double m = pw[0][a.mi[3 * kk]] * pw[1][a.mi[3 * kk + 1]] * pw[2][a.mi[3 * kk + 2]];
+                    cplx b = bt[kk];
+                    accr += b.x * m;
+                    acci += b.y * m;
+                }
             }
             if (a.scale) {                // i k / (4 pi)
                 const double sr = -k.y / (4.0 * M_PI), si = k.x / (4.0 * M_PI);
@@ -272,8 +296,13 @@ __global__ void __launch_bounds__(128) k_near_fp32(int nn, NearArgs a) {
                 acci = vi;
             }
             int out = a.perm_t[t0 + ti];
-            a.phi[2 * out] = accr;
-            a.phi[2 * out + 1] = acci;
+            if (nparts == 1) {
+                a.phi[2 * out] = accr;
+                a.phi[2 * out + 1] = acci;
+            } else {                  // chunks of one leaf add into zeroed outputs
+                atomicAdd(&a.phi[2 * out], accr);
+                atomicAdd(&a.phi[2 * out + 1], acci);
+            }
         }
     }
 }
@@ -300,10 +329,17 @@ int near_field_fp32(tefmm_plan_s *P, double *phi, cudaStream_t st) {
     a.beta = dp<cplx>(P->beta);
     a.im = img_view(P);
     a.fon = fon_thresholds(P);
+    a.near_fl = dp<int>(P->near_fl);
+    a.item_node = dp<int>(P->nitem_node);
+    a.item_part = dp<int>(P->nitem_part);
+    a.item_np = dp<int>(P->nitem_np);
     a.scale = P->opt.scale_output;
     a.phi = phi;
-    k_near_fp32<<<P->n_nodes, 128, 0, st>>>(P->n_nodes, a);
-    P->launches++;
+    if (P->n_near_items > 0) {
+        TRY(near_zero_split(P, a, st));
+        k_near_fp32<<<P->n_near_items, 128, 0, st>>>(P->n_near_items, a);
+        P->launches++;
+    }
     CUDA_TRY(cudaGetLastError());
     return TEFMM_OK;
 }

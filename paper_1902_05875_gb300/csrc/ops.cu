@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__r
             DevTerm t = im.terms[ti];
             if (t.tag != 2 && t.tag != 3) continue;
             double W0 = __dadd_rn(__dmul_rn(t.sz, dz), t.c);
-            if (a2_on) continue;   // Algorithm 2: added by k_tables_a2
+            if (a2_on && W0 >= t.zmin) continue;   // Algorithm 2: added by k_tables_a2
             for (int j = t.first; j < t.first + t.count; ++j) {
                 cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
                 recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 3, a, b, acc);
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(256, 4) k_tables(int ntab, const uint64_t *__r
             DevTerm t = im.terms[ti];
             if (t.tag != 0 && t.tag != 1) continue;
             double W0 = __dadd_rn(__dmul_rn(t.sz, zsum), t.c);
-            if (a2_on) continue;
+            if (a2_on && W0 >= t.zmin) continue;
             for (int j = t.first; j < t.first + t.count; ++j) {
                 cplx Wj = mkc(W0 - t.zmin - im.Z[j].x, -im.Z[j].y);
                 recur_accumulate(P2, cmax, k, X, Y, Wj, im.A[j], t.tag == 1, a, b, acc);
@@ -526,6 +526,7 @@ __global__ void __launch_bounds__(256) k_tables_a2(int ntab, const uint64_t *__r
         const DevTerm t = im.terms[ti];
         if (kind == 0 ? t.tag < 2 : t.tag > 1) continue;
         const double W0 = __dadd_rn(__dmul_rn(t.sz, zarg), t.c);
+        if (!(W0 >= t.zmin)) continue;      // below the slab's image distances: the images (k_tables)
         alg2_accumulate(a2, a2.t[lay][t.tag], X, Y, W0, t.tag == 1 || t.tag == 3, (cplx *)sm, np2,
                         tables + (int64_t)tb * np2);
     }
@@ -592,9 +593,12 @@ __device__ __forceinline__ cplx eikr_over_r(cplx ik, cplx R) {
     return cdiv(e, R);
 }
 
-__global__ void k_near_fp64(int nn, NearArgs a) {
-    int node = blockIdx.x;
-    if (node >= nn) return;
+__global__ void k_near_fp64(int n_items, NearArgs a) {
+    // one work item: near sources [src_lo, src_hi) of the leaf's list; chunk 0 also adds the L2P
+    const int it = blockIdx.x;
+    if (it >= n_items) return;
+    const int node = a.item_node[it], part = a.item_part[it], nparts = a.item_np[it];
+    const int64_t src_lo = (int64_t)part * NEAR_CHUNK, src_hi = src_lo + NEAR_CHUNK;
     const TreeArrays &T = a.T;
     if (T.split[node]) return;
     int t0 = T.t0[node], t1 = T.t1[node];
@@ -649,11 +653,20 @@ __global__ void k_near_fp64(int nn, NearArgs a) {
         cplx accf = mkc(0, 0);     // sum q e^{ikr}/r (free)
         cplx acci = mkc(0, 0);     // sum q A/(ik) e^{ikR}/R (images)
         __syncthreads();
-        for (int nb = nb0; nb < nb1; ++nb) {
+        int64_t off = 0;           // near sources of the list before entry nb
+        for (int nb = nb0; nb < nb1 && off < src_hi; ++nb) {
             int s = a.near_src[nb];
             int s0 = T.s0[s], s1 = T.s1[s];
-            // a same-level adjacent leaf: its far images went through M2L
-            const double thr = (a.fon.on && T.level[s] == l) ? a.fon.thr[l] : INFINITY;
+            const int64_t ns_e = s1 - s0;
+            const int b0 = (int)(s0 + max((int64_t)0, src_lo - off));
+            const int b1 = (int)(s0 + min(ns_e, src_hi - off));
+            off += ns_e;
+            if (b0 >= b1) continue;
+            s0 = b0;
+            s1 = b1;
+            // an entry with a far-of-near anchor: its far images went through M2L
+            const int fl = a.fon.on ? a.near_fl[nb] : -1;
+            const double thr = fl >= 0 ? a.fon.thr[fl] : INFINITY;
             for (int base = s0; base < s1; base += TILE) {
                 int cnt = min(TILE, s1 - base);
                 __syncthreads();
@@ -708,7 +721,7 @@ __global__ void k_near_fp64(int nn, NearArgs a) {
             }
             const cplx *bt = a.beta + (int64_t)node * a.np;
             cplx loc = mkc(0, 0);
-            for (int kk = 0; kk < a.np; ++kk) {
+            for (int kk = 0; part == 0 && kk < a.np; ++kk) {
                 double m = pw[0][a.mi[3 * kk]] * pw[1][a.mi[3 * kk + 1]] * pw[2][a.mi[3 * kk + 2]];
                 cplx b = bt[kk];
                 loc.x += b.x * m;
@@ -717,9 +730,26 @@ __global__ void k_near_fp64(int nn, NearArgs a) {
             tot = cadd(tot, loc);
             if (a.scale) tot = cmul(tot, mkc(-k.y / (4.0 * M_PI), k.x / (4.0 * M_PI)));   // i k / (4 pi)
             int out = a.perm_t[t0 + ti];
-            a.phi[2 * out] = tot.x;
-            a.phi[2 * out + 1] = tot.y;
+            if (nparts == 1) {
+                a.phi[2 * out] = tot.x;
+                a.phi[2 * out + 1] = tot.y;
+            } else {                  // chunks of one leaf add into zeroed outputs
+                atomicAdd(&a.phi[2 * out], tot.x);
+                atomicAdd(&a.phi[2 * out + 1], tot.y);
+            }
         }
+    }
+}
+
+// zero the outputs of the leaves whose near field is split over several work items
+__global__ void k_near_zero(int n_items, NearArgs a) {
+    const int it = blockIdx.x;
+    if (it >= n_items || a.item_part[it] != 0 || a.item_np[it] < 2) return;
+    const int node = a.item_node[it];
+    for (int t = a.T.t0[node] + threadIdx.x; t < a.T.t1[node]; t += blockDim.x) {
+        const int out = a.perm_t[t];
+        a.phi[2 * out] = 0.0;
+        a.phi[2 * out + 1] = 0.0;
     }
 }
 
@@ -734,6 +764,14 @@ int scan_i(tefmm_plan_s *P, const int *in, int *out, int64_t n, bool inclusive, 
 }
 
 }  // namespace
+
+int near_zero_split(tefmm_plan_s *P, const NearArgs &a, cudaStream_t st) {
+    k_near_zero<<<P->n_near_items, 64, 0, st>>>(P->n_near_items, a);
+    P->launches++;
+    CUDA_TRY(cudaGetLastError());
+    return TEFMM_OK;
+}
+
 
 // ---------------------------------------------------------------- host side
 int upward_pass(tefmm_plan_s *P, cudaStream_t st) {
@@ -955,10 +993,17 @@ int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st) {
     a.beta = dp<cplx>(P->beta);
     a.im = img_view(P);
     a.fon = fon_thresholds(P);
+    a.near_fl = dp<int>(P->near_fl);
+    a.item_node = dp<int>(P->nitem_node);
+    a.item_part = dp<int>(P->nitem_part);
+    a.item_np = dp<int>(P->nitem_np);
     a.scale = P->opt.scale_output;
     a.phi = phi;
-    k_near_fp64<<<P->n_nodes, 128, 0, st>>>(P->n_nodes, a);
-    P->launches++;
+    if (P->n_near_items > 0) {
+        TRY(near_zero_split(P, a, st));
+        k_near_fp64<<<P->n_near_items, 128, 0, st>>>(P->n_near_items, a);
+        P->launches++;
+    }
     CUDA_TRY(cudaGetLastError());
     return TEFMM_OK;
 }

@@ -75,6 +75,8 @@ struct NearArgs {
     int p, np;
     const int *mi;
     const int *near_ptr, *near_src;
+    const int *near_fl;        // far-of-near level l* per near entry (-1: none); read when fon.on
+    const int *item_node, *item_part, *item_np;   // near-field work items (leaf, chunk, chunks of the leaf)
     const double *sx, *sy, *sz, *sq, *tx, *ty, *tz;
     const int *perm_t;
     const cplx *beta;
@@ -83,6 +85,8 @@ struct NearArgs {
     int scale;                 // multiply each potential by i k_l / (4 pi) of its layer
     double *phi;
 };
+
+int near_zero_split(tefmm_plan_s *P, const NearArgs &a, cudaStream_t st);
 
 inline ImgView img_view(tefmm_plan_s *P) {
     ImgView im;

@@ -270,7 +270,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
                    &P->keyslot_flag, &P->keyslot_table, &P->pair_t, &P->pair_s, &P->pair_slot,
                    &P->pair_slot_sorted, &P->pair_idx, &P->pair_idx_sorted, &P->chunk_key,
                    &P->chunk_start, &P->chunk_cnt, &P->tables, &P->table_slot, &P->seg_tmp, &P->table_rep,
-                   &P->h_in, &P->h_out, &P->tc_ah, &P->tc_al, &P->tc_bt, &P->tc_cfA, &P->tc_cfB, &P->tc_W};
+                   &P->h_in, &P->h_out, &P->fon_cnt, &P->fon_ptr, &P->fon_key, &P->fon_key_sorted, &P->near_fl, &P->nitem_cnt, &P->nitem_pos, &P->nitem_node, &P->nitem_part, &P->nitem_np, &P->tc_ah, &P->tc_al, &P->tc_bt, &P->tc_cfA, &P->tc_cfB, &P->tc_W};
     for (DBuf *b : all) dbuf_free(*b);
     cross_release(P);
     alg2_release(P);

@@ -555,28 +555,78 @@ __global__ void k_count_pairs(int n_nodes, const int *__restrict__ near_ptr,
     }
 }
 
-// far-of-near pairs: the near-list entries of a target leaf that are leaves of
-// its own level (adjacent by construction)
-__global__ void k_fon_count(int n_nodes, const int *__restrict__ level, const int *__restrict__ ptr,
-                            const int *__restrict__ src, int *__restrict__ cnt) {
+// Far-of-near anchors.  For the near-list entry (target box t, source box s)
+// let l* be the coarser of their levels and T*, S* the boxes of level l* that
+// hold them.  When T* and S* are adjacent, the far images (-Re Z >= thr[l*])
+// of every particle pair under (T*, S*) go through one M2L from S* to T* (all
+// those pairs are near-list pairs with the same anchor: one of T*, S* is t or
+// s itself, a leaf, so no V pair covers them), and the entry's pair sum leaves
+// them out.  Per entry: fl = l* (or -1: not adjacent, all images in P2P) and
+// the anchor key (T* << 32 | S*, or ~0 for none).
+__global__ void k_fon_anchor(int n_nodes, const int *__restrict__ level, const int *__restrict__ parent,
+                             const int *__restrict__ ix, const int *__restrict__ iy, const int *__restrict__ iz,
+                             const int *__restrict__ ptr, const int *__restrict__ src,
+                             int *__restrict__ fl, unsigned long long *__restrict__ akey) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_nodes) return;
-    int c = 0;
-    for (int a = ptr[t]; a < ptr[t + 1]; ++a) c += level[src[a]] == level[t];
-    cnt[t] = c;
+    for (int a = ptr[t]; a < ptr[t + 1]; ++a) {
+        const int s = src[a];
+        const int ls = min(level[t], level[s]);
+        int T = t, S = s;
+        for (int guard = 0; level[T] > ls && guard < 32; ++guard) T = parent[T];
+        for (int guard = 0; level[S] > ls && guard < 32; ++guard) S = parent[S];
+        const bool adj = level[T] == ls && level[S] == ls && abs(ix[T] - ix[S]) <= 1 &&
+                         abs(iy[T] - iy[S]) <= 1 && abs(iz[T] - iz[S]) <= 1;
+        fl[a] = adj ? ls : -1;
+        akey[a] = adj ? (((unsigned long long)(unsigned)T << 32) | (unsigned)S) : ~0ULL;
+    }
 }
-__global__ void k_fon_fill(int n_nodes, const int *__restrict__ level, const int *__restrict__ ptr,
-                           const int *__restrict__ src, const int *__restrict__ fptr, int64_t base,
-                           int *__restrict__ pair_t, int *__restrict__ pair_s) {
+
+// unique anchors of the sorted keys -> (pair_t, pair_s) after the V pairs
+__global__ void k_fon_heads(int64_t n, const unsigned long long *__restrict__ k, int *__restrict__ head) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    head[i] = k[i] != ~0ULL && (i == 0 || k[i] != k[i - 1]);
+}
+__global__ void k_fon_fill(int64_t n, const unsigned long long *__restrict__ k, const int *__restrict__ head,
+                           const int *__restrict__ pos, int64_t base, int *__restrict__ pair_t,
+                           int *__restrict__ pair_s) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n || !head[i]) return;
+    const int64_t o = base + pos[i];
+    pair_t[o] = (int)(k[i] >> 32);
+    pair_s[o] = (int)(k[i] & 0xffffffffULL);
+}
+
+// Near-field work items: the near sources of a target leaf, taken in list
+// order, are cut into chunks of NEAR_CHUNK; each chunk is one CTA of the
+// near-field kernels, so that a leaf beside a dense region (W-type entries of
+// 10^5 sources) is spread over many CTAs instead of one.
+__global__ void k_near_items_count(int n_nodes, const int *__restrict__ split, const int *__restrict__ t0,
+                                   const int *__restrict__ t1, const int *__restrict__ s0,
+                                   const int *__restrict__ s1, const int *__restrict__ ptr,
+                                   const int *__restrict__ src, int *__restrict__ cnt) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_nodes) return;
-    int64_t o = base + fptr[t];
-    for (int a = ptr[t]; a < ptr[t + 1]; ++a)
-        if (level[src[a]] == level[t]) {
-            pair_t[o] = t;
-            pair_s[o] = src[a];
-            ++o;
-        }
+    int parts = 0;
+    if (!split[t] && t1[t] > t0[t]) {
+        int64_t ns = 0;
+        for (int a = ptr[t]; a < ptr[t + 1]; ++a) ns += s1[src[a]] - s0[src[a]];
+        parts = (int)max((int64_t)1, (ns + NEAR_CHUNK - 1) / NEAR_CHUNK);
+    }
+    cnt[t] = parts;
+}
+__global__ void k_near_items_fill(int n_nodes, const int *__restrict__ cnt, const int *__restrict__ pos,
+                                  int *__restrict__ item_node, int *__restrict__ item_part,
+                                  int *__restrict__ item_np) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes) return;
+    const int n = cnt[t], o = pos[t];
+    for (int j = 0; j < n; ++j) {
+        item_node[o + j] = t;
+        item_part[o + j] = j;
+        item_np[o + j] = n;
+    }
 }
 
 __global__ void k_layer_mismatch(int n_nodes, const int *__restrict__ layer,
@@ -922,22 +972,63 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
         P->launches++;
     }
     P->n_fon = 0;
-    if (P->opt.far_of_near && nn > 0) {
-        TRY(dbuf_ensure(P->fon_cnt, (size_t)(nn + 1) * 4));
-        TRY(dbuf_ensure(P->fon_ptr, (size_t)(nn + 1) * 4));
-        CUDA_TRY(cudaMemsetAsync(P->fon_cnt.p, 0, (size_t)(nn + 1) * 4, st));
-        k_fon_count<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_level), dp<int>(P->near_ptr),
-                                                       dp<int>(P->near_src), dp<int>(P->fon_cnt));
+    if (P->opt.far_of_near && P->n_near > 0) {
+        const int64_t ne = P->n_near;
+        TRY(dbuf_ensure(P->near_fl, (size_t)ne * 4));
+        TRY(dbuf_ensure(P->fon_key, (size_t)ne * 8));
+        TRY(dbuf_ensure(P->fon_key_sorted, (size_t)ne * 8));
+        TRY(dbuf_ensure(P->fon_cnt, (size_t)(ne + 1) * 4));
+        TRY(dbuf_ensure(P->fon_ptr, (size_t)(ne + 1) * 4));
+        k_fon_anchor<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_level), dp<int>(P->n_parent),
+                                                        dp<int>(P->n_ix), dp<int>(P->n_iy), dp<int>(P->n_iz),
+                                                        dp<int>(P->near_ptr), dp<int>(P->near_src),
+                                                        dp<int>(P->near_fl), dp<unsigned long long>(P->fon_key));
         P->launches++;
-        TRY(scan_excl(P, dp<int>(P->fon_cnt), dp<int>(P->fon_ptr), nn + 1, st));
+        size_t bytes = 0;
+        cub::DeviceRadixSort::SortKeys(nullptr, bytes, dp<unsigned long long>(P->fon_key),
+                                       dp<unsigned long long>(P->fon_key_sorted), (int)ne, 0, 64, st);
+        TRY(dbuf_ensure(P->cub_tmp, bytes));
+        CUDA_TRY(cub::DeviceRadixSort::SortKeys(P->cub_tmp.p, bytes, dp<unsigned long long>(P->fon_key),
+                                                dp<unsigned long long>(P->fon_key_sorted), (int)ne, 0, 64, st));
+        k_fon_heads<<<grid_for(ne, 256), 256, 0, st>>>(ne, dp<unsigned long long>(P->fon_key_sorted),
+                                                       dp<int>(P->fon_cnt));
+        P->launches++;
+        CUDA_TRY(cudaMemsetAsync(dp<int>(P->fon_cnt) + ne, 0, 4, st));
+        TRY(scan_excl(P, dp<int>(P->fon_cnt), dp<int>(P->fon_ptr), ne + 1, st));
         int nf = 0;
-        CUDA_TRY(cudaMemcpyAsync(&nf, dp<int>(P->fon_ptr) + nn, 4, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaMemcpyAsync(&nf, dp<int>(P->fon_ptr) + ne, 4, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaStreamSynchronize(st));
         P->n_fon = nf;
         if (nf > 0) {
-            k_fon_fill<<<grid_for(nn, 128), 128, 0, st>>>(nn, dp<int>(P->n_level), dp<int>(P->near_ptr),
-                                                          dp<int>(P->near_src), dp<int>(P->fon_ptr), P->n_v,
+            k_fon_fill<<<grid_for(ne, 256), 256, 0, st>>>(ne, dp<unsigned long long>(P->fon_key_sorted),
+                                                          dp<int>(P->fon_cnt), dp<int>(P->fon_ptr), P->n_v,
                                                           dp<int>(P->pair_t), dp<int>(P->v_src));
+            P->launches++;
+        }
+    }
+    // near-field work items
+    {
+        TRY(dbuf_ensure(P->nitem_cnt, (size_t)(P->n_nodes + 1) * 4));
+        TRY(dbuf_ensure(P->nitem_pos, (size_t)(P->n_nodes + 1) * 4));
+        CUDA_TRY(cudaMemsetAsync(dp<int>(P->nitem_cnt) + P->n_nodes, 0, 4, st));
+        if (P->n_nodes > 0) {
+            k_near_items_count<<<grid_for(P->n_nodes, 128), 128, 0, st>>>(
+                P->n_nodes, dp<int>(P->n_split), dp<int>(P->n_t0), dp<int>(P->n_t1), dp<int>(P->n_s0),
+                dp<int>(P->n_s1), dp<int>(P->near_ptr), dp<int>(P->near_src), dp<int>(P->nitem_cnt));
+            P->launches++;
+        }
+        TRY(scan_excl(P, dp<int>(P->nitem_cnt), dp<int>(P->nitem_pos), P->n_nodes + 1, st));
+        int ni = 0;
+        CUDA_TRY(cudaMemcpyAsync(&ni, dp<int>(P->nitem_pos) + P->n_nodes, 4, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        P->n_near_items = ni;
+        TRY(dbuf_ensure(P->nitem_node, (size_t)(ni + 1) * 4));
+        TRY(dbuf_ensure(P->nitem_part, (size_t)(ni + 1) * 4));
+        TRY(dbuf_ensure(P->nitem_np, (size_t)(ni + 1) * 4));
+        if (ni > 0) {
+            k_near_items_fill<<<grid_for(P->n_nodes, 128), 128, 0, st>>>(
+                P->n_nodes, dp<int>(P->nitem_cnt), dp<int>(P->nitem_pos), dp<int>(P->nitem_node),
+                dp<int>(P->nitem_part), dp<int>(P->nitem_np));
             P->launches++;
         }
     }

@@ -9,7 +9,7 @@
   images, pushed into the plan);
 * the mixed form with tables against the oracle direct sum, beside Algorithm
   1 (the table-versus-recurrence report);
-* a geometry whose pairs reach an image distance <= 0 is refused.
+* keys whose image distance lies below the particle slab's keep the images.
 """
 import math
 
@@ -102,12 +102,27 @@ def test_mixed_tables_versus_recurrence():
     assert err[1] < 1e-5 and err[2] < 1e-5, err
 
 
-def test_nonpositive_image_distance_is_refused():
+def test_keys_beyond_the_slab_keep_the_images():
+    """Three slabs: coarse boxes of the top layer have centres above its
+    particle slab (image distance down to -0.1), so some (key, term)
+    derivatives stay with the images while the rest come from the tables; the
+    FP64 form matches the oracle TE-FMM with the same rule (cross-layer fits
+    from the oracle)."""
     torch = need_gpu()
-    from paper_1902_05875_gb300 import tefmm
+    from oracle.tefmm import TEFMM
     from paper_1902_05875_gb300 import workloads as W
-    w = W.three_layer_slabs(6000, 4, 32, seed=0)
+    from _helpers import push_cross_fits
+    w = W.three_layer_slabs(3000, 3, 32, seed=0, n_images=16)
+    med, img = oracle_images(w)
     plan = make_plan(w, algorithm=2, table_n=8)
-    with pytest.raises(tefmm.TefmmError) as e:
-        gpu_eval(plan, torch, w.src, w.q)
-    assert e.value.status == tefmm.ERR_NOT_IMPLEMENTED
+    push_images(plan, img)
+    gpu_eval(plan, torch, w.src, w.q)
+    f = TEFMM(med, img, w.p, w.leaf_cap, n_images=w.n_images, algorithm=2, table_n=8).setup(w.src, w.src)
+    push_cross_fits(plan, f)
+    phi = gpu_eval(plan, torch, w.src, w.q)
+    st = plan.stats()
+    assert st["n_alg2_image_keys"] > 0 and st["n_alg2_tables"] > 0, st
+    ref = f.evaluate(w.q)
+    err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    print(f"three slabs, tables + images: {st['n_alg2_image_keys']} image keys, FP64 vs oracle {err:.2e}")
+    assert err <= 1e-11, err

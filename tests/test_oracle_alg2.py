@@ -14,7 +14,8 @@ eq. ``sysdifferential``).
   grid size (degree 7 Lagrange, order-8 convergence);
 * a medium's reaction term: the table derivatives agree with the DCIM image
   recurrence of Algorithm 1 to within the fit's own accuracy;
-* ranges: a layer whose pairs reach an image distance <= 0 is refused;
+* ranges: keys below the term's smallest image distance over the particle
+  slab stay with the images and out of the table ranges;
 * end to end: the oracle TE-FMM with Algorithm 2 tables matches the direct
   sum to the error of Algorithm 1.
 """
@@ -119,14 +120,18 @@ def test_medium_term_matches_dcim_recurrence(tag, tol):
     assert err < tol, err
 
 
-def test_ranges_refuse_nonpositive_image_distance():
+def test_ranges_leave_keys_below_the_slab_to_the_images():
     med = Medium([0.0, -1.2], [1.2, 1.5, 2.0])
-    # uu of the middle layer: zeta = z + z' + 2.4, reaching 0 for centres at -1.2
-    keys = [(0.5, 2, 0, 0, -1.0), (0.5, 2, 0, 0, -2.4)]
-    with pytest.raises(NotImplementedError):
-        A2.layer_ranges(med, 1, keys)
-    rho_max, rng = A2.layer_ranges(med, 1, keys[:1])
-    assert rho_max == 1.0 and abs(rng['uu'][0] - 1.4) < 1e-15
+    # uu of the middle layer: zeta = z + z' + 2.4; a particle slab [-1.1, -0.1]
+    # gives zeta_min = 0.2; a key with centres summing to -2.4 (zeta = 0) is left out
+    floor = {'uu': 0.2, 'dd': 0.2, 'ud': 1.4, 'du': 1.4}
+    keys = [(0.5, 2, 0, 0, -1.0), (0.5, 3, 1, 0, -2.4)]
+    rho_max, rng = A2.layer_ranges(med, 1, keys, floor)
+    assert rng['uu'] == (1.4, 2.4)          # zeta_hi widened from a single value
+    assert abs(rng['dd'][0] - 1.0) < 1e-15 and abs(rng['ud'][0] - 2.4) < 1e-15
+    assert rho_max == math.hypot(1.5, 0.5)     # the second key still serves dd, ud, du
+    rho_max, rng = A2.layer_ranges(med, 1, keys[1:], {'uu': 0.2, 'dd': 9.0, 'ud': 9.0, 'du': 9.0})
+    assert rng == {} and rho_max == 1.0
 
 
 def test_fmm_with_tables_matches_direct_sum():
