@@ -71,7 +71,18 @@ def quadrature_T(k, kmax, s, P2, rhos, zeta):
     k = complex(k)
     nodes, weights = contour_nodes(kmax, zeta, max(float(rhos.max()), 1e-3), nd=P2 + 2)
     kz = kz_branch(k, nodes)
-    base = weights * nodes * s(nodes) * np.exp(1j * kz * zeta) / kz / k
+    ez = np.exp(1j * kz * zeta)
+    with np.errstate(over='ignore', invalid='ignore'):
+        sv = np.asarray(s(nodes), dtype=complex)
+    # far out on the path a term's s_tau can come out as 0 * inf (an underflowed
+    # density times an overflowed e^{-i k_z D}); there e^{i k_z zeta} k_rho^(P2+1)
+    # is negligible, which is checked before those nodes are dropped
+    bad = ~np.isfinite(sv)
+    if bad.any():
+        if np.max(np.abs(ez[bad]) * np.abs(nodes[bad]) ** (P2 + 1)) > 1e-30:
+            raise FloatingPointError("s_tau not finite where the integrand is not negligible")
+        sv[bad] = 0.0
+    base = weights * nodes * sv * ez / kz / k
     idx = table_index(P2)
     out = np.zeros((len(rhos), len(idx)), dtype=complex)
     kzp = [(1j * kz) ** n for n in range(P2 + 1)]
