@@ -554,8 +554,9 @@ def main():
     flops_m2l = 8.0 * np_ * np_ * (st["n_m2l_items"] + st["n_m2l_items_cross"])
     img_layer = [sum(len(t["A"]) for t in imgs if t["layer"] == l) for l in range(len(w.k))]
     pairs_layer = st["n_p2p_pairs_layer"][:len(w.k)]
+    n_pairs, n_img_terms = int(sum(pairs_layer)), int(st["n_near_img_terms"])
     if mixed:
-        flops_near = sum(pp * (FLOPS32_FREE + FLOPS32_IMAGE * m) for pp, m in zip(pairs_layer, img_layer))
+        flops_near = FLOPS32_FREE * n_pairs + FLOPS32_IMAGE * n_img_terms
         ms_m2l_k = st["ms_m2l_kernel"]
         m2l_roof = {"kernel": "k_m2l_tc (tcgen05 kind::tf32, 3xTF32, key-grouped M2L, same- and cross-layer)",
                     "bound": "tensor", "achieved": flops_m2l / (ms_m2l_k * 1e-3) / 1e12,
@@ -568,10 +569,11 @@ def main():
                      "achieved": flops_near / (ph["ms_near"] * 1e-3) / 1e12, "peak": pk["fp32_fma_tflops"],
                      "unit": "TFLOP/s", "peak_source": "FP32 FMA throughput measured by this run",
                      "ms_per_step": ph["ms_near"],
-                     "work": f"{FLOPS32_FREE} + {FLOPS32_IMAGE} per image term per pair; pairs by target layer "
-                             f"{pairs_layer}, image terms per layer {img_layer}"}
+                     "work": f"{FLOPS32_FREE} per particle pair + {FLOPS32_IMAGE} per (pair, image term) evaluated; "
+                             f"{n_pairs} pairs, {n_img_terms} image terms after the far-of-near reading "
+                             f"(images per layer {img_layer})"}
     else:
-        flops_near = sum(pp * (FLOPS_FREE + FLOPS_IMAGE * m) for pp, m in zip(pairs_layer, img_layer))
+        flops_near = FLOPS_FREE * n_pairs + FLOPS_IMAGE * n_img_terms
         m2l_roof = {"kernel": "k_m2l_fp64 + k_m2l_x (key-grouped complex M2L, FP64)", "bound": "alu",
                     "achieved": flops_m2l / (ph["ms_m2l"] * 1e-3) / 1e12, "peak": pk["fp64_fma_tflops"],
                     "unit": "TFLOP/s", "peak_source": "FP64 FMA throughput measured by this run",

@@ -102,8 +102,9 @@ typedef struct {
                               new geometry leaves the ranges); FP64 degree-7 Lagrange
                               interpolation in each direction, assembled into Cartesian
                               derivatives through D+- = d_x +- i d_y.  The free-space part,
-                              cross-layer components and the near field keep Algorithm 1;
-                              far_of_near is ignored.  The integral converges for zeta > 0
+                              cross-layer components, the near field and the far-of-near
+                              translations (far images only) keep Algorithm 1's images.
+                              The integral converges for zeta > 0
                               only: a key whose image distance lies below the term's
                               smallest one over the layer's particle slab (zext; the
                               DCIM shift zeta_min), i.e. box centres of a coarse level
@@ -167,6 +168,8 @@ typedef struct {
     double ms_alg2_build;  /* ... host time of the last (re)build of those tables      */
     int n_alg2_image_keys; /* ... (key, term) derivatives of the last geometry taken from
                               the images instead (image distance below the slab's)   */
+    int64_t n_near_img_terms; /* last geometry: near-field (particle pair, image term)
+                              evaluations, after the far-of-near reading              */
 } tefmm_stats;
 
 /* Fill ``opt`` with defaults: p = 6, leaf_cap = 64, max_level = 20, FP64,

@@ -509,14 +509,14 @@ class TEFMM:
                  algorithm=1, table_n=64):
         self.med = med
         self.kh_max = kh_max
-        # Algorithm 2 (Sec. 4.2): same-layer reaction derivatives from
-        # interpolated tables of Sommerfeld integrals (oracle.alg2) instead of
-        # complex images; the near field keeps the images, and far-of-near
-        # (which splits the image set) does not apply
+        # Algorithm 2 (Sec. 4.2): same-layer reaction derivatives of the V
+        # pairs from interpolated tables of Sommerfeld integrals (oracle.alg2)
+        # instead of complex images; the near field keeps the images, and so
+        # do the far-of-near translations (their far images only)
         self.algorithm = algorithm
         self.table_n = table_n
         self.alg2 = {}
-        self.far_of_near = far_of_near and algorithm == 1
+        self.far_of_near = far_of_near
         self.images = images
         self.zext = zext if zext is not None else (images.zext if images is not None else None)
         # cross-layer images: dict (lt, ls, direction, level, izs, k3p) -> (A, Z);
@@ -580,7 +580,7 @@ class TEFMM:
         mi2 = multi_indices(P2)
         odd3 = (-1.0) ** mi2[:, 2]
         terms = {t['tag']: t for t in self.images.terms[l]} if self.images is not None else {}
-        if self.algorithm == 2:
+        if self.algorithm == 2 and far_thr is None:
             return self._tables_alg2(l, h, keysB, keysA, odd3)
         TB = np.zeros((len(keysB), len(mi2)), dtype=complex)
         TA = np.zeros((len(keysA), len(mi2)), dtype=complex)

@@ -377,7 +377,7 @@ int alg2_prepare(tefmm_plan_s *P, cudaStream_t st) {
     int n_images = 0;
     for (uint64_t key : keys) {
         const int kind = key_kind(key);
-        if (kind > 1) continue;            // far-of-near keys do not occur with tables
+        if (kind > 1) continue;            // far-of-near keys (kind 2) keep the images
         const int l = key_layer(key), lev = key_level(key);
         const double h = P->side / (double)(1 << lev);
         const double rho = hypot((double)key_dx(key) * h, (double)key_dy(key) * h);

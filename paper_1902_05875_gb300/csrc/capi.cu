@@ -280,6 +280,7 @@ extern "C" int tefmm_get_stats(tefmm_plan P, tefmm_stats *o) {
     o->n_alg2_tables = (int)P->a2.size();
     o->ms_alg2_build = P->ms_alg2_build;
     o->n_alg2_image_keys = P->n_alg2_image_keys;
+    o->n_near_img_terms = P->n_near_img_terms;
     o->leaf_cap_used = P->leaf_cap_eff;
     o->ms_autotune = P->ms_autotune;
     o->n_tables_built = P->n_tables_built;

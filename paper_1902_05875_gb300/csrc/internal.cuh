@@ -183,6 +183,7 @@ struct tefmm_plan_s {
     // near-field work items (one CTA each): target leaf, chunk index, chunks of that leaf
     DBuf nitem_cnt, nitem_pos, nitem_node, nitem_part, nitem_np;
     int n_near_items = 0;
+    int64_t n_near_img_terms = 0;   // pair x image-term evaluations of the near field
     int cap_D = 64, cap_X = 0;
 
     // expansions

@@ -205,7 +205,6 @@ extern "C" int tefmm_plan_create(int n_layers, const double *interfaces, const d
         (o.table_n != 0 && (o.table_n < 8 || o.table_n > 512)))
         return TEFMM_ERR_INVALID_ARG;
     if (o.split != TEFMM_SPLIT_TF32X3) return TEFMM_ERR_NOT_IMPLEMENTED;
-    if (o.algorithm == TEFMM_ALG_TABLES) o.far_of_near = 0;   // it splits image sets the tables replace
     // default particle ranges: the whole layer (top/bottom: one unit beyond the interface)
     for (int l = 0; l < n_layers; ++l) {
         double top = (l == 0) ? (n_layers > 1 ? interfaces[0] + 1.0 : 1.0) : interfaces[l - 1];

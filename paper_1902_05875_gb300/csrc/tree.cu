@@ -24,6 +24,7 @@
 #include <algorithm>
 
 #include "internal.cuh"
+#include "ops_common.cuh"
 
 namespace {
 
@@ -598,6 +599,31 @@ __global__ void k_fon_fill(int64_t n, const unsigned long long *__restrict__ k, 
     pair_s[o] = (int)(k[i] & 0xffffffffULL);
 }
 
+// Image terms the near-field kernels evaluate: per entry, its particle pairs
+// times the images of the target layer's terms that are near at the entry's
+// far-of-near level (all images when it has none).  c[l][lv] = that image
+// count for layer l at level lv, c[l][NBITS + 1] = all of the layer's images.
+struct NearImgCount {
+    int c[TEFMM_MAX_LAYERS][TEFMM_NBITS + 2];
+};
+__global__ void k_near_img_terms(int n_nodes, const int *__restrict__ layer, const int *__restrict__ t0,
+                                 const int *__restrict__ t1, const int *__restrict__ s0,
+                                 const int *__restrict__ s1, const int *__restrict__ ptr,
+                                 const int *__restrict__ src, const int *__restrict__ fl, NearImgCount nc,
+                                 unsigned long long *out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes) return;
+    const unsigned long long nt = (unsigned long long)(t1[t] - t0[t]);
+    const int l = layer[t] & 7;
+    unsigned long long acc = 0;
+    for (int a = ptr[t]; a < ptr[t + 1]; ++a) {
+        const int lv = fl ? fl[a] : -1;
+        const int nimg = nc.c[l][lv >= 0 ? lv : TEFMM_NBITS + 1];
+        acc += nt * (unsigned long long)(s1[src[a]] - s0[src[a]]) * (unsigned long long)nimg;
+    }
+    if (acc) atomicAdd(out, acc);
+}
+
 // Near-field work items: the near sources of a target leaf, taken in list
 // order, are cut into chunks of NEAR_CHUNK; each chunk is one CTA of the
 // near-field kernels, so that a leaf beside a dense region (W-type entries of
@@ -1006,6 +1032,27 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
             P->launches++;
         }
     }
+    // image terms the near field evaluates (for the near kernels' work figure)
+    {
+        NearImgCount nc{};
+        const FonThr ft = fon_thresholds(P);
+        for (const TermDesc &td : P->terms)
+            for (int j = td.first; j < td.first + td.count; ++j) {
+                const double depth = -P->Z[j].x;
+                for (int lv = 0; lv <= TEFMM_NBITS; ++lv)
+                    nc.c[td.layer][lv] += !(depth >= ft.thr[lv]);
+                nc.c[td.layer][TEFMM_NBITS + 1] += 1;
+            }
+        CUDA_TRY(cudaMemsetAsync(dp<unsigned long long>(P->counters) + 9, 0, 8, st));
+        if (nn > 0) {
+            k_near_img_terms<<<grid_for(nn, 128), 128, 0, st>>>(
+                nn, dp<int>(P->n_layer), dp<int>(P->n_t0), dp<int>(P->n_t1), dp<int>(P->n_s0), dp<int>(P->n_s1),
+                dp<int>(P->near_ptr), dp<int>(P->near_src),
+                (P->opt.far_of_near && P->n_near > 0) ? dp<int>(P->near_fl) : nullptr, nc,
+                dp<unsigned long long>(P->counters) + 9);
+            P->launches++;
+        }
+    }
     // near-field work items
     {
         TRY(dbuf_ensure(P->nitem_cnt, (size_t)(P->n_nodes + 1) * 4));
@@ -1032,10 +1079,11 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
             P->launches++;
         }
     }
-    unsigned long long np2p[9] = {};
-    CUDA_TRY(cudaMemcpyAsync(np2p, P->counters.p, 72, cudaMemcpyDeviceToHost, st));
+    unsigned long long np2p[10] = {};
+    CUDA_TRY(cudaMemcpyAsync(np2p, P->counters.p, 80, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     P->n_p2p_pairs = (int64_t)np2p[0];
     for (int l = 0; l < 8; ++l) P->p2p_by_layer[l] = (int64_t)np2p[1 + l];
+    P->n_near_img_terms = (int64_t)np2p[9];
     return TEFMM_OK;
 }

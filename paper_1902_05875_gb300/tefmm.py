@@ -53,7 +53,7 @@ class Stats(ctypes.Structure):
                 ("ms_m2l_kernel", ctypes.c_double), ("n_m2l_kernel_launches", ctypes.c_int),
                 ("n_p2p_pairs_layer", ctypes.c_int64 * 8), ("n_fon_pairs", ctypes.c_int64),
                 ("n_alg2_tables", ctypes.c_int), ("ms_alg2_build", ctypes.c_double),
-                ("n_alg2_image_keys", ctypes.c_int)]
+                ("n_alg2_image_keys", ctypes.c_int), ("n_near_img_terms", ctypes.c_int64)]
 
 
 EXPORTED = [

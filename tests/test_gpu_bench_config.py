@@ -74,18 +74,26 @@ def test_bench_config_mixed_matches_oracle(case):
 
 
 def test_far_of_near_changes_the_fp64_form_below_its_bound(case):
-    """The device's far-of-near path (far images of adjacent same-level leaf
-    pairs through M2L) against every image in P2P, FP64 form, same images:
-    the two agree far below the method's error (1e-8), and pairs were moved."""
+    """The device's far-of-near path (far images of near pairs through the
+    M2L of their anchors) against every image in P2P, FP64 form, same images:
+    the two agree far below the method's error (1e-8), and pairs were moved.
+    The near field's count of (pair, image term) evaluations is pairs x images
+    per target layer without the reading and smaller with it."""
     torch = need_gpu()
     w, med, img, f, idx = case
-    out = {}
+    out, terms = {}, {}
     for fon in (True, False):
         plan = make_plan(w, far_of_near=fon)
         push_images(plan, img)
         out[fon] = gpu_eval(plan, torch, w.src, w.q)
+        st = plan.stats()
+        terms[fon] = st["n_near_img_terms"]
         if fon:
-            assert plan.stats()["n_fon_pairs"] > 0
+            assert st["n_fon_pairs"] > 0
+        else:
+            per_layer = [sum(len(t["A"]) for t in plan.images() if t["layer"] == l) for l in range(len(w.k))]
+            assert terms[False] == sum(int(p) * m for p, m in zip(st["n_p2p_pairs_layer"], per_layer))
+    assert 0 < terms[True] < terms[False], terms
     err = np.linalg.norm(out[True] - out[False]) / np.linalg.norm(out[False])
     print(f"far-of-near on vs off (FP64 form, p=10): {err:.2e}")
     assert err <= 1e-8, err
