@@ -298,7 +298,7 @@ int m2l_apply_tc_cross(tefmm_plan_s *P, cudaStream_t st, const cplx *alpha_x, cp
 size_t m2l_tc_smem(int np, int MT, int tab_entries);
 void m2l_tc_geometry(int np, int MT, int *Kpad, int *Ncta, int *nsplit);
 #define NEAR_CHUNK 4096   // near sources per near-field work item
-#define TC_MT 1         // tiles of 128 pairs per pass, same-layer keys (two CTAs per SM)
+#define TC_MT 1         // tiles of 128 pairs per pass, same-layer keys
 #define TC_MT_CROSS 1   // cross-layer keys
 int downward_pass(tefmm_plan_s *P, cudaStream_t st);
 int near_field(tefmm_plan_s *P, double *phi, cudaStream_t st);
