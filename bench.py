@@ -546,6 +546,22 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     e2e_ms = float(np.mean(e2e_t)) * 1e3
 
+    # repeated products on one geometry (an iterative solver's use): set_points
+    # once, then only the charge-dependent phases (tefmm_apply) per step
+    plan.set_points(x, y, z)
+    plan.apply(q, out=out)
+    app_t = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record()
+        plan.apply(q, out=out)
+        a1.record()
+        torch.cuda.synchronize()
+        app_t.append(a0.elapsed_time(a1))
+    apply_ms = float(np.mean(app_t))
+
     # rooflines of the two dominant kernels, from their own device times
     pk_file, pk_src = peaks()
     pk = measure_peaks(torch)
@@ -608,6 +624,9 @@ def main():
         "e2e": {"value": world * N * N / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(N * 40), "d2h_bytes_per_step": int(N * 16),
                 "ms_per_step": e2e_ms},
+        "apply": {"ms_per_step": apply_ms, "value": N * N / (apply_ms * 1e-3), "unit": UNIT,
+                  "what": "tefmm_apply on the geometry of one tefmm_set_points (trees, lists, tables "
+                          "kept): the repeated products of an iterative solver"},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "peaks_file": {"source": pk_src, "hbm_gbs": pk_file.get("hbm_gbs"), "bf16_tflops": pk_file.get("bf16_tflops")},
