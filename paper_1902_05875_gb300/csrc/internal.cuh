@@ -163,7 +163,7 @@ struct tefmm_plan_s {
     int64_t ns = 0, nt = 0, nitems = 0;
     bool shared_pts = false;
     bool geom_ready = false;   // tree, lists and tables match the last points (eval or set_points)
-    DBuf keys_in, keys_out, vals_in, vals_out, cub_tmp, scan_tmp;
+    DBuf keys_in, keys_out, vals_in, vals_out, sort_tmp, scan_tmp;
     DBuf item_node, item_flag, item_scan, cnt_s, cnt_t;
     DBuf sx, sy, sz, sq, tx, ty, tz, perm_s, perm_t;
     DBuf n_layer, n_level, n_ix, n_iy, n_iz, n_parent, n_cfirst, n_nchild, n_s0, n_s1, n_t0,
@@ -318,6 +318,10 @@ int cross_prepare(tefmm_plan_s *P, cudaStream_t st);
 int cross_tables(tefmm_plan_s *P, cudaStream_t st);
 int cross_apply(tefmm_plan_s *P, cudaStream_t st);
 void cross_release(tefmm_plan_s *P);
+// sortscan.cu: int32 prefix sums and the stable radix sort of 64-bit keys
+int dev_scan_i32(tefmm_plan_s *P, const int *in, int *out, int64_t n, bool inclusive, cudaStream_t st);
+int dev_sort_u64(tefmm_plan_s *P, const uint64_t *kin, uint64_t *kout, const int *vin, int *vout, int64_t n,
+                 cudaStream_t st);
 // alg2.cu
 int alg2_prepare(tefmm_plan_s *P, cudaStream_t st);
 void alg2_release(tefmm_plan_s *P);

@@ -18,7 +18,6 @@
 //   B (sz*szp = -1): free space, up-down, down-up; key (level, layer, dx, dy, dz)
 //   A (sz*szp = +1): up-up, down-down;             key (level, layer, dx, dy, iz_t+iz_s)
 // with (-1)^{g3} folded into the down-up and down-down images.
-#include <cub/cub.cuh>
 
 #include "ops_common.cuh"
 #include "alg2.cuh"
@@ -754,13 +753,7 @@ __global__ void k_near_zero(int n_items, NearArgs a) {
 }
 
 int scan_i(tefmm_plan_s *P, const int *in, int *out, int64_t n, bool inclusive, cudaStream_t st) {
-    size_t bytes = 0;
-    if (inclusive) cub::DeviceScan::InclusiveSum(nullptr, bytes, in, out, (int)n, st);
-    else cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, (int)n, st);
-    TRY(dbuf_ensure(P->scan_tmp, bytes));
-    if (inclusive) CUDA_TRY(cub::DeviceScan::InclusiveSum(P->scan_tmp.p, bytes, in, out, (int)n, st));
-    else CUDA_TRY(cub::DeviceScan::ExclusiveSum(P->scan_tmp.p, bytes, in, out, (int)n, st));
-    return TEFMM_OK;
+    return dev_scan_i32(P, in, out, n, inclusive, st);
 }
 
 }  // namespace
@@ -832,14 +825,8 @@ int m2l_prepare(tefmm_plan_s *P, cudaStream_t st) {
                                                    dp<uint64_t>(P->pair_slot),
                                                    dp<int>(P->pair_idx), dp<int>(P->flags));
     P->launches++;
-    size_t bytes = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, bytes, dp<uint64_t>(P->pair_slot),
-                                    dp<uint64_t>(P->pair_slot_sorted), dp<int>(P->pair_idx),
-                                    dp<int>(P->pair_idx_sorted), (int)ni, 0, 64, st);
-    TRY(dbuf_ensure(P->cub_tmp, bytes));
-    CUDA_TRY(cub::DeviceRadixSort::SortPairs(P->cub_tmp.p, bytes, dp<uint64_t>(P->pair_slot),
-                                             dp<uint64_t>(P->pair_slot_sorted), dp<int>(P->pair_idx),
-                                             dp<int>(P->pair_idx_sorted), (int)ni, 0, 64, st));
+    TRY(dev_sort_u64(P, dp<uint64_t>(P->pair_slot), dp<uint64_t>(P->pair_slot_sorted), dp<int>(P->pair_idx),
+                     dp<int>(P->pair_idx_sorted), ni, st));
     const uint64_t *keys = dp<uint64_t>(P->pair_slot_sorted);
     // heads and segments (reuse item buffers as scratch)
     TRY(dbuf_ensure(P->item_flag, (ni + 1) * 4));

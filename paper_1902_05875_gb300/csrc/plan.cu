@@ -258,7 +258,7 @@ extern "C" int tefmm_plan_destroy(tefmm_plan P) {
     if (!P) return TEFMM_OK;
     DBuf *all[] = {&P->d_terms, &P->d_A, &P->d_Z, &P->d_k, &P->d_mi, &P->d_m2l_g, &P->d_m2l_cB,
                    &P->d_m2l_cA, &P->keys_in, &P->keys_out, &P->vals_in,
-                   &P->vals_out, &P->cub_tmp, &P->scan_tmp, &P->item_node, &P->item_flag,
+                   &P->vals_out, &P->sort_tmp, &P->scan_tmp, &P->item_node, &P->item_flag,
                    &P->item_scan, &P->cnt_s, &P->cnt_t, &P->sx, &P->sy, &P->sz, &P->sq, &P->tx,
                    &P->ty, &P->tz, &P->perm_s, &P->perm_t, &P->n_layer, &P->n_level, &P->n_ix,
                    &P->n_iy, &P->n_iz, &P->n_parent, &P->n_cfirst, &P->n_nchild, &P->n_s0,

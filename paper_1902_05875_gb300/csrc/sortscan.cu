@@ -1,0 +1,204 @@
+// Prefix sums and the stable radix sort of the tree, list and M2L-key
+// builders.
+//
+// Scan of int32 (exclusive or inclusive): tiles of SCAN_TILE values, one CTA
+// each.  A CTA scans its tile (per-thread sequential sums, then a warp-shuffle
+// scan of the thread totals) and writes the tile total.  The tile totals are
+// scanned the same way (recursively while there is more than one tile), and a
+// last kernel adds each tile's offset.
+//
+// Sort: least-significant-digit radix sort of 64-bit keys (optionally with an
+// int32 value each), 4-bit digits, 16 passes, stable.  A pass:
+// (1) every CTA counts the digits of its tile of SORT_TILE keys;
+// (2) the counts, laid out digit-major ([digit][tile]), are scanned, giving
+//     each (digit, tile) its first output position;
+// (3) every CTA re-reads its tile and writes each key to that position plus
+//     its rank among the tile's keys of the same digit.  The rank is the
+//     key's order within its thread's consecutive run, plus the keys of that
+//     digit held by the threads before it.  So equal digits keep their input
+//     order, which makes every pass, and the sort, stable.
+// The passes ping-pong between the output and a scratch buffer; the 16th
+// lands in the output.
+#include "internal.cuh"
+
+namespace {
+
+constexpr int SCAN_THREADS = 256, SCAN_ITEMS = 8, SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr int SORT_THREADS = 256, SORT_ITEMS = 16, SORT_TILE = SORT_THREADS * SORT_ITEMS;
+constexpr int RADIX_BITS = 4, RADIX = 1 << RADIX_BITS;
+
+// exclusive scan of v over the block (blockDim.x = 256); *total gets the sum
+__device__ __forceinline__ int block_excl_scan(int v, int *warp_sums, int *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) warp_sums[lane] = w;   // inclusive over warps
+    }
+    __syncthreads();
+    const int before = warp > 0 ? warp_sums[warp - 1] : 0;
+    const int res = before + x - v;
+    if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return res;
+}
+
+// per tile: out = exclusive (or inclusive) scan within the tile; sums[tile] = tile total
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tile(const int *__restrict__ in, int *__restrict__ out,
+                                                            int64_t n, int inclusive, int *__restrict__ sums) {
+    __shared__ int ws[32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = base + i < n ? in[base + i] : 0;
+        s += v[i];
+    }
+    int total = 0;
+    int run = block_excl_scan(s, ws, &total);
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (base + i < n) out[base + i] = inclusive ? run + v[i] : run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(int *__restrict__ out, int64_t n, const int *__restrict__ offs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += offs[i / SCAN_TILE];
+}
+
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// scratch ints for scanning n values: the tile totals of every recursion level
+int64_t scan_scratch(int64_t n) {
+    int64_t s = 0;
+    for (int64_t m = ceil_div(n, SCAN_TILE); m > 1; m = ceil_div(m, SCAN_TILE)) s += 2 * m;
+    return s + 2;
+}
+
+int scan_rec(const int *in, int *out, int64_t n, bool inclusive, int *scratch, cudaStream_t st) {
+    if (n <= 0) return TEFMM_OK;
+    const int64_t nt = ceil_div(n, SCAN_TILE);
+    int *sums = scratch, *offs = scratch + nt;
+    k_scan_tile<<<(unsigned)nt, SCAN_THREADS, 0, st>>>(in, out, n, inclusive ? 1 : 0, sums);
+    CUDA_TRY(cudaGetLastError());
+    if (nt > 1) {
+        TRY(scan_rec(sums, offs, nt, false, scratch + 2 * nt, st));
+        k_scan_add<<<(unsigned)ceil_div(n, 256), 256, 0, st>>>(out, n, offs);
+        CUDA_TRY(cudaGetLastError());
+    }
+    return TEFMM_OK;
+}
+
+}  // namespace
+
+int dev_scan_i32(tefmm_plan_s *P, const int *in, int *out, int64_t n, bool inclusive, cudaStream_t st) {
+    if (n <= 0) return TEFMM_OK;
+    TRY(dbuf_ensure(P->scan_tmp, (size_t)scan_scratch(n) * sizeof(int)));
+    TRY(scan_rec(in, out, n, inclusive, dp<int>(P->scan_tmp), st));
+    P->launches += 1 + 2 * (ceil_div(n, SCAN_TILE) > 1 ? 1 : 0);
+    return TEFMM_OK;
+}
+
+namespace {
+
+// digit counts of every tile: counts[digit * ntile + tile]
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_count(const uint64_t *__restrict__ keys, int64_t n,
+                                                              int shift, int ntile, int *__restrict__ counts) {
+    __shared__ int c[RADIX];
+    if (threadIdx.x < RADIX) c[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)threadIdx.x * SORT_ITEMS;
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i)
+        if (base + i < n) atomicAdd(&c[(int)((keys[base + i] >> shift) & (RADIX - 1))], 1);
+    __syncthreads();
+    if (threadIdx.x < RADIX) counts[(int64_t)threadIdx.x * ntile + blockIdx.x] = c[threadIdx.x];
+}
+
+// stable scatter of one tile by the digit at shift; offs = exclusive scan of the counts
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint64_t *__restrict__ kin,
+                                                                const int *__restrict__ vin,
+                                                                uint64_t *__restrict__ kout, int *__restrict__ vout,
+                                                                int64_t n, int shift, int ntile,
+                                                                const int *__restrict__ offs) {
+    __shared__ int ws[32];
+    __shared__ int first[RADIX];                       // output position of the tile's first key of each digit
+    __shared__ int rank[RADIX * SORT_THREADS];         // per digit and thread: keys of that digit before it
+    const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)threadIdx.x * SORT_ITEMS;
+    if (threadIdx.x < RADIX) first[threadIdx.x] = offs[(int64_t)threadIdx.x * ntile + blockIdx.x];
+    uint64_t k[SORT_ITEMS];
+    int d[SORT_ITEMS];
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+        const bool ok = base + i < n;
+        k[i] = ok ? kin[base + i] : 0;
+        d[i] = ok ? (int)((k[i] >> shift) & (RADIX - 1)) : -1;
+    }
+#pragma unroll
+    for (int dd = 0; dd < RADIX; ++dd) {
+        int cnt = 0;
+#pragma unroll
+        for (int i = 0; i < SORT_ITEMS; ++i) cnt += d[i] == dd;
+        rank[dd * SORT_THREADS + threadIdx.x] = block_excl_scan(cnt, ws, nullptr);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SORT_ITEMS; ++i) {
+        if (d[i] < 0) continue;
+        int &r = rank[d[i] * SORT_THREADS + threadIdx.x];   // this thread's column: no other writer
+        const int64_t pos = (int64_t)first[d[i]] + r;
+        ++r;
+        kout[pos] = k[i];
+        if (vin) vout[pos] = vin[base + i];
+    }
+}
+
+}  // namespace
+
+// Stable sort of n 64-bit keys (and int32 values when vin is given) into
+// kout / vout; kin / vin are left unchanged.
+int dev_sort_u64(tefmm_plan_s *P, const uint64_t *kin, uint64_t *kout, const int *vin, int *vout, int64_t n,
+                 cudaStream_t st) {
+    if (n <= 0) return TEFMM_OK;
+    const int64_t ntile = ceil_div(n, SORT_TILE);
+    const int64_t nc = RADIX * ntile;
+    // scratch: keys [n], values [n], counts [nc], offsets [nc]
+    const size_t kb = (size_t)n * 8, vb = vin ? (size_t)n * 4 : 0, cb = (size_t)nc * 4;
+    TRY(dbuf_ensure(P->sort_tmp, kb + vb + 2 * cb + 64));
+    unsigned char *t = (unsigned char *)P->sort_tmp.p;
+    uint64_t *ktmp = (uint64_t *)t;
+    int *vtmp = vin ? (int *)(t + kb) : nullptr;
+    int *counts = (int *)(t + kb + vb);
+    int *offs = counts + nc;
+    TRY(dbuf_ensure(P->scan_tmp, (size_t)scan_scratch(nc) * sizeof(int)));
+    for (int pass = 0; pass < 64 / RADIX_BITS; ++pass) {
+        const uint64_t *ks = pass == 0 ? kin : (pass % 2 == 1 ? ktmp : kout);
+        const int *vs = vin ? (pass == 0 ? vin : (pass % 2 == 1 ? vtmp : vout)) : nullptr;
+        uint64_t *kd = pass % 2 == 0 ? ktmp : kout;
+        int *vd = vin ? (pass % 2 == 0 ? vtmp : vout) : nullptr;
+        const int shift = pass * RADIX_BITS;
+        k_radix_count<<<(unsigned)ntile, SORT_THREADS, 0, st>>>(ks, n, shift, (int)ntile, counts);
+        CUDA_TRY(cudaGetLastError());
+        TRY(scan_rec(counts, offs, nc, false, dp<int>(P->scan_tmp), st));
+        k_radix_scatter<<<(unsigned)ntile, SORT_THREADS, 0, st>>>(ks, vs, kd, vd, n, shift, (int)ntile, offs);
+        CUDA_TRY(cudaGetLastError());
+        P->launches += 3;
+    }
+    return TEFMM_OK;
+}

@@ -17,7 +17,6 @@
 //   D(t): coarser adjacent source leaves handed down to t,
 //   X(t): source leaves not adjacent to t handed down from its parent,
 //   V(t): children of C(parent) boxes that are not adjacent to t.
-#include <cub/cub.cuh>
 
 #include <string.h>
 
@@ -668,18 +667,10 @@ __global__ void k_layer_mismatch(int n_nodes, const int *__restrict__ layer,
 }
 
 int scan_excl(tefmm_plan_s *P, const int *in, int *out, int64_t n, cudaStream_t st) {
-    size_t bytes = 0;
-    cub::DeviceScan::ExclusiveSum(nullptr, bytes, in, out, (int)n, st);
-    TRY(dbuf_ensure(P->scan_tmp, bytes));
-    CUDA_TRY(cub::DeviceScan::ExclusiveSum(P->scan_tmp.p, bytes, in, out, (int)n, st));
-    return TEFMM_OK;
+    return dev_scan_i32(P, in, out, n, false, st);
 }
 int scan_incl(tefmm_plan_s *P, const int *in, int *out, int64_t n, cudaStream_t st) {
-    size_t bytes = 0;
-    cub::DeviceScan::InclusiveSum(nullptr, bytes, in, out, (int)n, st);
-    TRY(dbuf_ensure(P->scan_tmp, bytes));
-    CUDA_TRY(cub::DeviceScan::InclusiveSum(P->scan_tmp.p, bytes, in, out, (int)n, st));
-    return TEFMM_OK;
+    return dev_scan_i32(P, in, out, n, true, st);
 }
 
 // grow node arrays keeping their contents
@@ -793,14 +784,8 @@ int tree_build(tefmm_plan_s *P, const double *sx, const double *sy, const double
                                                   dp<uint64_t>(P->keys_in), dp<int>(P->vals_in),
                                                   dp<int>(P->flags));
     P->launches++;
-    size_t bytes = 0;
-    cub::DeviceRadixSort::SortPairs(nullptr, bytes, dp<uint64_t>(P->keys_in),
-                                    dp<uint64_t>(P->keys_out), dp<int>(P->vals_in),
-                                    dp<int>(P->vals_out), (int)nitems, 0, 64, st);
-    TRY(dbuf_ensure(P->cub_tmp, bytes));
-    CUDA_TRY(cub::DeviceRadixSort::SortPairs(P->cub_tmp.p, bytes, dp<uint64_t>(P->keys_in),
-                                             dp<uint64_t>(P->keys_out), dp<int>(P->vals_in),
-                                             dp<int>(P->vals_out), (int)nitems, 0, 64, st));
+    TRY(dev_sort_u64(P, dp<uint64_t>(P->keys_in), dp<uint64_t>(P->keys_out), dp<int>(P->vals_in),
+                     dp<int>(P->vals_out), nitems, st));
     const uint64_t *keys = dp<uint64_t>(P->keys_out);
 
     // counting scans and sorted particle arrays
@@ -1010,12 +995,7 @@ int lists_build(tefmm_plan_s *P, cudaStream_t st) {
                                                         dp<int>(P->near_ptr), dp<int>(P->near_src),
                                                         dp<int>(P->near_fl), dp<unsigned long long>(P->fon_key));
         P->launches++;
-        size_t bytes = 0;
-        cub::DeviceRadixSort::SortKeys(nullptr, bytes, dp<unsigned long long>(P->fon_key),
-                                       dp<unsigned long long>(P->fon_key_sorted), (int)ne, 0, 64, st);
-        TRY(dbuf_ensure(P->cub_tmp, bytes));
-        CUDA_TRY(cub::DeviceRadixSort::SortKeys(P->cub_tmp.p, bytes, dp<unsigned long long>(P->fon_key),
-                                                dp<unsigned long long>(P->fon_key_sorted), (int)ne, 0, 64, st));
+        TRY(dev_sort_u64(P, dp<uint64_t>(P->fon_key), dp<uint64_t>(P->fon_key_sorted), nullptr, nullptr, ne, st));
         k_fon_heads<<<grid_for(ne, 256), 256, 0, st>>>(ne, dp<unsigned long long>(P->fon_key_sorted),
                                                        dp<int>(P->fon_cnt));
         P->launches++;
