@@ -399,6 +399,16 @@ int tefmm_plan_get_alg2_table(tefmm_plan plan, int layer, int tag, int *n, int *
 int tefmm_debug_inject(int kind, int n);
 int tefmm_debug_wait_probe(tefmm_plan plan, int ms, void *stream);
 
+/* The library's own primitives on caller DEVICE buffers, for their tests:
+ * tefmm_debug_sort_u64 sorts n 64-bit keys (and, when d_vals_in is not NULL,
+ * their int32 values) stably into d_keys_out / d_vals_out, leaving the inputs
+ * unchanged; tefmm_debug_scan_i32 writes the exclusive (inclusive != 0:
+ * inclusive) prefix sums of n int32 values.  Both allocate their scratch,
+ * synchronise the stream and free it.  Errors: INVALID_ARG, OOM, CUDA. */
+int tefmm_debug_sort_u64(const uint64_t *d_keys_in, uint64_t *d_keys_out, const int *d_vals_in,
+                         int *d_vals_out, int64_t n, void *stream);
+int tefmm_debug_scan_i32(const int *d_in, int *d_out, int64_t n, int inclusive, void *stream);
+
 /* ---- fit without device allocation -------------------------------------
  * The paper has no counterpart to this call; it is a convenience of this
  * library.  It runs the same device DCIM fit as tefmm_plan_create (same

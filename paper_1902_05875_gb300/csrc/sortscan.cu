@@ -202,3 +202,26 @@ int dev_sort_u64(tefmm_plan_s *P, const uint64_t *kin, uint64_t *kout, const int
     }
     return TEFMM_OK;
 }
+
+// ---- test hooks: the primitives on caller buffers (scratch from a throwaway plan record)
+extern "C" int tefmm_debug_sort_u64(const uint64_t *d_keys_in, uint64_t *d_keys_out, const int *d_vals_in,
+                                    int *d_vals_out, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!d_keys_in || !d_keys_out || (d_vals_in && !d_vals_out)))) return TEFMM_ERR_INVALID_ARG;
+    tefmm_plan_s tmp;
+    const int r = dev_sort_u64(&tmp, d_keys_in, d_keys_out, d_vals_in, d_vals_out, n, (cudaStream_t)stream);
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    dbuf_free(tmp.sort_tmp);
+    dbuf_free(tmp.scan_tmp);
+    if (r != TEFMM_OK) return r;
+    return e == cudaSuccess ? TEFMM_OK : TEFMM_ERR_CUDA;
+}
+
+extern "C" int tefmm_debug_scan_i32(const int *d_in, int *d_out, int64_t n, int inclusive, void *stream) {
+    if (n < 0 || (n > 0 && (!d_in || !d_out))) return TEFMM_ERR_INVALID_ARG;
+    tefmm_plan_s tmp;
+    const int r = dev_scan_i32(&tmp, d_in, d_out, n, inclusive != 0, (cudaStream_t)stream);
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    dbuf_free(tmp.scan_tmp);
+    if (r != TEFMM_OK) return r;
+    return e == cudaSuccess ? TEFMM_OK : TEFMM_ERR_CUDA;
+}

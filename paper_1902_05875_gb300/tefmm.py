@@ -64,6 +64,7 @@ EXPORTED = [
     "tefmm_eval_batched", "tefmm_set_points", "tefmm_apply", "tefmm_plan_set_cross_images",
     "tefmm_plan_status", "tefmm_batch_graph_create", "tefmm_batch_graph_launch", "tefmm_batch_graph_destroy",
     "tefmm_debug_inject", "tefmm_debug_wait_probe", "tefmm_plan_get_alg2_table",
+    "tefmm_debug_sort_u64", "tefmm_debug_scan_i32",
 ]
 
 _lib = None
@@ -108,6 +109,8 @@ def load(build_if_needed=True):
     lib.tefmm_plan_set_cross_images.argtypes = [P, ctypes.c_int, I, I, D, D]
     lib.tefmm_plan_status.argtypes = [P, P]
     lib.tefmm_plan_get_alg2_table.argtypes = [P, ctypes.c_int, ctypes.c_int, I, I, D, D]
+    lib.tefmm_debug_sort_u64.argtypes = [P, P, P, P, i64, P]
+    lib.tefmm_debug_scan_i32.argtypes = [P, P, i64, ctypes.c_int, P]
     lib.tefmm_debug_inject.argtypes = [ctypes.c_int, ctypes.c_int]
     lib.tefmm_debug_wait_probe.argtypes = [P, ctypes.c_int, P]
     lib.tefmm_batch_graph_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p),
