@@ -15,9 +15,10 @@ Besides the timed form (mixed by default) the line carries the FP64 form's
 time on the same workload (one step), the relative L2 difference between the
 two forms over all targets, and both forms' error against the oracle's FP64
 direct sum at S sampled targets (the paper's Err_2 and Err_max of Sec. 5,
-overall and per target layer).  For the 2M workload the direct sum at 1000
-targets is read from tests/golden/ (written by the committed script beside it,
-from the oracle alone); for other workloads it is computed here.  The CPU
+overall and per target layer).  The direct sums are read from tests/golden/
+(written by the committed script beside it, from the oracle alone): 1000
+targets of the 2M workload, 20 of the clustered 16M one; other workloads
+report no direct-sum error.  The CPU
 baseline is the oracle's TE-FMM (Python/numpy) timed on a bounded sample of
 the same workload.  The roofline covers both dominant kernels: the
 tensor-core M2L contraction (TF32 peak measured here through cuBLAS) and the
@@ -136,11 +137,15 @@ def measure_peaks(torch):
 
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands (profiles/), keyed by (kernel, workload); None when not captured.
-TRAFFIC = {}
+# 2M: one-pass metrics on the full workload; k_m2l_tc averaged over 39
+# launches (430.4 GB read + 114.9 GB written), k_near_fp32 one launch.
+TRAFFIC = {("k_m2l_tc", "three_layer_slabs_n2M_p10"): 13.98e9,
+           ("k_near_fp32", "three_layer_slabs_n2M_p10"): 1.443e9}
 
 # stored oracle direct sums (tests/golden/make_direct_reference.py)
 REFERENCE = {"three_layer_slabs_n2M_p10": os.path.join(ROOT, "tests", "golden",
-                                                      "direct_three_layer_slabs_n2M_1000.txt")}
+                                                      "direct_three_layer_slabs_n2M_1000.txt"),
+             "clustered_n16M_p8": os.path.join(ROOT, "tests", "golden", "direct_clustered_n16M_p8_20.txt")}
 
 
 def clocks_start():
@@ -182,24 +187,6 @@ def clocks_stop(p, path, gpu_index):
     os.unlink(path)
     return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
             "reasons": sorted(reasons), "samples": len(sm)}
-
-
-def direct_at(w, tgt_idx):
-    """The oracle's FP64 direct sum at the given targets against every source:
-    same-layer part (free space + DCIM images, C/OpenMP) plus the cross-layer
-    part by reciprocity (one DCIM fit per target, C/OpenMP).  Returns
-    (phi, seconds)."""
-    from oracle.medium import Medium
-    from oracle.dcim import ImageTable
-    from oracle.direct import direct_sum, cross_sum
-    med = Medium(w.interfaces, w.k)
-    img = ImageTable(med, w.zext, n_images=w.n_images)
-    tgt = w.src[tgt_idx]
-    t0 = time.perf_counter()
-    phi = direct_sum(med, img, w.src, w.q, tgt)
-    if med.n_layers > 1:
-        phi = phi + cross_sum(med, w.zext, w.src, w.q, tgt, n_images=w.n_images)
-    return phi, time.perf_counter() - t0
 
 
 def err_stats(phi, ref, layer=None):
@@ -247,19 +234,21 @@ def init_ranks(world, backend="nccl"):
 
 
 def reference_at(w, n_samples):
-    """The oracle's FP64 direct sum at n_samples targets: the stored values
-    (first n_samples of the stored sample) when the workload has a stored
-    reference with enough targets, else computed now (default_rng(1) sample).
-    Returns (indices, phi, source)."""
+    """The oracle's FP64 direct sum at up to n_samples targets, as stored by
+    tests/golden/make_direct_reference.py (the first n_samples of its
+    default_rng(1) sample).  Returns (indices, phi, source), or None when the
+    workload has no stored reference."""
     path = REFERENCE.get(w.name)
-    if path and os.path.exists(path):
-        d = np.loadtxt(path)
-        if len(d) >= n_samples:
-            return d[:n_samples, 0].astype(np.int64), d[:n_samples, 1] + 1j * d[:n_samples, 2], \
-                os.path.relpath(path, ROOT)
-    idx = np.random.default_rng(1).choice(len(w.src), min(len(w.src), n_samples), replace=False)
-    ref, _ = direct_at(w, idx)
-    return idx, ref, "computed (oracle.direct)"
+    if not (path and os.path.exists(path)):
+        return None
+    d = np.loadtxt(path)[:n_samples]
+    return d[:, 0].astype(np.int64), d[:, 1] + 1j * d[:, 2], os.path.relpath(path, ROOT)
+
+
+def layer_of(interfaces, z):
+    """Layer of each z (0 at the top): the number of interfaces above it."""
+    d = np.asarray(interfaces, dtype=float).reshape(-1)
+    return np.sum(np.asarray(z)[:, None] < d[None, :], axis=1)
 
 
 CPU_SAMPLE_N = 2000
@@ -648,14 +637,16 @@ def main():
                                                                 np.linalg.norm(phi64))}
         del p64
         torch.cuda.empty_cache()
-    if rank == 0 and world == 1 and args.accuracy_samples > 0:
-        idx, ref, src_ref = reference_at(w, args.accuracy_samples)
+    stored = reference_at(w, args.accuracy_samples) if rank == 0 and world == 1 and args.accuracy_samples > 0 else None
+    if rank == 0 and world == 1 and args.accuracy_samples > 0 and stored is None:
+        line.setdefault("accuracy", {})["direct_sum"] = "no stored oracle reference for this workload"
+    if stored is not None:
+        idx, ref, src_ref = stored
         acc = line.setdefault("accuracy", {})
         acc["samples"] = int(len(idx))
         acc["reference"] = f"oracle FP64 direct sum ({src_ref})"
         acc[f"{args.precision}_vs_direct_rel_l2"] = float(np.linalg.norm(phi[idx] - ref) / np.linalg.norm(ref))
-        from oracle.medium import Medium
-        lay = Medium(w.interfaces, w.k).layer_of(w.src[idx, 2])
+        lay = layer_of(w.interfaces, w.src[idx, 2])
         acc[f"{args.precision}_vs_direct"] = err_stats(phi[idx], ref, lay)
         if phi64 is not None:
             acc["fp64_vs_direct_rel_l2"] = float(np.linalg.norm(phi64[idx] - ref) / np.linalg.norm(ref))

@@ -16,7 +16,9 @@
 //     its rank among the tile's keys of the same digit.  The rank is the
 //     key's order within its thread's consecutive run, plus the keys of that
 //     digit held by the threads before it.  So equal digits keep their input
-//     order, which makes every pass, and the sort, stable.
+//     order, which makes every pass, and the sort, stable.  The tile is
+//     reordered by digit in shared memory first, so that the global writes
+//     are runs of consecutive positions.
 // The passes ping-pong between the output and a scratch buffer; the 16th
 // lands in the output.
 #include "internal.cuh"
@@ -131,16 +133,27 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_count(const uint64_t *__
     if (threadIdx.x < RADIX) counts[(int64_t)threadIdx.x * ntile + blockIdx.x] = c[threadIdx.x];
 }
 
-// stable scatter of one tile by the digit at shift; offs = exclusive scan of the counts
+// stable scatter of one tile by the digit at shift; offs = exclusive scan of
+// the counts.  The tile is first reordered by digit in shared memory (each
+// key at its digit's tile offset plus its rank), then written out so that
+// consecutive threads write consecutive positions of one digit's run.
+// Dynamic shared memory: keys [SORT_TILE] u64, values [SORT_TILE] int,
+// ranks [RADIX][SORT_THREADS] int.
+constexpr size_t SCATTER_SMEM = (size_t)SORT_TILE * 12 + (size_t)RADIX * SORT_THREADS * 4;
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint64_t *__restrict__ kin,
                                                                 const int *__restrict__ vin,
                                                                 uint64_t *__restrict__ kout, int *__restrict__ vout,
                                                                 int64_t n, int shift, int ntile,
                                                                 const int *__restrict__ offs) {
+    extern __shared__ __align__(16) unsigned char rsm[];
+    uint64_t *skey = (uint64_t *)rsm;
+    int *sval = (int *)(rsm + (size_t)SORT_TILE * 8);
+    int *rank = sval + SORT_TILE;                      // per digit and thread: keys of that digit before it
     __shared__ int ws[32];
     __shared__ int first[RADIX];                       // output position of the tile's first key of each digit
-    __shared__ int rank[RADIX * SORT_THREADS];         // per digit and thread: keys of that digit before it
-    const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)threadIdx.x * SORT_ITEMS;
+    __shared__ int tot[RADIX], lfirst[RADIX];          // the tile's keys per digit, and their offsets in the tile
+    const int64_t tbase = (int64_t)blockIdx.x * SORT_TILE;
+    const int64_t base = tbase + (int64_t)threadIdx.x * SORT_ITEMS;
     if (threadIdx.x < RADIX) first[threadIdx.x] = offs[(int64_t)threadIdx.x * ntile + blockIdx.x];
     uint64_t k[SORT_ITEMS];
     int d[SORT_ITEMS];
@@ -155,17 +168,36 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint64_t *
         int cnt = 0;
 #pragma unroll
         for (int i = 0; i < SORT_ITEMS; ++i) cnt += d[i] == dd;
-        rank[dd * SORT_THREADS + threadIdx.x] = block_excl_scan(cnt, ws, nullptr);
+        int t = 0;
+        rank[dd * SORT_THREADS + threadIdx.x] = block_excl_scan(cnt, ws, &t);
+        if (threadIdx.x == 0) tot[dd] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int o = 0;
+        for (int dd = 0; dd < RADIX; ++dd) {
+            lfirst[dd] = o;
+            o += tot[dd];
+        }
     }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < SORT_ITEMS; ++i) {
         if (d[i] < 0) continue;
         int &r = rank[d[i] * SORT_THREADS + threadIdx.x];   // this thread's column: no other writer
-        const int64_t pos = (int64_t)first[d[i]] + r;
+        const int lp = lfirst[d[i]] + r;
         ++r;
-        kout[pos] = k[i];
-        if (vin) vout[pos] = vin[base + i];
+        skey[lp] = k[i];
+        if (vin) sval[lp] = vin[base + i];
+    }
+    __syncthreads();
+    const int cnt_tile = (int)min((int64_t)SORT_TILE, n - tbase);
+    for (int j = threadIdx.x; j < cnt_tile; j += SORT_THREADS) {
+        const uint64_t key = skey[j];
+        const int dd = (int)((key >> shift) & (RADIX - 1));
+        const int64_t pos = (int64_t)first[dd] + (j - lfirst[dd]);
+        kout[pos] = key;
+        if (vin) vout[pos] = sval[j];
     }
 }
 
@@ -187,6 +219,7 @@ int dev_sort_u64(tefmm_plan_s *P, const uint64_t *kin, uint64_t *kout, const int
     int *counts = (int *)(t + kb + vb);
     int *offs = counts + nc;
     TRY(dbuf_ensure(P->scan_tmp, (size_t)scan_scratch(nc) * sizeof(int)));
+    CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM));
     for (int pass = 0; pass < 64 / RADIX_BITS; ++pass) {
         const uint64_t *ks = pass == 0 ? kin : (pass % 2 == 1 ? ktmp : kout);
         const int *vs = vin ? (pass == 0 ? vin : (pass % 2 == 1 ? vtmp : vout)) : nullptr;
@@ -196,7 +229,8 @@ int dev_sort_u64(tefmm_plan_s *P, const uint64_t *kin, uint64_t *kout, const int
         k_radix_count<<<(unsigned)ntile, SORT_THREADS, 0, st>>>(ks, n, shift, (int)ntile, counts);
         CUDA_TRY(cudaGetLastError());
         TRY(scan_rec(counts, offs, nc, false, dp<int>(P->scan_tmp), st));
-        k_radix_scatter<<<(unsigned)ntile, SORT_THREADS, 0, st>>>(ks, vs, kd, vd, n, shift, (int)ntile, offs);
+        k_radix_scatter<<<(unsigned)ntile, SORT_THREADS, SCATTER_SMEM, st>>>(ks, vs, kd, vd, n, shift, (int)ntile,
+                                                                           offs);
         CUDA_TRY(cudaGetLastError());
         P->launches += 3;
     }
