@@ -19,8 +19,11 @@
 //     order, which makes every pass, and the sort, stable.  The tile is
 //     reordered by digit in shared memory first, so that the global writes
 //     are runs of consecutive positions.
-// The passes ping-pong between the output and a scratch buffer; the 16th
-// lands in the output.
+// Only the passes over digits that differ between keys run (one OR/AND
+// reduction of the keys finds them); they ping-pong between the output and a
+// scratch buffer so that the last one lands in the output.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace {
@@ -139,6 +142,24 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_count(const uint64_t *__
 // consecutive threads write consecutive positions of one digit's run.
 // Dynamic shared memory: keys [SORT_TILE] u64, values [SORT_TILE] int,
 // ranks [RADIX][SORT_THREADS] int.
+// OR and AND of all keys: the bits that vary are OR ^ AND
+__global__ void k_key_bits(const uint64_t *__restrict__ keys, int64_t n, unsigned long long *__restrict__ orand) {
+    unsigned long long o = 0ULL, a = ~0ULL;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        o |= keys[i];
+        a &= keys[i];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        o |= __shfl_xor_sync(0xffffffffu, o, off);
+        a &= __shfl_xor_sync(0xffffffffu, a, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicOr(&orand[0], o);
+        atomicAnd(&orand[1], a);
+    }
+}
+
 constexpr size_t SCATTER_SMEM = (size_t)SORT_TILE * 12 + (size_t)RADIX * SORT_THREADS * 4;
 __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const uint64_t *__restrict__ kin,
                                                                 const int *__restrict__ vin,
@@ -220,19 +241,41 @@ int dev_sort_u64(tefmm_plan_s *P, const uint64_t *kin, uint64_t *kout, const int
     int *offs = counts + nc;
     TRY(dbuf_ensure(P->scan_tmp, (size_t)scan_scratch(nc) * sizeof(int)));
     CUDA_TRY(cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM));
-    for (int pass = 0; pass < 64 / RADIX_BITS; ++pass) {
-        const uint64_t *ks = pass == 0 ? kin : (pass % 2 == 1 ? ktmp : kout);
-        const int *vs = vin ? (pass == 0 ? vin : (pass % 2 == 1 ? vtmp : vout)) : nullptr;
-        uint64_t *kd = pass % 2 == 0 ? ktmp : kout;
-        int *vd = vin ? (pass % 2 == 0 ? vtmp : vout) : nullptr;
-        const int shift = pass * RADIX_BITS;
-        k_radix_count<<<(unsigned)ntile, SORT_THREADS, 0, st>>>(ks, n, shift, (int)ntile, counts);
+    // digits that are equal in every key leave the order unchanged: only the
+    // passes over digits that vary run
+    unsigned long long *orand = (unsigned long long *)(t + ((kb + vb + 2 * cb + 15) & ~(size_t)15));
+    unsigned long long init[2] = {0ULL, ~0ULL}, got[2] = {0ULL, 0ULL};
+    CUDA_TRY(cudaMemcpyAsync(orand, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    k_key_bits<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1216), 256, 0, st>>>(kin, n, orand);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(got, orand, sizeof(got), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    P->launches += 1;
+    const unsigned long long vary = got[0] ^ got[1];
+    int shifts[64 / RADIX_BITS], m = 0;
+    for (int pass = 0; pass < 64 / RADIX_BITS; ++pass)
+        if ((vary >> (pass * RADIX_BITS)) & (RADIX - 1)) shifts[m++] = pass * RADIX_BITS;
+    if (m == 0) {                                      // all keys equal: the input order is the order
+        CUDA_TRY(cudaMemcpyAsync(kout, kin, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
+        if (vin) CUDA_TRY(cudaMemcpyAsync(vout, vin, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+        return TEFMM_OK;
+    }
+    // ping-pong so that the last pass writes the output
+    const uint64_t *ks = kin;
+    const int *vs = vin;
+    for (int j = 0; j < m; ++j) {
+        const bool to_out = (m - 1 - j) % 2 == 0;
+        uint64_t *kd = to_out ? kout : ktmp;
+        int *vd = vin ? (to_out ? vout : vtmp) : nullptr;
+        k_radix_count<<<(unsigned)ntile, SORT_THREADS, 0, st>>>(ks, n, shifts[j], (int)ntile, counts);
         CUDA_TRY(cudaGetLastError());
         TRY(scan_rec(counts, offs, nc, false, dp<int>(P->scan_tmp), st));
-        k_radix_scatter<<<(unsigned)ntile, SORT_THREADS, SCATTER_SMEM, st>>>(ks, vs, kd, vd, n, shift, (int)ntile,
-                                                                           offs);
+        k_radix_scatter<<<(unsigned)ntile, SORT_THREADS, SCATTER_SMEM, st>>>(ks, vs, kd, vd, n, shifts[j],
+                                                                           (int)ntile, offs);
         CUDA_TRY(cudaGetLastError());
         P->launches += 3;
+        ks = kd;
+        vs = vd;
     }
     return TEFMM_OK;
 }
