@@ -142,21 +142,29 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_count(const uint64_t *__
 // consecutive threads write consecutive positions of one digit's run.
 // Dynamic shared memory: keys [SORT_TILE] u64, values [SORT_TILE] int,
 // ranks [RADIX][SORT_THREADS] int.
-// OR and AND of all keys: the bits that vary are OR ^ AND
+// OR and AND of the keys other than ~0 (the "no item" key of the M2L
+// builder), and whether a ~0 key occurs: orand = {OR, AND, any ~0}
 __global__ void k_key_bits(const uint64_t *__restrict__ keys, int64_t n, unsigned long long *__restrict__ orand) {
-    unsigned long long o = 0ULL, a = ~0ULL;
+    unsigned long long o = 0ULL, a = ~0ULL, inv = 0ULL;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        o |= keys[i];
-        a &= keys[i];
+        const unsigned long long k = keys[i];
+        if (k == ~0ULL) {
+            inv = 1ULL;
+        } else {
+            o |= k;
+            a &= k;
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         o |= __shfl_xor_sync(0xffffffffu, o, off);
         a &= __shfl_xor_sync(0xffffffffu, a, off);
+        inv |= __shfl_xor_sync(0xffffffffu, inv, off);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicOr(&orand[0], o);
         atomicAnd(&orand[1], a);
+        atomicOr(&orand[2], inv);
     }
 }
 
@@ -244,17 +252,30 @@ int dev_sort_u64(tefmm_plan_s *P, const uint64_t *kin, uint64_t *kout, const int
     // digits that are equal in every key leave the order unchanged: only the
     // passes over digits that vary run
     unsigned long long *orand = (unsigned long long *)(t + ((kb + vb + 2 * cb + 15) & ~(size_t)15));
-    unsigned long long init[2] = {0ULL, ~0ULL}, got[2] = {0ULL, 0ULL};
+    unsigned long long init[3] = {0ULL, ~0ULL, 0ULL}, got[3] = {0ULL, 0ULL, 0ULL};
     CUDA_TRY(cudaMemcpyAsync(orand, init, sizeof(init), cudaMemcpyHostToDevice, st));
     k_key_bits<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 1216), 256, 0, st>>>(kin, n, orand);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(got, orand, sizeof(got), cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     P->launches += 1;
-    const unsigned long long vary = got[0] ^ got[1];
+    // among the keys other than ~0, a digit equal in all of them leaves their
+    // order unchanged.  When ~0 keys occur, one such digit whose common value
+    // is below 15 also runs: there every other key is below ~0, so the ~0
+    // keys still sort last.
+    const unsigned long long vary = got[0] ^ got[1], common = got[1];
+    const bool has_inv = got[2] != 0ULL && got[1] != ~0ULL;   // (got[1] == ~0: every key is ~0)
     int shifts[64 / RADIX_BITS], m = 0;
-    for (int pass = 0; pass < 64 / RADIX_BITS; ++pass)
-        if ((vary >> (pass * RADIX_BITS)) & (RADIX - 1)) shifts[m++] = pass * RADIX_BITS;
+    bool sep = !has_inv;
+    for (int pass = 0; pass < 64 / RADIX_BITS; ++pass) {
+        const int sh = pass * RADIX_BITS;
+        const bool varies = (vary >> sh) & (RADIX - 1);
+        const bool below = ((common >> sh) & (RADIX - 1)) != (RADIX - 1);
+        if (varies || (!sep && below)) {
+            shifts[m++] = sh;
+            if (!varies) sep = true;
+        }
+    }
     if (m == 0) {                                      // all keys equal: the input order is the order
         CUDA_TRY(cudaMemcpyAsync(kout, kin, (size_t)n * 8, cudaMemcpyDeviceToDevice, st));
         if (vin) CUDA_TRY(cudaMemcpyAsync(vout, vin, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));

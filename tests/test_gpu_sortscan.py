@@ -1,8 +1,9 @@
 """The library's own radix sort and prefix sums (csrc/sortscan.cu) on the GPU,
 through their test hooks, against numpy: the sort against a stable argsort
-(keys with many duplicates, values = input positions, so stability is
-checked exactly), the scans against cumulative sums; sizes around the tile
-lengths (4096 keys, 2048 values) and empty input."""
+(keys with many duplicates, most digits equal in every key so that the sort
+skips their passes, 10% of them the all-ones key, values = input positions,
+so stability is checked exactly), the scans against cumulative sums; sizes
+around the tile lengths (4096 keys, 2048 values) and empty input."""
 import ctypes
 
 import numpy as np
@@ -29,6 +30,9 @@ def test_sort_is_a_stable_argsort(n):
     # high and low bits both vary; few distinct keys, so runs of equal keys are long
     keys = (rng.integers(0, 64, n).astype(np.uint64) << np.uint64(58)) | \
         rng.integers(0, 8, n).astype(np.uint64) | (rng.integers(0, 4, n).astype(np.uint64) << np.uint64(29))
+    # the M2L builder's "no item" key ~0 among them (it must sort last although
+    # most digits of the other keys are equal)
+    keys[rng.random(n) < 0.1] = np.uint64(0xFFFFFFFFFFFFFFFF)
     vals = np.arange(n, dtype=np.int32)
     kin = torch.tensor(keys.view(np.int64), device="cuda")
     vin = torch.tensor(vals, device="cuda")
