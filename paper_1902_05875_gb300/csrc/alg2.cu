@@ -298,18 +298,16 @@ A2View a2_view(tefmm_plan_s *P) {
 
 namespace {
 
-bool g_gl_ready[64];
-
 int build_table(tefmm_plan_s *P, Alg2Table &t, cudaStream_t st) {
-    int dev = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return TEFMM_ERR_CUDA;
-    if (!g_gl_ready[dev]) {
+    // the quadrature rule goes to the current device's constant memory before
+    // every build (128 bytes; no per-process flag that a device reset or a
+    // second host thread could leave stale)
+    {
         double x[A2_GL], w[A2_GL];
         gauss_legendre(A2_GL, x, w);
-        CUDA_TRY(cudaMemcpyToSymbol(c_gl_x, x, sizeof(x)));
-        CUDA_TRY(cudaMemcpyToSymbol(c_gl_w, w, sizeof(w)));
-        g_gl_ready[dev] = true;
+        CUDA_TRY(cudaMemcpyToSymbolAsync(c_gl_x, x, sizeof(x), 0, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaMemcpyToSymbolAsync(c_gl_w, w, sizeof(w), 0, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
     }
     A2Build B{};
     B.J.mode = 0;
